@@ -1,0 +1,208 @@
+"""The JGS2 Jacobi sweep and the time-step driver (Secs. 3-5, 8.1).
+
+Per sweep k, from x^k only (Jacobi, Sec. 8.1: all vertex sub-problems at once, N_i = 3):
+  g_i, H_ii    gradient and diagonal 3x3 block of E at x^k (Eq. reduced_local terms)
+  R_v          polar factor (det +1) of the volume-weighted mean deformation gradient of
+               the tets around v (Sec. 4.3; reading R5)
+  U_{i,a}      = R_a U_bar_{i,a} R_i^T                                   (Eq. tilde_phi)
+  H~_i         = sum_s w_s [U_i]_s^T H_hat_{e_s}(x^k) [U_i]_s             (Eq. cubature)
+  g~_i         = sum_s w_s sum_{a in e_s} U_{i,a}^T g_a(x^k)   (reading R3 "asm": the
+               assembled gradient at the element's vertices, so g~ -> 0 at equilibrium)
+  (H_ii + H~_i) d_i = -(g_i + g~_i)                                      (Eq. reduced_local)
+  x_i^{k+1} = x_i^k + d_i
+If H_ii + H~_i fails a Cholesky test the vertex takes the uncorrected step -H_ii^{-1} g_i
+(reading R7; H_ii itself is always positive definite for this material, see fem.py).
+
+Globalisation (reading R17): the per-vertex updates form a direction D; with line search
+on, x^{k+1} = x^k + alpha d with Armijo backtracking on the global energy over alpha = 2^-j,
+first along D, then along the uncorrected direction D_J (always a descent direction).
+Without it (the paper's plain Jacobi), x^{k+1} = x^k + D.
+
+Stopping (reading R9): r_k = |g(x^k)| / |g(x^0)| over free DOFs; stop at the first k with
+r_k <= rel_tol (returning x^k after k sweeps) or at max_sweeps.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import fem
+
+
+def polar_rotation(F):
+    """Rotation closest to F (det +1): U diag(1,1,det(U V^T)) V^T from the SVD."""
+    U, _, Vt = np.linalg.svd(F)
+    d = np.sign(np.linalg.det(U @ Vt))
+    D = np.ones(F.shape[:-2] + (3,))
+    D[..., 2] = d
+    return np.einsum("...ik,...k,...kj->...ij", U, D, Vt)
+
+
+def vertex_rotations(mesh: fem.Mesh, x):
+    """R_v = polar(F_v), F_v = sum_{e ni v} V_e F_e / sum_{e ni v} V_e (reading R5)."""
+    F = fem.deformation_gradient(mesh, x)
+    Fv = np.zeros((mesh.V, 3, 3))
+    wv = np.zeros(mesh.V)
+    for a in range(4):
+        np.add.at(Fv, mesh.tets[:, a], mesh.vol[:, None, None] * F)
+        np.add.at(wv, mesh.tets[:, a], mesh.vol)
+    Fv /= np.maximum(wv, 1e-300)[:, None, None]
+    return polar_rotation(Fv)
+
+
+@dataclass
+class SweepStats:
+    fallback: int = 0
+    ls_rejects: int = 0
+
+
+def element_gradients(mesh: fem.Mesh, x, z, h):
+    """Own gradient of E_hat_e per element corner (T,4,3): V_e P b_a + m_e/h^2 (x_a - z_a),
+    zero at pinned corners (the literal per-element term of Eq. cubature, reading "elem")."""
+    F = fem.deformation_gradient(mesh, x)
+    P = fem.snh_P(F, mesh.mu, mesh.lp)
+    ge = mesh.vol[:, None, None] * np.einsum("tij,taj->tai", P, mesh.b)
+    ge = ge + (mesh.rho * mesh.vol / 4.0 / h ** 2)[:, None, None] * (x - z)[mesh.tets]
+    ge[mesh.pinned[mesh.tets]] = 0.0
+    return ge
+
+
+def correction_terms(mesh: fem.Mesh, x, g, h, cub, R, psd=False, grad="asm", z=None):
+    """H~_i and g~_i of Eq. cubature for every vertex (zero for pinned / empty records)."""
+    He = fem.element_hessians(mesh, x, h, psd=psd, inertia=True)
+    ge = element_gradients(mesh, x, z, h) if grad == "elem" else None
+    V = mesh.V
+    Ht = np.zeros((V, 3, 3))
+    gt = np.zeros((V, 3))
+    for s in range(cub.n_cub):
+        e = cub.elem[:, s]
+        ok = (e >= 0) & ~mesh.pinned
+        if not ok.any():
+            continue
+        idx = np.nonzero(ok)[0]
+        es = e[ok]
+        corners = mesh.tets[es]                                   # (n,4)
+        Ra = R[corners]                                           # (n,4,3,3)
+        Ri = R[idx]                                               # (n,3,3)
+        U = np.einsum("naij,najk,nlk->nail", Ra, cub.ubar[idx, s], Ri)   # R_a Ub R_i^T
+        U12 = U.reshape(len(idx), 12, 3)
+        w = cub.weight[idx, s]
+        Ht[idx] += w[:, None, None] * np.einsum("npi,npq,nqj->nij", U12, He[es], U12)
+        ga = g[corners] if grad == "asm" else ge[es]              # (n,4,3)
+        gt[idx] += w[:, None] * np.einsum("naji,naj->ni", U, ga)
+    return Ht, gt
+
+
+def direction(mesh: fem.Mesh, x, z, h, cub=None, psd=False, grad="asm", stats=None):
+    """JGS2 direction D (x^{k+1} = x^k + D without line search), the uncorrected per-vertex
+    Newton direction D_J = -H_ii^{-1} g_i, and the gradient at x^k. cub=None: D = D_J."""
+    g = fem.vertex_gradient(mesh, x, z, h)
+    Hd = fem.vertex_diag_blocks(mesh, x, h)
+    if cub is not None:
+        R = vertex_rotations(mesh, x)
+        Ht, gt = correction_terms(mesh, x, g, h, cub, R, psd, grad, z)
+    else:
+        Ht = np.zeros_like(Hd)
+        gt = np.zeros_like(g)
+    D = np.zeros_like(x)
+    DJ = np.zeros_like(x)
+    for i in mesh.free:
+        LJ = np.linalg.cholesky(Hd[i])
+        DJ[i] = np.linalg.solve(LJ.T, np.linalg.solve(LJ, -g[i]))
+        try:
+            L = np.linalg.cholesky(Hd[i] + Ht[i])
+            D[i] = np.linalg.solve(L.T, np.linalg.solve(L, -(g[i] + gt[i])))
+        except np.linalg.LinAlgError:
+            D[i] = DJ[i]
+            if stats is not None:
+                stats.fallback += 1
+    return D, DJ, g
+
+
+def sweep(mesh: fem.Mesh, x, z, h, cub=None, psd=False, stats=None, grad="asm"):
+    """One Jacobi sweep without line search: x^{k+1} = x^k + D."""
+    D, _, _ = direction(mesh, x, z, h, cub, psd, grad, stats)
+    return x + D
+
+
+LS_TRIALS = 8
+ARMIJO_C = 1e-4
+
+
+def line_search(mesh: fem.Mesh, x, z, h, D, DJ, g, stats=None):
+    """Global backtracking on E (reading R17). Trials in order: the JGS2 direction D with
+    alpha_j = 2^-j (j < 8), then the uncorrected direction D_J with the same alphas; the
+    first trial with E(x + a d) - E(x) <= 1e-4 a g.d is taken (energy changes from
+    fem.energy_change, free of cancellation). If none passes the sweep does not move
+    (counted). Returns the step a*d."""
+    alphas = [1.0 / (1 << j) for j in range(LS_TRIALS)]
+    for d in (D, DJ):
+        slope = float(np.sum(g * d))
+        dE = fem.energy_change(mesh, x, z, h, d, alphas)
+        for a, de in zip(alphas, dE):
+            if de <= ARMIJO_C * a * slope:
+                return a * d
+    if stats is not None:
+        stats.ls_rejects += 1
+    return np.zeros_like(D)
+
+
+@dataclass
+class StepResult:
+    x: np.ndarray
+    v: np.ndarray
+    sweeps: int
+    residuals: list = field(default_factory=list)
+    fallback: int = 0
+    ls_rejects: int = 0
+    converged: bool = False
+
+
+def residual_norm(mesh, x, z, h):
+    return float(np.linalg.norm(fem.vertex_gradient(mesh, x, z, h)[mesh.free]))
+
+
+def run_sweeps(mesh: fem.Mesh, x, z, h, cub=None, n=1, psd=False, grad="asm", line_search_on=True):
+    """Exactly n sweeps from x (no convergence test)."""
+    x = np.array(x, dtype=np.float64, copy=True)
+    for _ in range(n):
+        D, DJ, g = direction(mesh, x, z, h, cub, psd, grad)
+        x = x + (line_search(mesh, x, z, h, D, DJ, g) if line_search_on else D)
+    return x
+
+
+def step(mesh: fem.Mesh, x_t, v_t, h, gravity, cub=None, rel_tol=1e-4, max_sweeps=100,
+         psd=False, grad="asm", line_search_on=True, record_x=False):
+    """One implicit-Euler step (Sec. 3) solved by JGS2 sweeps from x^0 = x_t (reading R8).
+
+    Sweep k computes g(x^k); r_k = |g(x^k)|/|g(x^0)|; the step stops at the first k with
+    r_k <= rel_tol or k = max_sweeps and returns x^k (k sweeps applied)."""
+    z = fem.inertia_target(x_t, v_t, h, gravity)
+    x = np.array(x_t, dtype=np.float64, copy=True)
+    stats = SweepStats()
+    res = []
+    xs = [] if record_x else None
+    g0 = None
+    k = 0
+    conv = False
+    while True:
+        D, DJ, g = direction(mesh, x, z, h, cub, psd, grad, stats)
+        gn = float(np.linalg.norm(g[mesh.free]))
+        if g0 is None:
+            g0 = gn
+        r = gn / g0 if g0 > 0 else 0.0
+        res.append(r)
+        if record_x:
+            xs.append(x.copy())
+        if r <= rel_tol or g0 == 0.0:
+            conv = True
+            break
+        if k >= max_sweeps:
+            break
+        x = x + (line_search(mesh, x, z, h, D, DJ, g, stats) if line_search_on else D)
+        k += 1
+    out = StepResult(x, (x - x_t) / h, k, res, stats.fallback, stats.ls_rejects, conv)
+    if record_x:
+        out.xs = xs
+    return out

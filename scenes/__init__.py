@@ -1,0 +1,266 @@
+"""Seeded synthetic scene generators shared by the CUDA path's tests/bench and the oracle.
+
+This module only builds inputs: lattice coordinates, tetrahedral connectivity, per-tet
+material parameters, pinned masks and initial velocities. It holds none of the method's
+arithmetic (no masses, no rest-shape inverses, no energies); each side derives those itself.
+
+The workloads mirror the paper's experiments (Sec. 8, Table 1): voxelised tetrahedral
+solids split into Kuhn tetrahedra, dropped under gravity, with a soft/stiff material mix.
+Every random draw uses numpy's PCG64 generator keyed by an explicit seed.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# The six Kuhn tetrahedra of a unit cube: each walks from corner 000 to corner 111 along
+# one permutation of the axes. Corner code = x + 2y + 4z.
+_PERMS = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+
+
+def _kuhn_local():
+    tets = []
+    for p in _PERMS:
+        c = [0, 0, 0]
+        path = [0]
+        for ax in p:
+            c[ax] = 1
+            path.append(c[0] + 2 * c[1] + 4 * c[2])
+        # orientation: even permutations give positive volume with this walk
+        a, b, d = np.eye(3)[p[0]], np.eye(3)[p[0]] + np.eye(3)[p[1]], np.ones(3)
+        if np.linalg.det(np.stack([a, b, d], axis=1)) < 0:
+            path[1], path[2] = path[2], path[1]
+        tets.append(path)
+    return np.array(tets, dtype=np.int64)
+
+
+KUHN = _kuhn_local()
+
+
+@dataclass
+class Scene:
+    """A tetrahedral scene. Arrays are in the caller's (generator's) vertex order."""
+    name: str
+    X: np.ndarray            # (V,3) float64 rest positions, also the initial positions
+    tets: np.ndarray         # (T,4) int32
+    youngs: np.ndarray       # (T,) float64 Pa
+    poisson: np.ndarray      # (T,) float64
+    density: np.ndarray      # (T,) float64 kg/m^3
+    pinned: np.ndarray       # (V,) uint8
+    v0: np.ndarray           # (V,3) float64 initial velocity
+    dt: float = 1.0 / 120.0
+    gravity: tuple = (0.0, 0.0, -9.8)
+    planes: np.ndarray = field(default_factory=lambda: np.zeros((0, 4)))  # (n, c): n.x >= c
+    dhat: float = 1e-3
+    kappa: float = 1e5
+    contact: int = 0
+    x0: np.ndarray | None = None  # initial positions if different from X
+
+    @property
+    def n_vertices(self):
+        return int(self.X.shape[0])
+
+    @property
+    def n_tets(self):
+        return int(self.tets.shape[0])
+
+
+def voxel_mesh(mask: np.ndarray, cell: tuple, origin=(0.0, 0.0, 0.0)):
+    """Kuhn-split every filled cell of a boolean (nx,ny,nz) cell mask.
+
+    Returns rest positions (V,3) and tets (T,4); vertices are numbered by first use in
+    x-fastest lattice order, cells are visited in the same order.
+    """
+    mask = np.asarray(mask, dtype=bool)
+    nx, ny, nz = mask.shape
+    cx, cy, cz = np.nonzero(mask.transpose(2, 1, 0))  # z, y, x order -> x fastest
+    cz, cy, cx = cx, cy, cz
+    order = np.lexsort((cx, cy, cz))
+    cx, cy, cz = cx[order], cy[order], cz[order]
+    corner = np.array([[i & 1, (i >> 1) & 1, (i >> 2) & 1] for i in range(8)])
+    lat = np.stack([cx, cy, cz], axis=1)[:, None, :] + corner[None, :, :]  # (C,8,3)
+    key = (lat[..., 2] * (ny + 1) + lat[..., 1]) * (nx + 1) + lat[..., 0]
+    uniq, inv = np.unique(key.ravel(), return_inverse=True)
+    inv = inv.reshape(key.shape)
+    tets = inv[:, KUHN].reshape(-1, 4)
+    gx = uniq % (nx + 1)
+    gy = (uniq // (nx + 1)) % (ny + 1)
+    gz = uniq // ((nx + 1) * (ny + 1))
+    X = np.stack([gx * cell[0], gy * cell[1], gz * cell[2]], axis=1) + np.asarray(origin)
+    return X.astype(np.float64), tets.astype(np.int32)
+
+
+def kuhn_grid(nvx, nvy, nvz, size):
+    """A box of nvx*nvy*nvz lattice vertices spanning `size`, every cell Kuhn-split."""
+    cell = (size[0] / (nvx - 1), size[1] / (nvy - 1), size[2] / (nvz - 1))
+    return voxel_mesh(np.ones((nvx - 1, nvy - 1, nvz - 1), bool), cell)
+
+
+def voxel_sphere(radius, cells_across, center=(0.0, 0.0, 0.0)):
+    """Cells of a cube lattice whose centres lie inside the sphere, Kuhn-split."""
+    n = int(cells_across)
+    h = 2.0 * radius / n
+    c = (np.arange(n) + 0.5) * h - radius
+    gx, gy, gz = np.meshgrid(c, c, c, indexing="ij")
+    mask = gx ** 2 + gy ** 2 + gz ** 2 <= radius ** 2
+    origin = np.asarray(center, dtype=np.float64) - radius
+    return voxel_mesh(mask, (h, h, h), origin)
+
+
+def _uniform_material(T, E, nu, rho):
+    return (np.full(T, float(E)), np.full(T, float(nu)), np.full(T, float(rho)))
+
+
+def cube_scene():
+    """5x5x5-vertex cube of side 0.1 m, 384 Kuhn tets, top face pinned, at rest."""
+    X, tets = kuhn_grid(5, 5, 5, (0.1, 0.1, 0.1))
+    E, nu, rho = _uniform_material(len(tets), 1e5, 0.4, 1000.0)
+    pinned = (np.abs(X[:, 2] - X[:, 2].max()) < 1e-12).astype(np.uint8)
+    return Scene("cube", X, tets, E, nu, rho, pinned, np.zeros_like(X))
+
+
+def beam_scene(nvx=100, nvy=20, nvz=20, length=0.1, width=0.02, E=1e7, nu=0.45,
+               vel_sigma=0.05, seed=0):
+    """Clamped stiff beam: long axis x, the x=0 face clamped, random initial velocity."""
+    X, tets = kuhn_grid(nvx, nvy, nvz, (length, width, width))
+    Ev, nuv, rho = _uniform_material(len(tets), E, nu, 1000.0)
+    pinned = (X[:, 0] < 1e-12).astype(np.uint8)
+    rng = np.random.default_rng(seed)
+    v0 = rng.normal(0.0, vel_sigma, size=X.shape)
+    v0[pinned.astype(bool)] = 0.0
+    return Scene("beam", X, tets, Ev, nuv, rho, pinned, v0)
+
+
+def box_planes(size=(1.0, 1.0, 2.0)):
+    """Floor and four side walls of an open-top box, as (normal, offset): n.x >= c."""
+    return np.array([
+        [0, 0, 1, 0.0],
+        [1, 0, 0, 0.0], [-1, 0, 0, -size[0]],
+        [0, 1, 0, 0.0], [0, -1, 0, -size[1]],
+    ], dtype=np.float64)
+
+
+def spheres_scene(n_spheres=10, radius=0.1, cells_across=48, seed=0, dhat=1e-3,
+                  E_stiff=2e6, E_soft=1e5, contact=1):
+    """Ten voxel spheres at seeded separated positions above a 1x1x2 m box.
+
+    Spheres 0..n/2-1 are stiff, the rest soft; all share one lattice shape.
+    """
+    Xs, ts = voxel_sphere(radius, cells_across)
+    rng = np.random.default_rng(seed)
+    centres = []
+    while len(centres) < n_spheres:
+        c = rng.uniform([0.15, 0.15, 0.5], [0.85, 0.85, 1.9])
+        if all(np.linalg.norm(c - d) >= 2 * radius + 2 * dhat for d in centres):
+            centres.append(c)
+    Xl, tl, El = [], [], []
+    for k, c in enumerate(centres):
+        Xl.append(Xs + c)
+        tl.append(ts + k * len(Xs))
+        El.append(np.full(len(ts), E_stiff if k < n_spheres // 2 else E_soft))
+    X = np.concatenate(Xl)
+    tets = np.concatenate(tl).astype(np.int32)
+    E = np.concatenate(El)
+    T = len(tets)
+    return Scene("spheres", X, tets, E, np.full(T, 0.4), np.full(T, 1000.0),
+                 np.zeros(len(X), np.uint8), np.zeros_like(X), planes=box_planes(),
+                 dhat=dhat, contact=contact)
+
+
+def blob_scene(index, t_min=1e3, t_max=5e4):
+    """One seeded random voxel blob (union of 1-6 spheres), bottom layer pinned.
+
+    The tet count is drawn log-uniform in [t_min, t_max]; the cell size is bisected
+    until the blob's tet count is within 10% of that target.
+    """
+    rng = np.random.default_rng(index)
+    k = int(rng.integers(1, 7))
+    centres = rng.uniform(0.0, 0.1, size=(k, 3))
+    radii = rng.uniform(0.02, 0.05, size=k)
+    target = float(np.exp(rng.uniform(np.log(t_min), np.log(t_max))))
+    E = float(np.exp(rng.uniform(np.log(1e4), np.log(1e7))))
+    nu = float(rng.uniform(0.3, 0.48))
+    lo = (centres - radii[:, None]).min(0)
+    hi = (centres + radii[:, None]).max(0)
+
+    def build(cell):
+        n = np.maximum(np.ceil((hi - lo) / cell).astype(int), 1)
+        cc = [lo[d] + (np.arange(n[d]) + 0.5) * cell for d in range(3)]
+        gx, gy, gz = np.meshgrid(*cc, indexing="ij")
+        P = np.stack([gx, gy, gz], -1)
+        mask = np.zeros(gx.shape, bool)
+        for c, r in zip(centres, radii):
+            mask |= ((P - c) ** 2).sum(-1) <= r * r
+        return mask
+
+    a, b = 1e-3, 5e-2
+    mask = build(b)
+    for _ in range(40):
+        cell = np.sqrt(a * b)
+        mask = build(cell)
+        t = 6 * int(mask.sum())
+        if abs(t - target) <= 0.1 * target:
+            break
+        if t > target:
+            a = cell
+        else:
+            b = cell
+    X, tets = voxel_mesh(mask, (cell, cell, cell), lo)
+    T = len(tets)
+    pinned = (np.abs(X[:, 2] - X[:, 2].min()) < 1e-9 * max(1.0, abs(X[:, 2].min()))).astype(np.uint8)
+    return Scene(f"blob{index}", X, tets, np.full(T, E), np.full(T, nu), np.full(T, 1000.0),
+                 pinned, np.zeros_like(X))
+
+
+def small_beam_scene(nvx=9, nvy=3, nvz=3, E=1e6, nu=0.45, seed=0, vel_sigma=0.05):
+    """A few-hundred-DOF clamped beam for fast tests (same recipe as the stiff beam)."""
+    return beam_scene(nvx, nvy, nvz, 0.1, 0.02, E, nu, vel_sigma, seed)
+
+
+def random_cubature(X, tets, pinned, n_cub=4, seed=0, w_max=2.0, u_sigma=0.3):
+    """Seeded synthetic cubature records for sweep-parity inputs (not a precompute).
+
+    For every free vertex: n_cub distinct elements drawn from its own body that do not
+    touch it, weights uniform in [0, w_max), and U_bar blocks with entries N(0, u_sigma^2)
+    (zero rows at pinned corners). Element draws are restricted to a random pool of at most
+    256 elements per body, as the library's pools are.
+    """
+    import scipy.sparse as sp
+    import scipy.sparse.csgraph as csg
+    V = len(X)
+    T = len(tets)
+    rows = np.repeat(tets[:, :1], 3, axis=1).ravel()
+    cols = tets[:, 1:].ravel()
+    G = sp.coo_matrix((np.ones(len(rows)), (rows, cols)), shape=(V, V))
+    nb, body = csg.connected_components(G, directed=False)
+    tbody = body[tets[:, 0]]
+    rng = np.random.default_rng(seed)
+    pools = {}
+    for b in range(nb):
+        el = np.nonzero(tbody == b)[0]
+        pools[b] = np.sort(rng.choice(el, size=min(256, len(el)), replace=False))
+    elem = -np.ones((V, n_cub), np.int64)
+    weight = np.zeros((V, n_cub))
+    ubar = np.zeros((V, n_cub, 4, 3, 3))
+    pin = np.asarray(pinned).astype(bool)
+    for i in np.nonzero(~pin)[0]:
+        pool = pools[body[i]]
+        ok = pool[~np.any(tets[pool] == i, axis=1)]
+        k = min(n_cub, len(ok))
+        if k == 0:
+            continue
+        pick = rng.choice(ok, size=k, replace=False)
+        elem[i, :k] = pick
+        weight[i, :k] = rng.uniform(0.0, w_max, size=k)
+        ubar[i, :k] = rng.normal(0.0, u_sigma, size=(k, 4, 3, 3))
+        ubar[i, :k][pin[tets[pick]]] = 0.0
+    return elem, weight, ubar
+
+
+def perturbed_state(X, pinned, scale, seed=0):
+    """x^k = X + smooth-ish random displacement of the free vertices (parity inputs)."""
+    rng = np.random.default_rng(seed)
+    d = rng.normal(0.0, scale, size=X.shape)
+    d[np.asarray(pinned).astype(bool)] = 0.0
+    return X + d
