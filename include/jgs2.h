@@ -1,0 +1,171 @@
+/*
+ * jgs2.h - C ABI of the B300 JGS2 library: the per-vertex parallel Jacobi sweep with the
+ * precomputed, co-rotated, cubature-sampled overshoot correction of
+ * Lan et al., "JGS2: Near Second-order Converging Jacobi/Gauss-Seidel for GPU
+ * Elastodynamics" (ACM TOG).
+ *
+ * Problem statement (Sec. 3, Eq. 1): each implicit-Euler time step minimises
+ *     E(x) = sum_v m_v/(2h^2) |x_v - z_v|^2 + sum_e V_e Psi(F_e),
+ *     z = x_t + h v_t + h^2 g,
+ * over the free vertices, where Psi is the stable Neo-Hookean energy (Table 1 caption)
+ *     Psi(F) = mu/2 (tr F^T F - 3) - mu (J - 1) + (lam + mu)/2 (J - 1)^2.
+ * After the step, v_{t+1} = (x_{t+1} - x_t)/h.
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns a jgs2_status; nothing aborts, traps or exits. On failure the
+ *    thread-local message of jgs2_last_error() says why.
+ *  - Host arrays passed in are read during the call only and copied; the caller keeps
+ *    ownership. Device state arrays (x, v) are caller-owned and must stay valid for the
+ *    duration of the call; the library never frees them.
+ *  - Vertex arrays are [V][3] row-major in the caller's vertex order; the library
+ *    reorders internally and writes back in the caller's order.
+ *  - A jgs2_mesh is not thread-safe: calls on one mesh must be serialised by the caller.
+ *    Different meshes may be used from different threads.
+ */
+#ifndef JGS2_H
+#define JGS2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  JGS2_OK = 0,
+  JGS2_EINVAL = 1,           /* bad argument (null pointer, size, index out of range) */
+  JGS2_ENOMEM = 2,           /* host or device allocation failed */
+  JGS2_ECUDA = 3,            /* a CUDA runtime call failed */
+  JGS2_ENOTPRECOMPUTED = 4,  /* jgs2_step with the correction on before a precompute */
+  JGS2_ENOTCONVERGED = 5,    /* max_sweeps reached; state is updated, report is filled */
+  JGS2_EDIVERGED = 6,        /* the residual became NaN/Inf; state is NOT written back */
+  JGS2_ENONSPD = 7,          /* reserved */
+  JGS2_ETIMEOUT = 8,         /* reserved for bounded device waits */
+  JGS2_EINTERSECT = 9        /* reserved for contact */
+} jgs2_status;
+
+/* Mesh description (Sec. 3). All pointers are host pointers, copied at create. */
+typedef struct {
+  int32_t n_vertices;        /* V > 0 */
+  int32_t n_tets;            /* T > 0 */
+  const double* rest_pos;    /* [V][3] rest positions X (m) */
+  const int32_t* tets;       /* [T][4] vertex indices; every tet must have positive volume */
+  const double* youngs;      /* [T] Young's modulus E (Pa) */
+  const double* poisson;     /* [T] Poisson ratio nu, in (-1, 0.5) */
+  const double* density;     /* [T] density rho (kg/m^3) */
+  const uint8_t* pinned;     /* [V] 1 = vertex held at its position x_t (not a DOF); may be NULL */
+  double gravity[3];         /* f_ext / m (m/s^2) */
+  double dt;                 /* time step h (s) > 0 */
+} jgs2_mesh_desc;
+
+typedef struct jgs2_mesh jgs2_mesh; /* opaque, library-owned */
+
+/* Precompute options (Secs. 5-6). */
+typedef struct {
+  int32_t n_cub;       /* cubature elements per vertex |S_i| (Table 1: 4 or 6); <= 8 */
+  int32_t n_train;     /* training poses: lowest eigenvectors of H_bar (Sec. 5) */
+  int32_t n_cand;      /* candidates drawn per greedy round (Sec. 5) */
+  int32_t n_pool;      /* per-body element pool the candidates come from */
+  double nnls_tol;     /* stop when the relative NNLS residual is below this (Sec. 5: 1%) */
+  uint64_t seed;       /* SplitMix64 seed of the pool / candidate draws */
+  int32_t n_threads;   /* host threads (0 = all cores) */
+} jgs2_precompute_opts;
+
+/* Cubature records produced elsewhere (e.g. by an independent implementation), in the
+ * caller's vertex order. Slot s of vertex i: element elem[i*n_cub+s] (caller tet index,
+ * -1 = unused slot), weight w[i*n_cub+s] >= 0, and the rows of U_bar_i at the element's
+ * four corners ubar[((i*n_cub+s)*4+a)*9 + 3*r + c] = (U_bar_{i,a})_{rc} (Eq. u, Sec. 6).
+ * Records of pinned vertices are ignored. */
+typedef struct {
+  int32_t n_cub;
+  const int32_t* elem;       /* [V][n_cub] */
+  const double* weight;      /* [V][n_cub] */
+  const double* ubar;        /* [V][n_cub][4][3][3] */
+} jgs2_cubature_blob;
+
+typedef enum { JGS2_FP64 = 0, JGS2_FP32 = 1 } jgs2_precision;
+typedef enum { JGS2_CORR_ASM = 0, JGS2_CORR_ELEM = 1, JGS2_CORR_OFF = 2 } jgs2_correction;
+
+typedef struct {
+  int32_t max_sweeps;        /* sweeps per step at most (>= 0) */
+  double rel_tol;            /* stop at |g(x^k)| <= rel_tol |g(x^0)| over free DOFs */
+  int32_t precision;         /* jgs2_precision: sweep arithmetic; reductions are FP64 */
+  int32_t correction;        /* jgs2_correction: gradient reading of Eq. cubature, or off */
+  int32_t line_search;       /* 1 = global Armijo backtracking on E (FP64 energy sums) */
+  int32_t check_every;       /* host reads the convergence flag every this many sweeps */
+  int32_t record_trace;      /* 1 = keep the per-sweep residual trace in the report */
+} jgs2_step_opts;
+
+#define JGS2_TRACE_MAX 4096
+
+typedef struct {
+  int32_t sweeps;            /* sweeps applied in the step */
+  int32_t converged;         /* 1 if rel_tol was reached */
+  int32_t fallback;          /* vertex solves that fell back to the uncorrected step */
+  int32_t ls_rejects;        /* sweeps where no line-search step satisfied Armijo */
+  double rel_residual;       /* |g(x_{t+1})| / |g(x_t)| */
+  double g0;                 /* |g(x^0)| */
+  double ms;                 /* wall time of the step on the stream (CUDA events) */
+  int32_t trace_len;
+  double trace[JGS2_TRACE_MAX]; /* r_k per sweep if record_trace */
+} jgs2_step_report;
+
+/* Default option values (n_cub 4, n_train 20, n_cand 32, n_pool 256, tol 0.01, seed 0). */
+void jgs2_precompute_opts_default(jgs2_precompute_opts* o);
+/* Defaults: max_sweeps 500, rel_tol 1e-4, FP32, asm, line search on, check_every 16. */
+void jgs2_step_opts_default(jgs2_step_opts* o);
+
+/* Validates the mesh (indices in range, positive volumes, material ranges), computes the
+ * rest-shape data in FP64 on the host (D_m^{-1}, V_e, lumped masses m_v = sum rho V_e/4),
+ * reorders vertices (free first, spatially sorted) and tets, builds the incidence lists
+ * and uploads everything to the current CUDA device. *out receives a new mesh. */
+jgs2_status jgs2_mesh_create(const jgs2_mesh_desc* desc, jgs2_mesh** out);
+
+/* Offline stage (Secs. 5-6), host FP64: factorises the rest Hessian H_bar = M/h^2 + K_bar
+ * of each distinct body once, computes A_i = (H_bar^{-1})_ii and the rows of
+ * U_bar_i = H_bar^{-1} S_i^T A_i^{-1} (Eq. u) that the cubature needs, the lowest
+ * eigenvectors of H_bar as training poses, and the greedy NNLS cubature sets
+ * (Eq. cubature_weight), then uploads the packed per-vertex records. */
+jgs2_status jgs2_precompute(jgs2_mesh* mesh, const jgs2_precompute_opts* opts);
+
+/* Loads cubature records computed elsewhere instead of running jgs2_precompute. */
+jgs2_status jgs2_precompute_import(jgs2_mesh* mesh, const jgs2_cubature_blob* blob);
+
+/* Copies the library's cubature records back out in the caller's vertex order: arrays
+ * sized as in jgs2_cubature_blob (n_cub from the precompute). Host pointers. */
+jgs2_status jgs2_precompute_export(const jgs2_mesh* mesh, int32_t* elem, double* weight,
+                                   double* ubar, double* residual /* [V], may be NULL */);
+int32_t jgs2_mesh_n_cub(const jgs2_mesh* mesh);
+
+/* One time step (Sec. 3) solved by JGS2 sweeps (Secs. 4-5, 8.1) from x^0 = x_t.
+ * x, v: caller-owned DEVICE arrays [V][3] of double on the mesh's device, read as
+ * (x_t, v_t) and overwritten with (x_{t+1}, v_{t+1}). stream: a cudaStream_t (NULL =
+ * default stream); all work is ordered on it and the call returns after the step
+ * completed. report may be NULL. Returns JGS2_ENOTCONVERGED (state written) when
+ * max_sweeps is hit, JGS2_EDIVERGED (state untouched) on a non-finite residual. */
+jgs2_status jgs2_step(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts,
+                      void* stream, jgs2_step_report* report);
+
+/* Same step with HOST arrays: copies x, v to the device, steps, copies back. */
+jgs2_status jgs2_step_host(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts,
+                           void* stream, jgs2_step_report* report);
+
+/* Sweep-level entry for parity checks: from the state (x^k = x_t + u, z) runs exactly
+ * n_sweeps sweeps without a convergence test. x_t, v_t, x_k: device [V][3] double, caller
+ * order; x_k is overwritten with x^{k+n}. */
+jgs2_status jgs2_sweeps(jgs2_mesh* mesh, const double* x_t, const double* v_t, double* x_k,
+                        int32_t n_sweeps, const jgs2_step_opts* opts, void* stream);
+
+/* Energy E(x) (Eq. 1) and gradient g(x) for the state (x_t, v_t, x): FP64 on the device.
+ * g: device [V][3] double (pinned rows 0), may be NULL. */
+jgs2_status jgs2_energy_gradient(jgs2_mesh* mesh, const double* x_t, const double* v_t,
+                                 const double* x, double* energy, double* g, void* stream);
+
+void jgs2_mesh_destroy(jgs2_mesh* mesh);
+const char* jgs2_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JGS2_H */

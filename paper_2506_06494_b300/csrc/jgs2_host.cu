@@ -1,0 +1,678 @@
+// Host side of the JGS2 library: C ABI, mesh ingest and reordering, the step driver.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/jgs2.h"
+#include "jgs2_host.h"
+#include "jgs2_kernels.cuh"
+
+namespace jgs2 {
+
+thread_local std::string g_last_error;
+
+jgs2_status fail(jgs2_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? JGS2_ENOMEM : JGS2_ECUDA,         \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                \
+  } while (0)
+
+template <typename X>
+static cudaError_t dalloc(X** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  return cudaMalloc((void**)p, n * sizeof(X));
+}
+
+template <typename T>
+void PrecBufs<T>::release() {
+  cudaFree(tets); cudaFree(u); cudaFree(dz); cudaFree(D); cudaFree(DJ); cudaFree(mh2);
+  cudaFree(cub_p); cudaFree(cub_w); cudaFree(cub_u); cudaFree(pool_H); cudaFree(pool_G);
+  *this = PrecBufs<T>();
+}
+template struct PrecBufs<float>;
+template struct PrecBufs<double>;
+
+Mesh::~Mesh() {
+  f32.release();
+  f64.release();
+  cudaFree(d_inc_off); cudaFree(d_inc_len); cudaFree(d_inc); cudaFree(d_pool_tet);
+  cudaFree(d_xt); cudaFree(d_vt); cudaFree(d_perm); cudaFree(d_state); cudaFree(d_partial);
+  cudaFree(d_trace); cudaFree(d_xbuf); cudaFree(d_vbuf);
+  if (h_state) cudaFreeHost(h_state);
+}
+
+static uint64_t spread3(uint64_t x) {
+  x &= 0x1fffff;
+  x = (x | x << 32) & 0x1f00000000ffffULL;
+  x = (x | x << 16) & 0x1f0000ff0000ffULL;
+  x = (x | x << 8) & 0x100f00f00f00f00fULL;
+  x = (x | x << 4) & 0x10c30c30c30c30c3ULL;
+  x = (x | x << 2) & 0x1249249249249249ULL;
+  return x;
+}
+
+// ------------------------------------------------------------------ mesh create
+
+jgs2_status mesh_create(const jgs2_mesh_desc* d, Mesh** out) {
+  if (!d || !out) return fail(JGS2_EINVAL, "null argument");
+  *out = nullptr;
+  const int V = d->n_vertices, T = d->n_tets;
+  if (V <= 0 || T <= 0) return fail(JGS2_EINVAL, "n_vertices and n_tets must be positive");
+  if (!d->rest_pos || !d->tets || !d->youngs || !d->poisson || !d->density)
+    return fail(JGS2_EINVAL, "null mesh array");
+  if (!(d->dt > 0.0) || !std::isfinite(d->dt)) return fail(JGS2_EINVAL, "dt must be positive");
+  std::unique_ptr<Mesh> m(new Mesh());
+  m->V = V;
+  m->T = T;
+  m->h = d->dt;
+  for (int q = 0; q < 3; ++q) m->grav[q] = d->gravity[q];
+  m->X.assign(d->rest_pos, d->rest_pos + 3 * (size_t)V);
+  m->tets_c.assign(d->tets, d->tets + 4 * (size_t)T);
+  m->E.assign(d->youngs, d->youngs + T);
+  m->nu.assign(d->poisson, d->poisson + T);
+  m->rho.assign(d->density, d->density + T);
+  m->pinned.assign(V, 0);
+  if (d->pinned)
+    for (int v = 0; v < V; ++v) m->pinned[v] = d->pinned[v] ? 1 : 0;
+  for (int v = 0; v < 3 * V; ++v)
+    if (!std::isfinite(m->X[v])) return fail(JGS2_EINVAL, "non-finite rest position");
+  // rest data (FP64): B = D_m^{-1}, V_e, Lame, mass shares
+  m->B.resize(9 * (size_t)T);
+  m->vol.resize(T);
+  m->mu.resize(T);
+  m->lp.resize(T);
+  m->mass.assign(V, 0.0);
+  for (int t = 0; t < T; ++t) {
+    const int* tv = &m->tets_c[4 * (size_t)t];
+    for (int a = 0; a < 4; ++a)
+      if (tv[a] < 0 || tv[a] >= V) return fail(JGS2_EINVAL, "tet index out of range at tet " + std::to_string(t));
+    if (!(m->E[t] > 0) || !(m->nu[t] > -1.0 && m->nu[t] < 0.5) || !(m->rho[t] > 0))
+      return fail(JGS2_EINVAL, "material out of range at tet " + std::to_string(t));
+    double Dm[9];
+    for (int k = 0; k < 3; ++k)
+      for (int i = 0; i < 3; ++i) Dm[3 * i + k] = m->X[3 * tv[k + 1] + i] - m->X[3 * tv[0] + i];
+    const double c00 = Dm[4] * Dm[8] - Dm[5] * Dm[7], c01 = Dm[5] * Dm[6] - Dm[3] * Dm[8],
+                 c02 = Dm[3] * Dm[7] - Dm[4] * Dm[6];
+    const double det = Dm[0] * c00 + Dm[1] * c01 + Dm[2] * c02;
+    if (!(det > 0.0)) return fail(JGS2_EINVAL, "non-positive tet volume at tet " + std::to_string(t));
+    double* B = &m->B[9 * (size_t)t];
+    B[0] = c00 / det;
+    B[1] = (Dm[2] * Dm[7] - Dm[1] * Dm[8]) / det;
+    B[2] = (Dm[1] * Dm[5] - Dm[2] * Dm[4]) / det;
+    B[3] = c01 / det;
+    B[4] = (Dm[0] * Dm[8] - Dm[2] * Dm[6]) / det;
+    B[5] = (Dm[2] * Dm[3] - Dm[0] * Dm[5]) / det;
+    B[6] = c02 / det;
+    B[7] = (Dm[1] * Dm[6] - Dm[0] * Dm[7]) / det;
+    B[8] = (Dm[0] * Dm[4] - Dm[1] * Dm[3]) / det;
+    m->vol[t] = det / 6.0;
+    const double E = m->E[t], nu = m->nu[t];
+    m->mu[t] = E / (2.0 * (1.0 + nu));
+    m->lp[t] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)) + m->mu[t];
+    for (int a = 0; a < 4; ++a) m->mass[tv[a]] += m->rho[t] * m->vol[t] / 4.0;
+  }
+  // internal order: free vertices along a Morton curve, then pinned vertices
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int v = 0; v < V; ++v)
+    for (int q = 0; q < 3; ++q) {
+      lo[q] = std::min(lo[q], m->X[3 * v + q]);
+      hi[q] = std::max(hi[q], m->X[3 * v + q]);
+    }
+  double ext = std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], 1e-300});
+  std::vector<uint64_t> key(V);
+  for (int v = 0; v < V; ++v) {
+    uint64_t c[3];
+    for (int q = 0; q < 3; ++q) c[q] = (uint64_t)std::min(2097151.0, std::floor((m->X[3 * v + q] - lo[q]) / ext * 2097151.0));
+    key[v] = spread3(c[0]) | spread3(c[1]) << 1 | spread3(c[2]) << 2;
+  }
+  m->perm.resize(V);
+  std::iota(m->perm.begin(), m->perm.end(), 0);
+  std::stable_sort(m->perm.begin(), m->perm.end(), [&](int a, int b) {
+    if (m->pinned[a] != m->pinned[b]) return m->pinned[a] < m->pinned[b];
+    return key[a] < key[b];
+  });
+  m->iperm.resize(V);
+  for (int i = 0; i < V; ++i) m->iperm[m->perm[i]] = i;
+  m->Vf = 0;
+  while (m->Vf < V && !m->pinned[m->perm[m->Vf]]) ++m->Vf;
+  // tets in internal ids, sorted by smallest corner
+  m->tperm.resize(T);
+  std::iota(m->tperm.begin(), m->tperm.end(), 0);
+  std::vector<int> tmin(T);
+  for (int t = 0; t < T; ++t) {
+    int mn = V;
+    for (int a = 0; a < 4; ++a) mn = std::min(mn, m->iperm[m->tets_c[4 * (size_t)t + a]]);
+    tmin[t] = mn;
+  }
+  std::stable_sort(m->tperm.begin(), m->tperm.end(), [&](int a, int b) { return tmin[a] < tmin[b]; });
+  m->tiperm.resize(T);
+  for (int i = 0; i < T; ++i) m->tiperm[m->tperm[i]] = i;
+  // incidence of free vertices, in internal tet order
+  std::vector<int> cnt(m->Vf, 0);
+  for (int ti = 0; ti < T; ++ti) {
+    const int t = m->tperm[ti];
+    for (int a = 0; a < 4; ++a) {
+      const int v = m->iperm[m->tets_c[4 * (size_t)t + a]];
+      if (v < m->Vf) cnt[v]++;
+    }
+  }
+  const int ns = (m->Vf + kSlice - 1) / kSlice;
+  m->n_slices = ns;
+  m->inc_off.assign(ns + 1, 0);
+  for (int s = 0; s < ns; ++s) {
+    int mx = 0;
+    for (int l = 0; l < kSlice && s * kSlice + l < m->Vf; ++l) mx = std::max(mx, cnt[s * kSlice + l]);
+    m->inc_off[s + 1] = m->inc_off[s] + mx * kSlice;
+  }
+  m->inc.assign(m->inc_off[ns], 0);
+  m->inc_len.assign(m->Vf, 0);
+  for (int ti = 0; ti < T; ++ti) {
+    const int t = m->tperm[ti];
+    for (int a = 0; a < 4; ++a) {
+      const int v = m->iperm[m->tets_c[4 * (size_t)t + a]];
+      if (v >= m->Vf) continue;
+      const int s = v / kSlice, l = v % kSlice;
+      m->inc[m->inc_off[s] + m->inc_len[v] * kSlice + l] = ti * 4 + a;
+      m->inc_len[v]++;
+    }
+  }
+  // bodies: connected components, numbered by smallest caller vertex index
+  {
+    std::vector<int> par(V);
+    std::iota(par.begin(), par.end(), 0);
+    auto find = [&](int a) {
+      while (par[a] != a) a = par[a] = par[par[a]];
+      return a;
+    };
+    for (int t = 0; t < T; ++t) {
+      const int r0 = find(m->tets_c[4 * (size_t)t]);
+      for (int a = 1; a < 4; ++a) {
+        const int r = find(m->tets_c[4 * (size_t)t + a]);
+        if (r != r0) par[r] = r0;
+      }
+    }
+    std::vector<int> id(V, -1);
+    m->body.assign(V, 0);
+    int nb = 0;
+    for (int v = 0; v < V; ++v) {
+      const int r = find(v);
+      if (id[r] < 0) id[r] = nb++;
+      m->body[v] = id[r];
+    }
+    m->n_bodies = nb;
+  }
+  // shared device arrays
+  CK(dalloc(&m->d_inc_off, ns + 1));
+  CK(dalloc(&m->d_inc_len, m->Vf));
+  CK(dalloc(&m->d_inc, m->inc.size()));
+  CK(dalloc(&m->d_xt, 3 * (size_t)V));
+  CK(dalloc(&m->d_vt, 3 * (size_t)V));
+  CK(dalloc(&m->d_perm, V));
+  CK(dalloc(&m->d_state, 1));
+  CK(dalloc(&m->d_trace, JGS2_TRACE_MAX));
+  const size_t np = std::max<size_t>(2 * kLsTrials * ((size_t)(T + 127) / 128 + (m->Vf + 127) / 128 + 1), 16);
+  CK(dalloc(&m->d_partial, np));
+  CK(cudaMallocHost((void**)&m->h_state, sizeof(StepState)));
+  CK(cudaMemcpy(m->d_inc_off, m->inc_off.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
+  if (m->Vf) CK(cudaMemcpy(m->d_inc_len, m->inc_len.data(), sizeof(int) * m->Vf, cudaMemcpyHostToDevice));
+  if (!m->inc.empty()) CK(cudaMemcpy(m->d_inc, m->inc.data(), sizeof(int) * m->inc.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(m->d_perm, m->perm.data(), sizeof(int) * V, cudaMemcpyHostToDevice));
+  CK(cudaMemset(m->d_state, 0, sizeof(StepState)));
+  *out = m.release();
+  return JGS2_OK;
+}
+
+// ------------------------------------------------------------------ per-precision buffers
+
+template <typename T>
+static PrecBufs<T>& bufs(Mesh* m);
+template <>
+PrecBufs<float>& bufs<float>(Mesh* m) { return m->f32; }
+template <>
+PrecBufs<double>& bufs<double>(Mesh* m) { return m->f64; }
+
+template <typename T>
+static jgs2_status ensure_prec(Mesh* m) {
+  PrecBufs<T>& b = bufs<T>(m);
+  if (!b.ready) {
+    const int V = m->V, T_ = m->T;
+    std::vector<TetRec<T>> rec(T_);
+    for (int ti = 0; ti < T_; ++ti) {
+      const int t = m->tperm[ti];
+      TetRec<T>& r = rec[ti];
+      for (int a = 0; a < 4; ++a) r.v[a] = m->iperm[m->tets_c[4 * (size_t)t + a]];
+      for (int q = 0; q < 9; ++q) {
+        r.B[q] = T(m->B[9 * (size_t)t + q]);
+        r.Ft[q] = T(q % 4 == 0 ? 1.0 : 0.0);
+      }
+      r.vol = T(m->vol[t]);
+      r.mu = T(m->mu[t]);
+      r.lp = T(m->lp[t]);
+      r.mq = T(m->rho[t] * m->vol[t] / 4.0);
+    }
+    std::vector<T> mh2(V, T(0));
+    for (int i = 0; i < m->Vf; ++i) mh2[i] = T(m->mass[m->perm[i]] / (m->h * m->h));
+    CK(dalloc(&b.tets, T_));
+    CK(dalloc(&b.u, V));
+    CK(dalloc(&b.dz, m->Vf));
+    CK(dalloc(&b.D, m->Vf));
+    CK(dalloc(&b.DJ, m->Vf));
+    CK(dalloc(&b.mh2, V));
+    CK(cudaMemcpy(b.tets, rec.data(), sizeof(TetRec<T>) * T_, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b.mh2, mh2.data(), sizeof(T) * V, cudaMemcpyHostToDevice));
+    CK(cudaMemset(b.D, 0, sizeof(Vec4<T>) * std::max(1, m->Vf)));
+    CK(cudaMemset(b.DJ, 0, sizeof(Vec4<T>) * std::max(1, m->Vf)));
+    b.ready = true;
+  }
+  if (m->cub_version != b.cub_version && m->n_cub > 0) {
+    cudaFree(b.cub_p); cudaFree(b.cub_w); cudaFree(b.cub_u); cudaFree(b.pool_H); cudaFree(b.pool_G);
+    const size_t Vf = m->Vf, nc = m->n_cub;
+    std::vector<T> w(nc * Vf), u(nc * 36 * Vf);
+    for (size_t s = 0; s < nc; ++s)
+      for (size_t i = 0; i < Vf; ++i) {
+        w[s * Vf + i] = T(m->cub_w[i * nc + s]);
+        for (int q = 0; q < 36; ++q) u[(s * 36 + q) * Vf + i] = T(m->cub_u[(i * nc + s) * 36 + q]);
+      }
+    std::vector<int32_t> p(nc * Vf);
+    for (size_t s = 0; s < nc; ++s)
+      for (size_t i = 0; i < Vf; ++i) p[s * Vf + i] = m->cub_p[i * nc + s];
+    CK(dalloc(&b.cub_p, nc * Vf));
+    CK(dalloc(&b.cub_w, nc * Vf));
+    CK(dalloc(&b.cub_u, nc * 36 * Vf));
+    CK(dalloc(&b.pool_H, (size_t)m->nP * kPackedH));
+    CK(dalloc(&b.pool_G, (size_t)m->nP * 12));
+    CK(cudaMemcpy(b.cub_p, p.data(), sizeof(int32_t) * p.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b.cub_w, w.data(), sizeof(T) * w.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b.cub_u, u.data(), sizeof(T) * u.size(), cudaMemcpyHostToDevice));
+    b.cub_version = m->cub_version;
+  }
+  return JGS2_OK;
+}
+
+template <typename T>
+static DevMesh<T> dev_view(Mesh* m) {
+  PrecBufs<T>& b = bufs<T>(m);
+  DevMesh<T> d;
+  d.V = m->V;
+  d.Vf = m->Vf;
+  d.T_ = m->T;
+  d.n_slices = m->n_slices;
+  d.nP = m->nP;
+  d.n_cub = m->n_cub;
+  d.tets = b.tets;
+  d.tets_mut = b.tets;
+  d.inc_off = m->d_inc_off;
+  d.inc_len = m->d_inc_len;
+  d.inc = m->d_inc;
+  d.u = b.u;
+  d.dz = b.dz;
+  d.D = b.D;
+  d.DJ = b.DJ;
+  d.mh2 = b.mh2;
+  d.cub_p = b.cub_p;
+  d.cub_w = b.cub_w;
+  d.cub_u = b.cub_u;
+  d.pool_tet = m->d_pool_tet;
+  d.pool_H = b.pool_H;
+  d.pool_G = b.pool_G;
+  d.xt = m->d_xt;
+  d.vt = m->d_vt;
+  d.perm = m->d_perm;
+  d.inv_h2 = 1.0 / (m->h * m->h);
+  d.h = m->h;
+  for (int q = 0; q < 3; ++q) d.grav[q] = m->grav[q];
+  return d;
+}
+
+// ------------------------------------------------------------------ cubature records
+
+jgs2_status set_cubature(Mesh* m, int n_cub, const std::vector<int>& elem_int /* [Vf][nc] internal tet, -1 */,
+                         const std::vector<double>& w, const std::vector<double>& u) {
+  if (n_cub <= 0 || n_cub > kMaxCub) return fail(JGS2_EINVAL, "n_cub must be in [1, 8]");
+  // pool = distinct referenced elements, ascending internal id
+  std::vector<int> pool;
+  for (int e : elem_int)
+    if (e >= 0) pool.push_back(e);
+  std::sort(pool.begin(), pool.end());
+  pool.erase(std::unique(pool.begin(), pool.end()), pool.end());
+  m->n_cub = n_cub;
+  m->nP = (int)pool.size();
+  m->pool = pool;
+  m->cub_p.assign(elem_int.size(), -1);
+  for (size_t q = 0; q < elem_int.size(); ++q)
+    if (elem_int[q] >= 0)
+      m->cub_p[q] = (int)(std::lower_bound(pool.begin(), pool.end(), elem_int[q]) - pool.begin());
+  m->cub_elem = elem_int;
+  m->cub_w = w;
+  m->cub_u = u;
+  cudaFree(m->d_pool_tet);
+  m->d_pool_tet = nullptr;
+  CK(dalloc(&m->d_pool_tet, std::max(1, m->nP)));
+  if (m->nP) CK(cudaMemcpy(m->d_pool_tet, pool.data(), sizeof(int) * m->nP, cudaMemcpyHostToDevice));
+  m->cub_version++;
+  return JGS2_OK;
+}
+
+jgs2_status import_cubature(Mesh* m, const jgs2_cubature_blob* b) {
+  if (!m || !b || !b->elem || !b->weight || !b->ubar) return fail(JGS2_EINVAL, "null argument");
+  const int nc = b->n_cub;
+  if (nc <= 0 || nc > kMaxCub) return fail(JGS2_EINVAL, "n_cub must be in [1, 8]");
+  const size_t Vf = m->Vf;
+  std::vector<int> e(Vf * nc, -1);
+  std::vector<double> w(Vf * nc, 0.0), u(Vf * nc * 36, 0.0);
+  for (size_t i = 0; i < Vf; ++i) {
+    const int c = m->perm[i];
+    for (int s = 0; s < nc; ++s) {
+      const int et = b->elem[(size_t)c * nc + s];
+      if (et < -1 || et >= m->T) return fail(JGS2_EINVAL, "cubature element out of range");
+      const double ww = b->weight[(size_t)c * nc + s];
+      if (et >= 0 && !(ww >= 0.0 && std::isfinite(ww))) return fail(JGS2_EINVAL, "cubature weight must be finite and >= 0");
+      if (et < 0) continue;
+      // the slot's 4 corners follow the caller tet's corner order, which the internal
+      // record keeps (corner a of internal tet = corner a of caller tet)
+      e[i * nc + s] = m->tiperm[et];
+      w[i * nc + s] = ww;
+      for (int q = 0; q < 36; ++q) u[(i * nc + s) * 36 + q] = b->ubar[((size_t)c * nc + s) * 36 + q];
+    }
+  }
+  m->cub_resid.assign(m->V, std::nan(""));
+  return set_cubature(m, nc, e, w, u);
+}
+
+// ------------------------------------------------------------------ step driver
+
+template <typename T>
+static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t s, int max_k, double rel_tol,
+                              bool check, StepState* hs) {
+  DevMesh<T> d = dev_view<T>(m);
+  const bool corr = o.correction != JGS2_CORR_OFF;
+  const int nbV = (m->Vf + 127) / 128;
+  const int nbT = (m->T + 127) / 128;
+  StepState init;
+  std::memset(&init, 0, sizeof(init));
+  init.max_sweeps = max_k;
+  init.rel_tol = rel_tol;
+  init.alpha = 1.0;
+  CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
+  const int every = std::max(1, o.check_every);
+  for (int k = 0; k <= max_k; ++k) {
+    if (corr && m->nP > 0) {
+      if (o.correction == JGS2_CORR_ASM)
+        k_pool<T, true><<<m->nP, 128, 0, s>>>(d, m->d_state);
+      else
+        k_pool<T, false><<<m->nP, 128, 0, s>>>(d, m->d_state);
+    }
+    if (nbV > 0) {
+      if (corr)
+        k_main<T, true><<<nbV, 128, 0, s>>>(d, m->d_state, k, m->d_partial, m->d_trace, o.record_trace);
+      else
+        k_main<T, false><<<nbV, 128, 0, s>>>(d, m->d_state, k, m->d_partial, m->d_trace, o.record_trace);
+    }
+    if (k == max_k) break;
+    if (o.line_search) {
+      if (corr)
+        k_energy<T, 2><<<nbT + nbV, 128, 0, s>>>(d, m->d_state, m->d_partial, nbT);
+      else
+        k_energy<T, 1><<<nbT + nbV, 128, 0, s>>>(d, m->d_state, m->d_partial, nbT);
+    }
+    if (nbV > 0) k_update<T><<<nbV, 128, 0, s>>>(d, m->d_state);
+    CK(cudaGetLastError());
+    if (check && (k + 1) % every == 0) {
+      CK(cudaMemcpyAsync(hs, m->d_state, sizeof(StepState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (hs->done) break;
+    }
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(hs, m->d_state, sizeof(StepState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return JGS2_OK;
+}
+
+static jgs2_status check_opts(const Mesh* m, const jgs2_step_opts* o) {
+  if (!o) return fail(JGS2_EINVAL, "null options");
+  if (o->max_sweeps < 0 || o->max_sweeps > 1000000) return fail(JGS2_EINVAL, "max_sweeps out of range");
+  if (o->precision != JGS2_FP64 && o->precision != JGS2_FP32) return fail(JGS2_EINVAL, "bad precision");
+  if (o->correction < 0 || o->correction > 2) return fail(JGS2_EINVAL, "bad correction");
+  if (o->correction != JGS2_CORR_OFF && m->n_cub == 0)
+    return fail(JGS2_ENOTPRECOMPUTED, "correction requested before jgs2_precompute / jgs2_precompute_import");
+  return JGS2_OK;
+}
+
+template <typename T>
+static jgs2_status step_impl(Mesh* m, double* x, double* v, const jgs2_step_opts* o, cudaStream_t s,
+                             jgs2_step_report* rep) {
+  jgs2_status st = ensure_prec<T>(m);
+  if (st != JGS2_OK) return st;
+  DevMesh<T> d = dev_view<T>(m);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  const int nb = (m->V + 127) / 128;
+  k_setup_vertices<T><<<nb, 128, 0, s>>>(d, x, v, nullptr);
+  k_setup_tets<T><<<(m->T + 127) / 128, 128, 0, s>>>(d);
+  CK(cudaGetLastError());
+  StepState* hs = m->h_state;
+  st = run_sweeps<T>(m, *o, s, o->max_sweeps, o->rel_tol, true, hs);
+  if (st != JGS2_OK) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+  }
+  if (hs->status == 0) k_finish<T><<<nb, 128, 0, s>>>(d, x, v);
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rep) {
+    rep->sweeps = hs->sweeps;
+    rep->converged = hs->converged;
+    rep->fallback = hs->fallback;
+    rep->ls_rejects = hs->ls_rejects;
+    rep->rel_residual = hs->r;
+    rep->g0 = hs->g0;
+    rep->ms = ms;
+    rep->trace_len = 0;
+    if (o->record_trace) {
+      const int n = std::min(hs->sweeps + 1, JGS2_TRACE_MAX);
+      CK(cudaMemcpy(rep->trace, m->d_trace, sizeof(double) * n, cudaMemcpyDeviceToHost));
+      rep->trace_len = n;
+    }
+  }
+  if (hs->status != 0) return fail((jgs2_status)hs->status, "residual became non-finite; state not written");
+  if (!hs->converged) return fail(JGS2_ENOTCONVERGED, "max_sweeps reached before rel_tol");
+  return JGS2_OK;
+}
+
+jgs2_status step(Mesh* m, double* x, double* v, const jgs2_step_opts* o, void* stream, jgs2_step_report* rep) {
+  if (!m || !x || !v) return fail(JGS2_EINVAL, "null argument");
+  jgs2_status st = check_opts(m, o);
+  if (st != JGS2_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  return o->precision == JGS2_FP64 ? step_impl<double>(m, x, v, o, s, rep) : step_impl<float>(m, x, v, o, s, rep);
+}
+
+template <typename T>
+static jgs2_status sweeps_impl(Mesh* m, const double* xt, const double* vt, double* xk, int n,
+                               const jgs2_step_opts* o, cudaStream_t s) {
+  jgs2_status st = ensure_prec<T>(m);
+  if (st != JGS2_OK) return st;
+  DevMesh<T> d = dev_view<T>(m);
+  const int nb = (m->V + 127) / 128;
+  k_setup_vertices<T><<<nb, 128, 0, s>>>(d, xt, vt, xk);
+  k_setup_tets<T><<<(m->T + 127) / 128, 128, 0, s>>>(d);
+  CK(cudaGetLastError());
+  // exactly n sweeps: no convergence test (rel_tol < 0), stop after the n-th update
+  st = run_sweeps<T>(m, *o, s, n, -1.0, false, m->h_state);
+  if (st != JGS2_OK) return st;
+  k_finish<T><<<nb, 128, 0, s>>>(d, xk, nullptr);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return JGS2_OK;
+}
+
+jgs2_status sweeps(Mesh* m, const double* xt, const double* vt, double* xk, int n, const jgs2_step_opts* o,
+                   void* stream) {
+  if (!m || !xt || !vt || !xk || n < 0) return fail(JGS2_EINVAL, "bad argument");
+  jgs2_status st = check_opts(m, o);
+  if (st != JGS2_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  return o->precision == JGS2_FP64 ? sweeps_impl<double>(m, xt, vt, xk, n, o, s)
+                                   : sweeps_impl<float>(m, xt, vt, xk, n, o, s);
+}
+
+jgs2_status energy_gradient(Mesh* m, const double* xt, const double* vt, const double* x, double* E, double* g,
+                            void* stream) {
+  if (!m || !xt || !vt || !x) return fail(JGS2_EINVAL, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  jgs2_status st = ensure_prec<double>(m);
+  if (st != JGS2_OK) return st;
+  DevMesh<double> d = dev_view<double>(m);
+  const int nb = (m->V + 127) / 128;
+  k_setup_vertices<double><<<nb, 128, 0, s>>>(d, xt, vt, x);
+  k_setup_tets<double><<<(m->T + 127) / 128, 128, 0, s>>>(d);
+  // pinned vertices keep x_t; a caller x that moves them is a different problem
+  if (g) k_grad<double><<<nb, 128, 0, s>>>(d, g);
+  if (E) {
+    const int nbT = (m->T + 127) / 128, nbV = (m->Vf + 127) / 128;
+    k_energy_abs<double><<<nbT + nbV, 128, 0, s>>>(d, m->d_partial, nbT);
+    std::vector<double> p(nbT + nbV);
+    CK(cudaMemcpyAsync(p.data(), m->d_partial, sizeof(double) * p.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double acc = 0.0;
+    for (double q : p) acc += q;
+    *E = acc;
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return JGS2_OK;
+}
+
+}  // namespace jgs2
+
+// ------------------------------------------------------------------ C ABI
+
+using namespace jgs2;
+
+extern "C" {
+
+void jgs2_precompute_opts_default(jgs2_precompute_opts* o) {
+  if (!o) return;
+  o->n_cub = 4;
+  o->n_train = 20;
+  o->n_cand = 32;
+  o->n_pool = 256;
+  o->nnls_tol = 0.01;
+  o->seed = 0;
+  o->n_threads = 0;
+}
+
+void jgs2_step_opts_default(jgs2_step_opts* o) {
+  if (!o) return;
+  o->max_sweeps = 500;
+  o->rel_tol = 1e-4;
+  o->precision = JGS2_FP32;
+  o->correction = JGS2_CORR_ASM;
+  o->line_search = 1;
+  o->check_every = 16;
+  o->record_trace = 0;
+}
+
+jgs2_status jgs2_mesh_create(const jgs2_mesh_desc* desc, jgs2_mesh** out) {
+  Mesh* m = nullptr;
+  jgs2_status s = mesh_create(desc, &m);
+  if (out) *out = reinterpret_cast<jgs2_mesh*>(m);
+  return s;
+}
+
+jgs2_status jgs2_precompute_import(jgs2_mesh* mesh, const jgs2_cubature_blob* blob) {
+  return import_cubature(reinterpret_cast<Mesh*>(mesh), blob);
+}
+
+int32_t jgs2_mesh_n_cub(const jgs2_mesh* mesh) {
+  return mesh ? reinterpret_cast<const Mesh*>(mesh)->n_cub : 0;
+}
+
+jgs2_status jgs2_precompute_export(const jgs2_mesh* mesh, int32_t* elem, double* weight, double* ubar,
+                                   double* residual) {
+  const Mesh* m = reinterpret_cast<const Mesh*>(mesh);
+  if (!m || !elem || !weight || !ubar) return fail(JGS2_EINVAL, "null argument");
+  const int nc = m->n_cub;
+  if (nc == 0) return fail(JGS2_ENOTPRECOMPUTED, "no cubature records");
+  for (int c = 0; c < m->V; ++c) {
+    const int i = m->iperm[c];
+    for (int s = 0; s < nc; ++s) {
+      const size_t o = (size_t)c * nc + s;
+      elem[o] = -1;
+      weight[o] = 0.0;
+      for (int q = 0; q < 36; ++q) ubar[o * 36 + q] = 0.0;
+      if (i >= m->Vf) continue;
+      const int e = m->cub_elem[(size_t)i * nc + s];
+      if (e < 0) continue;
+      elem[o] = m->tperm[e];
+      weight[o] = m->cub_w[(size_t)i * nc + s];
+      for (int q = 0; q < 36; ++q) ubar[o * 36 + q] = m->cub_u[((size_t)i * nc + s) * 36 + q];
+    }
+    if (residual) residual[c] = (size_t)c < m->cub_resid.size() ? m->cub_resid[c] : std::nan("");
+  }
+  return JGS2_OK;
+}
+
+jgs2_status jgs2_step(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts, void* stream,
+                      jgs2_step_report* report) {
+  return step(reinterpret_cast<Mesh*>(mesh), x, v, opts, stream, report);
+}
+
+jgs2_status jgs2_step_host(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts, void* stream,
+                           jgs2_step_report* report) {
+  Mesh* m = reinterpret_cast<Mesh*>(mesh);
+  if (!m || !x || !v) return fail(JGS2_EINVAL, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = 3 * (size_t)m->V;
+  if (!m->d_xbuf) {
+    CK(dalloc(&m->d_xbuf, n));
+    CK(dalloc(&m->d_vbuf, n));
+  }
+  CK(cudaMemcpyAsync(m->d_xbuf, x, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(m->d_vbuf, v, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  jgs2_status st = step(m, m->d_xbuf, m->d_vbuf, opts, stream, report);
+  if (st != JGS2_OK && st != JGS2_ENOTCONVERGED) return st;
+  CK(cudaMemcpyAsync(x, m->d_xbuf, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(v, m->d_vbuf, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return st;
+}
+
+jgs2_status jgs2_sweeps(jgs2_mesh* mesh, const double* x_t, const double* v_t, double* x_k, int32_t n_sweeps,
+                        const jgs2_step_opts* opts, void* stream) {
+  return sweeps(reinterpret_cast<Mesh*>(mesh), x_t, v_t, x_k, n_sweeps, opts, stream);
+}
+
+jgs2_status jgs2_energy_gradient(jgs2_mesh* mesh, const double* x_t, const double* v_t, const double* x,
+                                 double* energy, double* g, void* stream) {
+  return energy_gradient(reinterpret_cast<Mesh*>(mesh), x_t, v_t, x, energy, g, stream);
+}
+
+void jgs2_mesh_destroy(jgs2_mesh* mesh) { delete reinterpret_cast<Mesh*>(mesh); }
+
+const char* jgs2_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

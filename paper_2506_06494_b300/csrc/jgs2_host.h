@@ -1,0 +1,64 @@
+// Host-side mesh object of the JGS2 library (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/jgs2.h"
+#include "jgs2_internal.h"
+
+namespace jgs2 {
+
+template <typename T>
+struct PrecBufs {
+  bool ready = false;
+  int cub_version = -1;
+  TetRec<T>* tets = nullptr;
+  Vec4<T>* u = nullptr;
+  Vec4<T>* dz = nullptr;
+  Vec4<T>* D = nullptr;
+  Vec4<T>* DJ = nullptr;
+  T* mh2 = nullptr;
+  int32_t* cub_p = nullptr;
+  T* cub_w = nullptr;
+  T* cub_u = nullptr;
+  T* pool_H = nullptr;
+  T* pool_G = nullptr;
+  void release();
+};
+
+struct Mesh {
+  int V = 0, T = 0, Vf = 0, n_slices = 0, n_bodies = 0;
+  double h = 0.0;
+  double grav[3] = {0, 0, 0};
+  // caller-order inputs and FP64 rest data
+  std::vector<double> X, E, nu, rho;
+  std::vector<int> tets_c;
+  std::vector<uint8_t> pinned;
+  std::vector<double> B, vol, mu, lp, mass;
+  std::vector<int> body;  // caller vertex -> body id (by smallest caller vertex index)
+  // orderings
+  std::vector<int> perm, iperm;    // internal <-> caller vertex
+  std::vector<int> tperm, tiperm;  // internal <-> caller tet
+  std::vector<int> inc_off, inc_len, inc;
+  // cubature records, internal order: [Vf][n_cub]
+  int n_cub = 0, nP = 0, cub_version = 0;
+  std::vector<int> pool;          // internal tet ids of the pool, ascending
+  std::vector<int> cub_p, cub_elem;
+  std::vector<double> cub_w, cub_u, cub_resid;
+  // device
+  int32_t *d_inc_off = nullptr, *d_inc_len = nullptr, *d_inc = nullptr, *d_pool_tet = nullptr, *d_perm = nullptr;
+  double *d_xt = nullptr, *d_vt = nullptr, *d_partial = nullptr, *d_trace = nullptr;
+  double *d_xbuf = nullptr, *d_vbuf = nullptr;
+  StepState* d_state = nullptr;
+  StepState* h_state = nullptr;
+  PrecBufs<float> f32;
+  PrecBufs<double> f64;
+  ~Mesh();
+};
+
+jgs2_status fail(jgs2_status s, const std::string& msg);
+jgs2_status set_cubature(Mesh* m, int n_cub, const std::vector<int>& elem_int, const std::vector<double>& w,
+                         const std::vector<double>& u);
+
+}  // namespace jgs2

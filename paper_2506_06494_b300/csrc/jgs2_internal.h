@@ -1,0 +1,90 @@
+// Internal data layout of the JGS2 library (device side and host bookkeeping).
+//
+// HBM layout (all arrays in the library's internal vertex order: free vertices first,
+// sorted along a Morton curve of the rest positions, then pinned vertices):
+//   TetRec<T>   one 16-byte aligned record per tet, tets sorted by smallest corner:
+//               corner ids, D_m^{-1} (B), F(x_t) (per step), V_e, mu, lam' = lam + mu,
+//               rho V_e / 4 (the element's share of each corner's lumped mass).
+//   Vec4<T>     per-vertex displacement u = x - x_t (the sweep works in displacement so
+//               that FP32 keeps the precision of small per-step motions), the inertia
+//               offset dz = z - x_t = h v_t + h^2 g, and the sweep direction D.
+//   incidence   sliced-ELL list per 32-vertex slice: entry j of lane l sits at
+//               off[slice] + 32 j + l, value = 4*tet + corner (coalesced warp reads).
+//   cubature    per free vertex and slot s: pool slot index, weight, and U_bar rows
+//               (12x3) as [slot][36][Vf] so a warp's loads are coalesced.
+//   pool        per sweep, the rotated 12x12 element Hessian (78 packed values) and
+//               the 12 rotated gradient entries of every cubature element.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace jgs2 {
+
+constexpr int kSlice = 32;       // vertices per incidence slice (one warp)
+constexpr int kMaxCub = 8;       // cubature slots per vertex at most
+constexpr int kLsTrials = 8;     // line-search steps alpha = 2^-j, j < kLsTrials
+constexpr int kPackedH = 78;     // 12x12 symmetric, upper triangle row-major
+
+template <typename T>
+struct alignas(16) TetRec {
+  int32_t v[4];
+  T B[9];      // B = D_m^{-1}, row-major; corner k>0 uses row k-1, corner 0 minus the sum
+  T Ft[9];     // F(x_t), row-major (i, j) -> 3i + j
+  T vol, mu, lp, mq;
+};
+
+template <typename T>
+struct alignas(16) Vec4 {
+  T x, y, z, w;
+};
+
+// Device-resident step state (one per mesh), read and written by the sweep kernels.
+struct StepState {
+  int32_t done;        // set once the step stops (converged / max sweeps / diverged)
+  int32_t converged;
+  int32_t status;      // 0 ok, else a jgs2_status
+  int32_t sweeps;      // sweeps applied when done
+  int32_t fallback;    // vertex solves that fell back to the uncorrected step
+  int32_t ls_rejects;
+  int32_t max_sweeps;
+  int32_t pad;
+  double rel_tol;
+  double g0;           // |g(x^0)|
+  double r;            // last relative residual
+  double slope;        // g^T D of the current sweep
+  double slope_j;      // g^T D_J (uncorrected direction)
+  double alpha;        // accepted step of the current sweep
+  int32_t dir;         // 0: step along D, 1: along D_J
+  int32_t pad2;
+  uint32_t ticket_main;
+  uint32_t ticket_energy;
+};
+
+template <typename T>
+struct DevMesh {
+  int V, Vf, T_, n_slices, nP, n_cub;
+  const TetRec<T>* tets;
+  TetRec<T>* tets_mut;
+  const int32_t* inc_off;   // [n_slices + 1]
+  const int32_t* inc_len;   // [Vf]
+  const int32_t* inc;       // entries
+  Vec4<T>* u;               // [V]
+  Vec4<T>* dz;              // [Vf]
+  Vec4<T>* D;               // [Vf] JGS2 direction
+  Vec4<T>* DJ;              // [Vf] uncorrected direction -H_ii^{-1} g_i
+  const T* mh2;             // [V] m_v / h^2 (0 for pinned)
+  const int32_t* cub_p;     // [n_cub][Vf] pool slot, -1 unused
+  const T* cub_w;           // [n_cub][Vf]
+  const T* cub_u;           // [n_cub][36][Vf]
+  const int32_t* pool_tet;  // [nP]
+  T* pool_H;                // [nP][78]
+  T* pool_G;                // [nP][12]
+  double* xt;               // [V][3]
+  double* vt;               // [V][3]
+  const int32_t* perm;      // internal -> caller
+  double inv_h2;            // 1/h^2
+  double h;
+  double grav[3];
+};
+
+}  // namespace jgs2

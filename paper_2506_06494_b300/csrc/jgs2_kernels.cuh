@@ -1,0 +1,954 @@
+// Device code of the JGS2 sweep (sm_103a). One sweep k from x^k = x_t + u:
+//   k_pool    per cubature element: assembled gradient and rotation of its corners,
+//             the element Hessian at x^k rotated into the rest frames of its corners
+//             (the R_a factors of Eq. tilde_phi), and the rotated corner gradients.
+//   k_main    per free vertex: gather g_i, H_ii and the volume-weighted deformation
+//             gradient from the incident tets, R_i = polar(F_i), the cubature sums
+//             H~_i, g~_i (Eq. cubature), the 3x3 solve of Eq. reduced_local, the
+//             direction D_i, and the FP64 partial sums |g|^2 and g.D.
+//   k_energy  (line search) per tet and per free vertex: exact energy differences
+//             E(x + alpha_j D) - E(x) for alpha_j = 2^-j, FP64 sums; the last block
+//             picks the Armijo step.
+//   k_update  u += alpha D.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "jgs2_internal.h"
+
+namespace jgs2 {
+
+// ------------------------------------------------------------------ small helpers
+
+template <typename T>
+__device__ __forceinline__ T dsqrt(T x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Fixed-order block sum of NV doubles per thread; result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* [32*NV] */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) smem[j * 32 + wid] = v[j];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double x = lane < nw ? smem[j * 32 + lane] : 0.0;
+      v[j] = warp_sum(x);
+    }
+  }
+  __syncthreads();
+}
+
+// Sum of n partials (fixed order) by one block; result valid in thread 0.
+__device__ __forceinline__ double block_sum_array(const double* p, int n, int stride,
+                                                  double* smem) {
+  double acc[1] = {0.0};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc[0] += p[(size_t)i * stride];
+  block_sum<1>(acc, smem);
+  return acc[0];
+}
+
+// Last-block-done ticket: returns true in every thread of the block that finishes last.
+__device__ __forceinline__ bool last_block(uint32_t* ticket) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = atomicAdd(ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+template <typename T>
+__device__ __forceinline__ void load3(const Vec4<T>* a, int i, T (&o)[3]) {
+  Vec4<T> q = a[i];
+  o[0] = q.x;
+  o[1] = q.y;
+  o[2] = q.z;
+}
+
+// Deformation gradient of a tet at x = x_t + u: F = F(x_t) + [u1-u0, u2-u0, u3-u0] B.
+template <typename T>
+__device__ __forceinline__ void tet_F(const TetRec<T>& r, const Vec4<T>* u, T (&F)[9]) {
+  T u0[3], uk[3];
+  load3(u, r.v[0], u0);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) F[q] = r.Ft[q];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    load3(u, r.v[k + 1], uk);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      T d = uk[i] - u0[i];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) F[3 * i + j] += d * r.B[3 * k + j];
+    }
+  }
+}
+
+// cof F = dJ/dF: column j of cof is the cross product of the other two columns of F.
+template <typename T>
+__device__ __forceinline__ void cofactor(const T (&F)[9], T (&C)[9]) {
+  C[0] = F[4] * F[8] - F[5] * F[7];
+  C[3] = F[2] * F[7] - F[1] * F[8];
+  C[6] = F[1] * F[5] - F[2] * F[4];
+  C[1] = F[5] * F[6] - F[3] * F[8];
+  C[4] = F[0] * F[8] - F[2] * F[6];
+  C[7] = F[2] * F[3] - F[0] * F[5];
+  C[2] = F[3] * F[7] - F[4] * F[6];
+  C[5] = F[1] * F[6] - F[0] * F[7];
+  C[8] = F[0] * F[4] - F[1] * F[3];
+}
+
+template <typename T>
+__device__ __forceinline__ void corner_b(const TetRec<T>& r, int c, T (&b)[3]) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const T r0 = r.B[j], r1 = r.B[3 + j], r2 = r.B[6 + j];
+    b[j] = c == 0 ? -(r0 + r1 + r2) : (c == 1 ? r0 : (c == 2 ? r1 : r2));
+  }
+}
+
+// Gather of vertex v over its incident tets (Sec. 3 energy; Sec. 4.3 vertex rotation):
+//   g  += V_e P(F_e) b_c                      (elastic gradient, P = mu F + s cof F)
+//   H  += V_e (mu |b_c|^2 I + lam' G G^T)     (diagonal 3x3 block; G = cof(F) b_c. The
+//         det-Hessian term of dP/dF contributes nothing to a diagonal block because
+//         eps_jln b_j b_l = 0, so this block is exact and positive definite.)
+//   Fs += V_e F_e,  W += V_e
+template <typename T>
+__device__ __forceinline__ void gather_vertex(const DevMesh<T>& m, int v, T (&g)[3], T (&H)[6],
+                                              T (&Fs)[9], T& W) {
+  const int slice = v / kSlice, lane = v % kSlice;
+  const int base = m.inc_off[slice] + lane;
+  const int n = m.inc_len[v];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) g[q] = T(0);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) H[q] = T(0);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) Fs[q] = T(0);
+  W = T(0);
+  for (int j = 0; j < n; ++j) {
+    const int ent = __ldg(m.inc + base + j * kSlice);
+    const int t = ent >> 2, c = ent & 3;
+    const TetRec<T> r = m.tets[t];
+    T F[9], C[9], b[3];
+    tet_F(r, m.u, F);
+    cofactor(F, C);
+    const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
+    const T s = r.lp * (J - T(1)) - r.mu;
+    corner_b(r, c, b);
+    T Fb[3], G[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Fb[i] = F[3 * i] * b[0] + F[3 * i + 1] * b[1] + F[3 * i + 2] * b[2];
+      G[i] = C[3 * i] * b[0] + C[3 * i + 1] * b[1] + C[3 * i + 2] * b[2];
+    }
+    const T vm = r.vol * r.mu, vl = r.vol * r.lp, vs = r.vol * s;
+    const T bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) g[i] += vm * Fb[i] + vs * G[i];
+    H[0] += vm * bb + vl * G[0] * G[0];
+    H[1] += vl * G[0] * G[1];
+    H[2] += vl * G[0] * G[2];
+    H[3] += vm * bb + vl * G[1] * G[1];
+    H[4] += vl * G[1] * G[2];
+    H[5] += vm * bb + vl * G[2] * G[2];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Fs[q] += r.vol * F[q];
+    W += r.vol;
+  }
+}
+
+// Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations (Golub & Van Loan 8.5);
+// A packed (a00 a01 a02 a11 a12 a22), eigenvectors are the columns of V (row-major).
+template <typename T>
+__device__ void sym3_eig(T (&A)[6], T (&V)[9]) {
+  T a[3][3] = {{A[0], A[1], A[2]}, {A[1], A[3], A[4]}, {A[2], A[4], A[5]}};
+#pragma unroll
+  for (int q = 0; q < 9; ++q) V[q] = (q % 4 == 0) ? T(1) : T(0);
+  const T eps = sizeof(T) == 4 ? T(1e-7) : T(1e-16);
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    T off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+    T dia = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+    if (off <= eps * eps * dia || off == T(0)) break;
+#pragma unroll
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+      const T apq = a[p][q];
+      if (apq == T(0)) continue;
+      const T tau = (a[q][q] - a[p][p]) / (T(2) * apq);
+      const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + dsqrt(T(1) + tau * tau));
+      const T c = T(1) / dsqrt(T(1) + t * t), s = t * c;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const T akp = a[k][p], akq = a[k][q];
+        a[k][p] = c * akp - s * akq;
+        a[k][q] = s * akp + c * akq;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const T apk = a[p][k], aqk = a[q][k];
+        a[p][k] = c * apk - s * aqk;
+        a[q][k] = s * apk + c * aqk;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const T vkp = V[3 * k + p], vkq = V[3 * k + q];
+        V[3 * k + p] = c * vkp - s * vkq;
+        V[3 * k + q] = s * vkp + c * vkq;
+      }
+    }
+  }
+  A[0] = a[0][0];
+  A[3] = a[1][1];
+  A[5] = a[2][2];
+}
+
+// Rotation closest to F with det +1 (reading R5): F^T F = V S^2 V^T; u_k = F v_k / s_k
+// for the two largest s_k, u_3 = u_1 x u_2, det V forced to +1, R = U V^T. When det F < 0
+// this flips the smallest singular value, as the SVD-based polar with a sign fix does.
+template <typename T>
+__device__ void polar_rotation(const T (&F)[9], T (&R)[9]) {
+  T S[6];
+  S[0] = F[0] * F[0] + F[3] * F[3] + F[6] * F[6];
+  S[1] = F[0] * F[1] + F[3] * F[4] + F[6] * F[7];
+  S[2] = F[0] * F[2] + F[3] * F[5] + F[6] * F[8];
+  S[3] = F[1] * F[1] + F[4] * F[4] + F[7] * F[7];
+  S[4] = F[1] * F[2] + F[4] * F[5] + F[7] * F[8];
+  S[5] = F[2] * F[2] + F[5] * F[5] + F[8] * F[8];
+  T V[9];
+  sym3_eig(S, V);
+  T ev[3] = {S[0], S[3], S[5]};
+  int o[3] = {0, 1, 2};
+  // sort eigenvalues descending
+  if (ev[o[0]] < ev[o[1]]) { int t = o[0]; o[0] = o[1]; o[1] = t; }
+  if (ev[o[1]] < ev[o[2]]) { int t = o[1]; o[1] = o[2]; o[2] = t; }
+  if (ev[o[0]] < ev[o[1]]) { int t = o[0]; o[0] = o[1]; o[1] = t; }
+  T v1[3], v2[3], v3[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    v1[k] = V[3 * k + o[0]];
+    v2[k] = V[3 * k + o[1]];
+    v3[k] = V[3 * k + o[2]];
+  }
+  // det V = +1
+  const T dv = v1[0] * (v2[1] * v3[2] - v2[2] * v3[1]) - v1[1] * (v2[0] * v3[2] - v2[2] * v3[0]) +
+               v1[2] * (v2[0] * v3[1] - v2[1] * v3[0]);
+  if (dv < T(0)) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v3[k] = -v3[k];
+  }
+  T u1[3], u2[3], u3[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    u1[i] = F[3 * i] * v1[0] + F[3 * i + 1] * v1[1] + F[3 * i + 2] * v1[2];
+    u2[i] = F[3 * i] * v2[0] + F[3 * i + 1] * v2[1] + F[3 * i + 2] * v2[2];
+  }
+  T n1 = dsqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+  if (!(n1 > T(0))) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) R[q] = (q % 4 == 0) ? T(1) : T(0);
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) u1[i] /= n1;
+  const T d12 = u1[0] * u2[0] + u1[1] * u2[1] + u1[2] * u2[2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) u2[i] -= d12 * u1[i];
+  T n2 = dsqrt(u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2]);
+  if (!(n2 > T(1e-30) * n1)) {
+    // rank-1 F: any unit vector orthogonal to u1
+    T a[3] = {T(1), T(0), T(0)};
+    if (fabs(u1[0]) > T(0.9)) { a[0] = T(0); a[1] = T(1); }
+    const T d = a[0] * u1[0] + a[1] * u1[1] + a[2] * u1[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) u2[i] = a[i] - d * u1[i];
+    n2 = dsqrt(u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2]);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) u2[i] /= n2;
+  u3[0] = u1[1] * u2[2] - u1[2] * u2[1];
+  u3[1] = u1[2] * u2[0] - u1[0] * u2[2];
+  u3[2] = u1[0] * u2[1] - u1[1] * u2[0];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) R[3 * i + j] = u1[i] * v1[j] + u2[i] * v2[j] + u3[i] * v3[j];
+}
+
+// Packed index of (r, c), r <= c, of a symmetric 12x12 (upper triangle, row-major).
+__host__ __device__ constexpr int pk(int r, int c) {
+  return r <= c ? r * 12 - (r * (r - 1)) / 2 + (c - r) : c * 12 - (c * (c - 1)) / 2 + (r - c);
+}
+
+// 3x3 SPD solve by Cholesky; returns false if a pivot is not positive.
+template <typename T>
+__device__ __forceinline__ bool chol3_solve(const T (&A)[6], const T (&b)[3], T (&x)[3]) {
+  const T l00s = A[0];
+  if (!(l00s > T(0))) return false;
+  const T l00 = dsqrt(l00s);
+  const T l10 = A[1] / l00, l20 = A[2] / l00;
+  const T l11s = A[3] - l10 * l10;
+  if (!(l11s > T(0))) return false;
+  const T l11 = dsqrt(l11s);
+  const T l21 = (A[4] - l20 * l10) / l11;
+  const T l22s = A[5] - l20 * l20 - l21 * l21;
+  if (!(l22s > T(0))) return false;
+  const T l22 = dsqrt(l22s);
+  const T y0 = b[0] / l00;
+  const T y1 = (b[1] - l10 * y0) / l11;
+  const T y2 = (b[2] - l20 * y0 - l21 * y1) / l22;
+  x[2] = y2 / l22;
+  x[1] = (y1 - l21 * x[2]) / l11;
+  x[0] = (y0 - l10 * x[1] - l20 * x[2]) / l00;
+  return true;
+}
+
+// ------------------------------------------------------------------ kernels
+
+// Step setup: caller-order FP64 state -> internal order; u = x^0 - x_t = 0 (reading R8:
+// x^0 = x_t), dz = h v_t + h^2 g for free vertices.
+template <typename T>
+__global__ void k_setup_vertices(DevMesh<T> m, const double* __restrict__ x_caller,
+                                 const double* __restrict__ v_caller,
+                                 const double* __restrict__ xk_caller) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= m.V) return;
+  const int c = m.perm[v];
+  double x[3], vel[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    x[q] = x_caller[3 * c + q];
+    vel[q] = v < m.Vf ? v_caller[3 * c + q] : 0.0;
+    m.xt[3 * v + q] = x[q];
+    m.vt[3 * v + q] = vel[q];
+  }
+  Vec4<T> u0{T(0), T(0), T(0), T(0)};
+  if (xk_caller != nullptr && v < m.Vf) {
+    u0.x = T(xk_caller[3 * c] - x[0]);
+    u0.y = T(xk_caller[3 * c + 1] - x[1]);
+    u0.z = T(xk_caller[3 * c + 2] - x[2]);
+  }
+  m.u[v] = u0;
+  if (v < m.Vf) {
+    Vec4<T> d;
+    d.x = T(m.h * vel[0] + m.h * m.h * m.grav[0]);
+    d.y = T(m.h * vel[1] + m.h * m.h * m.grav[1]);
+    d.z = T(m.h * vel[2] + m.h * m.h * m.grav[2]);
+    d.w = T(0);
+    m.dz[v] = d;
+  }
+}
+
+// F(x_t) per tet in FP64 from the FP64 step-start positions (no cancellation in FP32).
+template <typename T>
+__global__ void k_setup_tets(DevMesh<T> m) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m.T_) return;
+  TetRec<T>& r = m.tets_mut[t];
+  double x0[3], D[9];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) x0[q] = m.xt[3 * r.v[0] + q];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) D[3 * i + k] = m.xt[3 * r.v[k + 1] + i] - x0[i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double f = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) f += D[3 * i + k] * double(r.B[3 * k + j]);
+      r.Ft[3 * i + j] = T(f);
+    }
+}
+
+// Per cubature element: 4 warps gather the element's corners (warp a -> corner a), then
+// one thread forms the element Hessian of E_hat_e = V_e Psi(F_e) + sum_a m_e/(2h^2)|x_a-z_a|^2
+// at x^k and rotates it and the corner gradients into the corners' rest frames.
+// ASM = true: corner gradients are the assembled g_a (reading R3 "asm");
+// ASM = false: the element's own gradient of E_hat_e (literal Eq. cubature, "elem").
+template <typename T, bool ASM>
+__global__ void __launch_bounds__(128) k_pool(DevMesh<T> m, const StepState* __restrict__ st) {
+  if (st->done) return;
+  const int p = blockIdx.x;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ T sR[4][9];
+  __shared__ T sg[4][3];
+  const int t = m.pool_tet[p];
+  const TetRec<T> rec = m.tets[t];
+  {
+    const int v = rec.v[wid];
+    T g[3] = {T(0), T(0), T(0)}, Fs[9], W = T(0);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Fs[q] = T(0);
+    if (v < m.Vf) {
+      // lanes split the incidence list of this vertex
+      const int slice = v / kSlice, ln = v % kSlice;
+      const int base = m.inc_off[slice] + ln;
+      const int n = m.inc_len[v];
+      for (int j = lane; j < n; j += 32) {
+        const int ent = m.inc[base + j * kSlice];
+        const int tt = ent >> 2, c = ent & 3;
+        const TetRec<T> r = m.tets[tt];
+        T F[9], C[9], b[3];
+        tet_F(r, m.u, F);
+        cofactor(F, C);
+        const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
+        const T s = r.lp * (J - T(1)) - r.mu;
+        corner_b(r, c, b);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const T Fb = F[3 * i] * b[0] + F[3 * i + 1] * b[1] + F[3 * i + 2] * b[2];
+          const T G = C[3 * i] * b[0] + C[3 * i + 1] * b[1] + C[3 * i + 2] * b[2];
+          g[i] += r.vol * (r.mu * Fb + s * G);
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Fs[q] += r.vol * F[q];
+        W += r.vol;
+      }
+      // fixed-order warp reduction (tree over lanes)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) g[i] += __shfl_down_sync(0xffffffffu, g[i], o);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Fs[q] += __shfl_down_sync(0xffffffffu, Fs[q], o);
+        W += __shfl_down_sync(0xffffffffu, W, o);
+      }
+    }
+    if (lane == 0) {
+      T R[9];
+      if (v < m.Vf) {
+        T uv[3], dz[3];
+        load3(m.u, v, uv);
+        load3(m.dz, v, dz);
+        const T mh = m.mh2[v];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) g[i] += mh * (uv[i] - dz[i]);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Fs[q] /= W;
+        polar_rotation(Fs, R);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) R[q] = (q % 4 == 0) ? T(1) : T(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) g[i] = T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < 9; ++q) sR[wid][q] = R[q];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) sg[wid][i] = g[i];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  // element quantities at x^k
+  T F[9], C[9];
+  tet_F(rec, m.u, F);
+  cofactor(F, C);
+  const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
+  const T s = rec.lp * (J - T(1)) - rec.mu;
+  // dP/dF = mu I + lam' c c^T + s d2J/dF2 (9x9, index 3i+j), c = vec(cof F)
+  T A[81];
+#pragma unroll
+  for (int a = 0; a < 9; ++a)
+#pragma unroll
+    for (int b = 0; b < 9; ++b) A[9 * a + b] = rec.lp * C[a] * C[b] + (a == b ? rec.mu : T(0));
+  // d2J/dF_ij dF_kl = eps_ikm eps_jln F_mn: nonzero only for i != k and j != l
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (i == k) continue;
+      const int mm = 3 - i - k;
+      const T sik = ((k - i + 3) % 3 == 1) ? T(1) : T(-1);  // eps_ikm
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+          if (j == l) continue;
+          const int n = 3 - j - l;
+          const T sjl = ((l - j + 3) % 3 == 1) ? T(1) : T(-1);  // eps_jln
+          A[9 * (3 * i + j) + 3 * k + l] += s * sik * sjl * F[3 * mm + n];
+        }
+    }
+  // b vectors of the 4 corners
+  T bv[4][3];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    T b[3];
+    corner_b(rec, c, b);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) bv[c][j] = b[j];
+  }
+  // H_e[(a,i),(c,k)] = V sum_{j,l} b_a[j] A[(i,j),(k,l)] b_c[l] + m_e/h^2 delta
+  T He[144];
+#pragma unroll 1
+  for (int a = 0; a < 4; ++a)
+#pragma unroll 1
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          T acc = T(0);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            T row = T(0);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) row += A[9 * (3 * i + j) + 3 * k + l] * bv[c][l];
+            acc += bv[a][j] * row;
+          }
+          He[12 * (3 * a + i) + 3 * c + k] = rec.vol * acc;
+        }
+  const T mi = rec.mq * T(m.inv_h2);
+#pragma unroll
+  for (int q = 0; q < 12; ++q) He[13 * q] += mi;
+  // rotate: H' = blockdiag(R)^T H blockdiag(R)
+  T Hr[144];
+#pragma unroll 1
+  for (int a = 0; a < 4; ++a)
+#pragma unroll 1
+    for (int c = 0; c < 4; ++c) {
+      T tmp[9];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+          T acc = T(0);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) acc += He[12 * (3 * a + i) + 3 * c + k] * sR[c][3 * k + l];
+          tmp[3 * i + l] = acc;
+        }
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+          T acc = T(0);
+#pragma unroll
+          for (int i = 0; i < 3; ++i) acc += sR[a][3 * i + j] * tmp[3 * i + l];
+          Hr[12 * (3 * a + j) + 3 * c + l] = acc;
+        }
+    }
+  T* Hp = m.pool_H + (size_t)p * kPackedH;
+#pragma unroll 1
+  for (int r = 0; r < 12; ++r)
+    for (int c = r; c < 12; ++c) Hp[pk(r, c)] = T(0.5) * (Hr[12 * r + c] + Hr[12 * c + r]);
+  // rotated corner gradients
+  T* Gp = m.pool_G + (size_t)p * 12;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    T ga[3];
+    if (ASM) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) ga[i] = sg[a][i];
+    } else {
+      const int v = rec.v[a];
+      if (v < m.Vf) {
+        T uv[3], dz[3];
+        load3(m.u, v, uv);
+        load3(m.dz, v, dz);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const T Pb = (rec.mu * F[3 * i] + s * C[3 * i]) * bv[a][0] +
+                       (rec.mu * F[3 * i + 1] + s * C[3 * i + 1]) * bv[a][1] +
+                       (rec.mu * F[3 * i + 2] + s * C[3 * i + 2]) * bv[a][2];
+          ga[i] = rec.vol * Pb + mi * (uv[i] - dz[i]);
+        }
+      } else {
+        ga[0] = ga[1] = ga[2] = T(0);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Gp[3 * a + j] = sR[a][j] * ga[0] + sR[a][3 + j] * ga[1] + sR[a][6 + j] * ga[2];
+  }
+}
+
+// The per-vertex sweep (Eqs. reduced_local, cubature; Sec. 8.1). Thread per free vertex.
+template <typename T, bool CORR>
+__global__ void __launch_bounds__(128) k_main(DevMesh<T> m, StepState* st, int k,
+                                              double* __restrict__ partial /* [3][grid] */,
+                                              double* __restrict__ trace, int record) {
+  if (st->done) return;
+  __shared__ double red[96];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[3] = {0.0, 0.0, 0.0};  // |g|^2, g.D, g.D_J
+  int fb = 0;
+  if (i < m.Vf) {
+    T g[3], H[6], Fs[9], W;
+    gather_vertex(m, i, g, H, Fs, W);
+    T ui[3], dz[3];
+    load3(m.u, i, ui);
+    load3(m.dz, i, dz);
+    const T mh = m.mh2[i];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) g[q] += mh * (ui[q] - dz[q]);
+    H[0] += mh;
+    H[3] += mh;
+    H[5] += mh;
+    T A[6], rhs[3];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) A[q] = H[q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) rhs[q] = -g[q];
+    if (CORR) {
+      T R[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Fs[q] /= W;
+      polar_rotation(Fs, R);
+      T Ht[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, gt[3] = {T(0), T(0), T(0)};
+      for (int s = 0; s < m.n_cub; ++s) {
+        const int p = m.cub_p[(size_t)s * m.Vf + i];
+        if (p < 0) continue;
+        const T w = m.cub_w[(size_t)s * m.Vf + i];
+        T U[36];
+        const T* up = m.cub_u + (size_t)s * 36 * m.Vf + i;
+#pragma unroll
+        for (int q = 0; q < 36; ++q) U[q] = up[(size_t)q * m.Vf];
+        const T* Hp = m.pool_H + (size_t)p * kPackedH;
+        const T* Gp = m.pool_G + (size_t)p * 12;
+#pragma unroll
+        for (int r = 0; r < 12; ++r) {
+          T tr[3] = {T(0), T(0), T(0)};
+#pragma unroll
+          for (int c = 0; c < 12; ++c) {
+            const T h = __ldg(Hp + pk(r, c));
+            tr[0] += h * U[3 * c];
+            tr[1] += h * U[3 * c + 1];
+            tr[2] += h * U[3 * c + 2];
+          }
+          const T wu0 = w * U[3 * r], wu1 = w * U[3 * r + 1], wu2 = w * U[3 * r + 2];
+          Ht[0] += wu0 * tr[0];
+          Ht[1] += wu0 * tr[1];
+          Ht[2] += wu0 * tr[2];
+          Ht[3] += wu1 * tr[1];
+          Ht[4] += wu1 * tr[2];
+          Ht[5] += wu2 * tr[2];
+          const T gr = __ldg(Gp + r);
+          gt[0] += wu0 * gr;
+          gt[1] += wu1 * gr;
+          gt[2] += wu2 * gr;
+        }
+      }
+      // back to world: H~ = R H~' R^T, g~ = R g~'
+      T Hf[9] = {Ht[0], Ht[1], Ht[2], Ht[1], Ht[3], Ht[4], Ht[2], Ht[4], Ht[5]};
+      T RH[9];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          RH[3 * a + b] = R[3 * a] * Hf[b] + R[3 * a + 1] * Hf[3 + b] + R[3 * a + 2] * Hf[6 + b];
+      T Hw[9];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          Hw[3 * a + b] = RH[3 * a] * R[3 * b] + RH[3 * a + 1] * R[3 * b + 1] + RH[3 * a + 2] * R[3 * b + 2];
+      A[0] += Hw[0];
+      A[1] += T(0.5) * (Hw[1] + Hw[3]);
+      A[2] += T(0.5) * (Hw[2] + Hw[6]);
+      A[3] += Hw[4];
+      A[4] += T(0.5) * (Hw[5] + Hw[7]);
+      A[5] += Hw[8];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) rhs[a] -= R[3 * a] * gt[0] + R[3 * a + 1] * gt[1] + R[3 * a + 2] * gt[2];
+    }
+    // uncorrected per-vertex Newton direction (H_ii is SPD for this material)
+    T dj[3];
+    {
+      T rg[3] = {-g[0], -g[1], -g[2]};
+      if (!chol3_solve(H, rg, dj)) dj[0] = dj[1] = dj[2] = T(0);
+    }
+    T d[3];
+    if (!CORR) {
+      d[0] = dj[0];
+      d[1] = dj[1];
+      d[2] = dj[2];
+    } else if (!chol3_solve(A, rhs, d)) {
+      // reading R7: the vertex takes the uncorrected step
+      d[0] = dj[0];
+      d[1] = dj[1];
+      d[2] = dj[2];
+      fb = 1;
+    }
+    Vec4<T> dv{d[0], d[1], d[2], T(0)};
+    m.D[i] = dv;
+    Vec4<T> djv{dj[0], dj[1], dj[2], T(0)};
+    m.DJ[i] = djv;
+    acc[0] = double(g[0]) * double(g[0]) + double(g[1]) * double(g[1]) + double(g[2]) * double(g[2]);
+    acc[1] = double(g[0]) * double(d[0]) + double(g[1]) * double(d[1]) + double(g[2]) * double(d[2]);
+    acc[2] = double(g[0]) * double(dj[0]) + double(g[1]) * double(dj[1]) + double(g[2]) * double(dj[2]);
+  }
+  if (__syncthreads_or(fb)) {
+    const int nfb = __syncthreads_count(fb);
+    if (threadIdx.x == 0) atomicAdd(&st->fallback, nfb);
+  }
+  block_sum<3>(acc, red);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = acc[0];
+    partial[gridDim.x + blockIdx.x] = acc[1];
+    partial[2 * gridDim.x + blockIdx.x] = acc[2];
+  }
+  if (!last_block(&st->ticket_main)) return;
+  const double r2 = block_sum_array(partial, gridDim.x, 1, red);
+  const double gd = block_sum_array(partial + gridDim.x, gridDim.x, 1, red);
+  const double gdj = block_sum_array(partial + 2 * gridDim.x, gridDim.x, 1, red);
+  if (threadIdx.x == 0) {
+    st->ticket_main = 0;
+    const double gn = sqrt(r2);
+    if (k == 0) st->g0 = gn;
+    const double g0 = st->g0;
+    const double r = g0 > 0.0 ? gn / g0 : 0.0;
+    st->r = r;
+    st->slope = gd;
+    st->slope_j = gdj;
+    st->alpha = 1.0;
+    st->dir = 0;
+    if (record && k < 4096) trace[k] = r;
+    if (!isfinite(r) || !isfinite(gd)) {
+      st->status = 6;  // JGS2_EDIVERGED
+      st->done = 1;
+      st->sweeps = k;
+    } else if (r <= st->rel_tol || g0 == 0.0) {
+      st->converged = 1;
+      st->done = 1;
+      st->sweeps = k;
+    } else if (k >= st->max_sweeps) {
+      st->done = 1;
+      st->sweeps = k;
+    }
+  }
+}
+
+// Exact energy change of a tet for the displacement increment alpha*d (no cancellation):
+// with G = alpha dF, det(F+G) - det F = cof(F):G + F:cof(G) + det G, and
+// Psi(F+G) - Psi(F) = mu/2 (2F:G + G:G) - mu dJ + lam'/2 dJ (dJ + 2(J - 1)).
+template <typename T>
+__device__ __forceinline__ void tet_dF(const TetRec<T>& r, const Vec4<T>* D, int Vf, T (&dF)[9]) {
+  T d0[3] = {T(0), T(0), T(0)}, dk[3];
+  if (r.v[0] < Vf) load3(D, r.v[0], d0);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) dF[q] = T(0);
+#pragma unroll
+  for (int kk = 0; kk < 3; ++kk) {
+    dk[0] = dk[1] = dk[2] = T(0);
+    if (r.v[kk + 1] < Vf) load3(D, r.v[kk + 1], dk);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) dF[3 * i + j] += (dk[i] - d0[i]) * r.B[3 * kk + j];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void tet_dpsi(const TetRec<T>& r, const T (&F)[9], const T (&C)[9], T J,
+                                         const T (&dF)[9], double* out /* [kLsTrials] */) {
+  T cdF[9];
+  cofactor(dF, cdF);
+  T FdF = T(0), dFdF = T(0), CdF = T(0), FcdF = T(0);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    FdF += F[q] * dF[q];
+    dFdF += dF[q] * dF[q];
+    CdF += C[q] * dF[q];
+    FcdF += F[q] * cdF[q];
+  }
+  const T detdF = dF[0] * cdF[0] + dF[1] * cdF[1] + dF[2] * cdF[2];
+#pragma unroll
+  for (int j = 0; j < kLsTrials; ++j) {
+    const T a = T(1) / T(1 << j);
+    const T dJ = a * CdF + a * a * FcdF + a * a * a * detdF;
+    const T dpsi = T(0.5) * r.mu * (T(2) * a * FdF + a * a * dFdF) - r.mu * dJ +
+                   T(0.5) * r.lp * dJ * (dJ + T(2) * (J - T(1)));
+    out[j] = double(r.vol) * double(dpsi);
+  }
+}
+
+// Line search (reading R17): energy changes along D (and along D_J when ND = 2) for
+// alpha_j = 2^-j; the last block takes the first Armijo-satisfying trial, D before D_J.
+template <typename T, int ND>
+__global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st,
+                                                double* __restrict__ partial /* [ND*8][grid] */,
+                                                int tet_blocks) {
+  if (st->done) return;
+  constexpr int NT = ND * kLsTrials;
+  __shared__ double red[32 * NT];
+  double acc[NT];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) acc[j] = 0.0;
+  if ((int)blockIdx.x < tet_blocks) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m.T_) {
+      const TetRec<T> r = m.tets[t];
+      T F[9], C[9], dF[9];
+      tet_F(r, m.u, F);
+      cofactor(F, C);
+      const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
+      tet_dF(r, m.D, m.Vf, dF);
+      tet_dpsi(r, F, C, J, dF, acc);
+      if (ND == 2) {
+        tet_dF(r, m.DJ, m.Vf, dF);
+        tet_dpsi(r, F, C, J, dF, acc + kLsTrials);
+      }
+    }
+  } else {
+    const int v = (blockIdx.x - tet_blocks) * blockDim.x + threadIdx.x;
+    if (v < m.Vf) {
+      T uv[3], dz[3], d[3];
+      load3(m.u, v, uv);
+      load3(m.dz, v, dz);
+      const double mh = double(m.mh2[v]);
+#pragma unroll
+      for (int dir = 0; dir < ND; ++dir) {
+        load3(dir == 0 ? m.D : m.DJ, v, d);
+        double dd = 0.0, de = 0.0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          dd += double(d[q]) * double(d[q]);
+          de += double(d[q]) * (double(uv[q]) - double(dz[q]));
+        }
+#pragma unroll
+        for (int j = 0; j < kLsTrials; ++j) {
+          const double a = 1.0 / double(1 << j);
+          acc[dir * kLsTrials + j] = 0.5 * mh * (2.0 * a * de + a * a * dd);
+        }
+      }
+    }
+  }
+  block_sum<NT>(acc, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NT; ++j) partial[(size_t)j * gridDim.x + blockIdx.x] = acc[j];
+  }
+  if (!last_block(&st->ticket_energy)) return;
+  double dE[NT];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) dE[j] = block_sum_array(partial + (size_t)j * gridDim.x, gridDim.x, 1, red);
+  if (threadIdx.x == 0) {
+    st->ticket_energy = 0;
+    double alpha = 0.0;
+    int dir = 0;
+    bool ok = false;
+    for (int dd = 0; dd < ND && !ok; ++dd) {
+      const double slope = dd == 0 ? st->slope : st->slope_j;
+      for (int j = 0; j < kLsTrials; ++j) {
+        const double a = 1.0 / double(1 << j);
+        if (dE[dd * kLsTrials + j] <= 1e-4 * a * slope) {
+          alpha = a;
+          dir = dd;
+          ok = true;
+          break;
+        }
+      }
+    }
+    if (!ok) st->ls_rejects += 1;
+    st->alpha = alpha;
+    st->dir = dir;
+  }
+}
+
+template <typename T>
+__global__ void k_update(DevMesh<T> m, const StepState* __restrict__ st) {
+  if (st->done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.Vf) return;
+  const T a = T(st->alpha);
+  Vec4<T> u = m.u[i];
+  const Vec4<T> d = st->dir ? m.DJ[i] : m.D[i];
+  u.x += a * d.x;
+  u.y += a * d.y;
+  u.z += a * d.z;
+  m.u[i] = u;
+}
+
+// x_{t+1} = x_t + u, v_{t+1} = u / h, written back in caller order.
+template <typename T>
+__global__ void k_finish(DevMesh<T> m, double* __restrict__ x_caller, double* __restrict__ v_caller) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= m.V) return;
+  const int c = m.perm[v];
+  T u[3];
+  load3(m.u, v, u);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    x_caller[3 * c + q] = m.xt[3 * v + q] + double(u[q]);
+    if (v_caller) v_caller[3 * c + q] = double(u[q]) / m.h;
+  }
+}
+
+// FP64 energy and gradient of the current state (parity helper).
+template <typename T>
+__global__ void k_grad(DevMesh<T> m, double* __restrict__ g_caller) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.V) return;
+  const int c = m.perm[i];
+  if (i >= m.Vf) {
+    g_caller[3 * c] = g_caller[3 * c + 1] = g_caller[3 * c + 2] = 0.0;
+    return;
+  }
+  T g[3], H[6], Fs[9], W;
+  gather_vertex(m, i, g, H, Fs, W);
+  T ui[3], dz[3];
+  load3(m.u, i, ui);
+  load3(m.dz, i, dz);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) g_caller[3 * c + q] = double(g[q] + m.mh2[i] * (ui[q] - dz[q]));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_energy_abs(DevMesh<T> m, double* __restrict__ partial,
+                                                    int tet_blocks) {
+  __shared__ double red[32];
+  double acc[1] = {0.0};
+  if ((int)blockIdx.x < tet_blocks) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m.T_) {
+      const TetRec<T> r = m.tets[t];
+      T F[9], C[9];
+      tet_F(r, m.u, F);
+      cofactor(F, C);
+      const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
+      T FF = T(0);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) FF += F[q] * F[q];
+      acc[0] = double(r.vol) * (0.5 * double(r.mu) * (double(FF) - 3.0) - double(r.mu) * (double(J) - 1.0) +
+                                0.5 * double(r.lp) * (double(J) - 1.0) * (double(J) - 1.0));
+    }
+  } else {
+    const int v = (blockIdx.x - tet_blocks) * blockDim.x + threadIdx.x;
+    if (v < m.Vf) {
+      T uv[3], dz[3];
+      load3(m.u, v, uv);
+      load3(m.dz, v, dz);
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) s += (double(uv[q]) - double(dz[q])) * (double(uv[q]) - double(dz[q]));
+      acc[0] = 0.5 * double(m.mh2[v]) * s;
+    }
+  }
+  block_sum<1>(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc[0];
+}
+
+}  // namespace jgs2

@@ -1,0 +1,242 @@
+"""Thin ctypes binding of libjgs2.so (argument marshalling only; every step of the sweep runs
+in the library's CUDA kernels). Names follow the C ABI in include/jgs2.h.
+
+Device state is passed as torch CUDA tensors (torch supplies device memory and streams);
+host arrays as numpy. There is no CPU fallback: if the shared library is missing or a
+call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libjgs2.so")
+
+TRACE_MAX = 4096
+FP64, FP32 = 0, 1
+CORR_ASM, CORR_ELEM, CORR_OFF = 0, 1, 2
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTPRECOMPUTED", 5: "ENOTCONVERGED",
+          6: "EDIVERGED", 7: "ENONSPD", 8: "ETIMEOUT", 9: "EINTERSECT"}
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("n_vertices", C.c_int32), ("n_tets", C.c_int32),
+                ("rest_pos", C.POINTER(C.c_double)), ("tets", C.POINTER(C.c_int32)),
+                ("youngs", C.POINTER(C.c_double)), ("poisson", C.POINTER(C.c_double)),
+                ("density", C.POINTER(C.c_double)), ("pinned", C.POINTER(C.c_uint8)),
+                ("gravity", C.c_double * 3), ("dt", C.c_double)]
+
+
+class PrecomputeOpts(C.Structure):
+    _fields_ = [("n_cub", C.c_int32), ("n_train", C.c_int32), ("n_cand", C.c_int32),
+                ("n_pool", C.c_int32), ("nnls_tol", C.c_double), ("seed", C.c_uint64),
+                ("n_threads", C.c_int32)]
+
+
+class CubatureBlob(C.Structure):
+    _fields_ = [("n_cub", C.c_int32), ("elem", C.POINTER(C.c_int32)),
+                ("weight", C.POINTER(C.c_double)), ("ubar", C.POINTER(C.c_double))]
+
+
+class StepOpts(C.Structure):
+    _fields_ = [("max_sweeps", C.c_int32), ("rel_tol", C.c_double), ("precision", C.c_int32),
+                ("correction", C.c_int32), ("line_search", C.c_int32), ("check_every", C.c_int32),
+                ("record_trace", C.c_int32)]
+
+
+class StepReport(C.Structure):
+    _fields_ = [("sweeps", C.c_int32), ("converged", C.c_int32), ("fallback", C.c_int32),
+                ("ls_rejects", C.c_int32), ("rel_residual", C.c_double), ("g0", C.c_double),
+                ("ms", C.c_double), ("trace_len", C.c_int32), ("trace", C.c_double * TRACE_MAX)]
+
+
+_lib = None
+
+EXPORTS = ["jgs2_precompute_opts_default", "jgs2_step_opts_default", "jgs2_mesh_create",
+           "jgs2_precompute", "jgs2_precompute_import", "jgs2_precompute_export",
+           "jgs2_mesh_n_cub", "jgs2_step", "jgs2_step_host", "jgs2_sweeps",
+           "jgs2_energy_gradient", "jgs2_mesh_destroy", "jgs2_last_error"]
+
+
+def lib():
+    """Loads libjgs2.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libjgs2.so not built ({LIB_PATH}); run python -m paper_2506_06494_b300.build")
+    L = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    L.jgs2_precompute_opts_default.argtypes = [C.POINTER(PrecomputeOpts)]
+    L.jgs2_step_opts_default.argtypes = [C.POINTER(StepOpts)]
+    L.jgs2_mesh_create.argtypes = [C.POINTER(MeshDesc), C.POINTER(P)]
+    L.jgs2_precompute.argtypes = [P, C.POINTER(PrecomputeOpts)]
+    L.jgs2_precompute_import.argtypes = [P, C.POINTER(CubatureBlob)]
+    L.jgs2_precompute_export.argtypes = [P, P, P, P, P]
+    L.jgs2_mesh_n_cub.argtypes = [P]
+    L.jgs2_mesh_n_cub.restype = C.c_int32
+    L.jgs2_step.argtypes = [P, P, P, C.POINTER(StepOpts), P, C.POINTER(StepReport)]
+    L.jgs2_step_host.argtypes = [P, P, P, C.POINTER(StepOpts), P, C.POINTER(StepReport)]
+    L.jgs2_sweeps.argtypes = [P, P, P, P, C.c_int32, C.POINTER(StepOpts), P]
+    L.jgs2_energy_gradient.argtypes = [P, P, P, P, P, P, P]
+    L.jgs2_mesh_destroy.argtypes = [P]
+    L.jgs2_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("jgs2_mesh_destroy", "jgs2_last_error", "jgs2_mesh_n_cub",
+                        "jgs2_precompute_opts_default", "jgs2_step_opts_default"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+class JGS2Error(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status, ok=(0,)):
+    if status not in ok:
+        raise JGS2Error(status, lib().jgs2_last_error().decode())
+    return status
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def step_opts(**kw) -> StepOpts:
+    o = StepOpts()
+    lib().jgs2_step_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def precompute_opts(**kw) -> PrecomputeOpts:
+    o = PrecomputeOpts()
+    lib().jgs2_precompute_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def _dev(t):
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous(), \
+        "device state must be a contiguous float64 CUDA tensor [V,3]"
+    return C.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    """A tet mesh living on the current CUDA device (jgs2_mesh_create)."""
+
+    def __init__(self, X, tets, youngs, poisson, density, pinned=None, gravity=(0, 0, -9.8), dt=1 / 120):
+        self._keep = [np.ascontiguousarray(X, dtype=np.float64),
+                      np.ascontiguousarray(tets, dtype=np.int32),
+                      np.ascontiguousarray(youngs, dtype=np.float64),
+                      np.ascontiguousarray(poisson, dtype=np.float64),
+                      np.ascontiguousarray(density, dtype=np.float64),
+                      None if pinned is None else np.ascontiguousarray(pinned, dtype=np.uint8)]
+        X, T, E, nu, rho, pin = self._keep
+        d = MeshDesc()
+        d.n_vertices = X.shape[0]
+        d.n_tets = T.shape[0]
+        d.rest_pos = _ptr(X, C.c_double)
+        d.tets = _ptr(T, C.c_int32)
+        d.youngs = _ptr(E, C.c_double)
+        d.poisson = _ptr(nu, C.c_double)
+        d.density = _ptr(rho, C.c_double)
+        d.pinned = _ptr(pin, C.c_uint8) if pin is not None else C.POINTER(C.c_uint8)()
+        for q in range(3):
+            d.gravity[q] = float(gravity[q])
+        d.dt = float(dt)
+        h = C.c_void_p()
+        _check(lib().jgs2_mesh_create(C.byref(d), C.byref(h)))
+        self.handle = h
+        self.V = int(X.shape[0])
+        self.T = int(T.shape[0])
+
+    @classmethod
+    def from_scene(cls, s):
+        return cls(s.X, s.tets, s.youngs, s.poisson, s.density, s.pinned, s.gravity, s.dt)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().jgs2_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def precompute(self, **kw):
+        o = precompute_opts(**kw)
+        _check(lib().jgs2_precompute(self.handle, C.byref(o)))
+
+    def precompute_import(self, elem, weight, ubar):
+        elem = np.ascontiguousarray(elem, dtype=np.int32)
+        weight = np.ascontiguousarray(weight, dtype=np.float64)
+        ubar = np.ascontiguousarray(ubar, dtype=np.float64)
+        V, nc = elem.shape
+        assert V == self.V and weight.shape == (V, nc) and ubar.size == V * nc * 36
+        b = CubatureBlob()
+        b.n_cub = nc
+        b.elem = _ptr(elem, C.c_int32)
+        b.weight = _ptr(weight, C.c_double)
+        b.ubar = _ptr(ubar, C.c_double)
+        _check(lib().jgs2_precompute_import(self.handle, C.byref(b)))
+
+    def precompute_export(self):
+        nc = lib().jgs2_mesh_n_cub(self.handle)
+        elem = np.zeros((self.V, nc), np.int32)
+        w = np.zeros((self.V, nc))
+        u = np.zeros((self.V, nc, 4, 3, 3))
+        r = np.zeros(self.V)
+        _check(lib().jgs2_precompute_export(self.handle, elem.ctypes.data, w.ctypes.data, u.ctypes.data,
+                                            r.ctypes.data))
+        return elem, w, u, r
+
+    def step(self, x, v, opts=None, stream=None, report=None):
+        """jgs2_step on float64 CUDA tensors x, v [V,3] (updated in place)."""
+        opts = opts or step_opts()
+        rep = report if report is not None else StepReport()
+        st = lib().jgs2_step(self.handle, _dev(x), _dev(v), C.byref(opts), C.c_void_p(_stream_ptr(stream)),
+                             C.byref(rep))
+        _check(st, ok=(0, 5))
+        return rep
+
+    def step_host(self, x, v, opts=None, stream=None, report=None):
+        """jgs2_step_host on C-contiguous float64 numpy arrays (updated in place)."""
+        assert x.dtype == np.float64 and v.dtype == np.float64 and x.flags.c_contiguous and v.flags.c_contiguous
+        opts = opts or step_opts()
+        rep = report if report is not None else StepReport()
+        st = lib().jgs2_step_host(self.handle, x.ctypes.data, v.ctypes.data, C.byref(opts),
+                                  C.c_void_p(_stream_ptr(stream)), C.byref(rep))
+        _check(st, ok=(0, 5))
+        return rep
+
+    def sweeps(self, x_t, v_t, x_k, n, opts=None, stream=None):
+        opts = opts or step_opts()
+        _check(lib().jgs2_sweeps(self.handle, _dev(x_t), _dev(v_t), _dev(x_k), int(n), C.byref(opts),
+                                 C.c_void_p(_stream_ptr(stream))))
+
+    def energy_gradient(self, x_t, v_t, x, stream=None):
+        import torch
+        g = torch.empty_like(x)
+        E = C.c_double()
+        _check(lib().jgs2_energy_gradient(self.handle, _dev(x_t), _dev(v_t), _dev(x), C.byref(E), _dev(g),
+                                          C.c_void_p(_stream_ptr(stream))))
+        return E.value, g

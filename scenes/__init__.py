@@ -240,21 +240,27 @@ def random_cubature(X, tets, pinned, n_cub=4, seed=0, w_max=2.0, u_sigma=0.3):
     for b in range(nb):
         el = np.nonzero(tbody == b)[0]
         pools[b] = np.sort(rng.choice(el, size=min(256, len(el)), replace=False))
-    elem = -np.ones((V, n_cub), np.int64)
-    weight = np.zeros((V, n_cub))
-    ubar = np.zeros((V, n_cub, 4, 3, 3))
     pin = np.asarray(pinned).astype(bool)
-    for i in np.nonzero(~pin)[0]:
-        pool = pools[body[i]]
-        ok = pool[~np.any(tets[pool] == i, axis=1)]
-        k = min(n_cub, len(ok))
-        if k == 0:
-            continue
-        pick = rng.choice(ok, size=k, replace=False)
-        elem[i, :k] = pick
-        weight[i, :k] = rng.uniform(0.0, w_max, size=k)
-        ubar[i, :k] = rng.normal(0.0, u_sigma, size=(k, 4, 3, 3))
-        ubar[i, :k][pin[tets[pick]]] = 0.0
+    free = np.nonzero(~pin)[0]
+    elem = -np.ones((V, n_cub), np.int64)
+    n_draw = 4 * n_cub
+    cand = np.empty((len(free), n_draw), np.int64)
+    for b in range(nb):
+        sel = body[free] == b
+        cand[sel] = pools[b][rng.integers(0, len(pools[b]), size=(int(sel.sum()), n_draw))]
+    ok = ~np.any(tets[cand] == free[:, None, None], axis=2)
+    for j in range(n_draw):  # first n_cub distinct, non-incident draws per vertex
+        c = cand[:, j]
+        dup = np.any(elem[free] == c[:, None], axis=1)
+        slot = (elem[free] >= 0).sum(axis=1)
+        take = ok[:, j] & ~dup & (slot < n_cub)
+        elem[free[take], slot[take]] = c[take]
+    used = elem >= 0
+    weight = np.where(used, rng.uniform(0.0, w_max, size=(V, n_cub)), 0.0)
+    ubar = rng.normal(0.0, u_sigma, size=(V, n_cub, 4, 3, 3))
+    ubar[~used] = 0.0
+    corner_pinned = used[..., None] & pin[tets[np.maximum(elem, 0)]]
+    ubar[corner_pinned] = 0.0
     return elem, weight, ubar
 
 

@@ -1,0 +1,88 @@
+"""The C ABI library loads, exports every symbol include/jgs2.h declares, and rejects bad
+mesh descriptions before touching a GPU (no compute calls here)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2506_06494_b300 as p
+import scenes
+from paper_2506_06494_b300 import jgs2 as J
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "jgs2.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(jgs2_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2506_06494_b300 import build
+    build.build()
+    return p.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    syms = declared_symbols()
+    assert "jgs2_step" in syms and "jgs2_mesh_create" in syms
+    for s in syms:
+        assert hasattr(L, s), s
+
+
+def test_default_options(L):
+    o = p.step_opts()
+    assert o.max_sweeps == 500 and o.rel_tol == 1e-4 and o.precision == p.FP32
+    assert o.correction == p.CORR_ASM and o.line_search == 1
+    q = p.precompute_opts()
+    assert q.n_cub == 4 and q.n_train == 20 and q.n_cand == 32 and q.nnls_tol == 0.01
+
+
+def _desc(X, T, E, nu, rho, pin=None, dt=1 / 120):
+    d = J.MeshDesc()
+    d.n_vertices = len(X)
+    d.n_tets = len(T)
+    d.rest_pos = X.ctypes.data_as(C.POINTER(C.c_double))
+    d.tets = T.ctypes.data_as(C.POINTER(C.c_int32))
+    d.youngs = E.ctypes.data_as(C.POINTER(C.c_double))
+    d.poisson = nu.ctypes.data_as(C.POINTER(C.c_double))
+    d.density = rho.ctypes.data_as(C.POINTER(C.c_double))
+    d.pinned = C.POINTER(C.c_uint8)() if pin is None else pin.ctypes.data_as(C.POINTER(C.c_uint8))
+    d.dt = dt
+    return d
+
+
+@pytest.mark.parametrize("case", ["inverted", "index", "material", "dt", "empty"])
+def test_mesh_create_rejects_bad_input(L, case):
+    s = scenes.cube_scene()
+    X = s.X.copy()
+    T = s.tets.astype(np.int32).copy()
+    E, nu, rho = s.youngs.copy(), s.poisson.copy(), s.density.copy()
+    dt = 1 / 120
+    if case == "inverted":
+        T[5, [1, 2]] = T[5, [2, 1]]
+    elif case == "index":
+        T[7, 3] = len(X)
+    elif case == "material":
+        nu[3] = 0.5
+    elif case == "dt":
+        dt = 0.0
+    d = _desc(X, T, E, nu, rho, None, dt)
+    if case == "empty":
+        d.n_tets = 0
+    h = C.c_void_p()
+    st = L.jgs2_mesh_create(C.byref(d), C.byref(h))
+    assert st == 1  # JGS2_EINVAL, raised before any device allocation
+    assert not h.value
+    assert len(L.jgs2_last_error()) > 0
+
+
+def test_null_arguments(L):
+    h = C.c_void_p()
+    assert L.jgs2_mesh_create(None, C.byref(h)) == 1
+    assert L.jgs2_step(None, None, None, None, None, None) == 1
+    assert L.jgs2_precompute_import(None, None) == 1
