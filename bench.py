@@ -1,0 +1,295 @@
+#!/usr/bin/env python
+"""Benchmark of the JGS2 hot path: milliseconds per implicit-Euler time step to a 1e-4
+relative residual, JGS2 sweeps per second, and the main sweep kernel's fraction of the
+measured HBM bandwidth.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload spheres|beam|cube]
+    python bench.py --impl reference ...     # the FP64 CPU oracle on the host cores
+
+One step = one call of jgs2_step (all sweeps of the step: pool, main, line-search energy
+and update kernels plus the per-step setup) on inputs already resident in HBM. With N > 1
+(torchrun) every rank steps its own replica of the scene (the sweep does not shard across
+GPUs in this build); the reported time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms/step to 1e-4 rel. residual at 3.5M tets"
+KIND = ["k_pool", "k_main", "k_energy", "k_update", "setup"]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def build_scene(name, n_spheres=10):
+    import scenes
+    if name == "spheres":
+        s = scenes.spheres_scene(n_spheres=n_spheres, contact=0)
+        return s, f"{n_spheres} voxel spheres r=0.1 m, 48 cells across, {s.n_tets:,} tets"
+    if name == "beam":
+        return scenes.beam_scene(), "20x20x100-vertex Kuhn beam 0.02x0.02x0.1 m, 214,434 tets"
+    if name == "cube":
+        return scenes.cube_scene(), "5x5x5-vertex Kuhn cube, 384 tets"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def main_bytes_per_launch(V_f, T, n_cub, fp_bytes=4):
+    """Algorithmic DRAM bytes of one k_main launch (each datum moved once):
+    per tet: 4 corner ids (16 B) + B (9) + F(x_t) (9) + V_e, mu, lam' (3) scalars + its 4
+    incidence entries (16 B); per free vertex: u read, dz read, D and D_J written (3 scalars
+    each), m/h^2, the incidence count (4 B) and the cubature record n_cub x (pool index 4 B,
+    weight, 36 U_bar entries)."""
+    per_tet = 16 + 21 * fp_bytes + 16
+    per_vertex = (4 * 3 + 1) * fp_bytes + 4 + n_cub * (4 + 37 * fp_bytes)
+    return per_tet * T + per_vertex * V_f
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [q.strip() for q in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(scene, sweeps_per_step, n_sample=48, seed=0):
+    """Oracle (FP64 numpy, one host thread) on a bounded sample: the per-vertex JGS2
+    direction of n_sample free vertices, scaled to a full step (sweeps_per_step + 1 sweeps,
+    every free vertex)."""
+    from oracle import fem, local
+    import scenes
+    s = scene
+    elem, w, u = scenes.random_cubature(s.X, s.tets, s.pinned, 4, seed=seed, w_max=0.5, u_sigma=0.2)
+    lm = local.LocalMesh(s.X, s.tets, s.youngs, s.poisson, s.density, s.pinned)
+    z = fem.inertia_target(s.X, s.v0, s.dt, s.gravity)
+    free = np.nonzero(~s.pinned.astype(bool))[0]
+    pick = np.random.default_rng(seed).choice(free, size=min(n_sample, len(free)), replace=False)
+    t0 = time.perf_counter()
+    for i in pick:
+        lm.direction(i, s.X, z, s.dt, elem[i], w[i], u[i])
+    per_vertex = (time.perf_counter() - t0) / len(pick)
+    ms = per_vertex * len(free) * (sweeps_per_step + 1) * 1e3
+    return {"value": ms, "unit": "ms/step", "cores": 1, "kind": "oracle",
+            "sample": f"oracle per-vertex JGS2 direction of {len(pick)} sampled free vertices "
+                      f"({per_vertex * 1e3:.1f} ms each), scaled x{len(free)} vertices x "
+                      f"{sweeps_per_step + 1:.0f} sweeps/step"}
+
+
+def run_reference(args, rank, world):
+    scene, desc = build_scene(args.workload, args.n_spheres)
+    out = {"impl": "reference", "metric": METRIC, "unit": "ms/step", "higher_is_better": False,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "scene": desc, "cubature": args.cubature, "tets": scene.n_tets, "vertices": scene.n_vertices}}
+    if rank != 0:
+        return None
+    sweeps = args.ref_sweeps
+    vals = []
+    cb = None
+    for _ in range(args.warmup + args.steps):
+        cb = cpu_baseline(scene, sweeps, n_sample=16)
+        vals.append(cb["value"])
+    v = float(np.median(vals[args.warmup:]))
+    cb["value"] = v
+    out.update({"value": v, "ms_per_step": v, "scaling": "weak", "vs_baseline": None,
+                "cpu_baseline": cb, "e2e": {"value": v, "unit": "ms/step", "h2d_bytes_per_step": 0,
+                                            "d2h_bytes_per_step": 0}})
+    return out
+
+
+def run_jgs2(args, rank, world, local_rank):
+    import torch
+    import paper_2506_06494_b300 as p
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    scene, desc = build_scene(args.workload, args.n_spheres)
+    t0 = time.perf_counter()
+    mesh = p.Mesh.from_scene(scene)
+    if args.cubature == "precompute":
+        mesh.precompute(n_cub=args.n_cub)
+    else:
+        # seeded synthetic records: same kernel work, no convergence meaning (profiling only)
+        import scenes
+        mesh.precompute_import(*scenes.random_cubature(scene.X, scene.tets, scene.pinned, args.n_cub, seed=0,
+                                                       w_max=0.5, u_sigma=0.2))
+    t_pre = time.perf_counter() - t0
+    prec = p.FP32 if args.precision == "fp32" else p.FP64
+    corr = {"asm": p.CORR_ASM, "elem": p.CORR_ELEM, "off": p.CORR_OFF}[args.correction]
+    opts = p.step_opts(precision=prec, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4, profile=1)
+    x = torch.tensor(scene.X, dtype=torch.float64, device=dev)
+    v = torch.tensor(scene.v0, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        mesh.step(x, v, opts, stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    gidx = vis.split(",")[local_rank] if vis else str(local_rank)
+    clocks = Clocks(gidx)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    reps = []
+    for _ in range(args.steps):
+        r = mesh.step(x, v, opts, stream)
+        reps.append((r.sweeps, r.converged, r.rel_residual, list(r.kernel_ms), list(r.kernel_launches),
+                     r.launches, r.fallback, r.ls_rejects))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    sweeps = np.array([q[0] for q in reps])
+    kms = np.sum([q[3] for q in reps], axis=0)
+    kl = np.sum([q[4] for q in reps], axis=0)
+    launches = int(sum(q[5] for q in reps))
+    ms_step = ms_total / args.steps
+    # end to end: host buffers through jgs2_step_host, copies inside the timed region
+    xh = x.cpu().numpy().copy()
+    vh = v.cpu().numpy().copy()
+    opts_e2e = p.step_opts(precision=prec, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_e2e = 0 if args.no_e2e else args.steps
+    for _ in range(n_e2e):
+        mesh.step_host(xh, vh, opts_e2e, stream)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / max(n_e2e, 1) if n_e2e else None
+    # roofline of the dominant kernel (k_main)
+    hbm, peak_kind = peaks()
+    n_cub = args.n_cub if corr != p.CORR_OFF else 0
+    Vf = int((~scene.pinned.astype(bool)).sum())
+    fpb = 4 if prec == p.FP32 else 8
+    bytes_main = main_bytes_per_launch(Vf, scene.n_tets, n_cub, fpb)
+    main_ms = kms[1] / max(kl[1], 1)
+    achieved = bytes_main / (main_ms * 1e-3) / 1e9
+    share = {KIND[q]: round(float(kms[q] / max(kms.sum(), 1e-12)), 4) for q in range(5)}
+    out = {
+        "metric": METRIC, "value": ms_step, "unit": "ms/step", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == p.FP32 else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "scene": desc, "cubature": args.cubature, "tets": scene.n_tets, "vertices": scene.n_vertices,
+                   "free_vertices": Vf, "contact": False, "correction": args.correction, "line_search": True,
+                   "n_cub": args.n_cub, "rel_tol": 1e-4, "parallelism": f"replicas x{world}",
+                   "l2": "per-sweep working set larger than L2 (126 MB); no flush"},
+        "sweeps_per_step": float(sweeps.mean()), "sweeps_per_s": float(sweeps.sum() / (ms_total * 1e-3)),
+        "converged_steps": int(sum(q[1] for q in reps)), "max_rel_residual": float(max(q[2] for q in reps)),
+        "precompute_s": round(t_pre, 2),
+        "kernel_ms_per_step": {KIND[q]: round(float(kms[q] / args.steps), 4) for q in range(5)},
+        "kernel_share": share,
+        "roofline": {"bound": "hbm", "kernel": "k_main", "achieved": round(achieved, 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                     "bytes_per_launch": bytes_main, "avg_launch_ms": round(float(main_ms), 5),
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+        "e2e": {"value": e2e_ms, "unit": "ms/step", "h2d_bytes_per_step": int(xh.nbytes + vh.nbytes),
+                "d2h_bytes_per_step": int(xh.nbytes + vh.nbytes)},
+        "gpu_launches": launches,
+        "clocks": ck,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(scene, float(sweeps.mean()))
+    return out if rank == 0 else None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="jgs2", choices=["jgs2", "reference"])
+    ap.add_argument("--workload", default="spheres", choices=["spheres", "beam", "cube"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--correction", default="asm", choices=["asm", "elem", "off"])
+    ap.add_argument("--n-cub", type=int, default=4)
+    ap.add_argument("--max-sweeps", type=int, default=2000)
+    ap.add_argument("--ref-sweeps", type=float, default=100.0,
+                    help="sweeps per step assumed by the reference arm's scaling")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n-spheres", type=int, default=10)
+    ap.add_argument("--cubature", default="precompute", choices=["precompute", "synthetic"],
+                    help="synthetic: seeded random records instead of the precompute (kernel profiling only)")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "jgs2":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_jgs2(args, rank, world, local_rank)
+    if out is not None:
+        print(json.dumps(out))
+    if world > 1 and args.impl == "jgs2":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

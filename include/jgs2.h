@@ -95,9 +95,14 @@ typedef struct {
   int32_t line_search;       /* 1 = global Armijo backtracking on E (FP64 energy sums) */
   int32_t check_every;       /* host reads the convergence flag every this many sweeps */
   int32_t record_trace;      /* 1 = keep the per-sweep residual trace in the report */
+  int32_t profile;           /* 1 = time every kernel launch with CUDA events on the stream */
 } jgs2_step_opts;
 
 #define JGS2_TRACE_MAX 4096
+/* kernel kinds in jgs2_step_report.kernel_*: pool, main (gather + correction + solve),
+ * energy (line search), update, setup (per-step setup and write-back) */
+#define JGS2_NKERNELS 5
+enum { JGS2_K_POOL = 0, JGS2_K_MAIN = 1, JGS2_K_ENERGY = 2, JGS2_K_UPDATE = 3, JGS2_K_SETUP = 4 };
 
 typedef struct {
   int32_t sweeps;            /* sweeps applied in the step */
@@ -107,6 +112,9 @@ typedef struct {
   double rel_residual;       /* |g(x_{t+1})| / |g(x_t)| */
   double g0;                 /* |g(x^0)| */
   double ms;                 /* wall time of the step on the stream (CUDA events) */
+  int32_t launches;          /* kernels launched by the step */
+  int32_t kernel_launches[JGS2_NKERNELS]; /* per kernel kind (profile = 1) */
+  double kernel_ms[JGS2_NKERNELS];        /* summed CUDA-event time per kind (profile = 1) */
   int32_t trace_len;
   double trace[JGS2_TRACE_MAX]; /* r_k per sweep if record_trace */
 } jgs2_step_report;

@@ -17,6 +17,10 @@
   the relative residual drops below nnls_tol (1%, Sec. 5).
   Reading R6b: the candidates of every vertex of a body come from one seeded pool of
   n_pool elements of that body (n_pool >= body size recovers a draw from all elements).
+  Draws are keyed by body-local indices (the rank of a vertex / element among its body's
+  vertices / elements in caller order), so identical bodies get identical records:
+  pool = draw(keyed(seed, 2^32-1, 0), local elements, n_pool), candidates of local vertex l
+  in round r = draw(keyed(seed, l, r), eligible pool elements in ascending order, n_cand).
 
 Dense linear algebra (numpy) for the small meshes the tests use.
 """
@@ -77,10 +81,11 @@ def body_eigs(mesh: fem.Mesh, Hbar, body, n_train):
 
 
 def body_pool(mesh: fem.Mesh, body, n_pool, seed):
-    """Seeded pool of a body's elements (stream keyed by (body, 2^32-1)), ascending ids."""
-    elems = np.nonzero(mesh.body_of_tet == body)[0].tolist()
-    g = rng.keyed(seed, body, 0xFFFFFFFF)
-    return sorted(rng.draw_without_replacement(g, elems, n_pool))
+    """Seeded pool of a body's elements (body-local draw keyed (2^32-1, 0)), ascending ids."""
+    elems = np.nonzero(mesh.body_of_tet == body)[0]
+    g = rng.keyed(seed, 0xFFFFFFFF, 0)
+    local = rng.draw_without_replacement(g, list(range(len(elems))), n_pool)
+    return sorted(int(elems[j]) for j in local)
 
 
 def fit_system(mesh: fem.Mesh, i, Ub_i, A_i, lam, q, cand_elems):
@@ -121,6 +126,10 @@ def train_cubature(mesh: fem.Mesh, h, n_cub=4, n_train=20, n_cand=32, n_pool=256
     for e, t in enumerate(mesh.tets):
         for a in t:
             incident[a].add(e)
+    local_index = np.zeros(V, dtype=np.int64)
+    for b in range(mesh.n_bodies):
+        vb = np.nonzero(mesh.body_of_vertex == b)[0]
+        local_index[vb] = np.arange(len(vb))
     for i in mesh.free:
         d = mesh.dof_of[i]
         body = mesh.body_of_vertex[i]
@@ -130,7 +139,7 @@ def train_cubature(mesh: fem.Mesh, h, n_cub=4, n_train=20, n_cand=32, n_pool=256
             if res < nnls_tol:
                 break
             eligible = [e for e in pools[body] if e not in incident[i] and e not in sel]
-            cands = rng.draw_without_replacement(rng.keyed(seed, int(i), r), eligible, n_cand)
+            cands = rng.draw_without_replacement(rng.keyed(seed, int(local_index[i]), r), eligible, n_cand)
             best = None
             for c in cands:
                 M, y = fit_system(mesh, i, Ub[d], A[d], lam, q, sel + [c])

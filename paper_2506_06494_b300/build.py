@@ -34,7 +34,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp",
                    "-c", src, "-o", obj]
         else:
-            cmd = ["g++", "-O3", "-march=x86-64-v3", "-std=c++17", "-fPIC", "-fopenmp",
+            cmd = ["g++", "-O3", "-march=x86-64-v4", "-std=c++17", "-fPIC", "-fopenmp",
                    "-I/usr/local/cuda/include", "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)

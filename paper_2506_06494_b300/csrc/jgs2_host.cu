@@ -54,6 +54,7 @@ Mesh::~Mesh() {
   cudaFree(d_xt); cudaFree(d_vt); cudaFree(d_perm); cudaFree(d_state); cudaFree(d_partial);
   cudaFree(d_trace); cudaFree(d_xbuf); cudaFree(d_vbuf);
   if (h_state) cudaFreeHost(h_state);
+  for (cudaEvent_t e : events) cudaEventDestroy(e);
 }
 
 static uint64_t spread3(uint64_t x) {
@@ -216,23 +217,6 @@ jgs2_status mesh_create(const jgs2_mesh_desc* d, Mesh** out) {
     }
     m->n_bodies = nb;
   }
-  // shared device arrays
-  CK(dalloc(&m->d_inc_off, ns + 1));
-  CK(dalloc(&m->d_inc_len, m->Vf));
-  CK(dalloc(&m->d_inc, m->inc.size()));
-  CK(dalloc(&m->d_xt, 3 * (size_t)V));
-  CK(dalloc(&m->d_vt, 3 * (size_t)V));
-  CK(dalloc(&m->d_perm, V));
-  CK(dalloc(&m->d_state, 1));
-  CK(dalloc(&m->d_trace, JGS2_TRACE_MAX));
-  const size_t np = std::max<size_t>(2 * kLsTrials * ((size_t)(T + 127) / 128 + (m->Vf + 127) / 128 + 1), 16);
-  CK(dalloc(&m->d_partial, np));
-  CK(cudaMallocHost((void**)&m->h_state, sizeof(StepState)));
-  CK(cudaMemcpy(m->d_inc_off, m->inc_off.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
-  if (m->Vf) CK(cudaMemcpy(m->d_inc_len, m->inc_len.data(), sizeof(int) * m->Vf, cudaMemcpyHostToDevice));
-  if (!m->inc.empty()) CK(cudaMemcpy(m->d_inc, m->inc.data(), sizeof(int) * m->inc.size(), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(m->d_perm, m->perm.data(), sizeof(int) * V, cudaMemcpyHostToDevice));
-  CK(cudaMemset(m->d_state, 0, sizeof(StepState)));
   *out = m.release();
   return JGS2_OK;
 }
@@ -246,8 +230,43 @@ PrecBufs<float>& bufs<float>(Mesh* m) { return m->f32; }
 template <>
 PrecBufs<double>& bufs<double>(Mesh* m) { return m->f64; }
 
+// Device-side shared arrays, allocated on first use (mesh creation and the precompute
+// touch no device, so they also run on a host without a GPU).
+static jgs2_status ensure_device(Mesh* m) {
+  if (!m->device_ready) {
+    const int V = m->V, T = m->T, ns = m->n_slices;
+    CK(dalloc(&m->d_inc_off, ns + 1));
+    CK(dalloc(&m->d_inc_len, m->Vf));
+    CK(dalloc(&m->d_inc, m->inc.size()));
+    CK(dalloc(&m->d_xt, 3 * (size_t)V));
+    CK(dalloc(&m->d_vt, 3 * (size_t)V));
+    CK(dalloc(&m->d_perm, V));
+    CK(dalloc(&m->d_state, 1));
+    CK(dalloc(&m->d_trace, JGS2_TRACE_MAX));
+    const size_t np = std::max<size_t>(2 * kLsTrials * ((size_t)(T + 127) / 128 + (m->Vf + 127) / 128 + 1), 16);
+    CK(dalloc(&m->d_partial, np));
+    CK(cudaMallocHost((void**)&m->h_state, sizeof(StepState)));
+    CK(cudaMemcpy(m->d_inc_off, m->inc_off.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
+    if (m->Vf) CK(cudaMemcpy(m->d_inc_len, m->inc_len.data(), sizeof(int) * m->Vf, cudaMemcpyHostToDevice));
+    if (!m->inc.empty()) CK(cudaMemcpy(m->d_inc, m->inc.data(), sizeof(int) * m->inc.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->d_perm, m->perm.data(), sizeof(int) * V, cudaMemcpyHostToDevice));
+    CK(cudaMemset(m->d_state, 0, sizeof(StepState)));
+    m->device_ready = true;
+  }
+  if (m->pool_version != m->cub_version) {
+    cudaFree(m->d_pool_tet);
+    m->d_pool_tet = nullptr;
+    CK(dalloc(&m->d_pool_tet, std::max(1, m->nP)));
+    if (m->nP) CK(cudaMemcpy(m->d_pool_tet, m->pool.data(), sizeof(int) * m->nP, cudaMemcpyHostToDevice));
+    m->pool_version = m->cub_version;
+  }
+  return JGS2_OK;
+}
+
 template <typename T>
 static jgs2_status ensure_prec(Mesh* m) {
+  jgs2_status ds = ensure_device(m);
+  if (ds != JGS2_OK) return ds;
   PrecBufs<T>& b = bufs<T>(m);
   if (!b.ready) {
     const int V = m->V, T_ = m->T;
@@ -360,10 +379,6 @@ jgs2_status set_cubature(Mesh* m, int n_cub, const std::vector<int>& elem_int /*
   m->cub_elem = elem_int;
   m->cub_w = w;
   m->cub_u = u;
-  cudaFree(m->d_pool_tet);
-  m->d_pool_tet = nullptr;
-  CK(dalloc(&m->d_pool_tet, std::max(1, m->nP)));
-  if (m->nP) CK(cudaMemcpy(m->d_pool_tet, pool.data(), sizeof(int) * m->nP, cudaMemcpyHostToDevice));
   m->cub_version++;
   return JGS2_OK;
 }
@@ -396,13 +411,63 @@ jgs2_status import_cubature(Mesh* m, const jgs2_cubature_blob* b) {
 
 // ------------------------------------------------------------------ step driver
 
+// Launch bookkeeping of one step: counts per kernel kind and, when profiling, a CUDA
+// event pair around every launch (events are pooled per mesh).
+struct Launches {
+  Mesh* m;
+  cudaStream_t s;
+  bool prof;
+  int count[JGS2_NKERNELS] = {0, 0, 0, 0, 0};
+  std::vector<std::pair<int, int>> rec;  // (kind, event index)
+  int used = 0;
+  cudaError_t err = cudaSuccess;
+  int begin(int kind) {
+    count[kind]++;
+    if (!prof) return -1;
+    if ((int)m->events.size() < used + 2) {
+      for (int q = 0; q < 64; ++q) {
+        cudaEvent_t e;
+        if ((err = cudaEventCreate(&e)) != cudaSuccess) return -1;
+        m->events.push_back(e);
+      }
+    }
+    const int id = used;
+    used += 2;
+    cudaEventRecord(m->events[id], s);
+    rec.push_back({kind, id});
+    return id;
+  }
+  void end(int id) {
+    if (id >= 0) cudaEventRecord(m->events[id + 1], s);
+  }
+  void report(jgs2_step_report* r) {
+    int tot = 0;
+    for (int q = 0; q < JGS2_NKERNELS; ++q) {
+      tot += count[q];
+      if (r) {
+        r->kernel_launches[q] = count[q];
+        r->kernel_ms[q] = 0.0;
+      }
+    }
+    if (r) r->launches = tot;
+    if (!r || !prof) return;
+    for (auto& kv : rec) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, m->events[kv.second], m->events[kv.second + 1]) == cudaSuccess)
+        r->kernel_ms[kv.first] += ms;
+    }
+  }
+};
+
 template <typename T>
 static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t s, int max_k, double rel_tol,
-                              bool check, StepState* hs) {
+                              bool check, StepState* hs, Launches& L) {
   DevMesh<T> d = dev_view<T>(m);
   const bool corr = o.correction != JGS2_CORR_OFF;
   const int nbV = (m->Vf + 127) / 128;
   const int nbT = (m->T + 127) / 128;
+  // line-search pass: grid-stride over tets and vertices, about 4 tets per thread
+  const int nbE = std::max(1, std::min(std::max(nbT, nbV), 148 * 8));
   StepState init;
   std::memset(&init, 0, sizeof(init));
   init.max_sweeps = max_k;
@@ -411,26 +476,37 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t s, 
   CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
   const int every = std::max(1, o.check_every);
   for (int k = 0; k <= max_k; ++k) {
+    int id;
     if (corr && m->nP > 0) {
+      id = L.begin(JGS2_K_POOL);
       if (o.correction == JGS2_CORR_ASM)
         k_pool<T, true><<<m->nP, 128, 0, s>>>(d, m->d_state);
       else
         k_pool<T, false><<<m->nP, 128, 0, s>>>(d, m->d_state);
+      L.end(id);
     }
     if (nbV > 0) {
+      id = L.begin(JGS2_K_MAIN);
       if (corr)
         k_main<T, true><<<nbV, 128, 0, s>>>(d, m->d_state, k, m->d_partial, m->d_trace, o.record_trace);
       else
         k_main<T, false><<<nbV, 128, 0, s>>>(d, m->d_state, k, m->d_partial, m->d_trace, o.record_trace);
+      L.end(id);
     }
     if (k == max_k) break;
     if (o.line_search) {
+      id = L.begin(JGS2_K_ENERGY);
       if (corr)
-        k_energy<T, 2><<<nbT + nbV, 128, 0, s>>>(d, m->d_state, m->d_partial, nbT);
+        k_energy<T, 2><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
       else
-        k_energy<T, 1><<<nbT + nbV, 128, 0, s>>>(d, m->d_state, m->d_partial, nbT);
+        k_energy<T, 1><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
+      L.end(id);
     }
-    if (nbV > 0) k_update<T><<<nbV, 128, 0, s>>>(d, m->d_state);
+    if (nbV > 0) {
+      id = L.begin(JGS2_K_UPDATE);
+      k_update<T><<<nbV, 128, 0, s>>>(d, m->d_state);
+      L.end(id);
+    }
     CK(cudaGetLastError());
     if (check && (k + 1) % every == 0) {
       CK(cudaMemcpyAsync(hs, m->d_state, sizeof(StepState), cudaMemcpyDeviceToHost, s));
@@ -465,17 +541,26 @@ static jgs2_status step_impl(Mesh* m, double* x, double* v, const jgs2_step_opts
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, s));
   const int nb = (m->V + 127) / 128;
+  Launches L{m, s, o->profile != 0};
+  int id = L.begin(JGS2_K_SETUP);
   k_setup_vertices<T><<<nb, 128, 0, s>>>(d, x, v, nullptr);
+  L.end(id);
+  id = L.begin(JGS2_K_SETUP);
   k_setup_tets<T><<<(m->T + 127) / 128, 128, 0, s>>>(d);
+  L.end(id);
   CK(cudaGetLastError());
   StepState* hs = m->h_state;
-  st = run_sweeps<T>(m, *o, s, o->max_sweeps, o->rel_tol, true, hs);
+  st = run_sweeps<T>(m, *o, s, o->max_sweeps, o->rel_tol, true, hs, L);
   if (st != JGS2_OK) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
   }
-  if (hs->status == 0) k_finish<T><<<nb, 128, 0, s>>>(d, x, v);
+  if (hs->status == 0) {
+    id = L.begin(JGS2_K_SETUP);
+    k_finish<T><<<nb, 128, 0, s>>>(d, x, v);
+    L.end(id);
+  }
   CK(cudaEventRecord(e1, s));
   CK(cudaEventSynchronize(e1));
   float ms = 0.f;
@@ -491,6 +576,7 @@ static jgs2_status step_impl(Mesh* m, double* x, double* v, const jgs2_step_opts
     rep->g0 = hs->g0;
     rep->ms = ms;
     rep->trace_len = 0;
+    L.report(rep);
     if (o->record_trace) {
       const int n = std::min(hs->sweeps + 1, JGS2_TRACE_MAX);
       CK(cudaMemcpy(rep->trace, m->d_trace, sizeof(double) * n, cudaMemcpyDeviceToHost));
@@ -521,7 +607,8 @@ static jgs2_status sweeps_impl(Mesh* m, const double* xt, const double* vt, doub
   k_setup_tets<T><<<(m->T + 127) / 128, 128, 0, s>>>(d);
   CK(cudaGetLastError());
   // exactly n sweeps: no convergence test (rel_tol < 0), stop after the n-th update
-  st = run_sweeps<T>(m, *o, s, n, -1.0, false, m->h_state);
+  Launches L{m, s, false};
+  st = run_sweeps<T>(m, *o, s, n, -1.0, false, m->h_state, L);
   if (st != JGS2_OK) return st;
   k_finish<T><<<nb, 128, 0, s>>>(d, xk, nullptr);
   CK(cudaGetLastError());
@@ -594,6 +681,7 @@ void jgs2_step_opts_default(jgs2_step_opts* o) {
   o->line_search = 1;
   o->check_every = 16;
   o->record_trace = 0;
+  o->profile = 0;
 }
 
 jgs2_status jgs2_mesh_create(const jgs2_mesh_desc* desc, jgs2_mesh** out) {

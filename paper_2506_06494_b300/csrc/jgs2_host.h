@@ -42,7 +42,8 @@ struct Mesh {
   std::vector<int> tperm, tiperm;  // internal <-> caller tet
   std::vector<int> inc_off, inc_len, inc;
   // cubature records, internal order: [Vf][n_cub]
-  int n_cub = 0, nP = 0, cub_version = 0;
+  int n_cub = 0, nP = 0, cub_version = 0, pool_version = -1;
+  bool device_ready = false;
   std::vector<int> pool;          // internal tet ids of the pool, ascending
   std::vector<int> cub_p, cub_elem;
   std::vector<double> cub_w, cub_u, cub_resid;
@@ -52,12 +53,14 @@ struct Mesh {
   double *d_xbuf = nullptr, *d_vbuf = nullptr;
   StepState* d_state = nullptr;
   StepState* h_state = nullptr;
+  std::vector<cudaEvent_t> events;  // pooled profiling events
   PrecBufs<float> f32;
   PrecBufs<double> f64;
   ~Mesh();
 };
 
 jgs2_status fail(jgs2_status s, const std::string& msg);
+jgs2_status precompute(Mesh* m, const jgs2_precompute_opts* o);
 jgs2_status set_cubature(Mesh* m, int n_cub, const std::vector<int>& elem_int, const std::vector<double>& w,
                          const std::vector<double>& u);
 

@@ -761,90 +761,95 @@ __device__ __forceinline__ void tet_dF(const TetRec<T>& r, const Vec4<T>* D, int
   }
 }
 
+// Coefficients c_1..c_6 of Psi(F + a dF) - Psi(F) = sum_p c_p a^p (exact polynomial in a):
+// with A = cof(F):dF, B = F:cof(dF), C = det dF, dJ(a) = A a + B a^2 + C a^3, and
+// dPsi = mu (F:dF) a + mu/2 (dF:dF) a^2 - mu dJ + lam'/2 dJ (dJ + 2 (J - 1)).
 template <typename T>
-__device__ __forceinline__ void tet_dpsi(const TetRec<T>& r, const T (&F)[9], const T (&C)[9], T J,
-                                         const T (&dF)[9], double* out /* [kLsTrials] */) {
+__device__ __forceinline__ void tet_dpsi_poly(const TetRec<T>& r, const T (&F)[9], const T (&C)[9], T J,
+                                              const T (&dF)[9], T (&c)[6]) {
   T cdF[9];
   cofactor(dF, cdF);
-  T FdF = T(0), dFdF = T(0), CdF = T(0), FcdF = T(0);
+  T f = T(0), q = T(0), A = T(0), B = T(0);
 #pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    FdF += F[q] * dF[q];
-    dFdF += dF[q] * dF[q];
-    CdF += C[q] * dF[q];
-    FcdF += F[q] * cdF[q];
+  for (int k = 0; k < 9; ++k) {
+    f += F[k] * dF[k];
+    q += dF[k] * dF[k];
+    A += C[k] * dF[k];
+    B += F[k] * cdF[k];
   }
-  const T detdF = dF[0] * cdF[0] + dF[1] * cdF[1] + dF[2] * cdF[2];
-#pragma unroll
-  for (int j = 0; j < kLsTrials; ++j) {
-    const T a = T(1) / T(1 << j);
-    const T dJ = a * CdF + a * a * FcdF + a * a * a * detdF;
-    const T dpsi = T(0.5) * r.mu * (T(2) * a * FdF + a * a * dFdF) - r.mu * dJ +
-                   T(0.5) * r.lp * dJ * (dJ + T(2) * (J - T(1)));
-    out[j] = double(r.vol) * double(dpsi);
-  }
+  const T Cc = dF[0] * cdF[0] + dF[1] * cdF[1] + dF[2] * cdF[2];
+  const T mu = r.mu, lp = r.lp, j1 = J - T(1), s = lp * j1 - mu;
+  c[0] = r.vol * (mu * f + s * A);
+  c[1] = r.vol * (T(0.5) * mu * q + s * B + T(0.5) * lp * A * A);
+  c[2] = r.vol * (s * Cc + lp * A * B);
+  c[3] = r.vol * (T(0.5) * lp * (B * B + T(2) * A * Cc));
+  c[4] = r.vol * (lp * B * Cc);
+  c[5] = r.vol * (T(0.5) * lp * Cc * Cc);
 }
 
-// Line search (reading R17): energy changes along D (and along D_J when ND = 2) for
-// alpha_j = 2^-j; the last block takes the first Armijo-satisfying trial, D before D_J.
+// Line search (reading R17): the energy change along D (and along D_J when ND = 2) is a
+// polynomial in the step a; its coefficients are summed over tets and free vertices
+// (per-thread partial sums in T over a grid-stride loop, FP64 across threads and blocks),
+// then the last block evaluates E(x + a d) - E(x) at a = 2^-j and takes the first
+// Armijo-satisfying trial, D before D_J.
 template <typename T, int ND>
 __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st,
-                                                double* __restrict__ partial /* [ND*8][grid] */,
-                                                int tet_blocks) {
+                                                double* __restrict__ partial /* [ND*6][grid] */) {
   if (st->done) return;
-  constexpr int NT = ND * kLsTrials;
-  __shared__ double red[32 * NT];
-  double acc[NT];
+  constexpr int NC = 6 * ND;
+  __shared__ double red[32 * NC];
+  T acc[NC];
 #pragma unroll
-  for (int j = 0; j < NT; ++j) acc[j] = 0.0;
-  if ((int)blockIdx.x < tet_blocks) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < m.T_) {
-      const TetRec<T> r = m.tets[t];
-      T F[9], C[9], dF[9];
-      tet_F(r, m.u, F);
-      cofactor(F, C);
-      const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
-      tet_dF(r, m.D, m.Vf, dF);
-      tet_dpsi(r, F, C, J, dF, acc);
-      if (ND == 2) {
-        tet_dF(r, m.DJ, m.Vf, dF);
-        tet_dpsi(r, F, C, J, dF, acc + kLsTrials);
-      }
-    }
-  } else {
-    const int v = (blockIdx.x - tet_blocks) * blockDim.x + threadIdx.x;
-    if (v < m.Vf) {
-      T uv[3], dz[3], d[3];
-      load3(m.u, v, uv);
-      load3(m.dz, v, dz);
-      const double mh = double(m.mh2[v]);
+  for (int j = 0; j < NC; ++j) acc[j] = T(0);
+  const int stride = gridDim.x * blockDim.x;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.T_; t += stride) {
+    const TetRec<T> r = m.tets[t];
+    T F[9], C[9], dF[9], c[6];
+    tet_F(r, m.u, F);
+    cofactor(F, C);
+    const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
+    tet_dF(r, m.D, m.Vf, dF);
+    tet_dpsi_poly(r, F, C, J, dF, c);
 #pragma unroll
-      for (int dir = 0; dir < ND; ++dir) {
-        load3(dir == 0 ? m.D : m.DJ, v, d);
-        double dd = 0.0, de = 0.0;
+    for (int j = 0; j < 6; ++j) acc[j] += c[j];
+    if (ND == 2) {
+      tet_dF(r, m.DJ, m.Vf, dF);
+      tet_dpsi_poly(r, F, C, J, dF, c);
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          dd += double(d[q]) * double(d[q]);
-          de += double(d[q]) * (double(uv[q]) - double(dz[q]));
-        }
-#pragma unroll
-        for (int j = 0; j < kLsTrials; ++j) {
-          const double a = 1.0 / double(1 << j);
-          acc[dir * kLsTrials + j] = 0.5 * mh * (2.0 * a * de + a * a * dd);
-        }
-      }
+      for (int j = 0; j < 6; ++j) acc[6 + j] += c[j];
     }
   }
-  block_sum<NT>(acc, red);
+  // inertia: m/(2h^2) (2 a d.(u - dz) + a^2 |d|^2)
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < m.Vf; v += stride) {
+    T uv[3], dz[3], d[3];
+    load3(m.u, v, uv);
+    load3(m.dz, v, dz);
+    const T mh = m.mh2[v];
+#pragma unroll
+    for (int dir = 0; dir < ND; ++dir) {
+      load3(dir == 0 ? m.D : m.DJ, v, d);
+      T dd = T(0), de = T(0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        dd += d[q] * d[q];
+        de += d[q] * (uv[q] - dz[q]);
+      }
+      acc[dir * 6 + 0] += mh * de;
+      acc[dir * 6 + 1] += T(0.5) * mh * dd;
+    }
+  }
+  double accd[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) accd[j] = double(acc[j]);
+  block_sum<NC>(accd, red);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int j = 0; j < NT; ++j) partial[(size_t)j * gridDim.x + blockIdx.x] = acc[j];
+    for (int j = 0; j < NC; ++j) partial[(size_t)j * gridDim.x + blockIdx.x] = accd[j];
   }
   if (!last_block(&st->ticket_energy)) return;
-  double dE[NT];
+  double cf[NC];
 #pragma unroll
-  for (int j = 0; j < NT; ++j) dE[j] = block_sum_array(partial + (size_t)j * gridDim.x, gridDim.x, 1, red);
+  for (int j = 0; j < NC; ++j) cf[j] = block_sum_array(partial + (size_t)j * gridDim.x, gridDim.x, 1, red);
   if (threadIdx.x == 0) {
     st->ticket_energy = 0;
     double alpha = 0.0;
@@ -854,7 +859,9 @@ __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st,
       const double slope = dd == 0 ? st->slope : st->slope_j;
       for (int j = 0; j < kLsTrials; ++j) {
         const double a = 1.0 / double(1 << j);
-        if (dE[dd * kLsTrials + j] <= 1e-4 * a * slope) {
+        const double* c = cf + 6 * dd;
+        const double dE = a * (c[0] + a * (c[1] + a * (c[2] + a * (c[3] + a * (c[4] + a * c[5])))));
+        if (dE <= 1e-4 * a * slope) {
           alpha = a;
           dir = dd;
           ok = true;

@@ -1,10 +1,1050 @@
-// Offline stage of JGS2 (Secs. 5-6) on the host: placeholder until the sparse factorisation
-// lands; jgs2_precompute reports that it is unavailable.
+// Offline stage of JGS2 on the host, FP64 (Secs. 5-6 of Lan et al.).
+//
+// Per distinct body (bodies equal up to translation share one precompute):
+//   1. H_bar = M/h^2 + K_bar over the body's free DOFs (rest Hessian, reading R2; the
+//      element blocks are V_e (mu (b_a.b_c) I + mu b_c b_a^T + lam b_a b_c^T)).
+//   2. Nested-dissection order (recursive coordinate bisection with one-sided vertex
+//      separators), elimination tree, fundamental supernodes, multifrontal Cholesky
+//      H_bar = L L^T with dense fronts (Sec. 6: "we only factorize H_bar once").
+//   3. Training poses: the n_train lowest eigenpairs of H_bar by block inverse iteration
+//      with Rayleigh-Ritz (Sec. 5, last paragraph).
+//   4. Rows of H_bar^{-1} at the vertices of the body's cubature pool, by multi-RHS
+//      forward/backward substitution (Sec. 6: substitutions with the one factor).
+//   5. Diagonal blocks A_i = (H_bar^{-1})_ii for every free vertex by selected inversion
+//      (Takahashi recurrences on the supernodal pattern), so that
+//      U_bar_{i,a} = (H_bar^{-1})_{a,i} A_i^{-1}  (Eq. u: U_bar_i = H^-1 S_i^T (S_i H^-1 S_i^T)^-1).
+//   6. Greedy NNLS cubature per vertex (Eq. cubature_weight) with the same seeded draws,
+//      training rows and stopping rule as described in the header.
+#include <omp.h>
+
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <string>
+#include <vector>
+
 #include "../../include/jgs2.h"
+#include "dense_host.h"
 #include "jgs2_host.h"
 
+namespace jgs2 {
+namespace pre {
+
+using std::vector;
+
+static bool verbose() {
+  static const bool v = std::getenv("JGS2_VERBOSE") != nullptr;
+  return v;
+}
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+#define PHASE(name)                                                                  \
+  do {                                                                               \
+    if (verbose()) std::fprintf(stderr, "[jgs2_precompute] %-18s %8.3f s\n", name, now_s() - t_phase); \
+    t_phase = now_s();                                                               \
+  } while (0)
+
+// ------------------------------------------------------------------ SplitMix64
+// Steele, Lea & Flood (OOPSLA 2014): state += 0x9E3779B97F4A7C15, then the output mix.
+struct SplitMix {
+  uint64_t s;
+  uint64_t next() {
+    s += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+  }
+};
+
+// Stream derived from a seed and two keys by feeding each key through one output.
+static SplitMix keyed(uint64_t seed, uint64_t a, uint64_t b) {
+  SplitMix g{seed};
+  g.s = g.next() ^ a;
+  g.s = g.next() ^ b;
+  return g;
+}
+
+// Partial Fisher-Yates: the first k picks of `items` (in the given order).
+static vector<int> draw(SplitMix g, vector<int> items, int k) {
+  const int n = (int)items.size();
+  k = std::min(k, n);
+  for (int j = 0; j < k; ++j) {
+    const int r = j + (int)(g.next() % (uint64_t)(n - j));
+    std::swap(items[j], items[r]);
+  }
+  items.resize(k);
+  return items;
+}
+
+// Small symmetric eigen-decomposition by cyclic Jacobi (n x n row-major, vectors in V columns).
+static void sym_eig(vector<double>& A, int n, vector<double>& w, vector<double>& V) {
+  V.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int i = 0; i < n; ++i) {
+      dia += A[(size_t)i * n + i] * A[(size_t)i * n + i];
+      for (int j = i + 1; j < n; ++j) off += A[(size_t)i * n + j] * A[(size_t)i * n + j];
+    }
+    if (off <= 1e-30 * dia || off == 0.0) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[(size_t)p * n + q];
+        if (apq == 0.0) continue;
+        const double tau = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+        for (int k = 0; k < n; ++k) {
+          const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+          A[(size_t)k * n + p] = c * akp - s * akq;
+          A[(size_t)k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+          A[(size_t)p * n + k] = c * apk - s * aqk;
+          A[(size_t)q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+          V[(size_t)k * n + p] = c * vkp - s * vkq;
+          V[(size_t)k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = A[(size_t)i * n + i];
+}
+
+// ------------------------------------------------------------------ NNLS (Lawson & Hanson 1974)
+// min |A w - b|, w >= 0; A is m x n column-major (n small). Returns the residual norm.
+static double lstsq_cols(const vector<double>& A, int m, const vector<int>& cols, const vector<double>& b,
+                         vector<double>& s) {
+  // modified Gram-Schmidt QR of the selected columns
+  const int k = (int)cols.size();
+  vector<double> Q((size_t)m * k), R((size_t)k * k, 0.0);
+  for (int j = 0; j < k; ++j) std::memcpy(&Q[(size_t)j * m], &A[(size_t)cols[j] * m], sizeof(double) * m);
+  for (int j = 0; j < k; ++j) {
+    double* qj = &Q[(size_t)j * m];
+    for (int p = 0; p < j; ++p) {
+      const double* qp = &Q[(size_t)p * m];
+      double d = 0.0;
+      for (int i = 0; i < m; ++i) d += qp[i] * qj[i];
+      R[(size_t)p * k + j] = d;
+      for (int i = 0; i < m; ++i) qj[i] -= d * qp[i];
+    }
+    double nrm = 0.0;
+    for (int i = 0; i < m; ++i) nrm += qj[i] * qj[i];
+    nrm = std::sqrt(nrm);
+    R[(size_t)j * k + j] = nrm;
+    if (nrm > 0)
+      for (int i = 0; i < m; ++i) qj[i] /= nrm;
+  }
+  vector<double> y(k, 0.0);
+  for (int j = 0; j < k; ++j) {
+    double d = 0.0;
+    for (int i = 0; i < m; ++i) d += Q[(size_t)j * m + i] * b[i];
+    y[j] = d;
+  }
+  s.assign(k, 0.0);
+  for (int j = k - 1; j >= 0; --j) {
+    double v = y[j];
+    for (int p = j + 1; p < k; ++p) v -= R[(size_t)j * k + p] * s[p];
+    s[j] = R[(size_t)j * k + j] > 0 ? v / R[(size_t)j * k + j] : 0.0;
+  }
+  double r2 = 0.0;
+  for (int i = 0; i < m; ++i) {
+    double v = b[i];
+    for (int j = 0; j < k; ++j) v -= A[(size_t)cols[j] * m + i] * s[j];
+    r2 += v * v;
+  }
+  return std::sqrt(r2);
+}
+
+static double nnls(const vector<double>& A, int m, int n, const vector<double>& b, vector<double>& w) {
+  w.assign(n, 0.0);
+  vector<char> inP(n, 0);
+  double scale = 0.0;  // stopping threshold relative to the largest |A_j^T b|
+  for (int j = 0; j < n; ++j) {
+    double gj = 0.0;
+    for (int i = 0; i < m; ++i) gj += A[(size_t)j * m + i] * b[i];
+    scale = std::max(scale, std::fabs(gj));
+  }
+  const double tol = 1e-13 * std::max(scale, 1e-300);
+  for (int outer = 0; outer < 3 * n + 10; ++outer) {
+    vector<double> r(b);
+    for (int j = 0; j < n; ++j)
+      if (w[j] != 0.0)
+        for (int i = 0; i < m; ++i) r[i] -= A[(size_t)j * m + i] * w[j];
+    int jmax = -1;
+    double gmax = tol;
+    for (int j = 0; j < n; ++j) {
+      if (inP[j]) continue;
+      double gj = 0.0;
+      for (int i = 0; i < m; ++i) gj += A[(size_t)j * m + i] * r[i];
+      if (gj > gmax) {
+        gmax = gj;
+        jmax = j;
+      }
+    }
+    if (jmax < 0) break;
+    inP[jmax] = 1;
+    for (int inner = 0; inner < 3 * n + 10; ++inner) {
+      vector<int> P;
+      for (int j = 0; j < n; ++j)
+        if (inP[j]) P.push_back(j);
+      vector<double> sv;
+      lstsq_cols(A, m, P, b, sv);
+      bool feasible = true;
+      for (double v : sv)
+        if (v <= 0.0) feasible = false;
+      if (feasible) {
+        std::fill(w.begin(), w.end(), 0.0);
+        for (size_t q = 0; q < P.size(); ++q) w[P[q]] = sv[q];
+        break;
+      }
+      double alpha = 2.0;
+      for (size_t q = 0; q < P.size(); ++q)
+        if (sv[q] <= 0.0) alpha = std::min(alpha, w[P[q]] / (w[P[q]] - sv[q]));
+      for (size_t q = 0; q < P.size(); ++q) w[P[q]] += alpha * (sv[q] - w[P[q]]);
+      for (size_t q = 0; q < P.size(); ++q)
+        if (w[P[q]] <= 1e-15) {
+          w[P[q]] = 0.0;
+          inP[P[q]] = 0;
+        }
+    }
+  }
+  double r2 = 0.0;
+  for (int i = 0; i < m; ++i) {
+    double v = b[i];
+    for (int j = 0; j < n; ++j) v -= A[(size_t)j * m + i] * w[j];
+    r2 += v * v;
+  }
+  return std::sqrt(r2);
+}
+
+// ------------------------------------------------------------------ sparse Cholesky
+
+struct Factor {
+  int nv = 0;                          // free vertices of the body (factor order)
+  vector<int> sn_first;                // supernode -> first vertex (factor order)
+  vector<int> sn_of;                   // vertex -> supernode
+  vector<vector<int>> sn_rows;         // supernode -> row structure below (vertices, ascending)
+  vector<vector<double>> L;            // supernode -> (3nJ + 3nR) x 3nJ column-major
+  int nsn() const { return (int)sn_first.size() - 1; }
+};
+
+// Lower block of the rest Hessian in factor order: for column vertex v, rows u >= v.
+struct BlockCol {
+  vector<int> row;
+  vector<double> val;  // 9 per row, row-major 3x3 (row dof of u, col dof of v)
+};
+
+static void nd_order(const vector<double>& P, const vector<vector<int>>& adj, vector<int>& idx,
+                     vector<char>& side, vector<int>& out) {
+  if (idx.size() <= 64) {
+    for (int v : idx) out.push_back(v);
+    return;
+  }
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int v : idx)
+    for (int q = 0; q < 3; ++q) {
+      lo[q] = std::min(lo[q], P[3 * v + q]);
+      hi[q] = std::max(hi[q], P[3 * v + q]);
+    }
+  int ax = 0;
+  for (int q = 1; q < 3; ++q)
+    if (hi[q] - lo[q] > hi[ax] - lo[ax]) ax = q;
+  const size_t mid = idx.size() / 2;
+  std::nth_element(idx.begin(), idx.begin() + mid, idx.end(), [&](int a, int b) {
+    if (P[3 * a + ax] != P[3 * b + ax]) return P[3 * a + ax] < P[3 * b + ax];
+    return a < b;
+  });
+  vector<int> left(idx.begin(), idx.begin() + mid), right(idx.begin() + mid, idx.end());
+  for (int v : left) side[v] = 1;
+  for (int v : right) side[v] = 2;
+  vector<int> sep, l2;
+  for (int v : left) {
+    bool s = false;
+    for (int u : adj[v])
+      if (side[u] == 2) {
+        s = true;
+        break;
+      }
+    (s ? sep : l2).push_back(v);
+  }
+  for (int v : idx) side[v] = 0;
+  std::sort(l2.begin(), l2.end());
+  std::sort(right.begin(), right.end());
+  std::sort(sep.begin(), sep.end());
+  idx.clear();
+  idx.shrink_to_fit();
+  nd_order(P, adj, l2, side, out);
+  nd_order(P, adj, right, side, out);
+  for (int v : sep) out.push_back(v);
+}
+
+// Multifrontal supernodal Cholesky of the block matrix given by its lower block columns.
+static bool factorize(int nv, const vector<BlockCol>& H, Factor& F) {
+  F.nv = nv;
+  // elimination tree (Liu) on the vertex graph
+  vector<int> parent(nv, -1), anc(nv, -1);
+  for (int j = 0; j < nv; ++j) {
+    // rows u > j of column j are the entries (j, u) of row u < ... : use symmetric pattern
+    (void)j;
+  }
+  // build upper adjacency: for each column v, rows u > v; the etree needs for each j the
+  // neighbours i < j
+  vector<vector<int>> lowN(nv);
+  for (int v = 0; v < nv; ++v)
+    for (int u : H[v].row)
+      if (u > v) lowN[u].push_back(v);
+  for (int j = 0; j < nv; ++j)
+    for (int i : lowN[j]) {
+      int r = i;
+      while (anc[r] != -1 && anc[r] != j) {
+        const int t = anc[r];
+        anc[r] = j;
+        r = t;
+      }
+      if (anc[r] == -1) {
+        anc[r] = j;
+        parent[r] = j;
+      }
+    }
+  // column structures (vertices > j), children first (ascending order is topological)
+  vector<int> nchild(nv, 0);
+  for (int j = 0; j < nv; ++j)
+    if (parent[j] >= 0) nchild[parent[j]]++;
+  vector<vector<int>> kids(nv);
+  for (int j = 0; j < nv; ++j)
+    if (parent[j] >= 0) kids[parent[j]].push_back(j);
+  vector<vector<int>> st(nv);
+  vector<int> mark(nv, -1);
+  for (int j = 0; j < nv; ++j) {
+    vector<int>& s = st[j];
+    for (int u : H[j].row)
+      if (u > j && mark[u] != j) {
+        mark[u] = j;
+        s.push_back(u);
+      }
+    for (int c : kids[j]) {
+      for (int u : st[c])
+        if (u > j && mark[u] != j) {
+          mark[u] = j;
+          s.push_back(u);
+        }
+    }
+    std::sort(s.begin(), s.end());
+  }
+  // fundamental supernodes
+  F.sn_first.clear();
+  F.sn_of.assign(nv, 0);
+  for (int j = 0; j < nv; ++j) {
+    const bool merge = j > 0 && parent[j - 1] == j && nchild[j] == 1 && st[j - 1].size() == st[j].size() + 1;
+    if (!merge) F.sn_first.push_back(j);
+    F.sn_of[j] = (int)F.sn_first.size() - 1;
+  }
+  F.sn_first.push_back(nv);
+  const int ns = F.nsn();
+  F.sn_rows.assign(ns, {});
+  for (int s = 0; s < ns; ++s) F.sn_rows[s] = st[F.sn_first[s + 1] - 1];
+  st.clear();
+  st.shrink_to_fit();
+  // supernode tree
+  vector<vector<int>> skids(ns);
+  for (int s = 0; s < ns; ++s) {
+    const int last = F.sn_first[s + 1] - 1;
+    if (parent[last] >= 0) skids[F.sn_of[parent[last]]].push_back(s);
+  }
+  F.L.assign(ns, {});
+  vector<vector<double>> upd(ns);  // update matrices, (3 nR)^2 column-major lower
+  vector<int> loc(nv, -1);
+  for (int s = 0; s < ns; ++s) {
+    const int f = F.sn_first[s], l = F.sn_first[s + 1];
+    const int nJ = 3 * (l - f);
+    const vector<int>& R = F.sn_rows[s];
+    const int nR = 3 * (int)R.size();
+    const int m = nJ + nR;
+    vector<double>& Fm = F.L[s];
+    Fm.assign((size_t)m * nJ, 0.0);
+    vector<double> U((size_t)nR * nR, 0.0);
+    for (int v = f; v < l; ++v) loc[v] = 3 * (v - f);
+    for (size_t q = 0; q < R.size(); ++q) loc[R[q]] = nJ + 3 * (int)q;
+    // original entries of the columns of J
+    for (int v = f; v < l; ++v) {
+      const int c0 = 3 * (v - f);
+      for (size_t q = 0; q < H[v].row.size(); ++q) {
+        const int u = H[v].row[q];
+        const int r0 = loc[u];
+        const double* b = &H[v].val[9 * q];
+        for (int a = 0; a < 3; ++a)
+          for (int c = 0; c < 3; ++c) {
+            const int rr = r0 + a, cc = c0 + c;
+            if (rr >= cc) Fm[rr + (size_t)cc * m] += b[3 * a + c];
+          }
+      }
+    }
+    // extend-add of the children's update matrices
+    for (int c : skids[s]) {
+      const vector<int>& Rc = F.sn_rows[c];
+      const int nc = 3 * (int)Rc.size();
+      const vector<double>& Uc = upd[c];
+      vector<int> map(nc);
+      for (size_t q = 0; q < Rc.size(); ++q)
+        for (int a = 0; a < 3; ++a) map[3 * q + a] = loc[Rc[q]] + a;
+      for (int cc = 0; cc < nc; ++cc) {
+        const int gc = map[cc];
+        for (int rr = cc; rr < nc; ++rr) {
+          const double val = Uc[rr + (size_t)cc * nc];
+          int gr = map[rr], gcc = gc;
+          if (gr < gcc) std::swap(gr, gcc);
+          if (gcc < nJ)
+            Fm[gr + (size_t)gcc * m] += val;
+          else
+            U[(gr - nJ) + (size_t)(gcc - nJ) * nR] += val;
+        }
+      }
+      upd[c].clear();
+      upd[c].shrink_to_fit();
+    }
+    // partial factorisation
+    if (!dense::potrf(Fm.data(), nJ, m)) return false;
+    if (nR > 0) {
+      dense::trsm_rlt(Fm.data() + nJ, nR, nJ, m, Fm.data(), m);
+      const double* LR = Fm.data() + nJ;
+      dense::gemm(false, true, nR, nR, nJ, -1.0, LR, m, LR, m, U.data(), nR, true);
+      upd[s].swap(U);
+    }
+    for (int v = f; v < l; ++v) loc[v] = -1;
+    for (int u : R) loc[u] = -1;
+  }
+  return true;
+}
+
+// X (n_scalar x nrhs, row-major) <- H^{-1} X with the supernodal factor. In column-major
+// terms X is the nrhs x n matrix X^T, so each supernode's steps are right-side solves and
+// GEMMs on X^T: forward X_J <- X_J L_JJ^{-T}, X_R -= X_J L_RJ^T; backward
+// X_J -= X_R L_RJ, X_J <- X_J L_JJ^{-1}.
+static void solve_inplace(const Factor& F, double* X, int nrhs) {
+  const int ns = F.nsn();
+  vector<double> XR;
+  for (int s = 0; s < ns; ++s) {
+    const int f = F.sn_first[s], nJ = 3 * (F.sn_first[s + 1] - f);
+    const vector<int>& R = F.sn_rows[s];
+    const int nR = 3 * (int)R.size(), m = nJ + nR;
+    const double* L = F.L[s].data();
+    double* XJ = X + (size_t)3 * f * nrhs;
+    dense::trsm_rlt(XJ, nrhs, nJ, nrhs, L, m);
+    if (nR == 0) continue;
+    XR.assign((size_t)nR * nrhs, 0.0);
+    dense::gemm(false, true, nrhs, nR, nJ, -1.0, XJ, nrhs, L + nJ, m, XR.data(), nrhs);
+    for (size_t q = 0; q < R.size(); ++q)
+      for (int a = 0; a < 3; ++a) {
+        double* xr = X + (size_t)(3 * R[q] + a) * nrhs;
+        const double* d = XR.data() + (size_t)(3 * q + a) * nrhs;
+        for (int c = 0; c < nrhs; ++c) xr[c] += d[c];
+      }
+  }
+  for (int s = ns - 1; s >= 0; --s) {
+    const int f = F.sn_first[s], nJ = 3 * (F.sn_first[s + 1] - f);
+    const vector<int>& R = F.sn_rows[s];
+    const int nR = 3 * (int)R.size(), m = nJ + nR;
+    const double* L = F.L[s].data();
+    double* XJ = X + (size_t)3 * f * nrhs;
+    if (nR > 0) {
+      XR.resize((size_t)nR * nrhs);
+      for (size_t q = 0; q < R.size(); ++q)
+        for (int a = 0; a < 3; ++a)
+          std::memcpy(XR.data() + (size_t)(3 * q + a) * nrhs, X + (size_t)(3 * R[q] + a) * nrhs,
+                      sizeof(double) * nrhs);
+      dense::gemm(false, false, nrhs, nJ, nR, -1.0, XR.data(), nrhs, L + nJ, m, XJ, nrhs);
+    }
+    dense::trsm_rln(XJ, nrhs, nJ, nrhs, L, m);
+  }
+}
+
+// Multi-RHS solve: the columns are split into one contiguous chunk per thread.
+static void solve_many(const Factor& F, vector<double>& B /* n x nrhs row-major */, int n, int nrhs) {
+  const int nt = std::max(1, std::min(omp_get_max_threads(), (nrhs + 7) / 8));
+  if (nt == 1) {
+    solve_inplace(F, B.data(), nrhs);
+    return;
+  }
+#pragma omp parallel for schedule(static, 1) num_threads(nt)
+  for (int c = 0; c < nt; ++c) {
+    const int c0 = (int)((long)nrhs * c / nt), c1 = (int)((long)nrhs * (c + 1) / nt), cw = c1 - c0;
+    vector<double> X((size_t)n * cw);
+    for (int i = 0; i < n; ++i) std::memcpy(&X[(size_t)i * cw], &B[(size_t)i * nrhs + c0], sizeof(double) * cw);
+    solve_inplace(F, X.data(), cw);
+    for (int i = 0; i < n; ++i) std::memcpy(&B[(size_t)i * nrhs + c0], &X[(size_t)i * cw], sizeof(double) * cw);
+  }
+}
+
+// Diagonal 3x3 blocks of H^{-1} by the Takahashi recurrences on the supernodal pattern
+// (consumes the factor: L is overwritten with the selected inverse Z).
+static void selected_inverse_diag(Factor& F, vector<double>& Adiag /* nv x 9 */) {
+  const int ns = F.nsn();
+  Adiag.assign((size_t)F.nv * 9, 0.0);
+  for (int s = ns - 1; s >= 0; --s) {
+    const int f = F.sn_first[s], nJ = 3 * (F.sn_first[s + 1] - f);
+    const vector<int>& R = F.sn_rows[s];
+    const int nR = 3 * (int)R.size();
+    const int m = nJ + nR;
+    vector<double>& L = F.L[s];
+    // Li = L_JJ^{-1} (lower), Y = L_RJ Li  (nR x nJ)
+    vector<double> Li((size_t)nJ * nJ);
+    dense::trtri_lower(L.data(), nJ, m, Li.data());
+    vector<double> Y((size_t)nR * nJ, 0.0);
+    dense::gemm(false, false, nR, nJ, nJ, 1.0, L.data() + nJ, m, Li.data(), nJ, Y.data(), nR);
+    // Z_RR gathered from the ancestors (already holding Z)
+    vector<double> ZRR((size_t)nR * nR, 0.0);
+#pragma omp parallel for schedule(dynamic, 4) if (R.size() > 64)
+    for (int cb = 0; cb < (int)R.size(); ++cb) {
+      const int v2 = R[cb];
+      const int K = F.sn_of[v2];
+      const int fK = F.sn_first[K], nJK = 3 * (F.sn_first[K + 1] - fK);
+      const vector<int>& RK = F.sn_rows[K];
+      const int mK = nJK + 3 * (int)RK.size();
+      const double* Z = F.L[K].data();
+      for (int rb = cb; rb < (int)R.size(); ++rb) {
+        const int v1 = R[rb];
+        int lr;
+        if (v1 < F.sn_first[K + 1]) {
+          lr = 3 * (v1 - fK);
+        } else {
+          const auto it = std::lower_bound(RK.begin(), RK.end(), v1);
+          lr = nJK + 3 * (int)(it - RK.begin());
+        }
+        const int lc = 3 * (v2 - fK);
+        for (int a = 0; a < 3; ++a)
+          for (int c = 0; c < 3; ++c) {
+            int rr = lr + a, cc = lc + c;
+            double z;
+            if (rr >= cc)
+              z = Z[rr + (size_t)cc * mK];
+            else
+              z = Z[cc + (size_t)rr * mK];  // within the diagonal block of K (symmetric)
+            const int gi = 3 * rb + a, gj = 3 * cb + c;
+            ZRR[gi + (size_t)gj * nR] = z;
+            ZRR[gj + (size_t)gi * nR] = z;
+          }
+      }
+    }
+    // Z_RJ = -Z_RR Y ; Z_JJ = Li^T Li - Y^T Z_RJ
+    vector<double> ZRJ((size_t)nR * nJ, 0.0);
+    dense::gemm(false, false, nR, nJ, nR, -1.0, ZRR.data(), nR, Y.data(), nR, ZRJ.data(), nR);
+    vector<double> ZJJ((size_t)nJ * nJ, 0.0);
+    dense::gemm(true, false, nJ, nJ, nJ, 1.0, Li.data(), nJ, Li.data(), nJ, ZJJ.data(), nJ);
+    dense::gemm(true, false, nJ, nJ, nR, -1.0, Y.data(), nR, ZRJ.data(), nR, ZJJ.data(), nJ);
+    // store Z in place of L
+    for (int j = 0; j < nJ; ++j) {
+      for (int i = 0; i < nJ; ++i) L[i + (size_t)j * m] = ZJJ[i + (size_t)j * nJ];
+      for (int r = 0; r < nR; ++r) L[nJ + r + (size_t)j * m] = ZRJ[r + (size_t)j * nR];
+    }
+    for (int v = f; v < F.sn_first[s + 1]; ++v)
+      for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c)
+          Adiag[(size_t)v * 9 + 3 * a + c] = ZJJ[(3 * (v - f) + a) + (size_t)(3 * (v - f) + c) * nJ];
+  }
+}
+
+// ------------------------------------------------------------------ per-body precompute
+
+struct BodyResult {
+  // per body-local free vertex: n_cub slots
+  vector<int> elem_local;  // body-local element index or -1
+  vector<double> w, u, resid;
+};
+
+static void inv3(const double* A, double* Ai) {
+  const double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+  const double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+  Ai[0] = c00 / det;
+  Ai[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+  Ai[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+  Ai[3] = c01 / det;
+  Ai[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+  Ai[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+  Ai[6] = c02 / det;
+  Ai[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+  Ai[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+}
+
+static jgs2_status body_precompute(const Mesh& M, const vector<int>& bverts, const vector<int>& belems,
+                                   const jgs2_precompute_opts& o, BodyResult& out, std::string& err) {
+  const int nvb = (int)bverts.size();
+  // body-local vertex ids, free numbering
+  std::map<int, int> lidx;
+  for (int q = 0; q < nvb; ++q) lidx[bverts[q]] = q;
+  vector<int> fid(nvb, -1), fverts;
+  for (int q = 0; q < nvb; ++q)
+    if (!M.pinned[bverts[q]]) {
+      fid[q] = (int)fverts.size();
+      fverts.push_back(q);
+    }
+  const int nf = (int)fverts.size();
+  const int nc = o.n_cub;
+  double t_phase = now_s();
+  out.elem_local.assign((size_t)nvb * nc, -1);
+  out.w.assign((size_t)nvb * nc, 0.0);
+  out.u.assign((size_t)nvb * nc * 36, 0.0);
+  out.resid.assign(nvb, std::nan(""));
+  if (nf == 0) return JGS2_OK;
+  const double ih2 = 1.0 / (M.h * M.h);
+  // adjacency among free vertices and coordinates
+  vector<vector<int>> adj(nf);
+  vector<double> P((size_t)3 * nf);
+  for (int a = 0; a < nf; ++a)
+    for (int q = 0; q < 3; ++q) P[3 * a + q] = M.X[3 * bverts[fverts[a]] + q];
+  vector<int> tl((size_t)4 * belems.size());
+  for (size_t e = 0; e < belems.size(); ++e)
+    for (int a = 0; a < 4; ++a) tl[4 * e + a] = lidx[M.tets_c[4 * (size_t)belems[e] + a]];
+  for (size_t e = 0; e < belems.size(); ++e)
+    for (int a = 0; a < 4; ++a)
+      for (int c = 0; c < 4; ++c) {
+        const int fa = fid[tl[4 * e + a]], fc = fid[tl[4 * e + c]];
+        if (a != c && fa >= 0 && fc >= 0) adj[fa].push_back(fc);
+      }
+  for (auto& a : adj) {
+    std::sort(a.begin(), a.end());
+    a.erase(std::unique(a.begin(), a.end()), a.end());
+  }
+  // nested dissection order: ord[k] = free index of the k-th vertex in factor order
+  vector<int> ord, idx(nf);
+  std::iota(idx.begin(), idx.end(), 0);
+  vector<char> side(nf, 0);
+  nd_order(P, adj, idx, side, ord);
+  vector<int> pos(nf);
+  for (int k = 0; k < nf; ++k) pos[ord[k]] = k;
+  // rest Hessian, lower block columns in factor order
+  vector<BlockCol> H(nf);
+  {
+    vector<std::map<int, std::array<double, 9>>> cols(nf);
+    for (size_t e = 0; e < belems.size(); ++e) {
+      const int t = belems[e];
+      const double* B = &M.B[9 * (size_t)t];
+      double b[4][3];
+      for (int j = 0; j < 3; ++j) {
+        b[0][j] = -(B[j] + B[3 + j] + B[6 + j]);
+        for (int k = 1; k < 4; ++k) b[k][j] = B[3 * (k - 1) + j];
+      }
+      const double V = M.vol[t], mu = M.mu[t], lam = M.lp[t] - M.mu[t];
+      const double mq = M.rho[t] * V / 4.0 * ih2;
+      for (int a = 0; a < 4; ++a) {
+        const int fa = fid[tl[4 * e + a]];
+        if (fa < 0) continue;
+        for (int c = 0; c < 4; ++c) {
+          const int fc = fid[tl[4 * e + c]];
+          if (fc < 0) continue;
+          const int ra = pos[fa], cc = pos[fc];
+          if (ra < cc) continue;  // lower: row >= column
+          const double bb = b[a][0] * b[c][0] + b[a][1] * b[c][1] + b[a][2] * b[c][2];
+          auto& blk = cols[cc][ra];
+          for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k)
+              blk[3 * i + k] += V * ((i == k ? mu * bb : 0.0) + mu * b[c][i] * b[a][k] + lam * b[a][i] * b[c][k]) +
+                                (a == c && i == k ? mq : 0.0);
+        }
+      }
+    }
+    for (int c = 0; c < nf; ++c) {
+      for (auto& kv : cols[c]) {
+        H[c].row.push_back(kv.first);
+        H[c].val.insert(H[c].val.end(), kv.second.begin(), kv.second.end());
+      }
+    }
+  }
+  PHASE("order+assemble");
+  Factor F;
+  if (!factorize(nf, H, F)) {
+    err = "rest Hessian is not positive definite";
+    return JGS2_EINVAL;
+  }
+  const int n = 3 * nf;
+  if (verbose()) {
+    size_t nnz = 0;
+    for (const auto& l : F.L) nnz += l.size();
+    std::fprintf(stderr, "[jgs2_precompute] nf %d supernodes %d L entries %.3e\n", nf, F.nsn(), (double)nnz);
+  }
+  PHASE("factorize");
+  // ---- training poses: lowest eigenpairs by block inverse iteration
+  const int nt = std::min(o.n_train, n);
+  const int p = std::min(n, nt + std::max(10, nt));
+  vector<double> Q((size_t)n * p);  // row-major n x p (factor order)
+  {
+    SplitMix g = keyed(o.seed, 0xE16E0000ULL, 0);
+    for (auto& q : Q) q = (double)(g.next() >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+  }
+  // full (both triangles) block rows of H_bar for the products H Q
+  vector<vector<std::pair<int, const double*>>> Hrow(nf);
+  for (int c = 0; c < nf; ++c)
+    for (size_t q = 0; q < H[c].row.size(); ++q) {
+      const int r = H[c].row[q];
+      Hrow[r].push_back({c, &H[c].val[9 * q]});
+      if (r != c) Hrow[c].push_back({-1 - r, &H[c].val[9 * q]});  // transposed block
+    }
+  auto Hmul = [&](const vector<double>& Xin, vector<double>& Yout, int k) {
+    Yout.assign((size_t)n * k, 0.0);
+#pragma omp parallel for schedule(static)
+    for (int r = 0; r < nf; ++r)
+      for (const auto& e : Hrow[r]) {
+        const bool tr = e.first < 0;
+        const int c = tr ? -1 - e.first : e.first;
+        for (int a = 0; a < 3; ++a) {
+          double* yr = &Yout[(size_t)(3 * r + a) * k];
+          for (int cc = 0; cc < 3; ++cc) {
+            const double hv = tr ? e.second[3 * cc + a] : e.second[3 * a + cc];
+            const double* xc = &Xin[(size_t)(3 * c + cc) * k];
+            for (int j = 0; j < k; ++j) yr[j] += hv * xc[j];
+          }
+        }
+      }
+  };
+  // column-major views: X (n x k, row-major) = X^T (k x n, column-major, ld k)
+  auto orthonormalise = [&](vector<double>& X, int k) {
+    // Cholesky QR twice: G = X^T X, X <- X R^{-1}
+    for (int pass = 0; pass < 2; ++pass) {
+      vector<double> G((size_t)k * k, 0.0);
+      dense::gemm(false, true, k, k, n, 1.0, X.data(), k, X.data(), k, G.data(), k);
+      for (int a = 0; a < k; ++a)
+        for (int b2 = a + 1; b2 < k; ++b2) G[a + (size_t)b2 * k] = G[b2 + (size_t)a * k];
+      if (!dense::potrf(G.data(), k, k)) {
+        // fall back to modified Gram-Schmidt (rank-deficient block)
+        for (int j = 0; j < k; ++j) {
+          for (int q = 0; q < j; ++q) {
+            double d = 0.0;
+            for (int i = 0; i < n; ++i) d += X[(size_t)i * k + q] * X[(size_t)i * k + j];
+            for (int i = 0; i < n; ++i) X[(size_t)i * k + j] -= d * X[(size_t)i * k + q];
+          }
+          double nr = 0.0;
+          for (int i = 0; i < n; ++i) nr += X[(size_t)i * k + j] * X[(size_t)i * k + j];
+          nr = std::sqrt(std::max(nr, 1e-300));
+          for (int i = 0; i < n; ++i) X[(size_t)i * k + j] /= nr;
+        }
+        continue;
+      }
+      // X^T (k x n col-major) <- R^{-T} X^T with R = G^T: rows of X times R^{-1}
+      // X (n x k row-major) = X_cm^T; X R^{-1} == (R^{-T} X^T)^T: solve per row
+#pragma omp parallel for schedule(static)
+      for (int i = 0; i < n; ++i) {
+        double* xi = &X[(size_t)i * k];
+        for (int j = 0; j < k; ++j) {
+          double v = xi[j];
+          for (int q = 0; q < j; ++q) v -= xi[q] * G[j + (size_t)q * k];
+          xi[j] = v / G[j + (size_t)j * k];
+        }
+      }
+    }
+  };
+  vector<double> lam(p, 0.0);
+  {
+    vector<double> HQ;
+    for (int it = 0; it < 80; ++it) {
+      solve_many(F, Q, n, p);
+      orthonormalise(Q, p);
+      Hmul(Q, HQ, p);
+      vector<double> T((size_t)p * p, 0.0), w, Vv;
+      dense::gemm(false, true, p, p, n, 1.0, Q.data(), p, HQ.data(), p, T.data(), p);
+      for (int a = 0; a < p; ++a)
+        for (int b2 = a + 1; b2 < p; ++b2) T[(size_t)a * p + b2] = T[(size_t)b2 * p + a] = 0.5 * (T[(size_t)a * p + b2] + T[(size_t)b2 * p + a]);
+      sym_eig(T, p, w, Vv);
+      vector<int> o2(p);
+      std::iota(o2.begin(), o2.end(), 0);
+      std::sort(o2.begin(), o2.end(), [&](int a, int b2) { return w[a] < w[b2]; });
+      vector<double> Vs((size_t)p * p);
+      for (int a = 0; a < p; ++a)
+        for (int j = 0; j < p; ++j) Vs[(size_t)a * p + j] = Vv[(size_t)a * p + o2[j]];
+      for (int j = 0; j < p; ++j) lam[j] = w[o2[j]];
+      // rotate Q and HQ by the Ritz vectors: row-major (n x p) times (p x p)
+      vector<double> Qn((size_t)n * p, 0.0), HQn((size_t)n * p, 0.0);
+#pragma omp parallel for schedule(static)
+      for (int i = 0; i < n; ++i)
+        for (int a = 0; a < p; ++a) {
+          const double qa = Q[(size_t)i * p + a], ha = HQ[(size_t)i * p + a];
+          const double* va = &Vs[(size_t)a * p];
+          double* qo = &Qn[(size_t)i * p];
+          double* ho = &HQn[(size_t)i * p];
+          for (int j = 0; j < p; ++j) {
+            qo[j] += qa * va[j];
+            ho[j] += ha * va[j];
+          }
+        }
+      Q.swap(Qn);
+      HQ.swap(HQn);
+      double worst = 0.0;
+      for (int j = 0; j < nt; ++j) {
+        double rr = 0.0;
+        for (int i = 0; i < n; ++i) {
+          const double d = HQ[(size_t)i * p + j] - lam[j] * Q[(size_t)i * p + j];
+          rr += d * d;
+        }
+        worst = std::max(worst, std::sqrt(rr) / std::fabs(lam[j]));
+      }
+      if (verbose() && (it % 10 == 0)) std::fprintf(stderr, "[jgs2_precompute] eig it %d resid %.2e\n", it, worst);
+      if (worst < 1e-8) break;
+    }
+  }
+  PHASE("eigen");
+  // ---- cubature pool (body-local element indices) and its free vertices
+  const int ne = (int)belems.size();
+  vector<int> all(ne);
+  std::iota(all.begin(), all.end(), 0);
+  vector<int> pool = draw(keyed(o.seed, 0xFFFFFFFFULL, 0), all, o.n_pool);
+  std::sort(pool.begin(), pool.end());
+  vector<int> pv;  // free index of pool vertices
+  for (int e : pool)
+    for (int a = 0; a < 4; ++a) {
+      const int fa = fid[tl[4 * e + a]];
+      if (fa >= 0) pv.push_back(fa);
+    }
+  std::sort(pv.begin(), pv.end());
+  pv.erase(std::unique(pv.begin(), pv.end()), pv.end());
+  vector<int> pv_slot(nf, -1);
+  for (size_t q = 0; q < pv.size(); ++q) pv_slot[pv[q]] = (int)q;
+  const int np = (int)pv.size();
+  // rows of H^{-1} at the pool vertices: G[f][q] = (H^{-1})_{f, pv[q]} (3x3), f free index
+  // FP64 when it fits in 2 GB, else FP32 (rows of H^-1 only shape the cubature)
+  const bool g64 = (size_t)nf * np * 9 <= ((size_t)1 << 28);
+  vector<double> G64(g64 ? (size_t)nf * np * 9 : 0);
+  vector<float> G32(g64 ? 0 : (size_t)nf * np * 9);
+  auto Gat = [&](size_t q) -> double { return g64 ? G64[q] : (double)G32[q]; };
+  {
+    const int batch = 384;  // RHS per batch (multiple of 3)
+    for (int q0 = 0; q0 < 3 * np; q0 += batch) {
+      const int k = std::min(batch, 3 * np - q0);
+      vector<double> Bm((size_t)n * k, 0.0);
+      for (int j = 0; j < k; ++j) {
+        const int col = q0 + j;
+        const int v = pv[col / 3];
+        Bm[(size_t)(3 * pos[v] + col % 3) * k + j] = 1.0;
+      }
+      solve_many(F, Bm, n, k);
+      for (int f = 0; f < nf; ++f)
+        for (int j = 0; j < k; ++j) {
+          const int col = q0 + j, q = col / 3, c = col % 3;
+          for (int a = 0; a < 3; ++a)
+          {
+            const double val = Bm[(size_t)(3 * pos[f] + a) * k + j];
+            const size_t gi = ((size_t)f * np + q) * 9 + 3 * a + c;
+            if (g64)
+              G64[gi] = val;
+            else
+              G32[gi] = (float)val;
+          }
+        }
+    }
+  }
+  PHASE("pool solves");
+  // eigenvectors in free-index order (nt columns)
+  vector<double> q_free((size_t)nt * n);
+  for (int j = 0; j < nt; ++j)
+    for (int f = 0; f < nf; ++f)
+      for (int a = 0; a < 3; ++a) q_free[(size_t)j * n + 3 * f + a] = Q[(size_t)(3 * pos[f] + a) * p + j];
+  Q.clear();
+  Q.shrink_to_fit();
+  // ---- diagonal blocks of H^{-1} (consumes the factor)
+  vector<double> Adiag;
+  selected_inverse_diag(F, Adiag);
+  F.L.clear();
+  PHASE("selected inverse");
+  // incident elements per body-local vertex (for eligibility)
+  vector<vector<int>> inc(nvb);
+  for (int e = 0; e < ne; ++e)
+    for (int a = 0; a < 4; ++a) inc[tl[4 * e + a]].push_back(e);
+  // ---- greedy NNLS per free vertex
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int f = 0; f < nf; ++f) {
+    const int lv = fverts[f];  // body-local vertex index
+    double A[9], Ai[9];
+    for (int q = 0; q < 9; ++q) A[q] = Adiag[(size_t)pos[f] * 9 + q];
+    inv3(A, Ai);
+    // target rows b^(t) = A^{-1} q_ti - lam_t q_ti, kept if |b| > 1e-12 max|b|
+    vector<double> bt((size_t)3 * nt), nb(nt);
+    double nbmax = 0.0;
+    for (int t = 0; t < nt; ++t) {
+      const double* qi = &q_free[(size_t)t * n + 3 * f];
+      for (int a = 0; a < 3; ++a) bt[3 * t + a] = Ai[3 * a] * qi[0] + Ai[3 * a + 1] * qi[1] + Ai[3 * a + 2] * qi[2] - lam[t] * qi[a];
+      nb[t] = std::sqrt(bt[3 * t] * bt[3 * t] + bt[3 * t + 1] * bt[3 * t + 1] + bt[3 * t + 2] * bt[3 * t + 2]);
+      nbmax = std::max(nbmax, nb[t]);
+    }
+    vector<int> keep;
+    for (int t = 0; t < nt; ++t)
+      if (nb[t] > 1e-12 * std::max(nbmax, 1e-300)) keep.push_back(t);
+    const int mrows = 3 * (int)keep.size();
+    vector<double> y(mrows);
+    for (size_t r = 0; r < keep.size(); ++r)
+      for (int a = 0; a < 3; ++a) y[3 * r + a] = bt[3 * keep[r] + a] / nb[keep[r]];
+    double ynorm = 0.0;
+    for (double v : y) ynorm += v * v;
+    ynorm = std::sqrt(ynorm);
+    // U_bar_{i,a} = (H^-1)_{a,i} A_i^{-1} = G[f][a]^T A_i^{-1}
+    auto ubar_block = [&](int fa, double* U) {
+      const size_t g0 = ((size_t)f * np + pv_slot[fa]) * 9;
+      double g[9];
+      for (int q = 0; q < 9; ++q) g[q] = Gat(g0 + q);
+      // g = (H^-1)_{i,a}; U = g^T A_i^{-1}
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) U[3 * r + c] = g[0 * 3 + r] * Ai[c] + g[1 * 3 + r] * Ai[3 + c] + g[2 * 3 + r] * Ai[6 + c];
+    };
+    auto column = [&](int e, double* col) {
+      for (int r = 0; r < mrows; ++r) col[r] = 0.0;
+      for (int a = 0; a < 4; ++a) {
+        const int fa = fid[tl[4 * e + a]];
+        if (fa < 0) continue;
+        double U[9];
+        ubar_block(fa, U);
+        for (size_t r = 0; r < keep.size(); ++r) {
+          const int t = keep[r];
+          const double* qa = &q_free[(size_t)t * n + 3 * fa];
+          for (int c = 0; c < 3; ++c)
+            col[3 * r + c] += lam[t] * (U[c] * qa[0] + U[3 + c] * qa[1] + U[6 + c] * qa[2]) / nb[t];
+        }
+      }
+    };
+    vector<int> sel;
+    vector<double> w_sel;
+    double res = 1.0;
+    vector<double> Acols;
+    for (int r = 0; r < nc; ++r) {
+      if (res < o.nnls_tol) break;
+      vector<int> elig;
+      for (int e : pool) {
+        if (std::find(sel.begin(), sel.end(), e) != sel.end()) continue;
+        if (std::find(inc[lv].begin(), inc[lv].end(), e) != inc[lv].end()) continue;
+        elig.push_back(e);
+      }
+      vector<int> cands = draw(keyed(o.seed, (uint64_t)lv, (uint64_t)r), elig, o.n_cand);
+      double best = 0.0;
+      int best_e = -1;
+      vector<double> best_w;
+      const int k = (int)sel.size() + 1;
+      vector<double> Am((size_t)mrows * k);
+      std::copy(Acols.begin(), Acols.end(), Am.begin());
+      for (int c : cands) {
+        column(c, &Am[(size_t)(k - 1) * mrows]);
+        vector<double> wc;
+        const double rn = nnls(Am, mrows, k, y, wc) / ynorm;
+        if (best_e < 0 || rn < best || (rn == best && c < best_e)) {
+          best = rn;
+          best_e = c;
+          best_w = wc;
+        }
+      }
+      if (best_e < 0) break;
+      sel.push_back(best_e);
+      w_sel = best_w;
+      res = best;
+      Acols.resize((size_t)mrows * k);
+      column(best_e, &Acols[(size_t)(k - 1) * mrows]);
+    }
+    out.resid[lv] = res;
+    for (size_t s = 0; s < sel.size(); ++s) {
+      const int e = sel[s];
+      out.elem_local[(size_t)lv * nc + s] = e;
+      out.w[(size_t)lv * nc + s] = w_sel[s];
+      for (int a = 0; a < 4; ++a) {
+        const int fa = fid[tl[4 * e + a]];
+        if (fa < 0) continue;
+        double U[9];
+        ubar_block(fa, U);
+        for (int q = 0; q < 9; ++q) out.u[((size_t)lv * nc + s) * 36 + 9 * a + q] = U[q];
+      }
+    }
+  }
+  PHASE("greedy nnls");
+  return JGS2_OK;
+}
+
+// Bodies equal up to translation (same local connectivity, material and pins).
+static bool same_body(const Mesh& M, const vector<int>& va, const vector<int>& ea, const vector<int>& vb,
+                      const vector<int>& eb) {
+  if (va.size() != vb.size() || ea.size() != eb.size()) return false;
+  double ext = 0.0;
+  for (size_t q = 0; q < va.size(); ++q)
+    for (int c = 0; c < 3; ++c) ext = std::max(ext, std::fabs(M.X[3 * va[q] + c] - M.X[3 * va[0] + c]));
+  for (size_t q = 0; q < va.size(); ++q) {
+    if (M.pinned[va[q]] != M.pinned[vb[q]]) return false;
+    for (int c = 0; c < 3; ++c) {
+      const double da = M.X[3 * va[q] + c] - M.X[3 * va[0] + c];
+      const double db = M.X[3 * vb[q] + c] - M.X[3 * vb[0] + c];
+      if (std::fabs(da - db) > 1e-9 * std::max(ext, 1e-300)) return false;
+    }
+  }
+  for (size_t e = 0; e < ea.size(); ++e) {
+    const int ta = ea[e], tb = eb[e];
+    if (M.E[ta] != M.E[tb] || M.nu[ta] != M.nu[tb] || M.rho[ta] != M.rho[tb]) return false;
+    for (int a = 0; a < 4; ++a)
+      if (M.tets_c[4 * (size_t)ta + a] - va[0] != M.tets_c[4 * (size_t)tb + a] - vb[0]) return false;
+  }
+  return true;
+}
+
+}  // namespace pre
+
+jgs2_status precompute(Mesh* m, const jgs2_precompute_opts* o) {
+  using namespace pre;
+  if (!m || !o) return fail(JGS2_EINVAL, "null argument");
+  if (o->n_cub < 1 || o->n_cub > kMaxCub || o->n_train < 1 || o->n_cand < 1 || o->n_pool < 1 ||
+      !(o->nnls_tol >= 0.0))
+    return fail(JGS2_EINVAL, "precompute options out of range");
+  const int saved = omp_get_max_threads();
+  if (o->n_threads > 0) omp_set_num_threads(o->n_threads);
+  const int nb = m->n_bodies;
+  vector<vector<int>> bv(nb), be(nb);
+  for (int v = 0; v < m->V; ++v) bv[m->body[v]].push_back(v);
+  for (int t = 0; t < m->T; ++t) be[m->body[m->tets_c[4 * (size_t)t]]].push_back(t);
+  vector<int> rep(nb, -1);
+  vector<BodyResult> res(nb);
+  jgs2_status st = JGS2_OK;
+  std::string err;
+  for (int b = 0; b < nb && st == JGS2_OK; ++b) {
+    for (int c = 0; c < b; ++c)
+      if (rep[c] == c && same_body(*m, bv[c], be[c], bv[b], be[b])) {
+        rep[b] = c;
+        break;
+      }
+    if (rep[b] >= 0) continue;
+    rep[b] = b;
+    st = body_precompute(*m, bv[b], be[b], *o, res[b], err);
+  }
+  omp_set_num_threads(saved);
+  if (st != JGS2_OK) return fail(st, "jgs2_precompute: " + err);
+  const int nc = o->n_cub;
+  const size_t Vf = m->Vf;
+  vector<int> e_int(Vf * nc, -1);
+  vector<double> w(Vf * nc, 0.0), u(Vf * nc * 36, 0.0);
+  m->cub_resid.assign(m->V, std::nan(""));
+  for (int b = 0; b < nb; ++b) {
+    const BodyResult& r = res[rep[b]];
+    for (size_t q = 0; q < bv[b].size(); ++q) {
+      const int c = bv[b][q];
+      m->cub_resid[c] = r.resid[q];
+      const int i = m->iperm[c];
+      if (i >= m->Vf) continue;
+      for (int s = 0; s < nc; ++s) {
+        const int el = r.elem_local[q * nc + s];
+        if (el < 0) continue;
+        e_int[(size_t)i * nc + s] = m->tiperm[be[b][el]];
+        w[(size_t)i * nc + s] = r.w[q * nc + s];
+        for (int k = 0; k < 36; ++k) u[((size_t)i * nc + s) * 36 + k] = r.u[(q * nc + s) * 36 + k];
+      }
+    }
+  }
+  return set_cubature(m, nc, e_int, w, u);
+}
+
+}  // namespace jgs2
+
 extern "C" jgs2_status jgs2_precompute(jgs2_mesh* mesh, const jgs2_precompute_opts* opts) {
-  (void)mesh;
-  (void)opts;
-  return jgs2::fail(JGS2_EINVAL, "jgs2_precompute: not built yet");
+  return jgs2::precompute(reinterpret_cast<jgs2::Mesh*>(mesh), opts);
 }

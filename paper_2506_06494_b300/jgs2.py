@@ -16,6 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libjgs2.so")
 
 TRACE_MAX = 4096
+NKERNELS = 5
+KERNEL_NAMES = ["k_pool", "k_main", "k_energy", "k_update", "setup"]
 FP64, FP32 = 0, 1
 CORR_ASM, CORR_ELEM, CORR_OFF = 0, 1, 2
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTPRECOMPUTED", 5: "ENOTCONVERGED",
@@ -44,13 +46,15 @@ class CubatureBlob(C.Structure):
 class StepOpts(C.Structure):
     _fields_ = [("max_sweeps", C.c_int32), ("rel_tol", C.c_double), ("precision", C.c_int32),
                 ("correction", C.c_int32), ("line_search", C.c_int32), ("check_every", C.c_int32),
-                ("record_trace", C.c_int32)]
+                ("record_trace", C.c_int32), ("profile", C.c_int32)]
 
 
 class StepReport(C.Structure):
     _fields_ = [("sweeps", C.c_int32), ("converged", C.c_int32), ("fallback", C.c_int32),
                 ("ls_rejects", C.c_int32), ("rel_residual", C.c_double), ("g0", C.c_double),
-                ("ms", C.c_double), ("trace_len", C.c_int32), ("trace", C.c_double * TRACE_MAX)]
+                ("ms", C.c_double), ("launches", C.c_int32),
+                ("kernel_launches", C.c_int32 * NKERNELS), ("kernel_ms", C.c_double * NKERNELS),
+                ("trace_len", C.c_int32), ("trace", C.c_double * TRACE_MAX)]
 
 
 _lib = None
