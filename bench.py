@@ -27,7 +27,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ms/step to 1e-4 rel. residual at 3.5M tets"
-KIND = ["k_pool", "k_main", "k_energy", "k_update", "setup"]
+KIND = ["k_pool", "k_gather", "k_correct", "k_energy", "k_update", "setup"]
 
 
 def peaks():
@@ -51,15 +51,24 @@ def build_scene(name, n_spheres=10):
     raise SystemExit(f"unknown workload {name}")
 
 
-def main_bytes_per_launch(V_f, T, n_cub, fp_bytes=4):
-    """Algorithmic DRAM bytes of one k_main launch (each datum moved once):
-    per tet: 4 corner ids (16 B) + B (9) + F(x_t) (9) + V_e, mu, lam' (3) scalars + its 4
-    incidence entries (16 B); per free vertex: u read, dz read, D and D_J written (3 scalars
-    each), m/h^2, the incidence count (4 B) and the cubature record n_cub x (pool index 4 B,
-    weight, 36 U_bar entries)."""
-    per_tet = 16 + 21 * fp_bytes + 16
-    per_vertex = (4 * 3 + 1) * fp_bytes + 4 + n_cub * (4 + 37 * fp_bytes)
-    return per_tet * T + per_vertex * V_f
+def kernel_bytes(V_f, T, n_cub, fp_bytes=4):
+    """Algorithmic DRAM bytes per launch (each datum moved once), by kernel.
+
+    tet record: 4 corner ids (16 B) + B (9) + F(x_t) (9) + V_e, mu, lam' (3 scalars);
+    k_gather: tet records + 4 incidence entries per tet (16 B); per free vertex u, dz read,
+      m/h^2, the incidence count, D_J written (3) and g, H, R written (18 scalars);
+    k_correct: per free vertex g, H, R read (18), D written (3), and n_cub cubature slots of
+      (pool index 4 B, weight, 36 U_bar entries); the pool's element data stays in L2;
+    k_energy: tet records; per free vertex u, dz, D, D_J (3 each) and m/h^2;
+    k_update: per free vertex u read and written, one direction read (3 each)."""
+    f = fp_bytes
+    rec = 16 + 21 * f
+    return {
+        "k_gather": T * (rec + 16) + V_f * ((3 + 3 + 1 + 3 + 18) * f + 4),
+        "k_correct": V_f * ((18 + 3) * f + n_cub * (4 + 37 * f)),
+        "k_energy": T * rec + V_f * (13 * f),
+        "k_update": V_f * (9 * f),
+    }
 
 
 class Clocks:
@@ -217,15 +226,22 @@ def run_jgs2(args, rank, world, local_rank):
     for _ in range(n_e2e):
         mesh.step_host(xh, vh, opts_e2e, stream)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / max(n_e2e, 1) if n_e2e else None
-    # roofline of the dominant kernel (k_main)
+    # roofline of the dominant kernel by time share
     hbm, peak_kind = peaks()
     n_cub = args.n_cub if corr != p.CORR_OFF else 0
     Vf = int((~scene.pinned.astype(bool)).sum())
     fpb = 4 if prec == p.FP32 else 8
-    bytes_main = main_bytes_per_launch(Vf, scene.n_tets, n_cub, fpb)
-    main_ms = kms[1] / max(kl[1], 1)
-    achieved = bytes_main / (main_ms * 1e-3) / 1e9
-    share = {KIND[q]: round(float(kms[q] / max(kms.sum(), 1e-12)), 4) for q in range(5)}
+    kb = kernel_bytes(Vf, scene.n_tets, n_cub, fpb)
+    share = {KIND[q]: round(float(kms[q] / max(kms.sum(), 1e-12)), 4) for q in range(len(KIND))}
+    per_kernel = {}
+    for q, name in enumerate(KIND):
+        if name in kb and kl[q] > 0:
+            avg = kms[q] / kl[q]
+            per_kernel[name] = {"avg_launch_ms": round(float(avg), 5), "bytes_per_launch": kb[name],
+                                "GB_s": round(kb[name] / (avg * 1e-3) / 1e9, 1),
+                                "frac": round(kb[name] / (avg * 1e-3) / 1e9 / hbm, 4)}
+    dom = max(per_kernel, key=lambda n: share[n])
+    achieved = per_kernel[dom]["GB_s"]
     out = {
         "metric": METRIC, "value": ms_step, "unit": "ms/step", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
@@ -237,11 +253,13 @@ def run_jgs2(args, rank, world, local_rank):
         "sweeps_per_step": float(sweeps.mean()), "sweeps_per_s": float(sweeps.sum() / (ms_total * 1e-3)),
         "converged_steps": int(sum(q[1] for q in reps)), "max_rel_residual": float(max(q[2] for q in reps)),
         "precompute_s": round(t_pre, 2),
-        "kernel_ms_per_step": {KIND[q]: round(float(kms[q] / args.steps), 4) for q in range(5)},
+        "kernel_ms_per_step": {KIND[q]: round(float(kms[q] / args.steps), 4) for q in range(len(KIND))},
         "kernel_share": share,
-        "roofline": {"bound": "hbm", "kernel": "k_main", "achieved": round(achieved, 1), "peak": hbm,
+        "kernels": per_kernel,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
-                     "bytes_per_launch": bytes_main, "avg_launch_ms": round(float(main_ms), 5),
+                     "bytes_per_launch": per_kernel[dom]["bytes_per_launch"],
+                     "avg_launch_ms": per_kernel[dom]["avg_launch_ms"],
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
         "e2e": {"value": e2e_ms, "unit": "ms/step", "h2d_bytes_per_step": int(xh.nbytes + vh.nbytes),
                 "d2h_bytes_per_step": int(xh.nbytes + vh.nbytes)},

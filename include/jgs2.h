@@ -99,10 +99,12 @@ typedef struct {
 } jgs2_step_opts;
 
 #define JGS2_TRACE_MAX 4096
-/* kernel kinds in jgs2_step_report.kernel_*: pool, main (gather + correction + solve),
- * energy (line search), update, setup (per-step setup and write-back) */
-#define JGS2_NKERNELS 5
-enum { JGS2_K_POOL = 0, JGS2_K_MAIN = 1, JGS2_K_ENERGY = 2, JGS2_K_UPDATE = 3, JGS2_K_SETUP = 4 };
+/* kernel kinds in jgs2_step_report.kernel_*: pool (cubature elements), gather (per-vertex
+ * gradient, diagonal block, rotation), correct (cubature correction + 3x3 solve), energy
+ * (line search), update, setup (per-step setup and write-back) */
+#define JGS2_NKERNELS 6
+enum { JGS2_K_POOL = 0, JGS2_K_GATHER = 1, JGS2_K_CORRECT = 2, JGS2_K_ENERGY = 3, JGS2_K_UPDATE = 4,
+       JGS2_K_SETUP = 5 };
 
 typedef struct {
   int32_t sweeps;            /* sweeps applied in the step */

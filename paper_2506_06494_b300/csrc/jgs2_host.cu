@@ -40,7 +40,7 @@ static cudaError_t dalloc(X** p, size_t n) {
 
 template <typename T>
 void PrecBufs<T>::release() {
-  cudaFree(tets); cudaFree(u); cudaFree(dz); cudaFree(D); cudaFree(DJ); cudaFree(mh2);
+  cudaFree(tets); cudaFree(u); cudaFree(dz); cudaFree(D); cudaFree(DJ); cudaFree(ghr); cudaFree(mh2);
   cudaFree(cub_p); cudaFree(cub_w); cudaFree(cub_u); cudaFree(pool_H); cudaFree(pool_G);
   *this = PrecBufs<T>();
 }
@@ -291,6 +291,7 @@ static jgs2_status ensure_prec(Mesh* m) {
     CK(dalloc(&b.dz, m->Vf));
     CK(dalloc(&b.D, m->Vf));
     CK(dalloc(&b.DJ, m->Vf));
+    CK(dalloc(&b.ghr, 18 * (size_t)m->Vf));
     CK(dalloc(&b.mh2, V));
     CK(cudaMemcpy(b.tets, rec.data(), sizeof(TetRec<T>) * T_, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(b.mh2, mh2.data(), sizeof(T) * V, cudaMemcpyHostToDevice));
@@ -342,6 +343,7 @@ static DevMesh<T> dev_view(Mesh* m) {
   d.dz = b.dz;
   d.D = b.D;
   d.DJ = b.DJ;
+  d.ghr = b.ghr;
   d.mh2 = b.mh2;
   d.cub_p = b.cub_p;
   d.cub_w = b.cub_w;
@@ -417,7 +419,7 @@ struct Launches {
   Mesh* m;
   cudaStream_t s;
   bool prof;
-  int count[JGS2_NKERNELS] = {0, 0, 0, 0, 0};
+  int count[JGS2_NKERNELS] = {0, 0, 0, 0, 0, 0};
   std::vector<std::pair<int, int>> rec;  // (kind, event index)
   int used = 0;
   cudaError_t err = cudaSuccess;
@@ -486,12 +488,17 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t s, 
       L.end(id);
     }
     if (nbV > 0) {
-      id = L.begin(JGS2_K_MAIN);
+      id = L.begin(JGS2_K_GATHER);
       if (corr)
-        k_main<T, true><<<nbV, 128, 0, s>>>(d, m->d_state, k, m->d_partial, m->d_trace, o.record_trace);
+        k_gather<T, true><<<nbV, 128, 0, s>>>(d, m->d_state, k, m->d_partial, m->d_trace, o.record_trace);
       else
-        k_main<T, false><<<nbV, 128, 0, s>>>(d, m->d_state, k, m->d_partial, m->d_trace, o.record_trace);
+        k_gather<T, false><<<nbV, 128, 0, s>>>(d, m->d_state, k, m->d_partial, m->d_trace, o.record_trace);
       L.end(id);
+      if (corr) {
+        id = L.begin(JGS2_K_CORRECT);
+        k_correct<T><<<nbV, 128, 0, s>>>(d, m->d_state, k, m->d_partial, m->d_trace, o.record_trace);
+        L.end(id);
+      }
     }
     if (k == max_k) break;
     if (o.line_search) {

@@ -18,6 +18,7 @@ struct PrecBufs {
   Vec4<T>* dz = nullptr;
   Vec4<T>* D = nullptr;
   Vec4<T>* DJ = nullptr;
+  T* ghr = nullptr;
   T* mh2 = nullptr;
   int32_t* cub_p = nullptr;
   T* cub_w = nullptr;

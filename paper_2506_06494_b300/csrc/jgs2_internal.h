@@ -72,6 +72,7 @@ struct DevMesh {
   Vec4<T>* dz;              // [Vf]
   Vec4<T>* D;               // [Vf] JGS2 direction
   Vec4<T>* DJ;              // [Vf] uncorrected direction -H_ii^{-1} g_i
+  T* ghr;                   // [18][Vf] g_i, H_ii (6), R_i (9) between the two sweep phases
   const T* mh2;             // [V] m_v / h^2 (0 for pinned)
   const int32_t* cub_p;     // [n_cub][Vf] pool slot, -1 unused
   const T* cub_w;           // [n_cub][Vf]

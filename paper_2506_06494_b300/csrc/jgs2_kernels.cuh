@@ -2,10 +2,11 @@
 //   k_pool    per cubature element: assembled gradient and rotation of its corners,
 //             the element Hessian at x^k rotated into the rest frames of its corners
 //             (the R_a factors of Eq. tilde_phi), and the rotated corner gradients.
-//   k_main    per free vertex: gather g_i, H_ii and the volume-weighted deformation
-//             gradient from the incident tets, R_i = polar(F_i), the cubature sums
-//             H~_i, g~_i (Eq. cubature), the 3x3 solve of Eq. reduced_local, the
-//             direction D_i, and the FP64 partial sums |g|^2 and g.D.
+//   k_gather  per free vertex: gather g_i, H_ii and the volume-weighted deformation
+//             gradient from the incident tets, R_i = polar(F_i), the uncorrected
+//             direction D_J, FP64 partial sums |g|^2 and g.D_J.
+//   k_correct per free vertex: the cubature sums H~_i, g~_i (Eq. cubature), the 3x3
+//             solve of Eq. reduced_local, the direction D_i and g.D.
 //   k_energy  (line search) per tet and per free vertex: exact energy differences
 //             E(x + alpha_j D) - E(x) for alpha_j = 2^-j, FP64 sums; the last block
 //             picks the Armijo step.
@@ -460,104 +461,79 @@ __global__ void __launch_bounds__(128) k_pool(DevMesh<T> m, const StepState* __r
       for (int i = 0; i < 3; ++i) sg[wid][i] = g[i];
     }
   }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  // element quantities at x^k
-  T F[9], C[9];
-  tet_F(rec, m.u, F);
-  cofactor(F, C);
-  const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
-  const T s = rec.lp * (J - T(1)) - rec.mu;
-  // dP/dF = mu I + lam' c c^T + s d2J/dF2 (9x9, index 3i+j), c = vec(cof F)
-  T A[81];
+  // element quantities at x^k, shared by the block
+  __shared__ T sF[9], sC[9], sA[81], sb[4][3];
+  __shared__ T ss;
+  if (threadIdx.x == 0) {
+    T F[9], C[9];
+    tet_F(rec, m.u, F);
+    cofactor(F, C);
+    const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
+    ss = rec.lp * (J - T(1)) - rec.mu;
 #pragma unroll
-  for (int a = 0; a < 9; ++a)
-#pragma unroll
-    for (int b = 0; b < 9; ++b) A[9 * a + b] = rec.lp * C[a] * C[b] + (a == b ? rec.mu : T(0));
-  // d2J/dF_ij dF_kl = eps_ikm eps_jln F_mn: nonzero only for i != k and j != l
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      if (i == k) continue;
-      const int mm = 3 - i - k;
-      const T sik = ((k - i + 3) % 3 == 1) ? T(1) : T(-1);  // eps_ikm
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-#pragma unroll
-        for (int l = 0; l < 3; ++l) {
-          if (j == l) continue;
-          const int n = 3 - j - l;
-          const T sjl = ((l - j + 3) % 3 == 1) ? T(1) : T(-1);  // eps_jln
-          A[9 * (3 * i + j) + 3 * k + l] += s * sik * sjl * F[3 * mm + n];
-        }
+    for (int q = 0; q < 9; ++q) {
+      sF[q] = F[q];
+      sC[q] = C[q];
     }
-  // b vectors of the 4 corners
-  T bv[4][3];
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    T b[3];
-    corner_b(rec, c, b);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) bv[c][j] = b[j];
-  }
-  // H_e[(a,i),(c,k)] = V sum_{j,l} b_a[j] A[(i,j),(k,l)] b_c[l] + m_e/h^2 delta
-  T He[144];
-#pragma unroll 1
-  for (int a = 0; a < 4; ++a)
-#pragma unroll 1
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          T acc = T(0);
-#pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            T row = T(0);
-#pragma unroll
-            for (int l = 0; l < 3; ++l) row += A[9 * (3 * i + j) + 3 * k + l] * bv[c][l];
-            acc += bv[a][j] * row;
-          }
-          He[12 * (3 * a + i) + 3 * c + k] = rec.vol * acc;
-        }
-  const T mi = rec.mq * T(m.inv_h2);
-#pragma unroll
-  for (int q = 0; q < 12; ++q) He[13 * q] += mi;
-  // rotate: H' = blockdiag(R)^T H blockdiag(R)
-  T Hr[144];
-#pragma unroll 1
-  for (int a = 0; a < 4; ++a)
-#pragma unroll 1
     for (int c = 0; c < 4; ++c) {
-      T tmp[9];
+      T b[3];
+      corner_b(rec, c, b);
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int l = 0; l < 3; ++l) {
-          T acc = T(0);
-#pragma unroll
-          for (int k = 0; k < 3; ++k) acc += He[12 * (3 * a + i) + 3 * c + k] * sR[c][3 * k + l];
-          tmp[3 * i + l] = acc;
-        }
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-#pragma unroll
-        for (int l = 0; l < 3; ++l) {
-          T acc = T(0);
-#pragma unroll
-          for (int i = 0; i < 3; ++i) acc += sR[a][3 * i + j] * tmp[3 * i + l];
-          Hr[12 * (3 * a + j) + 3 * c + l] = acc;
-        }
+      for (int j = 0; j < 3; ++j) sb[c][j] = b[j];
     }
-  T* Hp = m.pool_H + (size_t)p * kPackedH;
-#pragma unroll 1
-  for (int r = 0; r < 12; ++r)
-    for (int c = r; c < 12; ++c) Hp[pk(r, c)] = T(0.5) * (Hr[12 * r + c] + Hr[12 * c + r]);
-  // rotated corner gradients
-  T* Gp = m.pool_G + (size_t)p * 12;
+  }
+  __syncthreads();
+  // dP/dF = mu I + lam' c c^T + s d2J/dF2 (9x9, index 3i+j), c = vec(cof F);
+  // d2J/dF_ij dF_kl = eps_ikm eps_jln F_mn (nonzero only for i != k and j != l)
+  if (threadIdx.x < 81) {
+    const int row = threadIdx.x / 9, col = threadIdx.x % 9;
+    const int i = row / 3, j = row % 3, k = col / 3, l = col % 3;
+    T v = rec.lp * sC[row] * sC[col] + (row == col ? rec.mu : T(0));
+    if (i != k && j != l) {
+      const int mm = 3 - i - k, n = 3 - j - l;
+      const T sik = ((k - i + 3) % 3 == 1) ? T(1) : T(-1);
+      const T sjl = ((l - j + 3) % 3 == 1) ? T(1) : T(-1);
+      v += ss * sik * sjl * sF[3 * mm + n];
+    }
+    sA[threadIdx.x] = v;
+  }
+  __syncthreads();
+  const T mi = rec.mq * T(m.inv_h2);
+  // packed entry (r, c), r <= c, of H' = blockdiag(R)^T H_e blockdiag(R), with
+  // H_e[(a,i),(c,k)] = V sum_{j,l} b_a[j] A[(i,j),(k,l)] b_c[l] + m_e/h^2 delta
+  if (threadIdx.x < kPackedH) {
+    int r = 0, rem = threadIdx.x;
+    while (rem >= 12 - r) {
+      rem -= 12 - r;
+      ++r;
+    }
+    const int c = r + rem;
+    const int a = r / 3, jj = r % 3, cc = c / 3, ll = c % 3;
+    T Hac[9];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          T row = T(0);
+#pragma unroll
+          for (int l = 0; l < 3; ++l) row += sA[9 * (3 * i + j) + 3 * k + l] * sb[cc][l];
+          acc += sb[a][j] * row;
+        }
+        Hac[3 * i + k] = rec.vol * acc + ((a == cc && i == k) ? mi : T(0));
+      }
+    T v = T(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v += sR[a][3 * i + jj] * Hac[3 * i + k] * sR[cc][3 * k + ll];
+    m.pool_H[(size_t)p * kPackedH + threadIdx.x] = v;
+  } else if (threadIdx.x < kPackedH + 12) {
+    // rotated corner gradient entry (a, j)
+    const int e = threadIdx.x - kPackedH, a = e / 3, j = e % 3;
     T ga[3];
     if (ASM) {
 #pragma unroll
@@ -570,31 +546,60 @@ __global__ void __launch_bounds__(128) k_pool(DevMesh<T> m, const StepState* __r
         load3(m.dz, v, dz);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          const T Pb = (rec.mu * F[3 * i] + s * C[3 * i]) * bv[a][0] +
-                       (rec.mu * F[3 * i + 1] + s * C[3 * i + 1]) * bv[a][1] +
-                       (rec.mu * F[3 * i + 2] + s * C[3 * i + 2]) * bv[a][2];
+          const T Pb = (rec.mu * sF[3 * i] + ss * sC[3 * i]) * sb[a][0] +
+                       (rec.mu * sF[3 * i + 1] + ss * sC[3 * i + 1]) * sb[a][1] +
+                       (rec.mu * sF[3 * i + 2] + ss * sC[3 * i + 2]) * sb[a][2];
           ga[i] = rec.vol * Pb + mi * (uv[i] - dz[i]);
         }
       } else {
         ga[0] = ga[1] = ga[2] = T(0);
       }
     }
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      Gp[3 * a + j] = sR[a][j] * ga[0] + sR[a][3 + j] * ga[1] + sR[a][6 + j] * ga[2];
+    m.pool_G[(size_t)p * 12 + e] = sR[a][j] * ga[0] + sR[a][3 + j] * ga[1] + sR[a][6 + j] * ga[2];
   }
 }
 
-// The per-vertex sweep (Eqs. reduced_local, cubature; Sec. 8.1). Thread per free vertex.
+// Residual bookkeeping of sweep k (reading R9), run by one thread of the last block.
+__device__ __forceinline__ void finalize_sweep(StepState* st, int k, double r2, double gd, double gdj,
+                                               double* trace, int record) {
+  st->ticket_main = 0;
+  const double gn = sqrt(r2);
+  if (k == 0) st->g0 = gn;
+  const double g0 = st->g0;
+  const double r = g0 > 0.0 ? gn / g0 : 0.0;
+  st->r = r;
+  st->slope = gd;
+  st->slope_j = gdj;
+  st->alpha = 1.0;
+  st->dir = 0;
+  if (record && k < 4096) trace[k] = r;
+  if (!isfinite(r) || !isfinite(gd) || !isfinite(gdj)) {
+    st->status = 6;  // JGS2_EDIVERGED
+    st->done = 1;
+    st->sweeps = k;
+  } else if (r <= st->rel_tol || g0 == 0.0) {
+    st->converged = 1;
+    st->done = 1;
+    st->sweeps = k;
+  } else if (k >= st->max_sweeps) {
+    st->done = 1;
+    st->sweeps = k;
+  }
+}
+
+// Sweep phase 1, thread per free vertex: gather g_i and H_ii (+ inertia) over the incident
+// tets (Eq. reduced_local terms), the uncorrected direction D_J = -H_ii^{-1} g_i, and, with
+// the correction on, R_i = polar(F_i) (Eq. tilde_phi). Writes g, H, R as [18][Vf] for
+// phase 2 and the FP64 partial sums |g|^2 and g.D_J. Without the correction D = D_J and
+// this kernel closes the sweep's reduction.
 template <typename T, bool CORR>
-__global__ void __launch_bounds__(128) k_main(DevMesh<T> m, StepState* st, int k,
-                                              double* __restrict__ partial /* [3][grid] */,
-                                              double* __restrict__ trace, int record) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_gather(DevMesh<T> m, StepState* st, int k,
+                                                   double* __restrict__ partial /* [3][grid] */,
+                                                   double* __restrict__ trace, int record) {
   if (st->done) return;
   __shared__ double red[96];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[3] = {0.0, 0.0, 0.0};  // |g|^2, g.D, g.D_J
-  int fb = 0;
+  double acc[2] = {0.0, 0.0};  // |g|^2, g.D_J
   if (i < m.Vf) {
     T g[3], H[6], Fs[9], W;
     gather_vertex(m, i, g, H, Fs, W);
@@ -607,138 +612,140 @@ __global__ void __launch_bounds__(128) k_main(DevMesh<T> m, StepState* st, int k
     H[0] += mh;
     H[3] += mh;
     H[5] += mh;
-    T A[6], rhs[3];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) A[q] = H[q];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) rhs[q] = -g[q];
-    if (CORR) {
-      T R[9];
-#pragma unroll
-      for (int q = 0; q < 9; ++q) Fs[q] /= W;
-      polar_rotation(Fs, R);
-      T Ht[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, gt[3] = {T(0), T(0), T(0)};
-      for (int s = 0; s < m.n_cub; ++s) {
-        const int p = m.cub_p[(size_t)s * m.Vf + i];
-        if (p < 0) continue;
-        const T w = m.cub_w[(size_t)s * m.Vf + i];
-        T U[36];
-        const T* up = m.cub_u + (size_t)s * 36 * m.Vf + i;
-#pragma unroll
-        for (int q = 0; q < 36; ++q) U[q] = up[(size_t)q * m.Vf];
-        const T* Hp = m.pool_H + (size_t)p * kPackedH;
-        const T* Gp = m.pool_G + (size_t)p * 12;
-#pragma unroll
-        for (int r = 0; r < 12; ++r) {
-          T tr[3] = {T(0), T(0), T(0)};
-#pragma unroll
-          for (int c = 0; c < 12; ++c) {
-            const T h = __ldg(Hp + pk(r, c));
-            tr[0] += h * U[3 * c];
-            tr[1] += h * U[3 * c + 1];
-            tr[2] += h * U[3 * c + 2];
-          }
-          const T wu0 = w * U[3 * r], wu1 = w * U[3 * r + 1], wu2 = w * U[3 * r + 2];
-          Ht[0] += wu0 * tr[0];
-          Ht[1] += wu0 * tr[1];
-          Ht[2] += wu0 * tr[2];
-          Ht[3] += wu1 * tr[1];
-          Ht[4] += wu1 * tr[2];
-          Ht[5] += wu2 * tr[2];
-          const T gr = __ldg(Gp + r);
-          gt[0] += wu0 * gr;
-          gt[1] += wu1 * gr;
-          gt[2] += wu2 * gr;
-        }
-      }
-      // back to world: H~ = R H~' R^T, g~ = R g~'
-      T Hf[9] = {Ht[0], Ht[1], Ht[2], Ht[1], Ht[3], Ht[4], Ht[2], Ht[4], Ht[5]};
-      T RH[9];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-          RH[3 * a + b] = R[3 * a] * Hf[b] + R[3 * a + 1] * Hf[3 + b] + R[3 * a + 2] * Hf[6 + b];
-      T Hw[9];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-          Hw[3 * a + b] = RH[3 * a] * R[3 * b] + RH[3 * a + 1] * R[3 * b + 1] + RH[3 * a + 2] * R[3 * b + 2];
-      A[0] += Hw[0];
-      A[1] += T(0.5) * (Hw[1] + Hw[3]);
-      A[2] += T(0.5) * (Hw[2] + Hw[6]);
-      A[3] += Hw[4];
-      A[4] += T(0.5) * (Hw[5] + Hw[7]);
-      A[5] += Hw[8];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) rhs[a] -= R[3 * a] * gt[0] + R[3 * a + 1] * gt[1] + R[3 * a + 2] * gt[2];
-    }
-    // uncorrected per-vertex Newton direction (H_ii is SPD for this material)
     T dj[3];
     {
       T rg[3] = {-g[0], -g[1], -g[2]};
       if (!chol3_solve(H, rg, dj)) dj[0] = dj[1] = dj[2] = T(0);
     }
+    Vec4<T> djv{dj[0], dj[1], dj[2], T(0)};
+    m.DJ[i] = djv;
+    if (CORR) {
+      T R[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Fs[q] /= W;
+      polar_rotation(Fs, R);
+      T* o = m.ghr + i;
+      const size_t S = m.Vf;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) o[q * S] = g[q];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) o[(3 + q) * S] = H[q];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) o[(9 + q) * S] = R[q];
+    } else {
+      m.D[i] = djv;
+    }
+    acc[0] = double(g[0]) * double(g[0]) + double(g[1]) * double(g[1]) + double(g[2]) * double(g[2]);
+    acc[1] = double(g[0]) * double(dj[0]) + double(g[1]) * double(dj[1]) + double(g[2]) * double(dj[2]);
+  }
+  block_sum<2>(acc, red);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = acc[0];
+    partial[gridDim.x + blockIdx.x] = acc[1];
+  }
+  if (CORR) return;
+  if (!last_block(&st->ticket_main)) return;
+  const double r2 = block_sum_array(partial, gridDim.x, 1, red);
+  const double gdj = block_sum_array(partial + gridDim.x, gridDim.x, 1, red);
+  if (threadIdx.x == 0) finalize_sweep(st, k, r2, gdj, gdj, trace, record);
+}
+
+// Sweep phase 2, thread per free vertex: the cubature sums H~_i, g~_i (Eq. cubature) from
+// the rotated pool element data, the 3x3 solve of Eq. reduced_local, D_i, and g.D. The
+// last block closes the sweep's reduction with phase 1's partial sums.
+template <typename T>
+__global__ void __launch_bounds__(128) k_correct(DevMesh<T> m, StepState* st, int k,
+                                                 double* __restrict__ partial /* [3][grid] */,
+                                                 double* __restrict__ trace, int record) {
+  if (st->done) return;
+  __shared__ double red[96];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  int fb = 0;
+  if (i < m.Vf) {
+    const T* o = m.ghr + i;
+    const size_t S = m.Vf;
+    T g[3], H[6], R[9];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) g[q] = o[q * S];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) H[q] = o[(3 + q) * S];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) R[q] = o[(9 + q) * S];
+    T Ht[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, gt[3] = {T(0), T(0), T(0)};
+    for (int s = 0; s < m.n_cub; ++s) {
+      const int p = m.cub_p[(size_t)s * m.Vf + i];
+      if (p < 0) continue;
+      const T w = m.cub_w[(size_t)s * m.Vf + i];
+      T U[36];
+      const T* up = m.cub_u + (size_t)s * 36 * m.Vf + i;
+#pragma unroll
+      for (int q = 0; q < 36; ++q) U[q] = up[(size_t)q * m.Vf];
+      const T* Hp = m.pool_H + (size_t)p * kPackedH;
+      const T* Gp = m.pool_G + (size_t)p * 12;
+#pragma unroll
+      for (int r = 0; r < 12; ++r) {
+        T tr[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          const T h = __ldg(Hp + pk(r, c));
+          tr[0] += h * U[3 * c];
+          tr[1] += h * U[3 * c + 1];
+          tr[2] += h * U[3 * c + 2];
+        }
+        const T wu0 = w * U[3 * r], wu1 = w * U[3 * r + 1], wu2 = w * U[3 * r + 2];
+        Ht[0] += wu0 * tr[0];
+        Ht[1] += wu0 * tr[1];
+        Ht[2] += wu0 * tr[2];
+        Ht[3] += wu1 * tr[1];
+        Ht[4] += wu1 * tr[2];
+        Ht[5] += wu2 * tr[2];
+        const T gr = __ldg(Gp + r);
+        gt[0] += wu0 * gr;
+        gt[1] += wu1 * gr;
+        gt[2] += wu2 * gr;
+      }
+    }
+    // back to world: H~ = R H~' R^T, g~ = R g~'
+    T Hf[9] = {Ht[0], Ht[1], Ht[2], Ht[1], Ht[3], Ht[4], Ht[2], Ht[4], Ht[5]};
+    T RH[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        RH[3 * a + b] = R[3 * a] * Hf[b] + R[3 * a + 1] * Hf[3 + b] + R[3 * a + 2] * Hf[6 + b];
+    T Hw[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        Hw[3 * a + b] = RH[3 * a] * R[3 * b] + RH[3 * a + 1] * R[3 * b + 1] + RH[3 * a + 2] * R[3 * b + 2];
+    T A[6] = {H[0] + Hw[0], H[1] + T(0.5) * (Hw[1] + Hw[3]), H[2] + T(0.5) * (Hw[2] + Hw[6]),
+              H[3] + Hw[4], H[4] + T(0.5) * (Hw[5] + Hw[7]), H[5] + Hw[8]};
+    T rhs[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rhs[a] = -g[a] - (R[3 * a] * gt[0] + R[3 * a + 1] * gt[1] + R[3 * a + 2] * gt[2]);
     T d[3];
-    if (!CORR) {
-      d[0] = dj[0];
-      d[1] = dj[1];
-      d[2] = dj[2];
-    } else if (!chol3_solve(A, rhs, d)) {
+    if (!chol3_solve(A, rhs, d)) {
       // reading R7: the vertex takes the uncorrected step
-      d[0] = dj[0];
-      d[1] = dj[1];
-      d[2] = dj[2];
+      load3(m.DJ, i, d);
       fb = 1;
     }
     Vec4<T> dv{d[0], d[1], d[2], T(0)};
     m.D[i] = dv;
-    Vec4<T> djv{dj[0], dj[1], dj[2], T(0)};
-    m.DJ[i] = djv;
-    acc[0] = double(g[0]) * double(g[0]) + double(g[1]) * double(g[1]) + double(g[2]) * double(g[2]);
-    acc[1] = double(g[0]) * double(d[0]) + double(g[1]) * double(d[1]) + double(g[2]) * double(d[2]);
-    acc[2] = double(g[0]) * double(dj[0]) + double(g[1]) * double(dj[1]) + double(g[2]) * double(dj[2]);
+    acc[0] = double(g[0]) * double(d[0]) + double(g[1]) * double(d[1]) + double(g[2]) * double(d[2]);
   }
   if (__syncthreads_or(fb)) {
     const int nfb = __syncthreads_count(fb);
     if (threadIdx.x == 0) atomicAdd(&st->fallback, nfb);
   }
-  block_sum<3>(acc, red);
-  if (threadIdx.x == 0) {
-    partial[blockIdx.x] = acc[0];
-    partial[gridDim.x + blockIdx.x] = acc[1];
-    partial[2 * gridDim.x + blockIdx.x] = acc[2];
-  }
+  block_sum<1>(acc, red);
+  if (threadIdx.x == 0) partial[2 * gridDim.x + blockIdx.x] = acc[0];
   if (!last_block(&st->ticket_main)) return;
   const double r2 = block_sum_array(partial, gridDim.x, 1, red);
-  const double gd = block_sum_array(partial + gridDim.x, gridDim.x, 1, red);
-  const double gdj = block_sum_array(partial + 2 * gridDim.x, gridDim.x, 1, red);
-  if (threadIdx.x == 0) {
-    st->ticket_main = 0;
-    const double gn = sqrt(r2);
-    if (k == 0) st->g0 = gn;
-    const double g0 = st->g0;
-    const double r = g0 > 0.0 ? gn / g0 : 0.0;
-    st->r = r;
-    st->slope = gd;
-    st->slope_j = gdj;
-    st->alpha = 1.0;
-    st->dir = 0;
-    if (record && k < 4096) trace[k] = r;
-    if (!isfinite(r) || !isfinite(gd)) {
-      st->status = 6;  // JGS2_EDIVERGED
-      st->done = 1;
-      st->sweeps = k;
-    } else if (r <= st->rel_tol || g0 == 0.0) {
-      st->converged = 1;
-      st->done = 1;
-      st->sweeps = k;
-    } else if (k >= st->max_sweeps) {
-      st->done = 1;
-      st->sweeps = k;
-    }
-  }
+  const double gdj = block_sum_array(partial + gridDim.x, gridDim.x, 1, red);
+  const double gd = block_sum_array(partial + 2 * gridDim.x, gridDim.x, 1, red);
+  if (threadIdx.x == 0) finalize_sweep(st, k, r2, gd, gdj, trace, record);
 }
 
 // Exact energy change of a tet for the displacement increment alpha*d (no cancellation):
