@@ -172,6 +172,27 @@ jgs2_status jgs2_sweeps(jgs2_mesh* mesh, const double* x_t, const double* v_t, d
 jgs2_status jgs2_energy_gradient(jgs2_mesh* mesh, const double* x_t, const double* v_t,
                                  const double* x, double* energy, double* g, void* stream);
 
+/* Allocation-free variant of jgs2_energy_gradient (the paper has no counterpart; this is a
+ * service for callers that cannot allocate device memory while they run, such as a
+ * real-time loop that must not wait on cudaMalloc, or a process whose device memory is
+ * owned by a pooling allocator). It computes the same E(x) and g(x) but keeps the
+ * reduction's partial sums in a file-scope device array of JGS2_STATIC_PARTIALS_MAX + 1
+ * doubles (512 KB, held by every GPU that loads the library until exit) and calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *  - Limit: (n_tets + free vertices) / 128 (rounded up each) <= JGS2_STATIC_PARTIALS_MAX,
+ *    else JGS2_EINVAL with a message.
+ *  - The mesh's own device buffers must already exist: make one FP64 jgs2_step,
+ *    jgs2_sweeps or jgs2_energy_gradient call on the mesh first (else JGS2_EINVAL).
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call shares the array; calls that overlap on the GPU race. Each call writes
+ *    every slot it reads, so the array needs no clearing.
+ *  - x_t, v_t, x, g: device [V][3] double, caller order (g may be NULL); energy: host
+ *    pointer (may be NULL, not both). Synchronises the stream before returning. */
+#define JGS2_STATIC_PARTIALS_MAX 65536
+jgs2_status jgs2_energy_gradient_static(jgs2_mesh* mesh, const double* x_t, const double* v_t,
+                                        const double* x, double* energy, double* g, void* stream);
+
 void jgs2_mesh_destroy(jgs2_mesh* mesh);
 const char* jgs2_last_error(void);
 

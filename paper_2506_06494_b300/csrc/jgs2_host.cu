@@ -360,6 +360,12 @@ static DevMesh<T> dev_view(Mesh* m) {
   return d;
 }
 
+bool dev_view_f64_if_ready(Mesh* m, DevMesh<double>* out) {
+  if (!m || !m->device_ready || !m->f64.ready) return false;
+  *out = dev_view<double>(m);
+  return true;
+}
+
 // ------------------------------------------------------------------ cubature records
 
 jgs2_status set_cubature(Mesh* m, int n_cub, const std::vector<int>& elem_int /* [Vf][nc] internal tet, -1 */,

@@ -62,6 +62,8 @@ struct Mesh {
 
 jgs2_status fail(jgs2_status s, const std::string& msg);
 jgs2_status precompute(Mesh* m, const jgs2_precompute_opts* o);
+// FP64 device view if the mesh's device buffers already exist (never allocates).
+bool dev_view_f64_if_ready(Mesh* m, DevMesh<double>* out);
 jgs2_status set_cubature(Mesh* m, int n_cub, const std::vector<int>& elem_int, const std::vector<double>& w,
                          const std::vector<double>& u);
 
