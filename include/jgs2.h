@@ -57,6 +57,14 @@ typedef struct {
   const uint8_t* pinned;     /* [V] 1 = vertex held at its position x_t (not a DOF); may be NULL */
   double gravity[3];         /* f_ext / m (m/s^2) */
   double dt;                 /* time step h (s) > 0 */
+  /* IPC contact (Sec. 7, Eq. barrier). contact = 0 disables it; the other fields are
+   * then ignored. Pairs: surface vertex - boundary face, boundary edge - boundary edge
+   * (self-contact included) and surface vertex - wall plane n.x >= c. */
+  int32_t contact;
+  int32_t n_planes;          /* walls */
+  const double* planes;      /* [n_planes][4]: unit normal n (3) and offset c; may be NULL if 0 */
+  double dhat;               /* barrier support d^ (m) > 0 */
+  double kappa;              /* barrier stiffness (N/m) > 0 */
 } jgs2_mesh_desc;
 
 typedef struct jgs2_mesh jgs2_mesh; /* opaque, library-owned */
@@ -101,10 +109,11 @@ typedef struct {
 #define JGS2_TRACE_MAX 4096
 /* kernel kinds in jgs2_step_report.kernel_*: pool (cubature elements), gather (per-vertex
  * gradient, diagonal block, rotation), correct (cubature correction + 3x3 solve), energy
- * (line search), update, setup (per-step setup and write-back) */
-#define JGS2_NKERNELS 6
+ * (line search), update, setup (per-step setup and write-back), contact (broadphase, narrowphase
+ * and barrier terms, several launches counted as one pass) */
+#define JGS2_NKERNELS 7
 enum { JGS2_K_POOL = 0, JGS2_K_GATHER = 1, JGS2_K_CORRECT = 2, JGS2_K_ENERGY = 3, JGS2_K_UPDATE = 4,
-       JGS2_K_SETUP = 5 };
+       JGS2_K_SETUP = 5, JGS2_K_CONTACT = 6 };
 
 typedef struct {
   int32_t sweeps;            /* sweeps applied in the step */
@@ -192,6 +201,16 @@ jgs2_status jgs2_energy_gradient(jgs2_mesh* mesh, const double* x_t, const doubl
 #define JGS2_STATIC_PARTIALS_MAX 65536
 jgs2_status jgs2_energy_gradient_static(jgs2_mesh* mesh, const double* x_t, const double* v_t,
                                         const double* x, double* energy, double* g, void* stream);
+
+/* Candidate contact pairs with distance < radius at positions x (device [V][3] double,
+ * caller order; x_t likewise), in a canonical order for comparison with independent
+ * implementations: rows of 5 int32 (kind, a, b, c, d) in caller vertex ids -
+ * kind 0 vertex-wall (v, plane, -1, -1), kind 1 vertex-face (v, face vertices ascending),
+ * kind 2 edge-edge (edge 1 ascending, edge 2 ascending; edge 1 < edge 2). out: host
+ * [cap][5]; *n_out receives the pair count (rows beyond cap are not written; JGS2_ENOMEM
+ * if the count exceeds cap). Requires contact = 1. Synchronises the stream. */
+jgs2_status jgs2_contact_pairs(jgs2_mesh* mesh, const double* x_t, const double* x, double radius,
+                               int32_t* out, int32_t cap, int32_t* n_out, void* stream);
 
 void jgs2_mesh_destroy(jgs2_mesh* mesh);
 const char* jgs2_last_error(void);

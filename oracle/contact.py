@@ -1,0 +1,257 @@
+"""IPC contact for the oracle (Sec. 7, Eq. barrier), FP64, brute force.
+
+Barrier per primitive pair l (Eq. barrier): B(d) = -(d - dhat)^2 log(d / dhat) for
+0 < d < dhat, else 0; the energy adds kappa * sum_l B(d_l) (reading R11: kappa is a
+parameter, d the unsquared Euclidean distance). Pairs (reading R11): surface vertex -
+boundary triangle not containing it (VF), boundary edges sharing no vertex (EE), and
+vertex - wall plane n.x >= c (VW). Self-contact is included.
+
+Per-vertex terms (reading R12/R19): the barrier enters the vertex gradient exactly
+(dB/dx_k = kappa B'(d) dd/dx_k, where by the envelope theorem dd/dx_k = +/- w_k n with the
+closest-point weights w_k and unit normal n) and the diagonal block through its
+Gauss-Newton part kappa B''(d) (dd/dx_k)(dd/dx_k)^T (B'' > 0 on (0, dhat), so PSD).
+
+Step truncation (reading R11): a surface vertex's step is scaled so that
+|delta_v| <= 0.45 min(r_c - dhat, d_min,v), d_min,v = the smallest distance of a pair within
+the candidate radius r_c that involves v. No candidate pair's distance can shrink by 90% or
+more within one sweep, and no pair outside r_c can come within dhat, so the candidate list
+at x^k holds every barrier term along the sweep's line-search segment.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# ------------------------------------------------------------------ barrier
+
+
+def barrier(d, dhat):
+    d = np.asarray(d, dtype=np.float64)
+    out = np.zeros_like(d)
+    m = (d > 0) & (d < dhat)
+    out[m] = -(d[m] - dhat) ** 2 * np.log(d[m] / dhat)
+    out[d <= 0] = np.inf
+    return out
+
+
+def barrier_d1(d, dhat):
+    d = np.asarray(d, dtype=np.float64)
+    out = np.zeros_like(d)
+    m = (d > 0) & (d < dhat)
+    e = d[m] - dhat
+    out[m] = -2.0 * e * np.log(d[m] / dhat) - e * e / d[m]
+    return out
+
+
+def barrier_d2(d, dhat):
+    d = np.asarray(d, dtype=np.float64)
+    out = np.zeros_like(d)
+    m = (d > 0) & (d < dhat)
+    e = d[m] - dhat
+    out[m] = -2.0 * np.log(d[m] / dhat) - 4.0 * e / d[m] + e * e / (d[m] * d[m])
+    return out
+
+
+# ------------------------------------------------------------------ closest points
+
+
+def point_segment(p, a, b):
+    """Closest point of segment ab to p: (distance, t) with q = a + t (b - a)."""
+    ab = b - a
+    L2 = float(ab @ ab)
+    t = 0.0 if L2 == 0.0 else float(np.clip((p - a) @ ab / L2, 0.0, 1.0))
+    return float(np.linalg.norm(p - (a + t * ab))), t
+
+
+def point_triangle(p, a, b, c):
+    """Closest point of triangle abc to p by its definition: the interior projection if its
+    barycentric coordinates are non-negative, else the nearest of the three edges.
+    Returns (distance, weights (wa, wb, wc))."""
+    n = np.cross(b - a, c - a)
+    nn = float(n @ n)
+    if nn > 0.0:
+        q = p - (p - a) @ n / nn * n
+        # barycentric coordinates of q
+        v0, v1, v2 = b - a, c - a, q - a
+        d00, d01, d11 = v0 @ v0, v0 @ v1, v1 @ v1
+        d20, d21 = v2 @ v0, v2 @ v1
+        den = d00 * d11 - d01 * d01
+        wb = (d11 * d20 - d01 * d21) / den
+        wc = (d00 * d21 - d01 * d20) / den
+        wa = 1.0 - wb - wc
+        if wa >= 0 and wb >= 0 and wc >= 0:
+            return float(np.linalg.norm(p - q)), (wa, wb, wc)
+    best = None
+    for (u, v, iu, iv) in ((a, b, 0, 1), (b, c, 1, 2), (c, a, 2, 0)):
+        d, t = point_segment(p, u, v)
+        if best is None or d < best[0]:
+            w = [0.0, 0.0, 0.0]
+            w[iu] = 1.0 - t
+            w[iv] = t
+            best = (d, tuple(w))
+    return best
+
+
+def segment_segment(p0, p1, q0, q1):
+    """Closest points of segments p0p1 and q0q1 by definition: the interior critical point
+    of |p(s) - q(t)|^2 if it lies in [0,1]^2, else the best of the four point-segment
+    distances on the boundary. Returns (distance, s, t)."""
+    d1, d2, r = p1 - p0, q1 - q0, p0 - q0
+    a, e, b = d1 @ d1, d2 @ d2, d1 @ d2
+    c, f = d1 @ r, d2 @ r
+    den = a * e - b * b
+    cands = []
+    if den > 1e-14 * a * e and a > 0 and e > 0:
+        s = (b * f - c * e) / den
+        t = (a * f - b * c) / den
+        if 0 <= s <= 1 and 0 <= t <= 1:
+            cands.append((float(np.linalg.norm(p0 + s * d1 - q0 - t * d2)), float(s), float(t)))
+    for s in (0.0, 1.0):
+        d, t = point_segment(p0 + s * d1, q0, q1)
+        cands.append((d, s, t))
+    for t in (0.0, 1.0):
+        d, s = point_segment(q0 + t * d2, p0, p1)
+        cands.append((d, s, t))
+    return min(cands, key=lambda z: z[0])
+
+
+# ------------------------------------------------------------------ surface and pairs
+
+
+def surface(tets, X):
+    """Boundary faces (used by exactly one tet, oriented outward), their edges, vertices."""
+    faces = {}
+    for t in np.asarray(tets):
+        for k in range(4):
+            f = tuple(int(q) for q in np.delete(t, k))
+            key = tuple(sorted(f))
+            faces.setdefault(key, []).append((f, int(t[k])))
+    bf = []
+    for key, lst in faces.items():
+        if len(lst) != 1:
+            continue
+        (a, b, c), opp = lst[0]
+        n = np.cross(X[b] - X[a], X[c] - X[a])
+        if n @ (X[opp] - X[a]) > 0:
+            b, c = c, b
+        bf.append((a, b, c))
+    bf = np.array(sorted(bf, key=lambda f: tuple(sorted(f))), dtype=np.int64).reshape(-1, 3)
+    edges = set()
+    for a, b, c in bf:
+        for u, v in ((a, b), (b, c), (c, a)):
+            edges.add((min(u, v), max(u, v)))
+    be = np.array(sorted(edges), dtype=np.int64).reshape(-1, 2)
+    sv = np.unique(bf.ravel()) if len(bf) else np.zeros(0, np.int64)
+    return bf, be, sv
+
+
+class Contact:
+    def __init__(self, tets, X, planes, dhat, kappa, pinned=None):
+        self.faces, self.edges, self.sverts = surface(tets, X)
+        self.planes = np.asarray(planes, dtype=np.float64).reshape(-1, 4)
+        self.dhat = float(dhat)
+        self.kappa = float(kappa)
+        self.pinned = None if pinned is None else np.asarray(pinned).astype(bool)
+
+    def canonical(self, pairs):
+        """Rows (kind, a, b, c, d) in vertex ids: VW (0, v, plane, -1, -1), VF (1, v, face
+        vertices ascending), EE (2, edge 1, edge 2; each ascending, edge 1 < edge 2)."""
+        rows = []
+        for typ, a, b, _ in pairs:
+            if typ == 0:
+                rows.append((0, a, b, -1, -1))
+            elif typ == 1:
+                rows.append((1, a, *sorted(int(q) for q in self.faces[b])))
+            else:
+                e1 = tuple(sorted(int(q) for q in self.edges[a]))
+                e2 = tuple(sorted(int(q) for q in self.edges[b]))
+                rows.append((2, *min(e1, e2), *max(e1, e2)))
+        return sorted(rows)
+
+    def pairs(self, x, radius):
+        """Every pair with distance < radius, sorted by (type, a, b): type 0 = VW
+        (vertex, plane), 1 = VF (vertex, face index), 2 = EE (edge i < edge j).
+        All pairs are enumerated; an axis-aligned box distance (a lower bound of the
+        distance) skips the exact closest-point test where it already exceeds the radius."""
+        out = []
+        sv = self.sverts
+        for k, pl in enumerate(self.planes):
+            d = x[sv] @ pl[:3] - pl[3]
+            for v, dv in zip(sv[d < radius], d[d < radius]):
+                out.append((0, int(v), k, float(dv)))
+        F, E = self.faces, self.edges
+        if len(F):
+            flo, fhi = x[F].min(axis=1), x[F].max(axis=1)
+            p = x[sv]
+            gap = np.maximum(np.maximum(flo[None] - p[:, None], p[:, None] - fhi[None]), 0.0)
+            vi, fi = np.nonzero(np.linalg.norm(gap, axis=2) < radius)
+            for a, b in zip(vi, fi):
+                v = int(sv[a])
+                f = F[b]
+                if v in f:
+                    continue
+                d, _ = point_triangle(x[v], x[f[0]], x[f[1]], x[f[2]])
+                if d < radius:
+                    out.append((1, v, int(b), d))
+        if len(E):
+            elo, ehi = x[E].min(axis=1), x[E].max(axis=1)
+            gap = np.maximum(np.maximum(elo[None] - ehi[:, None], elo[:, None] - ehi[None]), 0.0)
+            ii, jj = np.nonzero(np.linalg.norm(gap, axis=2) < radius)
+            for i, j in zip(ii, jj):
+                if j <= i or len({*E[i], *E[j]}) < 4:
+                    continue
+                d, _, _ = segment_segment(x[E[i][0]], x[E[i][1]], x[E[j][0]], x[E[j][1]])
+                if d < radius:
+                    out.append((2, int(i), int(j), d))
+        out.sort(key=lambda z: z[:3])
+        return out
+
+    def pair_geometry(self, x, pr):
+        """(distance, [(vertex, dd/dx_vertex)]) of one pair at positions x."""
+        typ, a, b = pr[:3]
+        if typ == 0:
+            pl = self.planes[b]
+            return float(pl[:3] @ x[a] - pl[3]), [(a, pl[:3].copy())]
+        if typ == 1:
+            f = self.faces[b]
+            d, w = point_triangle(x[a], x[f[0]], x[f[1]], x[f[2]])
+            q = w[0] * x[f[0]] + w[1] * x[f[1]] + w[2] * x[f[2]]
+            n = (x[a] - q) / d if d > 0 else np.zeros(3)
+            return d, [(a, n), (f[0], -w[0] * n), (f[1], -w[1] * n), (f[2], -w[2] * n)]
+        e1, e2 = self.edges[a], self.edges[b]
+        d, s, t = segment_segment(x[e1[0]], x[e1[1]], x[e2[0]], x[e2[1]])
+        p = x[e1[0]] + s * (x[e1[1]] - x[e1[0]])
+        q = x[e2[0]] + t * (x[e2[1]] - x[e2[0]])
+        n = (p - q) / d if d > 0 else np.zeros(3)
+        return d, [(e1[0], (1 - s) * n), (e1[1], s * n), (e2[0], -(1 - t) * n), (e2[1], -t * n)]
+
+    def energy(self, x, pairs):
+        e = 0.0
+        for pr in pairs:
+            d, _ = self.pair_geometry(x, pr)
+            e += self.kappa * float(barrier(np.array([d]), self.dhat)[0])
+        return e
+
+    def vertex_terms(self, x, pairs, V):
+        """Barrier gradient (V,3) and Gauss-Newton diagonal blocks (V,3,3)."""
+        g = np.zeros((V, 3))
+        H = np.zeros((V, 3, 3))
+        for pr in pairs:
+            d, J = self.pair_geometry(x, pr)
+            if not (0 < d < self.dhat):
+                continue
+            b1 = self.kappa * float(barrier_d1(np.array([d]), self.dhat)[0])
+            b2 = self.kappa * float(barrier_d2(np.array([d]), self.dhat)[0])
+            for v, jv in J:
+                g[v] += b1 * jv
+                H[v] += b2 * np.outer(jv, jv)
+        return g, H
+
+    def step_limits(self, x, pairs, radius, V):
+        """0.45 min(radius - dhat, d_min,v) for surface vertices, inf elsewhere."""
+        lim = np.full(V, np.inf)
+        lim[self.sverts] = radius - self.dhat
+        for pr in pairs:
+            d, J = self.pair_geometry(x, pr)
+            for v, _ in J:
+                lim[v] = min(lim[v], d)
+        return 0.45 * lim

@@ -129,6 +129,14 @@ class Mesh:
         self.body_of_vertex = np.array([first[int(r)] for r in roots], dtype=np.int64)
         self.n_bodies = len(first)
         self.body_of_tet = self.body_of_vertex[self.tets[:, 0]] if T else np.zeros(0, int)
+        self.contact = None   # oracle.contact.Contact when the IPC barrier is on (Sec. 7)
+        self.rc = 0.0         # candidate radius of the step truncation
+
+    def enable_contact(self, planes, dhat, kappa, rc=None):
+        from . import contact
+        self.contact = contact.Contact(self.tets, self.X, planes, dhat, kappa, self.pinned)
+        self.rc = 2.0 * dhat if rc is None else float(rc)
+        return self
 
     @property
     def V(self):
@@ -167,7 +175,10 @@ def energy(mesh: Mesh, x, z, h):
     F = deformation_gradient(mesh, x)
     el = float(np.sum(mesh.vol * snh_psi(F, mesh.mu, mesh.lp)))
     d = (x - z)[mesh.free]
-    return el + float(np.sum(0.5 * mesh.mass[mesh.free] / h ** 2 * np.sum(d * d, axis=1)))
+    e = el + float(np.sum(0.5 * mesh.mass[mesh.free] / h ** 2 * np.sum(d * d, axis=1)))
+    if mesh.contact is not None:
+        e += mesh.contact.energy(x, mesh.contact.pairs(x, mesh.contact.dhat))
+    return e
 
 
 def vertex_gradient(mesh: Mesh, x, z, h):
@@ -178,6 +189,9 @@ def vertex_gradient(mesh: Mesh, x, z, h):
     g = np.zeros_like(x)
     np.add.at(g, mesh.tets.ravel(), ge.reshape(-1, 3))
     g += mesh.mass[:, None] / h ** 2 * (x - z)
+    if mesh.contact is not None:
+        gb, _ = mesh.contact.vertex_terms(x, mesh.contact.pairs(x, mesh.contact.dhat), mesh.V)
+        g += gb
     g[mesh.pinned] = 0.0
     return g
 
@@ -208,6 +222,9 @@ def vertex_diag_blocks(mesh: Mesh, x, h):
     for a in range(4):
         np.add.at(Hd, mesh.tets[:, a], He[:, 3 * a:3 * a + 3, 3 * a:3 * a + 3])
     Hd += (mesh.mass / h ** 2)[:, None, None] * np.eye(3)[None]
+    if mesh.contact is not None:
+        _, Hb = mesh.contact.vertex_terms(x, mesh.contact.pairs(x, mesh.contact.dhat), mesh.V)
+        Hd += Hb
     return Hd
 
 

@@ -117,6 +117,14 @@ def direction(mesh: fem.Mesh, x, z, h, cub=None, psd=False, grad="asm", stats=No
             D[i] = DJ[i]
             if stats is not None:
                 stats.fallback += 1
+    if mesh.contact is not None:
+        # step truncation (reading R11): |delta_v| <= 0.45 min(r_c, d_min,v)
+        cand = mesh.contact.pairs(x, mesh.rc)
+        lim = mesh.contact.step_limits(x, cand, mesh.rc, mesh.V)
+        for arr in (D, DJ):
+            nrm = np.linalg.norm(arr, axis=1)
+            sc = np.where(nrm > lim, lim / np.maximum(nrm, 1e-300), 1.0)
+            arr *= sc[:, None]
     return D, DJ, g
 
 
@@ -137,9 +145,15 @@ def line_search(mesh: fem.Mesh, x, z, h, D, DJ, g, stats=None):
     fem.energy_change, free of cancellation). If none passes the sweep does not move
     (counted). Returns the step a*d."""
     alphas = [1.0 / (1 << j) for j in range(LS_TRIALS)]
+    cand = mesh.contact.pairs(x, mesh.rc) if mesh.contact is not None else None
     for d in (D, DJ):
         slope = float(np.sum(g * d))
         dE = fem.energy_change(mesh, x, z, h, d, alphas)
+        if cand is not None:
+            # barrier change over the candidate pairs (truncation keeps every other pair
+            # outside dhat along the whole trial segment)
+            B0 = mesh.contact.energy(x, cand)
+            dE = [de + mesh.contact.energy(x + a * d, cand) - B0 for a, de in zip(alphas, dE)]
         for a, de in zip(alphas, dE):
             if de <= ARMIJO_C * a * slope:
                 return a * d

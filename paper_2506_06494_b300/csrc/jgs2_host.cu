@@ -7,8 +7,12 @@
 #include <cstring>
 #include <memory>
 #include <numeric>
+#include <set>
 #include <string>
 #include <vector>
+
+#include <cub/device/device_radix_sort.cuh>
+#include <map>
 
 #include "../../include/jgs2.h"
 #include "jgs2_host.h"
@@ -55,6 +59,12 @@ Mesh::~Mesh() {
   cudaFree(d_trace); cudaFree(d_xbuf); cudaFree(d_vbuf);
   if (h_state) cudaFreeHost(h_state);
   for (cudaEvent_t e : events) cudaEventDestroy(e);
+  cudaFree(d_planes); cudaFree(d_d0); cudaFree(d_bg); cudaFree(d_bH); cudaFree(d_faces); cudaFree(d_edges);
+  cudaFree(d_sverts); cudaFree(d_npairs); cudaFree(d_cflags); cudaFree(d_is_surf); cudaFree(d_pairs);
+  cudaFree(d_dmin); cudaFree(d_lim); cudaFree(d_cub);
+  for (int q = 0; q < 2; ++q) {
+    cudaFree(d_fids[q]); cudaFree(d_eids[q]); cudaFree(d_fkeys[q]); cudaFree(d_ekeys[q]);
+  }
 }
 
 static uint64_t spread3(uint64_t x) {
@@ -217,6 +227,75 @@ jgs2_status mesh_create(const jgs2_mesh_desc* d, Mesh** out) {
     }
     m->n_bodies = nb;
   }
+  // contact surface (Sec. 7): boundary faces (used by one tet) oriented outward, their
+  // edges and vertices, in internal vertex ids
+  if (d->contact) {
+    if (!(d->dhat > 0.0) || !(d->kappa > 0.0) || d->n_planes < 0 || (d->n_planes > 0 && !d->planes))
+      return fail(JGS2_EINVAL, "contact needs dhat > 0, kappa > 0 and n_planes planes");
+    m->contact = 1;
+    m->dhat = d->dhat;
+    m->kappa = d->kappa;
+    m->rc = 2.0 * d->dhat;
+    m->planes.assign(d->planes, d->planes + 4 * (size_t)d->n_planes);
+    std::map<std::array<int, 3>, std::pair<std::array<int, 3>, int>> fc;
+    std::map<std::array<int, 3>, int> count;
+    for (int t = 0; t < T; ++t) {
+      const int* tv = &m->tets_c[4 * (size_t)t];
+      for (int k = 0; k < 4; ++k) {
+        std::array<int, 3> f;
+        int q = 0;
+        for (int a = 0; a < 4; ++a)
+          if (a != k) f[q++] = tv[a];
+        std::array<int, 3> key = f;
+        std::sort(key.begin(), key.end());
+        if (++count[key] == 1) fc[key] = {f, tv[k]};
+      }
+    }
+    std::set<std::pair<int, int>> es;
+    std::vector<uint8_t> surf(V, 0);
+    double rmax = 0.0;
+    for (auto& kv : count) {
+      if (kv.second != 1) continue;
+      auto f = fc[kv.first].first;
+      const int opp = fc[kv.first].second;
+      const double* a = &m->X[3 * f[0]];
+      const double* b = &m->X[3 * f[1]];
+      const double* c = &m->X[3 * f[2]];
+      const double* o = &m->X[3 * opp];
+      const double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, w[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+      const double n[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+      if (n[0] * (o[0] - a[0]) + n[1] * (o[1] - a[1]) + n[2] * (o[2] - a[2]) > 0) std::swap(f[1], f[2]);
+      double cen[3];
+      for (int q = 0; q < 3; ++q) cen[q] = (a[q] + b[q] + c[q]) / 3.0;
+      for (int r = 0; r < 3; ++r) {
+        const double* pr = &m->X[3 * f[r]];
+        rmax = std::max(rmax, std::sqrt((pr[0] - cen[0]) * (pr[0] - cen[0]) + (pr[1] - cen[1]) * (pr[1] - cen[1]) +
+                                        (pr[2] - cen[2]) * (pr[2] - cen[2])));
+        const int x0 = f[r], x1 = f[(r + 1) % 3];
+        es.insert({std::min(x0, x1), std::max(x0, x1)});
+        surf[f[r]] = 1;
+      }
+      for (int r = 0; r < 3; ++r) m->sfaces.push_back(m->iperm[f[r]]);
+    }
+    for (auto& e : es) {
+      m->sedges.push_back(m->iperm[e.first]);
+      m->sedges.push_back(m->iperm[e.second]);
+      const double* a = &m->X[3 * e.first];
+      const double* b = &m->X[3 * e.second];
+      rmax = std::max(rmax, std::sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) +
+                                      (a[2] - b[2]) * (a[2] - b[2])));
+    }
+    m->is_surf.assign(V, 0);
+    for (int v = 0; v < V; ++v)
+      if (surf[v]) {
+        m->sverts.push_back(m->iperm[v]);
+        m->is_surf[m->iperm[v]] = 1;
+      }
+    // grid cell: a primitive within rc of a point has its centroid within rc + rmax of it;
+    // twice the rest size leaves room for deformation
+    m->cell = m->rc + 2.0 * rmax;
+    m->pair_cap = std::max<int>(1 << 16, 8 * (int)m->sverts.size() + 16 * d->n_planes);
+  }
   *out = m.release();
   return JGS2_OK;
 }
@@ -243,7 +322,7 @@ static jgs2_status ensure_device(Mesh* m) {
     CK(dalloc(&m->d_perm, V));
     CK(dalloc(&m->d_state, 1));
     CK(dalloc(&m->d_trace, JGS2_TRACE_MAX));
-    const size_t np = std::max<size_t>(2 * kLsTrials * ((size_t)(T + 127) / 128 + (m->Vf + 127) / 128 + 1), 16);
+    const size_t np = std::max<size_t>(4 * kLsTrials * ((size_t)(T + 127) / 128 + (m->Vf + 127) / 128 + 1), 16);
     CK(dalloc(&m->d_partial, np));
     CK(cudaMallocHost((void**)&m->h_state, sizeof(StepState)));
     CK(cudaMemcpy(m->d_inc_off, m->inc_off.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
@@ -251,6 +330,42 @@ static jgs2_status ensure_device(Mesh* m) {
     if (!m->inc.empty()) CK(cudaMemcpy(m->d_inc, m->inc.data(), sizeof(int) * m->inc.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(m->d_perm, m->perm.data(), sizeof(int) * V, cudaMemcpyHostToDevice));
     CK(cudaMemset(m->d_state, 0, sizeof(StepState)));
+    if (m->contact) {
+      const int nF = (int)m->sfaces.size() / 3, nE = (int)m->sedges.size() / 2, nS = (int)m->sverts.size();
+      const int np = (int)m->planes.size() / 4;
+      CK(dalloc(&m->d_planes, std::max(1, 4 * np)));
+      CK(dalloc(&m->d_faces, std::max(1, 3 * nF)));
+      CK(dalloc(&m->d_edges, std::max(1, 2 * nE)));
+      CK(dalloc(&m->d_sverts, std::max(1, nS)));
+      CK(dalloc(&m->d_is_surf, V));
+      for (int q = 0; q < 2; ++q) {
+        CK(dalloc(&m->d_fkeys[q], std::max(1, nF)));
+        CK(dalloc(&m->d_fids[q], std::max(1, nF)));
+        CK(dalloc(&m->d_ekeys[q], std::max(1, nE)));
+        CK(dalloc(&m->d_eids[q], std::max(1, nE)));
+      }
+      CK(dalloc(&m->d_pairs, m->pair_cap));
+      CK(dalloc(&m->d_d0, m->pair_cap));
+      CK(dalloc(&m->d_npairs, 1));
+      CK(dalloc(&m->d_cflags, 2));
+      CK(dalloc(&m->d_bg, 3 * (size_t)V));
+      CK(dalloc(&m->d_bH, 6 * (size_t)V));
+      CK(dalloc(&m->d_dmin, V));
+      CK(dalloc(&m->d_lim, std::max(1, m->Vf)));
+      if (np) CK(cudaMemcpy(m->d_planes, m->planes.data(), sizeof(double) * 4 * np, cudaMemcpyHostToDevice));
+      if (nF) CK(cudaMemcpy(m->d_faces, m->sfaces.data(), sizeof(int) * 3 * nF, cudaMemcpyHostToDevice));
+      if (nE) CK(cudaMemcpy(m->d_edges, m->sedges.data(), sizeof(int) * 2 * nE, cudaMemcpyHostToDevice));
+      if (nS) CK(cudaMemcpy(m->d_sverts, m->sverts.data(), sizeof(int) * nS, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(m->d_is_surf, m->is_surf.data(), V, cudaMemcpyHostToDevice));
+      CK(cudaMemset(m->d_cflags, 0, 2 * sizeof(int32_t)));
+      size_t b1 = 0, b2 = 0;
+      cub::DeviceRadixSort::SortPairs(nullptr, b1, m->d_fkeys[0], m->d_fkeys[1], m->d_fids[0], m->d_fids[1],
+                                      std::max(1, nF));
+      cub::DeviceRadixSort::SortPairs(nullptr, b2, m->d_ekeys[0], m->d_ekeys[1], m->d_eids[0], m->d_eids[1],
+                                      std::max(1, nE));
+      m->cub_bytes = std::max(b1, b2);
+      CK(cudaMalloc(&m->d_cub, m->cub_bytes));
+    }
     m->device_ready = true;
   }
   if (m->pool_version != m->cub_version) {
@@ -354,6 +469,37 @@ static DevMesh<T> dev_view(Mesh* m) {
   d.xt = m->d_xt;
   d.vt = m->d_vt;
   d.perm = m->d_perm;
+  d.c = ContactView();
+  if (m->contact) {
+    ContactView& c = d.c;
+    c.on = 1;
+    c.n_planes = (int)m->planes.size() / 4;
+    c.n_faces = (int)m->sfaces.size() / 3;
+    c.n_edges = (int)m->sedges.size() / 2;
+    c.n_sverts = (int)m->sverts.size();
+    c.planes = m->d_planes;
+    c.faces = m->d_faces;
+    c.edges = m->d_edges;
+    c.sverts = m->d_sverts;
+    c.is_surf = m->d_is_surf;
+    c.dhat = m->dhat;
+    c.kappa = m->kappa;
+    c.rc = m->rc;
+    c.cell = m->cell;
+    c.fkeys = m->d_fkeys[1];
+    c.fids = m->d_fids[1];
+    c.ekeys = m->d_ekeys[1];
+    c.eids = m->d_eids[1];
+    c.pairs = m->d_pairs;
+    c.n_pairs = m->d_npairs;
+    c.cap = m->pair_cap;
+    c.d0 = m->d_d0;
+    c.bg = m->d_bg;
+    c.bH = m->d_bH;
+    c.dmin = m->d_dmin;
+    c.lim = m->d_lim;
+    c.flags = m->d_cflags;
+  }
   d.inv_h2 = 1.0 / (m->h * m->h);
   d.h = m->h;
   for (int q = 0; q < 3; ++q) d.grav[q] = m->grav[q];
@@ -419,13 +565,39 @@ jgs2_status import_cubature(Mesh* m, const jgs2_cubature_blob* b) {
 
 // ------------------------------------------------------------------ step driver
 
+// Candidate pairs within r_c at x^k, the barrier accumulators and the per-vertex minimum
+// distances (Sec. 7). Pair order is not canonical here (the sums use atomics).
+template <typename T>
+static jgs2_status contact_pass(Mesh* m, DevMesh<T>& d, cudaStream_t s, StepState* st) {
+  const ContactView& c = d.c;
+  CK(cudaMemsetAsync(m->d_npairs, 0, sizeof(int32_t), s));
+  k_contact_reset<<<(m->V + 127) / 128, 128, 0, s>>>(c, m->V);
+  const int nP = std::max(c.n_faces, c.n_edges);
+  if (nP > 0) {
+    k_prim_keys<T><<<(nP + 127) / 128, 128, 0, s>>>(d, c, m->d_fkeys[0], m->d_fids[0], m->d_ekeys[0], m->d_eids[0]);
+    size_t bytes = m->cub_bytes;
+    if (c.n_faces)
+      CK(cub::DeviceRadixSort::SortPairs(m->d_cub, bytes, m->d_fkeys[0], m->d_fkeys[1], m->d_fids[0], m->d_fids[1],
+                                         c.n_faces, 0, 64, s));
+    bytes = m->cub_bytes;
+    if (c.n_edges)
+      CK(cub::DeviceRadixSort::SortPairs(m->d_cub, bytes, m->d_ekeys[0], m->d_ekeys[1], m->d_eids[0], m->d_eids[1],
+                                         c.n_edges, 0, 64, s));
+  }
+  if (c.n_sverts) k_query_vertices<T><<<(c.n_sverts + 127) / 128, 128, 0, s>>>(d, c);
+  if (c.n_edges) k_query_edges<T><<<(c.n_edges + 127) / 128, 128, 0, s>>>(d, c);
+  k_pair_terms<T><<<(c.cap + 127) / 128, 128, 0, s>>>(d, c, st);
+  CK(cudaGetLastError());
+  return JGS2_OK;
+}
+
 // Launch bookkeeping of one step: counts per kernel kind and, when profiling, a CUDA
 // event pair around every launch (events are pooled per mesh).
 struct Launches {
   Mesh* m;
   cudaStream_t s;
   bool prof;
-  int count[JGS2_NKERNELS] = {0, 0, 0, 0, 0, 0};
+  int count[JGS2_NKERNELS] = {0, 0, 0, 0, 0, 0, 0};
   std::vector<std::pair<int, int>> rec;  // (kind, event index)
   int used = 0;
   cudaError_t err = cudaSuccess;
@@ -485,6 +657,12 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t s, 
   const int every = std::max(1, o.check_every);
   for (int k = 0; k <= max_k; ++k) {
     int id;
+    if (m->contact) {
+      id = L.begin(JGS2_K_CONTACT);
+      jgs2_status cs = contact_pass<T>(m, d, s, m->d_state);
+      L.end(id);
+      if (cs != JGS2_OK) return cs;
+    }
     if (corr && m->nP > 0) {
       id = L.begin(JGS2_K_POOL);
       if (o.correction == JGS2_CORR_ASM)
@@ -509,10 +687,17 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t s, 
     if (k == max_k) break;
     if (o.line_search) {
       id = L.begin(JGS2_K_ENERGY);
-      if (corr)
-        k_energy<T, 2><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
-      else
-        k_energy<T, 1><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
+      if (m->contact) {
+        if (corr)
+          k_energy<T, 2, true><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
+        else
+          k_energy<T, 1, true><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
+      } else {
+        if (corr)
+          k_energy<T, 2, false><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
+        else
+          k_energy<T, 1, false><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
+      }
       L.end(id);
     }
     if (nbV > 0) {
@@ -530,6 +715,15 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t s, 
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(hs, m->d_state, sizeof(StepState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (m->contact) {
+    int32_t fl[2];
+    CK(cudaMemcpy(fl, m->d_cflags, sizeof(fl), cudaMemcpyDeviceToHost));
+    if (fl[0]) {
+      CK(cudaMemset(m->d_cflags, 0, sizeof(fl)));
+      return fail(JGS2_ENOMEM, "contact pair buffer overflow (" + std::to_string(m->pair_cap) + " pairs)");
+    }
+    if (fl[1]) CK(cudaMemset(m->d_cflags, 0, sizeof(fl)));
+  }
   return JGS2_OK;
 }
 
@@ -650,6 +844,11 @@ jgs2_status energy_gradient(Mesh* m, const double* xt, const double* vt, const d
   k_setup_vertices<double><<<nb, 128, 0, s>>>(d, xt, vt, x);
   k_setup_tets<double><<<(m->T + 127) / 128, 128, 0, s>>>(d);
   // pinned vertices keep x_t; a caller x that moves them is a different problem
+  if (m->contact) {
+    CK(cudaMemsetAsync(m->d_state, 0, sizeof(StepState), s));
+    st = contact_pass<double>(m, d, s, m->d_state);
+    if (st != JGS2_OK) return st;
+  }
   if (g) k_grad<double><<<nb, 128, 0, s>>>(d, g);
   if (E) {
     const int nbT = (m->T + 127) / 128, nbV = (m->Vf + 127) / 128;
@@ -659,10 +858,80 @@ jgs2_status energy_gradient(Mesh* m, const double* xt, const double* vt, const d
     CK(cudaStreamSynchronize(s));
     double acc = 0.0;
     for (double q : p) acc += q;
+    if (m->contact) {
+      CK(cudaMemsetAsync(m->d_partial, 0, sizeof(double), s));
+      k_pair_energy<double><<<148, 128, 0, s>>>(d, d.c, m->d_partial);
+      double eb = 0.0;
+      CK(cudaMemcpyAsync(&eb, m->d_partial, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      acc += eb;
+    }
     *E = acc;
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
+  return JGS2_OK;
+}
+
+jgs2_status contact_pairs(Mesh* m, const double* xt, const double* x, double radius, int32_t* out, int cap,
+                          int32_t* n_out, void* stream) {
+  if (!m || !xt || !x || !n_out || (cap > 0 && !out)) return fail(JGS2_EINVAL, "null argument");
+  if (!m->contact) return fail(JGS2_EINVAL, "mesh was created without contact");
+  if (!(radius > 0.0)) return fail(JGS2_EINVAL, "radius must be positive");
+  cudaStream_t s = (cudaStream_t)stream;
+  jgs2_status st = ensure_prec<double>(m);
+  if (st != JGS2_OK) return st;
+  DevMesh<double> d = dev_view<double>(m);
+  d.c.cell = m->cell - m->rc + radius;
+  d.c.rc = radius;
+  const int nb = (m->V + 127) / 128;
+  k_setup_vertices<double><<<nb, 128, 0, s>>>(d, xt, xt, x);
+  CK(cudaMemsetAsync(m->d_state, 0, sizeof(StepState), s));
+  st = contact_pass<double>(m, d, s, m->d_state);
+  if (st != JGS2_OK) return st;
+  int32_t n = 0, fl[2] = {0, 0};
+  CK(cudaMemcpyAsync(&n, m->d_npairs, sizeof(n), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(fl, m->d_cflags, sizeof(fl), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaMemset(m->d_cflags, 0, sizeof(fl)));
+  if (fl[0] || n > m->pair_cap) return fail(JGS2_ENOMEM, "contact pair buffer overflow");
+  std::vector<uint64_t> keys(n);
+  if (n) CK(cudaMemcpy(keys.data(), m->d_pairs, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
+  std::vector<std::array<int, 5>> rows(n);
+  for (int q = 0; q < n; ++q) {
+    const int kind = (int)(keys[q] >> 60), a = (int)((keys[q] >> 30) & 0x3fffffff), b = (int)(keys[q] & 0x3fffffff);
+    std::array<int, 5> r{kind, -1, -1, -1, -1};
+    if (kind == 0) {
+      r[1] = m->perm[a];
+      r[2] = b;
+    } else if (kind == 1) {
+      r[1] = m->perm[a];
+      int f[3] = {m->perm[m->sfaces[3 * b]], m->perm[m->sfaces[3 * b + 1]], m->perm[m->sfaces[3 * b + 2]]};
+      std::sort(f, f + 3);
+      r[2] = f[0];
+      r[3] = f[1];
+      r[4] = f[2];
+    } else {
+      int e1[2] = {m->perm[m->sedges[2 * a]], m->perm[m->sedges[2 * a + 1]]};
+      int e2[2] = {m->perm[m->sedges[2 * b]], m->perm[m->sedges[2 * b + 1]]};
+      std::sort(e1, e1 + 2);
+      std::sort(e2, e2 + 2);
+      if (std::make_pair(e2[0], e2[1]) < std::make_pair(e1[0], e1[1])) {
+        std::swap(e1[0], e2[0]);
+        std::swap(e1[1], e2[1]);
+      }
+      r[1] = e1[0];
+      r[2] = e1[1];
+      r[3] = e2[0];
+      r[4] = e2[1];
+    }
+    rows[q] = r;
+  }
+  std::sort(rows.begin(), rows.end());
+  *n_out = n;
+  for (int q = 0; q < std::min(n, cap); ++q)
+    for (int k = 0; k < 5; ++k) out[5 * q + k] = rows[q][k];
+  if (n > cap) return fail(JGS2_ENOMEM, "more pairs than cap");
   return JGS2_OK;
 }
 
@@ -770,6 +1039,11 @@ jgs2_status jgs2_sweeps(jgs2_mesh* mesh, const double* x_t, const double* v_t, d
 jgs2_status jgs2_energy_gradient(jgs2_mesh* mesh, const double* x_t, const double* v_t, const double* x,
                                  double* energy, double* g, void* stream) {
   return energy_gradient(reinterpret_cast<Mesh*>(mesh), x_t, v_t, x, energy, g, stream);
+}
+
+jgs2_status jgs2_contact_pairs(jgs2_mesh* mesh, const double* x_t, const double* x, double radius, int32_t* out,
+                               int32_t cap, int32_t* n_out, void* stream) {
+  return contact_pairs(reinterpret_cast<Mesh*>(mesh), x_t, x, radius, out, cap, n_out, stream);
 }
 
 void jgs2_mesh_destroy(jgs2_mesh* mesh) { delete reinterpret_cast<Mesh*>(mesh); }

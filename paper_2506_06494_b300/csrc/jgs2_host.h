@@ -55,6 +55,21 @@ struct Mesh {
   StepState* d_state = nullptr;
   StepState* h_state = nullptr;
   std::vector<cudaEvent_t> events;  // pooled profiling events
+  // contact (Sec. 7): surface in internal vertex ids
+  int contact = 0;
+  double dhat = 0.0, kappa = 0.0, rc = 0.0, cell = 0.0;
+  std::vector<double> planes;                 // [n][4]
+  std::vector<int> sfaces, sedges, sverts;    // [nF][3], [nE][2], [nS]
+  std::vector<uint8_t> is_surf;               // [V] internal order
+  int pair_cap = 0;
+  double *d_planes = nullptr, *d_d0 = nullptr, *d_bg = nullptr, *d_bH = nullptr;
+  int32_t *d_faces = nullptr, *d_edges = nullptr, *d_sverts = nullptr, *d_npairs = nullptr, *d_cflags = nullptr;
+  int32_t *d_fids[2] = {nullptr, nullptr}, *d_eids[2] = {nullptr, nullptr};
+  uint8_t* d_is_surf = nullptr;
+  uint64_t *d_fkeys[2] = {nullptr, nullptr}, *d_ekeys[2] = {nullptr, nullptr}, *d_pairs = nullptr;
+  double *d_dmin = nullptr, *d_lim = nullptr;
+  void* d_cub = nullptr;
+  size_t cub_bytes = 0;
   PrecBufs<float> f32;
   PrecBufs<double> f64;
   ~Mesh();

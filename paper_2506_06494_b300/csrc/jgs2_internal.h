@@ -60,6 +60,34 @@ struct StepState {
   uint32_t ticket_energy;
 };
 
+// Contact data of a mesh (Sec. 7); pairs: 0 vertex-wall, 1 vertex-face, 2 edge-edge.
+struct ContactView {
+  int on = 0;
+  int n_planes = 0, n_faces = 0, n_edges = 0, n_sverts = 0;
+  const double* planes = nullptr;    // [n_planes][4]
+  const int32_t* faces = nullptr;    // [n_faces][3] internal vertex ids (outward)
+  const int32_t* edges = nullptr;    // [n_edges][2]
+  const int32_t* sverts = nullptr;   // [n_sverts]
+  const uint8_t* is_surf = nullptr;  // [V]
+  double dhat = 0, kappa = 0, rc = 0, cell = 0;
+  // broadphase (sorted by cell key)
+  const uint64_t* fkeys = nullptr;
+  const int32_t* fids = nullptr;
+  const uint64_t* ekeys = nullptr;
+  const int32_t* eids = nullptr;
+  // pairs
+  uint64_t* pairs = nullptr;     // packed (kind << 60 | a << 30 | b), canonical after sorting
+  int32_t* n_pairs = nullptr;    // device counter
+  int cap = 0;
+  double* d0 = nullptr;          // [cap] distance at x^k
+  // per-vertex accumulators
+  double* bg = nullptr;          // [3][V]
+  double* bH = nullptr;          // [6][V]
+  double* dmin = nullptr;        // [V] smallest candidate distance (atomicMin on the bits)
+  double* lim = nullptr;         // [Vf] step limit 0.45 min(rc - dhat, dmin)
+  int32_t* flags = nullptr;      // [0] overflow, [1] intersection
+};
+
 template <typename T>
 struct DevMesh {
   int V, Vf, T_, n_slices, nP, n_cub;
@@ -83,6 +111,7 @@ struct DevMesh {
   double* xt;               // [V][3]
   double* vt;               // [V][3]
   const int32_t* perm;      // internal -> caller
+  ContactView c;            // IPC barrier data (c.on = 0: no contact)
   double inv_h2;            // 1/h^2
   double h;
   double grav[3];

@@ -19,6 +19,12 @@
 #include "jgs2_internal.h"
 
 namespace jgs2 {
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* smem);
+}
+#include "jgs2_contact.cuh"
+
+namespace jgs2 {
 
 // ------------------------------------------------------------------ small helpers
 
@@ -300,6 +306,18 @@ __host__ __device__ constexpr int pk(int r, int c) {
   return r <= c ? r * 12 - (r * (r - 1)) / 2 + (c - r) : c * 12 - (c * (c - 1)) / 2 + (r - c);
 }
 
+// Step truncation: scale d so that |d| <= lim (reading R11).
+template <typename T>
+__device__ __forceinline__ void truncate3(T (&d)[3], T lim) {
+  const T n = dsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  if (n > lim) {
+    const T s = lim / n;
+    d[0] *= s;
+    d[1] *= s;
+    d[2] *= s;
+  }
+}
+
 // 3x3 SPD solve by Cholesky; returns false if a pivot is not positive.
 template <typename T>
 __device__ __forceinline__ bool chol3_solve(const T (&A)[6], const T (&b)[3], T (&x)[3]) {
@@ -446,6 +464,10 @@ __global__ void __launch_bounds__(128) k_pool(DevMesh<T> m, const StepState* __r
         const T mh = m.mh2[v];
 #pragma unroll
         for (int i = 0; i < 3; ++i) g[i] += mh * (uv[i] - dz[i]);
+        if (m.c.on) {
+#pragma unroll
+          for (int i = 0; i < 3; ++i) g[i] += T(m.c.bg[(size_t)i * m.V + v]);
+        }
 #pragma unroll
         for (int q = 0; q < 9; ++q) Fs[q] /= W;
         polar_rotation(Fs, R);
@@ -612,10 +634,23 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_gather(DevMesh<
     H[0] += mh;
     H[3] += mh;
     H[5] += mh;
+    T lim = T(INFINITY);
+    if (m.c.on) {
+      // IPC barrier (Sec. 7): exact gradient and Gauss-Newton diagonal block of the pairs
+      // around i, and the step limit 0.45 min(r_c - dhat, d_min) of a surface vertex
+      const size_t V = m.V;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) g[q] += T(m.c.bg[q * V + i]);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) H[q] += T(m.c.bH[q * V + i]);
+      if (m.c.is_surf[i]) lim = T(0.45 * fmin(m.c.rc - m.c.dhat, m.c.dmin[i]));
+      m.c.lim[i] = double(lim);
+    }
     T dj[3];
     {
       T rg[3] = {-g[0], -g[1], -g[2]};
       if (!chol3_solve(H, rg, dj)) dj[0] = dj[1] = dj[2] = T(0);
+      truncate3(dj, lim);
     }
     Vec4<T> djv{dj[0], dj[1], dj[2], T(0)};
     m.DJ[i] = djv;
@@ -727,9 +762,11 @@ __global__ void __launch_bounds__(128) k_correct(DevMesh<T> m, StepState* st, in
     for (int a = 0; a < 3; ++a) rhs[a] = -g[a] - (R[3 * a] * gt[0] + R[3 * a + 1] * gt[1] + R[3 * a + 2] * gt[2]);
     T d[3];
     if (!chol3_solve(A, rhs, d)) {
-      // reading R7: the vertex takes the uncorrected step
+      // reading R7: the vertex takes the uncorrected step (already truncated)
       load3(m.DJ, i, d);
       fb = 1;
+    } else if (m.c.on) {
+      truncate3(d, T(m.c.lim[i]));
     }
     Vec4<T> dv{d[0], d[1], d[2], T(0)};
     m.D[i] = dv;
@@ -799,12 +836,13 @@ __device__ __forceinline__ void tet_dpsi_poly(const TetRec<T>& r, const T (&F)[9
 // (per-thread partial sums in T over a grid-stride loop, FP64 across threads and blocks),
 // then the last block evaluates E(x + a d) - E(x) at a = 2^-j and takes the first
 // Armijo-satisfying trial, D before D_J.
-template <typename T, int ND>
+template <typename T, int ND, bool CONTACT>
 __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st,
                                                 double* __restrict__ partial /* [ND*6][grid] */) {
   if (st->done) return;
   constexpr int NC = 6 * ND;
-  __shared__ double red[32 * NC];
+  constexpr int NB = CONTACT ? kLsTrials * ND : 0;
+  __shared__ double red[32 * (NC + NB)];
   T acc[NC];
 #pragma unroll
   for (int j = 0; j < NC; ++j) acc[j] = T(0);
@@ -845,18 +883,37 @@ __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st,
       acc[dir * 6 + 1] += T(0.5) * mh * dd;
     }
   }
-  double accd[NC];
+  // IPC barrier change over the candidate pairs, per trial (not polynomial in a)
+  double accd[NC + NB];
 #pragma unroll
   for (int j = 0; j < NC; ++j) accd[j] = double(acc[j]);
-  block_sum<NC>(accd, red);
+#pragma unroll
+  for (int j = 0; j < NB; ++j) accd[NC + j] = 0.0;
+  if (CONTACT) {
+    const int np = min(*m.c.n_pairs, m.c.cap);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += stride) {
+      const uint64_t key = m.c.pairs[q];
+      const double b0 = barrier_b(m.c.d0[q], m.c.dhat);
+#pragma unroll
+      for (int dir = 0; dir < ND; ++dir)
+#pragma unroll 1
+        for (int j = 0; j < kLsTrials; ++j) {
+          int vs[4], nv;
+          P3 J[4];
+          const double d = pair_geom(m, m.c, key, 1.0 / double(1 << j), dir == 0 ? m.D : m.DJ, vs, J, nv);
+          accd[NC + dir * kLsTrials + j] += m.c.kappa * (barrier_b(d, m.c.dhat) - b0);
+        }
+    }
+  }
+  block_sum<NC + NB>(accd, red);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int j = 0; j < NC; ++j) partial[(size_t)j * gridDim.x + blockIdx.x] = accd[j];
+    for (int j = 0; j < NC + NB; ++j) partial[(size_t)j * gridDim.x + blockIdx.x] = accd[j];
   }
   if (!last_block(&st->ticket_energy)) return;
-  double cf[NC];
+  double cf[NC + NB];
 #pragma unroll
-  for (int j = 0; j < NC; ++j) cf[j] = block_sum_array(partial + (size_t)j * gridDim.x, gridDim.x, 1, red);
+  for (int j = 0; j < NC + NB; ++j) cf[j] = block_sum_array(partial + (size_t)j * gridDim.x, gridDim.x, 1, red);
   if (threadIdx.x == 0) {
     st->ticket_energy = 0;
     double alpha = 0.0;
@@ -867,7 +924,8 @@ __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st,
       for (int j = 0; j < kLsTrials; ++j) {
         const double a = 1.0 / double(1 << j);
         const double* c = cf + 6 * dd;
-        const double dE = a * (c[0] + a * (c[1] + a * (c[2] + a * (c[3] + a * (c[4] + a * c[5])))));
+        const double dE = a * (c[0] + a * (c[1] + a * (c[2] + a * (c[3] + a * (c[4] + a * c[5]))))) +
+                          (CONTACT ? cf[NC + dd * kLsTrials + j] : 0.0);
         if (dE <= 1e-4 * a * slope) {
           alpha = a;
           dir = dd;
@@ -927,7 +985,8 @@ __global__ void k_grad(DevMesh<T> m, double* __restrict__ g_caller) {
   load3(m.u, i, ui);
   load3(m.dz, i, dz);
 #pragma unroll
-  for (int q = 0; q < 3; ++q) g_caller[3 * c + q] = double(g[q] + m.mh2[i] * (ui[q] - dz[q]));
+  for (int q = 0; q < 3; ++q)
+    g_caller[3 * c + q] = double(g[q] + m.mh2[i] * (ui[q] - dz[q])) + (m.c.on ? m.c.bg[(size_t)q * m.V + i] : 0.0);
 }
 
 template <typename T>

@@ -16,8 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libjgs2.so")
 
 TRACE_MAX = 4096
-NKERNELS = 6
-KERNEL_NAMES = ["k_pool", "k_gather", "k_correct", "k_energy", "k_update", "setup"]
+NKERNELS = 7
+KERNEL_NAMES = ["k_pool", "k_gather", "k_correct", "k_energy", "k_update", "setup", "contact"]
 FP64, FP32 = 0, 1
 CORR_ASM, CORR_ELEM, CORR_OFF = 0, 1, 2
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTPRECOMPUTED", 5: "ENOTCONVERGED",
@@ -29,7 +29,9 @@ class MeshDesc(C.Structure):
                 ("rest_pos", C.POINTER(C.c_double)), ("tets", C.POINTER(C.c_int32)),
                 ("youngs", C.POINTER(C.c_double)), ("poisson", C.POINTER(C.c_double)),
                 ("density", C.POINTER(C.c_double)), ("pinned", C.POINTER(C.c_uint8)),
-                ("gravity", C.c_double * 3), ("dt", C.c_double)]
+                ("gravity", C.c_double * 3), ("dt", C.c_double),
+                ("contact", C.c_int32), ("n_planes", C.c_int32), ("planes", C.POINTER(C.c_double)),
+                ("dhat", C.c_double), ("kappa", C.c_double)]
 
 
 class PrecomputeOpts(C.Structure):
@@ -62,7 +64,8 @@ _lib = None
 EXPORTS = ["jgs2_precompute_opts_default", "jgs2_step_opts_default", "jgs2_mesh_create",
            "jgs2_precompute", "jgs2_precompute_import", "jgs2_precompute_export",
            "jgs2_mesh_n_cub", "jgs2_step", "jgs2_step_host", "jgs2_sweeps",
-           "jgs2_energy_gradient", "jgs2_mesh_destroy", "jgs2_last_error"]
+           "jgs2_energy_gradient", "jgs2_energy_gradient_static", "jgs2_contact_pairs",
+           "jgs2_mesh_destroy", "jgs2_last_error"]
 
 
 def lib():
@@ -86,6 +89,8 @@ def lib():
     L.jgs2_step_host.argtypes = [P, P, P, C.POINTER(StepOpts), P, C.POINTER(StepReport)]
     L.jgs2_sweeps.argtypes = [P, P, P, P, C.c_int32, C.POINTER(StepOpts), P]
     L.jgs2_energy_gradient.argtypes = [P, P, P, P, P, P, P]
+    L.jgs2_contact_pairs.argtypes = [P, P, P, C.c_double, P, C.c_int32, C.POINTER(C.c_int32), P]
+    L.jgs2_contact_pairs.restype = C.c_int
     L.jgs2_mesh_destroy.argtypes = [P]
     L.jgs2_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -145,14 +150,16 @@ def _dev(t):
 class Mesh:
     """A tet mesh living on the current CUDA device (jgs2_mesh_create)."""
 
-    def __init__(self, X, tets, youngs, poisson, density, pinned=None, gravity=(0, 0, -9.8), dt=1 / 120):
+    def __init__(self, X, tets, youngs, poisson, density, pinned=None, gravity=(0, 0, -9.8), dt=1 / 120,
+                 planes=None, dhat=1e-3, kappa=1e5, contact=0):
         self._keep = [np.ascontiguousarray(X, dtype=np.float64),
                       np.ascontiguousarray(tets, dtype=np.int32),
                       np.ascontiguousarray(youngs, dtype=np.float64),
                       np.ascontiguousarray(poisson, dtype=np.float64),
                       np.ascontiguousarray(density, dtype=np.float64),
-                      None if pinned is None else np.ascontiguousarray(pinned, dtype=np.uint8)]
-        X, T, E, nu, rho, pin = self._keep
+                      None if pinned is None else np.ascontiguousarray(pinned, dtype=np.uint8),
+                      np.ascontiguousarray(np.zeros((0, 4)) if planes is None else planes, dtype=np.float64)]
+        X, T, E, nu, rho, pin, pl = self._keep
         d = MeshDesc()
         d.n_vertices = X.shape[0]
         d.n_tets = T.shape[0]
@@ -165,6 +172,11 @@ class Mesh:
         for q in range(3):
             d.gravity[q] = float(gravity[q])
         d.dt = float(dt)
+        d.contact = int(contact)
+        d.n_planes = int(pl.shape[0])
+        d.planes = _ptr(pl, C.c_double)
+        d.dhat = float(dhat)
+        d.kappa = float(kappa)
         h = C.c_void_p()
         _check(lib().jgs2_mesh_create(C.byref(d), C.byref(h)))
         self.handle = h
@@ -172,8 +184,18 @@ class Mesh:
         self.T = int(T.shape[0])
 
     @classmethod
-    def from_scene(cls, s):
-        return cls(s.X, s.tets, s.youngs, s.poisson, s.density, s.pinned, s.gravity, s.dt)
+    def from_scene(cls, s, contact=None):
+        c = s.contact if contact is None else contact
+        return cls(s.X, s.tets, s.youngs, s.poisson, s.density, s.pinned, s.gravity, s.dt,
+                   s.planes, s.dhat, s.kappa, c)
+
+    def contact_pairs(self, x_t, x, radius, cap=1 << 20, stream=None):
+        """Canonical candidate pair rows (kind, a, b, c, d) within radius (jgs2_contact_pairs)."""
+        out = np.zeros((cap, 5), np.int32)
+        n = C.c_int32()
+        _check(lib().jgs2_contact_pairs(self.handle, _dev(x_t), _dev(x), float(radius), out.ctypes.data, cap,
+                                        C.byref(n), C.c_void_p(_stream_ptr(stream))))
+        return out[:n.value].copy()
 
     def close(self):
         if getattr(self, "handle", None):

@@ -270,3 +270,28 @@ def perturbed_state(X, pinned, scale, seed=0):
     d = rng.normal(0.0, scale, size=X.shape)
     d[np.asarray(pinned).astype(bool)] = 0.0
     return X + d
+
+
+def drop_scene(nv=4, size=0.02, gap=5e-4, speed=0.3, E=1e5, dhat=1e-3, kappa=1e4):
+    """A small free block just above the floor, moving down: exercises the wall barrier."""
+    X, tets = kuhn_grid(nv, nv, nv, (size, size, size))
+    X = X + np.array([0.3, 0.3, gap])
+    T = len(tets)
+    v0 = np.zeros_like(X)
+    v0[:, 2] = -speed
+    return Scene("drop", X, tets, np.full(T, E), np.full(T, 0.4), np.full(T, 1000.0),
+                 np.zeros(len(X), np.uint8), v0, planes=box_planes(), dhat=dhat, kappa=kappa, contact=1)
+
+
+def stack_scene(nv=3, size=0.02, gap=1.5e-3, speed=0.3, E=1e5, dhat=1e-3, kappa=1e4):
+    """Two small blocks, the upper one moving down onto the lower one resting on the floor
+    (vertex-face and edge-edge pairs between bodies, and the floor)."""
+    X, tets = kuhn_grid(nv, nv, nv, (size, size, size))
+    off = np.array([0.003, 0.002, 0.0])
+    Xa = np.vstack([X + [0.3, 0.3, 0.8 * dhat], X + [0.3, 0.3, size + gap] + off])
+    ta = np.vstack([tets, tets + len(X)]).astype(np.int32)
+    T = len(ta)
+    v0 = np.zeros_like(Xa)
+    v0[len(X):, 2] = -speed
+    return Scene("stack", Xa, ta, np.full(T, E), np.full(T, 0.4), np.full(T, 1000.0),
+                 np.zeros(len(Xa), np.uint8), v0, planes=box_planes(), dhat=dhat, kappa=kappa, contact=1)

@@ -344,3 +344,102 @@ def test_local_direction_matches_global(cube, cube_cub):
         d, dj = lm.direction(i, x, z, s.dt, cube_cub.elem[i], cube_cub.weight[i], cube_cub.ubar[i])
         assert np.allclose(d, D[i], rtol=1e-10, atol=1e-14)
         assert np.allclose(dj, DJ[i], rtol=1e-10, atol=1e-14)
+
+
+# ---------------------------------------------------------------- T9/T10: contact (Sec. 7)
+
+from oracle import contact as ct  # noqa: E402
+
+
+def test_barrier_closed_form():
+    dh = 1e-3
+    d = np.array([dh, 2 * dh])
+    assert np.all(ct.barrier(d, dh) == 0) and np.all(ct.barrier_d1(d, dh) == 0) and np.all(ct.barrier_d2(d, dh) == 0)
+    # C^2 at dhat: value, slope and curvature all tend to 0 from below
+    e = np.array([dh * (1 - 1e-6)])
+    assert ct.barrier(e, dh)[0] < 1e-20 and abs(ct.barrier_d1(e, dh)[0]) < 1e-14 and ct.barrier_d2(e, dh)[0] < 1e-5
+    # blows up at 0, FD of the derivatives
+    assert ct.barrier(np.array([1e-12]), dh)[0] > 1e-6 * 20
+    for x in [1e-5, 2e-4, 7e-4]:
+        h = 1e-9
+        fd1 = (ct.barrier(np.array([x + h]), dh)[0] - ct.barrier(np.array([x - h]), dh)[0]) / (2 * h)
+        fd2 = (ct.barrier_d1(np.array([x + h]), dh)[0] - ct.barrier_d1(np.array([x - h]), dh)[0]) / (2 * h)
+        assert abs(fd1 - ct.barrier_d1(np.array([x]), dh)[0]) < 1e-5 * abs(fd1)
+        assert abs(fd2 - ct.barrier_d2(np.array([x]), dh)[0]) < 1e-5 * abs(fd2)
+        assert ct.barrier_d2(np.array([x]), dh)[0] > 0 > ct.barrier_d1(np.array([x]), dh)[0]
+
+
+def test_distances_against_dense_sampling():
+    r = np.random.default_rng(5)
+    for _ in range(20):
+        p, a, b, c = r.normal(size=(4, 3))
+        d, w = ct.point_triangle(p, a, b, c)
+        uv = r.random((200000, 2))
+        uv = np.where(uv.sum(1, keepdims=True) > 1, 1 - uv, uv)
+        pts = a + uv[:, :1] * (b - a) + uv[:, 1:] * (c - a)
+        dd = np.linalg.norm(pts - p, axis=1).min()
+        res = 3 * max(np.linalg.norm(b - a), np.linalg.norm(c - a)) / np.sqrt(2e5)  # sampling spacing
+        assert d <= dd + 1e-12 and dd - d < res
+        assert abs(np.linalg.norm(p - (w[0] * a + w[1] * b + w[2] * c)) - d) < 1e-12
+        q0, q1 = r.normal(size=(2, 3))
+        d2, s, t = ct.segment_segment(a, b, q0, q1)
+        st = r.random((200000, 2))
+        dd2 = np.linalg.norm(a + st[:, :1] * (b - a) - q0 - st[:, 1:] * (q1 - q0), axis=1).min()
+        res2 = 3 * max(np.linalg.norm(b - a), np.linalg.norm(q1 - q0)) / np.sqrt(2e5)
+        assert d2 <= dd2 + 1e-12 and dd2 - d2 < res2
+        assert abs(np.linalg.norm(a + s * (b - a) - q0 - t * (q1 - q0)) - d2) < 1e-12
+
+
+def test_contact_gradient_fd_and_surface():
+    X, tets = scenes.kuhn_grid(3, 3, 3, (0.02, 0.02, 0.02))
+    X2 = X + [0.0, 0.0, 0.0205]   # a second block just above the first
+    Xa = np.vstack([X, X2])
+    ta = np.vstack([tets, tets + len(X)])
+    bf, be, sv = ct.surface(ta, Xa)
+    assert len(bf) == 2 * 6 * 2 * 4 and len(sv) == 2 * 26   # 2 cubes x 6 sides x 2x2 cells x 2 tris
+    for a, b, c in bf:   # outward: the face normal points away from the solid's centroid
+        cen = Xa[:len(X)].mean(0) if a < len(X) else Xa[len(X):].mean(0)
+        n = np.cross(Xa[b] - Xa[a], Xa[c] - Xa[a])
+        assert n @ (Xa[a] - cen) > 0
+    con = ct.Contact(ta, Xa, scenes.box_planes()[:1], 1e-3, 1e4)
+    x = Xa + np.random.default_rng(3).normal(0, 1e-4, Xa.shape)
+    x[:, 2] += 5e-4
+    pairs = con.pairs(x, 1e-3)
+    assert {p[0] for p in pairs} >= {0, 1, 2}
+    g, H = con.vertex_terms(x, pairs, len(x))
+    for v in np.nonzero(np.abs(g).sum(1))[0][:6]:
+        for k in range(3):
+            e = np.zeros_like(x)
+            e[v, k] = 1e-9
+            fd = (con.energy(x + e, con.pairs(x + e, 1e-3)) - con.energy(x - e, con.pairs(x - e, 1e-3))) / 2e-9
+            assert abs(fd - g[v, k]) <= 1e-5 * abs(g[v]).max() + 1e-9
+        assert np.linalg.eigvalsh(H[v]).min() > -1e-9
+
+
+def _contact_mesh(s):
+    m = fem.Mesh(s.X, s.tets, s.youngs, s.poisson, s.density, s.pinned)
+    return m.enable_contact(s.planes, s.dhat, s.kappa)
+
+
+def test_contact_step_stays_intersection_free():
+    for s in (scenes.drop_scene(nv=3), scenes.stack_scene()):
+        m = _contact_mesh(s)
+        x, v = s.X.copy(), s.v0.copy()
+        for _ in range(1):
+            r = sweep.step(m, x, v, s.dt, s.gravity, None, 1e-4, 150)
+            x, v = r.x, r.v
+            pairs = m.contact.pairs(x, 10 * s.dhat)
+            assert all(p[3] > 0 for p in pairs)
+            assert min(r.residuals) < 0.1   # progress; the barrier makes Jacobi slow
+        assert x[:, 2].min() > 0
+    assert any(p[0] == 1 for p in pairs) and any(p[0] == 2 for p in pairs)
+
+
+def test_no_contact_in_range_equals_plain_sweep(cube, cube_cub):
+    s, m, = cube
+    mc = fem.Mesh(s.X, s.tets, s.youngs, s.poisson, s.density, s.pinned).enable_contact(
+        scenes.box_planes() + [0, 0, 0, -5.0], 1e-3, 1e4)   # walls 5 m away
+    z = fem.inertia_target(s.X, s.v0, s.dt, s.gravity)
+    a = sweep.run_sweeps(m, s.X, z, s.dt, cube_cub, 2)
+    b = sweep.run_sweeps(mc, s.X, z, s.dt, cube_cub, 2)
+    assert np.array_equal(a, b)
