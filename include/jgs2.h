@@ -181,6 +181,46 @@ jgs2_status jgs2_sweeps(jgs2_mesh* mesh, const double* x_t, const double* v_t, d
 jgs2_status jgs2_energy_gradient(jgs2_mesh* mesh, const double* x_t, const double* v_t,
                                  const double* x, double* energy, double* g, void* stream);
 
+/* Adjoint of one converged step (the paper has no adjoint; this is the implicit-function
+ * theorem applied to Eq. 1's optimality condition grad E(x*; x_t, v_t, E) = 0). For a loss
+ * L(x_{t+1}, v_{t+1}) with v_{t+1} = (x_{t+1} - x_t)/h and gbar = dL/dx_{t+1} + dL/dv_{t+1}/h:
+ *     H(x*) lam = gbar over free DOFs (H: the exact Hessian of E at x*, no projection)
+ *     dL/dx_t = (M/h^2) lam - dL/dv_{t+1}/h  (free),  dL/dx_{t+1} - H_pf lam  (pinned)
+ *     dL/dv_t = (M/h) lam  (free), 0 (pinned);  dL/dE_e += -lam_e . g_e^el(x*) / E_e
+ * The linear system is solved by flexible conjugate gradients preconditioned with the JGS2
+ * sweep in linear mode (H_ii, R_i and the cubature element Hessians at x*, Eq. cubature
+ * applied to the residual); correction = JGS2_CORR_OFF gives block-Jacobi preconditioning.
+ * All arrays are DEVICE pointers in caller order: x_t, v_t, x_t1, gx_t1, gv_t1, gx_t, gv_t
+ * [V][3] double; gE [T] double is ACCUMULATED (+=). Meshes with contact are rejected
+ * (JGS2_EINVAL): the barrier is not part of this adjoint. Returns JGS2_ENOTCONVERGED (all
+ * outputs written) if max_iters is reached first. Synchronises the stream. */
+typedef struct {
+  int32_t max_iters;     /* conjugate-gradient iterations at most */
+  double rel_tol;        /* stop at |r| <= rel_tol |gbar| */
+  int32_t precision;     /* jgs2_precision of the vectors and kernels; reductions are FP64 */
+  int32_t correction;    /* JGS2_CORR_ASM (JGS2 preconditioner) or JGS2_CORR_OFF (block Jacobi) */
+  int32_t check_every;   /* host reads the convergence flag every this many iterations */
+} jgs2_adjoint_opts;
+typedef struct {
+  int32_t iters;
+  int32_t converged;
+  double rel_residual;   /* |H lam - gbar| / |gbar| */
+  double ms;
+} jgs2_adjoint_report;
+/* Defaults: max_iters 5000, rel_tol 1e-6, FP64, block-Jacobi preconditioner (the JGS2
+ * preconditioner is available but, like the forward correction, its cubature estimate of the
+ * residual's reduced part can stall the iteration), check_every 32. */
+void jgs2_adjoint_opts_default(jgs2_adjoint_opts* o);
+jgs2_status jgs2_step_adjoint(jgs2_mesh* mesh, const double* x_t, const double* v_t, const double* x_t1,
+                              const double* gx_t1, const double* gv_t1, double* gx_t, double* gv_t,
+                              double* gE, const jgs2_adjoint_opts* opts, void* stream,
+                              jgs2_adjoint_report* report);
+
+/* Replaces the per-tet Young's moduli ([T] host, caller order, > 0). mu and lam' follow at
+ * the tets' Poisson ratios. The cubature records keep the rest subspace computed for the
+ * earlier moduli: under the "asm" reading that changes only the rate, not the result. */
+jgs2_status jgs2_mesh_set_youngs(jgs2_mesh* mesh, const double* youngs);
+
 /* Allocation-free variant of jgs2_energy_gradient (the paper has no counterpart; this is a
  * service for callers that cannot allocate device memory while they run, such as a
  * real-time loop that must not wait on cudaMalloc, or a process whose device memory is

@@ -99,6 +99,8 @@ class Mesh:
         self.b = np.empty((T, 4, 3))
         self.b[:, 1:, :] = B
         self.b[:, 0, :] = -B.sum(axis=1)
+        self.youngs = np.asarray(youngs, dtype=np.float64)
+        self.poisson = np.asarray(poisson, dtype=np.float64)
         self.mu, self.lp = lame(youngs, poisson)
         self.rho = np.asarray(density, dtype=np.float64)
         self.mass = np.zeros(V)

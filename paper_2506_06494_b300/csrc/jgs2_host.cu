@@ -15,6 +15,7 @@
 #include <map>
 
 #include "../../include/jgs2.h"
+#include "jgs2_adjoint.cuh"
 #include "jgs2_host.h"
 #include "jgs2_kernels.cuh"
 
@@ -45,7 +46,8 @@ static cudaError_t dalloc(X** p, size_t n) {
 template <typename T>
 void PrecBufs<T>::release() {
   cudaFree(tets); cudaFree(u); cudaFree(dz); cudaFree(D); cudaFree(DJ); cudaFree(ghr); cudaFree(mh2);
-  cudaFree(cub_p); cudaFree(cub_w); cudaFree(cub_u); cudaFree(pool_H); cudaFree(pool_G);
+  cudaFree(cub_p); cudaFree(cub_w); cudaFree(cub_u); cudaFree(pool_H); cudaFree(pool_G); cudaFree(pool_R);
+  cudaFree(a_lam); cudaFree(a_r); cudaFree(a_z); cudaFree(a_p); cudaFree(a_q); cudaFree(a_lin);
   *this = PrecBufs<T>();
 }
 template struct PrecBufs<float>;
@@ -56,7 +58,8 @@ Mesh::~Mesh() {
   f64.release();
   cudaFree(d_inc_off); cudaFree(d_inc_len); cudaFree(d_inc); cudaFree(d_pool_tet);
   cudaFree(d_xt); cudaFree(d_vt); cudaFree(d_perm); cudaFree(d_state); cudaFree(d_partial);
-  cudaFree(d_trace); cudaFree(d_xbuf); cudaFree(d_vbuf);
+  cudaFree(d_trace); cudaFree(d_xbuf); cudaFree(d_vbuf); cudaFree(d_tperm); cudaFree(d_youngs); cudaFree(d_coup);
+  cudaFree(d_adjsc);
   if (h_state) cudaFreeHost(h_state);
   for (cudaEvent_t e : events) cudaEventDestroy(e);
   cudaFree(d_planes); cudaFree(d_d0); cudaFree(d_bg); cudaFree(d_bH); cudaFree(d_faces); cudaFree(d_edges);
@@ -330,6 +333,10 @@ static jgs2_status ensure_device(Mesh* m) {
     if (!m->inc.empty()) CK(cudaMemcpy(m->d_inc, m->inc.data(), sizeof(int) * m->inc.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(m->d_perm, m->perm.data(), sizeof(int) * V, cudaMemcpyHostToDevice));
     CK(cudaMemset(m->d_state, 0, sizeof(StepState)));
+    CK(dalloc(&m->d_tperm, T));
+    CK(cudaMemcpy(m->d_tperm, m->tperm.data(), sizeof(int) * T, cudaMemcpyHostToDevice));
+    CK(dalloc(&m->d_youngs, T));
+    CK(cudaMemcpy(m->d_youngs, m->E.data(), sizeof(double) * T, cudaMemcpyHostToDevice));
     if (m->contact) {
       const int nF = (int)m->sfaces.size() / 3, nE = (int)m->sedges.size() / 2, nS = (int)m->sverts.size();
       const int np = (int)m->planes.size() / 4;
@@ -378,6 +385,25 @@ static jgs2_status ensure_device(Mesh* m) {
   return JGS2_OK;
 }
 
+// Host copy of the tet records in internal order (F(x_t) is filled per step on the device).
+template <typename T>
+static void tet_records(const Mesh* m, std::vector<TetRec<T>>& rec) {
+  rec.resize(m->T);
+  for (int ti = 0; ti < m->T; ++ti) {
+    const int t = m->tperm[ti];
+    TetRec<T>& r = rec[ti];
+    for (int a = 0; a < 4; ++a) r.v[a] = m->iperm[m->tets_c[4 * (size_t)t + a]];
+    for (int q = 0; q < 9; ++q) {
+      r.B[q] = T(m->B[9 * (size_t)t + q]);
+      r.Ft[q] = T(q % 4 == 0 ? 1.0 : 0.0);
+    }
+    r.vol = T(m->vol[t]);
+    r.mu = T(m->mu[t]);
+    r.lp = T(m->lp[t]);
+    r.mq = T(m->rho[t] * m->vol[t] / 4.0);
+  }
+}
+
 template <typename T>
 static jgs2_status ensure_prec(Mesh* m) {
   jgs2_status ds = ensure_device(m);
@@ -385,20 +411,8 @@ static jgs2_status ensure_prec(Mesh* m) {
   PrecBufs<T>& b = bufs<T>(m);
   if (!b.ready) {
     const int V = m->V, T_ = m->T;
-    std::vector<TetRec<T>> rec(T_);
-    for (int ti = 0; ti < T_; ++ti) {
-      const int t = m->tperm[ti];
-      TetRec<T>& r = rec[ti];
-      for (int a = 0; a < 4; ++a) r.v[a] = m->iperm[m->tets_c[4 * (size_t)t + a]];
-      for (int q = 0; q < 9; ++q) {
-        r.B[q] = T(m->B[9 * (size_t)t + q]);
-        r.Ft[q] = T(q % 4 == 0 ? 1.0 : 0.0);
-      }
-      r.vol = T(m->vol[t]);
-      r.mu = T(m->mu[t]);
-      r.lp = T(m->lp[t]);
-      r.mq = T(m->rho[t] * m->vol[t] / 4.0);
-    }
+    std::vector<TetRec<T>> rec;
+    tet_records<T>(m, rec);
     std::vector<T> mh2(V, T(0));
     for (int i = 0; i < m->Vf; ++i) mh2[i] = T(m->mass[m->perm[i]] / (m->h * m->h));
     CK(dalloc(&b.tets, T_));
@@ -431,6 +445,8 @@ static jgs2_status ensure_prec(Mesh* m) {
     CK(dalloc(&b.cub_u, nc * 36 * Vf));
     CK(dalloc(&b.pool_H, (size_t)m->nP * kPackedH));
     CK(dalloc(&b.pool_G, (size_t)m->nP * 12));
+    cudaFree(b.pool_R);
+    CK(dalloc(&b.pool_R, (size_t)m->nP * 36));
     CK(cudaMemcpy(b.cub_p, p.data(), sizeof(int32_t) * p.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(b.cub_w, w.data(), sizeof(T) * w.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(b.cub_u, u.data(), sizeof(T) * u.size(), cudaMemcpyHostToDevice));
@@ -466,6 +482,7 @@ static DevMesh<T> dev_view(Mesh* m) {
   d.pool_tet = m->d_pool_tet;
   d.pool_H = b.pool_H;
   d.pool_G = b.pool_G;
+  d.pool_R = b.pool_R;
   d.xt = m->d_xt;
   d.vt = m->d_vt;
   d.perm = m->d_perm;
@@ -935,6 +952,144 @@ jgs2_status contact_pairs(Mesh* m, const double* xt, const double* x, double rad
   return JGS2_OK;
 }
 
+// New Young's moduli (caller tet order): mu, lam' and the device records are updated. The
+// cubature records keep the rest subspace of the old moduli (it only shapes the rate).
+jgs2_status set_youngs(Mesh* m, const double* E) {
+  if (!m || !E) return fail(JGS2_EINVAL, "null argument");
+  for (int t = 0; t < m->T; ++t)
+    if (!(E[t] > 0.0) || !std::isfinite(E[t])) return fail(JGS2_EINVAL, "Young's modulus must be positive");
+  for (int t = 0; t < m->T; ++t) {
+    m->E[t] = E[t];
+    const double nu = m->nu[t];
+    m->mu[t] = E[t] / (2.0 * (1.0 + nu));
+    m->lp[t] = E[t] * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)) + m->mu[t];
+  }
+  if (m->device_ready) CK(cudaMemcpy(m->d_youngs, m->E.data(), sizeof(double) * m->T, cudaMemcpyHostToDevice));
+  if (m->f32.ready) {
+    std::vector<TetRec<float>> rec;
+    tet_records<float>(m, rec);
+    CK(cudaMemcpy(m->f32.tets, rec.data(), sizeof(TetRec<float>) * m->T, cudaMemcpyHostToDevice));
+  }
+  if (m->f64.ready) {
+    std::vector<TetRec<double>> rec;
+    tet_records<double>(m, rec);
+    CK(cudaMemcpy(m->f64.tets, rec.data(), sizeof(TetRec<double>) * m->T, cudaMemcpyHostToDevice));
+  }
+  return JGS2_OK;
+}
+
+template <typename T>
+static jgs2_status adjoint_impl(Mesh* m, const double* xt, const double* vt, const double* x1, const double* gx1,
+                                const double* gv1, double* gx, double* gv, double* gE, const jgs2_adjoint_opts* o,
+                                cudaStream_t s, jgs2_adjoint_report* rep) {
+  jgs2_status st = ensure_prec<T>(m);
+  if (st != JGS2_OK) return st;
+  PrecBufs<T>& b = bufs<T>(m);
+  const int Vf = m->Vf;
+  if (!b.a_lam) {
+    CK(dalloc(&b.a_lam, Vf));
+    CK(dalloc(&b.a_r, Vf));
+    CK(dalloc(&b.a_z, Vf));
+    CK(dalloc(&b.a_p, Vf));
+    CK(dalloc(&b.a_q, Vf));
+    CK(dalloc(&b.a_lin, 15 * (size_t)Vf));
+  }
+  if (!m->d_coup) {
+    CK(dalloc(&m->d_coup, 3 * (size_t)m->V));
+    CK(cudaMalloc(&m->d_adjsc, sizeof(AdjScalars)));
+  }
+  DevMesh<T> d = dev_view<T>(m);
+  const bool corr = o->correction != JGS2_CORR_OFF && m->nP > 0;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  const int nb = (m->V + 127) / 128, nbV = (Vf + 127) / 128, nbT = (m->T + 127) / 128;
+  k_setup_vertices<T><<<nb, 128, 0, s>>>(d, xt, vt, x1);
+  k_setup_tets<T><<<nbT, 128, 0, s>>>(d);
+  StepState init;
+  std::memset(&init, 0, sizeof(init));
+  init.max_sweeps = 1 << 30;
+  init.rel_tol = -1.0;
+  CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
+  // H_ii, R_i at x* (and the rotated cubature element Hessians)
+  if (corr) k_pool<T, true><<<m->nP, 128, 0, s>>>(d, m->d_state);
+  k_gather<T, true><<<nbV, 128, 0, s>>>(d, m->d_state, 0, m->d_partial, m->d_trace, 0);
+  if (corr)
+    k_lin_setup<T, true><<<nbV, 128, 0, s>>>(d, b.a_lin);
+  else
+    k_lin_setup<T, false><<<nbV, 128, 0, s>>>(d, b.a_lin);
+  AdjScalars* sc = static_cast<AdjScalars*>(m->d_adjsc);
+  AdjScalars sc0;
+  std::memset(&sc0, 0, sizeof(sc0));
+  CK(cudaMemcpyAsync(sc, &sc0, sizeof(sc0), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(b.a_lam, 0, sizeof(Vec4<T>) * Vf, s));
+  k_adj_rhs<T><<<nbV, 128, 0, s>>>(d, gx1, gv1, b.a_r);
+  const int nbD = std::max(1, std::min(nbV, 148 * 8));
+  const double tol2 = o->rel_tol * o->rel_tol;
+  k_dots<T><<<nbD, 128, 0, s>>>(d, b.a_r, b.a_r, b.a_r, b.a_r, m->d_partial, sc, 2, tol2, o->max_iters);
+  auto precond = [&]() {
+    if (corr) {
+      k_lin_pool<T><<<(m->nP * 12 + 127) / 128, 128, 0, s>>>(d, b.a_r, sc);
+      k_lin_precond<T, true><<<nbV, 128, 0, s>>>(d, b.a_lin, b.a_r, b.a_z, sc);
+    } else {
+      k_lin_precond<T, false><<<nbV, 128, 0, s>>>(d, b.a_lin, b.a_r, b.a_z, sc);
+    }
+  };
+  precond();
+  CK(cudaMemcpyAsync(b.a_p, b.a_z, sizeof(Vec4<T>) * Vf, cudaMemcpyDeviceToDevice, s));
+  AdjScalars hs;
+  const int every = std::max(1, o->check_every);
+  for (int it = 0; it < o->max_iters; ++it) {
+    k_hv<T><<<nbV, 128, 0, s>>>(d, b.a_p, b.a_q, sc);
+    k_dots<T><<<nbD, 128, 0, s>>>(d, b.a_p, b.a_q, b.a_r, b.a_p, m->d_partial, sc, 0, tol2, o->max_iters);
+    k_axpy2<T><<<nbV, 128, 0, s>>>(d, b.a_lam, b.a_r, b.a_p, b.a_q, sc);
+    precond();
+    k_dots<T><<<nbD, 128, 0, s>>>(d, b.a_z, b.a_q, b.a_r, b.a_r, m->d_partial, sc, 1, tol2, o->max_iters);
+    k_pupdate<T><<<nbV, 128, 0, s>>>(d, b.a_p, b.a_z, sc);
+    CK(cudaGetLastError());
+    if ((it + 1) % every == 0) {
+      CK(cudaMemcpyAsync(&hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (hs.done) break;
+    }
+  }
+  CK(cudaMemsetAsync(m->d_coup, 0, sizeof(double) * 3 * m->V, s));
+  k_adj_tets<T><<<nbT, 128, 0, s>>>(d, b.a_lam, m->d_tperm, m->d_youngs, m->d_coup, gE);
+  k_adj_out<T><<<nb, 128, 0, s>>>(d, b.a_lam, m->d_coup, gx1, gv1, gx, gv);
+  CK(cudaEventRecord(e1, s));
+  CK(cudaMemcpyAsync(&hs, sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const bool conv = hs.rr0 == 0.0 || hs.rr <= tol2 * hs.rr0;
+  if (rep) {
+    rep->iters = hs.iters;
+    rep->converged = conv ? 1 : 0;
+    rep->rel_residual = hs.rr0 > 0.0 ? std::sqrt(hs.rr / hs.rr0) : 0.0;
+    rep->ms = ms;
+  }
+  if (hs.done == 2) return fail(JGS2_ENONSPD, "Hessian not positive definite along a search direction");
+  if (!conv) return fail(JGS2_ENOTCONVERGED, "adjoint solve reached max_iters before rel_tol");
+  return JGS2_OK;
+}
+
+jgs2_status step_adjoint(Mesh* m, const double* xt, const double* vt, const double* x1, const double* gx1,
+                         const double* gv1, double* gx, double* gv, double* gE, const jgs2_adjoint_opts* o,
+                         void* stream, jgs2_adjoint_report* rep) {
+  if (!m || !xt || !vt || !x1 || !gx1 || !gv1 || !gx || !gv || !gE || !o) return fail(JGS2_EINVAL, "null argument");
+  if (m->contact) return fail(JGS2_EINVAL, "the adjoint does not include contact terms");
+  if (o->max_iters < 1 || !(o->rel_tol > 0.0)) return fail(JGS2_EINVAL, "bad adjoint options");
+  if (o->correction != JGS2_CORR_OFF && m->n_cub == 0)
+    return fail(JGS2_ENOTPRECOMPUTED, "corrected preconditioner requested before a precompute");
+  cudaStream_t s = (cudaStream_t)stream;
+  return o->precision == JGS2_FP64 ? adjoint_impl<double>(m, xt, vt, x1, gx1, gv1, gx, gv, gE, o, s, rep)
+                                   : adjoint_impl<float>(m, xt, vt, x1, gx1, gv1, gx, gv, gE, o, s, rep);
+}
+
 }  // namespace jgs2
 
 // ------------------------------------------------------------------ C ABI
@@ -1044,6 +1199,26 @@ jgs2_status jgs2_energy_gradient(jgs2_mesh* mesh, const double* x_t, const doubl
 jgs2_status jgs2_contact_pairs(jgs2_mesh* mesh, const double* x_t, const double* x, double radius, int32_t* out,
                                int32_t cap, int32_t* n_out, void* stream) {
   return contact_pairs(reinterpret_cast<Mesh*>(mesh), x_t, x, radius, out, cap, n_out, stream);
+}
+
+void jgs2_adjoint_opts_default(jgs2_adjoint_opts* o) {
+  if (!o) return;
+  o->max_iters = 5000;
+  o->rel_tol = 1e-6;
+  o->precision = JGS2_FP64;
+  o->correction = JGS2_CORR_OFF;
+  o->check_every = 32;
+}
+
+jgs2_status jgs2_step_adjoint(jgs2_mesh* mesh, const double* x_t, const double* v_t, const double* x_t1,
+                              const double* gx_t1, const double* gv_t1, double* gx_t, double* gv_t, double* gE,
+                              const jgs2_adjoint_opts* opts, void* stream, jgs2_adjoint_report* report) {
+  return step_adjoint(reinterpret_cast<Mesh*>(mesh), x_t, v_t, x_t1, gx_t1, gv_t1, gx_t, gv_t, gE, opts, stream,
+                      report);
+}
+
+jgs2_status jgs2_mesh_set_youngs(jgs2_mesh* mesh, const double* youngs) {
+  return set_youngs(reinterpret_cast<Mesh*>(mesh), youngs);
 }
 
 void jgs2_mesh_destroy(jgs2_mesh* mesh) { delete reinterpret_cast<Mesh*>(mesh); }

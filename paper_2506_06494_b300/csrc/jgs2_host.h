@@ -25,6 +25,10 @@ struct PrecBufs {
   T* cub_u = nullptr;
   T* pool_H = nullptr;
   T* pool_G = nullptr;
+  T* pool_R = nullptr;
+  // adjoint workspace
+  Vec4<T>*a_lam = nullptr, *a_r = nullptr, *a_z = nullptr, *a_p = nullptr, *a_q = nullptr;
+  T* a_lin = nullptr;
   void release();
 };
 
@@ -52,6 +56,10 @@ struct Mesh {
   int32_t *d_inc_off = nullptr, *d_inc_len = nullptr, *d_inc = nullptr, *d_pool_tet = nullptr, *d_perm = nullptr;
   double *d_xt = nullptr, *d_vt = nullptr, *d_partial = nullptr, *d_trace = nullptr;
   double *d_xbuf = nullptr, *d_vbuf = nullptr;
+  int32_t* d_tperm = nullptr;    // internal -> caller tet
+  double* d_youngs = nullptr;    // caller tet order
+  double* d_coup = nullptr;      // [3V] adjoint coupling of pinned vertices
+  void* d_adjsc = nullptr;       // AdjScalars
   StepState* d_state = nullptr;
   StepState* h_state = nullptr;
   std::vector<cudaEvent_t> events;  // pooled profiling events
@@ -77,6 +85,7 @@ struct Mesh {
 
 jgs2_status fail(jgs2_status s, const std::string& msg);
 jgs2_status precompute(Mesh* m, const jgs2_precompute_opts* o);
+jgs2_status set_youngs(Mesh* m, const double* youngs);
 // FP64 device view if the mesh's device buffers already exist (never allocates).
 bool dev_view_f64_if_ready(Mesh* m, DevMesh<double>* out);
 jgs2_status set_cubature(Mesh* m, int n_cub, const std::vector<int>& elem_int, const std::vector<double>& w,

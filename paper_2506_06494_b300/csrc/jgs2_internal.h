@@ -108,6 +108,7 @@ struct DevMesh {
   const int32_t* pool_tet;  // [nP]
   T* pool_H;                // [nP][78]
   T* pool_G;                // [nP][12]
+  T* pool_R;                // [nP][4][9] corner rotations of the last pool pass
   double* xt;               // [V][3]
   double* vt;               // [V][3]
   const int32_t* perm;      // internal -> caller

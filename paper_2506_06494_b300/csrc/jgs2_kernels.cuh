@@ -481,6 +481,10 @@ __global__ void __launch_bounds__(128) k_pool(DevMesh<T> m, const StepState* __r
       for (int q = 0; q < 9; ++q) sR[wid][q] = R[q];
 #pragma unroll
       for (int i = 0; i < 3; ++i) sg[wid][i] = g[i];
+      if (m.pool_R != nullptr) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) m.pool_R[(size_t)p * 36 + 9 * wid + q] = R[q];
+      }
     }
   }
   // element quantities at x^k, shared by the block

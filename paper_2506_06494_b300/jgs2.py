@@ -51,6 +51,16 @@ class StepOpts(C.Structure):
                 ("record_trace", C.c_int32), ("profile", C.c_int32)]
 
 
+class AdjointOpts(C.Structure):
+    _fields_ = [("max_iters", C.c_int32), ("rel_tol", C.c_double), ("precision", C.c_int32),
+                ("correction", C.c_int32), ("check_every", C.c_int32)]
+
+
+class AdjointReport(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("rel_residual", C.c_double),
+                ("ms", C.c_double)]
+
+
 class StepReport(C.Structure):
     _fields_ = [("sweeps", C.c_int32), ("converged", C.c_int32), ("fallback", C.c_int32),
                 ("ls_rejects", C.c_int32), ("rel_residual", C.c_double), ("g0", C.c_double),
@@ -65,6 +75,7 @@ EXPORTS = ["jgs2_precompute_opts_default", "jgs2_step_opts_default", "jgs2_mesh_
            "jgs2_precompute", "jgs2_precompute_import", "jgs2_precompute_export",
            "jgs2_mesh_n_cub", "jgs2_step", "jgs2_step_host", "jgs2_sweeps",
            "jgs2_energy_gradient", "jgs2_energy_gradient_static", "jgs2_contact_pairs",
+           "jgs2_step_adjoint", "jgs2_adjoint_opts_default", "jgs2_mesh_set_youngs",
            "jgs2_mesh_destroy", "jgs2_last_error"]
 
 
@@ -91,11 +102,14 @@ def lib():
     L.jgs2_energy_gradient.argtypes = [P, P, P, P, P, P, P]
     L.jgs2_contact_pairs.argtypes = [P, P, P, C.c_double, P, C.c_int32, C.POINTER(C.c_int32), P]
     L.jgs2_contact_pairs.restype = C.c_int
+    L.jgs2_adjoint_opts_default.argtypes = [C.POINTER(AdjointOpts)]
+    L.jgs2_step_adjoint.argtypes = [P] * 9 + [C.POINTER(AdjointOpts), P, C.POINTER(AdjointReport)]
+    L.jgs2_mesh_set_youngs.argtypes = [P, P]
     L.jgs2_mesh_destroy.argtypes = [P]
     L.jgs2_last_error.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("jgs2_mesh_destroy", "jgs2_last_error", "jgs2_mesh_n_cub",
-                        "jgs2_precompute_opts_default", "jgs2_step_opts_default"):
+                        "jgs2_precompute_opts_default", "jgs2_step_opts_default", "jgs2_adjoint_opts_default"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -128,6 +142,14 @@ def step_opts(**kw) -> StepOpts:
 def precompute_opts(**kw) -> PrecomputeOpts:
     o = PrecomputeOpts()
     lib().jgs2_precompute_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def adjoint_opts(**kw) -> AdjointOpts:
+    o = AdjointOpts()
+    lib().jgs2_adjoint_opts_default(C.byref(o))
     for k, v in kw.items():
         setattr(o, k, v)
     return o
@@ -258,6 +280,25 @@ class Mesh:
         opts = opts or step_opts()
         _check(lib().jgs2_sweeps(self.handle, _dev(x_t), _dev(v_t), _dev(x_k), int(n), C.byref(opts),
                                  C.c_void_p(_stream_ptr(stream))))
+
+    def set_youngs(self, youngs):
+        E = np.ascontiguousarray(youngs, dtype=np.float64)
+        assert E.shape == (self.T,)
+        _check(lib().jgs2_mesh_set_youngs(self.handle, E.ctypes.data))
+
+    def step_adjoint(self, x_t, v_t, x_t1, gx_t1, gv_t1, gE=None, opts=None, stream=None):
+        """jgs2_step_adjoint on CUDA tensors; returns (gx_t, gv_t, gE, report). gE accumulates."""
+        import torch
+        gx = torch.empty_like(x_t)
+        gv = torch.empty_like(x_t)
+        if gE is None:
+            gE = torch.zeros(self.T, dtype=torch.float64, device=x_t.device)
+        rep = AdjointReport()
+        st = lib().jgs2_step_adjoint(self.handle, _dev(x_t), _dev(v_t), _dev(x_t1), _dev(gx_t1), _dev(gv_t1),
+                                     _dev(gx), _dev(gv), C.c_void_p(gE.data_ptr()), C.byref(opts or adjoint_opts()),
+                                     C.c_void_p(_stream_ptr(stream)), C.byref(rep))
+        _check(st, ok=(0, 5))
+        return gx, gv, gE, rep
 
     def energy_gradient(self, x_t, v_t, x, stream=None):
         import torch

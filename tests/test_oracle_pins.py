@@ -443,3 +443,63 @@ def test_no_contact_in_range_equals_plain_sweep(cube, cube_cub):
     a = sweep.run_sweeps(m, s.X, z, s.dt, cube_cub, 2)
     b = sweep.run_sweeps(mc, s.X, z, s.dt, cube_cub, 2)
     assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------- T11: adjoint
+
+from oracle import adjoint  # noqa: E402
+
+
+def _solve_tight(s, m, x_t, v_t):
+    """Full Newton with dense solves from x_t until the residual stops decreasing."""
+    z = fem.inertia_target(x_t, v_t, s.dt, s.gravity)
+    x = x_t.copy()
+    best = np.inf
+    for _ in range(40):
+        xn = newton.newton_step_dense(m, x, z, s.dt)
+        r = np.linalg.norm(fem.vertex_gradient(m, xn, z, s.dt)[m.free])
+        if r >= best:
+            break
+        x, best = xn, r
+    return x
+
+
+def test_adjoint_against_central_differences():
+    s = scenes.small_beam_scene(5, 3, 3, E=2e5, vel_sigma=0.05, seed=2)
+    T = s.n_tets
+    E0 = s.youngs * np.random.default_rng(1).uniform(0.5, 1.5, T)
+    mk = lambda E: fem.Mesh(s.X, s.tets, E, s.poisson, s.density, s.pinned)  # noqa: E731
+    m = mk(E0)
+    x_t = scenes.perturbed_state(s.X, s.pinned, 1e-4, seed=4)
+    v_t = s.v0
+    x1 = _solve_tight(s, m, x_t, v_t)
+    r = np.random.default_rng(7)
+    cx, cv = r.normal(size=x1.shape), r.normal(size=x1.shape)
+    loss = lambda x1_, xt_: float(np.sum(cx * x1_) + np.sum(cv * (x1_ - xt_) / s.dt))  # noqa: E731
+    gx, gv, gE = adjoint.step_adjoint(m, x_t, v_t, x1, cx, cv, s.dt)
+    rel = 1e-4
+    # Young's modulus of a few elements (central differences, h = 1e-4 relative)
+    for e in [0, 7, T // 2, T - 1]:
+        Ep, Em = E0.copy(), E0.copy()
+        Ep[e] *= 1 + rel
+        Em[e] *= 1 - rel
+        fd = (loss(_solve_tight(s, mk(Ep), x_t, v_t), x_t) - loss(_solve_tight(s, mk(Em), x_t, v_t), x_t)) / (2 * rel * E0[e])
+        assert abs(fd - gE[e]) <= 1e-4 * abs(fd) + 1e-6 * np.abs(gE).max()
+    # initial state: a free and a pinned vertex component, and a velocity component
+    free = np.nonzero(~s.pinned.astype(bool))[0]
+    pin = np.nonzero(s.pinned.astype(bool))[0]
+    for (arr_name, v, k) in [("x", free[5], 2), ("x", pin[1], 0), ("v", free[9], 1)]:
+        eps = 1e-7
+        if arr_name == "x":
+            xp, xm = x_t.copy(), x_t.copy()
+            xp[v, k] += eps
+            xm[v, k] -= eps
+            fd = (loss(_solve_tight(s, m, xp, v_t), xp) - loss(_solve_tight(s, m, xm, v_t), xm)) / (2 * eps)
+            ref = gx[v, k]
+        else:
+            vp, vm = v_t.copy(), v_t.copy()
+            vp[v, k] += eps
+            vm[v, k] -= eps
+            fd = (loss(_solve_tight(s, m, x_t, vp), x_t) - loss(_solve_tight(s, m, x_t, vm), x_t)) / (2 * eps)
+            ref = gv[v, k]
+        assert abs(fd - ref) <= 1e-4 * abs(fd) + 1e-7, (arr_name, v, k, fd, ref)
