@@ -141,6 +141,24 @@ void jgs2_step_opts_default(jgs2_step_opts* o);
  * and uploads everything to the current CUDA device. *out receives a new mesh. */
 jgs2_status jgs2_mesh_create(const jgs2_mesh_desc* desc, jgs2_mesh** out);
 
+/* Batch of independent scenes in one mesh (several small solids stepped together, each
+ * with its own stopping test). descs: n_scenes descriptions (host; contact must be 0, dt
+ * and gravity equal in all). The batch's caller vertex / tet order is the concatenation of
+ * the scenes' orders. jgs2_step then sweeps every scene in the same kernel launches and
+ * stops each scene at its own r_k <= rel_tol (or max_sweeps); the report gives the
+ * maximum sweeps and residual over the scenes and converged = 1 only if all converged.
+ * The chunk of check_every sweeps is captured once in a CUDA graph and replayed. */
+jgs2_status jgs2_mesh_create_batch(const jgs2_mesh_desc* descs, int32_t n_scenes, jgs2_mesh** out);
+/* Per-scene results of the last jgs2_step on a batch mesh (host arrays [n_scenes], each
+ * may be NULL). */
+jgs2_status jgs2_batch_report(const jgs2_mesh* mesh, int32_t* sweeps, int32_t* converged,
+                              double* rel_residual);
+/* Times a few sweeps of the state (x, v: device [V][3] double, read only) with the vertex
+ * kernels at 64, 128 and 256 threads per block and keeps the fastest for opts->precision;
+ * *block_size (may be NULL) receives the choice. */
+jgs2_status jgs2_autotune(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts,
+                          void* stream, int32_t* block_size);
+
 /* Offline stage (Secs. 5-6), host FP64: factorises the rest Hessian H_bar = M/h^2 + K_bar
  * of each distinct body once, computes A_i = (H_bar^{-1})_ii and the rows of
  * U_bar_i = H_bar^{-1} S_i^T A_i^{-1} (Eq. u) that the cubature needs, the lowest

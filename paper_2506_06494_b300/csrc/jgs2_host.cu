@@ -62,6 +62,11 @@ Mesh::~Mesh() {
   cudaFree(d_adjsc);
   if (h_state) cudaFreeHost(h_state);
   for (cudaEvent_t e : events) cudaEventDestroy(e);
+  if (graph) cudaGraphExecDestroy(graph);
+  if (gstream) cudaStreamDestroy(gstream);
+  for (cudaEvent_t e : gev)
+    if (e) cudaEventDestroy(e);
+  cudaFree(d_vscene); cudaFree(d_tscene); cudaFree(d_ndone); cudaFree(d_scenes); cudaFree(d_sacc);
   cudaFree(d_planes); cudaFree(d_d0); cudaFree(d_bg); cudaFree(d_bH); cudaFree(d_faces); cudaFree(d_edges);
   cudaFree(d_sverts); cudaFree(d_npairs); cudaFree(d_cflags); cudaFree(d_is_surf); cudaFree(d_pairs);
   cudaFree(d_dmin); cudaFree(d_lim); cudaFree(d_cub);
@@ -82,7 +87,7 @@ static uint64_t spread3(uint64_t x) {
 
 // ------------------------------------------------------------------ mesh create
 
-jgs2_status mesh_create(const jgs2_mesh_desc* d, Mesh** out) {
+jgs2_status mesh_create(const jgs2_mesh_desc* d, Mesh** out, const std::vector<int>* scene_of_vertex = nullptr) {
   if (!d || !out) return fail(JGS2_EINVAL, "null argument");
   *out = nullptr;
   const int V = d->n_vertices, T = d->n_tets;
@@ -158,6 +163,8 @@ jgs2_status mesh_create(const jgs2_mesh_desc* d, Mesh** out) {
   std::iota(m->perm.begin(), m->perm.end(), 0);
   std::stable_sort(m->perm.begin(), m->perm.end(), [&](int a, int b) {
     if (m->pinned[a] != m->pinned[b]) return m->pinned[a] < m->pinned[b];
+    if (scene_of_vertex && (*scene_of_vertex)[a] != (*scene_of_vertex)[b])
+      return (*scene_of_vertex)[a] < (*scene_of_vertex)[b];
     return key[a] < key[b];
   });
   m->iperm.resize(V);
@@ -373,6 +380,18 @@ static jgs2_status ensure_device(Mesh* m) {
       m->cub_bytes = std::max(b1, b2);
       CK(cudaMalloc(&m->d_cub, m->cub_bytes));
     }
+    if (m->n_scenes > 0) {
+      std::vector<int> vs(std::max(1, m->Vf)), ts(T);
+      for (int i = 0; i < m->Vf; ++i) vs[i] = m->vscene[m->perm[i]];
+      for (int ti = 0; ti < T; ++ti) ts[ti] = m->vscene[m->tets_c[4 * (size_t)m->tperm[ti]]];
+      CK(dalloc(&m->d_vscene, std::max(1, m->Vf)));
+      CK(dalloc(&m->d_tscene, T));
+      CK(dalloc(&m->d_scenes, m->n_scenes));
+      CK(dalloc(&m->d_sacc, (size_t)m->n_scenes * kSceneAcc));
+      CK(dalloc(&m->d_ndone, 1));
+      CK(cudaMemcpy(m->d_vscene, vs.data(), sizeof(int) * std::max(1, m->Vf), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(m->d_tscene, ts.data(), sizeof(int) * T, cudaMemcpyHostToDevice));
+    }
     m->device_ready = true;
   }
   if (m->pool_version != m->cub_version) {
@@ -517,6 +536,12 @@ static DevMesh<T> dev_view(Mesh* m) {
     c.lim = m->d_lim;
     c.flags = m->d_cflags;
   }
+  d.n_scenes = m->n_scenes;
+  d.v_scene = m->d_vscene;
+  d.t_scene = m->d_tscene;
+  d.scenes = m->d_scenes;
+  d.sacc = m->d_sacc;
+  d.n_done = m->d_ndone;
   d.inv_h2 = 1.0 / (m->h * m->h);
   d.h = m->h;
   for (int q = 0; q < 3; ++q) d.grav[q] = m->grav[q];
@@ -608,6 +633,38 @@ static jgs2_status contact_pass(Mesh* m, DevMesh<T>& d, cudaStream_t s, StepStat
   return JGS2_OK;
 }
 
+// k_gather / k_correct with a runtime block size (64, 128 or 256 threads)
+template <typename T, bool BATCH>
+static void launch_gather(DevMesh<T>& d, bool corr, int bs, cudaStream_t s, StepState* st, int k, double* partial,
+                          double* trace, int rec) {
+  const int Vf = d.Vf;
+#define JGS2_G(B)                                                                                  \
+  if (corr)                                                                                        \
+    k_gather<T, true, BATCH, B><<<(Vf + B - 1) / B, B, 0, s>>>(d, st, k, partial, trace, rec);     \
+  else                                                                                             \
+    k_gather<T, false, BATCH, B><<<(Vf + B - 1) / B, B, 0, s>>>(d, st, k, partial, trace, rec);
+  if (bs == 64) {
+    JGS2_G(64)
+  } else if (bs == 256) {
+    JGS2_G(256)
+  } else {
+    JGS2_G(128)
+  }
+#undef JGS2_G
+}
+
+template <typename T, bool BATCH>
+static void launch_correct(DevMesh<T>& d, int bs, cudaStream_t s, StepState* st, int k, double* partial,
+                           double* trace, int rec) {
+  const int Vf = d.Vf;
+  if (bs == 64)
+    k_correct<T, BATCH, 64><<<(Vf + 63) / 64, 64, 0, s>>>(d, st, k, partial, trace, rec);
+  else if (bs == 256)
+    k_correct<T, BATCH, 256><<<(Vf + 255) / 256, 256, 0, s>>>(d, st, k, partial, trace, rec);
+  else
+    k_correct<T, BATCH, 128><<<(Vf + 127) / 128, 128, 0, s>>>(d, st, k, partial, trace, rec);
+}
+
 // Launch bookkeeping of one step: counts per kernel kind and, when profiling, a CUDA
 // event pair around every launch (events are pooled per mesh).
 struct Launches {
@@ -689,15 +746,13 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t s, 
       L.end(id);
     }
     if (nbV > 0) {
+      const int bs = m->bs[sizeof(T) == 4 ? 1 : 0];
       id = L.begin(JGS2_K_GATHER);
-      if (corr)
-        k_gather<T, true><<<nbV, 128, 0, s>>>(d, m->d_state, k, m->d_partial, m->d_trace, o.record_trace);
-      else
-        k_gather<T, false><<<nbV, 128, 0, s>>>(d, m->d_state, k, m->d_partial, m->d_trace, o.record_trace);
+      launch_gather<T, false>(d, corr, bs, s, m->d_state, k, m->d_partial, m->d_trace, o.record_trace);
       L.end(id);
       if (corr) {
         id = L.begin(JGS2_K_CORRECT);
-        k_correct<T><<<nbV, 128, 0, s>>>(d, m->d_state, k, m->d_partial, m->d_trace, o.record_trace);
+        launch_correct<T, false>(d, bs, s, m->d_state, k, m->d_partial, m->d_trace, o.record_trace);
         L.end(id);
       }
     }
@@ -744,6 +799,79 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t s, 
   return JGS2_OK;
 }
 
+// Batch meshes: every scene runs its own sweeps and stopping test; a chunk of check_every
+// sweeps (all kernels of all scenes, one launch per kernel) is captured once in a CUDA
+// graph and replayed until every scene has stopped.
+template <typename T>
+static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs, Launches& L) {
+  DevMesh<T> d = dev_view<T>(m);
+  // the caller's stream may be the legacy default stream, which cannot be captured: the
+  // sweeps run on a private stream ordered after (and before) the caller's work
+  if (!m->gstream) {
+    CK(cudaStreamCreateWithFlags(&m->gstream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&m->gev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&m->gev[1], cudaEventDisableTiming));
+  }
+  cudaStream_t s = m->gstream;
+  CK(cudaEventRecord(m->gev[0], cs));
+  CK(cudaStreamWaitEvent(s, m->gev[0], 0));
+  const bool corr = o.correction != JGS2_CORR_OFF && m->nP > 0;
+  const int S = m->n_scenes;
+  const int nbV = (m->Vf + 127) / 128, nbT = (m->T + 127) / 128;
+  const int bs = m->bs[sizeof(T) == 4 ? 1 : 0];
+  const int chunk = std::max(1, o.check_every);
+  StepState init;
+  std::memset(&init, 0, sizeof(init));
+  init.max_sweeps = 1 << 30;
+  init.rel_tol = -1.0;
+  CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(m->d_scenes, 0, sizeof(SceneState) * S, s));
+  CK(cudaMemsetAsync(m->d_sacc, 0, sizeof(double) * kSceneAcc * S, s));
+  CK(cudaMemsetAsync(m->d_ndone, 0, sizeof(int32_t), s));
+  const long key = ((((long)(sizeof(T) == 4) * 3 + o.correction) * 2 + (o.line_search != 0)) * 512 + bs) * 4096 +
+                   chunk + (long)(o.max_sweeps) * 1000003L + (long)(o.rel_tol * 1e12);
+  auto sweep_once = [&]() {
+    if (corr) k_pool<T, true><<<m->nP, 128, 0, s>>>(d, m->d_state);
+    launch_gather<T, true>(d, corr, bs, s, m->d_state, 0, m->d_partial, m->d_trace, 0);
+    if (corr) launch_correct<T, true>(d, bs, s, m->d_state, 0, m->d_partial, m->d_trace, 0);
+    k_scene_finalize_main<<<(S + 127) / 128, 128, 0, s>>>(m->d_scenes, m->d_sacc, S, o.rel_tol, o.max_sweeps,
+                                                           corr ? 1 : 0, m->d_ndone);
+    if (o.line_search) {
+      if (corr)
+        k_energy_batch<T, 2><<<nbT + nbV, 128, 0, s>>>(d, nbT);
+      else
+        k_energy_batch<T, 1><<<nbT + nbV, 128, 0, s>>>(d, nbT);
+      k_scene_finalize_energy<<<(S + 127) / 128, 128, 0, s>>>(m->d_scenes, m->d_sacc, S, corr ? 2 : 1);
+    }
+    k_update_batch<T><<<nbV, 128, 0, s>>>(d);
+  };
+  if (m->graph_key != key) {
+    if (m->graph) cudaGraphExecDestroy(m->graph);
+    m->graph = nullptr;
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int q = 0; q < chunk; ++q) sweep_once();
+    CK(cudaStreamEndCapture(s, &g));
+    cudaError_t e = cudaGraphInstantiate(&m->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(JGS2_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    m->graph_key = key;
+  }
+  const int per_sweep = (corr ? 3 : 1) + 2 + (o.line_search ? 2 : 0);
+  int32_t done = 0;
+  for (int sw = 0; sw <= o.max_sweeps; sw += chunk) {
+    CK(cudaGraphLaunch(m->graph, s));
+    L.count[JGS2_K_GATHER] += chunk * per_sweep;
+    CK(cudaMemcpyAsync(&done, m->d_ndone, sizeof(done), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (done >= S) break;
+  }
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(m->gev[1], s));
+  CK(cudaStreamWaitEvent(cs, m->gev[1], 0));
+  return JGS2_OK;
+}
+
 static jgs2_status check_opts(const Mesh* m, const jgs2_step_opts* o) {
   if (!o) return fail(JGS2_EINVAL, "null options");
   if (o->max_sweeps < 0 || o->max_sweeps > 1000000) return fail(JGS2_EINVAL, "max_sweeps out of range");
@@ -774,7 +902,28 @@ static jgs2_status step_impl(Mesh* m, double* x, double* v, const jgs2_step_opts
   L.end(id);
   CK(cudaGetLastError());
   StepState* hs = m->h_state;
-  st = run_sweeps<T>(m, *o, s, o->max_sweeps, o->rel_tol, true, hs, L);
+  if (m->n_scenes > 0) {
+    st = run_sweeps_batch<T>(m, *o, s, L);
+    if (st != JGS2_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return st;
+    }
+    std::vector<SceneState> sc(m->n_scenes);
+    CK(cudaMemcpy(sc.data(), m->d_scenes, sizeof(SceneState) * m->n_scenes, cudaMemcpyDeviceToHost));
+    std::memset(hs, 0, sizeof(StepState));
+    hs->converged = 1;
+    for (auto& q : sc) {
+      hs->sweeps = std::max(hs->sweeps, q.sweeps);
+      hs->converged &= q.converged;
+      hs->fallback += q.fallback;
+      hs->ls_rejects += q.ls_rejects;
+      hs->r = std::max(hs->r, q.r);
+      if (q.status) hs->status = q.status;
+    }
+  } else {
+    st = run_sweeps<T>(m, *o, s, o->max_sweeps, o->rel_tol, true, hs, L);
+  }
   if (st != JGS2_OK) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -952,6 +1101,128 @@ jgs2_status contact_pairs(Mesh* m, const double* xt, const double* x, double rad
   return JGS2_OK;
 }
 
+// Several scenes in one mesh (scene-major vertex order), each with its own convergence.
+jgs2_status mesh_create_batch(const jgs2_mesh_desc* ds, int n, Mesh** out) {
+  if (!ds || n <= 0 || !out) return fail(JGS2_EINVAL, "bad batch arguments");
+  jgs2_mesh_desc all = ds[0];
+  std::vector<double> X, E, nu, rho;
+  std::vector<int> tets, scene;
+  std::vector<uint8_t> pin;
+  int V = 0;
+  for (int k = 0; k < n; ++k) {
+    const jgs2_mesh_desc& d = ds[k];
+    if (d.contact) return fail(JGS2_EINVAL, "batch meshes do not support contact");
+    if (d.dt != all.dt || d.gravity[0] != all.gravity[0] || d.gravity[1] != all.gravity[1] ||
+        d.gravity[2] != all.gravity[2])
+      return fail(JGS2_EINVAL, "all scenes of a batch must share dt and gravity");
+    if (d.n_vertices <= 0 || d.n_tets <= 0 || !d.rest_pos || !d.tets || !d.youngs || !d.poisson || !d.density)
+      return fail(JGS2_EINVAL, "bad scene " + std::to_string(k));
+    X.insert(X.end(), d.rest_pos, d.rest_pos + 3 * (size_t)d.n_vertices);
+    for (int q = 0; q < 4 * d.n_tets; ++q) {
+      if (d.tets[q] < 0 || d.tets[q] >= d.n_vertices) return fail(JGS2_EINVAL, "tet index out of range");
+      tets.push_back(d.tets[q] + V);
+    }
+    E.insert(E.end(), d.youngs, d.youngs + d.n_tets);
+    nu.insert(nu.end(), d.poisson, d.poisson + d.n_tets);
+    rho.insert(rho.end(), d.density, d.density + d.n_tets);
+    for (int v = 0; v < d.n_vertices; ++v) {
+      pin.push_back(d.pinned ? (d.pinned[v] ? 1 : 0) : 0);
+      scene.push_back(k);
+    }
+    V += d.n_vertices;
+  }
+  all.n_vertices = V;
+  all.n_tets = (int)E.size();
+  all.rest_pos = X.data();
+  all.tets = tets.data();
+  all.youngs = E.data();
+  all.poisson = nu.data();
+  all.density = rho.data();
+  all.pinned = pin.data();
+  all.contact = 0;
+  Mesh* m = nullptr;
+  jgs2_status st = mesh_create(&all, &m, &scene);
+  if (st != JGS2_OK) return st;
+  m->n_scenes = n;
+  m->vscene = scene;
+  *out = m;
+  return JGS2_OK;
+}
+
+jgs2_status batch_report(const Mesh* m, int32_t* sweeps, int32_t* converged, double* rel) {
+  if (!m || m->n_scenes <= 0) return fail(JGS2_EINVAL, "not a batch mesh");
+  if (!m->d_scenes) return fail(JGS2_EINVAL, "no step has run on this mesh");
+  std::vector<SceneState> sc(m->n_scenes);
+  CK(cudaMemcpy(sc.data(), m->d_scenes, sizeof(SceneState) * m->n_scenes, cudaMemcpyDeviceToHost));
+  for (int k = 0; k < m->n_scenes; ++k) {
+    if (sweeps) sweeps[k] = sc[k].sweeps;
+    if (converged) converged[k] = sc[k].converged;
+    if (rel) rel[k] = sc[k].r;
+  }
+  return JGS2_OK;
+}
+
+// Autotuner: times a few sweeps of the state (x, v) with k_gather / k_correct at 64, 128
+// and 256 threads per block and keeps the fastest for this precision.
+template <typename T>
+static jgs2_status autotune_impl(Mesh* m, double* x, double* v, const jgs2_step_opts* o, cudaStream_t s,
+                                 int32_t* chosen) {
+  jgs2_status st = ensure_prec<T>(m);
+  if (st != JGS2_OK) return st;
+  DevMesh<T> d = dev_view<T>(m);
+  const int nb = (m->V + 127) / 128;
+  const bool corr = o->correction != JGS2_CORR_OFF && m->nP > 0;
+  k_setup_vertices<T><<<nb, 128, 0, s>>>(d, x, v, nullptr);
+  k_setup_tets<T><<<(m->T + 127) / 128, 128, 0, s>>>(d);
+  StepState init;
+  std::memset(&init, 0, sizeof(init));
+  init.max_sweeps = 1 << 30;
+  init.rel_tol = -1.0;
+  CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
+  if (corr) k_pool<T, true><<<m->nP, 128, 0, s>>>(d, m->d_state);
+  const int cands[3] = {64, 128, 256};
+  float best = 1e30f;
+  int pick = 128;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int c : cands) {
+    for (int rep = 0; rep < 2; ++rep) {
+      launch_gather<T, false>(d, corr, c, s, m->d_state, 1, m->d_partial, m->d_trace, 0);
+      if (corr) launch_correct<T, false>(d, c, s, m->d_state, 1, m->d_partial, m->d_trace, 0);
+    }
+    CK(cudaEventRecord(e0, s));
+    for (int rep = 0; rep < 5; ++rep) {
+      launch_gather<T, false>(d, corr, c, s, m->d_state, 1, m->d_partial, m->d_trace, 0);
+      if (corr) launch_correct<T, false>(d, c, s, m->d_state, 1, m->d_partial, m->d_trace, 0);
+    }
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  m->bs[sizeof(T) == 4 ? 1 : 0] = pick;
+  m->graph_key = -1;
+  if (chosen) *chosen = pick;
+  return JGS2_OK;
+}
+
+jgs2_status autotune(Mesh* m, double* x, double* v, const jgs2_step_opts* o, void* stream, int32_t* chosen) {
+  if (!m || !x || !v) return fail(JGS2_EINVAL, "null argument");
+  jgs2_status st = check_opts(m, o);
+  if (st != JGS2_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  return o->precision == JGS2_FP64 ? autotune_impl<double>(m, x, v, o, s, chosen)
+                                   : autotune_impl<float>(m, x, v, o, s, chosen);
+}
+
 // New Young's moduli (caller tet order): mu, lam' and the device records are updated. The
 // cubature records keep the rest subspace of the old moduli (it only shapes the rate).
 jgs2_status set_youngs(Mesh* m, const double* E) {
@@ -1014,7 +1285,7 @@ static jgs2_status adjoint_impl(Mesh* m, const double* xt, const double* vt, con
   CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
   // H_ii, R_i at x* (and the rotated cubature element Hessians)
   if (corr) k_pool<T, true><<<m->nP, 128, 0, s>>>(d, m->d_state);
-  k_gather<T, true><<<nbV, 128, 0, s>>>(d, m->d_state, 0, m->d_partial, m->d_trace, 0);
+  k_gather<T, true, false, 128><<<nbV, 128, 0, s>>>(d, m->d_state, 0, m->d_partial, m->d_trace, 0);
   if (corr)
     k_lin_setup<T, true><<<nbV, 128, 0, s>>>(d, b.a_lin);
   else
@@ -1219,6 +1490,22 @@ jgs2_status jgs2_step_adjoint(jgs2_mesh* mesh, const double* x_t, const double* 
 
 jgs2_status jgs2_mesh_set_youngs(jgs2_mesh* mesh, const double* youngs) {
   return set_youngs(reinterpret_cast<Mesh*>(mesh), youngs);
+}
+
+jgs2_status jgs2_mesh_create_batch(const jgs2_mesh_desc* descs, int32_t n_scenes, jgs2_mesh** out) {
+  Mesh* m = nullptr;
+  jgs2_status s = mesh_create_batch(descs, n_scenes, &m);
+  if (out) *out = reinterpret_cast<jgs2_mesh*>(m);
+  return s;
+}
+
+jgs2_status jgs2_batch_report(const jgs2_mesh* mesh, int32_t* sweeps, int32_t* converged, double* rel_residual) {
+  return batch_report(reinterpret_cast<const Mesh*>(mesh), sweeps, converged, rel_residual);
+}
+
+jgs2_status jgs2_autotune(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts, void* stream,
+                          int32_t* block_size) {
+  return autotune(reinterpret_cast<Mesh*>(mesh), x, v, opts, stream, block_size);
 }
 
 void jgs2_mesh_destroy(jgs2_mesh* mesh) { delete reinterpret_cast<Mesh*>(mesh); }

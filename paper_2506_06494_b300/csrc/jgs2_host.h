@@ -63,6 +63,19 @@ struct Mesh {
   StepState* d_state = nullptr;
   StepState* h_state = nullptr;
   std::vector<cudaEvent_t> events;  // pooled profiling events
+  // batch meshes (several independent scenes in one mesh, each with its own convergence)
+  int n_scenes = 0;                   // 0: not a batch mesh
+  std::vector<int> vscene;            // caller vertex -> scene
+  int32_t *d_vscene = nullptr, *d_tscene = nullptr, *d_ndone = nullptr;
+  SceneState* d_scenes = nullptr;
+  double* d_sacc = nullptr;
+  // block size of k_gather / k_correct per precision (autotuned, default 128)
+  int bs[2] = {128, 128};
+  // captured sweep chunk of a batch step: key = (precision, correction, line search, bs, chunk)
+  cudaGraphExec_t graph = nullptr;
+  long graph_key = -1;
+  cudaStream_t gstream = nullptr;   // private stream the graph is captured on and replayed on
+  cudaEvent_t gev[2] = {nullptr, nullptr};
   // contact (Sec. 7): surface in internal vertex ids
   int contact = 0;
   double dhat = 0.0, kappa = 0.0, rc = 0.0, cell = 0.0;

@@ -88,6 +88,13 @@ struct ContactView {
   int32_t* flags = nullptr;      // [0] overflow, [1] intersection
 };
 
+// Per-scene state of a batch mesh (one slot per scene; a single mesh is not batched).
+struct SceneState {
+  int32_t done, converged, status, sweeps, k, fallback, ls_rejects, dir;
+  double g0, r, slope, slope_j, alpha;
+};
+constexpr int kSceneAcc = 16;  // per-scene FP64 sums: |g|^2, g.D_J, g.D, 12 line-search coefficients
+
 template <typename T>
 struct DevMesh {
   int V, Vf, T_, n_slices, nP, n_cub;
@@ -113,6 +120,12 @@ struct DevMesh {
   double* vt;               // [V][3]
   const int32_t* perm;      // internal -> caller
   ContactView c;            // IPC barrier data (c.on = 0: no contact)
+  int n_scenes;             // batch meshes: scenes, vertex/tet scene ids, per-scene state
+  const int32_t* v_scene;   // [Vf]
+  const int32_t* t_scene;   // [T]
+  SceneState* scenes;       // [n_scenes]
+  double* sacc;             // [n_scenes][kSceneAcc]
+  int32_t* n_done;          // scenes finished in this step
   double inv_h2;            // 1/h^2
   double h;
   double grav[3];

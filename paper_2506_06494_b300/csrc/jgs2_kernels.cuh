@@ -83,6 +83,24 @@ __device__ __forceinline__ bool last_block(uint32_t* ticket) {
   return is_last;
 }
 
+// Batch meshes: adds NV per-thread values into the per-scene sums of scene sc (-1: none).
+// A warp whose lanes share one scene reduces first and adds once.
+template <int NV>
+__device__ __forceinline__ void scene_reduce(const double (&v)[NV], int sc, double* sacc, int off) {
+  const int s0 = __shfl_sync(0xffffffffu, sc, 0);
+  if (__all_sync(0xffffffffu, sc == s0)) {
+    if (s0 < 0) return;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      const double x = warp_sum(v[j]);
+      if ((threadIdx.x & 31) == 0) atomicAdd(sacc + (size_t)s0 * kSceneAcc + off + j, x);
+    }
+  } else if (sc >= 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) atomicAdd(sacc + (size_t)sc * kSceneAcc + off + j, v[j]);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void load3(const Vec4<T>* a, int i, T (&o)[3]) {
   Vec4<T> q = a[i];
@@ -618,15 +636,17 @@ __device__ __forceinline__ void finalize_sweep(StepState* st, int k, double r2, 
 // the correction on, R_i = polar(F_i) (Eq. tilde_phi). Writes g, H, R as [18][Vf] for
 // phase 2 and the FP64 partial sums |g|^2 and g.D_J. Without the correction D = D_J and
 // this kernel closes the sweep's reduction.
-template <typename T, bool CORR>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_gather(DevMesh<T> m, StepState* st, int k,
-                                                   double* __restrict__ partial /* [3][grid] */,
-                                                   double* __restrict__ trace, int record) {
-  if (st->done) return;
+template <typename T, bool CORR, bool BATCH, int BS>
+__global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 1024 : 512) / BS)
+    k_gather(DevMesh<T> m, StepState* st, int k, double* __restrict__ partial /* [3][grid] */,
+             double* __restrict__ trace, int record) {
+  if (!BATCH && st->done) return;
   __shared__ double red[96];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[2] = {0.0, 0.0};  // |g|^2, g.D_J
-  if (i < m.Vf) {
+  const int sc = (BATCH && i < m.Vf) ? m.v_scene[i] : -1;
+  const bool active = i < m.Vf && (!BATCH || !m.scenes[sc].done);
+  if (active) {
     T g[3], H[6], Fs[9], W;
     gather_vertex(m, i, g, H, Fs, W);
     T ui[3], dz[3];
@@ -677,6 +697,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_gather(DevMesh<
     acc[0] = double(g[0]) * double(g[0]) + double(g[1]) * double(g[1]) + double(g[2]) * double(g[2]);
     acc[1] = double(g[0]) * double(dj[0]) + double(g[1]) * double(dj[1]) + double(g[2]) * double(dj[2]);
   }
+  if (BATCH) {
+    scene_reduce<2>(acc, active ? sc : -1, m.sacc, 0);
+    return;
+  }
   block_sum<2>(acc, red);
   if (threadIdx.x == 0) {
     partial[blockIdx.x] = acc[0];
@@ -692,16 +716,18 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_gather(DevMesh<
 // Sweep phase 2, thread per free vertex: the cubature sums H~_i, g~_i (Eq. cubature) from
 // the rotated pool element data, the 3x3 solve of Eq. reduced_local, D_i, and g.D. The
 // last block closes the sweep's reduction with phase 1's partial sums.
-template <typename T>
-__global__ void __launch_bounds__(128) k_correct(DevMesh<T> m, StepState* st, int k,
-                                                 double* __restrict__ partial /* [3][grid] */,
-                                                 double* __restrict__ trace, int record) {
-  if (st->done) return;
+template <typename T, bool BATCH, int BS>
+__global__ void __launch_bounds__(BS) k_correct(DevMesh<T> m, StepState* st, int k,
+                                                double* __restrict__ partial /* [3][grid] */,
+                                                double* __restrict__ trace, int record) {
+  if (!BATCH && st->done) return;
   __shared__ double red[96];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[1] = {0.0};
   int fb = 0;
-  if (i < m.Vf) {
+  const int sc = (BATCH && i < m.Vf) ? m.v_scene[i] : -1;
+  const bool active = i < m.Vf && (!BATCH || !m.scenes[sc].done);
+  if (active) {
     const T* o = m.ghr + i;
     const size_t S = m.Vf;
     T g[3], H[6], R[9];
@@ -775,6 +801,11 @@ __global__ void __launch_bounds__(128) k_correct(DevMesh<T> m, StepState* st, in
     Vec4<T> dv{d[0], d[1], d[2], T(0)};
     m.D[i] = dv;
     acc[0] = double(g[0]) * double(d[0]) + double(g[1]) * double(d[1]) + double(g[2]) * double(d[2]);
+  }
+  if (BATCH) {
+    if (fb) atomicAdd(&m.scenes[sc].fallback, 1);
+    scene_reduce<1>(acc, active ? sc : -1, m.sacc, 2);
+    return;
   }
   if (__syncthreads_or(fb)) {
     const int nfb = __syncthreads_count(fb);
@@ -942,6 +973,153 @@ __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st,
     st->alpha = alpha;
     st->dir = dir;
   }
+}
+
+// Batch meshes: the same energy-change coefficients, summed per scene (thread per tet in
+// blocks [0, tet_blocks), thread per free vertex after; no contact).
+template <typename T, int ND>
+__global__ void __launch_bounds__(128) k_energy_batch(DevMesh<T> m, int tet_blocks) {
+  constexpr int NC = 6 * ND;
+  double acc[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) acc[j] = 0.0;
+  int sc = -1;
+  if ((int)blockIdx.x < tet_blocks) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m.T_) {
+      sc = m.t_scene[t];
+      if (!m.scenes[sc].done) {
+        const TetRec<T> r = m.tets[t];
+        T F[9], C[9], dF[9], c[6];
+        tet_F(r, m.u, F);
+        cofactor(F, C);
+        const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
+        tet_dF(r, m.D, m.Vf, dF);
+        tet_dpsi_poly(r, F, C, J, dF, c);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc[j] = double(c[j]);
+        if (ND == 2) {
+          tet_dF(r, m.DJ, m.Vf, dF);
+          tet_dpsi_poly(r, F, C, J, dF, c);
+#pragma unroll
+          for (int j = 0; j < 6; ++j) acc[6 + j] = double(c[j]);
+        }
+      } else {
+        sc = -1;
+      }
+    }
+  } else {
+    const int v = (blockIdx.x - tet_blocks) * blockDim.x + threadIdx.x;
+    if (v < m.Vf) {
+      sc = m.v_scene[v];
+      if (!m.scenes[sc].done) {
+        T uv[3], dz[3], d[3];
+        load3(m.u, v, uv);
+        load3(m.dz, v, dz);
+        const double mh = double(m.mh2[v]);
+#pragma unroll
+        for (int dir = 0; dir < ND; ++dir) {
+          load3(dir == 0 ? m.D : m.DJ, v, d);
+          double dd = 0.0, de = 0.0;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            dd += double(d[q]) * double(d[q]);
+            de += double(d[q]) * (double(uv[q]) - double(dz[q]));
+          }
+          acc[dir * 6 + 0] = mh * de;
+          acc[dir * 6 + 1] = 0.5 * mh * dd;
+        }
+      } else {
+        sc = -1;
+      }
+    }
+  }
+  scene_reduce<NC>(acc, sc, m.sacc, 3);
+}
+
+// Batch meshes, thread per scene: residual bookkeeping of the sweep (reading R9) from the
+// per-scene sums, then clear them.
+static __global__ void k_scene_finalize_main(SceneState* scenes, double* sacc, int n, double rel_tol, int max_sweeps,
+                                      int corr, int32_t* n_done) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  SceneState& S = scenes[s];
+  double* a = sacc + (size_t)s * kSceneAcc;
+  if (!S.done) {
+    const int k = S.k;
+    const double gn = sqrt(a[0]);
+    if (k == 0) S.g0 = gn;
+    const double r = S.g0 > 0.0 ? gn / S.g0 : 0.0;
+    S.r = r;
+    S.slope_j = a[1];
+    S.slope = corr ? a[2] : a[1];
+    S.alpha = 1.0;
+    S.dir = 0;
+    bool fin = false;
+    if (!isfinite(r) || !isfinite(S.slope)) {
+      S.status = 6;
+      fin = true;
+    } else if (r <= rel_tol || S.g0 == 0.0) {
+      S.converged = 1;
+      fin = true;
+    } else if (k >= max_sweeps) {
+      fin = true;
+    }
+    if (fin) {
+      S.done = 1;
+      S.sweeps = k;
+      atomicAdd(n_done, 1);
+    } else {
+      S.k = k + 1;
+    }
+  }
+  a[0] = a[1] = a[2] = 0.0;
+}
+
+// Batch meshes, thread per scene: Armijo choice from the per-scene polynomial sums.
+static __global__ void k_scene_finalize_energy(SceneState* scenes, double* sacc, int n, int nd) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  SceneState& S = scenes[s];
+  double* cf = sacc + (size_t)s * kSceneAcc + 3;
+  if (!S.done) {
+    double alpha = 0.0;
+    int dir = 0;
+    bool ok = false;
+    for (int dd = 0; dd < nd && !ok; ++dd) {
+      const double slope = dd == 0 ? S.slope : S.slope_j;
+      for (int j = 0; j < kLsTrials; ++j) {
+        const double a = 1.0 / double(1 << j);
+        const double* c = cf + 6 * dd;
+        const double dE = a * (c[0] + a * (c[1] + a * (c[2] + a * (c[3] + a * (c[4] + a * c[5])))));
+        if (dE <= 1e-4 * a * slope) {
+          alpha = a;
+          dir = dd;
+          ok = true;
+          break;
+        }
+      }
+    }
+    if (!ok) S.ls_rejects += 1;
+    S.alpha = alpha;
+    S.dir = dir;
+  }
+  for (int j = 0; j < 12; ++j) cf[j] = 0.0;
+}
+
+template <typename T>
+__global__ void k_update_batch(DevMesh<T> m) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.Vf) return;
+  const SceneState& S = m.scenes[m.v_scene[i]];
+  if (S.done) return;
+  const T a = T(S.alpha);
+  Vec4<T> u = m.u[i];
+  const Vec4<T> d = S.dir ? m.DJ[i] : m.D[i];
+  u.x += a * d.x;
+  u.y += a * d.y;
+  u.z += a * d.z;
+  m.u[i] = u;
 }
 
 template <typename T>

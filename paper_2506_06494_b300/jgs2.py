@@ -76,6 +76,7 @@ EXPORTS = ["jgs2_precompute_opts_default", "jgs2_step_opts_default", "jgs2_mesh_
            "jgs2_mesh_n_cub", "jgs2_step", "jgs2_step_host", "jgs2_sweeps",
            "jgs2_energy_gradient", "jgs2_energy_gradient_static", "jgs2_contact_pairs",
            "jgs2_step_adjoint", "jgs2_adjoint_opts_default", "jgs2_mesh_set_youngs",
+           "jgs2_mesh_create_batch", "jgs2_batch_report", "jgs2_autotune",
            "jgs2_mesh_destroy", "jgs2_last_error"]
 
 
@@ -105,6 +106,9 @@ def lib():
     L.jgs2_adjoint_opts_default.argtypes = [C.POINTER(AdjointOpts)]
     L.jgs2_step_adjoint.argtypes = [P] * 9 + [C.POINTER(AdjointOpts), P, C.POINTER(AdjointReport)]
     L.jgs2_mesh_set_youngs.argtypes = [P, P]
+    L.jgs2_mesh_create_batch.argtypes = [C.POINTER(MeshDesc), C.c_int32, C.POINTER(P)]
+    L.jgs2_batch_report.argtypes = [P, P, P, P]
+    L.jgs2_autotune.argtypes = [P, P, P, C.POINTER(StepOpts), P, C.POINTER(C.c_int32)]
     L.jgs2_mesh_destroy.argtypes = [P]
     L.jgs2_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -169,41 +173,77 @@ def _dev(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _desc(X, tets, youngs, poisson, density, pinned, gravity, dt, planes, dhat, kappa, contact, keep):
+    arrs = [np.ascontiguousarray(X, dtype=np.float64),
+            np.ascontiguousarray(tets, dtype=np.int32),
+            np.ascontiguousarray(youngs, dtype=np.float64),
+            np.ascontiguousarray(poisson, dtype=np.float64),
+            np.ascontiguousarray(density, dtype=np.float64),
+            None if pinned is None else np.ascontiguousarray(pinned, dtype=np.uint8),
+            np.ascontiguousarray(np.zeros((0, 4)) if planes is None else planes, dtype=np.float64)]
+    keep.extend(arrs)
+    X, T, E, nu, rho, pin, pl = arrs
+    d = MeshDesc()
+    d.n_vertices = X.shape[0]
+    d.n_tets = T.shape[0]
+    d.rest_pos = _ptr(X, C.c_double)
+    d.tets = _ptr(T, C.c_int32)
+    d.youngs = _ptr(E, C.c_double)
+    d.poisson = _ptr(nu, C.c_double)
+    d.density = _ptr(rho, C.c_double)
+    d.pinned = _ptr(pin, C.c_uint8) if pin is not None else C.POINTER(C.c_uint8)()
+    for q in range(3):
+        d.gravity[q] = float(gravity[q])
+    d.dt = float(dt)
+    d.contact = int(contact)
+    d.n_planes = int(pl.shape[0])
+    d.planes = _ptr(pl, C.c_double)
+    d.dhat = float(dhat)
+    d.kappa = float(kappa)
+    return d
+
+
 class Mesh:
     """A tet mesh living on the current CUDA device (jgs2_mesh_create)."""
 
+    @classmethod
+    def batch(cls, scenes_list):
+        """Several independent scenes in one mesh (jgs2_mesh_create_batch)."""
+        self = cls.__new__(cls)
+        self._keep = []
+        descs = (MeshDesc * len(scenes_list))()
+        for k, s in enumerate(scenes_list):
+            descs[k] = _desc(s.X, s.tets, s.youngs, s.poisson, s.density, s.pinned, s.gravity, s.dt,
+                             None, s.dhat, s.kappa, 0, self._keep)
+        h = C.c_void_p()
+        _check(lib().jgs2_mesh_create_batch(descs, len(scenes_list), C.byref(h)))
+        self.handle = h
+        self.V = int(sum(s.n_vertices for s in scenes_list))
+        self.T = int(sum(s.n_tets for s in scenes_list))
+        self.n_scenes = len(scenes_list)
+        return self
+
+    def batch_report(self):
+        n = self.n_scenes
+        sw, cv, rr = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n)
+        _check(lib().jgs2_batch_report(self.handle, sw.ctypes.data, cv.ctypes.data, rr.ctypes.data))
+        return sw, cv, rr
+
+    def autotune(self, x, v, opts=None, stream=None):
+        bs = C.c_int32()
+        _check(lib().jgs2_autotune(self.handle, _dev(x), _dev(v), C.byref(opts or step_opts()),
+                                   C.c_void_p(_stream_ptr(stream)), C.byref(bs)))
+        return bs.value
+
     def __init__(self, X, tets, youngs, poisson, density, pinned=None, gravity=(0, 0, -9.8), dt=1 / 120,
                  planes=None, dhat=1e-3, kappa=1e5, contact=0):
-        self._keep = [np.ascontiguousarray(X, dtype=np.float64),
-                      np.ascontiguousarray(tets, dtype=np.int32),
-                      np.ascontiguousarray(youngs, dtype=np.float64),
-                      np.ascontiguousarray(poisson, dtype=np.float64),
-                      np.ascontiguousarray(density, dtype=np.float64),
-                      None if pinned is None else np.ascontiguousarray(pinned, dtype=np.uint8),
-                      np.ascontiguousarray(np.zeros((0, 4)) if planes is None else planes, dtype=np.float64)]
-        X, T, E, nu, rho, pin, pl = self._keep
-        d = MeshDesc()
-        d.n_vertices = X.shape[0]
-        d.n_tets = T.shape[0]
-        d.rest_pos = _ptr(X, C.c_double)
-        d.tets = _ptr(T, C.c_int32)
-        d.youngs = _ptr(E, C.c_double)
-        d.poisson = _ptr(nu, C.c_double)
-        d.density = _ptr(rho, C.c_double)
-        d.pinned = _ptr(pin, C.c_uint8) if pin is not None else C.POINTER(C.c_uint8)()
-        for q in range(3):
-            d.gravity[q] = float(gravity[q])
-        d.dt = float(dt)
-        d.contact = int(contact)
-        d.n_planes = int(pl.shape[0])
-        d.planes = _ptr(pl, C.c_double)
-        d.dhat = float(dhat)
-        d.kappa = float(kappa)
+        self._keep = []
+        d = _desc(X, tets, youngs, poisson, density, pinned, gravity, dt, planes, dhat, kappa, contact, self._keep)
         h = C.c_void_p()
         _check(lib().jgs2_mesh_create(C.byref(d), C.byref(h)))
         self.handle = h
-        self.V = int(X.shape[0])
-        self.T = int(T.shape[0])
+        self.V = int(d.n_vertices)
+        self.T = int(d.n_tets)
 
     @classmethod
     def from_scene(cls, s, contact=None):
