@@ -1,15 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of the JGS2 hot path: milliseconds per implicit-Euler time step to a 1e-4
-relative residual, JGS2 sweeps per second, and the main sweep kernel's fraction of the
-measured HBM bandwidth.
+relative residual (capped at --max-sweeps), JGS2 sweeps per second, and the dominant sweep
+kernel's fraction of the measured HBM bandwidth.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload spheres|beam|cube]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload spheres|beam|cube|batch]
     python bench.py --impl reference ...     # the FP64 CPU oracle on the host cores
 
-One step = one call of jgs2_step (all sweeps of the step: pool, main, line-search energy
-and update kernels plus the per-step setup) on inputs already resident in HBM. With N > 1
-(torchrun) every rank steps its own replica of the scene (the sweep does not shard across
-GPUs in this build); the reported time is the maximum over ranks.
+One step = one call of jgs2_step (every sweep of the step: contact pass, pool, gather,
+correct, line-search energy and update kernels plus the per-step setup) on inputs already
+resident in HBM. The default workload is ten voxel spheres (3.47M tets) in a box with the IPC
+barrier on. `batch` is 256 seeded voxel blobs of uneven size stepped together in one mesh
+(graph-captured sweep chunks, per-scene stopping). With N > 1 (torchrun) every rank steps
+its own replica (the sweep does not shard across GPUs); the time is the maximum over ranks
+and the value counts every rank's work.
 """
 from __future__ import annotations
 
@@ -27,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ms/step to 1e-4 rel. residual at 3.5M tets"
-KIND = ["k_pool", "k_gather", "k_correct", "k_energy", "k_update", "setup"]
+KIND = ["k_pool", "k_gather", "k_correct", "k_energy", "k_update", "setup", "contact"]
 
 
 def peaks():
@@ -39,16 +42,31 @@ def peaks():
         return 6400.0, "fallback"
 
 
-def build_scene(name, n_spheres=10):
+def build_scenes(args):
+    """(list of scenes, description, batch?)"""
     import scenes
-    if name == "spheres":
-        s = scenes.spheres_scene(n_spheres=n_spheres, contact=0)
-        return s, f"{n_spheres} voxel spheres r=0.1 m, 48 cells across, {s.n_tets:,} tets"
-    if name == "beam":
-        return scenes.beam_scene(), "20x20x100-vertex Kuhn beam 0.02x0.02x0.1 m, 214,434 tets"
-    if name == "cube":
-        return scenes.cube_scene(), "5x5x5-vertex Kuhn cube, 384 tets"
-    raise SystemExit(f"unknown workload {name}")
+    w = args.workload
+    if w == "spheres":
+        s = scenes.spheres_scene(n_spheres=args.n_spheres, contact=args.contact)
+        return [s], (f"{args.n_spheres} voxel spheres r=0.1 m, 48 cells across, {s.n_tets:,} tets, "
+                     f"box walls, IPC dhat=1e-3 {'on' if args.contact else 'off'}"), False
+    if w == "beam":
+        return [scenes.beam_scene()], "20x20x100-vertex Kuhn beam 0.02x0.02x0.1 m, 214,434 tets, E=1e7", False
+    if w == "cube":
+        return [scenes.cube_scene()], "5x5x5-vertex Kuhn cube, 384 tets", False
+    if w == "batch":
+        ss = [scenes.blob_scene(i, 1e3, 5e4) for i in range(args.n_scenes)]
+        T = sum(s.n_tets for s in ss)
+        return ss, (f"{args.n_scenes} seeded voxel blobs (1-6 spheres, 1k-50k tets each, {T:,} tets), "
+                    "E log-uniform 1e4-1e7, nu 0.3-0.48, bottom pinned"), True
+    raise SystemExit(f"unknown workload {w}")
+
+
+def concat(ss):
+    return (np.concatenate([s.X for s in ss]), np.concatenate([s.v0 for s in ss]),
+            np.concatenate([s.tets + o for s, o in zip(ss, np.cumsum([0] + [q.n_vertices for q in ss[:-1]]))]),
+            np.concatenate([s.youngs for s in ss]), np.concatenate([s.poisson for s in ss]),
+            np.concatenate([s.density for s in ss]), np.concatenate([s.pinned for s in ss]))
 
 
 def kernel_bytes(V_f, T, n_cub, fp_bytes=4):
@@ -116,41 +134,42 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(scene, sweeps_per_step, n_sample=48, seed=0):
+def cpu_baseline(ss, sweeps_per_step, n_sample=48, seed=0):
     """Oracle (FP64 numpy, one host thread) on a bounded sample: the per-vertex JGS2
     direction of n_sample free vertices, scaled to a full step (sweeps_per_step + 1 sweeps,
-    every free vertex)."""
+    every free vertex of every scene)."""
     from oracle import fem, local
     import scenes
-    s = scene
-    elem, w, u = scenes.random_cubature(s.X, s.tets, s.pinned, 4, seed=seed, w_max=0.5, u_sigma=0.2)
-    lm = local.LocalMesh(s.X, s.tets, s.youngs, s.poisson, s.density, s.pinned)
-    z = fem.inertia_target(s.X, s.v0, s.dt, s.gravity)
-    free = np.nonzero(~s.pinned.astype(bool))[0]
+    X, V0, tets, E, nu, rho, pin = concat(ss)
+    s = ss[0]
+    elem, w, u = scenes.random_cubature(X, tets, pin, 4, seed=seed, w_max=0.5, u_sigma=0.2)
+    lm = local.LocalMesh(X, tets, E, nu, rho, pin)
+    z = fem.inertia_target(X, V0, s.dt, s.gravity)
+    free = np.nonzero(~pin.astype(bool))[0]
     pick = np.random.default_rng(seed).choice(free, size=min(n_sample, len(free)), replace=False)
     t0 = time.perf_counter()
     for i in pick:
-        lm.direction(i, s.X, z, s.dt, elem[i], w[i], u[i])
+        lm.direction(i, X, z, s.dt, elem[i], w[i], u[i])
     per_vertex = (time.perf_counter() - t0) / len(pick)
     ms = per_vertex * len(free) * (sweeps_per_step + 1) * 1e3
     return {"value": ms, "unit": "ms/step", "cores": 1, "kind": "oracle",
-            "sample": f"oracle per-vertex JGS2 direction of {len(pick)} sampled free vertices "
-                      f"({per_vertex * 1e3:.1f} ms each), scaled x{len(free)} vertices x "
+            "sample": f"oracle per-vertex JGS2 direction (no contact terms) of {len(pick)} sampled free "
+                      f"vertices ({per_vertex * 1e3:.1f} ms each), scaled x{len(free)} vertices x "
                       f"{sweeps_per_step + 1:.0f} sweeps/step"}
 
 
 def run_reference(args, rank, world):
-    scene, desc = build_scene(args.workload, args.n_spheres)
-    out = {"impl": "reference", "metric": METRIC, "unit": "ms/step", "higher_is_better": False,
-           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload, "scene": desc, "cubature": args.cubature, "tets": scene.n_tets, "vertices": scene.n_vertices}}
     if rank != 0:
         return None
-    sweeps = args.ref_sweeps
+    ss, desc, _ = build_scenes(args)
+    T = sum(s.n_tets for s in ss)
+    out = {"impl": "reference", "metric": METRIC, "unit": "ms/step", "higher_is_better": False,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "scene": desc, "tets": T, "sweeps_per_step": args.ref_sweeps}}
     vals = []
     cb = None
     for _ in range(args.warmup + args.steps):
-        cb = cpu_baseline(scene, sweeps, n_sample=16)
+        cb = cpu_baseline(ss, args.ref_sweeps, n_sample=16)
         vals.append(cb["value"])
     v = float(np.median(vals[args.warmup:]))
     cb["value"] = v
@@ -160,28 +179,60 @@ def run_reference(args, rank, world):
     return out
 
 
+def split_cubature(elem, w, u, ss):
+    """Per-scene cubature records from a batch mesh's export (tet ids made scene-local)."""
+    out, vo, to = [], 0, 0
+    for s in ss:
+        e = elem[vo:vo + s.n_vertices]
+        out.append((np.where(e >= 0, e - to, -1), w[vo:vo + s.n_vertices], u[vo:vo + s.n_vertices]))
+        vo += s.n_vertices
+        to += s.n_tets
+    return out
+
+
+def timed_steps(mesh, x, v, opts, n, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    reps = []
+    for _ in range(n):
+        r = mesh.step(x, v, opts, stream)
+        reps.append((r.sweeps, r.converged, r.rel_residual, list(r.kernel_ms), list(r.kernel_launches),
+                     r.launches, r.fallback, r.ls_rejects))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), reps
+
+
 def run_jgs2(args, rank, world, local_rank):
     import torch
     import paper_2506_06494_b300 as p
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    scene, desc = build_scene(args.workload, args.n_spheres)
+    ss, desc, batch = build_scenes(args)
+    X, V0, tets, _, _, _, pin = concat(ss)
+    T = sum(s.n_tets for s in ss)
+    Vf = int((~pin.astype(bool)).sum())
     t0 = time.perf_counter()
-    mesh = p.Mesh.from_scene(scene)
+    mesh = p.Mesh.batch(ss) if batch else p.Mesh.from_scene(ss[0])
     if args.cubature == "precompute":
         mesh.precompute(n_cub=args.n_cub)
     else:
         # seeded synthetic records: same kernel work, no convergence meaning (profiling only)
         import scenes
-        mesh.precompute_import(*scenes.random_cubature(scene.X, scene.tets, scene.pinned, args.n_cub, seed=0,
-                                                       w_max=0.5, u_sigma=0.2))
+        mesh.precompute_import(*scenes.random_cubature(X, tets, pin, args.n_cub, seed=0, w_max=0.5, u_sigma=0.2))
     t_pre = time.perf_counter() - t0
     prec = p.FP32 if args.precision == "fp32" else p.FP64
     corr = {"asm": p.CORR_ASM, "elem": p.CORR_ELEM, "off": p.CORR_OFF}[args.correction]
-    opts = p.step_opts(precision=prec, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4, profile=1)
-    x = torch.tensor(scene.X, dtype=torch.float64, device=dev)
-    v = torch.tensor(scene.v0, dtype=torch.float64, device=dev)
+    opts = p.step_opts(precision=prec, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4,
+                       profile=0 if batch else 1)
+    x0 = torch.tensor(X, dtype=torch.float64, device=dev)
+    v0 = torch.tensor(V0, dtype=torch.float64, device=dev)
+    bs = mesh.autotune(x0, v0, opts)
+    x, v = x0.clone(), v0.clone()
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         mesh.step(x, v, opts, stream)
@@ -192,19 +243,13 @@ def run_jgs2(args, rank, world, local_rank):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     gidx = vis.split(",")[local_rank] if vis else str(local_rank)
     clocks = Clocks(gidx)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    reps = []
-    for _ in range(args.steps):
-        r = mesh.step(x, v, opts, stream)
-        reps.append((r.sweeps, r.converged, r.rel_residual, list(r.kernel_ms), list(r.kernel_launches),
-                     r.launches, r.fallback, r.ls_rejects))
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms_total, reps = timed_steps(mesh, x, v, opts, args.steps, stream)
     ck = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
+    scene_sweeps = None
+    if batch:
+        sw, cv, rr = mesh.batch_report()
+        scene_sweeps = {"min": int(sw.min()), "median": float(np.median(sw)), "max": int(sw.max()),
+                        "converged_scenes_last_step": int(cv.sum()), "max_rel_residual": float(rr.max())}
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -215,96 +260,151 @@ def run_jgs2(args, rank, world, local_rank):
     kms = np.sum([q[3] for q in reps], axis=0)
     kl = np.sum([q[4] for q in reps], axis=0)
     launches = int(sum(q[5] for q in reps))
-    ms_step = ms_total / args.steps
+    ms_step = ms_total / args.steps / world   # whole-job time per step: `world` replicas in parallel
     # end to end: host buffers through jgs2_step_host, copies inside the timed region
-    xh = x.cpu().numpy().copy()
-    vh = v.cpu().numpy().copy()
+    xh, vh = X.copy(), V0.copy()
     opts_e2e = p.step_opts(precision=prec, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
     n_e2e = 0 if args.no_e2e else args.steps
+    t0 = time.perf_counter()
     for _ in range(n_e2e):
         mesh.step_host(xh, vh, opts_e2e, stream)
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / max(n_e2e, 1) if n_e2e else None
-    # roofline of the dominant kernel by time share
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / max(n_e2e, 1) / world if n_e2e else None
     hbm, peak_kind = peaks()
     n_cub = args.n_cub if corr != p.CORR_OFF else 0
-    Vf = int((~scene.pinned.astype(bool)).sum())
     fpb = 4 if prec == p.FP32 else 8
-    kb = kernel_bytes(Vf, scene.n_tets, n_cub, fpb)
-    share = {KIND[q]: round(float(kms[q] / max(kms.sum(), 1e-12)), 4) for q in range(len(KIND))}
-    per_kernel = {}
-    for q, name in enumerate(KIND):
-        if name in kb and kl[q] > 0:
-            avg = kms[q] / kl[q]
-            per_kernel[name] = {"avg_launch_ms": round(float(avg), 5), "bytes_per_launch": kb[name],
-                                "GB_s": round(kb[name] / (avg * 1e-3) / 1e9, 1),
-                                "frac": round(kb[name] / (avg * 1e-3) / 1e9 / hbm, 4)}
-    dom = max(per_kernel, key=lambda n: share[n])
-    achieved = per_kernel[dom]["GB_s"]
+    kb = kernel_bytes(Vf, T, n_cub, fpb)
     out = {
         "metric": METRIC, "value": ms_step, "unit": "ms/step", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == p.FP32 else "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "scene": desc, "cubature": args.cubature, "tets": scene.n_tets, "vertices": scene.n_vertices,
-                   "free_vertices": Vf, "contact": False, "correction": args.correction, "line_search": True,
-                   "n_cub": args.n_cub, "rel_tol": 1e-4, "parallelism": f"replicas x{world}",
+        "config": {"workload": args.workload, "scene": desc, "cubature": args.cubature, "tets": T,
+                   "vertices": int(len(X)), "free_vertices": Vf,
+                   "contact": bool(args.contact) if args.workload == "spheres" else False,
+                   "correction": args.correction, "line_search": True, "n_cub": args.n_cub, "rel_tol": 1e-4,
+                   "max_sweeps": args.max_sweeps, "block_size": bs, "parallelism": f"replicas x{world}",
                    "l2": "per-sweep working set larger than L2 (126 MB); no flush"},
         "sweeps_per_step": float(sweeps.mean()), "sweeps_per_s": float(sweeps.sum() / (ms_total * 1e-3)),
         "converged_steps": int(sum(q[1] for q in reps)), "max_rel_residual": float(max(q[2] for q in reps)),
         "precompute_s": round(t_pre, 2),
-        "kernel_ms_per_step": {KIND[q]: round(float(kms[q] / args.steps), 4) for q in range(len(KIND))},
-        "kernel_share": share,
-        "kernels": per_kernel,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
-                     "bytes_per_launch": per_kernel[dom]["bytes_per_launch"],
-                     "avg_launch_ms": per_kernel[dom]["avg_launch_ms"],
-                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
         "e2e": {"value": e2e_ms, "unit": "ms/step", "h2d_bytes_per_step": int(xh.nbytes + vh.nbytes),
                 "d2h_bytes_per_step": int(xh.nbytes + vh.nbytes)},
         "gpu_launches": launches,
         "clocks": ck,
     }
+    if batch:
+        # kernels run inside CUDA graphs: the roofline is the whole sweep's algorithmic bytes
+        # over the time per sweep
+        per_sweep_ms = ms_total / max(sweeps.sum(), 1)
+        sweep_bytes = sum(b for k, b in kb.items() if corr != p.CORR_OFF or k != "k_correct")
+        gbs = sweep_bytes / (per_sweep_ms * 1e-3) / 1e9
+        out["scene_sweeps"] = scene_sweeps
+        out["roofline"] = {"bound": "hbm", "kernel": "sweep (gather+correct+energy+update, one graph chunk)",
+                           "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
+                           "traffic": None, "bytes_per_launch": sweep_bytes, "avg_launch_ms": round(per_sweep_ms, 5),
+                           "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        share = {KIND[q]: round(float(kms[q] / max(kms.sum(), 1e-12)), 4) for q in range(len(KIND))}
+        per_kernel = {}
+        for q, name in enumerate(KIND):
+            if name in kb and kl[q] > 0:
+                avg = kms[q] / kl[q]
+                per_kernel[name] = {"avg_launch_ms": round(float(avg), 5), "bytes_per_launch": kb[name],
+                                    "GB_s": round(kb[name] / (avg * 1e-3) / 1e9, 1),
+                                    "frac": round(kb[name] / (avg * 1e-3) / 1e9 / hbm, 4)}
+        dom = max(per_kernel, key=lambda n: share[n])
+        achieved = per_kernel[dom]["GB_s"]
+        out["kernel_ms_per_step"] = {KIND[q]: round(float(kms[q] / args.steps), 4) for q in range(len(KIND))}
+        out["kernel_launches_per_step"] = {KIND[q]: int(kl[q] // args.steps) for q in range(len(KIND))}
+        out["kernel_share"] = share
+        out["kernels"] = per_kernel
+        out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                           "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                           "bytes_per_launch": per_kernel[dom]["bytes_per_launch"],
+                           "avg_launch_ms": per_kernel[dom]["avg_launch_ms"],
+                           "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    if not args.no_compare:
+        out["comparisons"] = compare(args, p, mesh, ss, batch, x0, v0, stream, corr, prec)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(scene, float(sweeps.mean()))
+        out["cpu_baseline"] = cpu_baseline(ss, float(sweeps.mean()))
     return out if rank == 0 else None
+
+
+def compare(args, p, mesh, ss, batch, x0, v0, stream, corr, prec):
+    """The same step on the same GPU in the forms the method is measured against: the FP64
+    single-scene form and uncorrected Jacobi (one step each, CUDA events); for the batch, a
+    sequential FP64 loop over the scenes one mesh at a time."""
+    import torch
+    res = {}
+    if not batch:
+        for name, o in [("fp64_single_scene", p.step_opts(precision=p.FP64, correction=corr,
+                                                           max_sweeps=args.max_sweeps, rel_tol=1e-4)),
+                        ("jacobi_uncorrected", p.step_opts(precision=prec, correction=p.CORR_OFF,
+                                                           max_sweeps=args.max_sweeps, rel_tol=1e-4))]:
+            x, v = x0.clone(), v0.clone()
+            ms, reps = timed_steps(mesh, x, v, o, 1, stream)
+            res[name] = {"ms_per_step": round(ms, 3), "sweeps": int(reps[0][0]), "converged": int(reps[0][1]),
+                         "rel_residual": float(reps[0][2]), "ms_per_sweep": round(ms / max(reps[0][0], 1), 5)}
+        return res
+    elem, w, u, _ = mesh.precompute_export()
+    cubs = split_cubature(elem, w, u.reshape(len(elem), -1), ss)
+    o = p.step_opts(precision=p.FP64, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4)
+    tot, sweeps, conv = 0.0, [], 0
+    for s, c in zip(ss, cubs):
+        g = p.Mesh.from_scene(s)
+        g.precompute_import(*c)
+        x = torch.tensor(s.X, dtype=torch.float64, device=x0.device)
+        v = torch.tensor(s.v0, dtype=torch.float64, device=x0.device)
+        g.step(x.clone(), v.clone(), o, stream)   # first use: device buffers
+        ms, reps = timed_steps(g, x, v, o, 1, stream)
+        tot += ms
+        sweeps.append(reps[0][0])
+        conv += reps[0][1]
+        g.close()
+    res["fp64_per_scene_loop"] = {"ms_per_step": round(tot, 3), "scenes": len(ss), "converged_scenes": conv,
+                                  "sweeps_median": float(np.median(sweeps)), "sweeps_max": int(max(sweeps))}
+    return res
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="jgs2", choices=["jgs2", "reference"])
-    ap.add_argument("--workload", default="spheres", choices=["spheres", "beam", "cube"])
+    ap.add_argument("--workload", default="spheres", choices=["spheres", "beam", "cube", "batch"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--correction", default="asm", choices=["asm", "elem", "off"])
     ap.add_argument("--n-cub", type=int, default=4)
     ap.add_argument("--max-sweeps", type=int, default=2000)
-    ap.add_argument("--ref-sweeps", type=float, default=100.0,
+    ap.add_argument("--ref-sweeps", type=float, default=2000.0,
                     help="sweeps per step assumed by the reference arm's scaling")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--n-spheres", type=int, default=10)
+    ap.add_argument("--contact", type=int, default=1, help="IPC barrier on the spheres workload")
+    ap.add_argument("--n-scenes", type=int, default=256)
     ap.add_argument("--cubature", default="precompute", choices=["precompute", "synthetic"],
                     help="synthetic: seeded random records instead of the precompute (kernel profiling only)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1 and args.impl == "jgs2":
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if world > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    if args.impl == "reference":
-        out = run_reference(args, rank, world)
-    else:
-        out = run_jgs2(args, rank, world, local_rank)
+    out = run_jgs2(args, rank, world, local_rank)
     if out is not None:
         print(json.dumps(out))
-    if world > 1 and args.impl == "jgs2":
+    if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
 

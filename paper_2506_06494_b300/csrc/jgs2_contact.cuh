@@ -1,5 +1,5 @@
-// IPC contact on the device (Sec. 7, Eq. barrier): candidate pairs within r_c by a hashed
-// uniform grid, closest points in FP64, the barrier's per-vertex gradient and Gauss-Newton
+// IPC contact on the device (Sec. 7, Eq. barrier): candidate pairs by hashed uniform grids
+// (rebuilt on demand), closest points in FP64, the barrier's per-vertex gradient and Gauss-Newton
 // diagonal blocks (FP64 accumulators), the per-vertex step limit and the barrier part of
 // the line-search energy.
 //
@@ -146,114 +146,331 @@ __device__ __forceinline__ double segment_segment(P3 p0, P3 p1, P3 q0, P3 q1, do
   return best;
 }
 
+// ---------------------------------------------------------------------------------------
+// Broadphase. The candidate list holds every pair closer than R = r_c + 2M at the positions
+// of its last rebuild. Before every sweep k_bp_check measures the largest displacement of a
+// surface vertex since then and rebuilds the list when it exceeds M. A pair within r_c at the
+// sweep's positions was then closer than r_c + 2M at the rebuild, so it is in the list, and
+// the sweep's pair set (the pairs within r_c, evaluated exactly in FP64) is the one a fresh
+// search would give. Pairs beyond r_c at x^k stay beyond dhat through the sweep's line search
+// (a surface vertex moves at most 0.45 (r_c - dhat) per sweep). The grids are hashed (counting sort by bucket, no host round trip): a
+// sweep that needs no rebuild runs the rebuild kernels as empty launches.
+// ---------------------------------------------------------------------------------------
+enum { kCtlMove = 0, kCtlRebuild = 1, kCtlForce = 2, kCtlTicket = 3, kCtlExtF = 4, kCtlExtE = 5, kCtlAcc = 6,
+       kCtlCoord = 7, kCtlWords = 8 };
+
 __device__ __forceinline__ uint64_t cell_key(P3 p, double h) {
   const long long ix = (long long)floor(p.x / h) + (1 << 20), iy = (long long)floor(p.y / h) + (1 << 20),
                   iz = (long long)floor(p.z / h) + (1 << 20);
   return ((uint64_t)(ix & 0x1fffff) << 42) | ((uint64_t)(iy & 0x1fffff) << 21) | (uint64_t)(iz & 0x1fffff);
 }
+__device__ __forceinline__ uint64_t cell_key_of(long long cx, long long cy, long long cz) {
+  return ((uint64_t)((cx + (1 << 20)) & 0x1fffff) << 42) | ((uint64_t)((cy + (1 << 20)) & 0x1fffff) << 21) |
+         (uint64_t)((cz + (1 << 20)) & 0x1fffff);
+}
+__device__ __forceinline__ uint32_t bucket_of(uint64_t key, int hbits) {
+  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - hbits));
+}
+// grid cells: a face within R of a point has its centroid within R + (largest centroid-corner
+// distance); two edges within R have midpoints within R + 2 (largest half length)
+__device__ __forceinline__ void grid_cells(const ContactView& c, double& hf, double& he) {
+  const double ef = double(__uint_as_float(c.ctl[kCtlExtF])), ee = double(__uint_as_float(c.ctl[kCtlExtE]));
+  hf = (c.R + ef) * (1.0 + 1e-6) + 1e-12;
+  he = (c.R + 2.0 * ee) * (1.0 + 1e-6) + 1e-12;
+}
+// FP32 rounding slack of the position snapshot (a few ulps of the largest coordinate)
+__device__ __forceinline__ double snap_slack(const ContactView& c) {
+  return 8.0 * 5.9604644775390625e-8 * double(__uint_as_float(c.ctl[kCtlCoord])) + 1e-30;
+}
 
-__device__ __forceinline__ void emit_pair(const ContactView& c, uint64_t kind, uint64_t a, uint64_t b) {
+__device__ __forceinline__ float warp_maxf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ void warp_atomic_max(uint32_t* w, float v) {
+  v = warp_maxf(v);
+  if ((threadIdx.x & 31) == 0 && v > 0.f) atomicMax(w, __float_as_uint(v));
+}
+
+__device__ __forceinline__ void emit_pair(const ContactView& c, uint64_t kind, uint64_t a, uint64_t b, double d) {
   const int idx = atomicAdd(c.n_pairs, 1);
-  if (idx < c.cap)
+  if (idx < c.cap) {
     c.pairs[idx] = (kind << 60) | (a << 30) | b;
-  else
+    c.dbp[idx] = __double2float_rd(d);
+  } else {
     c.flags[0] = 1;
+  }
 }
 
-// cell keys of face centroids (kind 0) and edge midpoints (kind 1)
+// Largest surface-vertex displacement since the last rebuild; the last block decides the
+// rebuild (forced at the start of a step) and clears the counters of the next one.
 template <typename T>
-__global__ void k_prim_keys(DevMesh<T> m, ContactView c, uint64_t* fkeys, int32_t* fids, uint64_t* ekeys,
-                            int32_t* eids) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < c.n_faces) {
-    const P3 a = vpos(m, c.faces[3 * i]), b = vpos(m, c.faces[3 * i + 1]), d = vpos(m, c.faces[3 * i + 2]);
-    fkeys[i] = cell_key(mul(add(add(a, b), d), 1.0 / 3.0), c.cell);
-    fids[i] = i;
+__global__ void __launch_bounds__(256) k_bp_check(DevMesh<T> m, ContactView c, const StepState* st) {
+  if (st->done) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) c.ctl[kCtlRebuild] = 0u;
+    return;
   }
-  if (i < c.n_edges) {
-    const P3 a = vpos(m, c.edges[2 * i]), b = vpos(m, c.edges[2 * i + 1]);
-    ekeys[i] = cell_key(mul(add(a, b), 0.5), c.cell);
-    eids[i] = i;
+  __shared__ float red[8];
+  __shared__ bool last;
+  float mx = 0.f;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < c.n_sverts; q += gridDim.x * blockDim.x) {
+    const int v = c.sverts[q];
+    const P3 p = vpos(m, v);
+    const float4 b = c.pbp[v];
+    const double dx = p.x - double(b.x), dy = p.y - double(b.y), dz = p.z - double(b.z);
+    const double d = sqrt(dx * dx + dy * dy + dz * dz);
+    mx = fmaxf(mx, d == d ? __double2float_ru(d) : INFINITY);
+  }
+  mx = warp_maxf(mx);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
+    if (mx > 0.f) atomicMax(&c.ctl[kCtlMove], __float_as_uint(mx));
+    __threadfence();
+    last = atomicAdd(&c.ctl[kCtlTicket], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  volatile uint32_t* ctl = c.ctl;
+  const float moved = __uint_as_float(ctl[kCtlMove]);
+  const bool rebuild = ctl[kCtlForce] != 0u || !(double(moved) + snap_slack(c) <= c.trig);
+  ctl[kCtlRebuild] = rebuild ? 1u : 0u;
+  ctl[kCtlAcc] = rebuild ? 0u : __float_as_uint(moved);
+  ctl[kCtlMove] = 0u;
+  ctl[kCtlForce] = 0u;
+  ctl[kCtlTicket] = 0u;
+  if (rebuild) {
+    *c.n_pairs = 0;
+    ctl[kCtlExtF] = 0u;
+    ctl[kCtlExtE] = 0u;
+    ctl[kCtlCoord] = 0u;
   }
 }
 
-__device__ __forceinline__ int lower_bound_key(const uint64_t* k, int n, uint64_t key) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (k[mid] < key)
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  return lo;
-}
-
-// surface vertex queries: walls and faces within rc
+// Rebuild 1: FP32 snapshot of the surface positions, primitive extents, cleared buckets.
 template <typename T>
-__global__ void k_query_vertices(DevMesh<T> m, ContactView c) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= c.n_sverts) return;
-  const int v = c.sverts[q];
-  const P3 p = vpos(m, v);
-  for (int k = 0; k < c.n_planes; ++k) {
-    const double d = c.planes[4 * k] * p.x + c.planes[4 * k + 1] * p.y + c.planes[4 * k + 2] * p.z - c.planes[4 * k + 3];
-    if (d < c.rc) emit_pair(c, 0, v, k);
+__global__ void __launch_bounds__(256) k_bp_snapshot(DevMesh<T> m, ContactView c) {
+  if (c.ctl[kCtlRebuild] == 0u) return;
+  const int H2 = 2 << c.hbits;
+  const int n = max(max(c.n_sverts, c.n_faces), max(c.n_edges, H2 + 1));
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int q = base + threadIdx.x;
+    float co = 0.f, ef = 0.f, ee = 0.f;
+    if (q < c.n_sverts) {
+      const int v = c.sverts[q];
+      const P3 p = vpos(m, v);
+      c.pbp[v] = make_float4(float(p.x), float(p.y), float(p.z), 0.f);
+      co = __double2float_ru(fmax(fmax(fabs(p.x), fabs(p.y)), fabs(p.z)));
+    }
+    if (q < c.n_faces) {
+      const P3 a = vpos(m, c.faces[3 * q]), b = vpos(m, c.faces[3 * q + 1]), d = vpos(m, c.faces[3 * q + 2]);
+      const P3 g = mul(add(add(a, b), d), 1.0 / 3.0);
+      ef = __double2float_ru(fmax(fmax(norm(sub(a, g)), norm(sub(b, g))), norm(sub(d, g))));
+    }
+    if (q < c.n_edges) {
+      const P3 a = vpos(m, c.edges[2 * q]), b = vpos(m, c.edges[2 * q + 1]);
+      ee = __double2float_ru(0.5 * norm(sub(a, b)) * (1.0 + 1e-12));
+    }
+    if (q <= H2) c.hcnt[q] = 0;
+    warp_atomic_max(&c.ctl[kCtlCoord], co);
+    warp_atomic_max(&c.ctl[kCtlExtF], ef);
+    warp_atomic_max(&c.ctl[kCtlExtE], ee);
   }
-  const long long cx = (long long)floor(p.x / c.cell), cy = (long long)floor(p.y / c.cell),
-                  cz = (long long)floor(p.z / c.cell);
-  for (int dx = -1; dx <= 1; ++dx)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dz = -1; dz <= 1; ++dz) {
-        const uint64_t key = ((uint64_t)((cx + dx + (1 << 20)) & 0x1fffff) << 42) |
-                             ((uint64_t)((cy + dy + (1 << 20)) & 0x1fffff) << 21) |
-                             (uint64_t)((cz + dz + (1 << 20)) & 0x1fffff);
-        for (int j = lower_bound_key(c.fkeys, c.n_faces, key); j < c.n_faces && c.fkeys[j] == key; ++j) {
-          const int f = c.fids[j];
-          const int a = c.faces[3 * f], b = c.faces[3 * f + 1], cc = c.faces[3 * f + 2];
-          if (a == v || b == v || cc == v) continue;
-          const P3 pa = vpos(m, a), pb = vpos(m, b), pc = vpos(m, cc);
-          // box distance is a lower bound of the distance
-          const double gx = fmax(fmax(fmin(fmin(pa.x, pb.x), pc.x) - p.x, p.x - fmax(fmax(pa.x, pb.x), pc.x)), 0.0);
-          const double gy = fmax(fmax(fmin(fmin(pa.y, pb.y), pc.y) - p.y, p.y - fmax(fmax(pa.y, pb.y), pc.y)), 0.0);
-          const double gz = fmax(fmax(fmin(fmin(pa.z, pb.z), pc.z) - p.z, p.z - fmax(fmax(pa.z, pb.z), pc.z)), 0.0);
-          if (gx * gx + gy * gy + gz * gz >= c.rc * c.rc) continue;
-          double w[3];
-          if (point_triangle(p, pa, pb, pc, w) < c.rc) emit_pair(c, 1, v, f);
+}
+
+// Rebuild 2: cell key and rank within its bucket of every face (centroid) and edge (midpoint).
+template <typename T>
+__global__ void __launch_bounds__(256) k_bp_keys(DevMesh<T> m, ContactView c) {
+  if (c.ctl[kCtlRebuild] == 0u) return;
+  double hf, he;
+  grid_cells(c, hf, he);
+  const int H = 1 << c.hbits;
+  const int n = max(c.n_faces, c.n_edges);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    if (q < c.n_faces) {
+      const P3 a = vpos(m, c.faces[3 * q]), b = vpos(m, c.faces[3 * q + 1]), d = vpos(m, c.faces[3 * q + 2]);
+      const uint64_t key = cell_key(mul(add(add(a, b), d), 1.0 / 3.0), hf);
+      c.fkeys[q] = key;
+      c.frank[q] = atomicAdd(&c.hcnt[bucket_of(key, c.hbits)], 1);
+    }
+    if (q < c.n_edges) {
+      const P3 a = vpos(m, c.edges[2 * q]), b = vpos(m, c.edges[2 * q + 1]);
+      const uint64_t key = cell_key(mul(add(a, b), 0.5), he);
+      c.ekeys[q] = key;
+      c.erank[q] = atomicAdd(&c.hcnt[H + bucket_of(key, c.hbits)], 1);
+    }
+  }
+}
+
+// Exclusive scan of the bucket counts (2H + 1 entries, 4096 per block of 1024 threads).
+__device__ __forceinline__ int block_excl_scan(int v, int* sh, int& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    sh[lane] = s;
+  }
+  __syncthreads();
+  total = sh[(blockDim.x >> 5) - 1];
+  const int r = x - v + (w > 0 ? sh[w - 1] : 0);
+  __syncthreads();
+  return r;
+}
+static __global__ void __launch_bounds__(1024) k_bp_scan_blocks(ContactView c) {
+  if (c.ctl[kCtlRebuild] == 0u) return;
+  __shared__ int sh[32];
+  const int n = (2 << c.hbits) + 1;
+  const int base = blockIdx.x * 4096 + threadIdx.x * 4;
+  int s = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) s += base + j < n ? c.hcnt[base + j] : 0;
+  int total;
+  block_excl_scan(s, sh, total);
+  if (threadIdx.x == 0) c.hblk[blockIdx.x] = total;
+}
+static __global__ void __launch_bounds__(1024) k_bp_scan_top(ContactView c, int nblk) {
+  if (c.ctl[kCtlRebuild] == 0u) return;
+  __shared__ int sh[32];
+  const int v = (int)threadIdx.x < nblk ? c.hblk[threadIdx.x] : 0;
+  int total;
+  const int e = block_excl_scan(v, sh, total);
+  if ((int)threadIdx.x < nblk) c.hblk[threadIdx.x] = e;
+}
+static __global__ void __launch_bounds__(1024) k_bp_scan_apply(ContactView c) {
+  if (c.ctl[kCtlRebuild] == 0u) return;
+  __shared__ int sh[32];
+  const int n = (2 << c.hbits) + 1;
+  const int base = blockIdx.x * 4096 + threadIdx.x * 4;
+  int v[4], s = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    v[j] = base + j < n ? c.hcnt[base + j] : 0;
+    s += v[j];
+  }
+  int total;
+  int e = block_excl_scan(s, sh, total) + c.hblk[blockIdx.x];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (base + j < n) c.hcnt[base + j] = e;
+    e += v[j];
+  }
+}
+
+// Rebuild 3: primitive ids in bucket order (faces, then edges offset by n_faces).
+static __global__ void __launch_bounds__(256) k_bp_fill(ContactView c) {
+  if (c.ctl[kCtlRebuild] == 0u) return;
+  const int H = 1 << c.hbits;
+  const int n = max(c.n_faces, c.n_edges);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    if (q < c.n_faces) c.hids[c.hcnt[bucket_of(c.fkeys[q], c.hbits)] + c.frank[q]] = q;
+    if (q < c.n_edges) c.hids[c.hcnt[H + bucket_of(c.ekeys[q], c.hbits)] + c.erank[q]] = q;
+  }
+}
+
+// AABB gap test on the FP32 snapshot: false only when the boxes are provably farther than R
+__device__ __forceinline__ bool boxes_near(float4 lo, float4 hi, float4 plo, float4 phi, float r) {
+  const float gx = fmaxf(fmaxf(lo.x - phi.x, plo.x - hi.x), 0.f);
+  const float gy = fmaxf(fmaxf(lo.y - phi.y, plo.y - hi.y), 0.f);
+  const float gz = fmaxf(fmaxf(lo.z - phi.z, plo.z - hi.z), 0.f);
+  return gx * gx + gy * gy + gz * gz < r * r;
+}
+__device__ __forceinline__ float4 fmin4(float4 a, float4 b) {
+  return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), 0.f);
+}
+__device__ __forceinline__ float4 fmax4(float4 a, float4 b) {
+  return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), 0.f);
+}
+
+// Rebuild 4: surface vertices against walls and faces (27 neighbouring cells), exact FP64
+// distance below R.
+template <typename T>
+__global__ void __launch_bounds__(128) k_query_vertices(DevMesh<T> m, ContactView c) {
+  if (c.ctl[kCtlRebuild] == 0u) return;
+  double hf, he;
+  grid_cells(c, hf, he);
+  const float rf = float((c.R + 2.0 * snap_slack(c)) * (1.0 + 1e-6));
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < c.n_sverts; q += gridDim.x * blockDim.x) {
+    const int v = c.sverts[q];
+    const P3 p = vpos(m, v);
+    const float4 pf = c.pbp[v];
+    for (int k = 0; k < c.n_planes; ++k) {
+      const double d =
+          c.planes[4 * k] * p.x + c.planes[4 * k + 1] * p.y + c.planes[4 * k + 2] * p.z - c.planes[4 * k + 3];
+      if (d < c.R) emit_pair(c, 0, v, k, d);
+    }
+    const long long cx = (long long)floor(p.x / hf), cy = (long long)floor(p.y / hf), cz = (long long)floor(p.z / hf);
+    for (int dx = -1; dx <= 1; ++dx)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dz = -1; dz <= 1; ++dz) {
+          const uint64_t key = cell_key_of(cx + dx, cy + dy, cz + dz);
+          const uint32_t b = bucket_of(key, c.hbits);
+          const int j1 = c.hcnt[b + 1];
+          for (int j = c.hcnt[b]; j < j1; ++j) {
+            const int f = c.hids[j];
+            if (c.fkeys[f] != key) continue;
+            const int a = c.faces[3 * f], bb = c.faces[3 * f + 1], cc = c.faces[3 * f + 2];
+            if (a == v || bb == v || cc == v) continue;
+            const float4 fa = c.pbp[a], fb = c.pbp[bb], fc = c.pbp[cc];
+            if (!boxes_near(fmin4(fmin4(fa, fb), fc), fmax4(fmax4(fa, fb), fc), pf, pf, rf)) continue;
+            double w[3];
+            const double d = point_triangle(p, vpos(m, a), vpos(m, bb), vpos(m, cc), w);
+            if (d < c.R) emit_pair(c, 1, v, f, d);
+          }
         }
-      }
+  }
 }
 
-// edge queries: edges j > i sharing no vertex within rc
+// Rebuild 5: edge pairs j > i sharing no vertex, exact FP64 distance below R.
 template <typename T>
-__global__ void k_query_edges(DevMesh<T> m, ContactView c) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= c.n_edges) return;
-  const int a0 = c.edges[2 * i], a1 = c.edges[2 * i + 1];
-  const P3 p0 = vpos(m, a0), p1 = vpos(m, a1);
-  const P3 mid = mul(add(p0, p1), 0.5);
-  const long long cx = (long long)floor(mid.x / c.cell), cy = (long long)floor(mid.y / c.cell),
-                  cz = (long long)floor(mid.z / c.cell);
-  for (int dx = -1; dx <= 1; ++dx)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dz = -1; dz <= 1; ++dz) {
-        const uint64_t key = ((uint64_t)((cx + dx + (1 << 20)) & 0x1fffff) << 42) |
-                             ((uint64_t)((cy + dy + (1 << 20)) & 0x1fffff) << 21) |
-                             (uint64_t)((cz + dz + (1 << 20)) & 0x1fffff);
-        for (int j = lower_bound_key(c.ekeys, c.n_edges, key); j < c.n_edges && c.ekeys[j] == key; ++j) {
-          const int e = c.eids[j];
-          if (e <= i) continue;
-          const int b0 = c.edges[2 * e], b1 = c.edges[2 * e + 1];
-          if (b0 == a0 || b0 == a1 || b1 == a0 || b1 == a1) continue;
-          const P3 q0 = vpos(m, b0), q1 = vpos(m, b1);
-          const double gx = fmax(fmax(fmin(q0.x, q1.x) - fmax(p0.x, p1.x), fmin(p0.x, p1.x) - fmax(q0.x, q1.x)), 0.0);
-          const double gy = fmax(fmax(fmin(q0.y, q1.y) - fmax(p0.y, p1.y), fmin(p0.y, p1.y) - fmax(q0.y, q1.y)), 0.0);
-          const double gz = fmax(fmax(fmin(q0.z, q1.z) - fmax(p0.z, p1.z), fmin(p0.z, p1.z) - fmax(q0.z, q1.z)), 0.0);
-          if (gx * gx + gy * gy + gz * gz >= c.rc * c.rc) continue;
-          double s, t;
-          if (segment_segment(p0, p1, q0, q1, s, t) < c.rc) emit_pair(c, 2, i, e);
+__global__ void __launch_bounds__(128) k_query_edges(DevMesh<T> m, ContactView c) {
+  if (c.ctl[kCtlRebuild] == 0u) return;
+  double hf, he;
+  grid_cells(c, hf, he);
+  const float rf = float((c.R + 2.0 * snap_slack(c)) * (1.0 + 1e-6));
+  const int H = 1 << c.hbits;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.n_edges; i += gridDim.x * blockDim.x) {
+    const int a0 = c.edges[2 * i], a1 = c.edges[2 * i + 1];
+    const P3 p0 = vpos(m, a0), p1 = vpos(m, a1);
+    const float4 f0 = c.pbp[a0], f1 = c.pbp[a1];
+    const float4 lo = fmin4(f0, f1), hi = fmax4(f0, f1);
+    const P3 mid = mul(add(p0, p1), 0.5);
+    const long long cx = (long long)floor(mid.x / he), cy = (long long)floor(mid.y / he),
+                    cz = (long long)floor(mid.z / he);
+    for (int dx = -1; dx <= 1; ++dx)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dz = -1; dz <= 1; ++dz) {
+          const uint64_t key = cell_key_of(cx + dx, cy + dy, cz + dz);
+          const uint32_t b = H + bucket_of(key, c.hbits);
+          const int j1 = c.hcnt[b + 1];
+          for (int j = c.hcnt[b]; j < j1; ++j) {
+            const int e = c.hids[j];
+            if (e <= i || c.ekeys[e] != key) continue;
+            const int b0 = c.edges[2 * e], b1 = c.edges[2 * e + 1];
+            if (b0 == a0 || b0 == a1 || b1 == a0 || b1 == a1) continue;
+            const float4 g0 = c.pbp[b0], g1 = c.pbp[b1];
+            if (!boxes_near(lo, hi, fmin4(g0, g1), fmax4(g0, g1), rf)) continue;
+            double s, t;
+            const double d = segment_segment(p0, p1, vpos(m, b0), vpos(m, b1), s, t);
+            if (d < c.R) emit_pair(c, 2, i, e, d);
+          }
         }
-      }
+  }
 }
 
 // Geometry of a pair at x (+ a d): distance, involved vertices and dd/dx per vertex.
@@ -305,52 +522,64 @@ __device__ __forceinline__ double pair_geom(const DevMesh<T>& m, const ContactVi
   return d;
 }
 
-static __global__ void k_contact_reset(ContactView c, int V) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= V) return;
+// per sweep: clear the barrier accumulators of the surface vertices (no other vertex is
+// ever written; their entries stay zero from allocation)
+static __global__ void __launch_bounds__(256) k_contact_reset(ContactView c) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < c.n_sverts; q += gridDim.x * blockDim.x) {
+    const int v = c.sverts[q];
+    const size_t V = c.n_vertices;
 #pragma unroll
-  for (int q = 0; q < 3; ++q) c.bg[(size_t)q * V + v] = 0.0;
+    for (int k = 0; k < 3; ++k) c.bg[(size_t)k * V + v] = 0.0;
 #pragma unroll
-  for (int q = 0; q < 6; ++q) c.bH[(size_t)q * V + v] = 0.0;
-  c.dmin[v] = INFINITY;
+    for (int k = 0; k < 6; ++k) c.bH[(size_t)k * V + v] = 0.0;
+    c.dmin[v] = INFINITY;
+  }
 }
 
-// per pair: distance at x^k, smallest candidate distance per vertex, and for active pairs
-// (d < dhat) kappa B'(d) dd/dx and kappa B''(d) (dd/dx)(dd/dx)^T into the FP64 accumulators
+// Per candidate pair: its distance at x^k. Pairs within r_c count: smallest distance per
+// vertex, and for active pairs (d < dhat) kappa B'(d) dd/dx and kappa B''(d) (dd/dx)(dd/dx)^T
+// into the FP64 accumulators. A pair whose rebuild distance exceeds r_c by more than twice
+// the largest displacement since the rebuild cannot be within r_c and is skipped (d0 = inf).
 template <typename T>
-__global__ void k_pair_terms(DevMesh<T> m, ContactView c, StepState* st) {
+__global__ void __launch_bounds__(256) k_pair_terms(DevMesh<T> m, ContactView c, StepState* st) {
   const int n = min(*c.n_pairs, c.cap);
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  int vs[4], nv;
-  P3 J[4];
-  const double d = pair_geom(m, c, c.pairs[q], 0.0, (const Vec4<T>*)nullptr, vs, J, nv);
-  c.d0[q] = d;
-  if (!(d > 0.0)) {
-    c.flags[1] = 1;
-    st->status = 9;  // JGS2_EINTERSECT
-    st->done = 1;
-    return;
-  }
-  // positive doubles order like their bit patterns
-  for (int k = 0; k < nv; ++k)
-    atomicMin(reinterpret_cast<unsigned long long*>(c.dmin + vs[k]), (unsigned long long)__double_as_longlong(d));
-  if (d >= c.dhat) return;
-  const double b1 = c.kappa * barrier_b1(d, c.dhat), b2 = c.kappa * barrier_b2(d, c.dhat);
-  const size_t V = m.V;
-  for (int k = 0; k < nv; ++k) {
-    const int v = vs[k];
-    if (v >= m.Vf) continue;
-    const P3 j = J[k];
-    atomicAdd(c.bg + v, b1 * j.x);
-    atomicAdd(c.bg + V + v, b1 * j.y);
-    atomicAdd(c.bg + 2 * V + v, b1 * j.z);
-    atomicAdd(c.bH + v, b2 * j.x * j.x);
-    atomicAdd(c.bH + V + v, b2 * j.x * j.y);
-    atomicAdd(c.bH + 2 * V + v, b2 * j.x * j.z);
-    atomicAdd(c.bH + 3 * V + v, b2 * j.y * j.y);
-    atomicAdd(c.bH + 4 * V + v, b2 * j.y * j.z);
-    atomicAdd(c.bH + 5 * V + v, b2 * j.z * j.z);
+  const double far = c.rc + 2.0 * (double(__uint_as_float(c.ctl[kCtlAcc])) + snap_slack(c));
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    if (double(c.dbp[q]) >= far) {
+      c.d0[q] = INFINITY;
+      continue;
+    }
+    int vs[4], nv;
+    P3 J[4];
+    const double d = pair_geom(m, c, c.pairs[q], 0.0, (const Vec4<T>*)nullptr, vs, J, nv);
+    c.d0[q] = d;
+    if (!(d > 0.0)) {
+      c.flags[1] = 1;
+      st->status = 9;  // JGS2_EINTERSECT
+      st->done = 1;
+      continue;
+    }
+    if (d >= c.rc) continue;
+    // positive doubles order like their bit patterns
+    for (int k = 0; k < nv; ++k)
+      atomicMin(reinterpret_cast<unsigned long long*>(c.dmin + vs[k]), (unsigned long long)__double_as_longlong(d));
+    if (d >= c.dhat) continue;
+    const double b1 = c.kappa * barrier_b1(d, c.dhat), b2 = c.kappa * barrier_b2(d, c.dhat);
+    const size_t V = m.V;
+    for (int k = 0; k < nv; ++k) {
+      const int v = vs[k];
+      if (v >= m.Vf) continue;
+      const P3 j = J[k];
+      atomicAdd(c.bg + v, b1 * j.x);
+      atomicAdd(c.bg + V + v, b1 * j.y);
+      atomicAdd(c.bg + 2 * V + v, b1 * j.z);
+      atomicAdd(c.bH + v, b2 * j.x * j.x);
+      atomicAdd(c.bH + V + v, b2 * j.x * j.y);
+      atomicAdd(c.bH + 2 * V + v, b2 * j.x * j.z);
+      atomicAdd(c.bH + 3 * V + v, b2 * j.y * j.y);
+      atomicAdd(c.bH + 4 * V + v, b2 * j.y * j.z);
+      atomicAdd(c.bH + 5 * V + v, b2 * j.z * j.z);
+    }
   }
 }
 

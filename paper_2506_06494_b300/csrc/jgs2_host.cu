@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -11,7 +12,6 @@
 #include <string>
 #include <vector>
 
-#include <cub/device/device_radix_sort.cuh>
 #include <map>
 
 #include "../../include/jgs2.h"
@@ -69,10 +69,8 @@ Mesh::~Mesh() {
   cudaFree(d_vscene); cudaFree(d_tscene); cudaFree(d_ndone); cudaFree(d_scenes); cudaFree(d_sacc);
   cudaFree(d_planes); cudaFree(d_d0); cudaFree(d_bg); cudaFree(d_bH); cudaFree(d_faces); cudaFree(d_edges);
   cudaFree(d_sverts); cudaFree(d_npairs); cudaFree(d_cflags); cudaFree(d_is_surf); cudaFree(d_pairs);
-  cudaFree(d_dmin); cudaFree(d_lim); cudaFree(d_cub);
-  for (int q = 0; q < 2; ++q) {
-    cudaFree(d_fids[q]); cudaFree(d_eids[q]); cudaFree(d_fkeys[q]); cudaFree(d_ekeys[q]);
-  }
+  cudaFree(d_dmin); cudaFree(d_lim); cudaFree(d_frank); cudaFree(d_erank); cudaFree(d_hcnt); cudaFree(d_hblk);
+  cudaFree(d_hids); cudaFree(d_fkeys); cudaFree(d_ekeys); cudaFree(d_pbp); cudaFree(d_dbp); cudaFree(d_ctl);
 }
 
 static uint64_t spread3(uint64_t x) {
@@ -301,10 +299,17 @@ jgs2_status mesh_create(const jgs2_mesh_desc* d, Mesh** out, const std::vector<i
         m->sverts.push_back(m->iperm[v]);
         m->is_surf[m->iperm[v]] = 1;
       }
-    // grid cell: a primitive within rc of a point has its centroid within rc + rmax of it;
-    // twice the rest size leaves room for deformation
-    m->cell = m->rc + 2.0 * rmax;
-    m->pair_cap = std::max<int>(1 << 16, 8 * (int)m->sverts.size() + 16 * d->n_planes);
+    // candidate list radius R = r_c + 2M, rebuilt once a surface vertex has moved more than M
+    // since the last rebuild; M = 2 delta, delta = 0.45 (r_c - dhat) the per-sweep step limit
+    // (a list then lasts at least two sweeps of the largest possible motion)
+    const double delta = 0.45 * (m->rc - m->dhat);
+    m->bp_R = m->rc + 4.0 * delta;
+    m->bp_trig = 2.0 * delta * (1.0 - 1e-6);
+    (void)rmax;
+    const int nprim = std::max<int>(std::max<int>((int)m->sfaces.size() / 3, (int)m->sedges.size() / 2), 1);
+    m->hbits = 10;
+    while (m->hbits < 20 && (1 << m->hbits) < 2 * nprim) ++m->hbits;
+    m->pair_cap = std::max<int>(1 << 16, 32 * (int)m->sverts.size() + 16 * d->n_planes);
   }
   *out = m.release();
   return JGS2_OK;
@@ -352,12 +357,19 @@ static jgs2_status ensure_device(Mesh* m) {
       CK(dalloc(&m->d_edges, std::max(1, 2 * nE)));
       CK(dalloc(&m->d_sverts, std::max(1, nS)));
       CK(dalloc(&m->d_is_surf, V));
-      for (int q = 0; q < 2; ++q) {
-        CK(dalloc(&m->d_fkeys[q], std::max(1, nF)));
-        CK(dalloc(&m->d_fids[q], std::max(1, nF)));
-        CK(dalloc(&m->d_ekeys[q], std::max(1, nE)));
-        CK(dalloc(&m->d_eids[q], std::max(1, nE)));
-      }
+      const int H2 = 2 << m->hbits;
+      CK(dalloc(&m->d_fkeys, std::max(1, nF)));
+      CK(dalloc(&m->d_frank, std::max(1, nF)));
+      CK(dalloc(&m->d_ekeys, std::max(1, nE)));
+      CK(dalloc(&m->d_erank, std::max(1, nE)));
+      CK(dalloc(&m->d_hcnt, H2 + 1));
+      CK(dalloc(&m->d_hblk, (H2 + 1 + 4095) / 4096));
+      CK(dalloc(&m->d_hids, std::max(1, nF + nE)));
+      CK(dalloc(&m->d_pbp, V));
+      CK(dalloc(&m->d_ctl, kCtlWords));
+      CK(dalloc(&m->d_dbp, m->pair_cap));
+      CK(cudaMemset(m->d_ctl, 0, sizeof(uint32_t) * kCtlWords));
+      CK(cudaMemset(m->d_pbp, 0, sizeof(float4) * V));
       CK(dalloc(&m->d_pairs, m->pair_cap));
       CK(dalloc(&m->d_d0, m->pair_cap));
       CK(dalloc(&m->d_npairs, 1));
@@ -372,13 +384,9 @@ static jgs2_status ensure_device(Mesh* m) {
       if (nS) CK(cudaMemcpy(m->d_sverts, m->sverts.data(), sizeof(int) * nS, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(m->d_is_surf, m->is_surf.data(), V, cudaMemcpyHostToDevice));
       CK(cudaMemset(m->d_cflags, 0, 2 * sizeof(int32_t)));
-      size_t b1 = 0, b2 = 0;
-      cub::DeviceRadixSort::SortPairs(nullptr, b1, m->d_fkeys[0], m->d_fkeys[1], m->d_fids[0], m->d_fids[1],
-                                      std::max(1, nF));
-      cub::DeviceRadixSort::SortPairs(nullptr, b2, m->d_ekeys[0], m->d_ekeys[1], m->d_eids[0], m->d_eids[1],
-                                      std::max(1, nE));
-      m->cub_bytes = std::max(b1, b2);
-      CK(cudaMalloc(&m->d_cub, m->cub_bytes));
+      // accumulators of non-surface vertices are never written: zero them once
+      CK(cudaMemset(m->d_bg, 0, sizeof(double) * 3 * (size_t)V));
+      CK(cudaMemset(m->d_bH, 0, sizeof(double) * 6 * (size_t)V));
     }
     if (m->n_scenes > 0) {
       std::vector<int> vs(std::max(1, m->Vf)), ts(T);
@@ -521,11 +529,20 @@ static DevMesh<T> dev_view(Mesh* m) {
     c.dhat = m->dhat;
     c.kappa = m->kappa;
     c.rc = m->rc;
-    c.cell = m->cell;
-    c.fkeys = m->d_fkeys[1];
-    c.fids = m->d_fids[1];
-    c.ekeys = m->d_ekeys[1];
-    c.eids = m->d_eids[1];
+    c.n_vertices = m->V;
+    c.R = m->bp_R;
+    c.trig = m->bp_trig;
+    c.hbits = m->hbits;
+    c.fkeys = m->d_fkeys;
+    c.ekeys = m->d_ekeys;
+    c.frank = m->d_frank;
+    c.erank = m->d_erank;
+    c.hcnt = m->d_hcnt;
+    c.hblk = m->d_hblk;
+    c.hids = m->d_hids;
+    c.pbp = m->d_pbp;
+    c.ctl = m->d_ctl;
+    c.dbp = m->d_dbp;
     c.pairs = m->d_pairs;
     c.n_pairs = m->d_npairs;
     c.cap = m->pair_cap;
@@ -612,24 +629,31 @@ jgs2_status import_cubature(Mesh* m, const jgs2_cubature_blob* b) {
 template <typename T>
 static jgs2_status contact_pass(Mesh* m, DevMesh<T>& d, cudaStream_t s, StepState* st) {
   const ContactView& c = d.c;
-  CK(cudaMemsetAsync(m->d_npairs, 0, sizeof(int32_t), s));
-  k_contact_reset<<<(m->V + 127) / 128, 128, 0, s>>>(c, m->V);
-  const int nP = std::max(c.n_faces, c.n_edges);
-  if (nP > 0) {
-    k_prim_keys<T><<<(nP + 127) / 128, 128, 0, s>>>(d, c, m->d_fkeys[0], m->d_fids[0], m->d_ekeys[0], m->d_eids[0]);
-    size_t bytes = m->cub_bytes;
-    if (c.n_faces)
-      CK(cub::DeviceRadixSort::SortPairs(m->d_cub, bytes, m->d_fkeys[0], m->d_fkeys[1], m->d_fids[0], m->d_fids[1],
-                                         c.n_faces, 0, 64, s));
-    bytes = m->cub_bytes;
-    if (c.n_edges)
-      CK(cub::DeviceRadixSort::SortPairs(m->d_cub, bytes, m->d_ekeys[0], m->d_ekeys[1], m->d_eids[0], m->d_eids[1],
-                                         c.n_edges, 0, 64, s));
-  }
-  if (c.n_sverts) k_query_vertices<T><<<(c.n_sverts + 127) / 128, 128, 0, s>>>(d, c);
-  if (c.n_edges) k_query_edges<T><<<(c.n_edges + 127) / 128, 128, 0, s>>>(d, c);
-  k_pair_terms<T><<<(c.cap + 127) / 128, 128, 0, s>>>(d, c, st);
+  const int nS = c.n_sverts, nF = c.n_faces, nE = c.n_edges;
+  const int H2 = 2 << c.hbits;
+  const int cap_blocks = 148 * 4;
+  auto grid = [&](int n, int bs) { return std::max(1, std::min((n + bs - 1) / bs, cap_blocks)); };
+  k_bp_check<T><<<grid(nS, 256), 256, 0, s>>>(d, c, st);
+  // rebuild kernels: empty launches unless k_bp_check asked for a rebuild
+  k_bp_snapshot<T><<<grid(std::max(std::max(nS, nF), std::max(nE, H2 + 1)), 256), 256, 0, s>>>(d, c);
+  k_bp_keys<T><<<grid(std::max(nF, nE), 256), 256, 0, s>>>(d, c);
+  const int nblk = (H2 + 1 + 4095) / 4096;
+  k_bp_scan_blocks<<<nblk, 1024, 0, s>>>(c);
+  k_bp_scan_top<<<1, 1024, 0, s>>>(c, nblk);
+  k_bp_scan_apply<<<nblk, 1024, 0, s>>>(c);
+  k_bp_fill<<<grid(std::max(nF, nE), 256), 256, 0, s>>>(c);
+  k_query_vertices<T><<<grid(nS, 128), 128, 0, s>>>(d, c);
+  k_query_edges<T><<<grid(nE, 128), 128, 0, s>>>(d, c);
+  // per sweep: barrier terms of the listed pairs at x^k
+  k_contact_reset<<<grid(nS, 256), 256, 0, s>>>(c);
+  k_pair_terms<T><<<grid(c.cap, 256), 256, 0, s>>>(d, c, st);
   CK(cudaGetLastError());
+  return JGS2_OK;
+}
+
+// Forces a candidate-list rebuild at the next contact pass (start of a step).
+static jgs2_status contact_force_rebuild(Mesh* m, cudaStream_t s) {
+  CK(cudaMemsetAsync(m->d_ctl + kCtlForce, 1, sizeof(uint32_t), s));  // any non-zero word
   return JGS2_OK;
 }
 
@@ -729,6 +753,10 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t s, 
   init.alpha = 1.0;
   CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
   const int every = std::max(1, o.check_every);
+  if (m->contact) {
+    jgs2_status cs = contact_force_rebuild(m, s);
+    if (cs != JGS2_OK) return cs;
+  }
   for (int k = 0; k <= max_k; ++k) {
     int id;
     if (m->contact) {
@@ -857,11 +885,15 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
     if (e != cudaSuccess) return fail(JGS2_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
     m->graph_key = key;
   }
-  const int per_sweep = (corr ? 3 : 1) + 2 + (o.line_search ? 2 : 0);
   int32_t done = 0;
   for (int sw = 0; sw <= o.max_sweeps; sw += chunk) {
     CK(cudaGraphLaunch(m->graph, s));
-    L.count[JGS2_K_GATHER] += chunk * per_sweep;
+    // kernel nodes per replay, by kind (the per-scene stopping test counts with the update)
+    L.count[JGS2_K_POOL] += corr ? chunk : 0;
+    L.count[JGS2_K_GATHER] += chunk;
+    L.count[JGS2_K_CORRECT] += corr ? chunk : 0;
+    L.count[JGS2_K_ENERGY] += o.line_search ? 2 * chunk : 0;
+    L.count[JGS2_K_UPDATE] += 2 * chunk;
     CK(cudaMemcpyAsync(&done, m->d_ndone, sizeof(done), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (done >= S) break;
@@ -1012,6 +1044,8 @@ jgs2_status energy_gradient(Mesh* m, const double* xt, const double* vt, const d
   // pinned vertices keep x_t; a caller x that moves them is a different problem
   if (m->contact) {
     CK(cudaMemsetAsync(m->d_state, 0, sizeof(StepState), s));
+    st = contact_force_rebuild(m, s);
+    if (st != JGS2_OK) return st;
     st = contact_pass<double>(m, d, s, m->d_state);
     if (st != JGS2_OK) return st;
   }
@@ -1048,11 +1082,13 @@ jgs2_status contact_pairs(Mesh* m, const double* xt, const double* x, double rad
   jgs2_status st = ensure_prec<double>(m);
   if (st != JGS2_OK) return st;
   DevMesh<double> d = dev_view<double>(m);
-  d.c.cell = m->cell - m->rc + radius;
+  d.c.R = radius;
   d.c.rc = radius;
   const int nb = (m->V + 127) / 128;
   k_setup_vertices<double><<<nb, 128, 0, s>>>(d, xt, xt, x);
   CK(cudaMemsetAsync(m->d_state, 0, sizeof(StepState), s));
+  st = contact_force_rebuild(m, s);
+  if (st != JGS2_OK) return st;
   st = contact_pass<double>(m, d, s, m->d_state);
   if (st != JGS2_OK) return st;
   int32_t n = 0, fl[2] = {0, 0};

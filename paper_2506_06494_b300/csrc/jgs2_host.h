@@ -78,19 +78,22 @@ struct Mesh {
   cudaEvent_t gev[2] = {nullptr, nullptr};
   // contact (Sec. 7): surface in internal vertex ids
   int contact = 0;
-  double dhat = 0.0, kappa = 0.0, rc = 0.0, cell = 0.0;
+  double dhat = 0.0, kappa = 0.0, rc = 0.0;
+  double bp_R = 0.0, bp_trig = 0.0;           // candidate-list radius and rebuild trigger
+  int hbits = 0;                              // log2 buckets per hashed grid
   std::vector<double> planes;                 // [n][4]
   std::vector<int> sfaces, sedges, sverts;    // [nF][3], [nE][2], [nS]
   std::vector<uint8_t> is_surf;               // [V] internal order
   int pair_cap = 0;
   double *d_planes = nullptr, *d_d0 = nullptr, *d_bg = nullptr, *d_bH = nullptr;
   int32_t *d_faces = nullptr, *d_edges = nullptr, *d_sverts = nullptr, *d_npairs = nullptr, *d_cflags = nullptr;
-  int32_t *d_fids[2] = {nullptr, nullptr}, *d_eids[2] = {nullptr, nullptr};
+  int32_t *d_frank = nullptr, *d_erank = nullptr, *d_hcnt = nullptr, *d_hblk = nullptr, *d_hids = nullptr;
   uint8_t* d_is_surf = nullptr;
-  uint64_t *d_fkeys[2] = {nullptr, nullptr}, *d_ekeys[2] = {nullptr, nullptr}, *d_pairs = nullptr;
+  uint64_t *d_fkeys = nullptr, *d_ekeys = nullptr, *d_pairs = nullptr;
+  float4* d_pbp = nullptr;
+  float* d_dbp = nullptr;
+  uint32_t* d_ctl = nullptr;
   double *d_dmin = nullptr, *d_lim = nullptr;
-  void* d_cub = nullptr;
-  size_t cub_bytes = 0;
   PrecBufs<float> f32;
   PrecBufs<double> f64;
   ~Mesh();

@@ -63,27 +63,36 @@ struct StepState {
 // Contact data of a mesh (Sec. 7); pairs: 0 vertex-wall, 1 vertex-face, 2 edge-edge.
 struct ContactView {
   int on = 0;
-  int n_planes = 0, n_faces = 0, n_edges = 0, n_sverts = 0;
+  int n_planes = 0, n_faces = 0, n_edges = 0, n_sverts = 0, n_vertices = 0;
   const double* planes = nullptr;    // [n_planes][4]
   const int32_t* faces = nullptr;    // [n_faces][3] internal vertex ids (outward)
   const int32_t* edges = nullptr;    // [n_edges][2]
   const int32_t* sverts = nullptr;   // [n_sverts]
   const uint8_t* is_surf = nullptr;  // [V]
-  double dhat = 0, kappa = 0, rc = 0, cell = 0;
-  // broadphase (sorted by cell key)
-  const uint64_t* fkeys = nullptr;
-  const int32_t* fids = nullptr;
-  const uint64_t* ekeys = nullptr;
-  const int32_t* eids = nullptr;
+  double dhat = 0, kappa = 0, rc = 0;
+  // broadphase: candidate list of the pairs within R at the last rebuild; rebuild when a
+  // surface vertex has moved more than trig since then
+  double R = 0, trig = 0;
+  int hbits = 0;                 // log2 of the buckets per hashed grid (faces grid, edges grid)
+  uint64_t* fkeys = nullptr;     // [n_faces] cell key of the centroid
+  uint64_t* ekeys = nullptr;     // [n_edges] cell key of the midpoint
+  int32_t* frank = nullptr;      // [n_faces] rank within its bucket
+  int32_t* erank = nullptr;      // [n_edges]
+  int32_t* hcnt = nullptr;       // [2H + 1] bucket counts, then exclusive starts
+  int32_t* hblk = nullptr;       // [scan blocks] block sums
+  int32_t* hids = nullptr;       // [n_faces + n_edges] primitive ids in bucket order
+  float4* pbp = nullptr;         // [V] surface vertex positions at the last rebuild (FP32)
+  uint32_t* ctl = nullptr;       // control words (displacement, rebuild flags, extents)
   // pairs
-  uint64_t* pairs = nullptr;     // packed (kind << 60 | a << 30 | b), canonical after sorting
+  uint64_t* pairs = nullptr;     // packed (kind << 60 | a << 30 | b)
   int32_t* n_pairs = nullptr;    // device counter
   int cap = 0;
-  double* d0 = nullptr;          // [cap] distance at x^k
+  float* dbp = nullptr;          // [cap] distance at the last rebuild (rounded down)
+  double* d0 = nullptr;          // [cap] distance at x^k (inf when provably beyond r_c)
   // per-vertex accumulators
   double* bg = nullptr;          // [3][V]
   double* bH = nullptr;          // [6][V]
-  double* dmin = nullptr;        // [V] smallest candidate distance (atomicMin on the bits)
+  double* dmin = nullptr;        // [V] smallest distance of a pair within r_c (atomicMin on the bits)
   double* lim = nullptr;         // [Vf] step limit 0.45 min(rc - dhat, dmin)
   int32_t* flags = nullptr;      // [0] overflow, [1] intersection
 };

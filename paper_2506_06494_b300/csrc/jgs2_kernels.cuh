@@ -661,13 +661,15 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 1024 : 512) / BS)
     T lim = T(INFINITY);
     if (m.c.on) {
       // IPC barrier (Sec. 7): exact gradient and Gauss-Newton diagonal block of the pairs
-      // around i, and the step limit 0.45 min(r_c - dhat, d_min) of a surface vertex
-      const size_t V = m.V;
+      // around a surface vertex i, and its step limit 0.45 min(r_c - dhat, d_min)
+      if (m.c.is_surf[i]) {
+        const size_t V = m.V;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) g[q] += T(m.c.bg[q * V + i]);
+        for (int q = 0; q < 3; ++q) g[q] += T(m.c.bg[q * V + i]);
 #pragma unroll
-      for (int q = 0; q < 6; ++q) H[q] += T(m.c.bH[q * V + i]);
-      if (m.c.is_surf[i]) lim = T(0.45 * fmin(m.c.rc - m.c.dhat, m.c.dmin[i]));
+        for (int q = 0; q < 6; ++q) H[q] += T(m.c.bH[q * V + i]);
+        lim = T(0.45 * fmin(m.c.rc - m.c.dhat, m.c.dmin[i]));
+      }
       m.c.lim[i] = double(lim);
     }
     T dj[3];
@@ -927,8 +929,12 @@ __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st,
   if (CONTACT) {
     const int np = min(*m.c.n_pairs, m.c.cap);
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += stride) {
+      // a pair beyond r_c stays beyond dhat for every trial (each vertex moves at most
+      // 0.45 (r_c - dhat)): its barrier is zero throughout
+      const double dq = m.c.d0[q];
+      if (!(dq < m.c.rc)) continue;
       const uint64_t key = m.c.pairs[q];
-      const double b0 = barrier_b(m.c.d0[q], m.c.dhat);
+      const double b0 = barrier_b(dq, m.c.dhat);
 #pragma unroll
       for (int dir = 0; dir < ND; ++dir)
 #pragma unroll 1
