@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ms/step to 1e-4 rel. residual at 3.5M tets"
-KIND = ["k_pool", "k_gather", "k_correct", "k_energy", "k_update", "setup", "contact"]
+KIND = ["k_pool", "k_gather", "k_correct", "k_energy", "k_update", "setup", "contact", "k_elem"]
 
 
 def peaks():
@@ -70,23 +70,40 @@ def concat(ss):
 
 
 def kernel_bytes(V_f, T, n_cub, fp_bytes=4):
-    """Algorithmic DRAM bytes per launch (each datum moved once), by kernel.
+    """DRAM bytes each sweep kernel must move per launch (every datum it reads or writes
+    counted once), by kernel.
 
-    tet record: 4 corner ids (16 B) + B (9) + F(x_t) (9) + V_e, mu, lam' (3 scalars);
-    k_gather: tet records + 4 incidence entries per tet (16 B); per free vertex u, dz read,
-      m/h^2, the incidence count, D_J written (3) and g, H, R written (18 scalars);
+    tet record fields read: 4 corner ids (16 B) + B (9) + F(x_t) (9) + V_e, mu, lam' (3);
+    k_elem: tet record fields, the corners' displacements (u, 16 B per vertex) and the
+      element record F_e, V_e, mu, lam' (12 scalars) written;
+    k_gather: element records and the four corner vectors b_a (4 x 4 scalars) per tet, 4
+      incidence entries per tet (16 B); per free vertex u, dz read, m/h^2, the incidence
+      count, D_J written (3) and g, H, R written (18 scalars);
     k_correct: per free vertex g, H, R read (18), D written (3), and n_cub cubature slots of
       (pool index 4 B, weight, 36 U_bar entries); the pool's element data stays in L2;
-    k_energy: tet records; per free vertex u, dz, D, D_J (3 each) and m/h^2;
+    k_energy (one direction; a second launch only when D fails): tet record fields; per free
+      vertex u, dz, the direction (3 each) and m/h^2;
     k_update: per free vertex u read and written, one direction read (3 each)."""
     f = fp_bytes
     rec = 16 + 21 * f
     return {
-        "k_gather": T * (rec + 16) + V_f * ((3 + 3 + 1 + 3 + 18) * f + 4),
+        "k_elem": T * (rec + 12 * f) + V_f * 4 * f,
+        "k_gather": T * (12 * f + 16 * f + 16) + V_f * ((3 + 3 + 1 + 3 + 18) * f + 4),
         "k_correct": V_f * ((18 + 3) * f + n_cub * (4 + 37 * f)),
-        "k_energy": T * rec + V_f * (13 * f),
+        "k_energy": T * rec + V_f * (10 * f),
         "k_update": V_f * (9 * f),
     }
+
+
+def sweep_bytes(V_f, T, n_cub, fp_bytes=4):
+    """Algorithmic bytes of one whole sweep (the method's compulsory traffic, each datum
+    once): per tet the corner ids, B, F(x_t), V_e and material (the tet record fields) and
+    four incidence entries; per free vertex x read and written, z, m, R written, g/H written
+    and read, and the cubature record (pool index, weight, 12x3 U_bar per slot)."""
+    f = fp_bytes
+    per_tet = 16 + 21 * f + 16
+    per_vertex = (3 + 3 + 3 + 1) * f + 9 * f + 2 * 9 * f + n_cub * (4 + 37 * f)
+    return T * per_tet + V_f * per_vertex
 
 
 class Clocks:
@@ -292,23 +309,30 @@ def run_jgs2(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": ck,
     }
+    # whole sweep: the method's algorithmic bytes per sweep over the step time per sweep
+    sw_tot = max(int(sweeps.sum()), 1)
+    sb = sweep_bytes(Vf, T, n_cub, fpb)
+    sweep_gbs = sb / (ms_total / sw_tot * 1e-3) / 1e9
+    out["sweep_roofline"] = {"bound": "hbm", "achieved": round(sweep_gbs, 1), "peak": hbm, "unit": "GB/s",
+                             "frac": round(sweep_gbs / hbm, 4), "bytes_per_sweep": sb,
+                             "ms_per_sweep": round(ms_total / sw_tot, 5),
+                             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
     if batch:
-        # kernels run inside CUDA graphs: the roofline is the whole sweep's algorithmic bytes
-        # over the time per sweep
-        per_sweep_ms = ms_total / max(sweeps.sum(), 1)
-        sweep_bytes = sum(b for k, b in kb.items() if corr != p.CORR_OFF or k != "k_correct")
-        gbs = sweep_bytes / (per_sweep_ms * 1e-3) / 1e9
         out["scene_sweeps"] = scene_sweeps
-        out["roofline"] = {"bound": "hbm", "kernel": "sweep (gather+correct+energy+update, one graph chunk)",
-                           "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
-                           "traffic": None, "bytes_per_launch": sweep_bytes, "avg_launch_ms": round(per_sweep_ms, 5),
-                           "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+        out["roofline"] = dict(out["sweep_roofline"], kernel="sweep (all kernels of a graph-captured chunk)",
+                               traffic=None)
     else:
+        # kernel times are CUDA events around every kernel group in the captured sweep graphs
+        # of the timed steps; a group's time per sweep that did work (gather-side kernels run
+        # sweeps + 1 times per step, the line search and update sweeps times; launches that
+        # returned at once after the stop add their time too, so the averages are upper bounds)
+        n_work = {"k_energy": sw_tot, "k_update": sw_tot}
         share = {KIND[q]: round(float(kms[q] / max(kms.sum(), 1e-12)), 4) for q in range(len(KIND))}
         per_kernel = {}
         for q, name in enumerate(KIND):
             if name in kb and kl[q] > 0:
-                avg = kms[q] / kl[q]
+                nw = n_work.get(name, sw_tot + args.steps)
+                avg = kms[q] / nw
                 per_kernel[name] = {"avg_launch_ms": round(float(avg), 5), "bytes_per_launch": kb[name],
                                     "GB_s": round(kb[name] / (avg * 1e-3) / 1e9, 1),
                                     "frac": round(kb[name] / (avg * 1e-3) / 1e9 / hbm, 4)}

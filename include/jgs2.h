@@ -110,10 +110,11 @@ typedef struct {
 /* kernel kinds in jgs2_step_report.kernel_*: pool (cubature elements), gather (per-vertex
  * gradient, diagonal block, rotation), correct (cubature correction + 3x3 solve), energy
  * (line search), update, setup (per-step setup and write-back), contact (broadphase, narrowphase
- * and barrier terms, several launches counted as one pass) */
-#define JGS2_NKERNELS 7
+ * and barrier terms), elem (per-tet deformation gradients of the sweep). kernel_launches
+ * counts kernels; a pass of several launches (contact: 11) counts each. */
+#define JGS2_NKERNELS 8
 enum { JGS2_K_POOL = 0, JGS2_K_GATHER = 1, JGS2_K_CORRECT = 2, JGS2_K_ENERGY = 3, JGS2_K_UPDATE = 4,
-       JGS2_K_SETUP = 5, JGS2_K_CONTACT = 6 };
+       JGS2_K_SETUP = 5, JGS2_K_CONTACT = 6, JGS2_K_ELEM = 7 };
 
 typedef struct {
   int32_t sweeps;            /* sweeps applied in the step */
@@ -179,7 +180,11 @@ int32_t jgs2_mesh_n_cub(const jgs2_mesh* mesh);
  * x, v: caller-owned DEVICE arrays [V][3] of double on the mesh's device, read as
  * (x_t, v_t) and overwritten with (x_{t+1}, v_{t+1}). stream: a cudaStream_t (NULL =
  * default stream); all work is ordered on it and the call returns after the step
- * completed. report may be NULL. Returns JGS2_ENOTCONVERGED (state written) when
+ * completed. The sweeps run as replays of a CUDA graph of check_every sweeps on a stream
+ * of the mesh, ordered after and before the caller's stream by events; the first step
+ * with a new configuration (precision, correction, line search, block size, check_every,
+ * profile, trace) captures the graph, so jgs2_step is not itself called inside a stream
+ * capture. report may be NULL. Returns JGS2_ENOTCONVERGED (state written) when
  * max_sweeps is hit, JGS2_EDIVERGED (state untouched) on a non-finite residual. */
 jgs2_status jgs2_step(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts,
                       void* stream, jgs2_step_report* report);

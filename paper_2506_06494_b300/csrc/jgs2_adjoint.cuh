@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(128) k_lin_setup(DevMesh<T> m, T* __restrict__
       const T* up = m.cub_u + (size_t)s * 36 * m.Vf + i;
 #pragma unroll
       for (int q = 0; q < 36; ++q) U[q] = up[(size_t)q * m.Vf];
-      const T* Hp = m.pool_H + (size_t)p * kPackedH;
+      const T* Hp = m.pool_H + (size_t)p * kPoolStride;
 #pragma unroll
       for (int r = 0; r < 12; ++r) {
         T tr[3] = {T(0), T(0), T(0)};

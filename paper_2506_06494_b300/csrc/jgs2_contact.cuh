@@ -473,6 +473,31 @@ __global__ void __launch_bounds__(128) k_query_edges(DevMesh<T> m, ContactView c
   }
 }
 
+// Length of the step d of vertex v (0 for pinned vertices, which never move).
+template <typename T>
+__device__ __forceinline__ double step_len(const DevMesh<T>& m, int v, const Vec4<T>* D) {
+  if (v >= m.Vf) return 0.0;
+  const Vec4<T> d = D[v];
+  return sqrt(double(d.x) * double(d.x) + double(d.y) * double(d.y) + double(d.z) * double(d.z));
+}
+
+// Bound on how much a pair's distance can shrink along a d (0 < a <= 1): the distance of a
+// point to a plane, of a point to a triangle and of two segments is 1-Lipschitz in each
+// side's motion, and a closest point on a triangle or segment is a convex combination of
+// its corners, so d(x + a d) >= d(x) - (max step on one side + max step on the other).
+template <typename T>
+__device__ __forceinline__ double pair_motion(const DevMesh<T>& m, const ContactView& c, uint64_t key,
+                                              const Vec4<T>* D) {
+  const int kind = (int)(key >> 60), ia = (int)((key >> 30) & 0x3fffffff), ib = (int)(key & 0x3fffffff);
+  if (kind == 0) return step_len(m, ia, D);
+  if (kind == 1) {
+    const int f0 = c.faces[3 * ib], f1 = c.faces[3 * ib + 1], f2 = c.faces[3 * ib + 2];
+    return step_len(m, ia, D) + fmax(step_len(m, f0, D), fmax(step_len(m, f1, D), step_len(m, f2, D)));
+  }
+  const int e0 = c.edges[2 * ia], e1 = c.edges[2 * ia + 1], g0 = c.edges[2 * ib], g1 = c.edges[2 * ib + 1];
+  return fmax(step_len(m, e0, D), step_len(m, e1, D)) + fmax(step_len(m, g0, D), step_len(m, g1, D));
+}
+
 // Geometry of a pair at x (+ a d): distance, involved vertices and dd/dx per vertex.
 template <typename T>
 __device__ __forceinline__ double pair_geom(const DevMesh<T>& m, const ContactView& c, uint64_t key, double a,

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <memory>
 #include <numeric>
 #include <set>
@@ -45,7 +46,7 @@ static cudaError_t dalloc(X** p, size_t n) {
 
 template <typename T>
 void PrecBufs<T>::release() {
-  cudaFree(tets); cudaFree(u); cudaFree(dz); cudaFree(D); cudaFree(DJ); cudaFree(ghr); cudaFree(mh2);
+  cudaFree(tets); cudaFree(frec); cudaFree(bc); cudaFree(u); cudaFree(dz); cudaFree(D); cudaFree(DJ); cudaFree(ghr); cudaFree(mh2);
   cudaFree(cub_p); cudaFree(cub_w); cudaFree(cub_u); cudaFree(pool_H); cudaFree(pool_G); cudaFree(pool_R);
   cudaFree(a_lam); cudaFree(a_r); cudaFree(a_z); cudaFree(a_p); cudaFree(a_q); cudaFree(a_lin);
   *this = PrecBufs<T>();
@@ -62,6 +63,7 @@ Mesh::~Mesh() {
   cudaFree(d_adjsc);
   if (h_state) cudaFreeHost(h_state);
   for (cudaEvent_t e : events) cudaEventDestroy(e);
+  for (cudaEvent_t e : gevents) cudaEventDestroy(e);
   if (graph) cudaGraphExecDestroy(graph);
   if (gstream) cudaStreamDestroy(gstream);
   for (cudaEvent_t e : gev)
@@ -337,7 +339,10 @@ static jgs2_status ensure_device(Mesh* m) {
     CK(dalloc(&m->d_perm, V));
     CK(dalloc(&m->d_state, 1));
     CK(dalloc(&m->d_trace, JGS2_TRACE_MAX));
-    const size_t np = std::max<size_t>(4 * kLsTrials * ((size_t)(T + 127) / 128 + (m->Vf + 127) / 128 + 1), 16);
+    // sweep partials: [3][vertex blocks] (gather/correct), [6][energy blocks] plus
+    // [kLsTrials][kPairTrialBlocks] (line search); batch and adjoint passes use fewer
+    const size_t np = std::max<size_t>(4 * kLsTrials * ((size_t)(T + 127) / 128 + (m->Vf + 127) / 128 + 1),
+                                       (size_t)6 * kEnergyBlocksMax + (size_t)kLsTrials * kPairTrialBlocks + 16);
     CK(dalloc(&m->d_partial, np));
     CK(cudaMallocHost((void**)&m->h_state, sizeof(StepState)));
     CK(cudaMemcpy(m->d_inc_off, m->inc_off.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
@@ -443,6 +448,8 @@ static jgs2_status ensure_prec(Mesh* m) {
     std::vector<T> mh2(V, T(0));
     for (int i = 0; i < m->Vf; ++i) mh2[i] = T(m->mass[m->perm[i]] / (m->h * m->h));
     CK(dalloc(&b.tets, T_));
+    CK(dalloc(&b.frec, T_));
+    CK(dalloc(&b.bc, 4 * (size_t)T_));
     CK(dalloc(&b.u, V));
     CK(dalloc(&b.dz, m->Vf));
     CK(dalloc(&b.D, m->Vf));
@@ -470,7 +477,7 @@ static jgs2_status ensure_prec(Mesh* m) {
     CK(dalloc(&b.cub_p, nc * Vf));
     CK(dalloc(&b.cub_w, nc * Vf));
     CK(dalloc(&b.cub_u, nc * 36 * Vf));
-    CK(dalloc(&b.pool_H, (size_t)m->nP * kPackedH));
+    CK(dalloc(&b.pool_H, (size_t)m->nP * kPoolStride));
     CK(dalloc(&b.pool_G, (size_t)m->nP * 12));
     cudaFree(b.pool_R);
     CK(dalloc(&b.pool_R, (size_t)m->nP * 36));
@@ -486,6 +493,10 @@ template <typename T>
 static DevMesh<T> dev_view(Mesh* m) {
   PrecBufs<T>& b = bufs<T>(m);
   DevMesh<T> d;
+  // zero every byte (padding included): a captured sweep graph is re-used only while the
+  // view compares equal byte for byte (all defaults of the view are zero)
+  static_assert(std::is_trivially_copyable<DevMesh<T>>::value, "device view must be trivially copyable");
+  std::memset(static_cast<void*>(&d), 0, sizeof(d));
   d.V = m->V;
   d.Vf = m->Vf;
   d.T_ = m->T;
@@ -494,6 +505,8 @@ static DevMesh<T> dev_view(Mesh* m) {
   d.n_cub = m->n_cub;
   d.tets = b.tets;
   d.tets_mut = b.tets;
+  d.frec = b.frec;
+  d.bc = b.bc;
   d.inc_off = m->d_inc_off;
   d.inc_len = m->d_inc_len;
   d.inc = m->d_inc;
@@ -626,6 +639,8 @@ jgs2_status import_cubature(Mesh* m, const jgs2_cubature_blob* b) {
 
 // Candidate pairs within r_c at x^k, the barrier accumulators and the per-vertex minimum
 // distances (Sec. 7). Pair order is not canonical here (the sums use atomics).
+constexpr int kContactKernels = 11;  // launches of one contact_pass
+
 template <typename T>
 static jgs2_status contact_pass(Mesh* m, DevMesh<T>& d, cudaStream_t s, StepState* st) {
   const ContactView& c = d.c;
@@ -659,14 +674,14 @@ static jgs2_status contact_force_rebuild(Mesh* m, cudaStream_t s) {
 
 // k_gather / k_correct with a runtime block size (64, 128 or 256 threads)
 template <typename T, bool BATCH>
-static void launch_gather(DevMesh<T>& d, bool corr, int bs, cudaStream_t s, StepState* st, int k, double* partial,
+static void launch_gather(DevMesh<T>& d, bool corr, int bs, cudaStream_t s, StepState* st, double* partial,
                           double* trace, int rec) {
   const int Vf = d.Vf;
 #define JGS2_G(B)                                                                                  \
   if (corr)                                                                                        \
-    k_gather<T, true, BATCH, B><<<(Vf + B - 1) / B, B, 0, s>>>(d, st, k, partial, trace, rec);     \
+    k_gather<T, true, BATCH, B><<<(Vf + B - 1) / B, B, 0, s>>>(d, st, partial, trace, rec);        \
   else                                                                                             \
-    k_gather<T, false, BATCH, B><<<(Vf + B - 1) / B, B, 0, s>>>(d, st, k, partial, trace, rec);
+    k_gather<T, false, BATCH, B><<<(Vf + B - 1) / B, B, 0, s>>>(d, st, partial, trace, rec);
   if (bs == 64) {
     JGS2_G(64)
   } else if (bs == 256) {
@@ -678,15 +693,15 @@ static void launch_gather(DevMesh<T>& d, bool corr, int bs, cudaStream_t s, Step
 }
 
 template <typename T, bool BATCH>
-static void launch_correct(DevMesh<T>& d, int bs, cudaStream_t s, StepState* st, int k, double* partial,
+static void launch_correct(DevMesh<T>& d, int bs, cudaStream_t s, StepState* st, double* partial,
                            double* trace, int rec) {
   const int Vf = d.Vf;
   if (bs == 64)
-    k_correct<T, BATCH, 64><<<(Vf + 63) / 64, 64, 0, s>>>(d, st, k, partial, trace, rec);
+    k_correct<T, BATCH, 64><<<(Vf + 63) / 64, 64, 0, s>>>(d, st, partial, trace, rec);
   else if (bs == 256)
-    k_correct<T, BATCH, 256><<<(Vf + 255) / 256, 256, 0, s>>>(d, st, k, partial, trace, rec);
+    k_correct<T, BATCH, 256><<<(Vf + 255) / 256, 256, 0, s>>>(d, st, partial, trace, rec);
   else
-    k_correct<T, BATCH, 128><<<(Vf + 127) / 128, 128, 0, s>>>(d, st, k, partial, trace, rec);
+    k_correct<T, BATCH, 128><<<(Vf + 127) / 128, 128, 0, s>>>(d, st, partial, trace, rec);
 }
 
 // Launch bookkeeping of one step: counts per kernel kind and, when profiling, a CUDA
@@ -695,12 +710,14 @@ struct Launches {
   Mesh* m;
   cudaStream_t s;
   bool prof;
-  int count[JGS2_NKERNELS] = {0, 0, 0, 0, 0, 0, 0};
+  int count[JGS2_NKERNELS] = {};
+  double gms[JGS2_NKERNELS] = {};  // event times of graph replays
   std::vector<std::pair<int, int>> rec;  // (kind, event index)
   int used = 0;
   cudaError_t err = cudaSuccess;
-  int begin(int kind) {
-    count[kind]++;
+  // a group of n kernels of one kind launched directly on the stream
+  int begin(int kind, int n = 1) {
+    count[kind] += n;
     if (!prof) return -1;
     if ((int)m->events.size() < used + 2) {
       for (int q = 0; q < 64; ++q) {
@@ -729,6 +746,7 @@ struct Launches {
     }
     if (r) r->launches = tot;
     if (!r || !prof) return;
+    for (int q = 0; q < JGS2_NKERNELS; ++q) r->kernel_ms[q] += gms[q];
     for (auto& kv : rec) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, m->events[kv.second], m->events[kv.second + 1]) == cudaSuccess)
@@ -737,84 +755,147 @@ struct Launches {
   }
 };
 
+// Private non-blocking stream (and ordering events) the sweep graphs are captured and
+// replayed on: the caller's stream may be the legacy default stream, which cannot be
+// captured. Work on it is ordered after and before the caller's stream by events.
+static jgs2_status ensure_gstream(Mesh* m) {
+  if (!m->gstream) {
+    CK(cudaStreamCreateWithFlags(&m->gstream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&m->gev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&m->gev[1], cudaEventDisableTiming));
+  }
+  return JGS2_OK;
+}
+
+// The sweeps of one step (single scene). Sweep k reads its index from the device step
+// state, so every sweep is the same sequence of launches: a chunk of check_every sweeps is
+// captured once per launch configuration into a CUDA graph and replayed until the device
+// flags the step done (converged, diverged or max_k sweeps). Sweeps after that flag are
+// empty launches. With check = false the host does not wait between replays and runs
+// ceil((max_k + 1) / chunk) of them. Profiling puts external event nodes around every
+// kernel group of the chunk; their times are read after each replay.
 template <typename T>
-static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t s, int max_k, double rel_tol,
+static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs, int max_k, double rel_tol,
                               bool check, StepState* hs, Launches& L) {
   DevMesh<T> d = dev_view<T>(m);
   const bool corr = o.correction != JGS2_CORR_OFF;
   const int nbV = (m->Vf + 127) / 128;
   const int nbT = (m->T + 127) / 128;
   // line-search pass: grid-stride over tets and vertices, about 4 tets per thread
-  const int nbE = std::max(1, std::min(std::max(nbT, nbV), 148 * 8));
+  const int nbE = std::max(1, std::min(std::max(nbT, nbV), kEnergyBlocksMax));
+  const int bs = m->bs[sizeof(T) == 4 ? 1 : 0];
+  const int chunk = std::max(1, o.check_every);
+  const bool prof = L.prof;
+  jgs2_status gs = ensure_gstream(m);
+  if (gs != JGS2_OK) return gs;
+  cudaStream_t s = m->gstream;
+  CK(cudaEventRecord(m->gev[0], cs));
+  CK(cudaStreamWaitEvent(s, m->gev[0], 0));
   StepState init;
   std::memset(&init, 0, sizeof(init));
   init.max_sweeps = max_k;
   init.rel_tol = rel_tol;
   init.alpha = 1.0;
   CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
-  const int every = std::max(1, o.check_every);
   if (m->contact) {
-    jgs2_status cs = contact_force_rebuild(m, s);
-    if (cs != JGS2_OK) return cs;
+    jgs2_status cst = contact_force_rebuild(m, s);
+    if (cst != JGS2_OK) return cst;
   }
-  for (int k = 0; k <= max_k; ++k) {
-    int id;
-    if (m->contact) {
-      id = L.begin(JGS2_K_CONTACT);
-      jgs2_status cs = contact_pass<T>(m, d, s, m->d_state);
-      L.end(id);
-      if (cs != JGS2_OK) return cs;
+  const long key = (((((((long)(sizeof(T) == 4) * 3 + o.correction) * 2 + (o.line_search != 0)) * 2 + m->contact) * 2 +
+                     (prof ? 1 : 0)) * 2 + (o.record_trace != 0)) * 512 + bs) * 8192 + chunk + (1L << 40);
+  const bool same_view = m->gdev.size() == sizeof(d) && std::memcmp(m->gdev.data(), &d, sizeof(d)) == 0;
+  if (m->graph_key != key || !same_view) {
+    if (m->graph) cudaGraphExecDestroy(m->graph);
+    m->graph = nullptr;
+    m->graph_key = -1;
+    m->ggroups.clear();
+    const size_t nev = prof ? (size_t)14 * chunk : 0;
+    while (m->gevents.size() < nev) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      m->gevents.push_back(e);
     }
-    if (corr && m->nP > 0) {
-      id = L.begin(JGS2_K_POOL);
-      if (o.correction == JGS2_CORR_ASM)
-        k_pool<T, true><<<m->nP, 128, 0, s>>>(d, m->d_state);
-      else
-        k_pool<T, false><<<m->nP, 128, 0, s>>>(d, m->d_state);
-      L.end(id);
-    }
-    if (nbV > 0) {
-      const int bs = m->bs[sizeof(T) == 4 ? 1 : 0];
-      id = L.begin(JGS2_K_GATHER);
-      launch_gather<T, false>(d, corr, bs, s, m->d_state, k, m->d_partial, m->d_trace, o.record_trace);
-      L.end(id);
-      if (corr) {
-        id = L.begin(JGS2_K_CORRECT);
-        launch_correct<T, false>(d, bs, s, m->d_state, k, m->d_partial, m->d_trace, o.record_trace);
-        L.end(id);
+    size_t evi = 0;
+    cudaError_t cerr = cudaSuccess;
+    auto group = [&](int kind, int n, auto&& launch) {
+      Mesh::GraphGroup g{kind, n, nullptr, nullptr};
+      if (prof) {
+        g.e0 = m->gevents[evi++];
+        g.e1 = m->gevents[evi++];
+        if (cerr == cudaSuccess) cerr = cudaEventRecordWithFlags(g.e0, s, cudaEventRecordExternal);
       }
-    }
-    if (k == max_k) break;
-    if (o.line_search) {
-      id = L.begin(JGS2_K_ENERGY);
-      if (m->contact) {
+      launch();
+      if (prof && cerr == cudaSuccess) cerr = cudaEventRecordWithFlags(g.e1, s, cudaEventRecordExternal);
+      m->ggroups.push_back(g);
+    };
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int q = 0; q < chunk; ++q) {
+      if (m->contact) group(JGS2_K_CONTACT, kContactKernels, [&] { contact_pass<T>(m, d, s, m->d_state); });
+      if (corr && m->nP > 0)
+        group(JGS2_K_POOL, 1, [&] {
+          if (o.correction == JGS2_CORR_ASM)
+            k_pool<T, true><<<m->nP, 128, 0, s>>>(d, m->d_state);
+          else
+            k_pool<T, false><<<m->nP, 128, 0, s>>>(d, m->d_state);
+        });
+      if (nbV > 0) {
+        group(JGS2_K_ELEM, 1, [&] { k_elem<T, false><<<nbT, 128, 0, s>>>(d, m->d_state); });
+        group(JGS2_K_GATHER, 1,
+              [&] { launch_gather<T, false>(d, corr, bs, s, m->d_state, m->d_partial, m->d_trace, o.record_trace); });
         if (corr)
-          k_energy<T, 2, true><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
-        else
-          k_energy<T, 1, true><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
-      } else {
-        if (corr)
-          k_energy<T, 2, false><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
-        else
-          k_energy<T, 1, false><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
+          group(JGS2_K_CORRECT, 1,
+                [&] { launch_correct<T, false>(d, bs, s, m->d_state, m->d_partial, m->d_trace, o.record_trace); });
       }
-      L.end(id);
+      if (o.line_search) {
+        // along D; along D_J only when every trial along D failed (those launches return
+        // at once otherwise)
+        const int npp = m->contact ? kPairTrialBlocks : 0;
+        double* pp = m->d_partial + (size_t)6 * nbE;
+        group(JGS2_K_ENERGY, (corr ? 2 : 1) * (m->contact ? 2 : 1), [&] {
+          if (m->contact) k_pair_trials<T, 0><<<npp, 128, 0, s>>>(d, m->d_state, pp);
+          k_energy<T, 0><<<nbE, 128, 0, s>>>(d, m->d_state, corr ? 1 : 0, m->d_partial, pp, npp);
+          if (corr) {
+            if (m->contact) k_pair_trials<T, 1><<<npp, 128, 0, s>>>(d, m->d_state, pp);
+            k_energy<T, 1><<<nbE, 128, 0, s>>>(d, m->d_state, 1, m->d_partial, pp, npp);
+          }
+        });
+      }
+      if (nbV > 0) group(JGS2_K_UPDATE, 1, [&] { k_update<T><<<nbV, 128, 0, s>>>(d, m->d_state); });
     }
-    if (nbV > 0) {
-      id = L.begin(JGS2_K_UPDATE);
-      k_update<T><<<nbV, 128, 0, s>>>(d, m->d_state);
-      L.end(id);
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) return fail(JGS2_ECUDA, std::string("sweep capture: ") + cudaGetErrorString(e));
+    if (cerr != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return fail(JGS2_ECUDA, std::string("sweep capture (timing events): ") + cudaGetErrorString(cerr));
     }
-    CK(cudaGetLastError());
-    if (check && (k + 1) % every == 0) {
+    e = cudaGraphInstantiate(&m->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(JGS2_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    m->graph_key = key;
+    m->gdev.assign(reinterpret_cast<const char*>(&d), reinterpret_cast<const char*>(&d) + sizeof(d));
+  }
+  const int replays = (max_k + chunk) / chunk;  // ceil((max_k + 1) / chunk)
+  for (int rp = 0; rp < replays; ++rp) {
+    CK(cudaGraphLaunch(m->graph, s));
+    for (const auto& g : m->ggroups) L.count[g.kind] += g.n;
+    if (check || prof) {
       CK(cudaMemcpyAsync(hs, m->d_state, sizeof(StepState), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      if (hs->done) break;
+      if (prof) {
+        for (const auto& g : m->ggroups) {
+          float ms = 0.f;
+          if (cudaEventElapsedTime(&ms, g.e0, g.e1) == cudaSuccess) L.gms[g.kind] += ms;
+        }
+      }
+      if (check && hs->done) break;
     }
   }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(hs, m->d_state, sizeof(StepState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  CK(cudaEventRecord(m->gev[1], s));
+  CK(cudaStreamWaitEvent(cs, m->gev[1], 0));
   if (m->contact) {
     int32_t fl[2];
     CK(cudaMemcpy(fl, m->d_cflags, sizeof(fl), cudaMemcpyDeviceToHost));
@@ -835,11 +916,8 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
   DevMesh<T> d = dev_view<T>(m);
   // the caller's stream may be the legacy default stream, which cannot be captured: the
   // sweeps run on a private stream ordered after (and before) the caller's work
-  if (!m->gstream) {
-    CK(cudaStreamCreateWithFlags(&m->gstream, cudaStreamNonBlocking));
-    CK(cudaEventCreateWithFlags(&m->gev[0], cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&m->gev[1], cudaEventDisableTiming));
-  }
+  jgs2_status gs = ensure_gstream(m);
+  if (gs != JGS2_OK) return gs;
   cudaStream_t s = m->gstream;
   CK(cudaEventRecord(m->gev[0], cs));
   CK(cudaStreamWaitEvent(s, m->gev[0], 0));
@@ -860,8 +938,9 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
                    chunk + (long)(o.max_sweeps) * 1000003L + (long)(o.rel_tol * 1e12);
   auto sweep_once = [&]() {
     if (corr) k_pool<T, true><<<m->nP, 128, 0, s>>>(d, m->d_state);
-    launch_gather<T, true>(d, corr, bs, s, m->d_state, 0, m->d_partial, m->d_trace, 0);
-    if (corr) launch_correct<T, true>(d, bs, s, m->d_state, 0, m->d_partial, m->d_trace, 0);
+    k_elem<T, true><<<nbT, 128, 0, s>>>(d, m->d_state);
+    launch_gather<T, true>(d, corr, bs, s, m->d_state, m->d_partial, m->d_trace, 0);
+    if (corr) launch_correct<T, true>(d, bs, s, m->d_state, m->d_partial, m->d_trace, 0);
     k_scene_finalize_main<<<(S + 127) / 128, 128, 0, s>>>(m->d_scenes, m->d_sacc, S, o.rel_tol, o.max_sweeps,
                                                            corr ? 1 : 0, m->d_ndone);
     if (o.line_search) {
@@ -890,6 +969,7 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
     CK(cudaGraphLaunch(m->graph, s));
     // kernel nodes per replay, by kind (the per-scene stopping test counts with the update)
     L.count[JGS2_K_POOL] += corr ? chunk : 0;
+    L.count[JGS2_K_ELEM] += chunk;
     L.count[JGS2_K_GATHER] += chunk;
     L.count[JGS2_K_CORRECT] += corr ? chunk : 0;
     L.count[JGS2_K_ENERGY] += o.line_search ? 2 * chunk : 0;
@@ -1216,21 +1296,24 @@ static jgs2_status autotune_impl(Mesh* m, double* x, double* v, const jgs2_step_
   init.rel_tol = -1.0;
   CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
   if (corr) k_pool<T, true><<<m->nP, 128, 0, s>>>(d, m->d_state);
+  k_elem<T, false><<<(m->T + 127) / 128, 128, 0, s>>>(d, m->d_state);
   const int cands[3] = {64, 128, 256};
   float best = 1e30f;
   int pick = 128;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
+  // every timed launch is sweep 0 of a fresh state: it sets |g(x^0)| and never stops the
+  // step (rel_tol < 0, no sweep cap), so each launch does the full work
   for (int c : cands) {
     for (int rep = 0; rep < 2; ++rep) {
-      launch_gather<T, false>(d, corr, c, s, m->d_state, 1, m->d_partial, m->d_trace, 0);
-      if (corr) launch_correct<T, false>(d, c, s, m->d_state, 1, m->d_partial, m->d_trace, 0);
+      launch_gather<T, false>(d, corr, c, s, m->d_state, m->d_partial, m->d_trace, 0);
+      if (corr) launch_correct<T, false>(d, c, s, m->d_state, m->d_partial, m->d_trace, 0);
     }
     CK(cudaEventRecord(e0, s));
     for (int rep = 0; rep < 5; ++rep) {
-      launch_gather<T, false>(d, corr, c, s, m->d_state, 1, m->d_partial, m->d_trace, 0);
-      if (corr) launch_correct<T, false>(d, c, s, m->d_state, 1, m->d_partial, m->d_trace, 0);
+      launch_gather<T, false>(d, corr, c, s, m->d_state, m->d_partial, m->d_trace, 0);
+      if (corr) launch_correct<T, false>(d, c, s, m->d_state, m->d_partial, m->d_trace, 0);
     }
     CK(cudaEventRecord(e1, s));
     CK(cudaEventSynchronize(e1));
@@ -1321,7 +1404,8 @@ static jgs2_status adjoint_impl(Mesh* m, const double* xt, const double* vt, con
   CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
   // H_ii, R_i at x* (and the rotated cubature element Hessians)
   if (corr) k_pool<T, true><<<m->nP, 128, 0, s>>>(d, m->d_state);
-  k_gather<T, true, false, 128><<<nbV, 128, 0, s>>>(d, m->d_state, 0, m->d_partial, m->d_trace, 0);
+  k_elem<T, false><<<nbT, 128, 0, s>>>(d, m->d_state);
+  k_gather<T, true, false, 128><<<nbV, 128, 0, s>>>(d, m->d_state, m->d_partial, m->d_trace, 0);
   if (corr)
     k_lin_setup<T, true><<<nbV, 128, 0, s>>>(d, b.a_lin);
   else

@@ -14,6 +14,8 @@ struct PrecBufs {
   bool ready = false;
   int cub_version = -1;
   TetRec<T>* tets = nullptr;
+  FRec<T>* frec = nullptr;
+  Vec4<T>* bc = nullptr;
   Vec4<T>* u = nullptr;
   Vec4<T>* dz = nullptr;
   Vec4<T>* D = nullptr;
@@ -76,6 +78,16 @@ struct Mesh {
   long graph_key = -1;
   cudaStream_t gstream = nullptr;   // private stream the graph is captured on and replayed on
   cudaEvent_t gev[2] = {nullptr, nullptr};
+  // single-scene steps: the device view the chunk was captured with (re-captured when a
+  // device buffer moves) and its kernel groups in launch order, each with the number of
+  // kernels and, when profiling, the pair of external timing events recorded around it
+  struct GraphGroup {
+    int kind, n;
+    cudaEvent_t e0, e1;
+  };
+  std::vector<char> gdev;
+  std::vector<GraphGroup> ggroups;
+  std::vector<cudaEvent_t> gevents;
   // contact (Sec. 7): surface in internal vertex ids
   int contact = 0;
   double dhat = 0.0, kappa = 0.0, rc = 0.0;

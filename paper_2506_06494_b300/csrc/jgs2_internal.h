@@ -5,6 +5,8 @@
 //   TetRec<T>   one 16-byte aligned record per tet, tets sorted by smallest corner:
 //               corner ids, D_m^{-1} (B), F(x_t) (per step), V_e, mu, lam' = lam + mu,
 //               rho V_e / 4 (the element's share of each corner's lumped mass).
+//   FRec<T>     per tet, rewritten every sweep by the element pass: F_e(x^k), V_e, mu, lam'.
+//   bc          per tet and corner, the corner vector b_a (Vec4, one 16-byte load).
 //   Vec4<T>     per-vertex displacement u = x - x_t (the sweep works in displacement so
 //               that FP32 keeps the precision of small per-step motions), the inertia
 //               offset dz = z - x_t = h v_t + h^2 g, and the sweep direction D.
@@ -12,7 +14,8 @@
 //               off[slice] + 32 j + l, value = 4*tet + corner (coalesced warp reads).
 //   cubature    per free vertex and slot s: pool slot index, weight, and U_bar rows
 //               (12x3) as [slot][36][Vf] so a warp's loads are coalesced.
-//   pool        per sweep, the rotated 12x12 element Hessian (78 packed values) and
+//   pool        per sweep, one 16-byte aligned row per cubature element: the rotated
+//               12x12 element Hessian (78 packed values), then
 //               the 12 rotated gradient entries of every cubature element.
 #pragma once
 #include <cstdint>
@@ -23,7 +26,10 @@ namespace jgs2 {
 constexpr int kSlice = 32;       // vertices per incidence slice (one warp)
 constexpr int kMaxCub = 8;       // cubature slots per vertex at most
 constexpr int kLsTrials = 8;     // line-search steps alpha = 2^-j, j < kLsTrials
+constexpr int kPairTrialBlocks = 148 * 4;  // blocks of the line-search barrier-trial pass
+constexpr int kEnergyBlocksMax = 148 * 8;  // blocks of the line-search energy pass, at most
 constexpr int kPackedH = 78;     // 12x12 symmetric, upper triangle row-major
+constexpr int kPoolStride = 92;  // pool row: 78 packed Hessian entries, 12 gradient entries, 2 pad
 
 template <typename T>
 struct alignas(16) TetRec {
@@ -38,6 +44,14 @@ struct alignas(16) Vec4 {
   T x, y, z, w;
 };
 
+// Per-sweep element record written by the element pass: F_e(x^k) and the element's
+// constants, read by the vertex gather (48 bytes in FP32: three 16-byte loads).
+template <typename T>
+struct alignas(16) FRec {
+  T F[9];
+  T vol, mu, lp;
+};
+
 // Device-resident step state (one per mesh), read and written by the sweep kernels.
 struct StepState {
   int32_t done;        // set once the step stops (converged / max sweeps / diverged)
@@ -47,7 +61,7 @@ struct StepState {
   int32_t fallback;    // vertex solves that fell back to the uncorrected step
   int32_t ls_rejects;
   int32_t max_sweeps;
-  int32_t pad;
+  int32_t k;           // index of the next sweep (read and advanced by finalize_sweep)
   double rel_tol;
   double g0;           // |g(x^0)|
   double r;            // last relative residual
@@ -55,7 +69,7 @@ struct StepState {
   double slope_j;      // g^T D_J (uncorrected direction)
   double alpha;        // accepted step of the current sweep
   int32_t dir;         // 0: step along D, 1: along D_J
-  int32_t pad2;
+  int32_t need_j;      // every line-search trial along D failed: try D_J
   uint32_t ticket_main;
   uint32_t ticket_energy;
 };
@@ -109,6 +123,8 @@ struct DevMesh {
   int V, Vf, T_, n_slices, nP, n_cub;
   const TetRec<T>* tets;
   TetRec<T>* tets_mut;
+  FRec<T>* frec;            // [T] F_e(x^k) of the current sweep (element pass)
+  Vec4<T>* bc;              // [T][4] corner vectors b_a = rows of D_m^{-1}, b_0 = -(b_1+b_2+b_3)
   const int32_t* inc_off;   // [n_slices + 1]
   const int32_t* inc_len;   // [Vf]
   const int32_t* inc;       // entries
@@ -122,7 +138,7 @@ struct DevMesh {
   const T* cub_w;           // [n_cub][Vf]
   const T* cub_u;           // [n_cub][36][Vf]
   const int32_t* pool_tet;  // [nP]
-  T* pool_H;                // [nP][78]
+  T* pool_H;                // [nP][92] packed rotated Hessian (78), rotated gradient (12), pad
   T* pool_G;                // [nP][12]
   T* pool_R;                // [nP][4][9] corner rotations of the last pool pass
   double* xt;               // [V][3]

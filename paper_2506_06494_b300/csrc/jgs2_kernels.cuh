@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
 
 #include "jgs2_internal.h"
 
@@ -55,6 +56,74 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* [32*N
     for (int j = 0; j < NV; ++j) {
       double x = lane < nw ? smem[j * 32 + lane] : 0.0;
       v[j] = warp_sum(x);
+    }
+  }
+  __syncthreads();
+}
+
+// Per-thread accumulator of a reduction. FP64 path: a double. FP32 path: a float-float
+// pair h + l (|l| <= ulp(h)/2, about 48 significant bits) formed with Knuth's two-sum and
+// exact FMA products on the FP32 units, so the sums keep FP64-class precision without
+// the FP64 pipe (a small fraction of FP32 throughput on this part).
+template <typename T>
+struct Acc;
+
+template <>
+struct Acc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ double value() const { return v; }
+  __device__ __forceinline__ void add_lane(int o) { v += __shfl_down_sync(0xffffffffu, v, o); }
+};
+
+template <>
+struct Acc<float> {
+  float h = 0.f, l = 0.f;
+  // (h, l) += (bh, bl): two-sum of the leading parts, then the trailing parts
+  __device__ __forceinline__ void add2(float bh, float bl) {
+    const float s = h + bh;
+    const float bb = s - h;
+    float e = (h - (s - bb)) + (bh - bb);
+    e += l + bl;
+    h = s + e;
+    l = e - (h - s);
+  }
+  __device__ __forceinline__ void add(float x) { add2(x, 0.f); }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    add2(p, fmaf(a, b, -p));  // a*b = p + fma(a, b, -p) exactly
+  }
+  __device__ __forceinline__ double value() const { return double(h) + double(l); }
+  __device__ __forceinline__ void add_lane(int o) {
+    const float bh = __shfl_down_sync(0xffffffffu, h, o);
+    const float bl = __shfl_down_sync(0xffffffffu, l, o);
+    add2(bh, bl);
+  }
+};
+
+// Fixed-order block sum of NV accumulators per thread; out valid in thread 0.
+// smem holds 32 * NV entries of Acc<T>.
+template <typename T, int NV>
+__device__ __forceinline__ void block_sum_acc(Acc<T> (&a)[NV], double (&out)[NV], Acc<T>* smem) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[j].add_lane(o);
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) smem[j * 32 + wid] = a[j];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      Acc<T> x;
+      if (lane < nw) x = smem[j * 32 + lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x.add_lane(o);
+      out[j] = x.value();
     }
   }
   __syncthreads();
@@ -109,6 +178,18 @@ __device__ __forceinline__ void load3(const Vec4<T>* a, int i, T (&o)[3]) {
   o[2] = q.z;
 }
 
+// Copies the records of tets [t0, t0 + n) into shared memory with coalesced 16-byte loads
+// (a record is a whole number of 16-byte words), so that the per-tet reads that follow
+// come from shared memory instead of strided global loads.
+template <typename T, int NT>
+__device__ __forceinline__ void stage_tets(const TetRec<T>* __restrict__ src, int t0, int n, TetRec<T>* dst) {
+  constexpr int W = int(sizeof(TetRec<T>) / 16);
+  static_assert(sizeof(TetRec<T>) % 16 == 0, "tet record must be a whole number of 16-byte words");
+  const float4* s = reinterpret_cast<const float4*>(src + t0);
+  float4* d = reinterpret_cast<float4*>(dst);
+  for (int q = threadIdx.x; q < n * W; q += NT) d[q] = __ldg(s + q);
+}
+
 // Deformation gradient of a tet at x = x_t + u: F = F(x_t) + [u1-u0, u2-u0, u3-u0] B.
 template <typename T>
 __device__ __forceinline__ void tet_F(const TetRec<T>& r, const Vec4<T>* u, T (&F)[9]) {
@@ -151,14 +232,15 @@ __device__ __forceinline__ void corner_b(const TetRec<T>& r, int c, T (&b)[3]) {
   }
 }
 
-// Gather of vertex v over its incident tets (Sec. 3 energy; Sec. 4.3 vertex rotation):
+// Gather of vertex v over its incident tets, each F_e formed from the tet record and the
+// displacements of its corners (used outside the sweep, where no element pass ran):
 //   g  += V_e P(F_e) b_c                      (elastic gradient, P = mu F + s cof F)
 //   H  += V_e (mu |b_c|^2 I + lam' G G^T)     (diagonal 3x3 block; G = cof(F) b_c. The
 //         det-Hessian term of dP/dF contributes nothing to a diagonal block because
 //         eps_jln b_j b_l = 0, so this block is exact and positive definite.)
 //   Fs += V_e F_e,  W += V_e
 template <typename T>
-__device__ __forceinline__ void gather_vertex(const DevMesh<T>& m, int v, T (&g)[3], T (&H)[6],
+__device__ __forceinline__ void gather_vertex_rec(const DevMesh<T>& m, int v, T (&g)[3], T (&H)[6],
                                               T (&Fs)[9], T& W) {
   const int slice = v / kSlice, lane = v % kSlice;
   const int base = m.inc_off[slice] + lane;
@@ -198,6 +280,58 @@ __device__ __forceinline__ void gather_vertex(const DevMesh<T>& m, int v, T (&g)
     H[5] += vm * bb + vl * G[2] * G[2];
 #pragma unroll
     for (int q = 0; q < 9; ++q) Fs[q] += r.vol * F[q];
+    W += r.vol;
+  }
+}
+
+// Gather of vertex v over its incident tets (Sec. 3 energy; Sec. 4.3 vertex rotation),
+// from the element pass's F_e (FRec, three 16-byte loads) and the corner vector b_c (one):
+//   g  += V_e P(F_e) b_c                      (elastic gradient, P = mu F + s cof F)
+//   H  += V_e (mu |b_c|^2 I + lam' G G^T)     (diagonal 3x3 block; G = cof(F) b_c. The
+//         det-Hessian term of dP/dF contributes nothing to a diagonal block because
+//         eps_jln b_j b_l = 0, so this block is exact and positive definite.)
+//   Fs += V_e F_e,  W += V_e
+template <typename T>
+__device__ __forceinline__ void gather_vertex(const DevMesh<T>& m, int v, T (&g)[3], T (&H)[6],
+                                              T (&Fs)[9], T& W) {
+  const int slice = v / kSlice, lane = v % kSlice;
+  const int base = m.inc_off[slice] + lane;
+  const int n = m.inc_len[v];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) g[q] = T(0);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) H[q] = T(0);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) Fs[q] = T(0);
+  W = T(0);
+  for (int j = 0; j < n; ++j) {
+    const int ent = __ldg(m.inc + base + j * kSlice);
+    const int t = ent >> 2, c = ent & 3;
+    const FRec<T> r = m.frec[t];
+    const Vec4<T> bq = m.bc[4 * (size_t)t + c];
+    const T b[3] = {bq.x, bq.y, bq.z};
+    T C[9];
+    cofactor(r.F, C);
+    const T J = r.F[0] * C[0] + r.F[1] * C[1] + r.F[2] * C[2];
+    const T s = r.lp * (J - T(1)) - r.mu;
+    T Fb[3], G[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Fb[i] = r.F[3 * i] * b[0] + r.F[3 * i + 1] * b[1] + r.F[3 * i + 2] * b[2];
+      G[i] = C[3 * i] * b[0] + C[3 * i + 1] * b[1] + C[3 * i + 2] * b[2];
+    }
+    const T vm = r.vol * r.mu, vl = r.vol * r.lp, vs = r.vol * s;
+    const T bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) g[i] += vm * Fb[i] + vs * G[i];
+    H[0] += vm * bb + vl * G[0] * G[0];
+    H[1] += vl * G[0] * G[1];
+    H[2] += vl * G[0] * G[2];
+    H[3] += vm * bb + vl * G[1] * G[1];
+    H[4] += vl * G[1] * G[2];
+    H[5] += vm * bb + vl * G[2] * G[2];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Fs[q] += r.vol * r.F[q];
     W += r.vol;
   }
 }
@@ -324,6 +458,84 @@ __host__ __device__ constexpr int pk(int r, int c) {
   return r <= c ? r * 12 - (r * (r - 1)) / 2 + (c - r) : c * 12 - (c * (c - 1)) / 2 + (r - c);
 }
 
+// Row and column of packed entry q (upper triangle of a symmetric 12x12, row-major).
+__host__ __device__ constexpr int pk_row(int q) {
+  int r = 0;
+  while (q >= 12 - r) {
+    q -= 12 - r;
+    ++r;
+  }
+  return r;
+}
+__host__ __device__ constexpr int pk_col(int q) {
+  int r = 0;
+  while (q >= 12 - r) {
+    q -= 12 - r;
+    ++r;
+  }
+  return r + q;
+}
+
+// One entry q of a streamed pool row (indices fixed at compile time): packed Hessian
+// entries accumulate M = H' U over the upper triangle, gradient entries g~' += w U^T G.
+template <int Q, typename T>
+__device__ __forceinline__ void pool_entry(T h, T w, const T (&U)[36], T (&M)[36], T (&gt)[3]) {
+  if constexpr (Q < kPackedH) {
+    constexpr int r = pk_row(Q), c = pk_col(Q);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) M[3 * r + k] += h * U[3 * c + k];
+    if constexpr (r != c) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) M[3 * c + k] += h * U[3 * r + k];
+    }
+  } else if constexpr (Q < kPackedH + 12) {
+    constexpr int r = Q - kPackedH;
+    const T wg = w * h;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gt[k] += wg * U[3 * r + k];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void load4(const T* __restrict__ p, T (&o)[4]);
+
+template <int Q4, typename T>
+__device__ __forceinline__ void pool_chunk(const T* __restrict__ Hp, T w, const T (&U)[36], T (&M)[36],
+                                           T (&gt)[3]) {
+  T hv[4];
+  load4(Hp + 4 * Q4, hv);
+  pool_entry<4 * Q4 + 0>(hv[0], w, U, M, gt);
+  pool_entry<4 * Q4 + 1>(hv[1], w, U, M, gt);
+  pool_entry<4 * Q4 + 2>(hv[2], w, U, M, gt);
+  pool_entry<4 * Q4 + 3>(hv[3], w, U, M, gt);
+}
+
+template <typename T, int... Q4>
+__device__ __forceinline__ void pool_row(const T* __restrict__ Hp, T w, const T (&U)[36], T (&M)[36], T (&gt)[3],
+                                         std::integer_sequence<int, Q4...>) {
+  (pool_chunk<Q4>(Hp, w, U, M, gt), ...);
+}
+
+// Four consecutive values from a 16-byte aligned address through the read-only path (one
+// 16-byte load in FP32, two in FP64).
+template <>
+__device__ __forceinline__ void load4<float>(const float* __restrict__ p, float (&o)[4]) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  o[0] = v.x;
+  o[1] = v.y;
+  o[2] = v.z;
+  o[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load4<double>(const double* __restrict__ p, double (&o)[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  o[0] = a.x;
+  o[1] = a.y;
+  o[2] = b.x;
+  o[3] = b.y;
+}
+
 // Step truncation: scale d so that |d| <= lim (reading R11).
 template <typename T>
 __device__ __forceinline__ void truncate3(T (&d)[3], T lim) {
@@ -417,6 +629,36 @@ __global__ void k_setup_tets(DevMesh<T> m) {
       for (int k = 0; k < 3; ++k) f += D[3 * i + k] * double(r.B[3 * k + j]);
       r.Ft[3 * i + j] = T(f);
     }
+  // corner vectors of the gather (the same values corner_b forms from the record)
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    T b[3];
+    corner_b(r, c, b);
+    m.bc[4 * (size_t)t + c] = Vec4<T>{b[0], b[1], b[2], T(0)};
+  }
+}
+
+// Element pass of a sweep (Sec. 3 energy terms, computed once per tet): F_e(x^k) =
+// F(x_t) + [u_1 - u_0, u_2 - u_0, u_3 - u_0] B with the tet's constants, for the vertex
+// gather. Tiles of 128 records are staged in shared memory with coalesced loads; each
+// thread writes one 16-byte aligned FRec. Batch meshes skip the tets of finished scenes.
+template <typename T, bool BATCH>
+__global__ void __launch_bounds__(128) k_elem(DevMesh<T> m, const StepState* __restrict__ st) {
+  if (!BATCH && st->done) return;
+  __shared__ __align__(16) TetRec<T> srec[128];
+  const int t0 = blockIdx.x * 128, n = min(128, m.T_ - t0);
+  stage_tets<T, 128>(m.tets, t0, n, srec);
+  __syncthreads();
+  if ((int)threadIdx.x >= n) return;
+  const int t = t0 + threadIdx.x;
+  if (BATCH && m.scenes[m.t_scene[t]].done) return;
+  const TetRec<T>& r = srec[threadIdx.x];
+  FRec<T> o;
+  tet_F(r, m.u, o.F);
+  o.vol = r.vol;
+  o.mu = r.mu;
+  o.lp = r.lp;
+  m.frec[t] = o;
 }
 
 // Per cubature element: 4 warps gather the element's corners (warp a -> corner a), then
@@ -574,7 +816,7 @@ __global__ void __launch_bounds__(128) k_pool(DevMesh<T> m, const StepState* __r
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int k = 0; k < 3; ++k) v += sR[a][3 * i + jj] * Hac[3 * i + k] * sR[cc][3 * k + ll];
-    m.pool_H[(size_t)p * kPackedH + threadIdx.x] = v;
+    m.pool_H[(size_t)p * kPoolStride + threadIdx.x] = v;
   } else if (threadIdx.x < kPackedH + 12) {
     // rotated corner gradient entry (a, j)
     const int e = threadIdx.x - kPackedH, a = e / 3, j = e % 3;
@@ -599,14 +841,15 @@ __global__ void __launch_bounds__(128) k_pool(DevMesh<T> m, const StepState* __r
         ga[0] = ga[1] = ga[2] = T(0);
       }
     }
-    m.pool_G[(size_t)p * 12 + e] = sR[a][j] * ga[0] + sR[a][3 + j] * ga[1] + sR[a][6 + j] * ga[2];
+    m.pool_H[(size_t)p * kPoolStride + kPackedH + e] = sR[a][j] * ga[0] + sR[a][3 + j] * ga[1] + sR[a][6 + j] * ga[2];
   }
 }
 
 // Residual bookkeeping of sweep k (reading R9), run by one thread of the last block.
-__device__ __forceinline__ void finalize_sweep(StepState* st, int k, double r2, double gd, double gdj,
+__device__ __forceinline__ void finalize_sweep(StepState* st, double r2, double gd, double gdj,
                                                double* trace, int record) {
   st->ticket_main = 0;
+  const int k = st->k;
   const double gn = sqrt(r2);
   if (k == 0) st->g0 = gn;
   const double g0 = st->g0;
@@ -616,6 +859,7 @@ __device__ __forceinline__ void finalize_sweep(StepState* st, int k, double r2, 
   st->slope_j = gdj;
   st->alpha = 1.0;
   st->dir = 0;
+  st->need_j = 0;
   if (record && k < 4096) trace[k] = r;
   if (!isfinite(r) || !isfinite(gd) || !isfinite(gdj)) {
     st->status = 6;  // JGS2_EDIVERGED
@@ -628,6 +872,8 @@ __device__ __forceinline__ void finalize_sweep(StepState* st, int k, double r2, 
   } else if (k >= st->max_sweeps) {
     st->done = 1;
     st->sweeps = k;
+  } else {
+    st->k = k + 1;
   }
 }
 
@@ -638,12 +884,13 @@ __device__ __forceinline__ void finalize_sweep(StepState* st, int k, double r2, 
 // this kernel closes the sweep's reduction.
 template <typename T, bool CORR, bool BATCH, int BS>
 __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 1024 : 512) / BS)
-    k_gather(DevMesh<T> m, StepState* st, int k, double* __restrict__ partial /* [3][grid] */,
+    k_gather(DevMesh<T> m, StepState* st, double* __restrict__ partial /* [3][grid] */,
              double* __restrict__ trace, int record) {
   if (!BATCH && st->done) return;
   __shared__ double red[96];
+  __shared__ Acc<T> sred[64];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[2] = {0.0, 0.0};  // |g|^2, g.D_J
+  Acc<T> acc[2];  // |g|^2, g.D_J
   const int sc = (BATCH && i < m.Vf) ? m.v_scene[i] : -1;
   const bool active = i < m.Vf && (!BATCH || !m.scenes[sc].done);
   if (active) {
@@ -696,36 +943,42 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 1024 : 512) / BS)
     } else {
       m.D[i] = djv;
     }
-    acc[0] = double(g[0]) * double(g[0]) + double(g[1]) * double(g[1]) + double(g[2]) * double(g[2]);
-    acc[1] = double(g[0]) * double(dj[0]) + double(g[1]) * double(dj[1]) + double(g[2]) * double(dj[2]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      acc[0].add_prod(g[q], g[q]);
+      acc[1].add_prod(g[q], dj[q]);
+    }
   }
   if (BATCH) {
-    scene_reduce<2>(acc, active ? sc : -1, m.sacc, 0);
+    const double av[2] = {acc[0].value(), acc[1].value()};
+    scene_reduce<2>(av, active ? sc : -1, m.sacc, 0);
     return;
   }
-  block_sum<2>(acc, red);
+  double bs[2];
+  block_sum_acc<T, 2>(acc, bs, sred);
   if (threadIdx.x == 0) {
-    partial[blockIdx.x] = acc[0];
-    partial[gridDim.x + blockIdx.x] = acc[1];
+    partial[blockIdx.x] = bs[0];
+    partial[gridDim.x + blockIdx.x] = bs[1];
   }
   if (CORR) return;
   if (!last_block(&st->ticket_main)) return;
   const double r2 = block_sum_array(partial, gridDim.x, 1, red);
   const double gdj = block_sum_array(partial + gridDim.x, gridDim.x, 1, red);
-  if (threadIdx.x == 0) finalize_sweep(st, k, r2, gdj, gdj, trace, record);
+  if (threadIdx.x == 0) finalize_sweep(st, r2, gdj, gdj, trace, record);
 }
 
 // Sweep phase 2, thread per free vertex: the cubature sums H~_i, g~_i (Eq. cubature) from
 // the rotated pool element data, the 3x3 solve of Eq. reduced_local, D_i, and g.D. The
 // last block closes the sweep's reduction with phase 1's partial sums.
 template <typename T, bool BATCH, int BS>
-__global__ void __launch_bounds__(BS) k_correct(DevMesh<T> m, StepState* st, int k,
+__global__ void __launch_bounds__(BS) k_correct(DevMesh<T> m, StepState* st,
                                                 double* __restrict__ partial /* [3][grid] */,
                                                 double* __restrict__ trace, int record) {
   if (!BATCH && st->done) return;
   __shared__ double red[96];
+  __shared__ Acc<T> sred[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[1] = {0.0};
+  Acc<T> acc[1];  // g.D
   int fb = 0;
   const int sc = (BATCH && i < m.Vf) ? m.v_scene[i] : -1;
   const bool active = i < m.Vf && (!BATCH || !m.scenes[sc].done);
@@ -748,29 +1001,23 @@ __global__ void __launch_bounds__(BS) k_correct(DevMesh<T> m, StepState* st, int
       const T* up = m.cub_u + (size_t)s * 36 * m.Vf + i;
 #pragma unroll
       for (int q = 0; q < 36; ++q) U[q] = up[(size_t)q * m.Vf];
-      const T* Hp = m.pool_H + (size_t)p * kPackedH;
-      const T* Gp = m.pool_G + (size_t)p * 12;
+      // stream the pool row (packed H', then the rotated corner gradients) in 16-byte
+      // loads: M = H' U (12x3) from the upper triangle, g~' += w U^T G
+      const T* Hp = m.pool_H + (size_t)p * kPoolStride;
+      T M[36];
+#pragma unroll
+      for (int q = 0; q < 36; ++q) M[q] = T(0);
+      pool_row(Hp, w, U, M, gt, std::make_integer_sequence<int, (kPackedH + 12 + 3) / 4>{});
+      // H~' += w U^T M (symmetric: six entries)
 #pragma unroll
       for (int r = 0; r < 12; ++r) {
-        T tr[3] = {T(0), T(0), T(0)};
-#pragma unroll
-        for (int c = 0; c < 12; ++c) {
-          const T h = __ldg(Hp + pk(r, c));
-          tr[0] += h * U[3 * c];
-          tr[1] += h * U[3 * c + 1];
-          tr[2] += h * U[3 * c + 2];
-        }
         const T wu0 = w * U[3 * r], wu1 = w * U[3 * r + 1], wu2 = w * U[3 * r + 2];
-        Ht[0] += wu0 * tr[0];
-        Ht[1] += wu0 * tr[1];
-        Ht[2] += wu0 * tr[2];
-        Ht[3] += wu1 * tr[1];
-        Ht[4] += wu1 * tr[2];
-        Ht[5] += wu2 * tr[2];
-        const T gr = __ldg(Gp + r);
-        gt[0] += wu0 * gr;
-        gt[1] += wu1 * gr;
-        gt[2] += wu2 * gr;
+        Ht[0] += wu0 * M[3 * r];
+        Ht[1] += wu0 * M[3 * r + 1];
+        Ht[2] += wu0 * M[3 * r + 2];
+        Ht[3] += wu1 * M[3 * r + 1];
+        Ht[4] += wu1 * M[3 * r + 2];
+        Ht[5] += wu2 * M[3 * r + 2];
       }
     }
     // back to world: H~ = R H~' R^T, g~ = R g~'
@@ -802,24 +1049,27 @@ __global__ void __launch_bounds__(BS) k_correct(DevMesh<T> m, StepState* st, int
     }
     Vec4<T> dv{d[0], d[1], d[2], T(0)};
     m.D[i] = dv;
-    acc[0] = double(g[0]) * double(d[0]) + double(g[1]) * double(d[1]) + double(g[2]) * double(d[2]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) acc[0].add_prod(g[q], d[q]);
   }
   if (BATCH) {
     if (fb) atomicAdd(&m.scenes[sc].fallback, 1);
-    scene_reduce<1>(acc, active ? sc : -1, m.sacc, 2);
+    const double av[1] = {acc[0].value()};
+    scene_reduce<1>(av, active ? sc : -1, m.sacc, 2);
     return;
   }
   if (__syncthreads_or(fb)) {
     const int nfb = __syncthreads_count(fb);
     if (threadIdx.x == 0) atomicAdd(&st->fallback, nfb);
   }
-  block_sum<1>(acc, red);
-  if (threadIdx.x == 0) partial[2 * gridDim.x + blockIdx.x] = acc[0];
+  double bs[1];
+  block_sum_acc<T, 1>(acc, bs, sred);
+  if (threadIdx.x == 0) partial[2 * gridDim.x + blockIdx.x] = bs[0];
   if (!last_block(&st->ticket_main)) return;
   const double r2 = block_sum_array(partial, gridDim.x, 1, red);
   const double gdj = block_sum_array(partial + gridDim.x, gridDim.x, 1, red);
   const double gd = block_sum_array(partial + 2 * gridDim.x, gridDim.x, 1, red);
-  if (threadIdx.x == 0) finalize_sweep(st, k, r2, gd, gdj, trace, record);
+  if (threadIdx.x == 0) finalize_sweep(st, r2, gd, gdj, trace, record);
 }
 
 // Exact energy change of a tet for the displacement increment alpha*d (no cancellation):
@@ -868,116 +1118,130 @@ __device__ __forceinline__ void tet_dpsi_poly(const TetRec<T>& r, const T (&F)[9
   c[5] = r.vol * (T(0.5) * lp * Cc * Cc);
 }
 
-// Line search (reading R17): the energy change along D (and along D_J when ND = 2) is a
-// polynomial in the step a; its coefficients are summed over tets and free vertices
-// (per-thread partial sums in T over a grid-stride loop, FP64 across threads and blocks),
-// then the last block evaluates E(x + a d) - E(x) at a = 2^-j and takes the first
-// Armijo-satisfying trial, D before D_J.
-template <typename T, int ND, bool CONTACT>
-__global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st,
-                                                double* __restrict__ partial /* [ND*6][grid] */) {
+// Line search (reading R17), IPC barrier part: the barrier change of the candidate pairs
+// for each trial step a = 2^-j along the direction (not polynomial in a), FP64 sums per
+// block into pp[j][blockIdx]. DIR as in k_energy, which adds these sums.
+template <typename T, int DIR>
+__global__ void __launch_bounds__(128) k_pair_trials(DevMesh<T> m, const StepState* __restrict__ st,
+                                                     double* __restrict__ pp /* [kLsTrials][grid] */) {
   if (st->done) return;
-  constexpr int NC = 6 * ND;
-  constexpr int NB = CONTACT ? kLsTrials * ND : 0;
-  __shared__ double red[32 * (NC + NB)];
-  T acc[NC];
+  if (DIR == 1 && !st->need_j) return;
+  __shared__ double red[32 * kLsTrials];
+  const Vec4<T>* dir = DIR == 0 ? m.D : m.DJ;
+  double acc[kLsTrials];
 #pragma unroll
-  for (int j = 0; j < NC; ++j) acc[j] = T(0);
-  const int stride = gridDim.x * blockDim.x;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.T_; t += stride) {
-    const TetRec<T> r = m.tets[t];
-    T F[9], C[9], dF[9], c[6];
-    tet_F(r, m.u, F);
-    cofactor(F, C);
-    const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
-    tet_dF(r, m.D, m.Vf, dF);
-    tet_dpsi_poly(r, F, C, J, dF, c);
+  for (int j = 0; j < kLsTrials; ++j) acc[j] = 0.0;
+  const int np = min(*m.c.n_pairs, m.c.cap);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) {
+    // a pair beyond r_c stays beyond dhat for every trial (each vertex moves at most
+    // 0.45 (r_c - dhat)): its barrier is zero throughout
+    const double dq = m.c.d0[q];
+    if (!(dq < m.c.rc)) continue;
+    const uint64_t key = m.c.pairs[q];
+    // no trial brings the pair within dhat (and it starts outside): zero change throughout
+    if (dq - pair_motion(m, m.c, key, dir) >= m.c.dhat * (1.0 + 1e-9)) continue;
+    const double b0 = barrier_b(dq, m.c.dhat);
+#pragma unroll 1
+    for (int j = 0; j < kLsTrials; ++j) {
+      int vs[4], nv;
+      P3 Jg[4];
+      const double d = pair_geom(m, m.c, key, 1.0 / double(1 << j), dir, vs, Jg, nv);
+      acc[j] += m.c.kappa * (barrier_b(d, m.c.dhat) - b0);
+    }
+  }
+  block_sum<kLsTrials>(acc, red);
+  if (threadIdx.x == 0) {
 #pragma unroll
-    for (int j = 0; j < 6; ++j) acc[j] += c[j];
-    if (ND == 2) {
-      tet_dF(r, m.DJ, m.Vf, dF);
+    for (int j = 0; j < kLsTrials; ++j) pp[(size_t)j * gridDim.x + blockIdx.x] = acc[j];
+  }
+}
+
+// Line search (reading R17), one direction per launch: DIR = 0 is the sweep direction D,
+// DIR = 1 the uncorrected direction D_J, tried only when every trial along D failed
+// (the launch returns at once otherwise). The energy change along the direction is a
+// polynomial in the step a; its coefficients are summed over tets (tiles of 128 records
+// staged in shared memory) and free vertices, per thread and per block with Acc<T>
+// (FP64-class), across blocks in FP64. The last block adds the barrier sums of
+// k_pair_trials (n_pp blocks; 0 without contact), evaluates E(x + a d) - E(x) at a = 2^-j
+// and takes the first Armijo-satisfying trial. has_j = 0 (no correction, D = D_J): a
+// failed D is a rejection.
+template <typename T, int DIR>
+__global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st, int has_j,
+                                                double* __restrict__ partial /* [6][grid] */,
+                                                const double* __restrict__ pp, int n_pp) {
+  if (st->done) return;
+  if (DIR == 1 && !st->need_j) return;
+  constexpr int NC = 6;
+  __shared__ __align__(16) TetRec<T> srec[128];
+  __shared__ Acc<T> sacc[32 * NC];
+  __shared__ double red[32];
+  const Vec4<T>* __restrict__ dir = DIR == 0 ? m.D : m.DJ;
+  Acc<T> acc[NC];
+  const int ntile = (m.T_ + 127) / 128;
+  for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int t0 = tile * 128, n = min(128, m.T_ - t0);
+    __syncthreads();  // the previous tile's records are consumed
+    stage_tets<T, 128>(m.tets, t0, n, srec);
+    __syncthreads();
+    if ((int)threadIdx.x < n) {
+      const TetRec<T>& r = srec[threadIdx.x];
+      T F[9], C[9], dF[9], c[6];
+      tet_F(r, m.u, F);
+      cofactor(F, C);
+      const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
+      tet_dF(r, dir, m.Vf, dF);
       tet_dpsi_poly(r, F, C, J, dF, c);
 #pragma unroll
-      for (int j = 0; j < 6; ++j) acc[6 + j] += c[j];
+      for (int j = 0; j < 6; ++j) acc[j].add(c[j]);
     }
   }
   // inertia: m/(2h^2) (2 a d.(u - dz) + a^2 |d|^2)
+  const int stride = gridDim.x * blockDim.x;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < m.Vf; v += stride) {
     T uv[3], dz[3], d[3];
     load3(m.u, v, uv);
     load3(m.dz, v, dz);
+    load3(dir, v, d);
     const T mh = m.mh2[v];
+    T dd = T(0), de = T(0);
 #pragma unroll
-    for (int dir = 0; dir < ND; ++dir) {
-      load3(dir == 0 ? m.D : m.DJ, v, d);
-      T dd = T(0), de = T(0);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        dd += d[q] * d[q];
-        de += d[q] * (uv[q] - dz[q]);
-      }
-      acc[dir * 6 + 0] += mh * de;
-      acc[dir * 6 + 1] += T(0.5) * mh * dd;
+    for (int q = 0; q < 3; ++q) {
+      dd += d[q] * d[q];
+      de += d[q] * (uv[q] - dz[q]);
     }
+    acc[0].add(mh * de);
+    acc[1].add(T(0.5) * mh * dd);
   }
-  // IPC barrier change over the candidate pairs, per trial (not polynomial in a)
-  double accd[NC + NB];
-#pragma unroll
-  for (int j = 0; j < NC; ++j) accd[j] = double(acc[j]);
-#pragma unroll
-  for (int j = 0; j < NB; ++j) accd[NC + j] = 0.0;
-  if (CONTACT) {
-    const int np = min(*m.c.n_pairs, m.c.cap);
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += stride) {
-      // a pair beyond r_c stays beyond dhat for every trial (each vertex moves at most
-      // 0.45 (r_c - dhat)): its barrier is zero throughout
-      const double dq = m.c.d0[q];
-      if (!(dq < m.c.rc)) continue;
-      const uint64_t key = m.c.pairs[q];
-      const double b0 = barrier_b(dq, m.c.dhat);
-#pragma unroll
-      for (int dir = 0; dir < ND; ++dir)
-#pragma unroll 1
-        for (int j = 0; j < kLsTrials; ++j) {
-          int vs[4], nv;
-          P3 J[4];
-          const double d = pair_geom(m, m.c, key, 1.0 / double(1 << j), dir == 0 ? m.D : m.DJ, vs, J, nv);
-          accd[NC + dir * kLsTrials + j] += m.c.kappa * (barrier_b(d, m.c.dhat) - b0);
-        }
-    }
-  }
-  block_sum<NC + NB>(accd, red);
+  double bs[NC];
+  block_sum_acc<T, NC>(acc, bs, sacc);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int j = 0; j < NC + NB; ++j) partial[(size_t)j * gridDim.x + blockIdx.x] = accd[j];
+    for (int j = 0; j < NC; ++j) partial[(size_t)j * gridDim.x + blockIdx.x] = bs[j];
   }
   if (!last_block(&st->ticket_energy)) return;
-  double cf[NC + NB];
+  double cf[NC + kLsTrials];
 #pragma unroll
-  for (int j = 0; j < NC + NB; ++j) cf[j] = block_sum_array(partial + (size_t)j * gridDim.x, gridDim.x, 1, red);
+  for (int j = 0; j < NC; ++j) cf[j] = block_sum_array(partial + (size_t)j * gridDim.x, gridDim.x, 1, red);
+#pragma unroll
+  for (int j = 0; j < kLsTrials; ++j) cf[NC + j] = n_pp > 0 ? block_sum_array(pp + (size_t)j * n_pp, n_pp, 1, red) : 0.0;
   if (threadIdx.x == 0) {
     st->ticket_energy = 0;
+    const double slope = DIR == 0 ? st->slope : st->slope_j;
     double alpha = 0.0;
-    int dir = 0;
     bool ok = false;
-    for (int dd = 0; dd < ND && !ok; ++dd) {
-      const double slope = dd == 0 ? st->slope : st->slope_j;
-      for (int j = 0; j < kLsTrials; ++j) {
-        const double a = 1.0 / double(1 << j);
-        const double* c = cf + 6 * dd;
-        const double dE = a * (c[0] + a * (c[1] + a * (c[2] + a * (c[3] + a * (c[4] + a * c[5]))))) +
-                          (CONTACT ? cf[NC + dd * kLsTrials + j] : 0.0);
-        if (dE <= 1e-4 * a * slope) {
-          alpha = a;
-          dir = dd;
-          ok = true;
-          break;
-        }
+    for (int j = 0; j < kLsTrials; ++j) {
+      const double a = 1.0 / double(1 << j);
+      const double dE = a * (cf[0] + a * (cf[1] + a * (cf[2] + a * (cf[3] + a * (cf[4] + a * cf[5]))))) + cf[NC + j];
+      if (dE <= 1e-4 * a * slope) {
+        alpha = a;
+        ok = true;
+        break;
       }
     }
-    if (!ok) st->ls_rejects += 1;
     st->alpha = alpha;
-    st->dir = dir;
+    st->dir = DIR;
+    if (DIR == 0) st->need_j = (!ok && has_j) ? 1 : 0;
+    if (!ok && (DIR == 1 || !has_j)) st->ls_rejects += 1;
   }
 }
 
@@ -990,12 +1254,16 @@ __global__ void __launch_bounds__(128) k_energy_batch(DevMesh<T> m, int tet_bloc
 #pragma unroll
   for (int j = 0; j < NC; ++j) acc[j] = 0.0;
   int sc = -1;
+  __shared__ __align__(16) TetRec<T> srec[128];
   if ((int)blockIdx.x < tet_blocks) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t0 = blockIdx.x * 128;
+    stage_tets<T, 128>(m.tets, t0, min(128, m.T_ - t0), srec);
+    __syncthreads();
+    const int t = t0 + threadIdx.x;
     if (t < m.T_) {
       sc = m.t_scene[t];
       if (!m.scenes[sc].done) {
-        const TetRec<T> r = m.tets[t];
+        const TetRec<T>& r = srec[threadIdx.x];
         T F[9], C[9], dF[9], c[6];
         tet_F(r, m.u, F);
         cofactor(F, C);
@@ -1168,7 +1436,7 @@ __global__ void k_grad(DevMesh<T> m, double* __restrict__ g_caller) {
     return;
   }
   T g[3], H[6], Fs[9], W;
-  gather_vertex(m, i, g, H, Fs, W);
+  gather_vertex_rec(m, i, g, H, Fs, W);
   T ui[3], dz[3];
   load3(m.u, i, ui);
   load3(m.dz, i, dz);

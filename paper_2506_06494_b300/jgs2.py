@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libjgs2.so")
 
 TRACE_MAX = 4096
-NKERNELS = 7
+NKERNELS = 8
 KERNEL_NAMES = ["k_pool", "k_gather", "k_correct", "k_energy", "k_update", "setup", "contact"]
 FP64, FP32 = 0, 1
 CORR_ASM, CORR_ELEM, CORR_OFF = 0, 1, 2
