@@ -244,8 +244,7 @@ def run_jgs2(args, rank, world, local_rank):
     t_pre = time.perf_counter() - t0
     prec = p.FP32 if args.precision == "fp32" else p.FP64
     corr = {"asm": p.CORR_ASM, "elem": p.CORR_ELEM, "off": p.CORR_OFF}[args.correction]
-    opts = p.step_opts(precision=prec, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4,
-                       profile=0 if batch else 1)
+    opts = p.step_opts(precision=prec, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4, profile=1)
     x0 = torch.tensor(X, dtype=torch.float64, device=dev)
     v0 = torch.tensor(V0, dtype=torch.float64, device=dev)
     bs = mesh.autotune(x0, v0, opts)
@@ -319,34 +318,31 @@ def run_jgs2(args, rank, world, local_rank):
                              "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
     if batch:
         out["scene_sweeps"] = scene_sweeps
-        out["roofline"] = dict(out["sweep_roofline"], kernel="sweep (all kernels of a graph-captured chunk)",
-                               traffic=None)
-    else:
-        # kernel times are CUDA events around every kernel group in the captured sweep graphs
-        # of the timed steps; a group's time per sweep that did work (gather-side kernels run
-        # sweeps + 1 times per step, the line search and update sweeps times; launches that
-        # returned at once after the stop add their time too, so the averages are upper bounds)
-        n_work = {"k_energy": sw_tot, "k_update": sw_tot}
-        share = {KIND[q]: round(float(kms[q] / max(kms.sum(), 1e-12)), 4) for q in range(len(KIND))}
-        per_kernel = {}
-        for q, name in enumerate(KIND):
-            if name in kb and kl[q] > 0:
-                nw = n_work.get(name, sw_tot + args.steps)
-                avg = kms[q] / nw
-                per_kernel[name] = {"avg_launch_ms": round(float(avg), 5), "bytes_per_launch": kb[name],
-                                    "GB_s": round(kb[name] / (avg * 1e-3) / 1e9, 1),
-                                    "frac": round(kb[name] / (avg * 1e-3) / 1e9 / hbm, 4)}
-        dom = max(per_kernel, key=lambda n: share[n])
-        achieved = per_kernel[dom]["GB_s"]
-        out["kernel_ms_per_step"] = {KIND[q]: round(float(kms[q] / args.steps), 4) for q in range(len(KIND))}
-        out["kernel_launches_per_step"] = {KIND[q]: int(kl[q] // args.steps) for q in range(len(KIND))}
-        out["kernel_share"] = share
-        out["kernels"] = per_kernel
-        out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-                           "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
-                           "bytes_per_launch": per_kernel[dom]["bytes_per_launch"],
-                           "avg_launch_ms": per_kernel[dom]["avg_launch_ms"],
-                           "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    # kernel times are CUDA events around every kernel group in the captured sweep graphs
+    # of the timed steps; a group's time per sweep that did work (gather-side kernels run
+    # sweeps + 1 times per step, the line search and update sweeps times; launches that
+    # returned at once after the stop add their time too, so the averages are upper bounds)
+    n_work = {"k_energy": sw_tot, "k_update": sw_tot}
+    share = {KIND[q]: round(float(kms[q] / max(kms.sum(), 1e-12)), 4) for q in range(len(KIND))}
+    per_kernel = {}
+    for q, name in enumerate(KIND):
+        if name in kb and kl[q] > 0:
+            nw = n_work.get(name, sw_tot + args.steps)
+            avg = kms[q] / nw
+            per_kernel[name] = {"avg_launch_ms": round(float(avg), 5), "bytes_per_launch": kb[name],
+                                "GB_s": round(kb[name] / (avg * 1e-3) / 1e9, 1),
+                                "frac": round(kb[name] / (avg * 1e-3) / 1e9 / hbm, 4)}
+    dom = max(per_kernel, key=lambda n: share[n])
+    achieved = per_kernel[dom]["GB_s"]
+    out["kernel_ms_per_step"] = {KIND[q]: round(float(kms[q] / args.steps), 4) for q in range(len(KIND))}
+    out["kernel_launches_per_step"] = {KIND[q]: int(kl[q] // args.steps) for q in range(len(KIND))}
+    out["kernel_share"] = share
+    out["kernels"] = per_kernel
+    out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                       "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                       "bytes_per_launch": per_kernel[dom]["bytes_per_launch"],
+                       "avg_launch_ms": per_kernel[dom]["avg_launch_ms"],
+                       "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
     if not args.no_compare:
         out["comparisons"] = compare(args, p, mesh, ss, batch, x0, v0, stream, corr, prec)
     if rank == 0 and not args.no_cpu_baseline:
@@ -390,13 +386,73 @@ def compare(args, p, mesh, ss, batch, x0, v0, stream, corr, prec):
     return res
 
 
+def run_adjoint(args, rank, world, local_rank):
+    """Differentiation workload: a rollout of the 20x20x100-vertex beam (214,434 tets) with
+    per-element Young's moduli E_e = 1e7 U(0.5, 1.5) (seed 0), loss = sum |x_n - xbar_n|^2
+    against a rollout with uniform E = 1e7, gradient dL/dE through jgs2_step_adjoint with
+    state checkpoints every 5 steps (segments recomputed in the backward pass). Timed: the
+    backward pass per step (recomputation + adjoint solve + parameter derivative), with the
+    forward rollout reported beside it. Forward and adjoint run at --precision (vectors and
+    kernels; reductions FP64-class either way)."""
+    import torch
+    import paper_2506_06494_b300 as p
+    from paper_2506_06494_b300 import autograd as AG
+    import scenes
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    s = scenes.beam_scene()
+    mesh = p.Mesh.from_scene(s)
+    if args.cubature == "precompute":
+        mesh.precompute(n_cub=args.n_cub)
+    else:
+        mesh.precompute_import(*scenes.random_cubature(s.X, s.tets, s.pinned, args.n_cub, seed=0, w_max=0.5,
+                                                       u_sigma=0.2))
+    prec = p.FP32 if args.precision == "fp32" else p.FP64
+    opts = p.step_opts(precision=prec, max_sweeps=args.max_sweeps, rel_tol=1e-4)
+    aopts = p.adjoint_opts(precision=prec, max_iters=5000, rel_tol=1e-6)
+    n = args.rollout_steps
+    x0 = torch.tensor(s.X, dtype=torch.float64, device=dev)
+    v0 = torch.tensor(s.v0, dtype=torch.float64, device=dev)
+    E0 = torch.full((s.n_tets,), 1e7, dtype=torch.float64, device=dev)
+    with torch.no_grad():
+        xbar, _ = AG.rollout(mesh, x0, v0, E0, n, 5, opts, aopts)
+    rng = np.random.default_rng(0)
+    E = torch.tensor(1e7 * rng.uniform(0.5, 1.5, s.n_tets), dtype=torch.float64, device=dev, requires_grad=True)
+    fwd, bwd, gnorm = [], [], None
+    for rep in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xn, _ = AG.rollout(mesh, x0, v0, E, n, 5, opts, aopts)
+        loss = ((xn - xbar) ** 2).sum()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        E.grad = None
+        loss.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        if rep >= args.warmup:
+            fwd.append((t1 - t0) * 1e3 / n)
+            bwd.append((t2 - t1) * 1e3 / n)
+        gnorm = float(E.grad.norm())
+    ms_b = float(np.median(bwd))
+    return {"metric": "adjoint ms per rollout step (backward: recompute + adjoint + dL/dE)", "value": ms_b,
+            "unit": "ms/step", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision.replace("fp", "f"), "data": "synthetic",
+            "config": {"workload": "adjoint", "scene": "20x20x100-vertex Kuhn beam 0.02x0.02x0.1 m, 214,434 tets, "
+                       "E_e = 1e7 U(0.5,1.5)", "rollout_steps": n, "checkpoint_every": 5,
+                       "cubature": args.cubature, "max_sweeps": args.max_sweeps, "adjoint_rel_tol": 1e-6},
+            "forward_ms_per_step": float(np.median(fwd)), "loss": float(loss), "grad_norm": gnorm}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="jgs2", choices=["jgs2", "reference"])
-    ap.add_argument("--workload", default="spheres", choices=["spheres", "beam", "cube", "batch"])
+    ap.add_argument("--workload", default="spheres", choices=["spheres", "beam", "cube", "batch", "adjoint"])
+    ap.add_argument("--rollout-steps", type=int, default=30, help="adjoint workload: steps of the rollout")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--correction", default="asm", choices=["asm", "elem", "off"])
     ap.add_argument("--n-cub", type=int, default=4)
@@ -425,7 +481,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    out = run_jgs2(args, rank, world, local_rank)
+    out = (run_adjoint if args.workload == "adjoint" else run_jgs2)(args, rank, world, local_rank)
     if out is not None:
         print(json.dumps(out))
     if world > 1:

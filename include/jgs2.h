@@ -41,7 +41,7 @@ typedef enum {
   JGS2_ENOTCONVERGED = 5,    /* max_sweeps reached; state is updated, report is filled */
   JGS2_EDIVERGED = 6,        /* the residual became NaN/Inf; state is NOT written back */
   JGS2_ENONSPD = 7,          /* reserved */
-  JGS2_ETIMEOUT = 8,         /* reserved for bounded device waits */
+  JGS2_ETIMEOUT = 8,         /* a bounded device wait (bulk-copy barrier) gave up; state NOT written */
   JGS2_EINTERSECT = 9        /* reserved for contact */
 } jgs2_status;
 

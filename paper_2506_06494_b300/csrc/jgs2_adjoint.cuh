@@ -104,13 +104,13 @@ __global__ void __launch_bounds__(128) k_lin_setup(DevMesh<T> m, T* __restrict__
   if (CORR) {
     T Ht[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     for (int s = 0; s < m.n_cub; ++s) {
-      const int p = m.cub_p[(size_t)s * m.Vf + i];
+      const int p = m.cub_p[(size_t)s * m.cs + i];
       if (p < 0) continue;
-      const T w = m.cub_w[(size_t)s * m.Vf + i];
+      const T w = m.cub_w[(size_t)s * m.cs + i];
       T U[36];
-      const T* up = m.cub_u + (size_t)s * 36 * m.Vf + i;
+      const T* up = m.cub_u + (size_t)s * 36 * m.cs + i;
 #pragma unroll
-      for (int q = 0; q < 36; ++q) U[q] = up[(size_t)q * m.Vf];
+      for (int q = 0; q < 36; ++q) U[q] = up[(size_t)q * m.cs];
       const T* Hp = m.pool_H + (size_t)p * kPoolStride;
 #pragma unroll
       for (int r = 0; r < 12; ++r) {
@@ -194,17 +194,17 @@ __global__ void __launch_bounds__(128) k_lin_precond(DevMesh<T> m, const T* __re
     for (int q = 0; q < 9; ++q) R[q] = lin[(6 + q) * S + i];
     T gt[3] = {T(0), T(0), T(0)};
     for (int s = 0; s < m.n_cub; ++s) {
-      const int p = m.cub_p[(size_t)s * m.Vf + i];
+      const int p = m.cub_p[(size_t)s * m.cs + i];
       if (p < 0) continue;
-      const T w = m.cub_w[(size_t)s * m.Vf + i];
-      const T* up = m.cub_u + (size_t)s * 36 * m.Vf + i;
+      const T w = m.cub_w[(size_t)s * m.cs + i];
+      const T* up = m.cub_u + (size_t)s * 36 * m.cs + i;
       const T* Gp = m.pool_G + (size_t)p * 12;
 #pragma unroll
       for (int rr = 0; rr < 12; ++rr) {
         const T gr = w * __ldg(Gp + rr);
-        gt[0] += up[(size_t)(3 * rr) * m.Vf] * gr;
-        gt[1] += up[(size_t)(3 * rr + 1) * m.Vf] * gr;
-        gt[2] += up[(size_t)(3 * rr + 2) * m.Vf] * gr;
+        gt[0] += up[(size_t)(3 * rr) * m.cs] * gr;
+        gt[1] += up[(size_t)(3 * rr + 1) * m.cs] * gr;
+        gt[2] += up[(size_t)(3 * rr + 2) * m.cs] * gr;
       }
     }
 #pragma unroll

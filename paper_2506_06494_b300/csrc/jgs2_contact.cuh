@@ -214,8 +214,15 @@ __global__ void __launch_bounds__(256) k_bp_check(DevMesh<T> m, ContactView c, c
   __shared__ float red[8];
   __shared__ bool last;
   float mx = 0.f;
+  const size_t V = c.n_vertices;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < c.n_sverts; q += gridDim.x * blockDim.x) {
     const int v = c.sverts[q];
+    // clear this sweep's barrier accumulators (only surface vertices are ever written)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c.bg[(size_t)k * V + v] = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) c.bH[(size_t)k * V + v] = 0.0;
+    c.dmin[v] = INFINITY;
     const P3 p = vpos(m, v);
     const float4 b = c.pbp[v];
     const double dx = p.x - double(b.x), dy = p.y - double(b.y), dz = p.z - double(b.z);
@@ -545,20 +552,6 @@ __device__ __forceinline__ double pair_geom(const DevMesh<T>& m, const ContactVi
   J[2] = mul(n, -(1.0 - t));
   J[3] = mul(n, -t);
   return d;
-}
-
-// per sweep: clear the barrier accumulators of the surface vertices (no other vertex is
-// ever written; their entries stay zero from allocation)
-static __global__ void __launch_bounds__(256) k_contact_reset(ContactView c) {
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < c.n_sverts; q += gridDim.x * blockDim.x) {
-    const int v = c.sverts[q];
-    const size_t V = c.n_vertices;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) c.bg[(size_t)k * V + v] = 0.0;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) c.bH[(size_t)k * V + v] = 0.0;
-    c.dmin[v] = INFINITY;
-  }
 }
 
 // Per candidate pair: its distance at x^k. Pairs within r_c count: smallest distance per

@@ -66,6 +66,9 @@ Mesh::~Mesh() {
   for (cudaEvent_t e : gevents) cudaEventDestroy(e);
   if (graph) cudaGraphExecDestroy(graph);
   if (gstream) cudaStreamDestroy(gstream);
+  if (gstream2) cudaStreamDestroy(gstream2);
+  for (cudaEvent_t e : gfork)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : gev)
     if (e) cudaEventDestroy(e);
   cudaFree(d_vscene); cudaFree(d_tscene); cudaFree(d_ndone); cudaFree(d_scenes); cudaFree(d_sacc);
@@ -464,19 +467,21 @@ static jgs2_status ensure_prec(Mesh* m) {
   }
   if (m->cub_version != b.cub_version && m->n_cub > 0) {
     cudaFree(b.cub_p); cudaFree(b.cub_w); cudaFree(b.cub_u); cudaFree(b.pool_H); cudaFree(b.pool_G);
-    const size_t Vf = m->Vf, nc = m->n_cub;
-    std::vector<T> w(nc * Vf), u(nc * 36 * Vf);
+    // rows of cs = Vf rounded up to 4 entries: every row starts 16-byte aligned (bulk copies);
+    // padding entries are unused slots (p = -1, w = 0, U_bar = 0)
+    const size_t Vf = m->Vf, nc = m->n_cub, cs = cub_stride(m->Vf);
+    std::vector<T> w(nc * cs, T(0)), u(nc * 36 * cs, T(0));
     for (size_t s = 0; s < nc; ++s)
       for (size_t i = 0; i < Vf; ++i) {
-        w[s * Vf + i] = T(m->cub_w[i * nc + s]);
-        for (int q = 0; q < 36; ++q) u[(s * 36 + q) * Vf + i] = T(m->cub_u[(i * nc + s) * 36 + q]);
+        w[s * cs + i] = T(m->cub_w[i * nc + s]);
+        for (int q = 0; q < 36; ++q) u[(s * 36 + q) * cs + i] = T(m->cub_u[(i * nc + s) * 36 + q]);
       }
-    std::vector<int32_t> p(nc * Vf);
+    std::vector<int32_t> p(nc * cs, -1);
     for (size_t s = 0; s < nc; ++s)
-      for (size_t i = 0; i < Vf; ++i) p[s * Vf + i] = m->cub_p[i * nc + s];
-    CK(dalloc(&b.cub_p, nc * Vf));
-    CK(dalloc(&b.cub_w, nc * Vf));
-    CK(dalloc(&b.cub_u, nc * 36 * Vf));
+      for (size_t i = 0; i < Vf; ++i) p[s * cs + i] = m->cub_p[i * nc + s];
+    CK(dalloc(&b.cub_p, nc * cs));
+    CK(dalloc(&b.cub_w, nc * cs));
+    CK(dalloc(&b.cub_u, nc * 36 * cs));
     CK(dalloc(&b.pool_H, (size_t)m->nP * kPoolStride));
     CK(dalloc(&b.pool_G, (size_t)m->nP * 12));
     cudaFree(b.pool_R);
@@ -519,6 +524,7 @@ static DevMesh<T> dev_view(Mesh* m) {
   d.cub_p = b.cub_p;
   d.cub_w = b.cub_w;
   d.cub_u = b.cub_u;
+  d.cs = cub_stride(m->Vf);
   d.pool_tet = m->d_pool_tet;
   d.pool_H = b.pool_H;
   d.pool_G = b.pool_G;
@@ -589,11 +595,17 @@ bool dev_view_f64_if_ready(Mesh* m, DevMesh<double>* out) {
 jgs2_status set_cubature(Mesh* m, int n_cub, const std::vector<int>& elem_int /* [Vf][nc] internal tet, -1 */,
                          const std::vector<double>& w, const std::vector<double>& u) {
   if (n_cub <= 0 || n_cub > kMaxCub) return fail(JGS2_EINVAL, "n_cub must be in [1, 8]");
-  // pool = distinct referenced elements, ascending internal id
+  // pool = distinct referenced elements, ordered by (body, internal id): the slots a block
+  // of nearby vertices references then form a short contiguous range (k_correct stages it)
   std::vector<int> pool;
   for (int e : elem_int)
     if (e >= 0) pool.push_back(e);
-  std::sort(pool.begin(), pool.end());
+  auto body_of = [&](int t) { return m->body[m->tets_c[4 * (size_t)m->tperm[t]]]; };
+  auto by_body = [&](int a, int b) {
+    const int ba = body_of(a), bb = body_of(b);
+    return ba != bb ? ba < bb : a < b;
+  };
+  std::sort(pool.begin(), pool.end(), by_body);
   pool.erase(std::unique(pool.begin(), pool.end()), pool.end());
   m->n_cub = n_cub;
   m->nP = (int)pool.size();
@@ -601,7 +613,7 @@ jgs2_status set_cubature(Mesh* m, int n_cub, const std::vector<int>& elem_int /*
   m->cub_p.assign(elem_int.size(), -1);
   for (size_t q = 0; q < elem_int.size(); ++q)
     if (elem_int[q] >= 0)
-      m->cub_p[q] = (int)(std::lower_bound(pool.begin(), pool.end(), elem_int[q]) - pool.begin());
+      m->cub_p[q] = (int)(std::lower_bound(pool.begin(), pool.end(), elem_int[q], by_body) - pool.begin());
   m->cub_elem = elem_int;
   m->cub_w = w;
   m->cub_u = u;
@@ -639,7 +651,7 @@ jgs2_status import_cubature(Mesh* m, const jgs2_cubature_blob* b) {
 
 // Candidate pairs within r_c at x^k, the barrier accumulators and the per-vertex minimum
 // distances (Sec. 7). Pair order is not canonical here (the sums use atomics).
-constexpr int kContactKernels = 11;  // launches of one contact_pass
+constexpr int kContactKernels = 10;  // launches of one contact_pass
 
 template <typename T>
 static jgs2_status contact_pass(Mesh* m, DevMesh<T>& d, cudaStream_t s, StepState* st) {
@@ -659,8 +671,7 @@ static jgs2_status contact_pass(Mesh* m, DevMesh<T>& d, cudaStream_t s, StepStat
   k_bp_fill<<<grid(std::max(nF, nE), 256), 256, 0, s>>>(c);
   k_query_vertices<T><<<grid(nS, 128), 128, 0, s>>>(d, c);
   k_query_edges<T><<<grid(nE, 128), 128, 0, s>>>(d, c);
-  // per sweep: barrier terms of the listed pairs at x^k
-  k_contact_reset<<<grid(nS, 256), 256, 0, s>>>(c);
+  // per sweep: barrier terms of the listed pairs at x^k (k_bp_check cleared the sums)
   k_pair_terms<T><<<grid(c.cap, 256), 256, 0, s>>>(d, c, st);
   CK(cudaGetLastError());
   return JGS2_OK;
@@ -755,14 +766,32 @@ struct Launches {
   }
 };
 
+// Blocks of k_energy that are resident at once on the device (capped at kEnergyBlocksMax,
+// which sizes the partial-sum buffer).
+template <typename T>
+static int energy_blocks() {
+  static int nb = 0;
+  if (nb == 0) {
+    int dev = 0, sms = 148, per_sm = 8;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_energy<T, 0>, 128, 0) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    nb = std::max(1, std::min(sms * per_sm, kEnergyBlocksMax));
+  }
+  return nb;
+}
+
 // Private non-blocking stream (and ordering events) the sweep graphs are captured and
 // replayed on: the caller's stream may be the legacy default stream, which cannot be
 // captured. Work on it is ordered after and before the caller's stream by events.
 static jgs2_status ensure_gstream(Mesh* m) {
   if (!m->gstream) {
     CK(cudaStreamCreateWithFlags(&m->gstream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&m->gstream2, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&m->gev[0], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&m->gev[1], cudaEventDisableTiming));
+    for (cudaEvent_t& e : m->gfork) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   return JGS2_OK;
 }
@@ -782,7 +811,9 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
   const int nbV = (m->Vf + 127) / 128;
   const int nbT = (m->T + 127) / 128;
   // line-search pass: grid-stride over tets and vertices, about 4 tets per thread
-  const int nbE = std::max(1, std::min(std::max(nbT, nbV), kEnergyBlocksMax));
+  // line-search pass: one full wave of resident blocks (SM count x blocks per SM at this
+  // kernel's registers and shared memory), grid-stride over tet tiles and vertices
+  const int nbE = std::max(1, std::min(std::max(nbT, nbV), energy_blocks<T>()));
   const int bs = m->bs[sizeof(T) == 4 ? 1 : 0];
   const int chunk = std::max(1, o.check_every);
   const bool prof = L.prof;
@@ -817,34 +848,53 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
     }
     size_t evi = 0;
     cudaError_t cerr = cudaSuccess;
-    auto group = [&](int kind, int n, auto&& launch) {
+    auto group = [&](int kind, int n, cudaStream_t gs, auto&& launch) {
       Mesh::GraphGroup g{kind, n, nullptr, nullptr};
       if (prof) {
         g.e0 = m->gevents[evi++];
         g.e1 = m->gevents[evi++];
-        if (cerr == cudaSuccess) cerr = cudaEventRecordWithFlags(g.e0, s, cudaEventRecordExternal);
+        if (cerr == cudaSuccess) cerr = cudaEventRecordWithFlags(g.e0, gs, cudaEventRecordExternal);
       }
       launch();
-      if (prof && cerr == cudaSuccess) cerr = cudaEventRecordWithFlags(g.e1, s, cudaEventRecordExternal);
+      if (prof && cerr == cudaSuccess) cerr = cudaEventRecordWithFlags(g.e1, gs, cudaEventRecordExternal);
       m->ggroups.push_back(g);
     };
+    // a second branch of the graph: work on s2 starts after the fork point on s and
+    // joins s before the kernel that needs it
+    cudaStream_t s2 = m->gstream2;
+    auto fork = [&](cudaEvent_t e) {
+      if (cerr == cudaSuccess) cerr = cudaEventRecord(e, s);
+      if (cerr == cudaSuccess) cerr = cudaStreamWaitEvent(s2, e, 0);
+    };
+    auto join = [&](cudaEvent_t e) {
+      if (cerr == cudaSuccess) cerr = cudaEventRecord(e, s2);
+      if (cerr == cudaSuccess) cerr = cudaStreamWaitEvent(s, e, 0);
+    };
+    const bool pool = corr && m->nP > 0;
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     for (int q = 0; q < chunk; ++q) {
-      if (m->contact) group(JGS2_K_CONTACT, kContactKernels, [&] { contact_pass<T>(m, d, s, m->d_state); });
-      if (corr && m->nP > 0)
-        group(JGS2_K_POOL, 1, [&] {
+      // contact pass (positions only) alongside the element pass; both feed the gather
+      if (m->contact) {
+        fork(m->gfork[0]);
+        group(JGS2_K_CONTACT, kContactKernels, s2, [&] { contact_pass<T>(m, d, s2, m->d_state); });
+      }
+      if (nbV > 0) group(JGS2_K_ELEM, 1, s, [&] { k_elem<T, false><<<nbT, 128, 0, s>>>(d, m->d_state); });
+      if (m->contact) join(m->gfork[1]);
+      if (nbV > 0)
+        group(JGS2_K_GATHER, 1, s,
+              [&] { launch_gather<T, false>(d, corr, bs, s, m->d_state, m->d_partial, m->d_trace, o.record_trace); });
+      // cubature pool after the gather, whose g and R at the pool elements' corners it reads
+      if (pool)
+        group(JGS2_K_POOL, 1, s, [&] {
           if (o.correction == JGS2_CORR_ASM)
-            k_pool<T, true><<<m->nP, 128, 0, s>>>(d, m->d_state);
+            k_pool<T, true><<<(m->nP + kPoolWarps - 1) / kPoolWarps, 32 * kPoolWarps, 0, s>>>(d, m->d_state);
           else
-            k_pool<T, false><<<m->nP, 128, 0, s>>>(d, m->d_state);
+            k_pool<T, false><<<(m->nP + kPoolWarps - 1) / kPoolWarps, 32 * kPoolWarps, 0, s>>>(d, m->d_state);
         });
       if (nbV > 0) {
-        group(JGS2_K_ELEM, 1, [&] { k_elem<T, false><<<nbT, 128, 0, s>>>(d, m->d_state); });
-        group(JGS2_K_GATHER, 1,
-              [&] { launch_gather<T, false>(d, corr, bs, s, m->d_state, m->d_partial, m->d_trace, o.record_trace); });
         if (corr)
-          group(JGS2_K_CORRECT, 1,
+          group(JGS2_K_CORRECT, 1, s,
                 [&] { launch_correct<T, false>(d, bs, s, m->d_state, m->d_partial, m->d_trace, o.record_trace); });
       }
       if (o.line_search) {
@@ -852,7 +902,7 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
         // at once otherwise)
         const int npp = m->contact ? kPairTrialBlocks : 0;
         double* pp = m->d_partial + (size_t)6 * nbE;
-        group(JGS2_K_ENERGY, (corr ? 2 : 1) * (m->contact ? 2 : 1), [&] {
+        group(JGS2_K_ENERGY, (corr ? 2 : 1) * (m->contact ? 2 : 1), s, [&] {
           if (m->contact) k_pair_trials<T, 0><<<npp, 128, 0, s>>>(d, m->d_state, pp);
           k_energy<T, 0><<<nbE, 128, 0, s>>>(d, m->d_state, corr ? 1 : 0, m->d_partial, pp, npp);
           if (corr) {
@@ -861,7 +911,7 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
           }
         });
       }
-      if (nbV > 0) group(JGS2_K_UPDATE, 1, [&] { k_update<T><<<nbV, 128, 0, s>>>(d, m->d_state); });
+      if (nbV > 0) group(JGS2_K_UPDATE, 1, s, [&] { k_update<T><<<nbV, 128, 0, s>>>(d, m->d_state); });
     }
     cudaError_t e = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess) return fail(JGS2_ECUDA, std::string("sweep capture: ") + cudaGetErrorString(e));
@@ -934,49 +984,98 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
   CK(cudaMemsetAsync(m->d_scenes, 0, sizeof(SceneState) * S, s));
   CK(cudaMemsetAsync(m->d_sacc, 0, sizeof(double) * kSceneAcc * S, s));
   CK(cudaMemsetAsync(m->d_ndone, 0, sizeof(int32_t), s));
-  const long key = ((((long)(sizeof(T) == 4) * 3 + o.correction) * 2 + (o.line_search != 0)) * 512 + bs) * 4096 +
-                   chunk + (long)(o.max_sweeps) * 1000003L + (long)(o.rel_tol * 1e12);
-  auto sweep_once = [&]() {
-    if (corr) k_pool<T, true><<<m->nP, 128, 0, s>>>(d, m->d_state);
-    k_elem<T, true><<<nbT, 128, 0, s>>>(d, m->d_state);
-    launch_gather<T, true>(d, corr, bs, s, m->d_state, m->d_partial, m->d_trace, 0);
-    if (corr) launch_correct<T, true>(d, bs, s, m->d_state, m->d_partial, m->d_trace, 0);
-    k_scene_finalize_main<<<(S + 127) / 128, 128, 0, s>>>(m->d_scenes, m->d_sacc, S, o.rel_tol, o.max_sweeps,
-                                                           corr ? 1 : 0, m->d_ndone);
-    if (o.line_search) {
-      if (corr)
-        k_energy_batch<T, 2><<<nbT + nbV, 128, 0, s>>>(d, nbT);
-      else
-        k_energy_batch<T, 1><<<nbT + nbV, 128, 0, s>>>(d, nbT);
-      k_scene_finalize_energy<<<(S + 127) / 128, 128, 0, s>>>(m->d_scenes, m->d_sacc, S, corr ? 2 : 1);
-    }
-    k_update_batch<T><<<nbV, 128, 0, s>>>(d);
-  };
-  if (m->graph_key != key) {
+  const bool prof = L.prof;
+  const long key = (((((long)(sizeof(T) == 4) * 3 + o.correction) * 2 + (o.line_search != 0)) * 2 + (prof ? 1 : 0)) *
+                        512 + bs) * 4096 + chunk + (long)(o.max_sweeps) * 1000003L + (long)(o.rel_tol * 1e12);
+  const bool same_view = m->gdev.size() == sizeof(d) && std::memcmp(m->gdev.data(), &d, sizeof(d)) == 0;
+  if (m->graph_key != key || !same_view) {
     if (m->graph) cudaGraphExecDestroy(m->graph);
     m->graph = nullptr;
+    m->graph_key = -1;
+    m->ggroups.clear();
+    const size_t nev = prof ? (size_t)14 * chunk : 0;
+    while (m->gevents.size() < nev) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      m->gevents.push_back(e);
+    }
+    size_t evi = 0;
+    cudaError_t cerr = cudaSuccess;
+    // kernel groups as in run_sweeps: kind, kernels, optional external timing events
+    auto group = [&](int kind, int n, cudaStream_t gs, auto&& launch) {
+      Mesh::GraphGroup g{kind, n, nullptr, nullptr};
+      if (prof) {
+        g.e0 = m->gevents[evi++];
+        g.e1 = m->gevents[evi++];
+        if (cerr == cudaSuccess) cerr = cudaEventRecordWithFlags(g.e0, gs, cudaEventRecordExternal);
+      }
+      launch();
+      if (prof && cerr == cudaSuccess) cerr = cudaEventRecordWithFlags(g.e1, gs, cudaEventRecordExternal);
+      m->ggroups.push_back(g);
+    };
+    cudaStream_t s2 = m->gstream2;
+    const int nbS = (S + 127) / 128;
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    for (int q = 0; q < chunk; ++q) sweep_once();
-    CK(cudaStreamEndCapture(s, &g));
-    cudaError_t e = cudaGraphInstantiate(&m->graph, g, 0);
+    for (int q = 0; q < chunk; ++q) {
+      group(JGS2_K_ELEM, 1, s, [&] { k_elem<T, true><<<nbT, 128, 0, s>>>(d, m->d_state); });
+      group(JGS2_K_GATHER, 1, s, [&] { launch_gather<T, true>(d, corr, bs, s, m->d_state, m->d_partial, m->d_trace, 0); });
+      // the cubature pool after the gather, whose g and R at the corners it reads
+      if (corr) {
+        group(JGS2_K_POOL, 1, s, [&] { k_pool<T, true><<<(m->nP + kPoolWarps - 1) / kPoolWarps, 32 * kPoolWarps, 0, s>>>(d, m->d_state); });
+        group(JGS2_K_CORRECT, 1, s,
+              [&] { launch_correct<T, true>(d, bs, s, m->d_state, m->d_partial, m->d_trace, 0); });
+      }
+      // per-scene stopping test (counted with the update)
+      group(JGS2_K_UPDATE, 1, s, [&] {
+        k_scene_finalize_main<<<nbS, 128, 0, s>>>(m->d_scenes, m->d_sacc, S, o.rel_tol, o.max_sweeps, corr ? 1 : 0,
+                                                  m->d_ndone);
+      });
+      if (o.line_search) {
+        // along D; along D_J only for the scenes whose trials along D all failed
+        group(JGS2_K_ENERGY, corr ? 4 : 2, s, [&] {
+          k_energy_batch<T, 0><<<nbT + nbV, 128, 0, s>>>(d, nbT);
+          k_scene_finalize_energy<0><<<nbS, 128, 0, s>>>(m->d_scenes, m->d_sacc, S, corr ? 1 : 0);
+          if (corr) {
+            k_energy_batch<T, 1><<<nbT + nbV, 128, 0, s>>>(d, nbT);
+            k_scene_finalize_energy<1><<<nbS, 128, 0, s>>>(m->d_scenes, m->d_sacc, S, 1);
+          }
+        });
+      }
+      group(JGS2_K_UPDATE, 1, s, [&] { k_update_batch<T><<<nbV, 128, 0, s>>>(d); });
+    }
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) return fail(JGS2_ECUDA, std::string("batch sweep capture: ") + cudaGetErrorString(e));
+    if (cerr != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return fail(JGS2_ECUDA, std::string("batch sweep capture (events): ") + cudaGetErrorString(cerr));
+    }
+    e = cudaGraphInstantiate(&m->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(JGS2_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
     m->graph_key = key;
+    m->gdev.assign(reinterpret_cast<const char*>(&d), reinterpret_cast<const char*>(&d) + sizeof(d));
   }
   int32_t done = 0;
   for (int sw = 0; sw <= o.max_sweeps; sw += chunk) {
     CK(cudaGraphLaunch(m->graph, s));
-    // kernel nodes per replay, by kind (the per-scene stopping test counts with the update)
-    L.count[JGS2_K_POOL] += corr ? chunk : 0;
-    L.count[JGS2_K_ELEM] += chunk;
-    L.count[JGS2_K_GATHER] += chunk;
-    L.count[JGS2_K_CORRECT] += corr ? chunk : 0;
-    L.count[JGS2_K_ENERGY] += o.line_search ? 2 * chunk : 0;
-    L.count[JGS2_K_UPDATE] += 2 * chunk;
+    for (const auto& g : m->ggroups) L.count[g.kind] += g.n;
     CK(cudaMemcpyAsync(&done, m->d_ndone, sizeof(done), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (prof) {
+      for (const auto& g : m->ggroups) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g.e0, g.e1) == cudaSuccess) L.gms[g.kind] += ms;
+      }
+    }
     if (done >= S) break;
+  }
+  {
+    // a bounded device wait that gave up stops the batch step (status in the step state)
+    StepState hs;
+    CK(cudaMemcpyAsync(&hs, m->d_state, sizeof(StepState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hs.status == JGS2_ETIMEOUT) return fail(JGS2_ETIMEOUT, "a bounded device wait timed out; state not written");
   }
   CK(cudaGetLastError());
   CK(cudaEventRecord(m->gev[1], s));
@@ -1068,7 +1167,12 @@ static jgs2_status step_impl(Mesh* m, double* x, double* v, const jgs2_step_opts
       rep->trace_len = n;
     }
   }
-  if (hs->status != 0) return fail((jgs2_status)hs->status, "residual became non-finite; state not written");
+  if (hs->status != 0) {
+    const char* why = hs->status == JGS2_ETIMEOUT     ? "a bounded device wait timed out; state not written"
+                      : hs->status == JGS2_EINTERSECT ? "contact pair at zero distance; state not written"
+                                                      : "residual became non-finite; state not written";
+    return fail((jgs2_status)hs->status, why);
+  }
   if (!hs->converged) return fail(JGS2_ENOTCONVERGED, "max_sweeps reached before rel_tol");
   return JGS2_OK;
 }
@@ -1295,8 +1399,11 @@ static jgs2_status autotune_impl(Mesh* m, double* x, double* v, const jgs2_step_
   init.max_sweeps = 1 << 30;
   init.rel_tol = -1.0;
   CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
-  if (corr) k_pool<T, true><<<m->nP, 128, 0, s>>>(d, m->d_state);
   k_elem<T, false><<<(m->T + 127) / 128, 128, 0, s>>>(d, m->d_state);
+  if (corr) {
+    launch_gather<T, false>(d, corr, 128, s, m->d_state, m->d_partial, m->d_trace, 0);
+    k_pool<T, true><<<(m->nP + kPoolWarps - 1) / kPoolWarps, 32 * kPoolWarps, 0, s>>>(d, m->d_state);
+  }
   const int cands[3] = {64, 128, 256};
   float best = 1e30f;
   int pick = 128;
@@ -1403,9 +1510,9 @@ static jgs2_status adjoint_impl(Mesh* m, const double* xt, const double* vt, con
   init.rel_tol = -1.0;
   CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
   // H_ii, R_i at x* (and the rotated cubature element Hessians)
-  if (corr) k_pool<T, true><<<m->nP, 128, 0, s>>>(d, m->d_state);
   k_elem<T, false><<<nbT, 128, 0, s>>>(d, m->d_state);
   k_gather<T, true, false, 128><<<nbV, 128, 0, s>>>(d, m->d_state, m->d_partial, m->d_trace, 0);
+  if (corr) k_pool<T, true><<<(m->nP + kPoolWarps - 1) / kPoolWarps, 32 * kPoolWarps, 0, s>>>(d, m->d_state);
   if (corr)
     k_lin_setup<T, true><<<nbV, 128, 0, s>>>(d, b.a_lin);
   else

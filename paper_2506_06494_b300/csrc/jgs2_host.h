@@ -77,7 +77,9 @@ struct Mesh {
   cudaGraphExec_t graph = nullptr;
   long graph_key = -1;
   cudaStream_t gstream = nullptr;   // private stream the graph is captured on and replayed on
+  cudaStream_t gstream2 = nullptr;  // second branch of a captured sweep (contact, pool)
   cudaEvent_t gev[2] = {nullptr, nullptr};
+  cudaEvent_t gfork[4] = {nullptr, nullptr, nullptr, nullptr};
   // single-scene steps: the device view the chunk was captured with (re-captured when a
   // device buffer moves) and its kernel groups in launch order, each with the number of
   // kernels and, when profiling, the pair of external timing events recorded around it

@@ -13,7 +13,8 @@
 //   incidence   sliced-ELL list per 32-vertex slice: entry j of lane l sits at
 //               off[slice] + 32 j + l, value = 4*tet + corner (coalesced warp reads).
 //   cubature    per free vertex and slot s: pool slot index, weight, and U_bar rows
-//               (12x3) as [slot][36][Vf] so a warp's loads are coalesced.
+//               (12x3) as [slot][36][cs] (cs = Vf rounded up to 4) so a warp's loads are
+//               coalesced and a block's rows can be bulk-copied.
 //   pool        per sweep, one 16-byte aligned row per cubature element: the rotated
 //               12x12 element Hessian (78 packed values), then
 //               the 12 rotated gradient entries of every cubature element.
@@ -29,6 +30,9 @@ constexpr int kLsTrials = 8;     // line-search steps alpha = 2^-j, j < kLsTrial
 constexpr int kPairTrialBlocks = 148 * 4;  // blocks of the line-search barrier-trial pass
 constexpr int kEnergyBlocksMax = 148 * 8;  // blocks of the line-search energy pass, at most
 constexpr int kPackedH = 78;     // 12x12 symmetric, upper triangle row-major
+// Row stride of the per-slot cubature record arrays: Vf rounded up to 4 entries, so that
+// every row starts on a 16-byte boundary.
+__host__ __device__ constexpr int cub_stride(int Vf) { return ((Vf + 3) / 4) * 4; }
 constexpr int kPoolStride = 92;  // pool row: 78 packed Hessian entries, 12 gradient entries, 2 pad
 
 template <typename T>
@@ -114,9 +118,10 @@ struct ContactView {
 // Per-scene state of a batch mesh (one slot per scene; a single mesh is not batched).
 struct SceneState {
   int32_t done, converged, status, sweeps, k, fallback, ls_rejects, dir;
+  int32_t need_j, pad;  // need_j: every line-search trial along D failed, try D_J
   double g0, r, slope, slope_j, alpha;
 };
-constexpr int kSceneAcc = 16;  // per-scene FP64 sums: |g|^2, g.D_J, g.D, 12 line-search coefficients
+constexpr int kSceneAcc = 16;  // per-scene FP64 sums: |g|^2, g.D_J, g.D, 6 line-search coefficients
 
 template <typename T>
 struct DevMesh {
@@ -134,9 +139,10 @@ struct DevMesh {
   Vec4<T>* DJ;              // [Vf] uncorrected direction -H_ii^{-1} g_i
   T* ghr;                   // [18][Vf] g_i, H_ii (6), R_i (9) between the two sweep phases
   const T* mh2;             // [V] m_v / h^2 (0 for pinned)
-  const int32_t* cub_p;     // [n_cub][Vf] pool slot, -1 unused
-  const T* cub_w;           // [n_cub][Vf]
-  const T* cub_u;           // [n_cub][36][Vf]
+  int cs;                   // row stride of the cubature records: Vf rounded up to 4
+  const int32_t* cub_p;     // [n_cub][cs] pool slot, -1 unused
+  const T* cub_w;           // [n_cub][cs]
+  const T* cub_u;           // [n_cub][36][cs]
   const int32_t* pool_tet;  // [nP]
   T* pool_H;                // [nP][92] packed rotated Hessian (78), rotated gradient (12), pad
   T* pool_G;                // [nP][12]

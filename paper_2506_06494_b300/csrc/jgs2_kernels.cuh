@@ -14,6 +14,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstdint>
 #include <utility>
 
@@ -129,6 +130,55 @@ __device__ __forceinline__ void block_sum_acc(Acc<T> (&a)[NV], double (&out)[NV]
   __syncthreads();
 }
 
+// Batch meshes: adds NV per-thread accumulators into the per-scene FP64 sums of scene sc
+// (-1: none). Called by every thread of the block. A block whose threads all belong to one
+// scene (or none) reduces with Acc<T> and adds once per value (scenes are contiguous, so
+// that is almost every block); otherwise a warp whose lanes share one scene adds once, and
+// a mixed warp adds per lane.
+template <typename T, int NV>
+__device__ __forceinline__ void scene_reduce_acc(Acc<T> (&a)[NV], int sc, double* sacc, int off) {
+  __shared__ int s_min, s_max;
+  __shared__ Acc<T> s_red[32 * NV];
+  if (threadIdx.x == 0) {
+    s_min = INT_MAX;
+    s_max = -1;
+  }
+  __syncthreads();
+  {
+    const int lo = __reduce_min_sync(0xffffffffu, sc >= 0 ? sc : INT_MAX);
+    const int hi = __reduce_max_sync(0xffffffffu, sc);
+    if ((threadIdx.x & 31) == 0) {
+      if (lo != INT_MAX) atomicMin(&s_min, lo);
+      if (hi >= 0) atomicMax(&s_max, hi);
+    }
+  }
+  __syncthreads();
+  const int bmin = s_min, bmax = s_max;
+  if (bmax < 0) return;  // nothing to add (block-uniform)
+  if (bmin == bmax) {
+    double out[NV];
+    block_sum_acc<T, NV>(a, out, s_red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int j = 0; j < NV; ++j) atomicAdd(sacc + (size_t)bmin * kSceneAcc + off + j, out[j]);
+    }
+    return;
+  }
+  const int s0 = __shfl_sync(0xffffffffu, sc, 0);
+  if (__all_sync(0xffffffffu, sc == s0)) {
+    if (s0 < 0) return;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a[j].add_lane(o);
+      if ((threadIdx.x & 31) == 0) atomicAdd(sacc + (size_t)s0 * kSceneAcc + off + j, a[j].value());
+    }
+  } else if (sc >= 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) atomicAdd(sacc + (size_t)sc * kSceneAcc + off + j, a[j].value());
+  }
+}
+
 // Sum of n partials (fixed order) by one block; result valid in thread 0.
 __device__ __forceinline__ double block_sum_array(const double* p, int n, int stride,
                                                   double* smem) {
@@ -152,30 +202,59 @@ __device__ __forceinline__ bool last_block(uint32_t* ticket) {
   return is_last;
 }
 
-// Batch meshes: adds NV per-thread values into the per-scene sums of scene sc (-1: none).
-// A warp whose lanes share one scene reduces first and adds once.
-template <int NV>
-__device__ __forceinline__ void scene_reduce(const double (&v)[NV], int sc, double* sacc, int off) {
-  const int s0 = __shfl_sync(0xffffffffu, sc, 0);
-  if (__all_sync(0xffffffffu, sc == s0)) {
-    if (s0 < 0) return;
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-      const double x = warp_sum(v[j]);
-      if ((threadIdx.x & 31) == 0) atomicAdd(sacc + (size_t)s0 * kSceneAcc + off + j, x);
-    }
-  } else if (sc >= 0) {
-#pragma unroll
-    for (int j = 0; j < NV; ++j) atomicAdd(sacc + (size_t)sc * kSceneAcc + off + j, v[j]);
-  }
-}
-
 template <typename T>
 __device__ __forceinline__ void load3(const Vec4<T>* a, int i, T (&o)[3]) {
   Vec4<T> q = a[i];
   o[0] = q.x;
   o[1] = q.y;
   o[2] = q.z;
+}
+
+// ------------------------------------------------------------------ bulk copies
+// Asynchronous global -> shared copies of contiguous byte ranges (cp.async.bulk, the
+// Blackwell copy engine's 1-D form) completed on an mbarrier: one thread posts the
+// expected byte count and the copy; every thread waits on the barrier's phase. Waits are
+// bounded (kWaitPolls polls of mbarrier.try_wait); a caller that gives up reports
+// JGS2_ETIMEOUT. Addresses and sizes are multiples of 16 bytes.
+constexpr int kWaitPolls = 1 << 20;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// true once the barrier's phase with this parity has completed; false after kWaitPolls polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < kWaitPolls; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
 }
 
 // Copies the records of tets [t0, t0 + n) into shared memory with coalesced 16-byte loads
@@ -304,6 +383,8 @@ __device__ __forceinline__ void gather_vertex(const DevMesh<T>& m, int v, T (&g)
 #pragma unroll
   for (int q = 0; q < 9; ++q) Fs[q] = T(0);
   W = T(0);
+  // two incidences per trip: their loads are in flight together
+#pragma unroll 4
   for (int j = 0; j < n; ++j) {
     const int ent = __ldg(m.inc + base + j * kSlice);
     const int t = ent >> 2, c = ent & 3;
@@ -499,21 +580,77 @@ __device__ __forceinline__ void pool_entry(T h, T w, const T (&U)[36], T (&M)[36
 template <typename T>
 __device__ __forceinline__ void load4(const T* __restrict__ p, T (&o)[4]);
 
-template <int Q4, typename T>
+template <int Q4, bool SMEM, typename T>
 __device__ __forceinline__ void pool_chunk(const T* __restrict__ Hp, T w, const T (&U)[36], T (&M)[36],
                                            T (&gt)[3]) {
   T hv[4];
-  load4(Hp + 4 * Q4, hv);
+  if constexpr (SMEM) {
+    // staged row in shared memory: plain 16-byte loads
+    if constexpr (sizeof(T) == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(Hp + 4 * Q4);
+      hv[0] = v.x;
+      hv[1] = v.y;
+      hv[2] = v.z;
+      hv[3] = v.w;
+    } else {
+      const double2 a = *reinterpret_cast<const double2*>(Hp + 4 * Q4);
+      const double2 b = *(reinterpret_cast<const double2*>(Hp + 4 * Q4) + 1);
+      hv[0] = a.x;
+      hv[1] = a.y;
+      hv[2] = b.x;
+      hv[3] = b.y;
+    }
+  } else {
+    load4(Hp + 4 * Q4, hv);
+  }
   pool_entry<4 * Q4 + 0>(hv[0], w, U, M, gt);
   pool_entry<4 * Q4 + 1>(hv[1], w, U, M, gt);
   pool_entry<4 * Q4 + 2>(hv[2], w, U, M, gt);
   pool_entry<4 * Q4 + 3>(hv[3], w, U, M, gt);
 }
 
-template <typename T, int... Q4>
+template <bool SMEM, typename T, int... Q4>
 __device__ __forceinline__ void pool_row(const T* __restrict__ Hp, T w, const T (&U)[36], T (&M)[36], T (&gt)[3],
                                          std::integer_sequence<int, Q4...>) {
-  (pool_chunk<Q4>(Hp, w, U, M, gt), ...);
+  (pool_chunk<Q4, SMEM>(Hp, w, U, M, gt), ...);
+}
+
+// One cubature slot of Eq. cubature: the pool row Hp (packed rotated element Hessian, then
+// the rotated corner gradients) against the slot's weight w and U_bar rows U (12x3):
+// H~' += w U^T H' U, g~' += w U^T G'.
+template <typename T>
+__device__ __forceinline__ void slot_sums(const T* __restrict__ Hp, T w, const T (&U)[36], T (&Ht)[6], T (&gt)[3]) {
+  // M = H' U (12x3) streamed from the upper triangle in 16-byte loads
+  T M[36];
+#pragma unroll
+  for (int q = 0; q < 36; ++q) M[q] = T(0);
+  pool_row<false>(Hp, w, U, M, gt, std::make_integer_sequence<int, (kPackedH + 12 + 3) / 4>{});
+  // H~' += w U^T M (symmetric: six entries)
+#pragma unroll
+  for (int r = 0; r < 12; ++r) {
+    const T wu0 = w * U[3 * r], wu1 = w * U[3 * r + 1], wu2 = w * U[3 * r + 2];
+    Ht[0] += wu0 * M[3 * r];
+    Ht[1] += wu0 * M[3 * r + 1];
+    Ht[2] += wu0 * M[3 * r + 2];
+    Ht[3] += wu1 * M[3 * r + 1];
+    Ht[4] += wu1 * M[3 * r + 2];
+    Ht[5] += wu2 * M[3 * r + 2];
+  }
+}
+
+// Cubature sums for vertex i over its n_cub slots, records read directly from global memory.
+template <typename T>
+__device__ __forceinline__ void cubature_sums(const DevMesh<T>& m, int i, T (&Ht)[6], T (&gt)[3]) {
+  for (int s = 0; s < m.n_cub; ++s) {
+    const int p = m.cub_p[(size_t)s * m.cs + i];
+    if (p < 0) continue;
+    const T w = m.cub_w[(size_t)s * m.cs + i];
+    T U[36];
+    const T* up = m.cub_u + (size_t)s * 36 * m.cs + i;
+#pragma unroll
+    for (int q = 0; q < 36; ++q) U[q] = up[(size_t)q * m.cs];
+    slot_sums(m.pool_H + (size_t)p * kPoolStride, w, U, Ht, gt);
+  }
 }
 
 // Four consecutive values from a 16-byte aligned address through the read-only path (one
@@ -646,7 +783,9 @@ template <typename T, bool BATCH>
 __global__ void __launch_bounds__(128) k_elem(DevMesh<T> m, const StepState* __restrict__ st) {
   if (!BATCH && st->done) return;
   __shared__ __align__(16) TetRec<T> srec[128];
-  const int t0 = blockIdx.x * 128, n = min(128, m.T_ - t0);
+  // tiles in descending order: the lowest tets, which the gather (ascending vertices)
+  // reads first, are written last and are still in L2 when it starts
+  const int t0 = (gridDim.x - 1 - blockIdx.x) * 128, n = min(128, m.T_ - t0);
   stage_tets<T, 128>(m.tets, t0, n, srec);
   __syncthreads();
   if ((int)threadIdx.x >= n) return;
@@ -661,187 +800,136 @@ __global__ void __launch_bounds__(128) k_elem(DevMesh<T> m, const StepState* __r
   m.frec[t] = o;
 }
 
-// Per cubature element: 4 warps gather the element's corners (warp a -> corner a), then
-// one thread forms the element Hessian of E_hat_e = V_e Psi(F_e) + sum_a m_e/(2h^2)|x_a-z_a|^2
-// at x^k and rotates it and the corner gradients into the corners' rest frames.
+// Per cubature element, one warp (kPoolWarps elements per block), after the sweep's gather:
+// lanes 0-3 take corner a's assembled gradient g_a and rotation R_a from the gather's
+// hand-off (identity and zero at pinned corners), then the lanes form dP/dF (81 entries)
+// and the 90 outputs: the element Hessian of E_hat_e = V_e Psi(F_e) + sum_a
+// m_e/(2h^2)|x_a - z_a|^2 at x^k rotated into the rest frames of its corners (packed, 78)
+// and the rotated corner gradients (12).
 // ASM = true: corner gradients are the assembled g_a (reading R3 "asm");
 // ASM = false: the element's own gradient of E_hat_e (literal Eq. cubature, "elem").
+constexpr int kPoolWarps = 4;
+
+template <typename T>
+struct PoolShared {
+  T R[4][9], g[4][3], b[4][3], A[81];
+};
+
 template <typename T, bool ASM>
-__global__ void __launch_bounds__(128) k_pool(DevMesh<T> m, const StepState* __restrict__ st) {
+__global__ void __launch_bounds__(32 * kPoolWarps) k_pool(DevMesh<T> m, const StepState* __restrict__ st) {
   if (st->done) return;
-  const int p = blockIdx.x;
+  __shared__ PoolShared<T> sh_all[kPoolWarps];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __shared__ T sR[4][9];
-  __shared__ T sg[4][3];
+  const int p = blockIdx.x * kPoolWarps + wid;
+  if (p >= m.nP) return;  // whole warps only; no block-wide barrier below
+  PoolShared<T>& sh = sh_all[wid];
   const int t = m.pool_tet[p];
-  const TetRec<T> rec = m.tets[t];
-  {
-    const int v = rec.v[wid];
-    T g[3] = {T(0), T(0), T(0)}, Fs[9], W = T(0);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) Fs[q] = T(0);
+  const TetRec<T>& rec = m.tets[t];  // read in place (global, cached)
+  if (lane < 4) {
+    const int v = rec.v[lane];
+    T R[9], g[3];
     if (v < m.Vf) {
-      // lanes split the incidence list of this vertex
-      const int slice = v / kSlice, ln = v % kSlice;
-      const int base = m.inc_off[slice] + ln;
-      const int n = m.inc_len[v];
-      for (int j = lane; j < n; j += 32) {
-        const int ent = m.inc[base + j * kSlice];
-        const int tt = ent >> 2, c = ent & 3;
-        const TetRec<T> r = m.tets[tt];
-        T F[9], C[9], b[3];
-        tet_F(r, m.u, F);
-        cofactor(F, C);
-        const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
-        const T s = r.lp * (J - T(1)) - r.mu;
-        corner_b(r, c, b);
+      const T* o = m.ghr + v;
+      const size_t S = m.Vf;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const T Fb = F[3 * i] * b[0] + F[3 * i + 1] * b[1] + F[3 * i + 2] * b[2];
-          const T G = C[3 * i] * b[0] + C[3 * i + 1] * b[1] + C[3 * i + 2] * b[2];
-          g[i] += r.vol * (r.mu * Fb + s * G);
-        }
+      for (int i = 0; i < 3; ++i) g[i] = o[i * S];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) Fs[q] += r.vol * F[q];
-        W += r.vol;
-      }
-      // fixed-order warp reduction (tree over lanes)
+      for (int q = 0; q < 9; ++q) R[q] = o[(9 + q) * S];
+    } else {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
+      for (int q = 0; q < 9; ++q) R[q] = (q % 4 == 0) ? T(1) : T(0);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) g[i] += __shfl_down_sync(0xffffffffu, g[i], o);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) Fs[q] += __shfl_down_sync(0xffffffffu, Fs[q], o);
-        W += __shfl_down_sync(0xffffffffu, W, o);
-      }
+      for (int i = 0; i < 3; ++i) g[i] = T(0);
     }
-    if (lane == 0) {
-      T R[9];
-      if (v < m.Vf) {
-        T uv[3], dz[3];
-        load3(m.u, v, uv);
-        load3(m.dz, v, dz);
-        const T mh = m.mh2[v];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) g[i] += mh * (uv[i] - dz[i]);
-        if (m.c.on) {
+    for (int q = 0; q < 9; ++q) sh.R[lane][q] = R[q];
 #pragma unroll
-          for (int i = 0; i < 3; ++i) g[i] += T(m.c.bg[(size_t)i * m.V + v]);
-        }
+    for (int i = 0; i < 3; ++i) sh.g[lane][i] = g[i];
+    const Vec4<T> bq = m.bc[4 * (size_t)t + lane];
+    sh.b[lane][0] = bq.x;
+    sh.b[lane][1] = bq.y;
+    sh.b[lane][2] = bq.z;
+    if (m.pool_R != nullptr) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) Fs[q] /= W;
-        polar_rotation(Fs, R);
-      } else {
-#pragma unroll
-        for (int q = 0; q < 9; ++q) R[q] = (q % 4 == 0) ? T(1) : T(0);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) g[i] = T(0);
-      }
-#pragma unroll
-      for (int q = 0; q < 9; ++q) sR[wid][q] = R[q];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) sg[wid][i] = g[i];
-      if (m.pool_R != nullptr) {
-#pragma unroll
-        for (int q = 0; q < 9; ++q) m.pool_R[(size_t)p * 36 + 9 * wid + q] = R[q];
-      }
+      for (int q = 0; q < 9; ++q) m.pool_R[(size_t)p * 36 + 9 * lane + q] = R[q];
     }
   }
-  // element quantities at x^k, shared by the block
-  __shared__ T sF[9], sC[9], sA[81], sb[4][3];
-  __shared__ T ss;
-  if (threadIdx.x == 0) {
-    T F[9], C[9];
-    tet_F(rec, m.u, F);
-    cofactor(F, C);
-    const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
-    ss = rec.lp * (J - T(1)) - rec.mu;
+  // element quantities at x^k (every lane), dP/dF = mu I + lam' c c^T + s d2J/dF2 (9x9,
+  // index 3i+j), c = vec(cof F); d2J/dF_ij dF_kl = eps_ikm eps_jln F_mn (i != k, j != l)
+  T F[9], C[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      sF[q] = F[q];
-      sC[q] = C[q];
-    }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      T b[3];
-      corner_b(rec, c, b);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) sb[c][j] = b[j];
-    }
-  }
-  __syncthreads();
-  // dP/dF = mu I + lam' c c^T + s d2J/dF2 (9x9, index 3i+j), c = vec(cof F);
-  // d2J/dF_ij dF_kl = eps_ikm eps_jln F_mn (nonzero only for i != k and j != l)
-  if (threadIdx.x < 81) {
-    const int row = threadIdx.x / 9, col = threadIdx.x % 9;
+  for (int q = 0; q < 9; ++q) F[q] = m.frec[t].F[q];
+  cofactor(F, C);
+  const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
+  const T mu = rec.mu, lp = rec.lp, vol = rec.vol;
+  const T ss = lp * (J - T(1)) - mu;
+  for (int e = lane; e < 81; e += 32) {
+    const int row = e / 9, col = e % 9;
     const int i = row / 3, j = row % 3, k = col / 3, l = col % 3;
-    T v = rec.lp * sC[row] * sC[col] + (row == col ? rec.mu : T(0));
+    T v = lp * C[row] * C[col] + (row == col ? mu : T(0));
     if (i != k && j != l) {
       const int mm = 3 - i - k, n = 3 - j - l;
       const T sik = ((k - i + 3) % 3 == 1) ? T(1) : T(-1);
       const T sjl = ((l - j + 3) % 3 == 1) ? T(1) : T(-1);
-      v += ss * sik * sjl * sF[3 * mm + n];
+      v += ss * sik * sjl * F[3 * mm + n];
     }
-    sA[threadIdx.x] = v;
+    sh.A[e] = v;
   }
-  __syncthreads();
+  __syncwarp();
   const T mi = rec.mq * T(m.inv_h2);
-  // packed entry (r, c), r <= c, of H' = blockdiag(R)^T H_e blockdiag(R), with
-  // H_e[(a,i),(c,k)] = V sum_{j,l} b_a[j] A[(i,j),(k,l)] b_c[l] + m_e/h^2 delta
-  if (threadIdx.x < kPackedH) {
-    int r = 0, rem = threadIdx.x;
-    while (rem >= 12 - r) {
-      rem -= 12 - r;
-      ++r;
-    }
-    const int c = r + rem;
-    const int a = r / 3, jj = r % 3, cc = c / 3, ll = c % 3;
-    T Hac[9];
+  T* Hrow = m.pool_H + (size_t)p * kPoolStride;
+  for (int e = lane; e < kPackedH + 12; e += 32) {
+    if (e < kPackedH) {
+      // packed entry (r, c), r <= c, of H' = blockdiag(R)^T H_e blockdiag(R), with
+      // H_e[(a,i),(c,k)] = V sum_{j,l} b_a[j] A[(i,j),(k,l)] b_c[l] + m_e/h^2 delta
+      const int r = pk_row(e), c = pk_col(e);
+      const int a = r / 3, jj = r % 3, cc = c / 3, ll = c % 3;
+      T Hac[9];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+      for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        T acc = T(0);
+        for (int k = 0; k < 3; ++k) {
+          T acc = T(0);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          T row = T(0);
+          for (int j = 0; j < 3; ++j) {
+            T row = T(0);
 #pragma unroll
-          for (int l = 0; l < 3; ++l) row += sA[9 * (3 * i + j) + 3 * k + l] * sb[cc][l];
-          acc += sb[a][j] * row;
+            for (int l = 0; l < 3; ++l) row += sh.A[9 * (3 * i + j) + 3 * k + l] * sh.b[cc][l];
+            acc += sh.b[a][j] * row;
+          }
+          Hac[3 * i + k] = vol * acc + ((a == cc && i == k) ? mi : T(0));
         }
-        Hac[3 * i + k] = rec.vol * acc + ((a == cc && i == k) ? mi : T(0));
-      }
-    T v = T(0);
+      T v = T(0);
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+      for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) v += sR[a][3 * i + jj] * Hac[3 * i + k] * sR[cc][3 * k + ll];
-    m.pool_H[(size_t)p * kPoolStride + threadIdx.x] = v;
-  } else if (threadIdx.x < kPackedH + 12) {
-    // rotated corner gradient entry (a, j)
-    const int e = threadIdx.x - kPackedH, a = e / 3, j = e % 3;
-    T ga[3];
-    if (ASM) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) ga[i] = sg[a][i];
+        for (int k = 0; k < 3; ++k) v += sh.R[a][3 * i + jj] * Hac[3 * i + k] * sh.R[cc][3 * k + ll];
+      Hrow[e] = v;
     } else {
-      const int v = rec.v[a];
-      if (v < m.Vf) {
-        T uv[3], dz[3];
-        load3(m.u, v, uv);
-        load3(m.dz, v, dz);
+      // rotated corner gradient entry (a, j)
+      const int q = e - kPackedH, a = q / 3, j = q % 3;
+      T ga[3];
+      if (ASM) {
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const T Pb = (rec.mu * sF[3 * i] + ss * sC[3 * i]) * sb[a][0] +
-                       (rec.mu * sF[3 * i + 1] + ss * sC[3 * i + 1]) * sb[a][1] +
-                       (rec.mu * sF[3 * i + 2] + ss * sC[3 * i + 2]) * sb[a][2];
-          ga[i] = rec.vol * Pb + mi * (uv[i] - dz[i]);
-        }
+        for (int i = 0; i < 3; ++i) ga[i] = sh.g[a][i];
       } else {
-        ga[0] = ga[1] = ga[2] = T(0);
+        const int v = rec.v[a];
+        if (v < m.Vf) {
+          T uv[3], dz[3];
+          load3(m.u, v, uv);
+          load3(m.dz, v, dz);
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const T Pb = (mu * F[3 * i] + ss * C[3 * i]) * sh.b[a][0] + (mu * F[3 * i + 1] + ss * C[3 * i + 1]) * sh.b[a][1] +
+                         (mu * F[3 * i + 2] + ss * C[3 * i + 2]) * sh.b[a][2];
+            ga[i] = vol * Pb + mi * (uv[i] - dz[i]);
+          }
+        } else {
+          ga[0] = ga[1] = ga[2] = T(0);
+        }
       }
+      Hrow[e] = sh.R[a][j] * ga[0] + sh.R[a][3 + j] * ga[1] + sh.R[a][6 + j] * ga[2];
     }
-    m.pool_H[(size_t)p * kPoolStride + kPackedH + e] = sR[a][j] * ga[0] + sR[a][3 + j] * ga[1] + sR[a][6 + j] * ga[2];
   }
 }
 
@@ -883,7 +971,7 @@ __device__ __forceinline__ void finalize_sweep(StepState* st, double r2, double 
 // phase 2 and the FP64 partial sums |g|^2 and g.D_J. Without the correction D = D_J and
 // this kernel closes the sweep's reduction.
 template <typename T, bool CORR, bool BATCH, int BS>
-__global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 1024 : 512) / BS)
+__global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
     k_gather(DevMesh<T> m, StepState* st, double* __restrict__ partial /* [3][grid] */,
              double* __restrict__ trace, int record) {
   if (!BATCH && st->done) return;
@@ -950,8 +1038,7 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 1024 : 512) / BS)
     }
   }
   if (BATCH) {
-    const double av[2] = {acc[0].value(), acc[1].value()};
-    scene_reduce<2>(av, active ? sc : -1, m.sacc, 0);
+    scene_reduce_acc<T, 2>(acc, active ? sc : -1, m.sacc, 0);
     return;
   }
   double bs[2];
@@ -968,10 +1055,10 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 1024 : 512) / BS)
 }
 
 // Sweep phase 2, thread per free vertex: the cubature sums H~_i, g~_i (Eq. cubature) from
-// the rotated pool element data, the 3x3 solve of Eq. reduced_local, D_i, and g.D. The
+// the rotated pool element data (L2-resident rows), the 3x3 solve of Eq. reduced_local, D_i, and g.D. The
 // last block closes the sweep's reduction with phase 1's partial sums.
 template <typename T, bool BATCH, int BS>
-__global__ void __launch_bounds__(BS) k_correct(DevMesh<T> m, StepState* st,
+__global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 512 : 256) / BS) k_correct(DevMesh<T> m, StepState* st,
                                                 double* __restrict__ partial /* [3][grid] */,
                                                 double* __restrict__ trace, int record) {
   if (!BATCH && st->done) return;
@@ -983,6 +1070,10 @@ __global__ void __launch_bounds__(BS) k_correct(DevMesh<T> m, StepState* st,
   const int sc = (BATCH && i < m.Vf) ? m.v_scene[i] : -1;
   const bool active = i < m.Vf && (!BATCH || !m.scenes[sc].done);
   if (active) {
+    T Ht[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, gt[3] = {T(0), T(0), T(0)};
+    cubature_sums(m, i, Ht, gt);
+    // the vertex's own g, H_ii, R_i from the gather (loaded after the cubature loop, so
+    // they hold no registers during it)
     const T* o = m.ghr + i;
     const size_t S = m.Vf;
     T g[3], H[6], R[9];
@@ -992,34 +1083,6 @@ __global__ void __launch_bounds__(BS) k_correct(DevMesh<T> m, StepState* st,
     for (int q = 0; q < 6; ++q) H[q] = o[(3 + q) * S];
 #pragma unroll
     for (int q = 0; q < 9; ++q) R[q] = o[(9 + q) * S];
-    T Ht[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, gt[3] = {T(0), T(0), T(0)};
-    for (int s = 0; s < m.n_cub; ++s) {
-      const int p = m.cub_p[(size_t)s * m.Vf + i];
-      if (p < 0) continue;
-      const T w = m.cub_w[(size_t)s * m.Vf + i];
-      T U[36];
-      const T* up = m.cub_u + (size_t)s * 36 * m.Vf + i;
-#pragma unroll
-      for (int q = 0; q < 36; ++q) U[q] = up[(size_t)q * m.Vf];
-      // stream the pool row (packed H', then the rotated corner gradients) in 16-byte
-      // loads: M = H' U (12x3) from the upper triangle, g~' += w U^T G
-      const T* Hp = m.pool_H + (size_t)p * kPoolStride;
-      T M[36];
-#pragma unroll
-      for (int q = 0; q < 36; ++q) M[q] = T(0);
-      pool_row(Hp, w, U, M, gt, std::make_integer_sequence<int, (kPackedH + 12 + 3) / 4>{});
-      // H~' += w U^T M (symmetric: six entries)
-#pragma unroll
-      for (int r = 0; r < 12; ++r) {
-        const T wu0 = w * U[3 * r], wu1 = w * U[3 * r + 1], wu2 = w * U[3 * r + 2];
-        Ht[0] += wu0 * M[3 * r];
-        Ht[1] += wu0 * M[3 * r + 1];
-        Ht[2] += wu0 * M[3 * r + 2];
-        Ht[3] += wu1 * M[3 * r + 1];
-        Ht[4] += wu1 * M[3 * r + 2];
-        Ht[5] += wu2 * M[3 * r + 2];
-      }
-    }
     // back to world: H~ = R H~' R^T, g~ = R g~'
     T Hf[9] = {Ht[0], Ht[1], Ht[2], Ht[1], Ht[3], Ht[4], Ht[2], Ht[4], Ht[5]};
     T RH[9];
@@ -1054,8 +1117,7 @@ __global__ void __launch_bounds__(BS) k_correct(DevMesh<T> m, StepState* st,
   }
   if (BATCH) {
     if (fb) atomicAdd(&m.scenes[sc].fallback, 1);
-    const double av[1] = {acc[0].value()};
-    scene_reduce<1>(av, active ? sc : -1, m.sacc, 2);
+    scene_reduce_acc<T, 1>(acc, active ? sc : -1, m.sacc, 2);
     return;
   }
   if (__syncthreads_or(fb)) {
@@ -1160,7 +1222,8 @@ __global__ void __launch_bounds__(128) k_pair_trials(DevMesh<T> m, const StepSta
 // DIR = 1 the uncorrected direction D_J, tried only when every trial along D failed
 // (the launch returns at once otherwise). The energy change along the direction is a
 // polynomial in the step a; its coefficients are summed over tets (tiles of 128 records
-// staged in shared memory) and free vertices, per thread and per block with Acc<T>
+// brought into shared memory by bulk copies, double-buffered in FP32) and free vertices,
+// per thread and per block with Acc<T>
 // (FP64-class), across blocks in FP64. The last block adds the barrier sums of
 // k_pair_trials (n_pp blocks; 0 without contact), evaluates E(x + a d) - E(x) at a = 2^-j
 // and takes the first Armijo-satisfying trial. has_j = 0 (no correction, D = D_J): a
@@ -1172,19 +1235,52 @@ __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st, int
   if (st->done) return;
   if (DIR == 1 && !st->need_j) return;
   constexpr int NC = 6;
-  __shared__ __align__(16) TetRec<T> srec[128];
+  // tiles of 128 records arrive by bulk copy; FP32 double-buffers them (the next tile is in
+  // flight while this one is evaluated), FP64 (records twice as large) uses one buffer
+  constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;
+  __shared__ __align__(128) TetRec<T> srec[NBUF][128];
+  __shared__ __align__(8) uint64_t bar[NBUF];
   __shared__ Acc<T> sacc[32 * NC];
   __shared__ double red[32];
   const Vec4<T>* __restrict__ dir = DIR == 0 ? m.D : m.DJ;
   Acc<T> acc[NC];
   const int ntile = (m.T_ + 127) / 128;
-  for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int b = 0; b < NBUF; ++b) mbar_init(&bar[b], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  auto issue = [&](int tl, int b) {
+    if (threadIdx.x == 0 && tl < ntile) {
+      const uint32_t bytes = uint32_t(min(128, m.T_ - tl * 128)) * uint32_t(sizeof(TetRec<T>));
+      mbar_expect_tx(&bar[b], bytes);
+      bulk_copy_g2s(&srec[b][0], m.tets + (size_t)tl * 128, bytes, &bar[b]);
+    }
+  };
+  issue(blockIdx.x, 0);
+  int k = 0;
+  for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x, ++k) {
     const int t0 = tile * 128, n = min(128, m.T_ - t0);
-    __syncthreads();  // the previous tile's records are consumed
-    stage_tets<T, 128>(m.tets, t0, n, srec);
-    __syncthreads();
+    const int b = NBUF == 2 ? (k & 1) : 0;
+    if (NBUF == 2) issue(tile + gridDim.x, b ^ 1);
+    const bool got = mbar_wait(&bar[b], uint32_t((k / NBUF) & 1));
+    if (__syncthreads_or(!got)) {
+      // the copy never completed: report, wait (bounded) for the copies in flight, leave
+      if (threadIdx.x == 0) {
+        st->status = 8;  // JGS2_ETIMEOUT
+        st->done = 1;
+      }
+      mbar_wait(&bar[b], uint32_t((k / NBUF) & 1));
+      if (NBUF == 2 && tile + (int)gridDim.x < ntile) mbar_wait(&bar[b ^ 1], uint32_t(((k + 1) / NBUF) & 1));
+      return;
+    }
+    const TetRec<T>* srec_b = srec[b];
     if ((int)threadIdx.x < n) {
-      const TetRec<T>& r = srec[threadIdx.x];
+      // F_e(x^k) is recomputed from the staged record and the corners' displacements
+      // (L2-resident) rather than read back from the element pass, whose records have
+      // left L2 by now
+      const TetRec<T>& r = srec_b[threadIdx.x];
       T F[9], C[9], dF[9], c[6];
       tet_F(r, m.u, F);
       cofactor(F, C);
@@ -1194,6 +1290,8 @@ __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st, int
 #pragma unroll
       for (int j = 0; j < 6; ++j) acc[j].add(c[j]);
     }
+    __syncthreads();  // buffer b is read; it may be refilled
+    if (NBUF == 1) issue(tile + gridDim.x, 0);
   }
   // inertia: m/(2h^2) (2 a d.(u - dz) + a^2 |d|^2)
   const int stride = gridDim.x * blockDim.x;
@@ -1245,70 +1343,76 @@ __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st, int
   }
 }
 
-// Batch meshes: the same energy-change coefficients, summed per scene (thread per tet in
-// blocks [0, tet_blocks), thread per free vertex after; no contact).
-template <typename T, int ND>
+// Batch meshes: the energy-change coefficients of k_energy along one direction (DIR 0: D,
+// DIR 1: D_J for the scenes whose trials along D all failed), summed per scene; thread per
+// tet in blocks [0, tet_blocks) (tiles staged in shared memory), thread per free vertex
+// after; no contact. Blocks whose scenes have nothing to do return before loading.
+template <typename T, int DIR>
 __global__ void __launch_bounds__(128) k_energy_batch(DevMesh<T> m, int tet_blocks) {
-  constexpr int NC = 6 * ND;
-  double acc[NC];
-#pragma unroll
-  for (int j = 0; j < NC; ++j) acc[j] = 0.0;
-  int sc = -1;
+  constexpr int NC = 6;
   __shared__ __align__(16) TetRec<T> srec[128];
-  if ((int)blockIdx.x < tet_blocks) {
-    const int t0 = blockIdx.x * 128;
-    stage_tets<T, 128>(m.tets, t0, min(128, m.T_ - t0), srec);
+  __shared__ int busy;
+  const bool tets = (int)blockIdx.x < tet_blocks;
+  const int i0 = tets ? blockIdx.x * 128 : (blockIdx.x - tet_blocks) * 128;
+  const int n = min(128, (tets ? m.T_ : m.Vf) - i0);
+  const int32_t* scene_of = tets ? m.t_scene : m.v_scene;
+  auto wants = [&](int sc) {
+    const SceneState& S = m.scenes[sc];
+    return !S.done && (DIR == 0 || S.need_j);
+  };
+  if (threadIdx.x == 0) {
+    // scenes are contiguous: the block covers scenes scene_of[i0] .. scene_of[i0 + n - 1]
+    int any = 0;
+    for (int sc = scene_of[i0]; sc <= scene_of[i0 + n - 1] && !any; ++sc) any = wants(sc) ? 1 : 0;
+    busy = any;
+  }
+  __syncthreads();
+  if (!busy) return;
+  const Vec4<T>* __restrict__ dir = DIR == 0 ? m.D : m.DJ;
+  Acc<T> acc[NC];
+  int sc = -1;
+  if (tets) {
+    stage_tets<T, 128>(m.tets, i0, n, srec);
     __syncthreads();
-    const int t = t0 + threadIdx.x;
-    if (t < m.T_) {
+    if ((int)threadIdx.x < n) {
+      const int t = i0 + threadIdx.x;
       sc = m.t_scene[t];
-      if (!m.scenes[sc].done) {
+      if (wants(sc)) {
         const TetRec<T>& r = srec[threadIdx.x];
         T F[9], C[9], dF[9], c[6];
         tet_F(r, m.u, F);
         cofactor(F, C);
         const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
-        tet_dF(r, m.D, m.Vf, dF);
+        tet_dF(r, dir, m.Vf, dF);
         tet_dpsi_poly(r, F, C, J, dF, c);
 #pragma unroll
-        for (int j = 0; j < 6; ++j) acc[j] = double(c[j]);
-        if (ND == 2) {
-          tet_dF(r, m.DJ, m.Vf, dF);
-          tet_dpsi_poly(r, F, C, J, dF, c);
-#pragma unroll
-          for (int j = 0; j < 6; ++j) acc[6 + j] = double(c[j]);
-        }
+        for (int j = 0; j < NC; ++j) acc[j].add(c[j]);
       } else {
         sc = -1;
       }
     }
-  } else {
-    const int v = (blockIdx.x - tet_blocks) * blockDim.x + threadIdx.x;
-    if (v < m.Vf) {
-      sc = m.v_scene[v];
-      if (!m.scenes[sc].done) {
-        T uv[3], dz[3], d[3];
-        load3(m.u, v, uv);
-        load3(m.dz, v, dz);
-        const double mh = double(m.mh2[v]);
+  } else if ((int)threadIdx.x < n) {
+    const int v = i0 + threadIdx.x;
+    sc = m.v_scene[v];
+    if (wants(sc)) {
+      T uv[3], dz[3], d[3];
+      load3(m.u, v, uv);
+      load3(m.dz, v, dz);
+      load3(dir, v, d);
+      const T mh = m.mh2[v];
+      T dd = T(0), de = T(0);
 #pragma unroll
-        for (int dir = 0; dir < ND; ++dir) {
-          load3(dir == 0 ? m.D : m.DJ, v, d);
-          double dd = 0.0, de = 0.0;
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            dd += double(d[q]) * double(d[q]);
-            de += double(d[q]) * (double(uv[q]) - double(dz[q]));
-          }
-          acc[dir * 6 + 0] = mh * de;
-          acc[dir * 6 + 1] = 0.5 * mh * dd;
-        }
-      } else {
-        sc = -1;
+      for (int q = 0; q < 3; ++q) {
+        dd += d[q] * d[q];
+        de += d[q] * (uv[q] - dz[q]);
       }
+      acc[0].add(mh * de);
+      acc[1].add(T(0.5) * mh * dd);
+    } else {
+      sc = -1;
     }
   }
-  scene_reduce<NC>(acc, sc, m.sacc, 3);
+  scene_reduce_acc<T, NC>(acc, sc, m.sacc, 3);
 }
 
 // Batch meshes, thread per scene: residual bookkeeping of the sweep (reading R9) from the
@@ -1329,6 +1433,7 @@ static __global__ void k_scene_finalize_main(SceneState* scenes, double* sacc, i
     S.slope = corr ? a[2] : a[1];
     S.alpha = 1.0;
     S.dir = 0;
+    S.need_j = 0;
     bool fin = false;
     if (!isfinite(r) || !isfinite(S.slope)) {
       S.status = 6;
@@ -1350,35 +1455,34 @@ static __global__ void k_scene_finalize_main(SceneState* scenes, double* sacc, i
   a[0] = a[1] = a[2] = 0.0;
 }
 
-// Batch meshes, thread per scene: Armijo choice from the per-scene polynomial sums.
-static __global__ void k_scene_finalize_energy(SceneState* scenes, double* sacc, int n, int nd) {
+// Batch meshes, thread per scene: Armijo choice along one direction from the per-scene
+// polynomial sums (DIR 0: D, recording need_j when every trial failed and D_J differs;
+// DIR 1: D_J for those scenes), then the sums are cleared for the next pass.
+template <int DIR>
+static __global__ void k_scene_finalize_energy(SceneState* scenes, double* sacc, int n, int has_j) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   SceneState& S = scenes[s];
   double* cf = sacc + (size_t)s * kSceneAcc + 3;
-  if (!S.done) {
+  if (!S.done && (DIR == 0 || S.need_j)) {
+    const double slope = DIR == 0 ? S.slope : S.slope_j;
     double alpha = 0.0;
-    int dir = 0;
     bool ok = false;
-    for (int dd = 0; dd < nd && !ok; ++dd) {
-      const double slope = dd == 0 ? S.slope : S.slope_j;
-      for (int j = 0; j < kLsTrials; ++j) {
-        const double a = 1.0 / double(1 << j);
-        const double* c = cf + 6 * dd;
-        const double dE = a * (c[0] + a * (c[1] + a * (c[2] + a * (c[3] + a * (c[4] + a * c[5])))));
-        if (dE <= 1e-4 * a * slope) {
-          alpha = a;
-          dir = dd;
-          ok = true;
-          break;
-        }
+    for (int j = 0; j < kLsTrials; ++j) {
+      const double a = 1.0 / double(1 << j);
+      const double dE = a * (cf[0] + a * (cf[1] + a * (cf[2] + a * (cf[3] + a * (cf[4] + a * cf[5])))));
+      if (dE <= 1e-4 * a * slope) {
+        alpha = a;
+        ok = true;
+        break;
       }
     }
-    if (!ok) S.ls_rejects += 1;
     S.alpha = alpha;
-    S.dir = dir;
+    S.dir = DIR;
+    if (DIR == 0) S.need_j = (!ok && has_j) ? 1 : 0;
+    if (!ok && (DIR == 1 || !has_j)) S.ls_rejects += 1;
   }
-  for (int j = 0; j < 12; ++j) cf[j] = 0.0;
+  for (int j = 0; j < 6; ++j) cf[j] = 0.0;
 }
 
 template <typename T>
