@@ -106,6 +106,15 @@ def sweep_bytes(V_f, T, n_cub, fp_bytes=4):
     return T * per_tet + V_f * per_vertex
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu --set full
+# capture of one launch, FP32, 2 voxel spheres: 694,272 tets, 126,826 free vertices; summary
+# and command in profiles/sweep_kernels_spheres2_fp32.md). It grows in proportion to the
+# tets, so a launch on another mesh is credited with traffic x T / 694,272. Only kernels whose
+# code has not changed since that capture are listed.
+NCU_TRAFFIC_TETS = 694272
+NCU_TRAFFIC = {"k_energy": 84.463104e6 + 2.722304e6, "k_elem": 79.797504e6 + 5.376768e6}
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -217,7 +226,8 @@ def timed_steps(mesh, x, v, opts, n, stream):
     for _ in range(n):
         r = mesh.step(x, v, opts, stream)
         reps.append((r.sweeps, r.converged, r.rel_residual, list(r.kernel_ms), list(r.kernel_launches),
-                     r.launches, r.fallback, r.ls_rejects))
+                     r.launches, r.fallback, r.ls_rejects, r.dj_steps, r.contact_rebuilds,
+                     r.contact_candidates, r.contact_near))
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1), reps
@@ -302,6 +312,11 @@ def run_jgs2(args, rank, world, local_rank):
                    "l2": "per-sweep working set larger than L2 (126 MB); no flush"},
         "sweeps_per_step": float(sweeps.mean()), "sweeps_per_s": float(sweeps.sum() / (ms_total * 1e-3)),
         "converged_steps": int(sum(q[1] for q in reps)), "max_rel_residual": float(max(q[2] for q in reps)),
+        "line_search_per_step": {"dj_steps": float(np.mean([q[8] for q in reps])),
+                                 "rejects": float(np.mean([q[7] for q in reps])),
+                                 "fallback_vertex_solves": float(np.mean([q[6] for q in reps]))},
+        "contact_rebuilds_per_step": float(np.mean([q[9] for q in reps])),
+        "contact_pairs_last_step": {"candidates": int(reps[-1][10]), "within_rc_last_sweep": int(reps[-1][11])},
         "precompute_s": round(t_pre, 2),
         "e2e": {"value": e2e_ms, "unit": "ms/step", "h2d_bytes_per_step": int(xh.nbytes + vh.nbytes),
                 "d2h_bytes_per_step": int(xh.nbytes + vh.nbytes)},
@@ -338,8 +353,13 @@ def run_jgs2(args, rank, world, local_rank):
     out["kernel_launches_per_step"] = {KIND[q]: int(kl[q] // args.steps) for q in range(len(KIND))}
     out["kernel_share"] = share
     out["kernels"] = per_kernel
+    traffic = NCU_TRAFFIC.get(dom)
+    if traffic is not None and prec == p.FP32 and not batch:
+        traffic = int(traffic * T / NCU_TRAFFIC_TETS)
+    else:
+        traffic = None
     out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-                       "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                       "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
                        "bytes_per_launch": per_kernel[dom]["bytes_per_launch"],
                        "avg_launch_ms": per_kernel[dom]["avg_launch_ms"],
                        "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}

@@ -121,6 +121,10 @@ typedef struct {
   int32_t converged;         /* 1 if rel_tol was reached */
   int32_t fallback;          /* vertex solves that fell back to the uncorrected step */
   int32_t ls_rejects;        /* sweeps where no line-search step satisfied Armijo */
+  int32_t dj_steps;          /* sweeps that stepped along the uncorrected direction D_J */
+  int32_t contact_rebuilds;  /* contact candidate-list rebuilds in the step (forced one included) */
+  int32_t contact_candidates; /* pairs in the candidate list at the end of the step */
+  int32_t contact_near;       /* candidate pairs within r_c at the step's last sweep */
   double rel_residual;       /* |g(x_{t+1})| / |g(x_t)| */
   double g0;                 /* |g(x^0)| */
   double ms;                 /* wall time of the step on the stream (CUDA events) */

@@ -157,7 +157,7 @@ __device__ __forceinline__ double segment_segment(P3 p0, P3 p1, P3 q0, P3 q1, do
 // sweep that needs no rebuild runs the rebuild kernels as empty launches.
 // ---------------------------------------------------------------------------------------
 enum { kCtlMove = 0, kCtlRebuild = 1, kCtlForce = 2, kCtlTicket = 3, kCtlExtF = 4, kCtlExtE = 5, kCtlAcc = 6,
-       kCtlCoord = 7, kCtlWords = 8 };
+       kCtlCoord = 7, kCtlNear = 8, kCtlWords = 9 };
 
 __device__ __forceinline__ uint64_t cell_key(P3 p, double h) {
   const long long ix = (long long)floor(p.x / h) + (1 << 20), iy = (long long)floor(p.y / h) + (1 << 20),
@@ -206,7 +206,7 @@ __device__ __forceinline__ void emit_pair(const ContactView& c, uint64_t kind, u
 // Largest surface-vertex displacement since the last rebuild; the last block decides the
 // rebuild (forced at the start of a step) and clears the counters of the next one.
 template <typename T>
-__global__ void __launch_bounds__(256) k_bp_check(DevMesh<T> m, ContactView c, const StepState* st) {
+__global__ void __launch_bounds__(256) k_bp_check(DevMesh<T> m, ContactView c, StepState* st) {
   if (st->done) {
     if (blockIdx.x == 0 && threadIdx.x == 0) c.ctl[kCtlRebuild] = 0u;
     return;
@@ -249,7 +249,9 @@ __global__ void __launch_bounds__(256) k_bp_check(DevMesh<T> m, ContactView c, c
   ctl[kCtlMove] = 0u;
   ctl[kCtlForce] = 0u;
   ctl[kCtlTicket] = 0u;
+  ctl[kCtlNear] = 0u;
   if (rebuild) {
+    st->rebuilds += 1;
     *c.n_pairs = 0;
     ctl[kCtlExtF] = 0u;
     ctl[kCtlExtE] = 0u;
@@ -379,15 +381,36 @@ static __global__ void __launch_bounds__(1024) k_bp_scan_apply(ContactView c) {
   }
 }
 
-// Rebuild 3: primitive ids in bucket order (faces, then edges offset by n_faces).
+// Rebuild 3: in bucket order (faces, then edges), each primitive's id, its FP32 centre on the
+// snapshot (face centroid, edge midpoint) and its cell key: the queries scan these three
+// contiguous arrays and reject most candidates on the centre alone.
 static __global__ void __launch_bounds__(256) k_bp_fill(ContactView c) {
   if (c.ctl[kCtlRebuild] == 0u) return;
   const int H = 1 << c.hbits;
   const int n = max(c.n_faces, c.n_edges);
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-    if (q < c.n_faces) c.hids[c.hcnt[bucket_of(c.fkeys[q], c.hbits)] + c.frank[q]] = q;
-    if (q < c.n_edges) c.hids[c.hcnt[H + bucket_of(c.ekeys[q], c.hbits)] + c.erank[q]] = q;
+    if (q < c.n_faces) {
+      const int pos = c.hcnt[bucket_of(c.fkeys[q], c.hbits)] + c.frank[q];
+      const float4 a = c.pbp[c.faces[3 * q]], b = c.pbp[c.faces[3 * q + 1]], d = c.pbp[c.faces[3 * q + 2]];
+      c.hids[pos] = q;
+      c.hrec[pos] = make_float4((a.x + b.x + d.x) / 3.f, (a.y + b.y + d.y) / 3.f, (a.z + b.z + d.z) / 3.f, 0.f);
+      c.hkey[pos] = c.fkeys[q];
+    }
+    if (q < c.n_edges) {
+      const int pos = c.hcnt[H + bucket_of(c.ekeys[q], c.hbits)] + c.erank[q];
+      const float4 a = c.pbp[c.edges[2 * q]], b = c.pbp[c.edges[2 * q + 1]];
+      c.hids[pos] = q;
+      c.hrec[pos] = make_float4(0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z), 0.f);
+      c.hkey[pos] = c.ekeys[q];
+    }
   }
+}
+
+// Centre prefilter on the FP32 snapshot: false only when the centres are provably farther
+// apart than r (r already holds the primitives' extents and the snapshot's rounding slack).
+__device__ __forceinline__ bool centres_near(float4 a, float4 b, float r) {
+  const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  return dx * dx + dy * dy + dz * dz <= r * r;
 }
 
 // AABB gap test on the FP32 snapshot: false only when the boxes are provably farther than R
@@ -412,6 +435,8 @@ __global__ void __launch_bounds__(128) k_query_vertices(DevMesh<T> m, ContactVie
   double hf, he;
   grid_cells(c, hf, he);
   const float rf = float((c.R + 2.0 * snap_slack(c)) * (1.0 + 1e-6));
+  // a face within R of a point has its centroid within R + (largest centroid-corner distance)
+  const float rs = float((c.R + double(__uint_as_float(c.ctl[kCtlExtF])) + 8.0 * snap_slack(c)) * (1.0 + 1e-5));
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < c.n_sverts; q += gridDim.x * blockDim.x) {
     const int v = c.sverts[q];
     const P3 p = vpos(m, v);
@@ -429,8 +454,8 @@ __global__ void __launch_bounds__(128) k_query_vertices(DevMesh<T> m, ContactVie
           const uint32_t b = bucket_of(key, c.hbits);
           const int j1 = c.hcnt[b + 1];
           for (int j = c.hcnt[b]; j < j1; ++j) {
+            if (!centres_near(c.hrec[j], pf, rs) || c.hkey[j] != key) continue;
             const int f = c.hids[j];
-            if (c.fkeys[f] != key) continue;
             const int a = c.faces[3 * f], bb = c.faces[3 * f + 1], cc = c.faces[3 * f + 2];
             if (a == v || bb == v || cc == v) continue;
             const float4 fa = c.pbp[a], fb = c.pbp[bb], fc = c.pbp[cc];
@@ -443,40 +468,48 @@ __global__ void __launch_bounds__(128) k_query_vertices(DevMesh<T> m, ContactVie
   }
 }
 
-// Rebuild 5: edge pairs j > i sharing no vertex, exact FP64 distance below R.
+// Rebuild 5: edge pairs sharing no vertex (each unordered pair once), exact FP64 distance
+// below R.
 template <typename T>
 __global__ void __launch_bounds__(128) k_query_edges(DevMesh<T> m, ContactView c) {
   if (c.ctl[kCtlRebuild] == 0u) return;
   double hf, he;
   grid_cells(c, hf, he);
   const float rf = float((c.R + 2.0 * snap_slack(c)) * (1.0 + 1e-6));
+  // two edges within R have midpoints within R + 2 (largest half length)
+  const float rs =
+      float((c.R + 2.0 * double(__uint_as_float(c.ctl[kCtlExtE])) + 8.0 * snap_slack(c)) * (1.0 + 1e-5));
   const int H = 1 << c.hbits;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.n_edges; i += gridDim.x * blockDim.x) {
     const int a0 = c.edges[2 * i], a1 = c.edges[2 * i + 1];
     const P3 p0 = vpos(m, a0), p1 = vpos(m, a1);
     const float4 f0 = c.pbp[a0], f1 = c.pbp[a1];
     const float4 lo = fmin4(f0, f1), hi = fmax4(f0, f1);
+    const float4 mf = make_float4(0.5f * (f0.x + f1.x), 0.5f * (f0.y + f1.y), 0.5f * (f0.z + f1.z), 0.f);
     const P3 mid = mul(add(p0, p1), 0.5);
     const long long cx = (long long)floor(mid.x / he), cy = (long long)floor(mid.y / he),
                     cz = (long long)floor(mid.z / he);
-    for (int dx = -1; dx <= 1; ++dx)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dz = -1; dz <= 1; ++dz) {
-          const uint64_t key = cell_key_of(cx + dx, cy + dy, cz + dz);
-          const uint32_t b = H + bucket_of(key, c.hbits);
-          const int j1 = c.hcnt[b + 1];
-          for (int j = c.hcnt[b]; j < j1; ++j) {
-            const int e = c.hids[j];
-            if (e <= i || c.ekeys[e] != key) continue;
-            const int b0 = c.edges[2 * e], b1 = c.edges[2 * e + 1];
-            if (b0 == a0 || b0 == a1 || b1 == a0 || b1 == a1) continue;
-            const float4 g0 = c.pbp[b0], g1 = c.pbp[b1];
-            if (!boxes_near(lo, hi, fmin4(g0, g1), fmax4(g0, g1), rf)) continue;
-            double s, t;
-            const double d = segment_segment(p0, p1, vpos(m, b0), vpos(m, b1), s, t);
-            if (d < c.R) emit_pair(c, 2, i, e, d);
-          }
-        }
+    // half stencil: the own cell (partners e > i) and the 13 cells after it in (dx, dy, dz)
+    // order (every partner); each unordered pair of cells is visited from one side only
+    for (int cell = 13; cell < 27; ++cell) {
+      const int dx = cell / 9 - 1, dy = (cell / 3) % 3 - 1, dz = cell % 3 - 1;
+      const bool own = cell == 13;
+      const uint64_t key = cell_key_of(cx + dx, cy + dy, cz + dz);
+      const uint32_t b = H + bucket_of(key, c.hbits);
+      const int j1 = c.hcnt[b + 1];
+      for (int j = c.hcnt[b]; j < j1; ++j) {
+        if (!centres_near(c.hrec[j], mf, rs) || c.hkey[j] != key) continue;
+        const int e = c.hids[j];
+        if (own && e <= i) continue;
+        const int b0 = c.edges[2 * e], b1 = c.edges[2 * e + 1];
+        if (b0 == a0 || b0 == a1 || b1 == a0 || b1 == a1) continue;
+        const float4 g0 = c.pbp[b0], g1 = c.pbp[b1];
+        if (!boxes_near(lo, hi, fmin4(g0, g1), fmax4(g0, g1), rf)) continue;
+        double s, t;
+        const double d = segment_segment(p0, p1, vpos(m, b0), vpos(m, b1), s, t);
+        if (d < c.R) emit_pair(c, 2, i, e, d);
+      }
+    }
   }
 }
 
@@ -554,16 +587,57 @@ __device__ __forceinline__ double pair_geom(const DevMesh<T>& m, const ContactVi
   return d;
 }
 
+// Displacement of surface vertex v since the last rebuild (current position minus the FP32
+// snapshot; the snapshot's rounding is covered by snap_slack).
+template <typename T>
+__device__ __forceinline__ float3 snap_disp(const DevMesh<T>& m, const ContactView& c, int v) {
+  const P3 p = vpos(m, v);
+  const float4 s = c.pbp[v];
+  return make_float3(float(p.x - double(s.x)), float(p.y - double(s.y)), float(p.z - double(s.z)));
+}
+__device__ __forceinline__ float dist3(float3 a, float3 b) {
+  const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  return sqrtf(dx * dx + dy * dy + dz * dz);
+}
+
+// Bound on how much a pair's distance changed since the last rebuild, from its vertices'
+// motion relative to one of them: a common translation leaves every distance unchanged,
+// and the point-plane, point-triangle and segment-segment distances are 1-Lipschitz in the
+// relative motion (closest points on a triangle or segment are convex combinations of its
+// corners). Walls do not move, so a vertex-wall pair takes the vertex's own motion.
+template <typename T>
+__device__ __forceinline__ float pair_rel_motion(const DevMesh<T>& m, const ContactView& c, uint64_t key) {
+  const int kind = (int)(key >> 60), ia = (int)((key >> 30) & 0x3fffffff), ib = (int)(key & 0x3fffffff);
+  if (kind == 0) {
+    const float3 d = snap_disp(m, c, ia);
+    return sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+  }
+  if (kind == 1) {
+    const float3 r = snap_disp(m, c, ia);
+    return fmaxf(dist3(snap_disp(m, c, c.faces[3 * ib]), r),
+                 fmaxf(dist3(snap_disp(m, c, c.faces[3 * ib + 1]), r), dist3(snap_disp(m, c, c.faces[3 * ib + 2]), r)));
+  }
+  const float3 r = snap_disp(m, c, c.edges[2 * ia]);
+  return dist3(snap_disp(m, c, c.edges[2 * ia + 1]), r) +
+         fmaxf(dist3(snap_disp(m, c, c.edges[2 * ib]), r), dist3(snap_disp(m, c, c.edges[2 * ib + 1]), r));
+}
+
 // Per candidate pair: its distance at x^k. Pairs within r_c count: smallest distance per
 // vertex, and for active pairs (d < dhat) kappa B'(d) dd/dx and kappa B''(d) (dd/dx)(dd/dx)^T
-// into the FP64 accumulators. A pair whose rebuild distance exceeds r_c by more than twice
-// the largest displacement since the rebuild cannot be within r_c and is skipped (d0 = inf).
+// into the FP64 accumulators. A pair whose rebuild distance exceeds r_c by more than its
+// distance can have changed since the rebuild (twice the largest displacement, or its own
+// vertices' relative motion) cannot be within r_c and is skipped (d0 = inf).
 template <typename T>
 __global__ void __launch_bounds__(256) k_pair_terms(DevMesh<T> m, ContactView c, StepState* st) {
+  if (st->done) return;
   const int n = min(*c.n_pairs, c.cap);
   const double far = c.rc + 2.0 * (double(__uint_as_float(c.ctl[kCtlAcc])) + snap_slack(c));
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-    if (double(c.dbp[q]) >= far) {
+    const double dbp = double(c.dbp[q]);
+    // beyond r_c by more than any motion since the rebuild could close: global bound
+    // first (one load), then the pair's own motion relative to one of its vertices
+    if (dbp >= far ||
+        dbp - double(pair_rel_motion(m, c, c.pairs[q])) * (1.0 + 1e-5) - 4.0 * snap_slack(c) >= c.rc) {
       c.d0[q] = INFINITY;
       continue;
     }
@@ -578,6 +652,7 @@ __global__ void __launch_bounds__(256) k_pair_terms(DevMesh<T> m, ContactView c,
       continue;
     }
     if (d >= c.rc) continue;
+    atomicAdd(&c.ctl[kCtlNear], 1u);  // pairs within r_c at this sweep (diagnostic)
     // positive doubles order like their bit patterns
     for (int k = 0; k < nv; ++k)
       atomicMin(reinterpret_cast<unsigned long long*>(c.dmin + vs[k]), (unsigned long long)__double_as_longlong(d));

@@ -75,7 +75,7 @@ Mesh::~Mesh() {
   cudaFree(d_planes); cudaFree(d_d0); cudaFree(d_bg); cudaFree(d_bH); cudaFree(d_faces); cudaFree(d_edges);
   cudaFree(d_sverts); cudaFree(d_npairs); cudaFree(d_cflags); cudaFree(d_is_surf); cudaFree(d_pairs);
   cudaFree(d_dmin); cudaFree(d_lim); cudaFree(d_frank); cudaFree(d_erank); cudaFree(d_hcnt); cudaFree(d_hblk);
-  cudaFree(d_hids); cudaFree(d_fkeys); cudaFree(d_ekeys); cudaFree(d_pbp); cudaFree(d_dbp); cudaFree(d_ctl);
+  cudaFree(d_hids); cudaFree(d_hrec); cudaFree(d_hkey); cudaFree(d_fkeys); cudaFree(d_ekeys); cudaFree(d_pbp); cudaFree(d_dbp); cudaFree(d_ctl);
 }
 
 static uint64_t spread3(uint64_t x) {
@@ -202,6 +202,11 @@ jgs2_status mesh_create(const jgs2_mesh_desc* d, Mesh** out, const std::vector<i
     int mx = 0;
     for (int l = 0; l < kSlice && s * kSlice + l < m->Vf; ++l) mx = std::max(mx, cnt[s * kSlice + l]);
     m->inc_off[s + 1] = m->inc_off[s] + mx * kSlice;
+  }
+  for (int q = 0; q < 3; ++q) {
+    const int spb = (64 << q) / kSlice;  // slices per block of 64, 128, 256 vertices
+    for (int s0 = 0; s0 < ns; s0 += spb)
+      m->inc_blk[q] = std::max(m->inc_blk[q], m->inc_off[std::min(s0 + spb, ns)] - m->inc_off[s0]);
   }
   m->inc.assign(m->inc_off[ns], 0);
   m->inc_len.assign(m->Vf, 0);
@@ -342,10 +347,10 @@ static jgs2_status ensure_device(Mesh* m) {
     CK(dalloc(&m->d_perm, V));
     CK(dalloc(&m->d_state, 1));
     CK(dalloc(&m->d_trace, JGS2_TRACE_MAX));
-    // sweep partials: [3][vertex blocks] (gather/correct), [6][energy blocks] plus
-    // [kLsTrials][kPairTrialBlocks] (line search); batch and adjoint passes use fewer
+    // sweep partials: [3][vertex blocks] (gather/correct), [12][energy blocks] plus
+    // [2 kLsTrials][kPairTrialBlocks] (line search); batch and adjoint passes use fewer
     const size_t np = std::max<size_t>(4 * kLsTrials * ((size_t)(T + 127) / 128 + (m->Vf + 127) / 128 + 1),
-                                       (size_t)6 * kEnergyBlocksMax + (size_t)kLsTrials * kPairTrialBlocks + 16);
+                                       (size_t)12 * kEnergyBlocksMax + (size_t)2 * kLsTrials * kPairTrialBlocks + 16);
     CK(dalloc(&m->d_partial, np));
     CK(cudaMallocHost((void**)&m->h_state, sizeof(StepState)));
     CK(cudaMemcpy(m->d_inc_off, m->inc_off.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
@@ -373,6 +378,8 @@ static jgs2_status ensure_device(Mesh* m) {
       CK(dalloc(&m->d_hcnt, H2 + 1));
       CK(dalloc(&m->d_hblk, (H2 + 1 + 4095) / 4096));
       CK(dalloc(&m->d_hids, std::max(1, nF + nE)));
+      CK(dalloc(&m->d_hrec, std::max(1, nF + nE)));
+      CK(dalloc(&m->d_hkey, std::max(1, nF + nE)));
       CK(dalloc(&m->d_pbp, V));
       CK(dalloc(&m->d_ctl, kCtlWords));
       CK(dalloc(&m->d_dbp, m->pair_cap));
@@ -439,10 +446,13 @@ static void tet_records(const Mesh* m, std::vector<TetRec<T>>& rec) {
   }
 }
 
+static cudaError_t prepare_gather(const Mesh* m);
+
 template <typename T>
 static jgs2_status ensure_prec(Mesh* m) {
   jgs2_status ds = ensure_device(m);
   if (ds != JGS2_OK) return ds;
+  CK(prepare_gather(m));
   PrecBufs<T>& b = bufs<T>(m);
   if (!b.ready) {
     const int V = m->V, T_ = m->T;
@@ -559,6 +569,8 @@ static DevMesh<T> dev_view(Mesh* m) {
     c.hcnt = m->d_hcnt;
     c.hblk = m->d_hblk;
     c.hids = m->d_hids;
+    c.hrec = m->d_hrec;
+    c.hkey = m->d_hkey;
     c.pbp = m->d_pbp;
     c.ctl = m->d_ctl;
     c.dbp = m->d_dbp;
@@ -683,16 +695,61 @@ static jgs2_status contact_force_rebuild(Mesh* m, cudaStream_t s) {
   return JGS2_OK;
 }
 
+// Dynamic shared memory of k_gather at bs threads: the block's incidence entries.
+static size_t gather_smem(const Mesh* m, int bs) {
+  const int q = bs == 64 ? 0 : (bs == 256 ? 2 : 1);
+  return (size_t)std::max(m->inc_blk[q], 4) * sizeof(int);
+}
+
+// Raises the dynamic shared memory limit of every k_gather variant to what this mesh needs
+// (once per new maximum; before any launch or graph capture of the mesh).
+static cudaError_t prepare_gather(const Mesh* m) {
+  static size_t have = 48 * 1024;
+  const size_t need = gather_smem(m, 256) > gather_smem(m, 128) ? gather_smem(m, 256) : gather_smem(m, 128);
+  if (need <= have) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  auto set = [&](auto kern) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+  };
+  set(k_gather<float, true, false, 64>);
+  set(k_gather<float, true, false, 128>);
+  set(k_gather<float, true, false, 256>);
+  set(k_gather<float, false, false, 64>);
+  set(k_gather<float, false, false, 128>);
+  set(k_gather<float, false, false, 256>);
+  set(k_gather<float, true, true, 64>);
+  set(k_gather<float, true, true, 128>);
+  set(k_gather<float, true, true, 256>);
+  set(k_gather<float, false, true, 64>);
+  set(k_gather<float, false, true, 128>);
+  set(k_gather<float, false, true, 256>);
+  set(k_gather<double, true, false, 64>);
+  set(k_gather<double, true, false, 128>);
+  set(k_gather<double, true, false, 256>);
+  set(k_gather<double, false, false, 64>);
+  set(k_gather<double, false, false, 128>);
+  set(k_gather<double, false, false, 256>);
+  set(k_gather<double, true, true, 64>);
+  set(k_gather<double, true, true, 128>);
+  set(k_gather<double, true, true, 256>);
+  set(k_gather<double, false, true, 64>);
+  set(k_gather<double, false, true, 128>);
+  set(k_gather<double, false, true, 256>);
+  if (e == cudaSuccess) have = need;
+  return e;
+}
+
 // k_gather / k_correct with a runtime block size (64, 128 or 256 threads)
 template <typename T, bool BATCH>
-static void launch_gather(DevMesh<T>& d, bool corr, int bs, cudaStream_t s, StepState* st, double* partial,
-                          double* trace, int rec) {
+static void launch_gather(DevMesh<T>& d, const Mesh* m, bool corr, int bs, cudaStream_t s, StepState* st,
+                          double* partial, double* trace, int rec) {
   const int Vf = d.Vf;
+  const size_t sm = gather_smem(m, bs);
 #define JGS2_G(B)                                                                                  \
   if (corr)                                                                                        \
-    k_gather<T, true, BATCH, B><<<(Vf + B - 1) / B, B, 0, s>>>(d, st, partial, trace, rec);        \
+    k_gather<T, true, BATCH, B><<<(Vf + B - 1) / B, B, sm, s>>>(d, st, partial, trace, rec);       \
   else                                                                                             \
-    k_gather<T, false, BATCH, B><<<(Vf + B - 1) / B, B, 0, s>>>(d, st, partial, trace, rec);
+    k_gather<T, false, BATCH, B><<<(Vf + B - 1) / B, B, sm, s>>>(d, st, partial, trace, rec);
   if (bs == 64) {
     JGS2_G(64)
   } else if (bs == 256) {
@@ -775,8 +832,12 @@ static int energy_blocks() {
     int dev = 0, sms = 148, per_sm = 8;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_energy<T, 0>, 128, 0) != cudaSuccess || per_sm < 1)
-      per_sm = 1;
+    // the variant with the most registers (both directions) sets the wave
+    int per_sm2 = 8;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_energy<T, 0>, 128, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_energy<T, 2>, 128, 0) != cudaSuccess)
+      per_sm = per_sm2 = 1;
+    per_sm = std::max(1, std::min(per_sm, per_sm2));
     nb = std::max(1, std::min(sms * per_sm, kEnergyBlocksMax));
   }
   return nb;
@@ -883,7 +944,7 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
       if (m->contact) join(m->gfork[1]);
       if (nbV > 0)
         group(JGS2_K_GATHER, 1, s,
-              [&] { launch_gather<T, false>(d, corr, bs, s, m->d_state, m->d_partial, m->d_trace, o.record_trace); });
+              [&] { launch_gather<T, false>(d, m, corr, bs, s, m->d_state, m->d_partial, m->d_trace, o.record_trace); });
       // cubature pool after the gather, whose g and R at the pool elements' corners it reads
       if (pool)
         group(JGS2_K_POOL, 1, s, [&] {
@@ -901,13 +962,18 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
         // along D; along D_J only when every trial along D failed (those launches return
         // at once otherwise)
         const int npp = m->contact ? kPairTrialBlocks : 0;
-        double* pp = m->d_partial + (size_t)6 * nbE;
-        group(JGS2_K_ENERGY, (corr ? 2 : 1) * (m->contact ? 2 : 1), s, [&] {
+        double* pp = m->d_partial + (size_t)12 * nbE;
+        group(JGS2_K_ENERGY, (corr ? 3 : 1) * (m->contact ? 3 : 2), s, [&] {
           if (m->contact) k_pair_trials<T, 0><<<npp, 128, 0, s>>>(d, m->d_state, pp);
-          k_energy<T, 0><<<nbE, 128, 0, s>>>(d, m->d_state, corr ? 1 : 0, m->d_partial, pp, npp);
+          k_energy<T, 0><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
+          k_ls_decide<0><<<1, 256, 0, s>>>(m->d_state, corr ? 1 : 0, m->d_partial, nbE, pp, npp);
           if (corr) {
             if (m->contact) k_pair_trials<T, 1><<<npp, 128, 0, s>>>(d, m->d_state, pp);
-            k_energy<T, 1><<<nbE, 128, 0, s>>>(d, m->d_state, 1, m->d_partial, pp, npp);
+            k_energy<T, 1><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
+            k_ls_decide<1><<<1, 256, 0, s>>>(m->d_state, 1, m->d_partial, nbE, pp, npp);
+            if (m->contact) k_pair_trials<T, 2><<<npp, 128, 0, s>>>(d, m->d_state, pp);
+            k_energy<T, 2><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
+            k_ls_decide<2><<<1, 256, 0, s>>>(m->d_state, 1, m->d_partial, nbE, pp, npp);
           }
         });
       }
@@ -1019,7 +1085,7 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     for (int q = 0; q < chunk; ++q) {
       group(JGS2_K_ELEM, 1, s, [&] { k_elem<T, true><<<nbT, 128, 0, s>>>(d, m->d_state); });
-      group(JGS2_K_GATHER, 1, s, [&] { launch_gather<T, true>(d, corr, bs, s, m->d_state, m->d_partial, m->d_trace, 0); });
+      group(JGS2_K_GATHER, 1, s, [&] { launch_gather<T, true>(d, m, corr, bs, s, m->d_state, m->d_partial, m->d_trace, 0); });
       // the cubature pool after the gather, whose g and R at the corners it reads
       if (corr) {
         group(JGS2_K_POOL, 1, s, [&] { k_pool<T, true><<<(m->nP + kPoolWarps - 1) / kPoolWarps, 32 * kPoolWarps, 0, s>>>(d, m->d_state); });
@@ -1033,12 +1099,14 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
       });
       if (o.line_search) {
         // along D; along D_J only for the scenes whose trials along D all failed
-        group(JGS2_K_ENERGY, corr ? 4 : 2, s, [&] {
+        group(JGS2_K_ENERGY, corr ? 6 : 2, s, [&] {
           k_energy_batch<T, 0><<<nbT + nbV, 128, 0, s>>>(d, nbT);
           k_scene_finalize_energy<0><<<nbS, 128, 0, s>>>(m->d_scenes, m->d_sacc, S, corr ? 1 : 0);
           if (corr) {
             k_energy_batch<T, 1><<<nbT + nbV, 128, 0, s>>>(d, nbT);
             k_scene_finalize_energy<1><<<nbS, 128, 0, s>>>(m->d_scenes, m->d_sacc, S, 1);
+            k_energy_batch<T, 2><<<nbT + nbV, 128, 0, s>>>(d, nbT);
+            k_scene_finalize_energy<2><<<nbS, 128, 0, s>>>(m->d_scenes, m->d_sacc, S, 1);
           }
         });
       }
@@ -1156,6 +1224,18 @@ static jgs2_status step_impl(Mesh* m, double* x, double* v, const jgs2_step_opts
     rep->converged = hs->converged;
     rep->fallback = hs->fallback;
     rep->ls_rejects = hs->ls_rejects;
+    rep->dj_steps = hs->dj_steps;
+    rep->contact_rebuilds = hs->rebuilds;
+    rep->contact_candidates = 0;
+    rep->contact_near = 0;
+    if (m->contact) {
+      uint32_t near = 0;
+      int32_t cand = 0;
+      CK(cudaMemcpy(&cand, m->d_npairs, sizeof(cand), cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(&near, m->d_ctl + kCtlNear, sizeof(near), cudaMemcpyDeviceToHost));
+      rep->contact_candidates = cand;
+      rep->contact_near = (int32_t)near;
+    }
     rep->rel_residual = hs->r;
     rep->g0 = hs->g0;
     rep->ms = ms;
@@ -1401,7 +1481,7 @@ static jgs2_status autotune_impl(Mesh* m, double* x, double* v, const jgs2_step_
   CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
   k_elem<T, false><<<(m->T + 127) / 128, 128, 0, s>>>(d, m->d_state);
   if (corr) {
-    launch_gather<T, false>(d, corr, 128, s, m->d_state, m->d_partial, m->d_trace, 0);
+    launch_gather<T, false>(d, m, corr, 128, s, m->d_state, m->d_partial, m->d_trace, 0);
     k_pool<T, true><<<(m->nP + kPoolWarps - 1) / kPoolWarps, 32 * kPoolWarps, 0, s>>>(d, m->d_state);
   }
   const int cands[3] = {64, 128, 256};
@@ -1414,12 +1494,12 @@ static jgs2_status autotune_impl(Mesh* m, double* x, double* v, const jgs2_step_
   // step (rel_tol < 0, no sweep cap), so each launch does the full work
   for (int c : cands) {
     for (int rep = 0; rep < 2; ++rep) {
-      launch_gather<T, false>(d, corr, c, s, m->d_state, m->d_partial, m->d_trace, 0);
+      launch_gather<T, false>(d, m, corr, c, s, m->d_state, m->d_partial, m->d_trace, 0);
       if (corr) launch_correct<T, false>(d, c, s, m->d_state, m->d_partial, m->d_trace, 0);
     }
     CK(cudaEventRecord(e0, s));
     for (int rep = 0; rep < 5; ++rep) {
-      launch_gather<T, false>(d, corr, c, s, m->d_state, m->d_partial, m->d_trace, 0);
+      launch_gather<T, false>(d, m, corr, c, s, m->d_state, m->d_partial, m->d_trace, 0);
       if (corr) launch_correct<T, false>(d, c, s, m->d_state, m->d_partial, m->d_trace, 0);
     }
     CK(cudaEventRecord(e1, s));
@@ -1511,7 +1591,7 @@ static jgs2_status adjoint_impl(Mesh* m, const double* xt, const double* vt, con
   CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
   // H_ii, R_i at x* (and the rotated cubature element Hessians)
   k_elem<T, false><<<nbT, 128, 0, s>>>(d, m->d_state);
-  k_gather<T, true, false, 128><<<nbV, 128, 0, s>>>(d, m->d_state, m->d_partial, m->d_trace, 0);
+  launch_gather<T, false>(d, m, true, 128, s, m->d_state, m->d_partial, m->d_trace, 0);
   if (corr) k_pool<T, true><<<(m->nP + kPoolWarps - 1) / kPoolWarps, 32 * kPoolWarps, 0, s>>>(d, m->d_state);
   if (corr)
     k_lin_setup<T, true><<<nbV, 128, 0, s>>>(d, b.a_lin);

@@ -48,6 +48,7 @@ struct Mesh {
   std::vector<int> perm, iperm;    // internal <-> caller vertex
   std::vector<int> tperm, tiperm;  // internal <-> caller tet
   std::vector<int> inc_off, inc_len, inc;
+  int inc_blk[3] = {0, 0, 0};     // largest incidence range of a 64/128/256-vertex block (entries)
   // cubature records, internal order: [Vf][n_cub]
   int n_cub = 0, nP = 0, cub_version = 0, pool_version = -1;
   bool device_ready = false;
@@ -102,6 +103,8 @@ struct Mesh {
   double *d_planes = nullptr, *d_d0 = nullptr, *d_bg = nullptr, *d_bH = nullptr;
   int32_t *d_faces = nullptr, *d_edges = nullptr, *d_sverts = nullptr, *d_npairs = nullptr, *d_cflags = nullptr;
   int32_t *d_frank = nullptr, *d_erank = nullptr, *d_hcnt = nullptr, *d_hblk = nullptr, *d_hids = nullptr;
+  float4* d_hrec = nullptr;
+  uint64_t* d_hkey = nullptr;
   uint8_t* d_is_surf = nullptr;
   uint64_t *d_fkeys = nullptr, *d_ekeys = nullptr, *d_pairs = nullptr;
   float4* d_pbp = nullptr;

@@ -27,7 +27,7 @@ namespace jgs2 {
 constexpr int kSlice = 32;       // vertices per incidence slice (one warp)
 constexpr int kMaxCub = 8;       // cubature slots per vertex at most
 constexpr int kLsTrials = 8;     // line-search steps alpha = 2^-j, j < kLsTrials
-constexpr int kPairTrialBlocks = 148 * 4;  // blocks of the line-search barrier-trial pass
+constexpr int kPairTrialBlocks = 148 * 4;  // blocks of the line-search barrier-trial pass (2 x kLsTrials sums each)
 constexpr int kEnergyBlocksMax = 148 * 8;  // blocks of the line-search energy pass, at most
 constexpr int kPackedH = 78;     // 12x12 symmetric, upper triangle row-major
 // Row stride of the per-slot cubature record arrays: Vf rounded up to 4 entries, so that
@@ -74,6 +74,10 @@ struct StepState {
   double alpha;        // accepted step of the current sweep
   int32_t dir;         // 0: step along D, 1: along D_J
   int32_t need_j;      // every line-search trial along D failed: try D_J
+  int32_t dj_steps;    // sweeps that stepped along D_J
+  int32_t rebuilds;    // contact candidate-list rebuilds
+  int32_t prev_dir;    // direction the last accepted line-search step took (0: D, 1: D_J)
+  int32_t ls_mode;     // this sweep's line-search pass: prev_dir as the sweep began
   uint32_t ticket_main;
   uint32_t ticket_energy;
 };
@@ -99,6 +103,8 @@ struct ContactView {
   int32_t* hcnt = nullptr;       // [2H + 1] bucket counts, then exclusive starts
   int32_t* hblk = nullptr;       // [scan blocks] block sums
   int32_t* hids = nullptr;       // [n_faces + n_edges] primitive ids in bucket order
+  float4* hrec = nullptr;        // [n_faces + n_edges] bucket order: FP32 centre (centroid / midpoint), pad
+  uint64_t* hkey = nullptr;      // [n_faces + n_edges] bucket order: cell key
   float4* pbp = nullptr;         // [V] surface vertex positions at the last rebuild (FP32)
   uint32_t* ctl = nullptr;       // control words (displacement, rebuild flags, extents)
   // pairs
@@ -118,7 +124,10 @@ struct ContactView {
 // Per-scene state of a batch mesh (one slot per scene; a single mesh is not batched).
 struct SceneState {
   int32_t done, converged, status, sweeps, k, fallback, ls_rejects, dir;
-  int32_t need_j, pad;  // need_j: every line-search trial along D failed, try D_J
+  int32_t need_j;    // every line-search trial along D failed: try D_J
+  int32_t prev_dir;  // direction the scene's last accepted line-search step took (0: D, 1: D_J)
+  int32_t ls_mode;   // this sweep's line-search pass: prev_dir as the sweep began
+  int32_t pad;
   double g0, r, slope, slope_j, alpha;
 };
 constexpr int kSceneAcc = 16;  // per-scene FP64 sums: |g|^2, g.D_J, g.D, 6 line-search coefficients

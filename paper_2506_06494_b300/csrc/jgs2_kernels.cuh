@@ -364,17 +364,17 @@ __device__ __forceinline__ void gather_vertex_rec(const DevMesh<T>& m, int v, T 
 }
 
 // Gather of vertex v over its incident tets (Sec. 3 energy; Sec. 4.3 vertex rotation),
-// from the element pass's F_e (FRec, three 16-byte loads) and the corner vector b_c (one):
+// from the element pass's F_e (FRec, three 16-byte loads) and the corner vector b_c (one);
+// incv points at the vertex's first incidence entry (entry j at incv[32 j], in the block's
+// shared-memory copy of its slices):
 //   g  += V_e P(F_e) b_c                      (elastic gradient, P = mu F + s cof F)
 //   H  += V_e (mu |b_c|^2 I + lam' G G^T)     (diagonal 3x3 block; G = cof(F) b_c. The
 //         det-Hessian term of dP/dF contributes nothing to a diagonal block because
 //         eps_jln b_j b_l = 0, so this block is exact and positive definite.)
 //   Fs += V_e F_e,  W += V_e
 template <typename T>
-__device__ __forceinline__ void gather_vertex(const DevMesh<T>& m, int v, T (&g)[3], T (&H)[6],
-                                              T (&Fs)[9], T& W) {
-  const int slice = v / kSlice, lane = v % kSlice;
-  const int base = m.inc_off[slice] + lane;
+__device__ __forceinline__ void gather_vertex(const DevMesh<T>& m, int v, const int* __restrict__ incv, T (&g)[3],
+                                              T (&H)[6], T (&Fs)[9], T& W) {
   const int n = m.inc_len[v];
 #pragma unroll
   for (int q = 0; q < 3; ++q) g[q] = T(0);
@@ -383,10 +383,10 @@ __device__ __forceinline__ void gather_vertex(const DevMesh<T>& m, int v, T (&g)
 #pragma unroll
   for (int q = 0; q < 9; ++q) Fs[q] = T(0);
   W = T(0);
-  // two incidences per trip: their loads are in flight together
+  // four incidences per trip: their record loads are in flight together
 #pragma unroll 4
   for (int j = 0; j < n; ++j) {
-    const int ent = __ldg(m.inc + base + j * kSlice);
+    const int ent = incv[j * kSlice];
     const int t = ent >> 2, c = ent & 3;
     const FRec<T> r = m.frec[t];
     const Vec4<T> bq = m.bc[4 * (size_t)t + c];
@@ -948,6 +948,7 @@ __device__ __forceinline__ void finalize_sweep(StepState* st, double r2, double 
   st->alpha = 1.0;
   st->dir = 0;
   st->need_j = 0;
+  st->ls_mode = st->prev_dir;
   if (record && k < 4096) trace[k] = r;
   if (!isfinite(r) || !isfinite(gd) || !isfinite(gdj)) {
     st->status = 6;  // JGS2_EDIVERGED
@@ -965,8 +966,9 @@ __device__ __forceinline__ void finalize_sweep(StepState* st, double r2, double 
   }
 }
 
-// Sweep phase 1, thread per free vertex: gather g_i and H_ii (+ inertia) over the incident
-// tets (Eq. reduced_local terms), the uncorrected direction D_J = -H_ii^{-1} g_i, and, with
+// Sweep phase 1, thread per free vertex (dynamic shared memory: the block's incidence
+// entries, inc_block_bytes of the launch's block size): gather g_i and H_ii (+ inertia)
+// over the incident tets (Eq. reduced_local terms), the uncorrected direction D_J = -H_ii^{-1} g_i, and, with
 // the correction on, R_i = polar(F_i) (Eq. tilde_phi). Writes g, H, R as [18][Vf] for
 // phase 2 and the FP64 partial sums |g|^2 and g.D_J. Without the correction D = D_J and
 // this kernel closes the sweep's reduction.
@@ -977,13 +979,26 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
   if (!BATCH && st->done) return;
   __shared__ double red[96];
   __shared__ Acc<T> sred[64];
+  // the block's incidence slices form one contiguous, 128-byte aligned range of entries;
+  // copy it into shared memory first (coalesced 16-byte loads), so that each incidence's
+  // record loads do not wait on a global load of its entry
+  extern __shared__ __align__(16) int s_inc[];
+  const int s0 = blockIdx.x * (BS / kSlice), s1 = min(s0 + BS / kSlice, m.n_slices);
+  const int e0 = m.inc_off[s0];
+  {
+    const int4* src = reinterpret_cast<const int4*>(m.inc + e0);
+    int4* dst = reinterpret_cast<int4*>(s_inc);
+    const int n4 = (m.inc_off[s1] - e0) / 4;
+    for (int q = threadIdx.x; q < n4; q += BS) dst[q] = __ldg(src + q);
+  }
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   Acc<T> acc[2];  // |g|^2, g.D_J
   const int sc = (BATCH && i < m.Vf) ? m.v_scene[i] : -1;
   const bool active = i < m.Vf && (!BATCH || !m.scenes[sc].done);
   if (active) {
     T g[3], H[6], Fs[9], W;
-    gather_vertex(m, i, g, H, Fs, W);
+    gather_vertex(m, i, s_inc + (m.inc_off[i / kSlice] - e0) + i % kSlice, g, H, Fs, W);
     T ui[3], dz[3];
     load3(m.u, i, ui);
     load3(m.dz, i, dz);
@@ -1180,19 +1195,32 @@ __device__ __forceinline__ void tet_dpsi_poly(const TetRec<T>& r, const T (&F)[9
   c[5] = r.vol * (T(0.5) * lp * Cc * Cc);
 }
 
-// Line search (reading R17), IPC barrier part: the barrier change of the candidate pairs
-// for each trial step a = 2^-j along the direction (not polynomial in a), FP64 sums per
-// block into pp[j][blockIdx]. DIR as in k_energy, which adds these sums.
+// Which line-search pass runs in a sweep (reading R17), by the mode latched when the sweep
+// began: DIR 0 along D, when the last accepted step was along D; DIR 1 along D_J, after
+// every trial of a DIR 0 pass failed; DIR 2 both directions in one pass, when the last
+// accepted step was along D_J (its D trials are then tried first, the same order as DIR 0
+// followed by DIR 1). One of the paths does the work; the others' launches return at once.
+template <int DIR>
+__device__ __forceinline__ bool ls_pass_runs(const StepState* st) {
+  if (st->done) return false;
+  if (DIR == 0) return st->ls_mode == 0;
+  if (DIR == 1) return st->need_j != 0;
+  return st->ls_mode != 0;
+}
+
+// Line search, IPC barrier part: the barrier change of the candidate pairs for each trial
+// step a = 2^-j along the pass's direction(s) (not polynomial in a), FP64 sums per block into
+// pp[(d * kLsTrials + j)][blockIdx], d the direction's place in the pass. k_energy adds them.
 template <typename T, int DIR>
 __global__ void __launch_bounds__(128) k_pair_trials(DevMesh<T> m, const StepState* __restrict__ st,
-                                                     double* __restrict__ pp /* [kLsTrials][grid] */) {
-  if (st->done) return;
-  if (DIR == 1 && !st->need_j) return;
-  __shared__ double red[32 * kLsTrials];
-  const Vec4<T>* dir = DIR == 0 ? m.D : m.DJ;
-  double acc[kLsTrials];
+                                                     double* __restrict__ pp /* [ND * kLsTrials][grid] */) {
+  if (!ls_pass_runs<DIR>(st)) return;
+  constexpr int ND = DIR == 2 ? 2 : 1;
+  constexpr int NB = ND * kLsTrials;
+  __shared__ double red[32 * NB];
+  double acc[NB];
 #pragma unroll
-  for (int j = 0; j < kLsTrials; ++j) acc[j] = 0.0;
+  for (int j = 0; j < NB; ++j) acc[j] = 0.0;
   const int np = min(*m.c.n_pairs, m.c.cap);
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) {
     // a pair beyond r_c stays beyond dhat for every trial (each vertex moves at most
@@ -1200,41 +1228,41 @@ __global__ void __launch_bounds__(128) k_pair_trials(DevMesh<T> m, const StepSta
     const double dq = m.c.d0[q];
     if (!(dq < m.c.rc)) continue;
     const uint64_t key = m.c.pairs[q];
-    // no trial brings the pair within dhat (and it starts outside): zero change throughout
-    if (dq - pair_motion(m, m.c, key, dir) >= m.c.dhat * (1.0 + 1e-9)) continue;
     const double b0 = barrier_b(dq, m.c.dhat);
+#pragma unroll
+    for (int dd = 0; dd < ND; ++dd) {
+      const Vec4<T>* dir = (DIR == 1 || dd == 1) ? m.DJ : m.D;
+      // no trial brings the pair within dhat (and it starts outside): zero change throughout
+      if (dq - pair_motion(m, m.c, key, dir) >= m.c.dhat * (1.0 + 1e-9)) continue;
 #pragma unroll 1
-    for (int j = 0; j < kLsTrials; ++j) {
-      int vs[4], nv;
-      P3 Jg[4];
-      const double d = pair_geom(m, m.c, key, 1.0 / double(1 << j), dir, vs, Jg, nv);
-      acc[j] += m.c.kappa * (barrier_b(d, m.c.dhat) - b0);
+      for (int j = 0; j < kLsTrials; ++j) {
+        int vs[4], nv;
+        P3 Jg[4];
+        const double d = pair_geom(m, m.c, key, 1.0 / double(1 << j), dir, vs, Jg, nv);
+        acc[dd * kLsTrials + j] += m.c.kappa * (barrier_b(d, m.c.dhat) - b0);
+      }
     }
   }
-  block_sum<kLsTrials>(acc, red);
+  block_sum<NB>(acc, red);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int j = 0; j < kLsTrials; ++j) pp[(size_t)j * gridDim.x + blockIdx.x] = acc[j];
+    for (int j = 0; j < NB; ++j) pp[(size_t)j * gridDim.x + blockIdx.x] = acc[j];
   }
 }
 
-// Line search (reading R17), one direction per launch: DIR = 0 is the sweep direction D,
-// DIR = 1 the uncorrected direction D_J, tried only when every trial along D failed
-// (the launch returns at once otherwise). The energy change along the direction is a
-// polynomial in the step a; its coefficients are summed over tets (tiles of 128 records
-// brought into shared memory by bulk copies, double-buffered in FP32) and free vertices,
-// per thread and per block with Acc<T>
-// (FP64-class), across blocks in FP64. The last block adds the barrier sums of
-// k_pair_trials (n_pp blocks; 0 without contact), evaluates E(x + a d) - E(x) at a = 2^-j
-// and takes the first Armijo-satisfying trial. has_j = 0 (no correction, D = D_J): a
-// failed D is a rejection.
+// Line search (reading R17), passes as in ls_pass_runs: DIR 0 along the sweep direction D,
+// DIR 1 along the uncorrected direction D_J (only when every trial along D failed), DIR 2
+// along both in one pass (the tile loads, F and the displacement gathers are shared). The
+// energy change along a direction is a polynomial in the step a; its coefficients are
+// summed over tets (tiles of 128 records brought into shared memory by bulk copies,
+// double-buffered in FP32) and free vertices, per thread and per block with Acc<T>
+// (FP64-class), into per-block partials; k_ls_decide adds them up and decides.
 template <typename T, int DIR>
-__global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st, int has_j,
-                                                double* __restrict__ partial /* [6][grid] */,
-                                                const double* __restrict__ pp, int n_pp) {
-  if (st->done) return;
-  if (DIR == 1 && !st->need_j) return;
-  constexpr int NC = 6;
+__global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st,
+                                                double* __restrict__ partial /* [6 ND][grid] */) {
+  if (!ls_pass_runs<DIR>(st)) return;
+  constexpr int ND = DIR == 2 ? 2 : 1;
+  constexpr int NC = 6 * ND;
   // tiles of 128 records arrive by bulk copy; FP32 double-buffers them (the next tile is in
   // flight while this one is evaluated), FP64 (records twice as large) uses one buffer
   constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;
@@ -1242,7 +1270,7 @@ __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st, int
   __shared__ __align__(8) uint64_t bar[NBUF];
   __shared__ Acc<T> sacc[32 * NC];
   __shared__ double red[32];
-  const Vec4<T>* __restrict__ dir = DIR == 0 ? m.D : m.DJ;
+  const Vec4<T>* dirs[2] = {DIR == 1 ? m.DJ : m.D, m.DJ};
   Acc<T> acc[NC];
   const int ntile = (m.T_ + 127) / 128;
   if (threadIdx.x == 0) {
@@ -1281,14 +1309,18 @@ __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st, int
       // (L2-resident) rather than read back from the element pass, whose records have
       // left L2 by now
       const TetRec<T>& r = srec_b[threadIdx.x];
-      T F[9], C[9], dF[9], c[6];
+      T F[9], C[9];
       tet_F(r, m.u, F);
       cofactor(F, C);
       const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
-      tet_dF(r, dir, m.Vf, dF);
-      tet_dpsi_poly(r, F, C, J, dF, c);
 #pragma unroll
-      for (int j = 0; j < 6; ++j) acc[j].add(c[j]);
+      for (int dd = 0; dd < ND; ++dd) {
+        T dF[9], c[6];
+        tet_dF(r, dirs[dd], m.Vf, dF);
+        tet_dpsi_poly(r, F, C, J, dF, c);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc[6 * dd + j].add(c[j]);
+      }
     }
     __syncthreads();  // buffer b is read; it may be refilled
     if (NBUF == 1) issue(tile + gridDim.x, 0);
@@ -1296,19 +1328,23 @@ __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st, int
   // inertia: m/(2h^2) (2 a d.(u - dz) + a^2 |d|^2)
   const int stride = gridDim.x * blockDim.x;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < m.Vf; v += stride) {
-    T uv[3], dz[3], d[3];
+    T uv[3], dz[3];
     load3(m.u, v, uv);
     load3(m.dz, v, dz);
-    load3(dir, v, d);
     const T mh = m.mh2[v];
-    T dd = T(0), de = T(0);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      dd += d[q] * d[q];
-      de += d[q] * (uv[q] - dz[q]);
+    for (int di = 0; di < ND; ++di) {
+      T d[3];
+      load3(dirs[di], v, d);
+      T dd = T(0), de = T(0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        dd += d[q] * d[q];
+        de += d[q] * (uv[q] - dz[q]);
+      }
+      acc[6 * di].add(mh * de);
+      acc[6 * di + 1].add(T(0.5) * mh * dd);
     }
-    acc[0].add(mh * de);
-    acc[1].add(T(0.5) * mh * dd);
   }
   double bs[NC];
   block_sum_acc<T, NC>(acc, bs, sacc);
@@ -1316,40 +1352,70 @@ __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st, int
 #pragma unroll
     for (int j = 0; j < NC; ++j) partial[(size_t)j * gridDim.x + blockIdx.x] = bs[j];
   }
-  if (!last_block(&st->ticket_energy)) return;
-  double cf[NC + kLsTrials];
+}
+
+// Line search decision (one block, after the pass's k_pair_trials and k_energy): sums every
+// partial array in one pass (FP64), evaluates E(x + a d) - E(x) at a = 2^-j along the
+// pass's direction(s) in order and takes the first Armijo-satisfying trial. has_j = 0 (no
+// correction, D = D_J): a failed D is a rejection.
+template <int DIR>
+__global__ void __launch_bounds__(256) k_ls_decide(StepState* st, int has_j, const double* __restrict__ partial,
+                                                   int n_part, const double* __restrict__ pp, int n_pp) {
+  if (!ls_pass_runs<DIR>(st)) return;
+  constexpr int ND = DIR == 2 ? 2 : 1;
+  constexpr int NC = 6 * ND;
+  constexpr int NB = ND * kLsTrials;
+  __shared__ double red[32 * (NC + NB)];
+  double cf[NC + NB];
 #pragma unroll
-  for (int j = 0; j < NC; ++j) cf[j] = block_sum_array(partial + (size_t)j * gridDim.x, gridDim.x, 1, red);
+  for (int j = 0; j < NC + NB; ++j) cf[j] = 0.0;
+  for (int q = threadIdx.x; q < n_part; q += blockDim.x) {
 #pragma unroll
-  for (int j = 0; j < kLsTrials; ++j) cf[NC + j] = n_pp > 0 ? block_sum_array(pp + (size_t)j * n_pp, n_pp, 1, red) : 0.0;
-  if (threadIdx.x == 0) {
-    st->ticket_energy = 0;
-    const double slope = DIR == 0 ? st->slope : st->slope_j;
-    double alpha = 0.0;
-    bool ok = false;
+    for (int j = 0; j < NC; ++j) cf[j] += partial[(size_t)j * n_part + q];
+  }
+  for (int q = threadIdx.x; q < n_pp; q += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < NB; ++j) cf[NC + j] += pp[(size_t)j * n_pp + q];
+  }
+  block_sum<NC + NB>(cf, red);
+  if (threadIdx.x != 0) return;
+  double alpha = 0.0;
+  int chosen = -1;
+  for (int dd = 0; dd < ND && chosen < 0; ++dd) {
+    const int dir_id = (DIR == 1 || dd == 1) ? 1 : 0;
+    const double slope = dir_id == 0 ? st->slope : st->slope_j;
+    const double* c = cf + 6 * dd;
     for (int j = 0; j < kLsTrials; ++j) {
       const double a = 1.0 / double(1 << j);
-      const double dE = a * (cf[0] + a * (cf[1] + a * (cf[2] + a * (cf[3] + a * (cf[4] + a * cf[5]))))) + cf[NC + j];
+      const double dE = a * (c[0] + a * (c[1] + a * (c[2] + a * (c[3] + a * (c[4] + a * c[5]))))) +
+                        cf[NC + dd * kLsTrials + j];
       if (dE <= 1e-4 * a * slope) {
         alpha = a;
-        ok = true;
+        chosen = dir_id;
         break;
       }
     }
-    st->alpha = alpha;
-    st->dir = DIR;
-    if (DIR == 0) st->need_j = (!ok && has_j) ? 1 : 0;
-    if (!ok && (DIR == 1 || !has_j)) st->ls_rejects += 1;
   }
+  const bool ok = chosen >= 0;
+  st->alpha = alpha;
+  st->dir = ok ? chosen : (DIR == 1 ? 1 : 0);
+  if (DIR == 0) st->need_j = (!ok && has_j) ? 1 : 0;
+  if (ok) {
+    st->prev_dir = chosen;
+    if (chosen == 1) st->dj_steps += 1;
+  }
+  if (!ok && (DIR != 0 || !has_j)) st->ls_rejects += 1;
 }
 
-// Batch meshes: the energy-change coefficients of k_energy along one direction (DIR 0: D,
-// DIR 1: D_J for the scenes whose trials along D all failed), summed per scene; thread per
-// tet in blocks [0, tet_blocks) (tiles staged in shared memory), thread per free vertex
-// after; no contact. Blocks whose scenes have nothing to do return before loading.
+// Batch meshes: the energy-change coefficients of k_energy, per scene, for the pass each
+// scene takes (as ls_pass_runs, per scene: DIR 0 along D after a D sweep, DIR 1 along D_J
+// after a failed DIR 0, DIR 2 along both after a D_J sweep); thread per tet in blocks
+// [0, tet_blocks) (tiles staged in shared memory), thread per free vertex after; no
+// contact. Blocks whose scenes have nothing to do return before loading.
 template <typename T, int DIR>
 __global__ void __launch_bounds__(128) k_energy_batch(DevMesh<T> m, int tet_blocks) {
-  constexpr int NC = 6;
+  constexpr int ND = DIR == 2 ? 2 : 1;
+  constexpr int NC = 6 * ND;
   __shared__ __align__(16) TetRec<T> srec[128];
   __shared__ int busy;
   const bool tets = (int)blockIdx.x < tet_blocks;
@@ -1358,7 +1424,7 @@ __global__ void __launch_bounds__(128) k_energy_batch(DevMesh<T> m, int tet_bloc
   const int32_t* scene_of = tets ? m.t_scene : m.v_scene;
   auto wants = [&](int sc) {
     const SceneState& S = m.scenes[sc];
-    return !S.done && (DIR == 0 || S.need_j);
+    return !S.done && (DIR == 0 ? S.ls_mode == 0 : (DIR == 1 ? S.need_j != 0 : S.ls_mode != 0));
   };
   if (threadIdx.x == 0) {
     // scenes are contiguous: the block covers scenes scene_of[i0] .. scene_of[i0 + n - 1]
@@ -1368,7 +1434,7 @@ __global__ void __launch_bounds__(128) k_energy_batch(DevMesh<T> m, int tet_bloc
   }
   __syncthreads();
   if (!busy) return;
-  const Vec4<T>* __restrict__ dir = DIR == 0 ? m.D : m.DJ;
+  const Vec4<T>* dirs[2] = {DIR == 1 ? m.DJ : m.D, m.DJ};
   Acc<T> acc[NC];
   int sc = -1;
   if (tets) {
@@ -1379,14 +1445,18 @@ __global__ void __launch_bounds__(128) k_energy_batch(DevMesh<T> m, int tet_bloc
       sc = m.t_scene[t];
       if (wants(sc)) {
         const TetRec<T>& r = srec[threadIdx.x];
-        T F[9], C[9], dF[9], c[6];
+        T F[9], C[9];
         tet_F(r, m.u, F);
         cofactor(F, C);
         const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
-        tet_dF(r, dir, m.Vf, dF);
-        tet_dpsi_poly(r, F, C, J, dF, c);
 #pragma unroll
-        for (int j = 0; j < NC; ++j) acc[j].add(c[j]);
+        for (int dd = 0; dd < ND; ++dd) {
+          T dF[9], c[6];
+          tet_dF(r, dirs[dd], m.Vf, dF);
+          tet_dpsi_poly(r, F, C, J, dF, c);
+#pragma unroll
+          for (int j = 0; j < 6; ++j) acc[6 * dd + j].add(c[j]);
+        }
       } else {
         sc = -1;
       }
@@ -1395,19 +1465,23 @@ __global__ void __launch_bounds__(128) k_energy_batch(DevMesh<T> m, int tet_bloc
     const int v = i0 + threadIdx.x;
     sc = m.v_scene[v];
     if (wants(sc)) {
-      T uv[3], dz[3], d[3];
+      T uv[3], dz[3];
       load3(m.u, v, uv);
       load3(m.dz, v, dz);
-      load3(dir, v, d);
       const T mh = m.mh2[v];
-      T dd = T(0), de = T(0);
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        dd += d[q] * d[q];
-        de += d[q] * (uv[q] - dz[q]);
+      for (int di = 0; di < ND; ++di) {
+        T d[3];
+        load3(dirs[di], v, d);
+        T dd = T(0), de = T(0);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          dd += d[q] * d[q];
+          de += d[q] * (uv[q] - dz[q]);
+        }
+        acc[6 * di].add(mh * de);
+        acc[6 * di + 1].add(T(0.5) * mh * dd);
       }
-      acc[0].add(mh * de);
-      acc[1].add(T(0.5) * mh * dd);
     } else {
       sc = -1;
     }
@@ -1434,6 +1508,7 @@ static __global__ void k_scene_finalize_main(SceneState* scenes, double* sacc, i
     S.alpha = 1.0;
     S.dir = 0;
     S.need_j = 0;
+    S.ls_mode = S.prev_dir;
     bool fin = false;
     if (!isfinite(r) || !isfinite(S.slope)) {
       S.status = 6;
@@ -1455,34 +1530,42 @@ static __global__ void k_scene_finalize_main(SceneState* scenes, double* sacc, i
   a[0] = a[1] = a[2] = 0.0;
 }
 
-// Batch meshes, thread per scene: Armijo choice along one direction from the per-scene
-// polynomial sums (DIR 0: D, recording need_j when every trial failed and D_J differs;
-// DIR 1: D_J for those scenes), then the sums are cleared for the next pass.
+// Batch meshes, thread per scene: Armijo choice from the per-scene polynomial sums of the
+// scene's pass (DIR as in k_energy_batch; DIR 0 records need_j when every trial failed and
+// D_J differs), then the sums are cleared for the next pass.
 template <int DIR>
 static __global__ void k_scene_finalize_energy(SceneState* scenes, double* sacc, int n, int has_j) {
+  constexpr int ND = DIR == 2 ? 2 : 1;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   SceneState& S = scenes[s];
   double* cf = sacc + (size_t)s * kSceneAcc + 3;
-  if (!S.done && (DIR == 0 || S.need_j)) {
-    const double slope = DIR == 0 ? S.slope : S.slope_j;
+  const bool runs = !S.done && (DIR == 0 ? S.ls_mode == 0 : (DIR == 1 ? S.need_j != 0 : S.ls_mode != 0));
+  if (runs) {
     double alpha = 0.0;
-    bool ok = false;
-    for (int j = 0; j < kLsTrials; ++j) {
-      const double a = 1.0 / double(1 << j);
-      const double dE = a * (cf[0] + a * (cf[1] + a * (cf[2] + a * (cf[3] + a * (cf[4] + a * cf[5])))));
-      if (dE <= 1e-4 * a * slope) {
-        alpha = a;
-        ok = true;
-        break;
+    int chosen = -1;
+    for (int dd = 0; dd < ND && chosen < 0; ++dd) {
+      const int dir_id = (DIR == 1 || dd == 1) ? 1 : 0;
+      const double slope = dir_id == 0 ? S.slope : S.slope_j;
+      const double* c = cf + 6 * dd;
+      for (int j = 0; j < kLsTrials; ++j) {
+        const double a = 1.0 / double(1 << j);
+        const double dE = a * (c[0] + a * (c[1] + a * (c[2] + a * (c[3] + a * (c[4] + a * c[5])))));
+        if (dE <= 1e-4 * a * slope) {
+          alpha = a;
+          chosen = dir_id;
+          break;
+        }
       }
     }
+    const bool ok = chosen >= 0;
     S.alpha = alpha;
-    S.dir = DIR;
+    S.dir = ok ? chosen : (DIR == 1 ? 1 : 0);
     if (DIR == 0) S.need_j = (!ok && has_j) ? 1 : 0;
-    if (!ok && (DIR == 1 || !has_j)) S.ls_rejects += 1;
+    if (ok) S.prev_dir = chosen;
+    if (!ok && (DIR != 0 || !has_j)) S.ls_rejects += 1;
   }
-  for (int j = 0; j < 6; ++j) cf[j] = 0.0;
+  for (int j = 0; j < 6 * ND; ++j) cf[j] = 0.0;
 }
 
 template <typename T>
