@@ -140,7 +140,8 @@ void jgs2_precompute_opts_default(jgs2_precompute_opts* o);
 /* Defaults: max_sweeps 500, rel_tol 1e-4, FP32, asm, line search on, check_every 16. */
 void jgs2_step_opts_default(jgs2_step_opts* o);
 
-/* Validates the mesh (indices in range, positive volumes, material ranges), computes the
+/* Validates the mesh (indices in range, positive volumes, material ranges, every free
+ * vertex in some tet; JGS2_EINVAL otherwise, before any device allocation), computes the
  * rest-shape data in FP64 on the host (D_m^{-1}, V_e, lumped masses m_v = sum rho V_e/4),
  * reorders vertices (free first, spatially sorted) and tets, builds the incidence lists
  * and uploads everything to the current CUDA device. *out receives a new mesh. */
@@ -189,7 +190,9 @@ int32_t jgs2_mesh_n_cub(const jgs2_mesh* mesh);
  * with a new configuration (precision, correction, line search, block size, check_every,
  * profile, trace) captures the graph, so jgs2_step is not itself called inside a stream
  * capture. report may be NULL. Returns JGS2_ENOTCONVERGED (state written) when
- * max_sweeps is hit, JGS2_EDIVERGED (state untouched) on a non-finite residual. */
+ * max_sweeps is hit, JGS2_EDIVERGED (state untouched) on a non-finite residual. A mesh
+ * without free vertices (every vertex pinned) or with g(x^0) = 0 returns JGS2_OK after 0
+ * sweeps with x_{t+1} = x_t (r = 0). */
 jgs2_status jgs2_step(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts,
                       void* stream, jgs2_step_report* report);
 
@@ -218,8 +221,8 @@ jgs2_status jgs2_energy_gradient(jgs2_mesh* mesh, const double* x_t, const doubl
  * sweep in linear mode (H_ii, R_i and the cubature element Hessians at x*, Eq. cubature
  * applied to the residual); correction = JGS2_CORR_OFF gives block-Jacobi preconditioning.
  * All arrays are DEVICE pointers in caller order: x_t, v_t, x_t1, gx_t1, gv_t1, gx_t, gv_t
- * [V][3] double; gE [T] double is ACCUMULATED (+=). Meshes with contact are rejected
- * (JGS2_EINVAL): the barrier is not part of this adjoint. Returns JGS2_ENOTCONVERGED (all
+ * [V][3] double; gE [T] double is ACCUMULATED (+=). Meshes with contact, or without a
+ * free vertex, are rejected (JGS2_EINVAL): the barrier is not part of this adjoint. Returns JGS2_ENOTCONVERGED (all
  * outputs written) if max_iters is reached first. Synchronises the stream. */
 typedef struct {
   int32_t max_iters;     /* conjugate-gradient iterations at most */

@@ -148,6 +148,11 @@ jgs2_status mesh_create(const jgs2_mesh_desc* d, Mesh** out, const std::vector<i
     m->lp[t] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)) + m->mu[t];
     for (int a = 0; a < 4; ++a) m->mass[tv[a]] += m->rho[t] * m->vol[t] / 4.0;
   }
+  // a free vertex outside every tet would have no mass and no elastic term (a singular
+  // 3x3 system): an input error
+  for (int v = 0; v < V; ++v)
+    if (!m->pinned[v] && !(m->mass[v] > 0.0))
+      return fail(JGS2_EINVAL, "free vertex " + std::to_string(v) + " belongs to no tet");
   // internal order: free vertices along a Morton curve, then pinned vertices
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
   for (int v = 0; v < V; ++v)
@@ -1079,7 +1084,6 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
       if (prof && cerr == cudaSuccess) cerr = cudaEventRecordWithFlags(g.e1, gs, cudaEventRecordExternal);
       m->ggroups.push_back(g);
     };
-    cudaStream_t s2 = m->gstream2;
     const int nbS = (S + 127) / 128;
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -1181,7 +1185,11 @@ static jgs2_status step_impl(Mesh* m, double* x, double* v, const jgs2_step_opts
   L.end(id);
   CK(cudaGetLastError());
   StepState* hs = m->h_state;
-  if (m->n_scenes > 0) {
+  if (m->Vf == 0) {
+    // no free vertex: every position is prescribed, x_{t+1} = x_t with no sweep (r = 0)
+    std::memset(hs, 0, sizeof(StepState));
+    hs->converged = 1;
+  } else if (m->n_scenes > 0) {
     st = run_sweeps_batch<T>(m, *o, s, L);
     if (st != JGS2_OK) {
       cudaEventDestroy(e0);
@@ -1277,7 +1285,7 @@ static jgs2_status sweeps_impl(Mesh* m, const double* xt, const double* vt, doub
   CK(cudaGetLastError());
   // exactly n sweeps: no convergence test (rel_tol < 0), stop after the n-th update
   Launches L{m, s, false};
-  st = run_sweeps<T>(m, *o, s, n, -1.0, false, m->h_state, L);
+  if (m->Vf > 0) st = run_sweeps<T>(m, *o, s, n, -1.0, false, m->h_state, L);
   if (st != JGS2_OK) return st;
   k_finish<T><<<nb, 128, 0, s>>>(d, xk, nullptr);
   CK(cudaGetLastError());
@@ -1469,6 +1477,11 @@ static jgs2_status autotune_impl(Mesh* m, double* x, double* v, const jgs2_step_
                                  int32_t* chosen) {
   jgs2_status st = ensure_prec<T>(m);
   if (st != JGS2_OK) return st;
+  if (m->Vf == 0) {
+    // nothing to time: the step of a mesh without free vertices launches no sweep kernel
+    if (chosen) *chosen = m->bs[sizeof(T) == 4 ? 1 : 0];
+    return JGS2_OK;
+  }
   DevMesh<T> d = dev_view<T>(m);
   const int nb = (m->V + 127) / 128;
   const bool corr = o->correction != JGS2_CORR_OFF && m->nP > 0;
@@ -1661,6 +1674,7 @@ jgs2_status step_adjoint(Mesh* m, const double* xt, const double* vt, const doub
   if (!m || !xt || !vt || !x1 || !gx1 || !gv1 || !gx || !gv || !gE || !o) return fail(JGS2_EINVAL, "null argument");
   if (m->contact) return fail(JGS2_EINVAL, "the adjoint does not include contact terms");
   if (o->max_iters < 1 || !(o->rel_tol > 0.0)) return fail(JGS2_EINVAL, "bad adjoint options");
+  if (m->Vf == 0) return fail(JGS2_EINVAL, "the mesh has no free vertex");
   if (o->correction != JGS2_CORR_OFF && m->n_cub == 0)
     return fail(JGS2_ENOTPRECOMPUTED, "corrected preconditioner requested before a precompute");
   cudaStream_t s = (cudaStream_t)stream;

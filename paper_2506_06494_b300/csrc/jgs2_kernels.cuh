@@ -580,39 +580,21 @@ __device__ __forceinline__ void pool_entry(T h, T w, const T (&U)[36], T (&M)[36
 template <typename T>
 __device__ __forceinline__ void load4(const T* __restrict__ p, T (&o)[4]);
 
-template <int Q4, bool SMEM, typename T>
+template <int Q4, typename T>
 __device__ __forceinline__ void pool_chunk(const T* __restrict__ Hp, T w, const T (&U)[36], T (&M)[36],
                                            T (&gt)[3]) {
   T hv[4];
-  if constexpr (SMEM) {
-    // staged row in shared memory: plain 16-byte loads
-    if constexpr (sizeof(T) == 4) {
-      const float4 v = *reinterpret_cast<const float4*>(Hp + 4 * Q4);
-      hv[0] = v.x;
-      hv[1] = v.y;
-      hv[2] = v.z;
-      hv[3] = v.w;
-    } else {
-      const double2 a = *reinterpret_cast<const double2*>(Hp + 4 * Q4);
-      const double2 b = *(reinterpret_cast<const double2*>(Hp + 4 * Q4) + 1);
-      hv[0] = a.x;
-      hv[1] = a.y;
-      hv[2] = b.x;
-      hv[3] = b.y;
-    }
-  } else {
-    load4(Hp + 4 * Q4, hv);
-  }
+  load4(Hp + 4 * Q4, hv);
   pool_entry<4 * Q4 + 0>(hv[0], w, U, M, gt);
   pool_entry<4 * Q4 + 1>(hv[1], w, U, M, gt);
   pool_entry<4 * Q4 + 2>(hv[2], w, U, M, gt);
   pool_entry<4 * Q4 + 3>(hv[3], w, U, M, gt);
 }
 
-template <bool SMEM, typename T, int... Q4>
+template <typename T, int... Q4>
 __device__ __forceinline__ void pool_row(const T* __restrict__ Hp, T w, const T (&U)[36], T (&M)[36], T (&gt)[3],
                                          std::integer_sequence<int, Q4...>) {
-  (pool_chunk<Q4, SMEM>(Hp, w, U, M, gt), ...);
+  (pool_chunk<Q4>(Hp, w, U, M, gt), ...);
 }
 
 // One cubature slot of Eq. cubature: the pool row Hp (packed rotated element Hessian, then
@@ -624,7 +606,7 @@ __device__ __forceinline__ void slot_sums(const T* __restrict__ Hp, T w, const T
   T M[36];
 #pragma unroll
   for (int q = 0; q < 36; ++q) M[q] = T(0);
-  pool_row<false>(Hp, w, U, M, gt, std::make_integer_sequence<int, (kPackedH + 12 + 3) / 4>{});
+  pool_row(Hp, w, U, M, gt, std::make_integer_sequence<int, (kPackedH + 12 + 3) / 4>{});
   // H~' += w U^T M (symmetric: six entries)
 #pragma unroll
   for (int r = 0; r < 12; ++r) {
@@ -1269,7 +1251,6 @@ __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st,
   __shared__ __align__(128) TetRec<T> srec[NBUF][128];
   __shared__ __align__(8) uint64_t bar[NBUF];
   __shared__ Acc<T> sacc[32 * NC];
-  __shared__ double red[32];
   const Vec4<T>* dirs[2] = {DIR == 1 ? m.DJ : m.D, m.DJ};
   Acc<T> acc[NC];
   const int ntile = (m.T_ + 127) / 128;

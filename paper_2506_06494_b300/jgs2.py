@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libjgs2.so")
 
 TRACE_MAX = 4096
 NKERNELS = 8
-KERNEL_NAMES = ["k_pool", "k_gather", "k_correct", "k_energy", "k_update", "setup", "contact"]
+KERNEL_NAMES = ["k_pool", "k_gather", "k_correct", "k_energy", "k_update", "setup", "contact", "k_elem"]
 FP64, FP32 = 0, 1
 CORR_ASM, CORR_ELEM, CORR_OFF = 0, 1, 2
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTPRECOMPUTED", 5: "ENOTCONVERGED",

@@ -56,7 +56,7 @@ def _desc(X, T, E, nu, rho, pin=None, dt=1 / 120):
     return d
 
 
-@pytest.mark.parametrize("case", ["inverted", "index", "material", "dt", "empty"])
+@pytest.mark.parametrize("case", ["inverted", "index", "material", "dt", "empty", "isolated"])
 def test_mesh_create_rejects_bad_input(L, case):
     s = scenes.cube_scene()
     X = s.X.copy()
@@ -71,6 +71,8 @@ def test_mesh_create_rejects_bad_input(L, case):
         nu[3] = 0.5
     elif case == "dt":
         dt = 0.0
+    elif case == "isolated":  # a free vertex in no tet: no mass, singular 3x3 system
+        X = np.vstack([X, [[1.0, 1.0, 1.0]]])
     d = _desc(X, T, E, nu, rho, None, dt)
     if case == "empty":
         d.n_tets = 0
@@ -79,6 +81,21 @@ def test_mesh_create_rejects_bad_input(L, case):
     assert st == 1  # JGS2_EINVAL, raised before any device allocation
     assert not h.value
     assert len(L.jgs2_last_error()) > 0
+
+
+def test_pinned_vertex_outside_every_tet_is_accepted(L):
+    """A pinned vertex that no tet references carries no DOF: the mesh is valid (creation
+    is host-only, so this runs without a GPU)."""
+    s = scenes.cube_scene()
+    X = np.vstack([s.X, [[1.0, 1.0, 1.0]]])
+    T = s.tets.astype(np.int32).copy()
+    pin = np.zeros(len(X), np.uint8)
+    pin[-1] = 1
+    E, nu, rho = s.youngs.copy(), s.poisson.copy(), s.density.copy()
+    d = _desc(X, T, E, nu, rho, pin)
+    h = C.c_void_p()
+    assert L.jgs2_mesh_create(C.byref(d), C.byref(h)) == 0
+    L.jgs2_mesh_destroy(h)
 
 
 def test_null_arguments(L):
