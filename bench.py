@@ -11,8 +11,10 @@ correct, line-search energy and update kernels plus the per-step setup) on input
 resident in HBM. The default workload is ten voxel spheres (3.47M tets) in a box with the IPC
 barrier on. `batch` is 256 seeded voxel blobs of uneven size stepped together in one mesh
 (graph-captured sweep chunks, per-scene stopping). With N > 1 (torchrun) every rank steps
-its own replica (the sweep does not shard across GPUs); the time is the maximum over ranks
-and the value counts every rank's work.
+its own replica of a single scene (one scene's sweep does not shard across GPUs), while the
+batch workload shards the job's N x n_scenes blobs across the ranks by tet count, with no
+exchange between them. The time is the maximum over ranks and the value counts every
+rank's work.
 """
 from __future__ import annotations
 
@@ -42,8 +44,35 @@ def peaks():
         return 6400.0, "fallback"
 
 
-def build_scenes(args):
-    """(list of scenes, description, batch?)"""
+def shard_scenes(sizes, world):
+    """Scene indices per rank, balanced by size: largest scene first to the least-loaded
+    rank (ties to the lower rank); each rank's list in ascending order. No scene is shared:
+    the batch shards with no exchange between ranks."""
+    order = sorted(range(len(sizes)), key=lambda i: (-sizes[i], i))
+    load = [0.0] * world
+    out = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        out[r].append(i)
+        load[r] += sizes[i]
+    return [sorted(o) for o in out]
+
+
+def over_ranks(value, op="max", device=None):
+    """A per-rank float reduced over the process group ("max" or "sum"; the value itself
+    when there is no group)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def build_scenes(args, rank=0, world=1):
+    """(list of scenes, description, batch?). The batch workload has n_scenes scenes per
+    rank: the job's n_scenes * world seeded blobs are sharded by tet count."""
     import scenes
     w = args.workload
     if w == "spheres":
@@ -55,9 +84,12 @@ def build_scenes(args):
     if w == "cube":
         return [scenes.cube_scene()], "5x5x5-vertex Kuhn cube, 384 tets", False
     if w == "batch":
-        ss = [scenes.blob_scene(i, 1e3, 5e4) for i in range(args.n_scenes)]
+        n = args.n_scenes * world
+        mine = shard_scenes([scenes.blob_tet_target(i, 1e3, 5e4) for i in range(n)], world)[rank]
+        ss = [scenes.blob_scene(i, 1e3, 5e4) for i in mine]
         T = sum(s.n_tets for s in ss)
-        return ss, (f"{args.n_scenes} seeded voxel blobs (1-6 spheres, 1k-50k tets each, {T:,} tets), "
+        shard = f", rank {rank}'s shard of {n}" if world > 1 else ""
+        return ss, (f"{len(ss)} seeded voxel blobs{shard} (1-6 spheres, 1k-50k tets each, {T:,} tets), "
                     "E log-uniform 1e4-1e7, nu 0.3-0.48, bottom pinned"), True
     raise SystemExit(f"unknown workload {w}")
 
@@ -239,7 +271,7 @@ def run_jgs2(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    ss, desc, batch = build_scenes(args)
+    ss, desc, batch = build_scenes(args, rank, world)
     X, V0, tets, _, _, _, pin = concat(ss)
     T = sum(s.n_tets for s in ss)
     Vf = int((~pin.astype(bool)).sum())
@@ -279,9 +311,7 @@ def run_jgs2(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+        ms_total = over_ranks(ms_total, "max", dev)
     sweeps = np.array([q[0] for q in reps])
     kms = np.sum([q[3] for q in reps], axis=0)
     kl = np.sum([q[4] for q in reps], axis=0)
@@ -308,9 +338,11 @@ def run_jgs2(args, rank, world, local_rank):
                    "vertices": int(len(X)), "free_vertices": Vf,
                    "contact": bool(args.contact) if args.workload == "spheres" else False,
                    "correction": args.correction, "line_search": True, "n_cub": args.n_cub, "rel_tol": 1e-4,
-                   "max_sweeps": args.max_sweeps, "block_size": bs, "parallelism": f"replicas x{world}",
+                   "max_sweeps": args.max_sweeps, "block_size": bs,
+                   "parallelism": f"{'scene shards' if batch else 'replicas'} x{world}",
                    "l2": "per-sweep working set larger than L2 (126 MB); no flush"},
-        "sweeps_per_step": float(sweeps.mean()), "sweeps_per_s": float(sweeps.sum() / (ms_total * 1e-3)),
+        "sweeps_per_step": float(sweeps.mean()),
+        "sweeps_per_s": over_ranks(float(sweeps.sum()), "sum", dev if world > 1 else None) / (ms_total * 1e-3),
         "converged_steps": int(sum(q[1] for q in reps)), "max_rel_residual": float(max(q[2] for q in reps)),
         "line_search_per_step": {"dj_steps": float(np.mean([q[8] for q in reps])),
                                  "rejects": float(np.mean([q[7] for q in reps])),

@@ -168,12 +168,7 @@ def spheres_scene(n_spheres=10, radius=0.1, cells_across=48, seed=0, dhat=1e-3,
                  dhat=dhat, contact=contact)
 
 
-def blob_scene(index, t_min=1e3, t_max=5e4):
-    """One seeded random voxel blob (union of 1-6 spheres), bottom layer pinned.
-
-    The tet count is drawn log-uniform in [t_min, t_max]; the cell size is bisected
-    until the blob's tet count is within 10% of that target.
-    """
+def _blob_params(index, t_min, t_max):
     rng = np.random.default_rng(index)
     k = int(rng.integers(1, 7))
     centres = rng.uniform(0.0, 0.1, size=(k, 3))
@@ -181,6 +176,22 @@ def blob_scene(index, t_min=1e3, t_max=5e4):
     target = float(np.exp(rng.uniform(np.log(t_min), np.log(t_max))))
     E = float(np.exp(rng.uniform(np.log(1e4), np.log(1e7))))
     nu = float(rng.uniform(0.3, 0.48))
+    return k, centres, radii, target, E, nu
+
+
+def blob_tet_target(index, t_min=1e3, t_max=5e4):
+    """The tet count blob_scene(index) aims at (its mesh is within 10% of it), without
+    building the mesh: enough to balance scenes across ranks."""
+    return _blob_params(index, t_min, t_max)[3]
+
+
+def blob_scene(index, t_min=1e3, t_max=5e4):
+    """One seeded random voxel blob (union of 1-6 spheres), bottom layer pinned.
+
+    The tet count is drawn log-uniform in [t_min, t_max]; the cell size is bisected
+    until the blob's tet count is within 10% of that target.
+    """
+    k, centres, radii, target, E, nu = _blob_params(index, t_min, t_max)
     lo = (centres - radii[:, None]).min(0)
     hi = (centres + radii[:, None]).max(0)
 
