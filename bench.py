@@ -259,7 +259,7 @@ def timed_steps(mesh, x, v, opts, n, stream):
         r = mesh.step(x, v, opts, stream)
         reps.append((r.sweeps, r.converged, r.rel_residual, list(r.kernel_ms), list(r.kernel_launches),
                      r.launches, r.fallback, r.ls_rejects, r.dj_steps, r.contact_rebuilds,
-                     r.contact_candidates, r.contact_near))
+                     r.contact_candidates, r.contact_near, r.profiled_sweeps))
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1), reps
@@ -365,23 +365,29 @@ def run_jgs2(args, rank, world, local_rank):
                              "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
     if batch:
         out["scene_sweeps"] = scene_sweeps
-    # kernel times are CUDA events around every kernel group in the captured sweep graphs
-    # of the timed steps; a group's time per sweep that did work (gather-side kernels run
-    # sweeps + 1 times per step, the line search and update sweeps times; launches that
-    # returned at once after the stop add their time too, so the averages are upper bounds)
-    n_work = {"k_energy": sw_tot, "k_update": sw_tot}
-    share = {KIND[q]: round(float(kms[q] / max(kms.sum(), 1e-12)), 4) for q in range(len(KIND))}
+    # kernel times: CUDA events, inside the timed steps, around every kernel group of the
+    # first sweep of each replayed chunk of the sweep graph (one sweep in check_every is
+    # sampled; the per-step setup kernels are timed in full). A sweep kernel's average is
+    # its sampled time over the sampled sweeps; its time per step, that average times the
+    # sweeps per step.
+    psw = max(int(sum(q[12] for q in reps)), 1)
+    avg_ms = {}
+    for q, name in enumerate(KIND):
+        avg_ms[name] = float(kms[q] / args.steps if name == "setup" else kms[q] / psw)
+    est_step = {n: avg_ms[n] * (1.0 if n == "setup" else sw_tot / args.steps) for n in KIND}
+    tot = max(sum(est_step.values()), 1e-12)
+    share = {n: round(est_step[n] / tot, 4) for n in KIND}
     per_kernel = {}
     for q, name in enumerate(KIND):
-        if name in kb and kl[q] > 0:
-            nw = n_work.get(name, sw_tot + args.steps)
-            avg = kms[q] / nw
-            per_kernel[name] = {"avg_launch_ms": round(float(avg), 5), "bytes_per_launch": kb[name],
+        if name in kb and kl[q] > 0 and avg_ms[name] > 0:
+            avg = avg_ms[name]
+            per_kernel[name] = {"avg_launch_ms": round(avg, 5), "bytes_per_launch": kb[name],
                                 "GB_s": round(kb[name] / (avg * 1e-3) / 1e9, 1),
                                 "frac": round(kb[name] / (avg * 1e-3) / 1e9 / hbm, 4)}
     dom = max(per_kernel, key=lambda n: share[n])
     achieved = per_kernel[dom]["GB_s"]
-    out["kernel_ms_per_step"] = {KIND[q]: round(float(kms[q] / args.steps), 4) for q in range(len(KIND))}
+    out["profiled_sweeps"] = psw
+    out["kernel_ms_per_step"] = {n: round(est_step[n], 4) for n in KIND}
     out["kernel_launches_per_step"] = {KIND[q]: int(kl[q] // args.steps) for q in range(len(KIND))}
     out["kernel_share"] = share
     out["kernels"] = per_kernel

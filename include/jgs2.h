@@ -103,7 +103,10 @@ typedef struct {
   int32_t line_search;       /* 1 = global Armijo backtracking on E (FP64 energy sums) */
   int32_t check_every;       /* host reads the convergence flag every this many sweeps */
   int32_t record_trace;      /* 1 = keep the per-sweep residual trace in the report */
-  int32_t profile;           /* 1 = time every kernel launch with CUDA events on the stream */
+  int32_t profile;           /* 1 = time the kernels with CUDA events: the per-step kernels, and
+                              * every kernel group of the last sweep of each replayed chunk
+                              * of check_every sweeps (a sample, so the events barely slow the
+                              * step) */
 } jgs2_step_opts;
 
 #define JGS2_TRACE_MAX 4096
@@ -129,8 +132,11 @@ typedef struct {
   double g0;                 /* |g(x^0)| */
   double ms;                 /* wall time of the step on the stream (CUDA events) */
   int32_t launches;          /* kernels launched by the step */
-  int32_t kernel_launches[JGS2_NKERNELS]; /* per kernel kind (profile = 1) */
-  double kernel_ms[JGS2_NKERNELS];        /* summed CUDA-event time per kind (profile = 1) */
+  int32_t profiled_sweeps;   /* sweeps whose kernel groups were timed (profile = 1): one per
+                              * replayed chunk whose last sweep ran before the step stopped */
+  int32_t kernel_launches[JGS2_NKERNELS]; /* per kernel kind */
+  double kernel_ms[JGS2_NKERNELS];        /* summed CUDA-event time per kind (profile = 1): per-step
+                                           * kernels in full, sweep kernels over the profiled sweeps */
   int32_t trace_len;
   double trace[JGS2_TRACE_MAX]; /* r_k per sweep if record_trace */
 } jgs2_step_report;

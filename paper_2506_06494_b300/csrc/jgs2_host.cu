@@ -784,7 +784,8 @@ struct Launches {
   cudaStream_t s;
   bool prof;
   int count[JGS2_NKERNELS] = {};
-  double gms[JGS2_NKERNELS] = {};  // event times of graph replays
+  double gms[JGS2_NKERNELS] = {};  // event times of graph replays (the profiled sweeps)
+  int psweeps = 0;                 // profiled sweeps: one per replay begun before the stop
   std::vector<std::pair<int, int>> rec;  // (kind, event index)
   int used = 0;
   cudaError_t err = cudaSuccess;
@@ -817,7 +818,10 @@ struct Launches {
         r->kernel_ms[q] = 0.0;
       }
     }
-    if (r) r->launches = tot;
+    if (r) {
+      r->launches = tot;
+      r->profiled_sweeps = prof ? psweeps : 0;
+    }
     if (!r || !prof) return;
     for (int q = 0; q < JGS2_NKERNELS; ++q) r->kernel_ms[q] += gms[q];
     for (auto& kv : rec) {
@@ -906,7 +910,9 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
     m->graph = nullptr;
     m->graph_key = -1;
     m->ggroups.clear();
-    const size_t nev = prof ? (size_t)14 * chunk : 0;
+    // profiling: event nodes around the kernel groups of the chunk's last sweep only (not
+    // the first: a step's sweep 0 always rebuilds the contact list)
+    const size_t nev = prof ? (size_t)14 : 0;
     while (m->gevents.size() < nev) {
       cudaEvent_t e;
       CK(cudaEventCreate(&e));
@@ -914,15 +920,16 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
     }
     size_t evi = 0;
     cudaError_t cerr = cudaSuccess;
+    bool timed = false;  // set per sweep of the chunk
     auto group = [&](int kind, int n, cudaStream_t gs, auto&& launch) {
       Mesh::GraphGroup g{kind, n, nullptr, nullptr};
-      if (prof) {
+      if (timed) {
         g.e0 = m->gevents[evi++];
         g.e1 = m->gevents[evi++];
         if (cerr == cudaSuccess) cerr = cudaEventRecordWithFlags(g.e0, gs, cudaEventRecordExternal);
       }
       launch();
-      if (prof && cerr == cudaSuccess) cerr = cudaEventRecordWithFlags(g.e1, gs, cudaEventRecordExternal);
+      if (timed && cerr == cudaSuccess) cerr = cudaEventRecordWithFlags(g.e1, gs, cudaEventRecordExternal);
       m->ggroups.push_back(g);
     };
     // a second branch of the graph: work on s2 starts after the fork point on s and
@@ -940,6 +947,7 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     for (int q = 0; q < chunk; ++q) {
+      timed = prof && q == chunk - 1;
       // contact pass (positions only) alongside the element pass; both feed the gather
       if (m->contact) {
         fork(m->gfork[0]);
@@ -1003,10 +1011,12 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
     if (check || prof) {
       CK(cudaMemcpyAsync(hs, m->d_state, sizeof(StepState), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      if (prof) {
+      // the timed (last) sweep of this replay did work unless the step stopped before it
+      if (prof && (!hs->done || rp * chunk + chunk - 1 <= hs->sweeps)) {
+        L.psweeps += 1;
         for (const auto& g : m->ggroups) {
           float ms = 0.f;
-          if (cudaEventElapsedTime(&ms, g.e0, g.e1) == cudaSuccess) L.gms[g.kind] += ms;
+          if (g.e0 && cudaEventElapsedTime(&ms, g.e0, g.e1) == cudaSuccess) L.gms[g.kind] += ms;
         }
       }
       if (check && hs->done) break;
@@ -1064,7 +1074,7 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
     m->graph = nullptr;
     m->graph_key = -1;
     m->ggroups.clear();
-    const size_t nev = prof ? (size_t)14 * chunk : 0;
+    const size_t nev = prof ? (size_t)14 : 0;
     while (m->gevents.size() < nev) {
       cudaEvent_t e;
       CK(cudaEventCreate(&e));
@@ -1072,22 +1082,24 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
     }
     size_t evi = 0;
     cudaError_t cerr = cudaSuccess;
-    // kernel groups as in run_sweeps: kind, kernels, optional external timing events
+    bool timed = false;
+    // kernel groups as in run_sweeps: kind, kernels, timing events on the chunk's last sweep
     auto group = [&](int kind, int n, cudaStream_t gs, auto&& launch) {
       Mesh::GraphGroup g{kind, n, nullptr, nullptr};
-      if (prof) {
+      if (timed) {
         g.e0 = m->gevents[evi++];
         g.e1 = m->gevents[evi++];
         if (cerr == cudaSuccess) cerr = cudaEventRecordWithFlags(g.e0, gs, cudaEventRecordExternal);
       }
       launch();
-      if (prof && cerr == cudaSuccess) cerr = cudaEventRecordWithFlags(g.e1, gs, cudaEventRecordExternal);
+      if (timed && cerr == cudaSuccess) cerr = cudaEventRecordWithFlags(g.e1, gs, cudaEventRecordExternal);
       m->ggroups.push_back(g);
     };
     const int nbS = (S + 127) / 128;
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     for (int q = 0; q < chunk; ++q) {
+      timed = prof && q == chunk - 1;
       group(JGS2_K_ELEM, 1, s, [&] { k_elem<T, true><<<nbT, 128, 0, s>>>(d, m->d_state); });
       group(JGS2_K_GATHER, 1, s, [&] { launch_gather<T, true>(d, m, corr, bs, s, m->d_state, m->d_partial, m->d_trace, 0); });
       // the cubature pool after the gather, whose g and R at the corners it reads
@@ -1135,9 +1147,21 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
     CK(cudaMemcpyAsync(&done, m->d_ndone, sizeof(done), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (prof) {
-      for (const auto& g : m->ggroups) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, g.e0, g.e1) == cudaSuccess) L.gms[g.kind] += ms;
+      // the timed (last) sweep of this replay did work unless every scene stopped before it
+      bool did = done < S;
+      if (!did) {
+        std::vector<SceneState> sc(S);
+        CK(cudaMemcpy(sc.data(), m->d_scenes, sizeof(SceneState) * S, cudaMemcpyDeviceToHost));
+        int kmax = 0;
+        for (const auto& q : sc) kmax = std::max(kmax, (int)q.sweeps);
+        did = sw + chunk - 1 <= kmax;
+      }
+      if (did) {
+        L.psweeps += 1;
+        for (const auto& g : m->ggroups) {
+          float ms = 0.f;
+          if (g.e0 && cudaEventElapsedTime(&ms, g.e0, g.e1) == cudaSuccess) L.gms[g.kind] += ms;
+        }
       }
     }
     if (done >= S) break;

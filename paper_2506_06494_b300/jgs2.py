@@ -66,7 +66,7 @@ class StepReport(C.Structure):
                 ("ls_rejects", C.c_int32), ("dj_steps", C.c_int32), ("contact_rebuilds", C.c_int32),
                 ("contact_candidates", C.c_int32), ("contact_near", C.c_int32),
                 ("rel_residual", C.c_double), ("g0", C.c_double),
-                ("ms", C.c_double), ("launches", C.c_int32),
+                ("ms", C.c_double), ("launches", C.c_int32), ("profiled_sweeps", C.c_int32),
                 ("kernel_launches", C.c_int32 * NKERNELS), ("kernel_ms", C.c_double * NKERNELS),
                 ("trace_len", C.c_int32), ("trace", C.c_double * TRACE_MAX)]
 

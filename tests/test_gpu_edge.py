@@ -21,7 +21,7 @@ def single_tet():
     X = np.array([[0.0, 0.0, 0.0], [0.01, 0.0, 0.0], [0.0, 0.01, 0.0], [0.002, 0.003, 0.01]])
     T = np.array([[0, 1, 2, 3]], np.int32)
     pin = np.array([1, 1, 1, 0], np.uint8)
-    v0 = np.array([[0.0, 0.0, 0.0]] * 3 + [[0.05, -0.02, 0.1]])
+    v0 = np.array([[0.0, 0.0, 0.0]] * 3 + [[0.5, -0.2, 1.0]])
     return scenes.Scene("single tet", X, T, np.array([1e5]), np.array([0.4]), np.array([1000.0]), pin, v0)
 
 
