@@ -138,13 +138,14 @@ def sweep_bytes(V_f, T, n_cub, fp_bytes=4):
     return T * per_tet + V_f * per_vertex
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu --set full
-# capture of one launch, FP32, 2 voxel spheres: 694,272 tets, 126,826 free vertices; summary
-# and command in profiles/sweep_kernels_spheres2_fp32.md). It grows in proportion to the
-# tets, so a launch on another mesh is credited with traffic x T / 694,272. Only kernels whose
-# code has not changed since that capture are listed.
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of
+# one launch, FP32, 2 voxel spheres: 694,272 tets, 126,826 free vertices; summaries and
+# commands in profiles/sweep_kernels_spheres2_fp32.md; k_energy is its one-direction pass).
+# It grows in proportion to the tets, so a launch on another mesh is credited with
+# traffic x T / 694,272. Only kernels whose code has not changed since their capture are
+# listed.
 NCU_TRAFFIC_TETS = 694272
-NCU_TRAFFIC = {"k_energy": 84.463104e6 + 2.722304e6, "k_elem": 79.797504e6 + 5.376768e6}
+NCU_TRAFFIC = {"k_energy": 84.397056e6 + 2.023424e6, "k_elem": 79.797504e6 + 5.376768e6}
 
 
 class Clocks:
@@ -286,7 +287,11 @@ def run_jgs2(args, rank, world, local_rank):
     t_pre = time.perf_counter() - t0
     prec = p.FP32 if args.precision == "fp32" else p.FP64
     corr = {"asm": p.CORR_ASM, "elem": p.CORR_ELEM, "off": p.CORR_OFF}[args.correction]
-    opts = p.step_opts(precision=prec, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4, profile=1)
+    # chunks of 16 sweeps (the library's default), fewer when the cap is lower: the timed
+    # (last) sweep of a chunk must fall inside the step
+    chunk = max(1, min(16, args.max_sweeps + 1))
+    opts = p.step_opts(precision=prec, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4, profile=1,
+                       check_every=chunk)
     x0 = torch.tensor(X, dtype=torch.float64, device=dev)
     v0 = torch.tensor(V0, dtype=torch.float64, device=dev)
     bs = mesh.autotune(x0, v0, opts)
@@ -366,7 +371,7 @@ def run_jgs2(args, rank, world, local_rank):
     if batch:
         out["scene_sweeps"] = scene_sweeps
     # kernel times: CUDA events, inside the timed steps, around every kernel group of the
-    # first sweep of each replayed chunk of the sweep graph (one sweep in check_every is
+    # last sweep of each replayed chunk of the sweep graph (one sweep in check_every is
     # sampled; the per-step setup kernels are timed in full). A sweep kernel's average is
     # its sampled time over the sampled sweeps; its time per step, that average times the
     # sweeps per step.
@@ -384,23 +389,27 @@ def run_jgs2(args, rank, world, local_rank):
             per_kernel[name] = {"avg_launch_ms": round(avg, 5), "bytes_per_launch": kb[name],
                                 "GB_s": round(kb[name] / (avg * 1e-3) / 1e9, 1),
                                 "frac": round(kb[name] / (avg * 1e-3) / 1e9 / hbm, 4)}
-    dom = max(per_kernel, key=lambda n: share[n])
-    achieved = per_kernel[dom]["GB_s"]
     out["profiled_sweeps"] = psw
     out["kernel_ms_per_step"] = {n: round(est_step[n], 4) for n in KIND}
     out["kernel_launches_per_step"] = {KIND[q]: int(kl[q] // args.steps) for q in range(len(KIND))}
     out["kernel_share"] = share
     out["kernels"] = per_kernel
-    traffic = NCU_TRAFFIC.get(dom)
-    if traffic is not None and prec == p.FP32 and not batch:
-        traffic = int(traffic * T / NCU_TRAFFIC_TETS)
+    if per_kernel:
+        dom = max(per_kernel, key=lambda n: share[n])
+        achieved = per_kernel[dom]["GB_s"]
+        traffic = NCU_TRAFFIC.get(dom)
+        if traffic is not None and prec == p.FP32 and not batch:
+            traffic = int(traffic * T / NCU_TRAFFIC_TETS)
+        else:
+            traffic = None
+        out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                           "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
+                           "bytes_per_launch": per_kernel[dom]["bytes_per_launch"],
+                           "avg_launch_ms": per_kernel[dom]["avg_launch_ms"],
+                           "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
     else:
-        traffic = None
-    out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-                       "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
-                       "bytes_per_launch": per_kernel[dom]["bytes_per_launch"],
-                       "avg_launch_ms": per_kernel[dom]["avg_launch_ms"],
-                       "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+        # every step stopped before the timed last sweep of its first chunk
+        out["roofline"] = None
     if not args.no_compare:
         out["comparisons"] = compare(args, p, mesh, ss, batch, x0, v0, stream, corr, prec)
     if rank == 0 and not args.no_cpu_baseline:
