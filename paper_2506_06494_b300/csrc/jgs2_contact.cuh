@@ -157,7 +157,7 @@ __device__ __forceinline__ double segment_segment(P3 p0, P3 p1, P3 q0, P3 q1, do
 // sweep that needs no rebuild runs the rebuild kernels as empty launches.
 // ---------------------------------------------------------------------------------------
 enum { kCtlMove = 0, kCtlRebuild = 1, kCtlForce = 2, kCtlTicket = 3, kCtlExtF = 4, kCtlExtE = 5, kCtlAcc = 6,
-       kCtlCoord = 7, kCtlNear = 8, kCtlWords = 9 };
+       kCtlCoord = 7, kCtlNear = 8, kCtlStep = 9, kCtlPath = 10, kCtlWords = 11 };
 
 __device__ __forceinline__ uint64_t cell_key(P3 p, double h) {
   const long long ix = (long long)floor(p.x / h) + (1 << 20), iy = (long long)floor(p.y / h) + (1 << 20),
@@ -198,6 +198,7 @@ __device__ __forceinline__ void emit_pair(const ContactView& c, uint64_t kind, u
   if (idx < c.cap) {
     c.pairs[idx] = (kind << 60) | (a << 30) | b;
     c.dbp[idx] = __double2float_rd(d);
+    c.pmarg[idx] = -1.f;  // no motion check yet
   } else {
     c.flags[0] = 1;
   }
@@ -246,6 +247,11 @@ __global__ void __launch_bounds__(256) k_bp_check(DevMesh<T> m, ContactView c, S
   const bool rebuild = ctl[kCtlForce] != 0u || !(double(moved) + snap_slack(c) <= c.trig);
   ctl[kCtlRebuild] = rebuild ? 1u : 0u;
   ctl[kCtlAcc] = rebuild ? 0u : __float_as_uint(moved);
+  // path bound: the sum of the sweeps' largest vertex steps since the rebuild (k_update
+  // leaves the last one in kCtlStep), rounded up; no vertex has moved farther since then
+  const float path = rebuild ? 0.f : __fadd_ru(__uint_as_float(ctl[kCtlPath]), __uint_as_float(ctl[kCtlStep]));
+  ctl[kCtlPath] = __float_as_uint(path);
+  ctl[kCtlStep] = 0u;
   ctl[kCtlMove] = 0u;
   ctl[kCtlForce] = 0u;
   ctl[kCtlTicket] = 0u;
@@ -632,15 +638,34 @@ __global__ void __launch_bounds__(256) k_pair_terms(DevMesh<T> m, ContactView c,
   if (st->done) return;
   const int n = min(*c.n_pairs, c.cap);
   const double far = c.rc + 2.0 * (double(__uint_as_float(c.ctl[kCtlAcc])) + snap_slack(c));
+  const float path = __uint_as_float(c.ctl[kCtlPath]);
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
     const double dbp = double(c.dbp[q]);
     // beyond r_c by more than any motion since the rebuild could close: global bound
-    // first (one load), then the pair's own motion relative to one of its vertices
-    if (dbp >= far ||
-        dbp - double(pair_rel_motion(m, c, c.pairs[q])) * (1.0 + 1e-5) - 4.0 * snap_slack(c) >= c.rc) {
+    // first (one load)
+    if (dbp >= far) {
       c.d0[q] = INFINITY;
       continue;
     }
+    // then the margin found at the pair's last motion check, less what the motion since
+    // then can have taken from it: every vertex has moved at most (path - ppath) since,
+    // and the pair's relative-motion bound grows by at most 4 times that (edge-edge: two
+    // relative displacements, each by at most twice the motion)
+    const float mq = c.pmarg[q];
+    if (mq >= 0.f && double(mq) - 4.0 * (double(path) - double(c.ppath[q])) * (1.0 + 1e-5) >= 0.0) {
+      c.d0[q] = INFINITY;
+      continue;
+    }
+    // then the pair's own motion relative to one of its vertices since the rebuild
+    const double marg =
+        dbp - double(pair_rel_motion(m, c, c.pairs[q])) * (1.0 + 1e-5) - 4.0 * snap_slack(c) - c.rc;
+    if (marg >= 0.0) {
+      c.pmarg[q] = __double2float_rd(marg);
+      c.ppath[q] = path;
+      c.d0[q] = INFINITY;
+      continue;
+    }
+    c.pmarg[q] = -1.f;
     int vs[4], nv;
     P3 J[4];
     const double d = pair_geom(m, c, c.pairs[q], 0.0, (const Vec4<T>*)nullptr, vs, J, nv);

@@ -76,6 +76,7 @@ Mesh::~Mesh() {
   cudaFree(d_sverts); cudaFree(d_npairs); cudaFree(d_cflags); cudaFree(d_is_surf); cudaFree(d_pairs);
   cudaFree(d_dmin); cudaFree(d_lim); cudaFree(d_frank); cudaFree(d_erank); cudaFree(d_hcnt); cudaFree(d_hblk);
   cudaFree(d_hids); cudaFree(d_hrec); cudaFree(d_hkey); cudaFree(d_fkeys); cudaFree(d_ekeys); cudaFree(d_pbp); cudaFree(d_dbp); cudaFree(d_ctl);
+  cudaFree(d_pmarg); cudaFree(d_ppath);
 }
 
 static uint64_t spread3(uint64_t x) {
@@ -388,6 +389,8 @@ static jgs2_status ensure_device(Mesh* m) {
       CK(dalloc(&m->d_pbp, V));
       CK(dalloc(&m->d_ctl, kCtlWords));
       CK(dalloc(&m->d_dbp, m->pair_cap));
+      CK(dalloc(&m->d_pmarg, m->pair_cap));
+      CK(dalloc(&m->d_ppath, m->pair_cap));
       CK(cudaMemset(m->d_ctl, 0, sizeof(uint32_t) * kCtlWords));
       CK(cudaMemset(m->d_pbp, 0, sizeof(float4) * V));
       CK(dalloc(&m->d_pairs, m->pair_cap));
@@ -579,6 +582,8 @@ static DevMesh<T> dev_view(Mesh* m) {
     c.pbp = m->d_pbp;
     c.ctl = m->d_ctl;
     c.dbp = m->d_dbp;
+    c.pmarg = m->d_pmarg;
+    c.ppath = m->d_ppath;
     c.pairs = m->d_pairs;
     c.n_pairs = m->d_npairs;
     c.cap = m->pair_cap;

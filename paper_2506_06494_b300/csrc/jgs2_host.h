@@ -109,6 +109,7 @@ struct Mesh {
   uint64_t *d_fkeys = nullptr, *d_ekeys = nullptr, *d_pairs = nullptr;
   float4* d_pbp = nullptr;
   float* d_dbp = nullptr;
+  float *d_pmarg = nullptr, *d_ppath = nullptr;
   uint32_t* d_ctl = nullptr;
   double *d_dmin = nullptr, *d_lim = nullptr;
   PrecBufs<float> f32;

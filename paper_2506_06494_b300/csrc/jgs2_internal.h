@@ -113,6 +113,9 @@ struct ContactView {
   int cap = 0;
   float* dbp = nullptr;          // [cap] distance at the last rebuild (rounded down)
   double* d0 = nullptr;          // [cap] distance at x^k (inf when provably beyond r_c)
+  float* pmarg = nullptr;        // [cap] margin beyond r_c at the pair's last motion check
+                                 // (rounded down; < 0: check again at every sweep)
+  float* ppath = nullptr;        // [cap] path bound (kCtlPath) when that margin was taken
   // per-vertex accumulators
   double* bg = nullptr;          // [3][V]
   double* bH = nullptr;          // [6][V]

@@ -1565,17 +1565,40 @@ __global__ void k_update_batch(DevMesh<T> m) {
 }
 
 template <typename T>
-__global__ void k_update(DevMesh<T> m, const StepState* __restrict__ st) {
+__global__ void __launch_bounds__(128) k_update(DevMesh<T> m, const StepState* __restrict__ st) {
   if (st->done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.Vf) return;
-  const T a = T(st->alpha);
-  Vec4<T> u = m.u[i];
-  const Vec4<T> d = st->dir ? m.DJ[i] : m.D[i];
-  u.x += a * d.x;
-  u.y += a * d.y;
-  u.z += a * d.z;
-  m.u[i] = u;
+  float step = 0.f;
+  if (i < m.Vf) {
+    const T a = T(st->alpha);
+    Vec4<T> u = m.u[i];
+    const Vec4<T> d = st->dir ? m.DJ[i] : m.D[i];
+    u.x += a * d.x;
+    u.y += a * d.y;
+    u.z += a * d.z;
+    m.u[i] = u;
+    if (m.c.on) {
+      // an upper bound of the vertex's motion for the contact skip test's path bound, in
+      // FP32: |a d| with a 1e-5 relative allowance for its own rounding, plus the rounding
+      // of u + a d (a few FP32 ulps of the new u)
+      const float dx = float(d.x), dy = float(d.y), dz = float(d.z);
+      const float ux = float(u.x), uy = float(u.y), uz = float(u.z);
+      step = fabsf(float(a)) * sqrtf(dx * dx + dy * dy + dz * dz) * (1.f + 1e-5f) +
+             3e-7f * sqrtf(ux * ux + uy * uy + uz * uz);
+    }
+  }
+  if (m.c.on) {
+    // the sweep's largest step: warp and block maxima, one atomic per block (non-negative
+    // floats order like their bit patterns)
+    __shared__ uint32_t wmax[4];
+    const uint32_t w = __reduce_max_sync(0xffffffffu, __float_as_uint(step));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const uint32_t b = max(max(wmax[0], wmax[1]), max(wmax[2], wmax[3]));
+      if (b != 0u) atomicMax(&m.c.ctl[kCtlStep], b);
+    }
+  }
 }
 
 // x_{t+1} = x_t + u, v_{t+1} = u / h, written back in caller order.
