@@ -1,0 +1,64 @@
+"""The library's host precompute (jgs2_precompute: FP64 C++ on the host, no GPU needed)
+against the oracle's (Secs. 5-6). The U_bar rows it exports equal the oracle's Eq. u rows
+at the same elements' corners. The greedy NNLS sets (Eq. cubature_weight) with their
+weights and fit residuals equal the oracle's wherever both saw the same training poses.
+On the cube that is every vertex. Elsewhere, eigenvectors of repeated eigenvalues can be
+any basis of their eigenspace, so a few vertices may legitimately pick other elements.
+Weights and residuals agree to 1e-6: the library's training poses come from block inverse
+iteration, stopped at a relative eigen-residual of 1e-8, and the oracle's from a dense
+eigensolver."""
+import numpy as np
+import pytest
+
+import paper_2506_06494_b300 as p
+import scenes
+from oracle import fem, precompute
+
+
+def lib_precompute(s):
+    g = p.Mesh.from_scene(s)
+    g.precompute(n_cub=4)
+    out = g.precompute_export()
+    g.close()
+    return out
+
+
+def test_cube_precompute_matches_oracle():
+    s = scenes.cube_scene()
+    m = fem.Mesh(s.X, s.tets, s.youngs, s.poisson, s.density, s.pinned)
+    cub = precompute.train_cubature(m, s.dt)
+    e, w, u, r = lib_precompute(s)
+    free = ~s.pinned.astype(bool)
+    assert np.array_equal(e, cub.elem)
+    assert np.allclose(w, cub.weight, rtol=1e-6, atol=1e-9)
+    assert np.max(np.abs(u - cub.ubar)) <= 1e-12 * np.max(np.abs(cub.ubar))
+    assert np.allclose(r[free], cub.residual[free], rtol=1e-6, atol=1e-9)
+
+
+def test_beam_precompute_ubar_rows_and_sets():
+    s = scenes.small_beam_scene()
+    m = fem.Mesh(s.X, s.tets, s.youngs, s.poisson, s.density, s.pinned)
+    Hbar = precompute.rest_hessian(m, s.dt)
+    Ub, _ = precompute.ubar_all(m, Hbar)
+    cub = precompute.train_cubature(m, s.dt, Hbar=Hbar)
+    e, w, u, r = lib_precompute(s)
+    free = np.nonzero(~s.pinned.astype(bool))[0]
+    scale = np.max(np.abs(Ub))
+    # every exported U_bar block is the oracle's Eq. u row of that corner (zero if pinned)
+    n_checked = 0
+    for i in free:
+        di = m.dof_of[i]
+        for k in range(e.shape[1]):
+            if e[i, k] < 0:
+                continue
+            for c, a in enumerate(s.tets[e[i, k]]):
+                da = m.dof_of[a]
+                ref = np.zeros((3, 3)) if da < 0 else Ub[di][3 * da:3 * da + 3]
+                assert np.max(np.abs(u[i, k, c] - ref)) <= 1e-12 * scale
+                n_checked += 1
+    assert n_checked > 3 * len(free)
+    same = np.all(e[free] == cub.elem[free], axis=1)
+    assert same.mean() >= 0.95
+    rows = free[same]
+    assert np.allclose(w[rows], cub.weight[rows], rtol=1e-6, atol=1e-9)
+    assert np.allclose(r[rows], cub.residual[rows], rtol=1e-6, atol=1e-9)
