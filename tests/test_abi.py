@@ -103,3 +103,27 @@ def test_null_arguments(L):
     assert L.jgs2_mesh_create(None, C.byref(h)) == 1
     assert L.jgs2_step(None, None, None, None, None, None) == 1
     assert L.jgs2_precompute_import(None, None) == 1
+
+
+def test_batch_create_validates_scenes(L):
+    """jgs2_mesh_create_batch (host-only, no GPU): scenes must share dt and gravity, and a
+    batch carries no contact."""
+    a, b = scenes.cube_scene(), scenes.cube_scene()
+    m = p.Mesh.batch([a, b])  # valid: two scenes
+    assert m.n_scenes == 2 and m.V == 2 * a.n_vertices
+    m.close()
+    b.dt = a.dt / 2
+    with pytest.raises(p.JGS2Error):
+        p.Mesh.batch([a, b])
+    b = scenes.cube_scene()
+    b.gravity = (0.0, 0.0, -1.0)
+    with pytest.raises(p.JGS2Error):
+        p.Mesh.batch([a, b])
+    keep = []
+    descs = (J.MeshDesc * 2)()
+    for k, s in enumerate([a, scenes.cube_scene()]):
+        descs[k] = J._desc(s.X, s.tets, s.youngs, s.poisson, s.density, s.pinned, s.gravity, s.dt,
+                           None, 1e-3, 1e4, 1 if k == 1 else 0, keep)
+    h = C.c_void_p()
+    assert L.jgs2_mesh_create_batch(descs, 2, C.byref(h)) == 1  # JGS2_EINVAL
+    assert not h.value
