@@ -1,0 +1,54 @@
+"""The seeded synthetic inputs follow their stated recipes (the workloads the paper's
+scenes are replaced by): sizes, pinning, materials, velocities, placement and, for the
+blobs, the tet-count target. The seeds are fixed, so these are exact."""
+import numpy as np
+
+import scenes
+
+
+def test_cube():
+    s = scenes.cube_scene()
+    assert (s.n_vertices, s.n_tets) == (125, 384)
+    assert s.pinned.sum() == 25 and np.all(s.X[s.pinned.astype(bool), 2] == s.X[:, 2].max())
+    assert np.allclose(s.X.max(0) - s.X.min(0), 0.1)
+    assert np.all(s.youngs == 1e5) and np.all(s.poisson == 0.4) and np.all(s.density == 1000.0)
+    assert np.all(s.v0 == 0.0) and s.dt == 1.0 / 120.0
+
+
+def test_beam():
+    s = scenes.beam_scene()
+    assert (s.n_vertices, s.n_tets) == (40_000, 19 * 19 * 99 * 6)
+    assert np.allclose(s.X.max(0) - s.X.min(0), [0.1, 0.02, 0.02])
+    pin = s.pinned.astype(bool)
+    assert pin.sum() == 400 and np.all(s.X[pin, 0] == 0.0)
+    assert np.all(s.youngs == 1e7) and np.all(s.poisson == 0.45)
+    assert np.all(s.v0[pin] == 0.0)
+    assert abs(s.v0[~pin].std() - 0.05) < 0.001 and abs(s.v0[~pin].mean()) < 0.001
+
+
+def test_ten_spheres():
+    s = scenes.spheres_scene()
+    assert (s.n_vertices, s.n_tets) == (634_130, 3_471_360)
+    n, t = s.n_vertices // 10, s.n_tets // 10
+    assert (n, t) == (63_413, 347_136)
+    X = s.X.reshape(10, n, 3)
+    c = X.mean(1)
+    assert np.all(c >= [0.15, 0.15, 0.5]) and np.all(c <= [0.85, 0.85, 1.9])
+    d = np.linalg.norm(c[:, None] - c[None], axis=2) + 10 * np.eye(10)
+    assert d.min() >= 2 * 0.1 + 2 * s.dhat
+    assert np.all(s.youngs[:5 * t] == 2e6) and np.all(s.youngs[5 * t:] == 1e5)
+    assert s.contact == 1 and s.dhat == 1e-3 and len(s.planes) == 5
+    for pl in s.planes:  # every vertex inside the box, well away from the walls
+        assert (s.X @ pl[:3] - pl[3]).min() > 10 * s.dhat
+    assert not s.pinned.any() and np.all(s.v0 == 0.0)
+
+
+def test_blobs_hit_their_tet_targets():
+    for i in range(8):
+        s = scenes.blob_scene(i)
+        target = scenes.blob_tet_target(i)
+        assert 1e3 <= target <= 5e4
+        assert abs(s.n_tets - target) <= 0.1 * target
+        pin = s.pinned.astype(bool)
+        assert pin.any() and np.all(np.isclose(s.X[pin, 2], s.X[:, 2].min()))
+        assert 1e4 <= s.youngs[0] <= 1e7 and 0.3 <= s.poisson[0] <= 0.48
