@@ -1,5 +1,5 @@
 """Full-space references: projected Newton (Sec. 8.3, Eq. newton_system) and the
-"exact dynamic" subspace of Secs. 4.1-4.2 used to check the optimality theorem."""
+exact dynamic subspace of Secs. 4.1-4.2 used to check the optimality theorem."""
 from __future__ import annotations
 
 import numpy as np

@@ -1,6 +1,6 @@
 """SplitMix64 (Steele, Lea & Flood, OOPSLA 2014), used for the seeded cubature draws.
 
-The paper draws cubature candidates "randomly" (Sec. 5) without naming a generator. Both
+The paper draws cubature candidates at random (Sec. 5) without naming a generator. Both
 sides implement this one published generator independently so their draws coincide.
 
 keyed(seed, a, b) derives a stream state from a seed and two integer keys by feeding the
