@@ -475,7 +475,7 @@ static void solve_inplace(const Factor& F, double* X, int nrhs) {
 
 // Multi-RHS solve: the columns are split into one contiguous chunk per thread.
 static void solve_many(const Factor& F, vector<double>& B /* n x nrhs row-major */, int n, int nrhs) {
-  const int nt = std::max(1, std::min(omp_get_max_threads(), (nrhs + 7) / 8));
+  const int nt = std::max(1, std::min(omp_get_max_threads(), (nrhs + 3) / 4));
   if (nt == 1) {
     solve_inplace(F, B.data(), nrhs);
     return;
