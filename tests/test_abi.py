@@ -127,3 +127,18 @@ def test_batch_create_validates_scenes(L):
     h = C.c_void_p()
     assert L.jgs2_mesh_create_batch(descs, 2, C.byref(h)) == 1  # JGS2_EINVAL
     assert not h.value
+
+
+@pytest.mark.parametrize("bad", [np.nan, 0.0, -1e5, np.inf])
+def test_poisoned_youngs_modulus_is_rejected(L, bad):
+    """jgs2_mesh_set_youngs validates every modulus before it changes anything (host-only
+    before the mesh reaches a device)."""
+    s = scenes.cube_scene()
+    g = p.Mesh.from_scene(s)
+    E = np.full(s.n_tets, 1e5)
+    E[17] = bad
+    with pytest.raises(p.JGS2Error) as err:
+        g.set_youngs(E)
+    assert err.value.status == 1
+    g.set_youngs(np.full(s.n_tets, 2e5))  # a valid set is accepted
+    g.close()

@@ -74,3 +74,20 @@ def test_zero_sweep_cap_returns_the_state_unchanged(cuda):
     assert rep.converged == 0 and rep.sweeps == 0 and abs(rep.rel_residual - 1.0) < 1e-12
     assert np.array_equal(x.cpu().numpy(), s.X)
     assert np.array_equal(v.cpu().numpy(), np.zeros_like(s.X))
+
+
+@pytest.mark.parametrize("prec", [p.FP64, p.FP32])
+def test_non_finite_state_is_reported_and_left_alone(cuda, prec):
+    """A NaN position makes the first residual non-finite: the step stops with
+    JGS2_EDIVERGED and writes nothing back."""
+    s = scenes.cube_scene()
+    g = p.Mesh.from_scene(s)
+    x0 = s.X.copy()
+    x0[3] = np.nan  # a free vertex
+    x, v = t(x0, cuda), t(s.v0, cuda)
+    with pytest.raises(p.JGS2Error) as err:
+        g.step(x, v, p.step_opts(precision=prec, correction=p.CORR_OFF, max_sweeps=10))
+    assert err.value.status == 6
+    xa = x.cpu().numpy()
+    assert np.all(np.isnan(xa[3])) and np.array_equal(np.delete(xa, 3, axis=0), np.delete(x0, 3, axis=0))
+    assert np.array_equal(v.cpu().numpy(), s.v0)
