@@ -78,6 +78,11 @@ typedef struct {
   double nnls_tol;     /* stop when the relative NNLS residual is below this (Sec. 5: 1%) */
   uint64_t seed;       /* SplitMix64 seed of the pool / candidate draws */
   int32_t n_threads;   /* host threads (0 = all cores) */
+  int32_t gs;          /* 1 = Gauss-Seidel groups (Sec. 8.1): free vertices greedily coloured in
+                        * caller order, each colour a generalised sub-problem whose U_bar_i
+                        * keeps the group's other DOFs fixed (one factorisation per colour).
+                        * The records suit a sweep that runs the colours in turn; jgs2_step
+                        * runs the Jacobi sweep (0, the default) */
 } jgs2_precompute_opts;
 
 /* Cubature records produced elsewhere (e.g. by an independent implementation), in the
@@ -141,7 +146,7 @@ typedef struct {
   double trace[JGS2_TRACE_MAX]; /* r_k per sweep if record_trace */
 } jgs2_step_report;
 
-/* Default option values (n_cub 4, n_train 20, n_cand 32, n_pool 256, tol 0.01, seed 0). */
+/* Default option values (n_cub 4, n_train 20, n_cand 32, n_pool 256, tol 0.01, seed 0, gs 0). */
 void jgs2_precompute_opts_default(jgs2_precompute_opts* o);
 /* Defaults: max_sweeps 500, rel_tol 1e-4, FP32, asm, line search on, check_every 16. */
 void jgs2_step_opts_default(jgs2_step_opts* o);

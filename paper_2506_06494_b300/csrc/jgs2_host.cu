@@ -1728,6 +1728,7 @@ void jgs2_precompute_opts_default(jgs2_precompute_opts* o) {
   o->nnls_tol = 0.01;
   o->seed = 0;
   o->n_threads = 0;
+  o->gs = 0;
 }
 
 void jgs2_step_opts_default(jgs2_step_opts* o) {

@@ -812,6 +812,220 @@ static jgs2_status body_precompute(const Mesh& M, const vector<int>& bverts, con
   vector<int> pv_slot(nf, -1);
   for (size_t q = 0; q < pv.size(); ++q) pv_slot[pv[q]] = (int)q;
   const int np = (int)pv.size();
+  if (o.gs) {
+    // ---- Gauss-Seidel groups (Sec. 8.1): greedy colouring of the free vertices in caller
+    // order; each colour is one generalised sub-problem whose U_bar_i^G keeps the group's
+    // other DOFs at zero: on C = the free vertices of the other colours,
+    // U_bar_{i,a}^G = -sum_c (H_CC^{-1})_{a,c} H_{c,i} over the neighbours c of i in C.
+    vector<int> colour(nf, -1);
+    int ncol = 0;
+    for (int f = 0; f < nf; ++f) {  // free index order = body-local (caller) order
+      vector<char> used(nf + 1, 0);
+      for (int c : adj[f])
+        if (c < f && colour[c] >= 0) used[colour[c]] = 1;
+      int k = 0;
+      while (used[k]) ++k;
+      colour[f] = k;
+      ncol = std::max(ncol, k + 1);
+    }
+    // full 3x3 blocks H_{r,c} of the rest Hessian by free index (both triangles)
+    auto Hblock = [&](int r, int c, double* out9) {
+      const bool lower = pos[r] >= pos[c];
+      const BlockCol& col = H[lower ? pos[c] : pos[r]];
+      const int row = lower ? pos[r] : pos[c];
+      const auto it = std::lower_bound(col.row.begin(), col.row.end(), row);
+      if (it == col.row.end() || *it != row) {
+        std::fill(out9, out9 + 9, 0.0);
+        return;
+      }
+      const double* b = &col.val[9 * (size_t)(it - col.row.begin())];
+      for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) out9[3 * a + k] = lower ? b[3 * a + k] : b[3 * k + a];
+    };
+    // training poses in free-index order
+    vector<double> qf((size_t)nt * n);
+    for (int j = 0; j < nt; ++j)
+      for (int f = 0; f < nf; ++f)
+        for (int a = 0; a < 3; ++a) qf[(size_t)j * n + 3 * f + a] = Q[(size_t)(3 * pos[f] + a) * p + j];
+    vector<vector<int>> inc(nvb);
+    for (int e = 0; e < ne; ++e)
+      for (int a = 0; a < 4; ++a) inc[tl[4 * e + a]].push_back(e);
+    for (int g = 0; g < ncol; ++g) {
+      // H_CC in the body's factor order restricted to C
+      vector<int> cidx(nf, -1), corder;
+      for (int k = 0; k < nf; ++k)
+        if (colour[ord[k]] != g) {
+          cidx[ord[k]] = (int)corder.size();
+          corder.push_back(ord[k]);
+        }
+      const int nC = (int)corder.size(), n3 = 3 * nC;
+      vector<int> G;
+      for (int f = 0; f < nf; ++f)
+        if (colour[f] == g) G.push_back(f);
+      vector<double> Z, GC;  // Z: H_CC^{-1} q_C (n3 x nt); GC: H_CC^{-1} at pool columns
+      vector<int> cslot(np, -1);
+      int npc = 0;
+      if (nC > 0) {
+        vector<BlockCol> Hc(nC);
+        for (int kc = 0; kc < nC; ++kc) {
+          const BlockCol& col = H[pos[corder[kc]]];
+          for (size_t q = 0; q < col.row.size(); ++q) {
+            const int rf = ord[col.row[q]];
+            if (cidx[rf] < 0) continue;
+            Hc[kc].row.push_back(cidx[rf]);
+            Hc[kc].val.insert(Hc[kc].val.end(), col.val.begin() + 9 * q, col.val.begin() + 9 * q + 9);
+          }
+        }
+        Factor Fc;
+        if (!factorize(nC, Hc, Fc)) {
+          err = "rest Hessian restricted to a colour's complement is not positive definite";
+          return JGS2_EINVAL;
+        }
+        Z.assign((size_t)n3 * nt, 0.0);
+        for (int kc = 0; kc < nC; ++kc)
+          for (int a = 0; a < 3; ++a)
+            for (int t = 0; t < nt; ++t) Z[(size_t)(3 * kc + a) * nt + t] = qf[(size_t)t * n + 3 * corder[kc] + a];
+        solve_many(Fc, Z, n3, nt);
+        for (int q = 0; q < np; ++q)
+          if (cidx[pv[q]] >= 0) cslot[q] = npc++;
+        GC.assign((size_t)nC * npc * 9, 0.0);  // [kc][slot] 3x3: (H_CC^{-1})_{c, pool vertex}
+        const int batch = 384;
+        vector<int> pcols;
+        for (int q = 0; q < np; ++q)
+          if (cslot[q] >= 0) pcols.push_back(q);
+        for (int q0 = 0; q0 < 3 * npc; q0 += batch) {
+          const int k = std::min(batch, 3 * npc - q0);
+          vector<double> Bm((size_t)n3 * k, 0.0);
+          for (int j = 0; j < k; ++j) {
+            const int col = q0 + j;
+            Bm[(size_t)(3 * cidx[pv[pcols[col / 3]]] + col % 3) * k + j] = 1.0;
+          }
+          solve_many(Fc, Bm, n3, k);
+          for (int kc = 0; kc < nC; ++kc)
+            for (int j = 0; j < k; ++j) {
+              const int col = q0 + j, sl = col / 3, c = col % 3;
+              for (int a = 0; a < 3; ++a) GC[((size_t)kc * npc + sl) * 9 + 3 * a + c] = Bm[(size_t)(3 * kc + a) * k + j];
+            }
+        }
+      }
+#pragma omp parallel for schedule(dynamic, 8)
+      for (int gi = 0; gi < (int)G.size(); ++gi) {
+        const int f = G[gi], lv = fverts[f];
+        // neighbours of i in C with H_{c,i}
+        vector<int> nb_c;
+        vector<double> Hci;
+        for (int c : adj[f])
+          if (cidx[c] >= 0) {
+            double b9[9];
+            Hblock(c, f, b9);
+            nb_c.push_back(c);
+            Hci.insert(Hci.end(), b9, b9 + 9);
+          }
+        // target b_t = lam_t (U_bar_i^T q_t - q_ti) = -lam_t sum_c H_{i,c} (H_CC^{-1} q_t)_c
+        vector<double> bt((size_t)3 * nt, 0.0), nbv(nt);
+        double nbmax = 0.0;
+        for (int t = 0; t < nt; ++t) {
+          for (size_t m2 = 0; m2 < nb_c.size(); ++m2) {
+            const double* hb = &Hci[9 * m2];  // H_{c,i}: rows c, cols i; H_{i,c} = hb^T
+            const double* z = &Z[(size_t)(3 * cidx[nb_c[m2]]) * nt + t];
+            for (int a = 0; a < 3; ++a)
+              bt[3 * t + a] -= lam[t] * (hb[a] * z[0] + hb[3 + a] * z[(size_t)nt] + hb[6 + a] * z[(size_t)2 * nt]);
+          }
+          nbv[t] = std::sqrt(bt[3 * t] * bt[3 * t] + bt[3 * t + 1] * bt[3 * t + 1] + bt[3 * t + 2] * bt[3 * t + 2]);
+          nbmax = std::max(nbmax, nbv[t]);
+        }
+        // U_bar_{i,a}^G for a free vertex a (zero inside the group)
+        auto ubar_block = [&](int fa, double* U) {
+          std::fill(U, U + 9, 0.0);
+          if (cidx[fa] < 0) return;
+          const int sl = cslot[pv_slot[fa]];
+          for (size_t m2 = 0; m2 < nb_c.size(); ++m2) {
+            const double* gq = &GC[((size_t)cidx[nb_c[m2]] * npc + sl) * 9];  // (H_CC^{-1})_{c,a}
+            const double* hb = &Hci[9 * m2];
+            // U_{a,i} -= (H_CC^{-1})_{a,c} H_{c,i} = gq^T hb
+            for (int r = 0; r < 3; ++r)
+              for (int c = 0; c < 3; ++c)
+                U[3 * r + c] -= gq[r] * hb[c] + gq[3 + r] * hb[3 + c] + gq[6 + r] * hb[6 + c];
+          }
+        };
+        vector<int> keep;
+        for (int t = 0; t < nt; ++t)
+          if (nbv[t] > 1e-12 * std::max(nbmax, 1e-300)) keep.push_back(t);
+        const int mrows = 3 * (int)keep.size();
+        vector<double> y(mrows);
+        for (size_t r = 0; r < keep.size(); ++r)
+          for (int a = 0; a < 3; ++a) y[3 * r + a] = bt[3 * keep[r] + a] / nbv[keep[r]];
+        double ynorm = 0.0;
+        for (double v : y) ynorm += v * v;
+        ynorm = std::sqrt(ynorm);
+        auto column = [&](int e, double* col) {
+          for (int r = 0; r < mrows; ++r) col[r] = 0.0;
+          for (int a = 0; a < 4; ++a) {
+            const int fa = fid[tl[4 * e + a]];
+            if (fa < 0) continue;
+            double U[9];
+            ubar_block(fa, U);
+            for (size_t r = 0; r < keep.size(); ++r) {
+              const int t = keep[r];
+              const double* qa = &qf[(size_t)t * n + 3 * fa];
+              for (int c = 0; c < 3; ++c)
+                col[3 * r + c] += lam[t] * (U[c] * qa[0] + U[3 + c] * qa[1] + U[6 + c] * qa[2]) / nbv[t];
+            }
+          }
+        };
+        vector<int> sel;
+        vector<double> w_sel, Acols;
+        double res = 1.0;
+        for (int r = 0; r < nc && mrows > 0; ++r) {
+          if (res < o.nnls_tol) break;
+          vector<int> elig;
+          for (int e : pool) {
+            if (std::find(sel.begin(), sel.end(), e) != sel.end()) continue;
+            if (std::find(inc[lv].begin(), inc[lv].end(), e) != inc[lv].end()) continue;
+            elig.push_back(e);
+          }
+          vector<int> cands = draw(keyed(o.seed, (uint64_t)lv, (uint64_t)r), elig, o.n_cand);
+          double best = 0.0;
+          int best_e = -1;
+          vector<double> best_w;
+          const int k = (int)sel.size() + 1;
+          vector<double> Am((size_t)mrows * k);
+          std::copy(Acols.begin(), Acols.end(), Am.begin());
+          for (int c : cands) {
+            column(c, &Am[(size_t)(k - 1) * mrows]);
+            vector<double> wc;
+            const double rn = nnls(Am, mrows, k, y, wc) / ynorm;
+            if (best_e < 0 || rn < best || (rn == best && c < best_e)) {
+              best = rn;
+              best_e = c;
+              best_w = wc;
+            }
+          }
+          if (best_e < 0) break;
+          sel.push_back(best_e);
+          w_sel = best_w;
+          res = best;
+          Acols.resize((size_t)mrows * k);
+          column(best_e, &Acols[(size_t)(k - 1) * mrows]);
+        }
+        out.resid[lv] = res;
+        for (size_t s2 = 0; s2 < sel.size(); ++s2) {
+          const int e = sel[s2];
+          out.elem_local[(size_t)lv * nc + s2] = e;
+          out.w[(size_t)lv * nc + s2] = w_sel[s2];
+          for (int a = 0; a < 4; ++a) {
+            const int fa = fid[tl[4 * e + a]];
+            if (fa < 0) continue;
+            double U[9];
+            ubar_block(fa, U);
+            for (int q = 0; q < 9; ++q) out.u[((size_t)lv * nc + s2) * 36 + 9 * a + q] = U[q];
+          }
+        }
+      }
+    }
+    PHASE("gs groups");
+    return JGS2_OK;
+  }
   // rows of H^{-1} at the pool vertices: G[f][q] = (H^{-1})_{f, pv[q]} (3x3), f free index
   // FP64 when it fits in 2 GB, else FP32 (rows of H^-1 only shape the cubature)
   const bool g64 = (size_t)nf * np * 9 <= ((size_t)1 << 28);

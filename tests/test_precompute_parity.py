@@ -62,3 +62,37 @@ def test_beam_precompute_ubar_rows_and_sets():
     rows = free[same]
     assert np.allclose(w[rows], cub.weight[rows], rtol=1e-6, atol=1e-9)
     assert np.allclose(r[rows], cub.residual[rows], rtol=1e-6, atol=1e-9)
+
+
+@pytest.mark.parametrize("name", ["cube", "beam"])
+def test_gs_group_precompute_matches_oracle(name):
+    """jgs2_precompute with gs = 1 (Sec. 8.1 groups) against oracle/gs.py: every exported
+    U_bar block is the oracle's group U_bar row (zero inside the group), and the greedy
+    sets, weights and residuals agree wherever both picked the same elements."""
+    from oracle import gs
+    s = scenes.cube_scene() if name == "cube" else scenes.small_beam_scene()
+    m = fem.Mesh(s.X, s.tets, s.youngs, s.poisson, s.density, s.pinned)
+    col = gs.greedy_colouring(m)
+    Hbar = precompute.rest_hessian(m, s.dt)
+    Ub = gs.ubar_groups(m, Hbar, col)
+    cub = gs.train_cubature_gs(m, s.dt, col, Hbar=Hbar)
+    g = p.Mesh.from_scene(s)
+    g.precompute(n_cub=4, gs=1)
+    e, w, u, r = g.precompute_export()
+    g.close()
+    free = np.nonzero(~s.pinned.astype(bool))[0]
+    scale = np.max(np.abs(Ub))
+    for i in free:
+        di = m.dof_of[i]
+        for k in range(e.shape[1]):
+            if e[i, k] < 0:
+                continue
+            for c, a in enumerate(s.tets[e[i, k]]):
+                da = m.dof_of[a]
+                ref = np.zeros((3, 3)) if da < 0 else Ub[di][3 * da:3 * da + 3]
+                assert np.max(np.abs(u[i, k, c] - ref)) <= 1e-12 * scale
+    same = np.all(e[free] == cub.elem[free], axis=1)
+    assert same.mean() >= 0.95
+    rows = free[same]
+    assert np.allclose(w[rows], cub.weight[rows], rtol=1e-5, atol=1e-8)
+    assert np.allclose(r[rows], cub.residual[rows], rtol=1e-5, atol=1e-8)
