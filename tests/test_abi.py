@@ -39,7 +39,7 @@ def test_default_options(L):
     assert o.max_sweeps == 500 and o.rel_tol == 1e-4 and o.precision == p.FP32
     assert o.correction == p.CORR_ASM and o.line_search == 1
     q = p.precompute_opts()
-    assert q.n_cub == 4 and q.n_train == 20 and q.n_cand == 32 and q.nnls_tol == 0.01
+    assert q.n_cub == 4 and q.n_train == 20 and q.n_cand == 32 and q.nnls_tol == 0.01 and q.gs == 0
 
 
 def _desc(X, T, E, nu, rho, pin=None, dt=1 / 120):
