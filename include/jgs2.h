@@ -207,6 +207,17 @@ int32_t jgs2_mesh_n_cub(const jgs2_mesh* mesh);
 jgs2_status jgs2_step(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts,
                       void* stream, jgs2_step_report* report);
 
+/* The same step by Gauss-Seidel sweeps (Sec. 8.1): the free vertices are coloured greedily
+ * in caller order (no two of a colour share a tet); a GS sweep runs the colours in turn,
+ * each as one sweep whose directions and line search move only that colour, at the
+ * positions the earlier colours left. Use it with records from jgs2_precompute(gs = 1)
+ * (or import) or with correction = JGS2_CORR_OFF. The relative residual is taken in FP64 at
+ * the start of each GS sweep; report->sweeps counts GS sweeps and the trace holds their
+ * residuals. x, v: device [V][3] double as in jgs2_step. Meshes with contact or batches
+ * return JGS2_EINVAL. The profile fields of the report are not filled. */
+jgs2_status jgs2_step_gs(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts,
+                         void* stream, jgs2_step_report* report);
+
 /* Same step with HOST arrays: copies x, v to the device, steps, copies back. */
 jgs2_status jgs2_step_host(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts,
                            void* stream, jgs2_step_report* report);

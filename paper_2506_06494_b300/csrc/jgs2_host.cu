@@ -77,6 +77,7 @@ Mesh::~Mesh() {
   cudaFree(d_dmin); cudaFree(d_lim); cudaFree(d_frank); cudaFree(d_erank); cudaFree(d_hcnt); cudaFree(d_hblk);
   cudaFree(d_hids); cudaFree(d_hrec); cudaFree(d_hkey); cudaFree(d_fkeys); cudaFree(d_ekeys); cudaFree(d_pbp); cudaFree(d_dbp); cudaFree(d_ctl);
   cudaFree(d_pmarg); cudaFree(d_ppath);
+  cudaFree(d_gsmask); cudaFree(d_vmask); cudaFree(d_gs_xt); cudaFree(d_gs_xk); cudaFree(d_gs_g);
 }
 
 static uint64_t spread3(uint64_t x) {
@@ -523,6 +524,7 @@ static DevMesh<T> dev_view(Mesh* m) {
   d.V = m->V;
   d.Vf = m->Vf;
   d.T_ = m->T;
+  d.vmask = m->vmask_on ? m->d_vmask : nullptr;
   d.n_slices = m->n_slices;
   d.nP = m->nP;
   d.n_cub = m->n_cub;
@@ -1711,6 +1713,114 @@ jgs2_status step_adjoint(Mesh* m, const double* xt, const double* vt, const doub
                                    : adjoint_impl<float>(m, xt, vt, x1, gx1, gv1, gx, gv, gE, o, s, rep);
 }
 
+// v_{t+1} = (x_{t+1} - x_t) / h over 3V doubles (caller order).
+static __global__ void k_gs_velocity(const double* __restrict__ x1, const double* __restrict__ xt,
+                                     double* __restrict__ v, int n, double ih) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) v[q] = (x1[q] - xt[q]) * ih;
+}
+
+// Gauss-Seidel step (Sec. 8.1; readings R19-R21): the free vertices are coloured greedily in
+// caller order; a GS sweep runs the colours in turn, each as one sweep of the Jacobi
+// machinery whose directions are masked to the colour (the line search then moves only that
+// colour). The relative residual is taken in FP64 at the start of each GS sweep.
+jgs2_status step_gs(Mesh* m, double* x, double* v, const jgs2_step_opts* o, void* stream,
+                    jgs2_step_report* rep) {
+  if (!m || !x || !v) return fail(JGS2_EINVAL, "null argument");
+  jgs2_status st = check_opts(m, o);
+  if (st != JGS2_OK) return st;
+  if (m->contact || m->n_scenes > 0)
+    return fail(JGS2_EINVAL, "the Gauss-Seidel step takes single scenes without contact");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int V = m->V, Vf = m->Vf;
+  const size_t n3 = 3 * (size_t)V;
+  if (!m->d_gsmask && Vf > 0) {
+    // greedy colouring in caller order over the free vertices that share a tet
+    std::vector<std::vector<int>> nbr(V);
+    for (int t = 0; t < m->T; ++t)
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b)
+          if (a != b) nbr[m->tets_c[4 * (size_t)t + a]].push_back(m->tets_c[4 * (size_t)t + b]);
+    std::vector<int> col(V, -1);
+    int ncol = 0;
+    for (int c = 0; c < V; ++c) {
+      if (m->pinned[c]) continue;
+      std::vector<char> used(nbr[c].size() + 1, 0);
+      for (int u : nbr[c])
+        if (col[u] >= 0 && col[u] < (int)used.size()) used[col[u]] = 1;
+      int k = 0;
+      while (used[k]) ++k;
+      col[c] = k;
+      ncol = std::max(ncol, k + 1);
+    }
+    std::vector<uint8_t> masks((size_t)ncol * Vf, 0);
+    for (int i = 0; i < Vf; ++i) masks[(size_t)col[m->perm[i]] * Vf + i] = 1;
+    CK(dalloc(&m->d_gsmask, masks.size()));
+    CK(cudaMemcpy(m->d_gsmask, masks.data(), masks.size(), cudaMemcpyHostToDevice));
+    CK(dalloc(&m->d_vmask, (size_t)Vf));
+    CK(dalloc(&m->d_gs_xt, n3));
+    CK(dalloc(&m->d_gs_xk, n3));
+    CK(dalloc(&m->d_gs_g, n3));
+    m->gs_ncol = ncol;
+  }
+  if (rep) std::memset(rep, 0, sizeof(*rep));
+  if (Vf == 0) {
+    // no free vertex: x_{t+1} = x_t, v_{t+1} = 0
+    CK(cudaMemsetAsync(v, 0, sizeof(double) * n3, s));
+    CK(cudaStreamSynchronize(s));
+    if (rep) rep->converged = 1;
+    return JGS2_OK;
+  }
+  CK(cudaMemcpyAsync(m->d_gs_xt, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(m->d_gs_xk, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s));
+  std::vector<double> g(n3);
+  double g0 = 0.0, r = 0.0;
+  int k = 0;
+  bool conv = false;
+  for (;;) {
+    st = energy_gradient(m, m->d_gs_xt, v, m->d_gs_xk, nullptr, m->d_gs_g, s);
+    if (st != JGS2_OK) return st;
+    CK(cudaMemcpy(g.data(), m->d_gs_g, sizeof(double) * n3, cudaMemcpyDeviceToHost));
+    double gn = 0.0;
+    for (double q : g) gn += q * q;  // pinned rows are zero
+    gn = std::sqrt(gn);
+    if (k == 0) g0 = gn;
+    r = g0 > 0.0 ? gn / g0 : 0.0;
+    if (!std::isfinite(r)) return fail(JGS2_EDIVERGED, "residual became non-finite; state not written");
+    if (rep && k < JGS2_TRACE_MAX && o->record_trace) {
+      rep->trace[k] = r;
+      rep->trace_len = k + 1;
+    }
+    if (r <= o->rel_tol || g0 == 0.0) {
+      conv = true;
+      break;
+    }
+    if (k >= o->max_sweeps) break;
+    for (int c = 0; c < m->gs_ncol; ++c) {
+      CK(cudaMemcpyAsync(m->d_vmask, m->d_gsmask + (size_t)c * Vf, (size_t)Vf, cudaMemcpyDeviceToDevice, s));
+      m->vmask_on = true;
+      st = sweeps(m, m->d_gs_xt, v, m->d_gs_xk, 1, o, stream);
+      m->vmask_on = false;
+      if (st != JGS2_OK) return st;
+      if (m->h_state->status != 0)
+        return fail((jgs2_status)m->h_state->status, "a Gauss-Seidel colour pass failed; state not written");
+    }
+    ++k;
+  }
+  CK(cudaMemcpyAsync(x, m->d_gs_xk, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s));
+  k_gs_velocity<<<(int)((n3 + 255) / 256), 256, 0, s>>>(m->d_gs_xk, m->d_gs_xt, v, (int)n3, 1.0 / m->h);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  if (rep) {
+    rep->sweeps = k;
+    rep->converged = conv ? 1 : 0;
+    rep->rel_residual = r;
+    rep->g0 = g0;
+  }
+  if (!conv) return fail(JGS2_ENOTCONVERGED, "max_sweeps reached before rel_tol");
+  return JGS2_OK;
+}
+
 }  // namespace jgs2
 
 // ------------------------------------------------------------------ C ABI
@@ -1786,6 +1896,11 @@ jgs2_status jgs2_precompute_export(const jgs2_mesh* mesh, int32_t* elem, double*
 jgs2_status jgs2_step(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts, void* stream,
                       jgs2_step_report* report) {
   return step(reinterpret_cast<Mesh*>(mesh), x, v, opts, stream, report);
+}
+
+jgs2_status jgs2_step_gs(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts, void* stream,
+                         jgs2_step_report* report) {
+  return step_gs(reinterpret_cast<Mesh*>(mesh), x, v, opts, stream, report);
 }
 
 jgs2_status jgs2_step_host(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts, void* stream,

@@ -110,6 +110,11 @@ struct Mesh {
   float4* d_pbp = nullptr;
   float* d_dbp = nullptr;
   float *d_pmarg = nullptr, *d_ppath = nullptr;
+  // Gauss-Seidel step: per-colour masks [ncol][Vf], the active mask, scratch states
+  uint8_t *d_gsmask = nullptr, *d_vmask = nullptr;
+  int gs_ncol = 0;
+  bool vmask_on = false;
+  double *d_gs_xt = nullptr, *d_gs_xk = nullptr, *d_gs_g = nullptr;
   uint32_t* d_ctl = nullptr;
   double *d_dmin = nullptr, *d_lim = nullptr;
   PrecBufs<float> f32;

@@ -149,6 +149,8 @@ struct DevMesh {
   Vec4<T>* dz;              // [Vf]
   Vec4<T>* D;               // [Vf] JGS2 direction
   Vec4<T>* DJ;              // [Vf] uncorrected direction -H_ii^{-1} g_i
+  const uint8_t* vmask;     // [Vf] or null: vertices that move in this sweep (a Gauss-Seidel
+                            // colour); the others get D = D_J = 0
   T* ghr;                   // [18][Vf] g_i, H_ii (6), R_i (9) between the two sweep phases
   const T* mh2;             // [V] m_v / h^2 (0 for pinned)
   int cs;                   // row stride of the cubature records: Vf rounded up to 4

@@ -1009,6 +1009,7 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
       T rg[3] = {-g[0], -g[1], -g[2]};
       if (!chol3_solve(H, rg, dj)) dj[0] = dj[1] = dj[2] = T(0);
       truncate3(dj, lim);
+      if (m.vmask && !m.vmask[i]) dj[0] = dj[1] = dj[2] = T(0);  // not this colour
     }
     Vec4<T> djv{dj[0], dj[1], dj[2], T(0)};
     m.DJ[i] = djv;
@@ -1107,6 +1108,7 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 512 : 256) / BS) k_corre
     } else if (m.c.on) {
       truncate3(d, T(m.c.lim[i]));
     }
+    if (m.vmask && !m.vmask[i]) d[0] = d[1] = d[2] = T(0);  // not this colour
     Vec4<T> dv{d[0], d[1], d[2], T(0)};
     m.D[i] = dv;
 #pragma unroll

@@ -75,7 +75,7 @@ _lib = None
 
 EXPORTS = ["jgs2_precompute_opts_default", "jgs2_step_opts_default", "jgs2_mesh_create",
            "jgs2_precompute", "jgs2_precompute_import", "jgs2_precompute_export",
-           "jgs2_mesh_n_cub", "jgs2_step", "jgs2_step_host", "jgs2_sweeps",
+           "jgs2_mesh_n_cub", "jgs2_step", "jgs2_step_gs", "jgs2_step_host", "jgs2_sweeps",
            "jgs2_energy_gradient", "jgs2_energy_gradient_static", "jgs2_contact_pairs",
            "jgs2_step_adjoint", "jgs2_adjoint_opts_default", "jgs2_mesh_set_youngs",
            "jgs2_mesh_create_batch", "jgs2_batch_report", "jgs2_autotune",
@@ -100,6 +100,7 @@ def lib():
     L.jgs2_mesh_n_cub.argtypes = [P]
     L.jgs2_mesh_n_cub.restype = C.c_int32
     L.jgs2_step.argtypes = [P, P, P, C.POINTER(StepOpts), P, C.POINTER(StepReport)]
+    L.jgs2_step_gs.argtypes = [P, P, P, C.POINTER(StepOpts), P, C.POINTER(StepReport)]
     L.jgs2_step_host.argtypes = [P, P, P, C.POINTER(StepOpts), P, C.POINTER(StepReport)]
     L.jgs2_sweeps.argtypes = [P, P, P, P, C.c_int32, C.POINTER(StepOpts), P]
     L.jgs2_energy_gradient.argtypes = [P, P, P, P, P, P, P]
@@ -305,6 +306,15 @@ class Mesh:
         rep = report if report is not None else StepReport()
         st = lib().jgs2_step(self.handle, _dev(x), _dev(v), C.byref(opts), C.c_void_p(_stream_ptr(stream)),
                              C.byref(rep))
+        _check(st, ok=(0, 5))
+        return rep
+
+    def step_gs(self, x, v, opts=None, stream=None, report=None):
+        """jgs2_step_gs (Gauss-Seidel sweeps) on float64 CUDA tensors x, v [V,3]."""
+        opts = opts or step_opts()
+        rep = report if report is not None else StepReport()
+        st = lib().jgs2_step_gs(self.handle, _dev(x), _dev(v), C.byref(opts), C.c_void_p(_stream_ptr(stream)),
+                                C.byref(rep))
         _check(st, ok=(0, 5))
         return rep
 
