@@ -142,3 +142,17 @@ def test_poisoned_youngs_modulus_is_rejected(L, bad):
     assert err.value.status == 1
     g.set_youngs(np.full(s.n_tets, 2e5))  # a valid set is accepted
     g.close()
+
+
+def test_gs_step_rejects_contact_and_batches(L):
+    """jgs2_step_gs takes single scenes without contact; the check comes before any device
+    work, so dummy host pointers never reach a kernel."""
+    dummy = np.zeros(3)
+    ptr = dummy.ctypes.data_as(C.c_void_p)
+    opts = p.step_opts(correction=p.CORR_OFF)
+    drop = p.Mesh.from_scene(scenes.drop_scene())
+    assert L.jgs2_step_gs(drop.handle, ptr, ptr, C.byref(opts), None, None) == 1  # JGS2_EINVAL
+    drop.close()
+    batch = p.Mesh.batch([scenes.cube_scene(), scenes.cube_scene()])
+    assert L.jgs2_step_gs(batch.handle, ptr, ptr, C.byref(opts), None, None) == 1
+    batch.close()
