@@ -1,4 +1,5 @@
-"""Plain FP64 CPU oracle for the JGS2 per-vertex Jacobi sweep (test infrastructure only).
+"""Plain FP64 CPU oracle for the JGS2 per-vertex Jacobi sweep and its Gauss-Seidel mode
+(test infrastructure only).
 
 This package is the checker, not the product: only `tests/`, `__graft_entry__.smoke()` and
 the CPU-baseline leg of `bench.py` may import it. It shares no code with the CUDA path;
@@ -7,11 +8,13 @@ the method.
 
 Every function states the passage of the paper (Lan et al., "JGS2: Near Second-order
 Converging Jacobi/Gauss-Seidel for GPU Elastodynamics") it follows. Readings of passages
-the paper leaves open are listed in `oracle/readings.py` and in the design notes.
+the paper leaves open are stated in the module docstrings (sweep.py, gs.py, contact.py)
+and in the design notes.
 
 Pins (tests/test_oracle_*.py): finite differences, rest-state closed forms, the
 Schur-complement / KKT identities of Sec. 6, the optimality theorem of Sec. 4.2, rigid
 rotation and translation invariance, the fixed point against a projected Newton solve,
-and the convergence-rate claim of Sec. 8. Parity is pinned for every function here
-except the cubature candidate draw, whose random choices are compared by fit residual.
+the convergence-rate claim of Sec. 8, and the Gauss-Seidel groups against the Jacobi
+path. Parity is pinned for every function here except the cubature candidate draw, whose
+random choices are compared by fit residual.
 """
