@@ -879,7 +879,7 @@ static jgs2_status ensure_gstream(Mesh* m) {
 // flags the step done (converged, diverged or max_k sweeps). Sweeps after that flag are
 // empty launches. With check = false the host does not wait between replays and runs
 // ceil((max_k + 1) / chunk) of them. Profiling puts external event nodes around every
-// kernel group of the chunk; their times are read after each replay.
+// kernel group of the chunk's last sweep; their times are read after each replay.
 template <typename T>
 static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs, int max_k, double rel_tol,
                               bool check, StepState* hs, Launches& L) {

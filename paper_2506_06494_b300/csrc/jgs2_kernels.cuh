@@ -1,16 +1,20 @@
 // Device code of the JGS2 sweep (sm_103a). One sweep k from x^k = x_t + u:
-//   k_pool    per cubature element: assembled gradient and rotation of its corners,
-//             the element Hessian at x^k rotated into the rest frames of its corners
-//             (the R_a factors of Eq. tilde_phi), and the rotated corner gradients.
-//   k_gather  per free vertex: gather g_i, H_ii and the volume-weighted deformation
-//             gradient from the incident tets, R_i = polar(F_i), the uncorrected
-//             direction D_J, FP64 partial sums |g|^2 and g.D_J.
-//   k_correct per free vertex: the cubature sums H~_i, g~_i (Eq. cubature), the 3x3
-//             solve of Eq. reduced_local, the direction D_i and g.D.
-//   k_energy  (line search) per tet and per free vertex: exact energy differences
-//             E(x + alpha_j D) - E(x) for alpha_j = 2^-j, FP64 sums; the last block
-//             picks the Armijo step.
-//   k_update  u += alpha D.
+//   k_elem       per tet: F_e(x^k) into the element records (tiles staged in shared memory).
+//   k_gather     per free vertex: g_i, H_ii and the volume-weighted deformation gradient
+//                from the incident element records, R_i = polar(F_i), the uncorrected
+//                direction D_J, FP64-class partial sums |g|^2 and g.D_J.
+//   k_pool       per cubature pool element: the element Hessian at x^k rotated into the
+//                rest frames of its corners (the R_a factors of Eq. tilde_phi) and the
+//                rotated corner gradients, from the gather's g and R.
+//   k_correct    per free vertex: the cubature sums H~_i, g~_i (Eq. cubature), the 3x3
+//                solve of Eq. reduced_local, the direction D_i and g.D; its last block
+//                closes the sweep's reduction (residual, stopping test).
+//   k_pair_trials, k_energy, k_ls_decide  (line search, reading R17): the barrier and the
+//                exact elastic/inertial energy change E(x + alpha_j d) - E(x) for
+//                alpha_j = 2^-j along the pass's direction(s); one block picks the step.
+//   k_update     u += alpha d.
+// A Gauss-Seidel colour pass runs the same kernels with a vertex mask (DevMesh::vmask):
+// vertices off the colour get D = D_J = 0.
 #pragma once
 #include <cuda_runtime.h>
 
