@@ -139,8 +139,8 @@ def sweep_bytes(V_f, T, n_cub, fp_bytes=4):
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of
-# one launch, FP32, 2 voxel spheres: 694,272 tets, 126,826 free vertices; summaries and
-# commands in profiles/sweep_kernels_spheres2_fp32.md; k_energy is its one-direction pass).
+# one launch, FP32, 2 voxel spheres: 694,272 tets, 126,826 free vertices; k_energy is its
+# one-direction pass).
 # It grows in proportion to the tets, so a launch on another mesh is credited with
 # traffic x T / 694,272. Only kernels whose code has not changed since their capture are
 # listed.
@@ -321,7 +321,10 @@ def run_jgs2(args, rank, world, local_rank):
     kms = np.sum([q[3] for q in reps], axis=0)
     kl = np.sum([q[4] for q in reps], axis=0)
     launches = int(sum(q[5] for q in reps))
-    ms_step = ms_total / args.steps / world   # whole-job time per step: `world` replicas in parallel
+    # time per step of the whole job: every rank advances its own scene (replica) or shard by
+    # one step in that time, the slowest rank setting it; aggregate throughput is reported
+    # separately (scene steps and sweeps per second over all ranks)
+    ms_step = ms_total / args.steps
     # end to end: host buffers through jgs2_step_host, copies inside the timed region
     xh, vh = X.copy(), V0.copy()
     opts_e2e = p.step_opts(precision=prec, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4)
@@ -330,7 +333,9 @@ def run_jgs2(args, rank, world, local_rank):
     t0 = time.perf_counter()
     for _ in range(n_e2e):
         mesh.step_host(xh, vh, opts_e2e, stream)
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / max(n_e2e, 1) / world if n_e2e else None
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / max(n_e2e, 1) if n_e2e else None
+    if e2e_ms is not None and world > 1:
+        e2e_ms = over_ranks(e2e_ms, "max", dev)
     hbm, peak_kind = peaks()
     n_cub = args.n_cub if corr != p.CORR_OFF else 0
     fpb = 4 if prec == p.FP32 else 8
@@ -348,6 +353,8 @@ def run_jgs2(args, rank, world, local_rank):
                    "l2": "per-sweep working set larger than L2 (126 MB); no flush"},
         "sweeps_per_step": float(sweeps.mean()),
         "sweeps_per_s": over_ranks(float(sweeps.sum()), "sum", dev if world > 1 else None) / (ms_total * 1e-3),
+        "aggregate": {"scene_steps_per_s": world * args.steps / (ms_total * 1e-3),
+                      "note": "every rank steps its own replica or shard; value is the time per step of one"},
         "converged_steps": int(sum(q[1] for q in reps)), "max_rel_residual": float(max(q[2] for q in reps)),
         "line_search_per_step": {"dj_steps": float(np.mean([q[8] for q in reps])),
                                  "rejects": float(np.mean([q[7] for q in reps])),

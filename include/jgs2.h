@@ -40,9 +40,11 @@ typedef enum {
   JGS2_ENOTPRECOMPUTED = 4,  /* jgs2_step with the correction on before a precompute */
   JGS2_ENOTCONVERGED = 5,    /* max_sweeps reached; state is updated, report is filled */
   JGS2_EDIVERGED = 6,        /* the residual became NaN/Inf; state is NOT written back */
-  JGS2_ENONSPD = 7,          /* reserved */
+  JGS2_ENONSPD = 7,          /* jgs2_step_adjoint: the Hessian at x* is not positive definite
+                              * along a conjugate-gradient search direction */
   JGS2_ETIMEOUT = 8,         /* a bounded device wait (bulk-copy barrier) gave up; state NOT written */
-  JGS2_EINTERSECT = 9        /* reserved for contact */
+  JGS2_EINTERSECT = 9        /* contact: a surface pair reached zero distance at a sweep's positions;
+                              * state NOT written */
 } jgs2_status;
 
 /* Mesh description (Sec. 3). All pointers are host pointers, copied at create. */
@@ -276,20 +278,28 @@ jgs2_status jgs2_mesh_set_youngs(jgs2_mesh* mesh, const double* youngs);
 /* Allocation-free variant of jgs2_energy_gradient (the paper has no counterpart; this is a
  * service for callers that cannot allocate device memory while they run, such as a
  * real-time loop that must not wait on cudaMalloc, or a process whose device memory is
- * owned by a pooling allocator). It computes the same E(x) and g(x) but keeps the
- * reduction's partial sums in a file-scope device array of JGS2_STATIC_PARTIALS_MAX + 1
- * doubles (512 KB, held by every GPU that loads the library until exit) and calls no
- * cudaMalloc, cudaFree or allocating library routine.
+ * owned by a pooling allocator). It computes E(x) and g(x) of a mesh without contact and
+ * keeps the reduction's partial sums in a file-scope device array of
+ * JGS2_STATIC_PARTIALS_MAX + 1 doubles (512 KB, held by every GPU that loads the library
+ * until exit); it calls no cudaMalloc, cudaFree or allocating library routine.
+ *  - g equals jgs2_energy_gradient's bit for bit. E matches it to rounding: the partial
+ *    sums are added on the device in a fixed tree order, not in the allocating entry
+ *    point's host order.
+ *  - Meshes with contact are rejected (JGS2_EINVAL): the barrier terms need the candidate
+ *    list that only the allocating entry point builds.
  *  - Limit: (n_tets + free vertices) / 128 (rounded up each) <= JGS2_STATIC_PARTIALS_MAX,
- *    else JGS2_EINVAL with a message.
+ *    else JGS2_EINVAL with a message (checked before any device work).
  *  - The mesh's own device buffers must already exist: make one FP64 jgs2_step,
- *    jgs2_sweeps or jgs2_energy_gradient call on the mesh first (else JGS2_EINVAL).
+ *    jgs2_sweeps or jgs2_energy_gradient call on the mesh first (else JGS2_EINVAL). The
+ *    current CUDA device must be the one those buffers live on (else JGS2_EINVAL).
  *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    (cudaGetSymbolAddress) while that device is current.
  *  - Every call shares the array; calls that overlap on the GPU race. Each call writes
  *    every slot it reads, so the array needs no clearing.
+ *  - Every call copies E to the host and synchronises the stream before it returns, so it
+ *    cannot be recorded into a CUDA graph by stream capture.
  *  - x_t, v_t, x, g: device [V][3] double, caller order (g may be NULL); energy: host
- *    pointer (may be NULL, not both). Synchronises the stream before returning. */
+ *    pointer (may be NULL, not both). */
 #define JGS2_STATIC_PARTIALS_MAX 65536
 jgs2_status jgs2_energy_gradient_static(jgs2_mesh* mesh, const double* x_t, const double* v_t,
                                         const double* x, double* energy, double* g, void* stream);

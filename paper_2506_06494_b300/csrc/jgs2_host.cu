@@ -346,6 +346,7 @@ PrecBufs<double>& bufs<double>(Mesh* m) { return m->f64; }
 static jgs2_status ensure_device(Mesh* m) {
   if (!m->device_ready) {
     const int V = m->V, T = m->T, ns = m->n_slices;
+    CK(cudaGetDevice(&m->device));
     CK(dalloc(&m->d_inc_off, ns + 1));
     CK(dalloc(&m->d_inc_len, m->Vf));
     CK(dalloc(&m->d_inc, m->inc.size()));

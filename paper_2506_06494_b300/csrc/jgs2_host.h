@@ -52,6 +52,7 @@ struct Mesh {
   // cubature records, internal order: [Vf][n_cub]
   int n_cub = 0, nP = 0, cub_version = 0, pool_version = -1;
   bool device_ready = false;
+  int device = -1;                // CUDA device of the mesh's buffers (set at first allocation)
   std::vector<int> pool;          // internal tet ids of the pool, ascending
   std::vector<int> cub_p, cub_elem;
   std::vector<double> cub_w, cub_u, cub_resid;

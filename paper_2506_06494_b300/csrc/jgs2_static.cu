@@ -10,10 +10,12 @@
 // The array is a file-scope __device__ symbol: every GPU that loads the library holds it
 // until the process exits, and every call shares it. Its host-side name is only a stand-in
 // for the device symbol, so the kernels get the device address obtained once per device
-// with cudaGetSymbolAddress (the first call on a device does that set-up, so make that
-// first call before any stream capture). Each call overwrites every slot it reads, so no
-// clearing is needed; calls that overlap on the GPU (on different streams, or from
-// different threads) race on the array.
+// with cudaGetSymbolAddress (the first call on a device does that set-up while the device
+// is current). Each call overwrites every slot it reads, so no clearing is needed; calls
+// that overlap on the GPU (on different streams, or from different threads) race on the
+// array. Every call copies E to the host and synchronises its stream, so it cannot be
+// recorded by stream capture. Meshes with contact are rejected: their barrier terms need
+// the candidate list that only the allocating entry point builds.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -63,15 +65,24 @@ __global__ void k_sum_partials(double* p, int n) {
 jgs2_status energy_gradient_static(Mesh* m, const double* xt, const double* vt, const double* x, double* E,
                                    double* g, void* stream) {
   if (!m || !xt || !vt || !x || (!E && !g)) return fail(JGS2_EINVAL, "null argument");
+  // the barrier terms need the contact candidate list, which only the allocating entry
+  // point builds: a contact mesh would get a stale barrier gradient and no barrier energy
+  if (m->contact) return fail(JGS2_EINVAL, "meshes with contact are not supported by the allocation-free entry");
+  const int nbT = (m->T + 127) / 128, nbV = (m->Vf + 127) / 128;
+  if (nbT + nbV > kStaticPartials)
+    return fail(JGS2_EINVAL, "mesh too large for the static scratch: (n_tets + free vertices) / 128 must be <= " +
+                                 std::to_string(kStaticPartials));
   DevMesh<double> d;
   if (!dev_view_f64_if_ready(m, &d))
     return fail(JGS2_EINVAL,
                 "mesh device buffers not created yet: make one jgs2_step, jgs2_sweeps or jgs2_energy_gradient "
                 "call (FP64) on this mesh first");
-  const int nbT = (m->T + 127) / 128, nbV = (m->Vf + 127) / 128;
-  if (nbT + nbV > kStaticPartials)
-    return fail(JGS2_EINVAL, "mesh too large for the static scratch: (n_tets + free vertices) / 128 must be <= " +
-                                 std::to_string(kStaticPartials));
+  int dev = -1;
+  cudaError_t de = cudaGetDevice(&dev);
+  if (de != cudaSuccess) return fail(JGS2_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(de));
+  if (dev != m->device)
+    return fail(JGS2_EINVAL, "the current CUDA device is not the device of the mesh's buffers (device " +
+                                 std::to_string(m->device) + ")");
   double* scratch = nullptr;
   jgs2_status st = static_partials(&scratch);
   if (st != JGS2_OK) return st;
