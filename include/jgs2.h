@@ -114,6 +114,13 @@ typedef struct {
                               * every kernel group of the last sweep of each replayed chunk
                               * of check_every sweeps (a sample, so the events barely slow the
                               * step) */
+  double dx_tol;             /* > 0: also stop at the first sweep k >= 1 whose last update moved
+                              * the free vertices by |x^k - x^{k-1}|_2 <= dx_tol * length_scale
+                              * (2-norm over all free DOFs): Sec. 8's convergence check on a scene
+                              * normalised to a unit cube. 0 = off (the default). Single scenes
+                              * only (JGS2_EINVAL on a batch mesh); jgs2_step_gs ignores it */
+  double length_scale;       /* L of that normalisation (m); <= 0: the largest extent of the
+                              * bounding box of the rest positions */
 } jgs2_step_opts;
 
 #define JGS2_TRACE_MAX 4096
@@ -146,11 +153,15 @@ typedef struct {
                                            * kernels in full, sweep kernels over the profiled sweeps */
   int32_t trace_len;
   double trace[JGS2_TRACE_MAX]; /* r_k per sweep if record_trace */
+  int32_t stopped_dx;        /* 1 if the step stopped on the position-change test (dx_tol) */
+  int32_t pad_;
+  double last_dx;            /* |x^k - x^{k-1}|_2 / L of the step's last update (0 if no sweep) */
 } jgs2_step_report;
 
 /* Default option values (n_cub 4, n_train 20, n_cand 32, n_pool 256, tol 0.01, seed 0, gs 0). */
 void jgs2_precompute_opts_default(jgs2_precompute_opts* o);
-/* Defaults: max_sweeps 500, rel_tol 1e-4, FP32, asm, line search on, check_every 16. */
+/* Defaults: max_sweeps 500, rel_tol 1e-4, FP32, asm, line search on, check_every 16, no
+ * position-change test (dx_tol 0, length_scale 0). */
 void jgs2_step_opts_default(jgs2_step_opts* o);
 
 /* Validates the mesh (indices in range, positive volumes, material ranges, every free
@@ -202,8 +213,10 @@ int32_t jgs2_mesh_n_cub(const jgs2_mesh* mesh);
  * of the mesh, ordered after and before the caller's stream by events; the first step
  * with a new configuration (precision, correction, line search, block size, check_every,
  * profile, trace) captures the graph, so jgs2_step is not itself called inside a stream
- * capture. report may be NULL. Returns JGS2_ENOTCONVERGED (state written) when
- * max_sweeps is hit, JGS2_EDIVERGED (state untouched) on a non-finite residual. A mesh
+ * capture. report may be NULL. Returns JGS2_OK when r_k <= rel_tol or, with dx_tol > 0,
+ * when the position-change test stops the step (report->stopped_dx); JGS2_ENOTCONVERGED
+ * (state written) when max_sweeps is hit, JGS2_EDIVERGED (state untouched) on a
+ * non-finite residual. A mesh
  * without free vertices (every vertex pinned) or with g(x^0) = 0 returns JGS2_OK after 0
  * sweeps with x_{t+1} = x_t (r = 0). */
 jgs2_status jgs2_step(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts,
@@ -313,6 +326,13 @@ jgs2_status jgs2_energy_gradient_static(jgs2_mesh* mesh, const double* x_t, cons
  * if the count exceeds cap). Requires contact = 1. Synchronises the stream. */
 jgs2_status jgs2_contact_pairs(jgs2_mesh* mesh, const double* x_t, const double* x, double radius,
                                int32_t* out, int32_t cap, int32_t* n_out, void* stream);
+
+/* Measured arithmetic peak of the current device's CUDA cores (the paper has no
+ * counterpart; it gives the roofline of the ALU-bound kernels a measured denominator):
+ * eight independent FMA chains per thread, four 256-thread blocks per SM, best of five
+ * timed launches (CUDA events on `stream`). precision: JGS2_FP32 or JGS2_FP64; *gflops
+ * receives GFLOP/s (2 per FMA). Allocates a small device buffer; synchronises the stream. */
+jgs2_status jgs2_alu_peak(int32_t precision, double* gflops, void* stream);
 
 void jgs2_mesh_destroy(jgs2_mesh* mesh);
 const char* jgs2_last_error(void);

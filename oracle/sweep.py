@@ -19,7 +19,11 @@ first along D, then along the uncorrected direction D_J (always a descent direct
 Without it (the paper's plain Jacobi), x^{k+1} = x^k + D.
 
 Stopping (reading R9): r_k = |g(x^k)| / |g(x^0)| over free DOFs; stop at the first k with
-r_k <= rel_tol (returning x^k after k sweeps) or at max_sweeps.
+r_k <= rel_tol (returning x^k after k sweeps) or at max_sweeps. Optionally also Sec. 8's
+check: the paper normalises a scene into a unit cube and stops when the positions change by
+less than a tolerance between two consecutive iterations; read here as the 2-norm over all
+free DOFs, |x^k - x^{k-1}| <= dx_tol * L (k >= 1), L the normalising length (default: the
+largest extent of the rest positions' bounding box), tested after the residual test.
 """
 from __future__ import annotations
 
@@ -171,6 +175,7 @@ class StepResult:
     fallback: int = 0
     ls_rejects: int = 0
     converged: bool = False
+    stopped_dx: bool = False
 
 
 def residual_norm(mesh, x, z, h):
@@ -187,19 +192,23 @@ def run_sweeps(mesh: fem.Mesh, x, z, h, cub=None, n=1, psd=False, grad="asm", li
 
 
 def step(mesh: fem.Mesh, x_t, v_t, h, gravity, cub=None, rel_tol=1e-4, max_sweeps=100,
-         psd=False, grad="asm", line_search_on=True, record_x=False):
+         psd=False, grad="asm", line_search_on=True, record_x=False, dx_tol=0.0, length_scale=0.0):
     """One implicit-Euler step (Sec. 3) solved by JGS2 sweeps from x^0 = x_t (reading R8).
 
     Sweep k computes g(x^k); r_k = |g(x^k)|/|g(x^0)|; the step stops at the first k with
-    r_k <= rel_tol or k = max_sweeps and returns x^k (k sweeps applied)."""
+    r_k <= rel_tol, or (dx_tol > 0, k >= 1) |x^k - x^{k-1}| <= dx_tol L, or k = max_sweeps,
+    and returns x^k (k sweeps applied)."""
     z = fem.inertia_target(x_t, v_t, h, gravity)
     x = np.array(x_t, dtype=np.float64, copy=True)
+    L = length_scale if length_scale > 0 else float(np.max(mesh.X.max(axis=0) - mesh.X.min(axis=0)))
     stats = SweepStats()
     res = []
     xs = [] if record_x else None
     g0 = None
     k = 0
     conv = False
+    stop_dx = False
+    dx_last = None
     while True:
         D, DJ, g = direction(mesh, x, z, h, cub, psd, grad, stats)
         gn = float(np.linalg.norm(g[mesh.free]))
@@ -212,11 +221,16 @@ def step(mesh: fem.Mesh, x_t, v_t, h, gravity, cub=None, rel_tol=1e-4, max_sweep
         if r <= rel_tol or g0 == 0.0:
             conv = True
             break
+        if dx_tol > 0 and dx_last is not None and dx_last <= dx_tol * L:
+            stop_dx = True
+            break
         if k >= max_sweeps:
             break
-        x = x + (line_search(mesh, x, z, h, D, DJ, g, stats) if line_search_on else D)
+        step_k = line_search(mesh, x, z, h, D, DJ, g, stats) if line_search_on else D
+        dx_last = float(np.linalg.norm(step_k[mesh.free]))
+        x = x + step_k
         k += 1
-    out = StepResult(x, (x - x_t) / h, k, res, stats.fallback, stats.ls_rejects, conv)
+    out = StepResult(x, (x - x_t) / h, k, res, stats.fallback, stats.ls_rejects, conv, stop_dx)
     if record_x:
         out.xs = xs
     return out

@@ -115,6 +115,14 @@ jgs2_status mesh_create(const jgs2_mesh_desc* d, Mesh** out, const std::vector<i
     for (int v = 0; v < V; ++v) m->pinned[v] = d->pinned[v] ? 1 : 0;
   for (int v = 0; v < 3 * V; ++v)
     if (!std::isfinite(m->X[v])) return fail(JGS2_EINVAL, "non-finite rest position");
+  for (int q = 0; q < 3; ++q) {
+    double lo = m->X[q], hi = m->X[q];
+    for (int v = 1; v < V; ++v) {
+      lo = std::min(lo, m->X[3 * (size_t)v + q]);
+      hi = std::max(hi, m->X[3 * (size_t)v + q]);
+    }
+    m->extent = std::max(m->extent, hi - lo);
+  }
   // rest data (FP64): B = D_m^{-1}, V_e, Lame, mass shares
   m->B.resize(9 * (size_t)T);
   m->vol.resize(T);
@@ -905,6 +913,11 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
   init.max_sweeps = max_k;
   init.rel_tol = rel_tol;
   init.alpha = 1.0;
+  if (rel_tol >= 0.0 && o.dx_tol > 0.0) {
+    // Sec. 8: |x^k - x^{k-1}| on the scene normalised to a unit cube
+    const double L = o.length_scale > 0.0 ? o.length_scale : m->extent;
+    init.dx2_tol = (o.dx_tol * L) * (o.dx_tol * L);
+  }
   CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
   if (m->contact) {
     jgs2_status cst = contact_force_rebuild(m, s);
@@ -1194,6 +1207,9 @@ static jgs2_status check_opts(const Mesh* m, const jgs2_step_opts* o) {
   if (o->correction < 0 || o->correction > 2) return fail(JGS2_EINVAL, "bad correction");
   if (o->correction != JGS2_CORR_OFF && m->n_cub == 0)
     return fail(JGS2_ENOTPRECOMPUTED, "correction requested before jgs2_precompute / jgs2_precompute_import");
+  if (!(o->dx_tol >= 0.0)) return fail(JGS2_EINVAL, "dx_tol must be >= 0");
+  if (o->dx_tol > 0.0 && m->n_scenes > 0)
+    return fail(JGS2_EINVAL, "the position-change test (dx_tol) is for single scenes, not batch meshes");
   return JGS2_OK;
 }
 
@@ -1280,6 +1296,11 @@ static jgs2_status step_impl(Mesh* m, double* x, double* v, const jgs2_step_opts
     rep->g0 = hs->g0;
     rep->ms = ms;
     rep->trace_len = 0;
+    rep->stopped_dx = hs->stopped_dx;
+    {
+      const double L = o->length_scale > 0.0 ? o->length_scale : m->extent;
+      rep->last_dx = (hs->sweeps > 0 && L > 0.0) ? std::sqrt(hs->dx2) / L : 0.0;
+    }
     L.report(rep);
     if (o->record_trace) {
       const int n = std::min(hs->sweeps + 1, JGS2_TRACE_MAX);
@@ -1293,7 +1314,7 @@ static jgs2_status step_impl(Mesh* m, double* x, double* v, const jgs2_step_opts
                                                       : "residual became non-finite; state not written";
     return fail((jgs2_status)hs->status, why);
   }
-  if (!hs->converged) return fail(JGS2_ENOTCONVERGED, "max_sweeps reached before rel_tol");
+  if (!hs->converged && !hs->stopped_dx) return fail(JGS2_ENOTCONVERGED, "max_sweeps reached before rel_tol");
   return JGS2_OK;
 }
 
@@ -1852,6 +1873,8 @@ void jgs2_step_opts_default(jgs2_step_opts* o) {
   o->check_every = 16;
   o->record_trace = 0;
   o->profile = 0;
+  o->dx_tol = 0.0;
+  o->length_scale = 0.0;
 }
 
 jgs2_status jgs2_mesh_create(const jgs2_mesh_desc* desc, jgs2_mesh** out) {

@@ -38,6 +38,7 @@ struct Mesh {
   int V = 0, T = 0, Vf = 0, n_slices = 0, n_bodies = 0;
   double h = 0.0;
   double grav[3] = {0, 0, 0};
+  double extent = 0.0;             // largest extent of the rest positions' bounding box
   // caller-order inputs and FP64 rest data
   std::vector<double> X, E, nu, rho;
   std::vector<int> tets_c;

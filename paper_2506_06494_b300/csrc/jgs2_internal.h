@@ -80,6 +80,14 @@ struct StepState {
   int32_t ls_mode;     // this sweep's line-search pass: prev_dir as the sweep began
   uint32_t ticket_main;
   uint32_t ticket_energy;
+  // position-change stopping test (Sec. 8's |dx| check): |x^k - x^{k-1}|^2 of the last
+  // update, the squared tolerance (0: off), and |D|^2, |D_J|^2 of the current sweep
+  double dx2;
+  double dx2_tol;
+  double dd2;
+  double ddj2;
+  int32_t stopped_dx;  // the step stopped on the position-change test
+  int32_t pad_dx;
 };
 
 // Contact data of a mesh (Sec. 7); pairs: 0 vertex-wall, 1 vertex-face, 2 edge-edge.

@@ -920,8 +920,11 @@ __global__ void __launch_bounds__(32 * kPoolWarps) k_pool(DevMesh<T> m, const St
 }
 
 // Residual bookkeeping of sweep k (reading R9), run by one thread of the last block.
-__device__ __forceinline__ void finalize_sweep(StepState* st, double r2, double gd, double gdj,
-                                               double* trace, int record) {
+// dd2, ddj2: |D|^2 and |D_J|^2 of the sweep's directions. Besides r_k <= rel_tol, a step
+// with the position-change test on (dx2_tol > 0) stops at the first k >= 1 whose last
+// update moved the free vertices by |x^k - x^{k-1}|^2 <= dx2_tol (Sec. 8).
+__device__ __forceinline__ void finalize_sweep(StepState* st, double r2, double gd, double gdj, double dd2,
+                                               double ddj2, double* trace, int record) {
   st->ticket_main = 0;
   const int k = st->k;
   const double gn = sqrt(r2);
@@ -935,6 +938,10 @@ __device__ __forceinline__ void finalize_sweep(StepState* st, double r2, double 
   st->dir = 0;
   st->need_j = 0;
   st->ls_mode = st->prev_dir;
+  const double dx2_last = st->dx2;
+  st->dd2 = dd2;
+  st->ddj2 = ddj2;
+  st->dx2 = dd2;  // the update without line search (alpha 1 along D); k_ls_decide overrides
   if (record && k < 4096) trace[k] = r;
   if (!isfinite(r) || !isfinite(gd) || !isfinite(gdj)) {
     st->status = 6;  // JGS2_EDIVERGED
@@ -942,6 +949,10 @@ __device__ __forceinline__ void finalize_sweep(StepState* st, double r2, double 
     st->sweeps = k;
   } else if (r <= st->rel_tol || g0 == 0.0) {
     st->converged = 1;
+    st->done = 1;
+    st->sweeps = k;
+  } else if (k >= 1 && st->dx2_tol > 0.0 && dx2_last <= st->dx2_tol) {
+    st->stopped_dx = 1;
     st->done = 1;
     st->sweeps = k;
   } else if (k >= st->max_sweeps) {
@@ -964,7 +975,7 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
              double* __restrict__ trace, int record) {
   if (!BATCH && st->done) return;
   __shared__ double red[96];
-  __shared__ Acc<T> sred[64];
+  __shared__ Acc<T> sred[96];
   // the block's incidence slices form one contiguous, 128-byte aligned range of entries;
   // copy it into shared memory first (coalesced 16-byte loads), so that each incidence's
   // record loads do not wait on a global load of its entry
@@ -979,7 +990,7 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
   }
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  Acc<T> acc[2];  // |g|^2, g.D_J
+  Acc<T> acc[3];  // |g|^2, g.D_J, |D_J|^2
   const int sc = (BATCH && i < m.Vf) ? m.v_scene[i] : -1;
   const bool active = i < m.Vf && (!BATCH || !m.scenes[sc].done);
   if (active) {
@@ -1037,23 +1048,27 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
     for (int q = 0; q < 3; ++q) {
       acc[0].add_prod(g[q], g[q]);
       acc[1].add_prod(g[q], dj[q]);
+      if (!BATCH) acc[2].add_prod(dj[q], dj[q]);
     }
   }
   if (BATCH) {
-    scene_reduce_acc<T, 2>(acc, active ? sc : -1, m.sacc, 0);
+    Acc<T> sacc2[2] = {acc[0], acc[1]};
+    scene_reduce_acc<T, 2>(sacc2, active ? sc : -1, m.sacc, 0);
     return;
   }
-  double bs[2];
-  block_sum_acc<T, 2>(acc, bs, sred);
+  double bs[3];
+  block_sum_acc<T, 3>(acc, bs, sred);
   if (threadIdx.x == 0) {
     partial[blockIdx.x] = bs[0];
     partial[gridDim.x + blockIdx.x] = bs[1];
+    partial[3 * gridDim.x + blockIdx.x] = bs[2];
   }
   if (CORR) return;
   if (!last_block(&st->ticket_main)) return;
   const double r2 = block_sum_array(partial, gridDim.x, 1, red);
   const double gdj = block_sum_array(partial + gridDim.x, gridDim.x, 1, red);
-  if (threadIdx.x == 0) finalize_sweep(st, r2, gdj, gdj, trace, record);
+  const double djj = block_sum_array(partial + 3 * gridDim.x, gridDim.x, 1, red);
+  if (threadIdx.x == 0) finalize_sweep(st, r2, gdj, gdj, djj, djj, trace, record);
 }
 
 // Sweep phase 2, thread per free vertex: the cubature sums H~_i, g~_i (Eq. cubature) from
@@ -1065,9 +1080,9 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 512 : 256) / BS) k_corre
                                                 double* __restrict__ trace, int record) {
   if (!BATCH && st->done) return;
   __shared__ double red[96];
-  __shared__ Acc<T> sred[32];
+  __shared__ Acc<T> sred[64];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  Acc<T> acc[1];  // g.D
+  Acc<T> acc[2];  // g.D, |D|^2
   int fb = 0;
   const int sc = (BATCH && i < m.Vf) ? m.v_scene[i] : -1;
   const bool active = i < m.Vf && (!BATCH || !m.scenes[sc].done);
@@ -1116,25 +1131,34 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 512 : 256) / BS) k_corre
     Vec4<T> dv{d[0], d[1], d[2], T(0)};
     m.D[i] = dv;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) acc[0].add_prod(g[q], d[q]);
+    for (int q = 0; q < 3; ++q) {
+      acc[0].add_prod(g[q], d[q]);
+      if (!BATCH) acc[1].add_prod(d[q], d[q]);
+    }
   }
   if (BATCH) {
     if (fb) atomicAdd(&m.scenes[sc].fallback, 1);
-    scene_reduce_acc<T, 1>(acc, active ? sc : -1, m.sacc, 2);
+    Acc<T> sacc1[1] = {acc[0]};
+    scene_reduce_acc<T, 1>(sacc1, active ? sc : -1, m.sacc, 2);
     return;
   }
   if (__syncthreads_or(fb)) {
     const int nfb = __syncthreads_count(fb);
     if (threadIdx.x == 0) atomicAdd(&st->fallback, nfb);
   }
-  double bs[1];
-  block_sum_acc<T, 1>(acc, bs, sred);
-  if (threadIdx.x == 0) partial[2 * gridDim.x + blockIdx.x] = bs[0];
+  double bs[2];
+  block_sum_acc<T, 2>(acc, bs, sred);
+  if (threadIdx.x == 0) {
+    partial[2 * gridDim.x + blockIdx.x] = bs[0];
+    partial[4 * gridDim.x + blockIdx.x] = bs[1];
+  }
   if (!last_block(&st->ticket_main)) return;
   const double r2 = block_sum_array(partial, gridDim.x, 1, red);
   const double gdj = block_sum_array(partial + gridDim.x, gridDim.x, 1, red);
   const double gd = block_sum_array(partial + 2 * gridDim.x, gridDim.x, 1, red);
-  if (threadIdx.x == 0) finalize_sweep(st, r2, gd, gdj, trace, record);
+  const double djj = block_sum_array(partial + 3 * gridDim.x, gridDim.x, 1, red);
+  const double dd = block_sum_array(partial + 4 * gridDim.x, gridDim.x, 1, red);
+  if (threadIdx.x == 0) finalize_sweep(st, r2, gd, gdj, dd, djj, trace, record);
 }
 
 // Exact energy change of a tet for the displacement increment alpha*d (no cancellation):
@@ -1387,6 +1411,8 @@ __global__ void __launch_bounds__(256) k_ls_decide(StepState* st, int has_j, con
   st->alpha = alpha;
   st->dir = ok ? chosen : (DIR == 1 ? 1 : 0);
   if (DIR == 0) st->need_j = (!ok && has_j) ? 1 : 0;
+  // |x^{k+1} - x^k|^2 of this sweep's update (zero when no trial passed)
+  st->dx2 = alpha * alpha * (st->dir ? st->ddj2 : st->dd2);
   if (ok) {
     st->prev_dir = chosen;
     if (chosen == 1) st->dj_steps += 1;

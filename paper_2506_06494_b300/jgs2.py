@@ -48,7 +48,8 @@ class CubatureBlob(C.Structure):
 class StepOpts(C.Structure):
     _fields_ = [("max_sweeps", C.c_int32), ("rel_tol", C.c_double), ("precision", C.c_int32),
                 ("correction", C.c_int32), ("line_search", C.c_int32), ("check_every", C.c_int32),
-                ("record_trace", C.c_int32), ("profile", C.c_int32)]
+                ("record_trace", C.c_int32), ("profile", C.c_int32), ("dx_tol", C.c_double),
+                ("length_scale", C.c_double)]
 
 
 class AdjointOpts(C.Structure):
@@ -68,7 +69,8 @@ class StepReport(C.Structure):
                 ("rel_residual", C.c_double), ("g0", C.c_double),
                 ("ms", C.c_double), ("launches", C.c_int32), ("profiled_sweeps", C.c_int32),
                 ("kernel_launches", C.c_int32 * NKERNELS), ("kernel_ms", C.c_double * NKERNELS),
-                ("trace_len", C.c_int32), ("trace", C.c_double * TRACE_MAX)]
+                ("trace_len", C.c_int32), ("trace", C.c_double * TRACE_MAX),
+                ("stopped_dx", C.c_int32), ("pad_", C.c_int32), ("last_dx", C.c_double)]
 
 
 _lib = None
@@ -78,7 +80,7 @@ EXPORTS = ["jgs2_precompute_opts_default", "jgs2_step_opts_default", "jgs2_mesh_
            "jgs2_mesh_n_cub", "jgs2_step", "jgs2_step_gs", "jgs2_step_host", "jgs2_sweeps",
            "jgs2_energy_gradient", "jgs2_energy_gradient_static", "jgs2_contact_pairs",
            "jgs2_step_adjoint", "jgs2_adjoint_opts_default", "jgs2_mesh_set_youngs",
-           "jgs2_mesh_create_batch", "jgs2_batch_report", "jgs2_autotune",
+           "jgs2_mesh_create_batch", "jgs2_batch_report", "jgs2_autotune", "jgs2_alu_peak",
            "jgs2_mesh_destroy", "jgs2_last_error"]
 
 
@@ -112,6 +114,7 @@ def lib():
     L.jgs2_mesh_create_batch.argtypes = [C.POINTER(MeshDesc), C.c_int32, C.POINTER(P)]
     L.jgs2_batch_report.argtypes = [P, P, P, P]
     L.jgs2_autotune.argtypes = [P, P, P, C.POINTER(StepOpts), P, C.POINTER(C.c_int32)]
+    L.jgs2_alu_peak.argtypes = [C.c_int32, C.POINTER(C.c_double), P]
     L.jgs2_mesh_destroy.argtypes = [P]
     L.jgs2_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -136,6 +139,13 @@ def _check(status, ok=(0,)):
 
 def _ptr(a, ctype):
     return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def alu_peak(precision, stream=None) -> float:
+    """jgs2_alu_peak: the current device's measured FMA throughput in GFLOP/s."""
+    g = C.c_double()
+    _check(lib().jgs2_alu_peak(int(precision), C.byref(g), C.c_void_p(_stream_ptr(stream))))
+    return g.value
 
 
 def step_opts(**kw) -> StepOpts:

@@ -141,6 +141,30 @@ def box_planes(size=(1.0, 1.0, 2.0)):
     ], dtype=np.float64)
 
 
+def sphere_centres(n_spheres=10, radius=0.1, seed=0, dhat=1e-3):
+    """Seeded centres of the spheres scene: uniform in [0.15,0.85]^2 x [0.5,1.9], rejected
+    until every pair is at least 2 radius + 2 dhat apart."""
+    rng = np.random.default_rng(seed)
+    centres = []
+    while len(centres) < n_spheres:
+        c = rng.uniform([0.15, 0.15, 0.5], [0.85, 0.85, 1.9])
+        if all(np.linalg.norm(c - d) >= 2 * radius + 2 * dhat for d in centres):
+            centres.append(c)
+    return centres
+
+
+def sphere_of_scene(k, n_spheres=10, radius=0.1, cells_across=48, seed=0, dhat=1e-3,
+                    E_stiff=2e6, E_soft=1e5):
+    """Sphere k of spheres_scene alone (same coordinates and material, no contact): the
+    spheres are separate bodies, so a body-by-body computation can take them one at a time."""
+    Xs, ts = voxel_sphere(radius, cells_across)
+    c = sphere_centres(n_spheres, radius, seed, dhat)[k]
+    T = len(ts)
+    E = E_stiff if k < n_spheres // 2 else E_soft
+    return Scene(f"sphere{k}", Xs + c, ts.astype(np.int32), np.full(T, E), np.full(T, 0.4),
+                 np.full(T, 1000.0), np.zeros(len(Xs), np.uint8), np.zeros_like(Xs))
+
+
 def spheres_scene(n_spheres=10, radius=0.1, cells_across=48, seed=0, dhat=1e-3,
                   E_stiff=2e6, E_soft=1e5, contact=1):
     """Ten voxel spheres at seeded separated positions above a 1x1x2 m box.
@@ -148,12 +172,7 @@ def spheres_scene(n_spheres=10, radius=0.1, cells_across=48, seed=0, dhat=1e-3,
     Spheres 0..n/2-1 are stiff, the rest soft; all share one lattice shape.
     """
     Xs, ts = voxel_sphere(radius, cells_across)
-    rng = np.random.default_rng(seed)
-    centres = []
-    while len(centres) < n_spheres:
-        c = rng.uniform([0.15, 0.15, 0.5], [0.85, 0.85, 1.9])
-        if all(np.linalg.norm(c - d) >= 2 * radius + 2 * dhat for d in centres):
-            centres.append(c)
+    centres = sphere_centres(n_spheres, radius, seed, dhat)
     Xl, tl, El = [], [], []
     for k, c in enumerate(centres):
         Xl.append(Xs + c)
