@@ -126,12 +126,15 @@ typedef struct {
 #define JGS2_TRACE_MAX 4096
 /* kernel kinds in jgs2_step_report.kernel_*: pool (cubature elements), gather (per-vertex
  * gradient, diagonal block, rotation), correct (cubature correction + 3x3 solve), energy
- * (line search), update, setup (per-step setup and write-back), contact (broadphase, narrowphase
- * and barrier terms), elem (per-tet deformation gradients of the sweep). kernel_launches
- * counts kernels; a pass of several launches (contact: 11) counts each. */
-#define JGS2_NKERNELS 8
+ * (the line search's energy-change pass over tets and vertices), update, setup (per-step
+ * setup and write-back), contact (broadphase, narrowphase and barrier terms), elem (per-tet
+ * deformation gradients of the sweep), ls_pairs (the line search's barrier trials) and
+ * ls_decide (the line search's one-block decision). kernel_launches counts kernels; a pass
+ * of several launches (contact: 11) counts each. The line search launches every pass
+ * variant each sweep, and only the variants the sweep needs do work (ls_passes). */
+#define JGS2_NKERNELS 10
 enum { JGS2_K_POOL = 0, JGS2_K_GATHER = 1, JGS2_K_CORRECT = 2, JGS2_K_ENERGY = 3, JGS2_K_UPDATE = 4,
-       JGS2_K_SETUP = 5, JGS2_K_CONTACT = 6, JGS2_K_ELEM = 7 };
+       JGS2_K_SETUP = 5, JGS2_K_CONTACT = 6, JGS2_K_ELEM = 7, JGS2_K_LS_PAIRS = 8, JGS2_K_LS_DECIDE = 9 };
 
 typedef struct {
   int32_t sweeps;            /* sweeps applied in the step */
@@ -156,6 +159,10 @@ typedef struct {
   int32_t stopped_dx;        /* 1 if the step stopped on the position-change test (dx_tol) */
   int32_t pad_;
   double last_dx;            /* |x^k - x^{k-1}|_2 / L of the step's last update (0 if no sweep) */
+  int32_t ls_passes[3];      /* line-search passes that did work: [0] along D, [1] along D_J after
+                              * every D trial failed, [2] both directions in one pass (after a
+                              * sweep that stepped along D_J) */
+  int32_t pad2_;
 } jgs2_step_report;
 
 /* Default option values (n_cub 4, n_train 20, n_cand 32, n_pool 256, tol 0.01, seed 0, gs 0). */

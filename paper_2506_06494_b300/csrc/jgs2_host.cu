@@ -933,7 +933,7 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
     m->ggroups.clear();
     // profiling: event nodes around the kernel groups of the chunk's last sweep only (not
     // the first: a step's sweep 0 always rebuilds the contact list)
-    const size_t nev = prof ? (size_t)14 : 0;
+    const size_t nev = prof ? (size_t)32 : 0;
     while (m->gevents.size() < nev) {
       cudaEvent_t e;
       CK(cudaEventCreate(&e));
@@ -997,19 +997,25 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
         // at once otherwise)
         const int npp = m->contact ? kPairTrialBlocks : 0;
         double* pp = m->d_partial + (size_t)12 * nbE;
-        group(JGS2_K_ENERGY, (corr ? 3 : 1) * (m->contact ? 3 : 2), s, [&] {
-          if (m->contact) k_pair_trials<T, 0><<<npp, 128, 0, s>>>(d, m->d_state, pp);
-          k_energy<T, 0><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
+        // one timing group per launch, so that each kernel of the pass is timed alone
+        if (m->contact)
+          group(JGS2_K_LS_PAIRS, 1, s, [&] { k_pair_trials<T, 0><<<npp, 128, 0, s>>>(d, m->d_state, pp); });
+        group(JGS2_K_ENERGY, 1, s, [&] { k_energy<T, 0><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial); });
+        group(JGS2_K_LS_DECIDE, 1, s, [&] {
           k_ls_decide<0><<<1, 256, 0, s>>>(m->d_state, corr ? 1 : 0, m->d_partial, nbE, pp, npp);
-          if (corr) {
-            if (m->contact) k_pair_trials<T, 1><<<npp, 128, 0, s>>>(d, m->d_state, pp);
-            k_energy<T, 1><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
-            k_ls_decide<1><<<1, 256, 0, s>>>(m->d_state, 1, m->d_partial, nbE, pp, npp);
-            if (m->contact) k_pair_trials<T, 2><<<npp, 128, 0, s>>>(d, m->d_state, pp);
-            k_energy<T, 2><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial);
-            k_ls_decide<2><<<1, 256, 0, s>>>(m->d_state, 1, m->d_partial, nbE, pp, npp);
-          }
         });
+        if (corr) {
+          if (m->contact)
+            group(JGS2_K_LS_PAIRS, 1, s, [&] { k_pair_trials<T, 1><<<npp, 128, 0, s>>>(d, m->d_state, pp); });
+          group(JGS2_K_ENERGY, 1, s, [&] { k_energy<T, 1><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial); });
+          group(JGS2_K_LS_DECIDE, 1, s,
+                [&] { k_ls_decide<1><<<1, 256, 0, s>>>(m->d_state, 1, m->d_partial, nbE, pp, npp); });
+          if (m->contact)
+            group(JGS2_K_LS_PAIRS, 1, s, [&] { k_pair_trials<T, 2><<<npp, 128, 0, s>>>(d, m->d_state, pp); });
+          group(JGS2_K_ENERGY, 1, s, [&] { k_energy<T, 2><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial); });
+          group(JGS2_K_LS_DECIDE, 1, s,
+                [&] { k_ls_decide<2><<<1, 256, 0, s>>>(m->d_state, 1, m->d_partial, nbE, pp, npp); });
+        }
       }
       if (nbV > 0) group(JGS2_K_UPDATE, 1, s, [&] { k_update<T><<<nbV, 128, 0, s>>>(d, m->d_state); });
     }
@@ -1095,7 +1101,7 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
     m->graph = nullptr;
     m->graph_key = -1;
     m->ggroups.clear();
-    const size_t nev = prof ? (size_t)14 : 0;
+    const size_t nev = prof ? (size_t)32 : 0;
     while (m->gevents.size() < nev) {
       cudaEvent_t e;
       CK(cudaEventCreate(&e));
@@ -1297,6 +1303,7 @@ static jgs2_status step_impl(Mesh* m, double* x, double* v, const jgs2_step_opts
     rep->ms = ms;
     rep->trace_len = 0;
     rep->stopped_dx = hs->stopped_dx;
+    for (int q = 0; q < 3; ++q) rep->ls_passes[q] = hs->ls_passes[q];
     {
       const double L = o->length_scale > 0.0 ? o->length_scale : m->extent;
       rep->last_dx = (hs->sweeps > 0 && L > 0.0) ? std::sqrt(hs->dx2) / L : 0.0;

@@ -88,6 +88,8 @@ struct StepState {
   double ddj2;
   int32_t stopped_dx;  // the step stopped on the position-change test
   int32_t pad_dx;
+  int32_t ls_passes[3];  // line-search passes that did work, by pass (D, D_J, both)
+  int32_t pad_ls;
 };
 
 // Contact data of a mesh (Sec. 7); pairs: 0 vertex-wall, 1 vertex-face, 2 edge-edge.

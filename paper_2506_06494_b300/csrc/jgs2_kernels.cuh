@@ -1413,6 +1413,7 @@ __global__ void __launch_bounds__(256) k_ls_decide(StepState* st, int has_j, con
   if (DIR == 0) st->need_j = (!ok && has_j) ? 1 : 0;
   // |x^{k+1} - x^k|^2 of this sweep's update (zero when no trial passed)
   st->dx2 = alpha * alpha * (st->dir ? st->ddj2 : st->dd2);
+  st->ls_passes[DIR] += 1;
   if (ok) {
     st->prev_dir = chosen;
     if (chosen == 1) st->dj_steps += 1;

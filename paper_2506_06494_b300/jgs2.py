@@ -16,8 +16,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libjgs2.so")
 
 TRACE_MAX = 4096
-NKERNELS = 8
-KERNEL_NAMES = ["k_pool", "k_gather", "k_correct", "k_energy", "k_update", "setup", "contact", "k_elem"]
+NKERNELS = 10
+KERNEL_NAMES = ["k_pool", "k_gather", "k_correct", "k_energy", "k_update", "setup", "contact", "k_elem",
+                "k_pair_trials", "k_ls_decide"]
 FP64, FP32 = 0, 1
 CORR_ASM, CORR_ELEM, CORR_OFF = 0, 1, 2
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTPRECOMPUTED", 5: "ENOTCONVERGED",
@@ -70,7 +71,8 @@ class StepReport(C.Structure):
                 ("ms", C.c_double), ("launches", C.c_int32), ("profiled_sweeps", C.c_int32),
                 ("kernel_launches", C.c_int32 * NKERNELS), ("kernel_ms", C.c_double * NKERNELS),
                 ("trace_len", C.c_int32), ("trace", C.c_double * TRACE_MAX),
-                ("stopped_dx", C.c_int32), ("pad_", C.c_int32), ("last_dx", C.c_double)]
+                ("stopped_dx", C.c_int32), ("pad_", C.c_int32), ("last_dx", C.c_double),
+                ("ls_passes", C.c_int32 * 3), ("pad2_", C.c_int32)]
 
 
 _lib = None

@@ -25,7 +25,24 @@ def test_sweep_byte_model():
     assert b.sweep_bytes(634_130, 3_471_360, 4) == 882_080_040   # ten spheres, FP32
     kb = b.kernel_bytes(634_130, 3_471_360, 4, 4)
     assert kb["k_energy"] == 3_471_360 * 100 + 634_130 * 40
+    assert kb["k_energy_2"] == 3_471_360 * 100 + 634_130 * 52
     assert kb["k_correct"] == 634_130 * (84 + 4 * 152)
+
+
+def test_scope_byte_model():
+    """The hot-path scope's per-unit figures: 76 B per tet and 756 B per free vertex in FP32
+    (743 MB per sweep at 3.47M tets)."""
+    b = _bench()
+    assert b.survey_sweep_bytes(0, 1, 4) == 76
+    assert b.survey_sweep_bytes(1, 0, 4) == 756
+    assert abs(b.survey_sweep_bytes(634_130, 3_471_360, 4) - 743e6) < 1e6
+
+
+def test_makespan():
+    b = _bench()
+    assert b.makespan([3.0, 1.0, 1.0, 1.0], 2) == 3.0
+    assert b.makespan([2.0, 2.0, 2.0], 2) == 4.0
+    assert b.makespan([1.0] * 10, 16) == 1.0
 
 
 def test_reference_arm_json_line():

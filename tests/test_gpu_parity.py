@@ -108,6 +108,23 @@ def test_step_fp64_matches_oracle(cuda, cube):
     assert rel(v.cpu().numpy(), o.v, o.v) <= 1e-9
 
 
+def test_step_position_change_stop_matches_oracle(cuda, cube):
+    """Sec. 8's stopping test (|x^k - x^{k-1}| <= dx_tol L): the FP64 step stops at the
+    oracle's sweep, with its positions."""
+    s, m, cub = cube
+    gm = gpu_mesh(s, cub)
+    x = t(s.X, cuda)
+    v = t(s.v0, cuda)
+    rep = gm.step(x, v, p.step_opts(precision=p.FP64, max_sweeps=400, dx_tol=1e-4, length_scale=0.1))
+    o = sweep.step(m, s.X, s.v0, s.dt, s.gravity, cub, 1e-4, 400, dx_tol=1e-4, length_scale=0.1,
+                   record_x=True)
+    assert o.stopped_dx and not o.converged
+    assert rep.stopped_dx == 1 and rep.converged == 0 and rep.sweeps == o.sweeps
+    assert rel(x.cpu().numpy(), o.x, o.x - s.X) <= 1e-9
+    last = np.linalg.norm((o.xs[-1] - o.xs[-2])[m.free]) / 0.1
+    assert last <= 1e-4 and abs(rep.last_dx - last) <= 1e-6 * last
+
+
 def test_step_fp32_converges_to_oracle_solution(cuda, cube):
     """FP32 sweeps take their own line-search path, so the step is checked by what must hold
     for any valid result: the FP64 oracle's relative residual at the GPU's x_{t+1} meets the

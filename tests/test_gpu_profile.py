@@ -34,3 +34,11 @@ def test_profiled_step_equals_plain_step(cuda, prec):
     names = p.jgs2.KERNEL_NAMES
     for kind in ("k_elem", "k_gather", "k_correct", "k_energy", "k_update", "setup"):
         assert kms[names.index(kind)] > 0.0, kind
+
+
+def test_alu_peak_is_measured(cuda):
+    """jgs2_alu_peak: FMA throughput of the CUDA cores (the ALU roofline's denominator), with
+    FP32 far above FP64 on this part."""
+    f32 = p.alu_peak(p.FP32)
+    f64 = p.alu_peak(p.FP64)
+    assert 1e3 < f32 < 2e5 and 10.0 < f64 < f32 / 4
