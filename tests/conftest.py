@@ -21,3 +21,9 @@ def cuda():
     import paper_2506_06494_b300 as p
     p.lib()  # raises if the library is missing: GPU tests never run on a fallback
     return torch.device("cuda:0")
+
+
+# the convergence study module sits beside the tests that import it
+TESTS = os.path.dirname(os.path.abspath(__file__))
+if TESTS not in sys.path:
+    sys.path.insert(0, TESTS)
