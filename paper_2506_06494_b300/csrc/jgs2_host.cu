@@ -1306,7 +1306,7 @@ static jgs2_status step_impl(Mesh* m, double* x, double* v, const jgs2_step_opts
     for (int q = 0; q < 3; ++q) rep->ls_passes[q] = hs->ls_passes[q];
     {
       const double L = o->length_scale > 0.0 ? o->length_scale : m->extent;
-      rep->last_dx = (hs->sweeps > 0 && L > 0.0) ? std::sqrt(hs->dx2) / L : 0.0;
+      rep->last_dx = (hs->sweeps > 0 && L > 0.0) ? std::sqrt(hs->dx2_applied) / L : 0.0;
     }
     L.report(rep);
     if (o->record_trace) {

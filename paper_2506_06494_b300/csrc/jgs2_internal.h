@@ -88,6 +88,7 @@ struct StepState {
   double ddj2;
   int32_t stopped_dx;  // the step stopped on the position-change test
   int32_t pad_dx;
+  double dx2_applied;  // |x^k - x^{k-1}|^2 of the last update applied (for the report)
   int32_t ls_passes[3];  // line-search passes that did work, by pass (D, D_J, both)
   int32_t pad_ls;
 };

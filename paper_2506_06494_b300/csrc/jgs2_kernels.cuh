@@ -939,6 +939,7 @@ __device__ __forceinline__ void finalize_sweep(StepState* st, double r2, double 
   st->need_j = 0;
   st->ls_mode = st->prev_dir;
   const double dx2_last = st->dx2;
+  st->dx2_applied = k >= 1 ? dx2_last : 0.0;
   st->dd2 = dd2;
   st->ddj2 = ddj2;
   st->dx2 = dd2;  // the update without line search (alpha 1 along D); k_ls_decide overrides

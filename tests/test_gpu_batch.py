@@ -102,3 +102,26 @@ def test_batch_equals_single_scene_steps(cuda, batch):
         xs = xb.cpu().numpy()[off:off + s.n_vertices]
         assert np.linalg.norm(xs - x.cpu().numpy()) <= 1e-3 * np.linalg.norm(x.cpu().numpy() - s.X)
         off += s.n_vertices
+
+
+def test_batch_fp32_matches_oracle_per_scene(cuda, batch):
+    """The FP32 batch against the FP64 oracle scene by scene: every scene runs exactly 6
+    sweeps (a tolerance out of reach, a cap of 6) with its own line search; per scene, the
+    largest vertex error is at most 1e-4 of the largest vertex displacement."""
+    ss, ms, cubs, outs = batch
+    g = p.Mesh.batch(ss)
+    g.precompute_import(*concat_cub(ss, cubs))
+    X = np.concatenate([s.X for s in ss])
+    V0 = np.concatenate([s.v0 for s in ss])
+    x, v = t(X, cuda), t(V0, cuda)
+    g.step(x, v, p.step_opts(precision=p.FP32, max_sweeps=6, rel_tol=1e-14, check_every=3))
+    sw, _, _ = g.batch_report()
+    xg_all = x.cpu().numpy()
+    off = 0
+    for k, (s, m, c) in enumerate(zip(ss, ms, cubs)):
+        o = sweep.step(m, s.X, s.v0, s.dt, s.gravity, c, 1e-14, 6)
+        assert sw[k] == o.sweeps == 6
+        xg = xg_all[off:off + s.n_vertices]
+        err = np.linalg.norm(xg - o.x, axis=1).max() / np.linalg.norm(o.x - s.X, axis=1).max()
+        assert err <= 1e-4, (k, err)
+        off += s.n_vertices

@@ -74,8 +74,9 @@ def test_sweeps_with_contact(cuda, prec, corr, name):
     g.sweeps(t(s.X, cuda), t(s.v0, cuda), xg, 2, p.step_opts(precision=prec, correction=corr))
     z = fem.inertia_target(s.X, s.v0, s.dt, s.gravity)
     xo = sweep.run_sweeps(m, x, z, s.dt, None if corr == p.CORR_OFF else cub, 2)
-    err = np.linalg.norm(xg.cpu().numpy() - xo) / np.linalg.norm(xo - x)
-    assert err <= TOL[prec] * (10 if prec == p.FP32 else 1), err
+    # per vertex: largest vertex error over the largest vertex displacement
+    err = np.linalg.norm(xg.cpu().numpy() - xo, axis=1).max() / np.linalg.norm(xo - x, axis=1).max()
+    assert err <= TOL[prec], err
 
 
 def test_step_with_contact_fp64_matches_oracle(cuda):

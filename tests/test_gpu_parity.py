@@ -1,8 +1,9 @@
 """GPU parity: the CUDA sweep (through the C ABI) against the FP64 oracle.
 
-Tolerances: FP64 path 1e-9 relative position error per sweep (relative to the sweep's
-displacement), FP32 path 1e-4. Identical precompute data goes to both sides: the GPU gets
-the oracle's cubature records (or a seeded synthetic record set) through
+Tolerances, per vertex: max_i |x_gpu,i - x_orc,i| / max_i |x_orc,i - x_start,i| (the largest
+vertex error over the largest vertex displacement of the sweeps compared) is at most 1e-9 for
+the FP64 path and 1e-4 for the FP32 path. Identical precompute data goes to both sides: the
+GPU gets the oracle's cubature records (or a seeded synthetic record set) through
 jgs2_precompute_import.
 """
 import numpy as np
@@ -49,7 +50,9 @@ def gpu_mesh(s, cub=None):
 
 
 def rel(a, b, ref):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(ref), 1e-300)
+    """Largest per-vertex error of a against b over the largest per-vertex norm of ref."""
+    a, b, ref = (np.asarray(q).reshape(-1, 3) for q in (a, b, ref))
+    return np.linalg.norm(a - b, axis=1).max() / max(np.linalg.norm(ref, axis=1).max(), 1e-300)
 
 
 def test_energy_gradient_fp64(cuda, cube):
@@ -90,7 +93,7 @@ def test_three_sweeps_multiblock_beam(cuda, beam, prec):
     gm.sweeps(t(s.X, cuda), t(s.v0, cuda), xg, 3, p.step_opts(precision=prec))
     z = fem.inertia_target(s.X, s.v0, s.dt, s.gravity)
     xo = sweep.run_sweeps(m, xk, z, s.dt, cub, 3)
-    assert rel(xg.cpu().numpy(), xo, xo - xk) <= TOL[prec] * (10 if prec == p.FP32 else 1)
+    assert rel(xg.cpu().numpy(), xo, xo - xk) <= TOL[prec]
 
 
 def test_step_fp64_matches_oracle(cuda, cube):
@@ -196,7 +199,7 @@ def _sampled_direction_check(cuda, s, prec, n_samples, seed):
     free = np.nonzero(~s.pinned.astype(bool))[0]
     for i in rng.choice(free, size=n_samples, replace=False):
         d, _ = lm.direction(i, xk, z, s.dt, elem[i], w[i], u[i])
-        assert np.linalg.norm(D_gpu[i] - d) <= TOL[prec] * 10 * np.linalg.norm(d), i
+        assert np.linalg.norm(D_gpu[i] - d) <= TOL[prec] * np.linalg.norm(d), i
 
 
 @pytest.mark.parametrize("prec", [p.FP32, p.FP64])
