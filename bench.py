@@ -420,7 +420,9 @@ def run_jgs2(args, rank, world, local_rank):
                        check_every=chunk)
     x0 = torch.tensor(X, dtype=torch.float64, device=dev)
     v0 = torch.tensor(V0, dtype=torch.float64, device=dev)
-    bs = mesh.autotune(x0, v0, opts)
+    mesh.autotune(x0, v0, opts)
+    gbs, gtpv, cbs = mesh.launch_config(prec)
+    bs = {"gather_block": gbs, "gather_threads_per_vertex": gtpv, "correct_block": cbs}
     x, v = x0.clone(), v0.clone()
     for _ in range(args.warmup):
         mesh.step(x, v, opts, stream)

@@ -190,11 +190,17 @@ jgs2_status jgs2_mesh_create_batch(const jgs2_mesh_desc* descs, int32_t n_scenes
  * may be NULL). */
 jgs2_status jgs2_batch_report(const jgs2_mesh* mesh, int32_t* sweeps, int32_t* converged,
                               double* rel_residual);
-/* Times a few sweeps of the state (x, v: device [V][3] double, read only) with the vertex
- * kernels at 64, 128 and 256 threads per block and keeps the fastest for opts->precision;
- * *block_size (may be NULL) receives the choice. */
+/* Launch-shape autotuner: on the state (x, v: device [V][3] double, read only) times the
+ * gather kernel in each of its shapes (threads per block x threads per vertex: 64, 128,
+ * 256 x 1 and 128, 256 x 4; with 4 threads per vertex the incidences of a vertex are split
+ * over the lanes of its group) and the correction kernel at 64, 128 and 256 threads per
+ * block, and keeps the fastest of each for opts->precision. *block_size (may be NULL)
+ * receives the correction kernel's choice; jgs2_mesh_launch_config gives all three. */
 jgs2_status jgs2_autotune(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts,
                           void* stream, int32_t* block_size);
+/* The mesh's launch shapes for precision: config[0] gather threads per block, config[1]
+ * gather threads per vertex, config[2] correction threads per block (host int32_t[3]). */
+jgs2_status jgs2_mesh_launch_config(const jgs2_mesh* mesh, int32_t precision, int32_t* config);
 
 /* Offline stage (Secs. 5-6), host FP64: factorises the rest Hessian H_bar = M/h^2 + K_bar
  * of each distinct body once, computes A_i = (H_bar^{-1})_ii and the rows of

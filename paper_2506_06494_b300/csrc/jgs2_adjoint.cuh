@@ -111,25 +111,8 @@ __global__ void __launch_bounds__(128) k_lin_setup(DevMesh<T> m, T* __restrict__
       const T* up = m.cub_u + (size_t)s * 36 * m.cs + i;
 #pragma unroll
       for (int q = 0; q < 36; ++q) U[q] = up[(size_t)q * m.cs];
-      const T* Hp = m.pool_H + (size_t)p * kPoolStride;
-#pragma unroll
-      for (int r = 0; r < 12; ++r) {
-        T tr[3] = {T(0), T(0), T(0)};
-#pragma unroll
-        for (int c = 0; c < 12; ++c) {
-          const T h = __ldg(Hp + pk(r, c));
-          tr[0] += h * U[3 * c];
-          tr[1] += h * U[3 * c + 1];
-          tr[2] += h * U[3 * c + 2];
-        }
-        const T wu0 = w * U[3 * r], wu1 = w * U[3 * r + 1], wu2 = w * U[3 * r + 2];
-        Ht[0] += wu0 * tr[0];
-        Ht[1] += wu0 * tr[1];
-        Ht[2] += wu0 * tr[2];
-        Ht[3] += wu1 * tr[1];
-        Ht[4] += wu1 * tr[2];
-        Ht[5] += wu2 * tr[2];
-      }
+      T gdummy[3] = {T(0), T(0), T(0)};
+      slot_sums(m.pool_H + (size_t)p * kPoolStride, w, U, Ht, gdummy);
     }
     T Hf[9] = {Ht[0], Ht[1], Ht[2], Ht[1], Ht[3], Ht[4], Ht[2], Ht[4], Ht[5]}, RH[9], Hw[9];
 #pragma unroll

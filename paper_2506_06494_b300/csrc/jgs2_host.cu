@@ -218,8 +218,8 @@ jgs2_status mesh_create(const jgs2_mesh_desc* d, Mesh** out, const std::vector<i
     for (int l = 0; l < kSlice && s * kSlice + l < m->Vf; ++l) mx = std::max(mx, cnt[s * kSlice + l]);
     m->inc_off[s + 1] = m->inc_off[s] + mx * kSlice;
   }
-  for (int q = 0; q < 3; ++q) {
-    const int spb = (64 << q) / kSlice;  // slices per block of 64, 128, 256 vertices
+  for (int q = 0; q < 4; ++q) {
+    const int spb = (q < 3 ? (64 << q) : 32) / kSlice;  // slices per block of 64, 128, 256, 32 vertices
     for (int s0 = 0; s0 < ns; s0 += spb)
       m->inc_blk[q] = std::max(m->inc_blk[q], m->inc_off[std::min(s0 + spb, ns)] - m->inc_off[s0]);
   }
@@ -716,67 +716,80 @@ static jgs2_status contact_force_rebuild(Mesh* m, cudaStream_t s) {
   return JGS2_OK;
 }
 
-// Dynamic shared memory of k_gather at bs threads: the block's incidence entries.
-static size_t gather_smem(const Mesh* m, int bs) {
-  const int q = bs == 64 ? 0 : (bs == 256 ? 2 : 1);
+// Dynamic shared memory of k_gather for blocks of vpb vertices: the block's incidence
+// entries.
+static size_t gather_smem(const Mesh* m, int vpb) {
+  const int q = vpb == 64 ? 0 : (vpb == 256 ? 2 : (vpb == 32 ? 3 : 1));
   return (size_t)std::max(m->inc_blk[q], 4) * sizeof(int);
 }
+
+// k_gather launch shapes (threads per block, threads per vertex) the library builds.
+static const int kGatherShapes[5][2] = {{64, 1}, {128, 1}, {256, 1}, {128, 4}, {256, 4}};
 
 // Raises the dynamic shared memory limit of every k_gather variant to what this mesh needs
 // (once per new maximum; before any launch or graph capture of the mesh).
 static cudaError_t prepare_gather(const Mesh* m) {
   static size_t have = 48 * 1024;
-  const size_t need = gather_smem(m, 256) > gather_smem(m, 128) ? gather_smem(m, 256) : gather_smem(m, 128);
+  size_t need = 0;
+  for (int vpb : {32, 64, 128, 256}) need = std::max(need, gather_smem(m, vpb));
   if (need <= have) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   auto set = [&](auto kern) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
   };
-  set(k_gather<float, true, false, 64>);
-  set(k_gather<float, true, false, 128>);
-  set(k_gather<float, true, false, 256>);
-  set(k_gather<float, false, false, 64>);
-  set(k_gather<float, false, false, 128>);
-  set(k_gather<float, false, false, 256>);
-  set(k_gather<float, true, true, 64>);
-  set(k_gather<float, true, true, 128>);
-  set(k_gather<float, true, true, 256>);
-  set(k_gather<float, false, true, 64>);
-  set(k_gather<float, false, true, 128>);
-  set(k_gather<float, false, true, 256>);
-  set(k_gather<double, true, false, 64>);
-  set(k_gather<double, true, false, 128>);
-  set(k_gather<double, true, false, 256>);
-  set(k_gather<double, false, false, 64>);
-  set(k_gather<double, false, false, 128>);
-  set(k_gather<double, false, false, 256>);
-  set(k_gather<double, true, true, 64>);
-  set(k_gather<double, true, true, 128>);
-  set(k_gather<double, true, true, 256>);
-  set(k_gather<double, false, true, 64>);
-  set(k_gather<double, false, true, 128>);
-  set(k_gather<double, false, true, 256>);
+#define JGS2_SET(T)                                            \
+  set(k_gather<T, true, false, 64, 1>);                        \
+  set(k_gather<T, true, false, 128, 1>);                       \
+  set(k_gather<T, true, false, 256, 1>);                       \
+  set(k_gather<T, true, false, 128, 4>);                       \
+  set(k_gather<T, true, false, 256, 4>);                       \
+  set(k_gather<T, false, false, 64, 1>);                       \
+  set(k_gather<T, false, false, 128, 1>);                      \
+  set(k_gather<T, false, false, 256, 1>);                      \
+  set(k_gather<T, false, false, 128, 4>);                      \
+  set(k_gather<T, false, false, 256, 4>);                      \
+  set(k_gather<T, true, true, 64, 1>);                         \
+  set(k_gather<T, true, true, 128, 1>);                        \
+  set(k_gather<T, true, true, 256, 1>);                        \
+  set(k_gather<T, true, true, 128, 4>);                        \
+  set(k_gather<T, true, true, 256, 4>);                        \
+  set(k_gather<T, false, true, 64, 1>);                        \
+  set(k_gather<T, false, true, 128, 1>);                       \
+  set(k_gather<T, false, true, 256, 1>);                       \
+  set(k_gather<T, false, true, 128, 4>);                       \
+  set(k_gather<T, false, true, 256, 4>);
+  JGS2_SET(float)
+  JGS2_SET(double)
+#undef JGS2_SET
   if (e == cudaSuccess) have = need;
   return e;
 }
 
-// k_gather / k_correct with a runtime block size (64, 128 or 256 threads)
+// k_gather with a runtime shape: bs threads per block (64, 128 or 256), tpv threads per
+// vertex (1; or 4 with 128 or 256 threads)
 template <typename T, bool BATCH>
-static void launch_gather(DevMesh<T>& d, const Mesh* m, bool corr, int bs, cudaStream_t s, StepState* st,
+static void launch_gather(DevMesh<T>& d, const Mesh* m, bool corr, int bs, int tpv, cudaStream_t s, StepState* st,
                           double* partial, double* trace, int rec) {
   const int Vf = d.Vf;
-  const size_t sm = gather_smem(m, bs);
-#define JGS2_G(B)                                                                                  \
-  if (corr)                                                                                        \
-    k_gather<T, true, BATCH, B><<<(Vf + B - 1) / B, B, sm, s>>>(d, st, partial, trace, rec);       \
-  else                                                                                             \
-    k_gather<T, false, BATCH, B><<<(Vf + B - 1) / B, B, sm, s>>>(d, st, partial, trace, rec);
-  if (bs == 64) {
-    JGS2_G(64)
+#define JGS2_G(B, P)                                                                                      \
+  {                                                                                                       \
+    const size_t sm = gather_smem(m, B / P);                                                              \
+    const int nb = (Vf + B / P - 1) / (B / P);                                                            \
+    if (corr)                                                                                             \
+      k_gather<T, true, BATCH, B, P><<<nb, B, sm, s>>>(d, st, partial, trace, rec);                       \
+    else                                                                                                  \
+      k_gather<T, false, BATCH, B, P><<<nb, B, sm, s>>>(d, st, partial, trace, rec);                      \
+  }
+  if (tpv == 4 && bs == 256) {
+    JGS2_G(256, 4)
+  } else if (tpv == 4) {
+    JGS2_G(128, 4)
+  } else if (bs == 64) {
+    JGS2_G(64, 1)
   } else if (bs == 256) {
-    JGS2_G(256)
+    JGS2_G(256, 1)
   } else {
-    JGS2_G(128)
+    JGS2_G(128, 1)
   }
 #undef JGS2_G
 }
@@ -900,7 +913,8 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
   // line-search pass: one full wave of resident blocks (SM count x blocks per SM at this
   // kernel's registers and shared memory), grid-stride over tet tiles and vertices
   const int nbE = std::max(1, std::min(std::max(nbT, nbV), energy_blocks<T>()));
-  const int bs = m->bs[sizeof(T) == 4 ? 1 : 0];
+  const int pi = sizeof(T) == 4 ? 1 : 0;
+  const int bs = m->bs[pi], gbs = m->gbs[pi], gtpv = m->gtpv[pi];
   const int chunk = std::max(1, o.check_every);
   const bool prof = L.prof;
   jgs2_status gs = ensure_gstream(m);
@@ -923,8 +937,16 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
     jgs2_status cst = contact_force_rebuild(m, s);
     if (cst != JGS2_OK) return cst;
   }
-  const long key = (((((((long)(sizeof(T) == 4) * 3 + o.correction) * 2 + (o.line_search != 0)) * 2 + m->contact) * 2 +
-                     (prof ? 1 : 0)) * 2 + (o.record_trace != 0)) * 512 + bs) * 8192 + chunk + (1L << 40);
+  long key = (long)(sizeof(T) == 4);
+  key = key * 3 + o.correction;
+  key = key * 2 + (o.line_search != 0);
+  key = key * 2 + m->contact;
+  key = key * 2 + (prof ? 1 : 0);
+  key = key * 2 + (o.record_trace != 0);
+  key = key * 512 + bs;
+  key = key * 512 + gbs;
+  key = key * 8 + gtpv;
+  key = key * 8192 + chunk + (1L << 60);
   const bool same_view = m->gdev.size() == sizeof(d) && std::memcmp(m->gdev.data(), &d, sizeof(d)) == 0;
   if (m->graph_key != key || !same_view) {
     if (m->graph) cudaGraphExecDestroy(m->graph);
@@ -978,7 +1000,9 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
       if (m->contact) join(m->gfork[1]);
       if (nbV > 0)
         group(JGS2_K_GATHER, 1, s,
-              [&] { launch_gather<T, false>(d, m, corr, bs, s, m->d_state, m->d_partial, m->d_trace, o.record_trace); });
+              [&] {
+                launch_gather<T, false>(d, m, corr, gbs, gtpv, s, m->d_state, m->d_partial, m->d_trace, o.record_trace);
+              });
       // cubature pool after the gather, whose g and R at the pool elements' corners it reads
       if (pool)
         group(JGS2_K_POOL, 1, s, [&] {
@@ -1082,7 +1106,8 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
   const bool corr = o.correction != JGS2_CORR_OFF && m->nP > 0;
   const int S = m->n_scenes;
   const int nbV = (m->Vf + 127) / 128, nbT = (m->T + 127) / 128;
-  const int bs = m->bs[sizeof(T) == 4 ? 1 : 0];
+  const int pi = sizeof(T) == 4 ? 1 : 0;
+  const int bs = m->bs[pi], gbs = m->gbs[pi], gtpv = m->gtpv[pi];
   const int chunk = std::max(1, o.check_every);
   StepState init;
   std::memset(&init, 0, sizeof(init));
@@ -1093,8 +1118,9 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
   CK(cudaMemsetAsync(m->d_sacc, 0, sizeof(double) * kSceneAcc * S, s));
   CK(cudaMemsetAsync(m->d_ndone, 0, sizeof(int32_t), s));
   const bool prof = L.prof;
-  const long key = (((((long)(sizeof(T) == 4) * 3 + o.correction) * 2 + (o.line_search != 0)) * 2 + (prof ? 1 : 0)) *
-                        512 + bs) * 4096 + chunk + (long)(o.max_sweeps) * 1000003L + (long)(o.rel_tol * 1e12);
+  const long key = ((((((long)(sizeof(T) == 4) * 3 + o.correction) * 2 + (o.line_search != 0)) * 2 + (prof ? 1 : 0)) *
+                          512 + bs) * 4096 + gbs * 8 + gtpv) * 4096 + chunk + (long)(o.max_sweeps) * 1000003L +
+                        (long)(o.rel_tol * 1e12);
   const bool same_view = m->gdev.size() == sizeof(d) && std::memcmp(m->gdev.data(), &d, sizeof(d)) == 0;
   if (m->graph_key != key || !same_view) {
     if (m->graph) cudaGraphExecDestroy(m->graph);
@@ -1128,7 +1154,8 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
     for (int q = 0; q < chunk; ++q) {
       timed = prof && q == chunk - 1;
       group(JGS2_K_ELEM, 1, s, [&] { k_elem<T, true><<<nbT, 128, 0, s>>>(d, m->d_state); });
-      group(JGS2_K_GATHER, 1, s, [&] { launch_gather<T, true>(d, m, corr, bs, s, m->d_state, m->d_partial, m->d_trace, 0); });
+      group(JGS2_K_GATHER, 1, s,
+            [&] { launch_gather<T, true>(d, m, corr, gbs, gtpv, s, m->d_state, m->d_partial, m->d_trace, 0); });
       // the cubature pool after the gather, whose g and R at the corners it reads
       if (corr) {
         group(JGS2_K_POOL, 1, s, [&] { k_pool<T, true><<<(m->nP + kPoolWarps - 1) / kPoolWarps, 32 * kPoolWarps, 0, s>>>(d, m->d_state); });
@@ -1530,16 +1557,18 @@ jgs2_status batch_report(const Mesh* m, int32_t* sweeps, int32_t* converged, dou
   return JGS2_OK;
 }
 
-// Autotuner: times a few sweeps of the state (x, v) with k_gather / k_correct at 64, 128
-// and 256 threads per block and keeps the fastest for this precision.
+// Autotuner: on the state (x, v), times k_gather in each launch shape (threads per block x
+// threads per vertex: 64/128/256 x 1, 128/256 x 4) and k_correct at 64, 128 and 256 threads
+// per block, and keeps the fastest of each for this precision.
 template <typename T>
 static jgs2_status autotune_impl(Mesh* m, double* x, double* v, const jgs2_step_opts* o, cudaStream_t s,
                                  int32_t* chosen) {
   jgs2_status st = ensure_prec<T>(m);
   if (st != JGS2_OK) return st;
+  const int pi = sizeof(T) == 4 ? 1 : 0;
   if (m->Vf == 0) {
     // nothing to time: the step of a mesh without free vertices launches no sweep kernel
-    if (chosen) *chosen = m->bs[sizeof(T) == 4 ? 1 : 0];
+    if (chosen) *chosen = m->bs[pi];
     return JGS2_OK;
   }
   DevMesh<T> d = dev_view<T>(m);
@@ -1553,43 +1582,54 @@ static jgs2_status autotune_impl(Mesh* m, double* x, double* v, const jgs2_step_
   init.rel_tol = -1.0;
   CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
   k_elem<T, false><<<(m->T + 127) / 128, 128, 0, s>>>(d, m->d_state);
-  if (corr) {
-    launch_gather<T, false>(d, m, corr, 128, s, m->d_state, m->d_partial, m->d_trace, 0);
-    k_pool<T, true><<<(m->nP + kPoolWarps - 1) / kPoolWarps, 32 * kPoolWarps, 0, s>>>(d, m->d_state);
-  }
-  const int cands[3] = {64, 128, 256};
-  float best = 1e30f;
-  int pick = 128;
+  launch_gather<T, false>(d, m, corr, 128, 1, s, m->d_state, m->d_partial, m->d_trace, 0);
+  if (corr) k_pool<T, true><<<(m->nP + kPoolWarps - 1) / kPoolWarps, 32 * kPoolWarps, 0, s>>>(d, m->d_state);
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  // every timed launch is sweep 0 of a fresh state: it sets |g(x^0)| and never stops the
-  // step (rel_tol < 0, no sweep cap), so each launch does the full work
-  for (int c : cands) {
-    for (int rep = 0; rep < 2; ++rep) {
-      launch_gather<T, false>(d, m, corr, c, s, m->d_state, m->d_partial, m->d_trace, 0);
-      if (corr) launch_correct<T, false>(d, c, s, m->d_state, m->d_partial, m->d_trace, 0);
-    }
-    CK(cudaEventRecord(e0, s));
-    for (int rep = 0; rep < 5; ++rep) {
-      launch_gather<T, false>(d, m, corr, c, s, m->d_state, m->d_partial, m->d_trace, 0);
-      if (corr) launch_correct<T, false>(d, c, s, m->d_state, m->d_partial, m->d_trace, 0);
-    }
-    CK(cudaEventRecord(e1, s));
-    CK(cudaEventSynchronize(e1));
+  // times `launch` (2 untimed, 5 timed launches); every launch is sweep 0 of a fresh state:
+  // it sets |g(x^0)| and never stops the step (rel_tol < 0, no sweep cap), so each launch
+  // does the full work
+  auto time_it = [&](auto&& launch) -> float {
+    for (int rep = 0; rep < 2; ++rep) launch();
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 5; ++rep) launch();
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  float best = 1e30f;
+  int gpick = 0;
+  for (int c = 0; c < 5; ++c) {
+    const int b = kGatherShapes[c][0], p = kGatherShapes[c][1];
+    const float ms =
+        time_it([&] { launch_gather<T, false>(d, m, corr, b, p, s, m->d_state, m->d_partial, m->d_trace, 0); });
     if (ms < best) {
       best = ms;
-      pick = c;
+      gpick = c;
+    }
+  }
+  int cpick = 128;
+  if (corr) {
+    best = 1e30f;
+    for (int c : {64, 128, 256}) {
+      const float ms = time_it([&] { launch_correct<T, false>(d, c, s, m->d_state, m->d_partial, m->d_trace, 0); });
+      if (ms < best) {
+        best = ms;
+        cpick = c;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CK(cudaGetLastError());
-  m->bs[sizeof(T) == 4 ? 1 : 0] = pick;
+  m->bs[pi] = cpick;
+  m->gbs[pi] = kGatherShapes[gpick][0];
+  m->gtpv[pi] = kGatherShapes[gpick][1];
   m->graph_key = -1;
-  if (chosen) *chosen = pick;
+  if (chosen) *chosen = cpick;
   return JGS2_OK;
 }
 
@@ -1664,7 +1704,7 @@ static jgs2_status adjoint_impl(Mesh* m, const double* xt, const double* vt, con
   CK(cudaMemcpyAsync(m->d_state, &init, sizeof(StepState), cudaMemcpyHostToDevice, s));
   // H_ii, R_i at x* (and the rotated cubature element Hessians)
   k_elem<T, false><<<nbT, 128, 0, s>>>(d, m->d_state);
-  launch_gather<T, false>(d, m, true, 128, s, m->d_state, m->d_partial, m->d_trace, 0);
+  launch_gather<T, false>(d, m, true, 128, 1, s, m->d_state, m->d_partial, m->d_trace, 0);
   if (corr) k_pool<T, true><<<(m->nP + kPoolWarps - 1) / kPoolWarps, 32 * kPoolWarps, 0, s>>>(d, m->d_state);
   if (corr)
     k_lin_setup<T, true><<<nbV, 128, 0, s>>>(d, b.a_lin);
@@ -2003,6 +2043,17 @@ jgs2_status jgs2_batch_report(const jgs2_mesh* mesh, int32_t* sweeps, int32_t* c
 jgs2_status jgs2_autotune(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts, void* stream,
                           int32_t* block_size) {
   return autotune(reinterpret_cast<Mesh*>(mesh), x, v, opts, stream, block_size);
+}
+
+jgs2_status jgs2_mesh_launch_config(const jgs2_mesh* mesh, int32_t precision, int32_t* config) {
+  const Mesh* m = reinterpret_cast<const Mesh*>(mesh);
+  if (!m || !config) return fail(JGS2_EINVAL, "null argument");
+  if (precision != JGS2_FP64 && precision != JGS2_FP32) return fail(JGS2_EINVAL, "bad precision");
+  const int pi = precision == JGS2_FP32 ? 1 : 0;
+  config[0] = m->gbs[pi];
+  config[1] = m->gtpv[pi];
+  config[2] = m->bs[pi];
+  return JGS2_OK;
 }
 
 void jgs2_mesh_destroy(jgs2_mesh* mesh) { delete reinterpret_cast<Mesh*>(mesh); }

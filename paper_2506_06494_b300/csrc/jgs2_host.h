@@ -49,7 +49,7 @@ struct Mesh {
   std::vector<int> perm, iperm;    // internal <-> caller vertex
   std::vector<int> tperm, tiperm;  // internal <-> caller tet
   std::vector<int> inc_off, inc_len, inc;
-  int inc_blk[3] = {0, 0, 0};     // largest incidence range of a 64/128/256-vertex block (entries)
+  int inc_blk[4] = {0, 0, 0, 0};  // largest incidence range of a 64/128/256/32-vertex block (entries)
   // cubature records, internal order: [Vf][n_cub]
   int n_cub = 0, nP = 0, cub_version = 0, pool_version = -1;
   bool device_ready = false;
@@ -74,8 +74,11 @@ struct Mesh {
   int32_t *d_vscene = nullptr, *d_tscene = nullptr, *d_ndone = nullptr;
   SceneState* d_scenes = nullptr;
   double* d_sacc = nullptr;
-  // block size of k_gather / k_correct per precision (autotuned, default 128)
+  // launch shapes per precision (autotuned): k_correct block size, k_gather block size and
+  // threads per vertex
   int bs[2] = {128, 128};
+  int gbs[2] = {128, 128};
+  int gtpv[2] = {1, 1};
   // captured sweep chunk of a batch step: key = (precision, correction, line search, bs, chunk)
   cudaGraphExec_t graph = nullptr;
   long graph_key = -1;

@@ -16,8 +16,8 @@
 //               (12x3) as [slot][36][cs] (cs = Vf rounded up to 4) so a warp's loads are
 //               coalesced and a block's rows can be bulk-copied.
 //   pool        per sweep, one 16-byte aligned row per cubature element: the rotated
-//               12x12 element Hessian (78 packed values), then
-//               the 12 rotated gradient entries of every cubature element.
+//               12x12 element Hessian as its ten 3x3 corner blocks (a, c), a <= c, in row
+//               order (90 values), then the 12 rotated gradient entries, 2 pad.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -29,11 +29,11 @@ constexpr int kMaxCub = 8;       // cubature slots per vertex at most
 constexpr int kLsTrials = 8;     // line-search steps alpha = 2^-j, j < kLsTrials
 constexpr int kPairTrialBlocks = 148 * 4;  // blocks of the line-search barrier-trial pass (2 x kLsTrials sums each)
 constexpr int kEnergyBlocksMax = 148 * 8;  // blocks of the line-search energy pass, at most
-constexpr int kPackedH = 78;     // 12x12 symmetric, upper triangle row-major
+constexpr int kPoolH = 90;       // 12x12 symmetric as ten 3x3 corner blocks (a <= c)
 // Row stride of the per-slot cubature record arrays: Vf rounded up to 4 entries, so that
 // every row starts on a 16-byte boundary.
 __host__ __device__ constexpr int cub_stride(int Vf) { return ((Vf + 3) / 4) * 4; }
-constexpr int kPoolStride = 92;  // pool row: 78 packed Hessian entries, 12 gradient entries, 2 pad
+constexpr int kPoolStride = 104;  // pool row: 90 Hessian block entries, 12 gradient entries, 2 pad
 
 template <typename T>
 struct alignas(16) TetRec {
@@ -169,7 +169,7 @@ struct DevMesh {
   const T* cub_w;           // [n_cub][cs]
   const T* cub_u;           // [n_cub][36][cs]
   const int32_t* pool_tet;  // [nP]
-  T* pool_H;                // [nP][92] packed rotated Hessian (78), rotated gradient (12), pad
+  T* pool_H;                // [nP][104] rotated Hessian blocks (90), rotated gradient (12), pad
   T* pool_G;                // [nP][12]
   T* pool_R;                // [nP][4][9] corner rotations of the last pool pass
   double* xt;               // [V][3]

@@ -376,9 +376,11 @@ __device__ __forceinline__ void gather_vertex_rec(const DevMesh<T>& m, int v, T 
 //         det-Hessian term of dP/dF contributes nothing to a diagonal block because
 //         eps_jln b_j b_l = 0, so this block is exact and positive definite.)
 //   Fs += V_e F_e,  W += V_e
-template <typename T>
+// With TPV > 1 lanes per vertex, lane q of the vertex's group takes incidences q, q + TPV,
+// ... and the group's partial sums are added by the caller.
+template <typename T, int TPV = 1>
 __device__ __forceinline__ void gather_vertex(const DevMesh<T>& m, int v, const int* __restrict__ incv, T (&g)[3],
-                                              T (&H)[6], T (&Fs)[9], T& W) {
+                                              T (&H)[6], T (&Fs)[9], T& W, int q0 = 0) {
   const int n = m.inc_len[v];
 #pragma unroll
   for (int q = 0; q < 3; ++q) g[q] = T(0);
@@ -387,9 +389,10 @@ __device__ __forceinline__ void gather_vertex(const DevMesh<T>& m, int v, const 
 #pragma unroll
   for (int q = 0; q < 9; ++q) Fs[q] = T(0);
   W = T(0);
-  // four incidences per trip: their record loads are in flight together
-#pragma unroll 4
-  for (int j = 0; j < n; ++j) {
+  // four incidences per trip (two with lanes sharing the vertex): their record loads are
+  // in flight together
+#pragma unroll(TPV == 1 ? 4 : 2)
+  for (int j = q0; j < n; j += TPV) {
     const int ent = incv[j * kSlice];
     const int t = ent >> 2, c = ent & 3;
     const FRec<T> r = m.frec[t];
@@ -538,43 +541,61 @@ __device__ void polar_rotation(const T (&F)[9], T (&R)[9]) {
     for (int j = 0; j < 3; ++j) R[3 * i + j] = u1[i] * v1[j] + u2[i] * v2[j] + u3[i] * v3[j];
 }
 
-// Packed index of (r, c), r <= c, of a symmetric 12x12 (upper triangle, row-major).
-__host__ __device__ constexpr int pk(int r, int c) {
-  return r <= c ? r * 12 - (r * (r - 1)) / 2 + (c - r) : c * 12 - (c * (c - 1)) / 2 + (r - c);
+// Pool row layout of a symmetric 12x12 (corner blocks): the 3x3 blocks (a, c), a <= c, of
+// corners a and c, in row order (0,0) (0,1) (0,2) (0,3) (1,1) (1,2) (1,3) (2,2) (2,3) (3,3),
+// each row-major. Block b of corner pair (a, c): 4a - a(a-1)/2 + (c - a).
+__host__ __device__ constexpr int pool_block(int a, int c) { return 4 * a - (a * (a - 1)) / 2 + (c - a); }
+__host__ __device__ constexpr int pool_block_row(int b) { return b < 4 ? 0 : (b < 7 ? 1 : (b < 9 ? 2 : 3)); }
+__host__ __device__ constexpr int pool_block_col(int b) {
+  return pool_block_row(b) + (b - pool_block(pool_block_row(b), pool_block_row(b)));
+}
+// Index of entry (r, c) of the symmetric 12x12 in the pool row.
+__host__ __device__ constexpr int pool_idx(int r, int c) {
+  return (r / 3) <= (c / 3) ? 9 * pool_block(r / 3, c / 3) + 3 * (r % 3) + (c % 3)
+                            : 9 * pool_block(c / 3, r / 3) + 3 * (c % 3) + (r % 3);
 }
 
-// Row and column of packed entry q (upper triangle of a symmetric 12x12, row-major).
-__host__ __device__ constexpr int pk_row(int q) {
-  int r = 0;
-  while (q >= 12 - r) {
-    q -= 12 - r;
-    ++r;
-  }
-  return r;
-}
-__host__ __device__ constexpr int pk_col(int q) {
-  int r = 0;
-  while (q >= 12 - r) {
-    q -= 12 - r;
-    ++r;
-  }
-  return r + q;
-}
-
-// One entry q of a streamed pool row (indices fixed at compile time): packed Hessian
-// entries accumulate M = H' U over the upper triangle, gradient entries g~' += w U^T G.
+// One entry q of a streamed pool row (indices fixed at compile time). Block (a, c) entries
+// accumulate P = H'_ac U_c (3x3); its last entry closes the block: Q = U_a^T P and
+// H~' += w (Q + Q^T) (w Q for a diagonal block, which is symmetric). Gradient entries:
+// g~' += w U^T G.
 template <int Q, typename T>
-__device__ __forceinline__ void pool_entry(T h, T w, const T (&U)[36], T (&M)[36], T (&gt)[3]) {
-  if constexpr (Q < kPackedH) {
-    constexpr int r = pk_row(Q), c = pk_col(Q);
+__device__ __forceinline__ void pool_entry(T h, T w, const T (&U)[36], T (&P)[9], T (&Ht)[6], T (&gt)[3]) {
+  if constexpr (Q < kPoolH) {
+    constexpr int b = Q / 9, e = Q % 9, i = e / 3, j = e % 3;
+    constexpr int a = pool_block_row(b), c = pool_block_col(b);
+    if constexpr (e == 0) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) M[3 * r + k] += h * U[3 * c + k];
-    if constexpr (r != c) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) M[3 * c + k] += h * U[3 * r + k];
+      for (int q = 0; q < 9; ++q) P[q] = T(0);
     }
-  } else if constexpr (Q < kPackedH + 12) {
-    constexpr int r = Q - kPackedH;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) P[3 * i + k] += h * U[3 * (3 * c + j) + k];
+    if constexpr (e == 8) {
+      T Qm[9];
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          Qm[3 * l + k] = U[3 * (3 * a) + l] * P[k] + U[3 * (3 * a + 1) + l] * P[3 + k] +
+                          U[3 * (3 * a + 2) + l] * P[6 + k];
+      if constexpr (a == c) {
+        Ht[0] += w * Qm[0];
+        Ht[1] += w * Qm[1];
+        Ht[2] += w * Qm[2];
+        Ht[3] += w * Qm[4];
+        Ht[4] += w * Qm[5];
+        Ht[5] += w * Qm[8];
+      } else {
+        Ht[0] += w * (Qm[0] + Qm[0]);
+        Ht[1] += w * (Qm[1] + Qm[3]);
+        Ht[2] += w * (Qm[2] + Qm[6]);
+        Ht[3] += w * (Qm[4] + Qm[4]);
+        Ht[4] += w * (Qm[5] + Qm[7]);
+        Ht[5] += w * (Qm[8] + Qm[8]);
+      }
+    }
+  } else if constexpr (Q < kPoolH + 12) {
+    constexpr int r = Q - kPoolH;
     const T wg = w * h;
 #pragma unroll
     for (int k = 0; k < 3; ++k) gt[k] += wg * U[3 * r + k];
@@ -585,43 +606,31 @@ template <typename T>
 __device__ __forceinline__ void load4(const T* __restrict__ p, T (&o)[4]);
 
 template <int Q4, typename T>
-__device__ __forceinline__ void pool_chunk(const T* __restrict__ Hp, T w, const T (&U)[36], T (&M)[36],
+__device__ __forceinline__ void pool_chunk(const T* __restrict__ Hp, T w, const T (&U)[36], T (&P)[9], T (&Ht)[6],
                                            T (&gt)[3]) {
   T hv[4];
   load4(Hp + 4 * Q4, hv);
-  pool_entry<4 * Q4 + 0>(hv[0], w, U, M, gt);
-  pool_entry<4 * Q4 + 1>(hv[1], w, U, M, gt);
-  pool_entry<4 * Q4 + 2>(hv[2], w, U, M, gt);
-  pool_entry<4 * Q4 + 3>(hv[3], w, U, M, gt);
+  pool_entry<4 * Q4 + 0>(hv[0], w, U, P, Ht, gt);
+  pool_entry<4 * Q4 + 1>(hv[1], w, U, P, Ht, gt);
+  pool_entry<4 * Q4 + 2>(hv[2], w, U, P, Ht, gt);
+  pool_entry<4 * Q4 + 3>(hv[3], w, U, P, Ht, gt);
 }
 
 template <typename T, int... Q4>
-__device__ __forceinline__ void pool_row(const T* __restrict__ Hp, T w, const T (&U)[36], T (&M)[36], T (&gt)[3],
-                                         std::integer_sequence<int, Q4...>) {
-  (pool_chunk<Q4>(Hp, w, U, M, gt), ...);
+__device__ __forceinline__ void pool_row(const T* __restrict__ Hp, T w, const T (&U)[36], T (&P)[9], T (&Ht)[6],
+                                         T (&gt)[3], std::integer_sequence<int, Q4...>) {
+  (pool_chunk<Q4>(Hp, w, U, P, Ht, gt), ...);
 }
 
-// One cubature slot of Eq. cubature: the pool row Hp (packed rotated element Hessian, then
+// One cubature slot of Eq. cubature: the pool row Hp (rotated element Hessian blocks, then
 // the rotated corner gradients) against the slot's weight w and U_bar rows U (12x3):
-// H~' += w U^T H' U, g~' += w U^T G'.
+// H~' += w U^T H' U = w sum_{a <= c} (U_a^T H'_ac U_c + its transpose if a != c),
+// g~' += w U^T G'. Blocks are closed one at a time, so only a 3x3 partial product is
+// live besides U.
 template <typename T>
 __device__ __forceinline__ void slot_sums(const T* __restrict__ Hp, T w, const T (&U)[36], T (&Ht)[6], T (&gt)[3]) {
-  // M = H' U (12x3) streamed from the upper triangle in 16-byte loads
-  T M[36];
-#pragma unroll
-  for (int q = 0; q < 36; ++q) M[q] = T(0);
-  pool_row(Hp, w, U, M, gt, std::make_integer_sequence<int, (kPackedH + 12 + 3) / 4>{});
-  // H~' += w U^T M (symmetric: six entries)
-#pragma unroll
-  for (int r = 0; r < 12; ++r) {
-    const T wu0 = w * U[3 * r], wu1 = w * U[3 * r + 1], wu2 = w * U[3 * r + 2];
-    Ht[0] += wu0 * M[3 * r];
-    Ht[1] += wu0 * M[3 * r + 1];
-    Ht[2] += wu0 * M[3 * r + 2];
-    Ht[3] += wu1 * M[3 * r + 1];
-    Ht[4] += wu1 * M[3 * r + 2];
-    Ht[5] += wu2 * M[3 * r + 2];
-  }
+  T P[9];
+  pool_row(Hp, w, U, P, Ht, gt, std::make_integer_sequence<int, (kPoolH + 12 + 3) / 4>{});
 }
 
 // Cubature sums for vertex i over its n_cub slots, records read directly from global memory.
@@ -864,12 +873,12 @@ __global__ void __launch_bounds__(32 * kPoolWarps) k_pool(DevMesh<T> m, const St
   __syncwarp();
   const T mi = rec.mq * T(m.inv_h2);
   T* Hrow = m.pool_H + (size_t)p * kPoolStride;
-  for (int e = lane; e < kPackedH + 12; e += 32) {
-    if (e < kPackedH) {
-      // packed entry (r, c), r <= c, of H' = blockdiag(R)^T H_e blockdiag(R), with
-      // H_e[(a,i),(c,k)] = V sum_{j,l} b_a[j] A[(i,j),(k,l)] b_c[l] + m_e/h^2 delta
-      const int r = pk_row(e), c = pk_col(e);
-      const int a = r / 3, jj = r % 3, cc = c / 3, ll = c % 3;
+  for (int e = lane; e < kPoolH + 12; e += 32) {
+    if (e < kPoolH) {
+      // entry (jj, ll) of block (a, cc), a <= cc, of H' = blockdiag(R)^T H_e blockdiag(R),
+      // with H_e[(a,i),(c,k)] = V sum_{j,l} b_a[j] A[(i,j),(k,l)] b_c[l] + m_e/h^2 delta
+      const int blk = e / 9, q = e % 9;
+      const int a = pool_block_row(blk), cc = pool_block_col(blk), jj = q / 3, ll = q % 3;
       T Hac[9];
 #pragma unroll
       for (int i = 0; i < 3; ++i)
@@ -893,7 +902,7 @@ __global__ void __launch_bounds__(32 * kPoolWarps) k_pool(DevMesh<T> m, const St
       Hrow[e] = v;
     } else {
       // rotated corner gradient entry (a, j)
-      const int q = e - kPackedH, a = q / 3, j = q % 3;
+      const int q = e - kPoolH, a = q / 3, j = q % 3;
       T ga[3];
       if (ASM) {
 #pragma unroll
@@ -970,10 +979,17 @@ __device__ __forceinline__ void finalize_sweep(StepState* st, double r2, double 
 // the correction on, R_i = polar(F_i) (Eq. tilde_phi). Writes g, H, R as [18][Vf] for
 // phase 2 and the FP64 partial sums |g|^2 and g.D_J. Without the correction D = D_J and
 // this kernel closes the sweep's reduction.
-template <typename T, bool CORR, bool BATCH, int BS>
+// TPV threads per vertex (1 or 4; BS / TPV vertices per block, a whole number of 32-vertex
+// slices): with 4, the lanes of a vertex's group split its incidences and add their sums
+// with warp shuffles, so more record loads are in flight per vertex; every lane of the group
+// then holds the vertex's sums and lane 0 writes its results.
+template <typename T, bool CORR, bool BATCH, int BS, int TPV = 1>
 __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
     k_gather(DevMesh<T> m, StepState* st, double* __restrict__ partial /* [3][grid] */,
              double* __restrict__ trace, int record) {
+  static_assert(TPV == 1 || TPV == 4, "1 or 4 threads per vertex");
+  static_assert((BS / TPV) % kSlice == 0, "whole slices per block");
+  constexpr int VPB = BS / TPV;
   if (!BATCH && st->done) return;
   __shared__ double red[96];
   __shared__ Acc<T> sred[96];
@@ -981,7 +997,7 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
   // copy it into shared memory first (coalesced 16-byte loads), so that each incidence's
   // record loads do not wait on a global load of its entry
   extern __shared__ __align__(16) int s_inc[];
-  const int s0 = blockIdx.x * (BS / kSlice), s1 = min(s0 + BS / kSlice, m.n_slices);
+  const int s0 = blockIdx.x * (VPB / kSlice), s1 = min(s0 + VPB / kSlice, m.n_slices);
   const int e0 = m.inc_off[s0];
   {
     const int4* src = reinterpret_cast<const int4*>(m.inc + e0);
@@ -990,13 +1006,38 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
     for (int q = threadIdx.x; q < n4; q += BS) dst[q] = __ldg(src + q);
   }
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * VPB + (int)threadIdx.x / TPV;
+  const int lane_v = (int)threadIdx.x % TPV;
   Acc<T> acc[3];  // |g|^2, g.D_J, |D_J|^2
   const int sc = (BATCH && i < m.Vf) ? m.v_scene[i] : -1;
   const bool active = i < m.Vf && (!BATCH || !m.scenes[sc].done);
+  T g[3], H[6], Fs[9], W;
+  if (active) gather_vertex<T, TPV>(m, i, s_inc + (m.inc_off[i / kSlice] - e0) + i % kSlice, g, H, Fs, W, lane_v);
+  if (TPV > 1) {
+    // groups are aligned runs of TPV lanes of one warp; every lane takes part (inactive
+    // lanes add zeros)
+    if (!active) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) g[q] = T(0);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) H[q] = T(0);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Fs[q] = T(0);
+      W = T(0);
+    }
+#pragma unroll
+    for (int o = 1; o < TPV; o <<= 1) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) g[q] += __shfl_xor_sync(0xffffffffu, g[q], o);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) H[q] += __shfl_xor_sync(0xffffffffu, H[q], o);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Fs[q] += __shfl_xor_sync(0xffffffffu, Fs[q], o);
+      W += __shfl_xor_sync(0xffffffffu, W, o);
+    }
+  }
+  const bool writer = active && lane_v == 0;
   if (active) {
-    T g[3], H[6], Fs[9], W;
-    gather_vertex(m, i, s_inc + (m.inc_off[i / kSlice] - e0) + i % kSlice, g, H, Fs, W);
     T ui[3], dz[3];
     load3(m.u, i, ui);
     load3(m.dz, i, dz);
@@ -1018,7 +1059,7 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
         for (int q = 0; q < 6; ++q) H[q] += T(m.c.bH[q * V + i]);
         lim = T(0.45 * fmin(m.c.rc - m.c.dhat, m.c.dmin[i]));
       }
-      m.c.lim[i] = double(lim);
+      if (writer) m.c.lim[i] = double(lim);
     }
     T dj[3];
     {
@@ -1028,33 +1069,37 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
       if (m.vmask && !m.vmask[i]) dj[0] = dj[1] = dj[2] = T(0);  // not this colour
     }
     Vec4<T> djv{dj[0], dj[1], dj[2], T(0)};
-    m.DJ[i] = djv;
+    if (writer) m.DJ[i] = djv;
     if (CORR) {
       T R[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) Fs[q] /= W;
       polar_rotation(Fs, R);
-      T* o = m.ghr + i;
-      const size_t S = m.Vf;
+      if (writer) {
+        T* o = m.ghr + i;
+        const size_t S = m.Vf;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) o[q * S] = g[q];
+        for (int q = 0; q < 3; ++q) o[q * S] = g[q];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) o[(3 + q) * S] = H[q];
+        for (int q = 0; q < 6; ++q) o[(3 + q) * S] = H[q];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) o[(9 + q) * S] = R[q];
-    } else {
+        for (int q = 0; q < 9; ++q) o[(9 + q) * S] = R[q];
+      }
+    } else if (writer) {
       m.D[i] = djv;
     }
+    if (writer) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      acc[0].add_prod(g[q], g[q]);
-      acc[1].add_prod(g[q], dj[q]);
-      if (!BATCH) acc[2].add_prod(dj[q], dj[q]);
+      for (int q = 0; q < 3; ++q) {
+        acc[0].add_prod(g[q], g[q]);
+        acc[1].add_prod(g[q], dj[q]);
+        if (!BATCH) acc[2].add_prod(dj[q], dj[q]);
+      }
     }
   }
   if (BATCH) {
     Acc<T> sacc2[2] = {acc[0], acc[1]};
-    scene_reduce_acc<T, 2>(sacc2, active ? sc : -1, m.sacc, 0);
+    scene_reduce_acc<T, 2>(sacc2, writer ? sc : -1, m.sacc, 0);
     return;
   }
   double bs[3];
@@ -1076,7 +1121,7 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
 // the rotated pool element data (L2-resident rows), the 3x3 solve of Eq. reduced_local, D_i, and g.D. The
 // last block closes the sweep's reduction with phase 1's partial sums.
 template <typename T, bool BATCH, int BS>
-__global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 512 : 256) / BS) k_correct(DevMesh<T> m, StepState* st,
+__global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 256) / BS) k_correct(DevMesh<T> m, StepState* st,
                                                 double* __restrict__ partial /* [3][grid] */,
                                                 double* __restrict__ trace, int record) {
   if (!BATCH && st->done) return;

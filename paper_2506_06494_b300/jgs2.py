@@ -82,7 +82,7 @@ EXPORTS = ["jgs2_precompute_opts_default", "jgs2_step_opts_default", "jgs2_mesh_
            "jgs2_mesh_n_cub", "jgs2_step", "jgs2_step_gs", "jgs2_step_host", "jgs2_sweeps",
            "jgs2_energy_gradient", "jgs2_energy_gradient_static", "jgs2_contact_pairs",
            "jgs2_step_adjoint", "jgs2_adjoint_opts_default", "jgs2_mesh_set_youngs",
-           "jgs2_mesh_create_batch", "jgs2_batch_report", "jgs2_autotune", "jgs2_alu_peak",
+           "jgs2_mesh_create_batch", "jgs2_batch_report", "jgs2_autotune", "jgs2_mesh_launch_config", "jgs2_alu_peak",
            "jgs2_mesh_destroy", "jgs2_last_error"]
 
 
@@ -117,6 +117,7 @@ def lib():
     L.jgs2_batch_report.argtypes = [P, P, P, P]
     L.jgs2_autotune.argtypes = [P, P, P, C.POINTER(StepOpts), P, C.POINTER(C.c_int32)]
     L.jgs2_alu_peak.argtypes = [C.c_int32, C.POINTER(C.c_double), P]
+    L.jgs2_mesh_launch_config.argtypes = [P, C.c_int32, P]
     L.jgs2_mesh_destroy.argtypes = [P]
     L.jgs2_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -249,6 +250,12 @@ class Mesh:
         _check(lib().jgs2_autotune(self.handle, _dev(x), _dev(v), C.byref(opts or step_opts()),
                                    C.c_void_p(_stream_ptr(stream)), C.byref(bs)))
         return bs.value
+
+    def launch_config(self, precision):
+        """(gather threads per block, gather threads per vertex, correction threads per block)."""
+        cfg = np.zeros(3, dtype=np.int32)
+        _check(lib().jgs2_mesh_launch_config(self.handle, int(precision), cfg.ctypes.data))
+        return tuple(int(c) for c in cfg)
 
     def __init__(self, X, tets, youngs, poisson, density, pinned=None, gravity=(0, 0, -9.8), dt=1 / 120,
                  planes=None, dhat=1e-3, kappa=1e5, contact=0):
