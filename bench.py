@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ms/step to 1e-4 rel. residual at 3.5M tets"
 KIND = ["k_pool", "k_gather", "k_correct", "k_energy", "k_update", "setup", "contact", "k_elem",
-        "k_pair_trials", "k_ls_decide"]
+        "k_pair_trials", "k_ls_decide", "k_batch_persistent"]
 
 
 def peaks():

@@ -121,6 +121,18 @@ typedef struct {
                               * only (JGS2_EINVAL on a batch mesh); jgs2_step_gs ignores it */
   double length_scale;       /* L of that normalisation (m); <= 0: the largest extent of the
                               * bounding box of the rest positions */
+  int32_t persistent;        /* batch meshes: 1 = each chunk of check_every sweeps is one
+                              * persistent cooperative launch over all scenes' tet and vertex
+                              * tiles, its phases separated by a bounded grid barrier (captured in
+                              * a CUDA graph); 0 = one launch per kernel (the default). Single
+                              * scenes ignore it */
+  int32_t wait_polls;        /* polls of one bounded device wait before it gives up with
+                              * JGS2_ETIMEOUT; 0 = the default (2^20, about 0.2 s) */
+  int32_t test_unreachable_barrier; /* test hook, 0 in use: 1 makes the persistent launch's first
+                              * grid barrier wait for one block more than the grid has, so the wait
+                              * runs out after wait_polls polls and the step returns JGS2_ETIMEOUT
+                              * with the state not written */
+  int32_t pad_;
 } jgs2_step_opts;
 
 #define JGS2_TRACE_MAX 4096
@@ -132,9 +144,10 @@ typedef struct {
  * ls_decide (the line search's one-block decision). kernel_launches counts kernels; a pass
  * of several launches (contact: 11) counts each. The line search launches every pass
  * variant each sweep, and only the variants the sweep needs do work (ls_passes). */
-#define JGS2_NKERNELS 10
+#define JGS2_NKERNELS 11
 enum { JGS2_K_POOL = 0, JGS2_K_GATHER = 1, JGS2_K_CORRECT = 2, JGS2_K_ENERGY = 3, JGS2_K_UPDATE = 4,
-       JGS2_K_SETUP = 5, JGS2_K_CONTACT = 6, JGS2_K_ELEM = 7, JGS2_K_LS_PAIRS = 8, JGS2_K_LS_DECIDE = 9 };
+       JGS2_K_SETUP = 5, JGS2_K_CONTACT = 6, JGS2_K_ELEM = 7, JGS2_K_LS_PAIRS = 8, JGS2_K_LS_DECIDE = 9,
+       JGS2_K_PERSISTENT = 10 /* a persistent batch launch (a chunk of whole sweeps) */ };
 
 typedef struct {
   int32_t sweeps;            /* sweeps applied in the step */
@@ -168,7 +181,8 @@ typedef struct {
 /* Default option values (n_cub 4, n_train 20, n_cand 32, n_pool 256, tol 0.01, seed 0, gs 0). */
 void jgs2_precompute_opts_default(jgs2_precompute_opts* o);
 /* Defaults: max_sweeps 500, rel_tol 1e-4, FP32, asm, line search on, check_every 16, no
- * position-change test (dx_tol 0, length_scale 0). */
+ * position-change test (dx_tol 0, length_scale 0), per-kernel launches (persistent 0),
+ * wait_polls 0 (2^20), no test hook. */
 void jgs2_step_opts_default(jgs2_step_opts* o);
 
 /* Validates the mesh (indices in range, positive volumes, material ranges, every free

@@ -19,6 +19,7 @@
 #include "jgs2_adjoint.cuh"
 #include "jgs2_host.h"
 #include "jgs2_kernels.cuh"
+#include "jgs2_persistent.cuh"
 
 namespace jgs2 {
 
@@ -72,6 +73,7 @@ Mesh::~Mesh() {
   for (cudaEvent_t e : gev)
     if (e) cudaEventDestroy(e);
   cudaFree(d_vscene); cudaFree(d_tscene); cudaFree(d_ndone); cudaFree(d_scenes); cudaFree(d_sacc);
+  cudaFree(d_gbar);
   cudaFree(d_planes); cudaFree(d_d0); cudaFree(d_bg); cudaFree(d_bH); cudaFree(d_faces); cudaFree(d_edges);
   cudaFree(d_sverts); cudaFree(d_npairs); cudaFree(d_cflags); cudaFree(d_is_surf); cudaFree(d_pairs);
   cudaFree(d_dmin); cudaFree(d_lim); cudaFree(d_frank); cudaFree(d_erank); cudaFree(d_hcnt); cudaFree(d_hblk);
@@ -430,6 +432,11 @@ static jgs2_status ensure_device(Mesh* m) {
       CK(dalloc(&m->d_scenes, m->n_scenes));
       CK(dalloc(&m->d_sacc, (size_t)m->n_scenes * kSceneAcc));
       CK(dalloc(&m->d_ndone, 1));
+      {
+        GridBarrier* gb = nullptr;
+        CK(dalloc(&gb, 1));
+        m->d_gbar = gb;
+      }
       CK(cudaMemcpy(m->d_vscene, vs.data(), sizeof(int) * std::max(1, m->Vf), cudaMemcpyHostToDevice));
       CK(cudaMemcpy(m->d_tscene, ts.data(), sizeof(int) * T, cudaMemcpyHostToDevice));
     }
@@ -1090,6 +1097,126 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
   return JGS2_OK;
 }
 
+// The persistent batch kernel for the sweep's flags (correction, line search, threads per
+// vertex of the gather).
+template <typename T>
+static void (*persistent_kernel(bool corr, bool ls, int tpv))(DevMesh<T>, PersistArgs) {
+  if (tpv == 4) {
+    if (corr) return ls ? k_batch_persistent<T, true, true, 4> : k_batch_persistent<T, true, false, 4>;
+    return ls ? k_batch_persistent<T, false, true, 4> : k_batch_persistent<T, false, false, 4>;
+  }
+  if (corr) return ls ? k_batch_persistent<T, true, true, 1> : k_batch_persistent<T, true, false, 1>;
+  return ls ? k_batch_persistent<T, false, true, 1> : k_batch_persistent<T, false, false, 1>;
+}
+
+// Batch meshes, persistent form: each chunk of check_every sweeps is one cooperative launch
+// (grid: every block resident, the occupancy limit times the SM count) whose phases are
+// separated by the bounded grid barrier, captured with the barrier reset in a CUDA graph
+// and replayed until every scene has stopped or a wait gave up.
+template <typename T>
+static jgs2_status run_batch_persistent(Mesh* m, const jgs2_step_opts& o, cudaStream_t s, Launches& L,
+                                        DevMesh<T>& d, bool corr) {
+  const int pi = sizeof(T) == 4 ? 1 : 0;
+  const int tpv = m->gtpv[pi] == 4 ? 4 : 1;
+  const int S = m->n_scenes;
+  const int chunk = std::max(1, o.check_every);
+  PersistArgs a{};
+  a.chunk = chunk;
+  a.nbT = (m->T + 127) / 128;
+  a.nbG = (m->Vf + 128 / tpv - 1) / (128 / tpv);
+  a.nbP = (m->nP + kPoolWarps - 1) / kPoolWarps;
+  a.nbC = (m->Vf + 127) / 128;
+  a.nbV = (m->Vf + 127) / 128;
+  a.nbS = (S + 127) / 128;
+  a.corr = corr ? 1 : 0;
+  a.ls = o.line_search ? 1 : 0;
+  a.max_sweeps = o.max_sweeps;
+  a.rel_tol = o.rel_tol;
+  a.wait_polls = o.wait_polls > 0 ? o.wait_polls : (1 << 20);
+  a.bar = static_cast<GridBarrier*>(m->d_gbar);
+  a.st = m->d_state;
+  a.partial = m->d_partial;
+  auto kern = persistent_kernel<T>(corr, o.line_search != 0, tpv);
+  const size_t smem = gather_smem(m, 128 / tpv);
+  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int nbps = 0, dev = 0, sms = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbps, kern, 128, smem));
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (nbps < 1) return fail(JGS2_ECUDA, "persistent batch kernel cannot be resident on an SM");
+  const int grid = nbps * sms;
+  long key = (long)(sizeof(T) == 4);
+  key = key * 2 + (corr ? 1 : 0);
+  key = key * 2 + (o.line_search != 0);
+  key = key * 8 + tpv;
+  key = key * 2 + (o.test_unreachable_barrier != 0);
+  key = key * 4096 + chunk;
+  key = key * 1000003L + o.max_sweeps;
+  key = key * 4194304L + (long)a.wait_polls;
+  key = (key ^ (long)(o.rel_tol * 1e12)) | (1L << 61);
+  const bool same_view = m->gdev.size() == sizeof(d) && std::memcmp(m->gdev.data(), &d, sizeof(d)) == 0;
+  if (m->graph_key != key || !same_view) {
+    if (m->graph) cudaGraphExecDestroy(m->graph);
+    m->graph = nullptr;
+    m->graph_key = -1;
+    m->ggroups.clear();
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync(m->d_gbar, 0, sizeof(GridBarrier), s);
+    if (e == cudaSuccess && o.test_unreachable_barrier)
+      e = cudaMemsetAsync(static_cast<char*>(m->d_gbar) + offsetof(GridBarrier, extra), 1, 1, s);
+    if (e == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(grid);
+      cfg.blockDim = dim3(128);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      e = cudaLaunchKernelEx(&cfg, kern, d, a);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) {
+      if (e2 == cudaSuccess) cudaGraphDestroy(g);
+      return fail(JGS2_ECUDA, std::string("persistent batch launch capture: ") + cudaGetErrorString(e));
+    }
+    if (e2 != cudaSuccess) return fail(JGS2_ECUDA, std::string("persistent batch capture: ") + cudaGetErrorString(e2));
+    e = cudaGraphInstantiate(&m->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(JGS2_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    m->graph_key = key;
+    m->gdev.assign(reinterpret_cast<const char*>(&d), reinterpret_cast<const char*>(&d) + sizeof(d));
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (L.prof) {
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+  }
+  int32_t done = 0;
+  StepState hs;
+  for (int sw = 0; sw <= o.max_sweeps; sw += chunk) {
+    if (L.prof) CK(cudaEventRecord(e0, s));
+    CK(cudaGraphLaunch(m->graph, s));
+    if (L.prof) CK(cudaEventRecord(e1, s));
+    L.count[JGS2_K_PERSISTENT] += 1;
+    CK(cudaMemcpyAsync(&done, m->d_ndone, sizeof(done), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&hs, m->d_state, sizeof(StepState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (L.prof) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) L.gms[JGS2_K_PERSISTENT] += ms;
+    }
+    if (hs.status != 0 || done >= S) break;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  return JGS2_OK;
+}
+
 // Batch meshes: every scene runs its own sweeps and stopping test; a chunk of check_every
 // sweeps (all kernels of all scenes, one launch per kernel) is captured once in a CUDA
 // graph and replayed until every scene has stopped.
@@ -1117,6 +1244,17 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
   CK(cudaMemsetAsync(m->d_scenes, 0, sizeof(SceneState) * S, s));
   CK(cudaMemsetAsync(m->d_sacc, 0, sizeof(double) * kSceneAcc * S, s));
   CK(cudaMemsetAsync(m->d_ndone, 0, sizeof(int32_t), s));
+  if (o.persistent) {
+    jgs2_status pst = run_batch_persistent<T>(m, o, s, L, d, corr);
+    if (pst != JGS2_OK) return pst;
+    StepState hs;
+    CK(cudaMemcpyAsync(&hs, m->d_state, sizeof(StepState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hs.status == JGS2_ETIMEOUT) return fail(JGS2_ETIMEOUT, "a bounded device wait timed out; state not written");
+    CK(cudaEventRecord(m->gev[1], s));
+    CK(cudaStreamWaitEvent(cs, m->gev[1], 0));
+    return JGS2_OK;
+  }
   const bool prof = L.prof;
   const long key = ((((((long)(sizeof(T) == 4) * 3 + o.correction) * 2 + (o.line_search != 0)) * 2 + (prof ? 1 : 0)) *
                           512 + bs) * 4096 + gbs * 8 + gtpv) * 4096 + chunk + (long)(o.max_sweeps) * 1000003L +
@@ -1241,6 +1379,7 @@ static jgs2_status check_opts(const Mesh* m, const jgs2_step_opts* o) {
   if (o->correction != JGS2_CORR_OFF && m->n_cub == 0)
     return fail(JGS2_ENOTPRECOMPUTED, "correction requested before jgs2_precompute / jgs2_precompute_import");
   if (!(o->dx_tol >= 0.0)) return fail(JGS2_EINVAL, "dx_tol must be >= 0");
+  if (o->wait_polls < 0) return fail(JGS2_EINVAL, "wait_polls must be >= 0");
   if (o->dx_tol > 0.0 && m->n_scenes > 0)
     return fail(JGS2_EINVAL, "the position-change test (dx_tol) is for single scenes, not batch meshes");
   return JGS2_OK;
@@ -1922,6 +2061,10 @@ void jgs2_step_opts_default(jgs2_step_opts* o) {
   o->profile = 0;
   o->dx_tol = 0.0;
   o->length_scale = 0.0;
+  o->persistent = 0;
+  o->wait_polls = 0;
+  o->test_unreachable_barrier = 0;
+  o->pad_ = 0;
 }
 
 jgs2_status jgs2_mesh_create(const jgs2_mesh_desc* desc, jgs2_mesh** out) {

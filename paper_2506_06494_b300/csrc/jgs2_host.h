@@ -72,6 +72,7 @@ struct Mesh {
   int n_scenes = 0;                   // 0: not a batch mesh
   std::vector<int> vscene;            // caller vertex -> scene
   int32_t *d_vscene = nullptr, *d_tscene = nullptr, *d_ndone = nullptr;
+  void* d_gbar = nullptr;             // grid barrier of the persistent batch launch
   SceneState* d_scenes = nullptr;
   double* d_sacc = nullptr;
   // launch shapes per precision (autotuned): k_correct block size, k_gather block size and

@@ -604,22 +604,29 @@ __device__ __forceinline__ void pool_entry(T h, T w, const T (&U)[36], T (&P)[9]
 
 template <typename T>
 __device__ __forceinline__ void load4(const T* __restrict__ p, T (&o)[4]);
+template <typename T>
+__device__ __forceinline__ void load4_coherent(const T* p, T (&o)[4]);
 
-template <int Q4, typename T>
-__device__ __forceinline__ void pool_chunk(const T* __restrict__ Hp, T w, const T (&U)[36], T (&P)[9], T (&Ht)[6],
+// NC = false: the pool rows were written earlier in the same (persistent) launch, so they
+// are read with plain coherent loads instead of the read-only path.
+template <int Q4, bool NC, typename T>
+__device__ __forceinline__ void pool_chunk(const T* Hp, T w, const T (&U)[36], T (&P)[9], T (&Ht)[6],
                                            T (&gt)[3]) {
   T hv[4];
-  load4(Hp + 4 * Q4, hv);
+  if constexpr (NC)
+    load4(Hp + 4 * Q4, hv);
+  else
+    load4_coherent(Hp + 4 * Q4, hv);
   pool_entry<4 * Q4 + 0>(hv[0], w, U, P, Ht, gt);
   pool_entry<4 * Q4 + 1>(hv[1], w, U, P, Ht, gt);
   pool_entry<4 * Q4 + 2>(hv[2], w, U, P, Ht, gt);
   pool_entry<4 * Q4 + 3>(hv[3], w, U, P, Ht, gt);
 }
 
-template <typename T, int... Q4>
-__device__ __forceinline__ void pool_row(const T* __restrict__ Hp, T w, const T (&U)[36], T (&P)[9], T (&Ht)[6],
-                                         T (&gt)[3], std::integer_sequence<int, Q4...>) {
-  (pool_chunk<Q4>(Hp, w, U, P, Ht, gt), ...);
+template <bool NC, typename T, int... Q4>
+__device__ __forceinline__ void pool_row(const T* Hp, T w, const T (&U)[36], T (&P)[9], T (&Ht)[6], T (&gt)[3],
+                                         std::integer_sequence<int, Q4...>) {
+  (pool_chunk<Q4, NC>(Hp, w, U, P, Ht, gt), ...);
 }
 
 // One cubature slot of Eq. cubature: the pool row Hp (rotated element Hessian blocks, then
@@ -627,14 +634,14 @@ __device__ __forceinline__ void pool_row(const T* __restrict__ Hp, T w, const T 
 // H~' += w U^T H' U = w sum_{a <= c} (U_a^T H'_ac U_c + its transpose if a != c),
 // g~' += w U^T G'. Blocks are closed one at a time, so only a 3x3 partial product is
 // live besides U.
-template <typename T>
-__device__ __forceinline__ void slot_sums(const T* __restrict__ Hp, T w, const T (&U)[36], T (&Ht)[6], T (&gt)[3]) {
+template <typename T, bool NC = true>
+__device__ __forceinline__ void slot_sums(const T* Hp, T w, const T (&U)[36], T (&Ht)[6], T (&gt)[3]) {
   T P[9];
-  pool_row(Hp, w, U, P, Ht, gt, std::make_integer_sequence<int, (kPoolH + 12 + 3) / 4>{});
+  pool_row<NC>(Hp, w, U, P, Ht, gt, std::make_integer_sequence<int, (kPoolH + 12 + 3) / 4>{});
 }
 
 // Cubature sums for vertex i over its n_cub slots, records read directly from global memory.
-template <typename T>
+template <typename T, bool NC = true>
 __device__ __forceinline__ void cubature_sums(const DevMesh<T>& m, int i, T (&Ht)[6], T (&gt)[3]) {
   for (int s = 0; s < m.n_cub; ++s) {
     const int p = m.cub_p[(size_t)s * m.cs + i];
@@ -644,7 +651,7 @@ __device__ __forceinline__ void cubature_sums(const DevMesh<T>& m, int i, T (&Ht
     const T* up = m.cub_u + (size_t)s * 36 * m.cs + i;
 #pragma unroll
     for (int q = 0; q < 36; ++q) U[q] = up[(size_t)q * m.cs];
-    slot_sums(m.pool_H + (size_t)p * kPoolStride, w, U, Ht, gt);
+    slot_sums<T, NC>(m.pool_H + (size_t)p * kPoolStride, w, U, Ht, gt);
   }
 }
 
@@ -666,6 +673,18 @@ __device__ __forceinline__ void load4<double>(const double* __restrict__ p, doub
   o[1] = a.y;
   o[2] = b.x;
   o[3] = b.y;
+}
+// The same four values through plain (coherent, L1-cached) global loads.
+template <>
+__device__ __forceinline__ void load4_coherent<float>(const float* p, float (&o)[4]) {
+  asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3])
+               : "l"(p));
+}
+template <>
+__device__ __forceinline__ void load4_coherent<double>(const double* p, double (&o)[4]) {
+  asm volatile("ld.global.v2.f64 {%0, %1}, [%2];" : "=d"(o[0]), "=d"(o[1]) : "l"(p));
+  asm volatile("ld.global.v2.f64 {%0, %1}, [%2];" : "=d"(o[2]), "=d"(o[3]) : "l"(p + 2));
 }
 
 // Step truncation: scale d so that |d| <= lim (reading R11).
@@ -774,13 +793,12 @@ __global__ void k_setup_tets(DevMesh<T> m) {
 // F(x_t) + [u_1 - u_0, u_2 - u_0, u_3 - u_0] B with the tet's constants, for the vertex
 // gather. Tiles of 128 records are staged in shared memory with coalesced loads; each
 // thread writes one 16-byte aligned FRec. Batch meshes skip the tets of finished scenes.
+// One tile of 128 tets: block bid of nb (srec: the block's 128-record staging buffer).
 template <typename T, bool BATCH>
-__global__ void __launch_bounds__(128) k_elem(DevMesh<T> m, const StepState* __restrict__ st) {
-  if (!BATCH && st->done) return;
-  __shared__ __align__(16) TetRec<T> srec[128];
+__device__ __forceinline__ void elem_body(const DevMesh<T>& m, int bid, int nb, TetRec<T>* srec) {
   // tiles in descending order: the lowest tets, which the gather (ascending vertices)
   // reads first, are written last and are still in L2 when it starts
-  const int t0 = (gridDim.x - 1 - blockIdx.x) * 128, n = min(128, m.T_ - t0);
+  const int t0 = (nb - 1 - bid) * 128, n = min(128, m.T_ - t0);
   stage_tets<T, 128>(m.tets, t0, n, srec);
   __syncthreads();
   if ((int)threadIdx.x >= n) return;
@@ -793,6 +811,13 @@ __global__ void __launch_bounds__(128) k_elem(DevMesh<T> m, const StepState* __r
   o.mu = r.mu;
   o.lp = r.lp;
   m.frec[t] = o;
+}
+
+template <typename T, bool BATCH>
+__global__ void __launch_bounds__(128) k_elem(DevMesh<T> m, const StepState* __restrict__ st) {
+  if (!BATCH && st->done) return;
+  __shared__ __align__(16) TetRec<T> srec[128];
+  elem_body<T, BATCH>(m, blockIdx.x, gridDim.x, srec);
 }
 
 // Per cubature element, one warp (kPoolWarps elements per block), after the sweep's gather:
@@ -811,11 +836,10 @@ struct PoolShared {
 };
 
 template <typename T, bool ASM>
-__global__ void __launch_bounds__(32 * kPoolWarps) k_pool(DevMesh<T> m, const StepState* __restrict__ st) {
-  if (st->done) return;
+__device__ __forceinline__ void pool_body(const DevMesh<T>& m, int bid) {
   __shared__ PoolShared<T> sh_all[kPoolWarps];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int p = blockIdx.x * kPoolWarps + wid;
+  const int p = bid * kPoolWarps + wid;
   if (p >= m.nP) return;  // whole warps only; no block-wide barrier below
   PoolShared<T>& sh = sh_all[wid];
   const int t = m.pool_tet[p];
@@ -928,6 +952,12 @@ __global__ void __launch_bounds__(32 * kPoolWarps) k_pool(DevMesh<T> m, const St
   }
 }
 
+template <typename T, bool ASM>
+__global__ void __launch_bounds__(32 * kPoolWarps) k_pool(DevMesh<T> m, const StepState* __restrict__ st) {
+  if (st->done) return;
+  pool_body<T, ASM>(m, blockIdx.x);
+}
+
 // Residual bookkeeping of sweep k (reading R9), run by one thread of the last block.
 // dd2, ddj2: |D|^2 and |D_J|^2 of the sweep's directions. Besides r_k <= rel_tol, a step
 // with the position-change test on (dx2_tol > 0) stops at the first k >= 1 whose last
@@ -983,21 +1013,19 @@ __device__ __forceinline__ void finalize_sweep(StepState* st, double r2, double 
 // slices): with 4, the lanes of a vertex's group split its incidences and add their sums
 // with warp shuffles, so more record loads are in flight per vertex; every lane of the group
 // then holds the vertex's sums and lane 0 writes its results.
-template <typename T, bool CORR, bool BATCH, int BS, int TPV = 1>
-__global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
-    k_gather(DevMesh<T> m, StepState* st, double* __restrict__ partial /* [3][grid] */,
-             double* __restrict__ trace, int record) {
+template <typename T, bool CORR, bool BATCH, int BS, int TPV>
+__device__ __forceinline__ void gather_body(const DevMesh<T>& m, StepState* st, double* __restrict__ partial,
+                                            double* __restrict__ trace, int record, int bid, int nb) {
   static_assert(TPV == 1 || TPV == 4, "1 or 4 threads per vertex");
   static_assert((BS / TPV) % kSlice == 0, "whole slices per block");
   constexpr int VPB = BS / TPV;
-  if (!BATCH && st->done) return;
   __shared__ double red[96];
   __shared__ Acc<T> sred[96];
   // the block's incidence slices form one contiguous, 128-byte aligned range of entries;
   // copy it into shared memory first (coalesced 16-byte loads), so that each incidence's
   // record loads do not wait on a global load of its entry
   extern __shared__ __align__(16) int s_inc[];
-  const int s0 = blockIdx.x * (VPB / kSlice), s1 = min(s0 + VPB / kSlice, m.n_slices);
+  const int s0 = bid * (VPB / kSlice), s1 = min(s0 + VPB / kSlice, m.n_slices);
   const int e0 = m.inc_off[s0];
   {
     const int4* src = reinterpret_cast<const int4*>(m.inc + e0);
@@ -1006,7 +1034,7 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
     for (int q = threadIdx.x; q < n4; q += BS) dst[q] = __ldg(src + q);
   }
   __syncthreads();
-  const int i = blockIdx.x * VPB + (int)threadIdx.x / TPV;
+  const int i = bid * VPB + (int)threadIdx.x / TPV;
   const int lane_v = (int)threadIdx.x % TPV;
   Acc<T> acc[3];  // |g|^2, g.D_J, |D_J|^2
   const int sc = (BATCH && i < m.Vf) ? m.v_scene[i] : -1;
@@ -1105,36 +1133,42 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
   double bs[3];
   block_sum_acc<T, 3>(acc, bs, sred);
   if (threadIdx.x == 0) {
-    partial[blockIdx.x] = bs[0];
-    partial[gridDim.x + blockIdx.x] = bs[1];
-    partial[3 * gridDim.x + blockIdx.x] = bs[2];
+    partial[bid] = bs[0];
+    partial[nb + bid] = bs[1];
+    partial[3 * nb + bid] = bs[2];
   }
   if (CORR) return;
   if (!last_block(&st->ticket_main)) return;
-  const double r2 = block_sum_array(partial, gridDim.x, 1, red);
-  const double gdj = block_sum_array(partial + gridDim.x, gridDim.x, 1, red);
-  const double djj = block_sum_array(partial + 3 * gridDim.x, gridDim.x, 1, red);
+  const double r2 = block_sum_array(partial, nb, 1, red);
+  const double gdj = block_sum_array(partial + nb, nb, 1, red);
+  const double djj = block_sum_array(partial + 3 * nb, nb, 1, red);
   if (threadIdx.x == 0) finalize_sweep(st, r2, gdj, gdj, djj, djj, trace, record);
+}
+
+template <typename T, bool CORR, bool BATCH, int BS, int TPV = 1>
+__global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
+    k_gather(DevMesh<T> m, StepState* st, double* __restrict__ partial /* [3][grid] */,
+             double* __restrict__ trace, int record) {
+  if (!BATCH && st->done) return;
+  gather_body<T, CORR, BATCH, BS, TPV>(m, st, partial, trace, record, blockIdx.x, gridDim.x);
 }
 
 // Sweep phase 2, thread per free vertex: the cubature sums H~_i, g~_i (Eq. cubature) from
 // the rotated pool element data (L2-resident rows), the 3x3 solve of Eq. reduced_local, D_i, and g.D. The
 // last block closes the sweep's reduction with phase 1's partial sums.
-template <typename T, bool BATCH, int BS>
-__global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 256) / BS) k_correct(DevMesh<T> m, StepState* st,
-                                                double* __restrict__ partial /* [3][grid] */,
-                                                double* __restrict__ trace, int record) {
-  if (!BATCH && st->done) return;
+template <typename T, bool BATCH, int BS, bool NC = true>
+__device__ __forceinline__ void correct_body(const DevMesh<T>& m, StepState* st, double* __restrict__ partial,
+                                             double* __restrict__ trace, int record, int bid, int nb) {
   __shared__ double red[96];
   __shared__ Acc<T> sred[64];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = bid * BS + threadIdx.x;
   Acc<T> acc[2];  // g.D, |D|^2
   int fb = 0;
   const int sc = (BATCH && i < m.Vf) ? m.v_scene[i] : -1;
   const bool active = i < m.Vf && (!BATCH || !m.scenes[sc].done);
   if (active) {
     T Ht[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, gt[3] = {T(0), T(0), T(0)};
-    cubature_sums(m, i, Ht, gt);
+    cubature_sums<T, NC>(m, i, Ht, gt);
     // the vertex's own g, H_ii, R_i from the gather (loaded after the cubature loop, so
     // they hold no registers during it)
     const T* o = m.ghr + i;
@@ -1195,16 +1229,24 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 256) / BS) k_corre
   double bs[2];
   block_sum_acc<T, 2>(acc, bs, sred);
   if (threadIdx.x == 0) {
-    partial[2 * gridDim.x + blockIdx.x] = bs[0];
-    partial[4 * gridDim.x + blockIdx.x] = bs[1];
+    partial[2 * nb + bid] = bs[0];
+    partial[4 * nb + bid] = bs[1];
   }
   if (!last_block(&st->ticket_main)) return;
-  const double r2 = block_sum_array(partial, gridDim.x, 1, red);
-  const double gdj = block_sum_array(partial + gridDim.x, gridDim.x, 1, red);
-  const double gd = block_sum_array(partial + 2 * gridDim.x, gridDim.x, 1, red);
-  const double djj = block_sum_array(partial + 3 * gridDim.x, gridDim.x, 1, red);
-  const double dd = block_sum_array(partial + 4 * gridDim.x, gridDim.x, 1, red);
+  const double r2 = block_sum_array(partial, nb, 1, red);
+  const double gdj = block_sum_array(partial + nb, nb, 1, red);
+  const double gd = block_sum_array(partial + 2 * nb, nb, 1, red);
+  const double djj = block_sum_array(partial + 3 * nb, nb, 1, red);
+  const double dd = block_sum_array(partial + 4 * nb, nb, 1, red);
   if (threadIdx.x == 0) finalize_sweep(st, r2, gd, gdj, dd, djj, trace, record);
+}
+
+template <typename T, bool BATCH, int BS>
+__global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 256) / BS) k_correct(DevMesh<T> m, StepState* st,
+                                                double* __restrict__ partial /* [3][grid] */,
+                                                double* __restrict__ trace, int record) {
+  if (!BATCH && st->done) return;
+  correct_body<T, BATCH, BS>(m, st, partial, trace, record, blockIdx.x, gridDim.x);
 }
 
 // Exact energy change of a tet for the displacement increment alpha*d (no cancellation):
@@ -1473,13 +1515,12 @@ __global__ void __launch_bounds__(256) k_ls_decide(StepState* st, int has_j, con
 // [0, tet_blocks) (tiles staged in shared memory), thread per free vertex after; no
 // contact. Blocks whose scenes have nothing to do return before loading.
 template <typename T, int DIR>
-__global__ void __launch_bounds__(128) k_energy_batch(DevMesh<T> m, int tet_blocks) {
+__device__ __forceinline__ void energy_batch_body(const DevMesh<T>& m, int tet_blocks, int bid, TetRec<T>* srec) {
   constexpr int ND = DIR == 2 ? 2 : 1;
   constexpr int NC = 6 * ND;
-  __shared__ __align__(16) TetRec<T> srec[128];
   __shared__ int busy;
-  const bool tets = (int)blockIdx.x < tet_blocks;
-  const int i0 = tets ? blockIdx.x * 128 : (blockIdx.x - tet_blocks) * 128;
+  const bool tets = bid < tet_blocks;
+  const int i0 = tets ? bid * 128 : (bid - tet_blocks) * 128;
   const int n = min(128, (tets ? m.T_ : m.Vf) - i0);
   const int32_t* scene_of = tets ? m.t_scene : m.v_scene;
   auto wants = [&](int sc) {
@@ -1549,11 +1590,16 @@ __global__ void __launch_bounds__(128) k_energy_batch(DevMesh<T> m, int tet_bloc
   scene_reduce_acc<T, NC>(acc, sc, m.sacc, 3);
 }
 
+template <typename T, int DIR>
+__global__ void __launch_bounds__(128) k_energy_batch(DevMesh<T> m, int tet_blocks) {
+  __shared__ __align__(16) TetRec<T> srec[128];
+  energy_batch_body<T, DIR>(m, tet_blocks, blockIdx.x, srec);
+}
+
 // Batch meshes, thread per scene: residual bookkeeping of the sweep (reading R9) from the
 // per-scene sums, then clear them.
-static __global__ void k_scene_finalize_main(SceneState* scenes, double* sacc, int n, double rel_tol, int max_sweeps,
-                                      int corr, int32_t* n_done) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void scene_finalize_main_body(SceneState* scenes, double* sacc, int n, double rel_tol,
+                                                         int max_sweeps, int corr, int32_t* n_done, int s) {
   if (s >= n) return;
   SceneState& S = scenes[s];
   double* a = sacc + (size_t)s * kSceneAcc;
@@ -1590,13 +1636,17 @@ static __global__ void k_scene_finalize_main(SceneState* scenes, double* sacc, i
   a[0] = a[1] = a[2] = 0.0;
 }
 
+static __global__ void k_scene_finalize_main(SceneState* scenes, double* sacc, int n, double rel_tol, int max_sweeps,
+                                             int corr, int32_t* n_done) {
+  scene_finalize_main_body(scenes, sacc, n, rel_tol, max_sweeps, corr, n_done, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // Batch meshes, thread per scene: Armijo choice from the per-scene polynomial sums of the
 // scene's pass (DIR as in k_energy_batch; DIR 0 records need_j when every trial failed and
 // D_J differs), then the sums are cleared for the next pass.
 template <int DIR>
-static __global__ void k_scene_finalize_energy(SceneState* scenes, double* sacc, int n, int has_j) {
+__device__ __forceinline__ void scene_finalize_energy_body(SceneState* scenes, double* sacc, int n, int has_j, int s) {
   constexpr int ND = DIR == 2 ? 2 : 1;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   SceneState& S = scenes[s];
   double* cf = sacc + (size_t)s * kSceneAcc + 3;
@@ -1628,9 +1678,13 @@ static __global__ void k_scene_finalize_energy(SceneState* scenes, double* sacc,
   for (int j = 0; j < 6 * ND; ++j) cf[j] = 0.0;
 }
 
+template <int DIR>
+static __global__ void k_scene_finalize_energy(SceneState* scenes, double* sacc, int n, int has_j) {
+  scene_finalize_energy_body<DIR>(scenes, sacc, n, has_j, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 template <typename T>
-__global__ void k_update_batch(DevMesh<T> m) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void update_batch_body(const DevMesh<T>& m, int i) {
   if (i >= m.Vf) return;
   const SceneState& S = m.scenes[m.v_scene[i]];
   if (S.done) return;
@@ -1641,6 +1695,11 @@ __global__ void k_update_batch(DevMesh<T> m) {
   u.y += a * d.y;
   u.z += a * d.z;
   m.u[i] = u;
+}
+
+template <typename T>
+__global__ void k_update_batch(DevMesh<T> m) {
+  update_batch_body<T>(m, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <typename T>

@@ -16,9 +16,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libjgs2.so")
 
 TRACE_MAX = 4096
-NKERNELS = 10
+NKERNELS = 11
 KERNEL_NAMES = ["k_pool", "k_gather", "k_correct", "k_energy", "k_update", "setup", "contact", "k_elem",
-                "k_pair_trials", "k_ls_decide"]
+                "k_pair_trials", "k_ls_decide", "k_batch_persistent"]
 FP64, FP32 = 0, 1
 CORR_ASM, CORR_ELEM, CORR_OFF = 0, 1, 2
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTPRECOMPUTED", 5: "ENOTCONVERGED",
@@ -50,7 +50,8 @@ class StepOpts(C.Structure):
     _fields_ = [("max_sweeps", C.c_int32), ("rel_tol", C.c_double), ("precision", C.c_int32),
                 ("correction", C.c_int32), ("line_search", C.c_int32), ("check_every", C.c_int32),
                 ("record_trace", C.c_int32), ("profile", C.c_int32), ("dx_tol", C.c_double),
-                ("length_scale", C.c_double)]
+                ("length_scale", C.c_double), ("persistent", C.c_int32), ("wait_polls", C.c_int32),
+                ("test_unreachable_barrier", C.c_int32), ("pad_", C.c_int32)]
 
 
 class AdjointOpts(C.Structure):

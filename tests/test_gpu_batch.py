@@ -49,15 +49,17 @@ def test_batch_scenes_stop_independently(batch):
     assert len(set(sweeps[:3])) == 3 and sweeps[3] == sweeps[4] == CAP
 
 
-@pytest.mark.parametrize("bs", [None, 64, 256])
-def test_batch_fp64_matches_oracle_per_scene(cuda, batch, bs):
+@pytest.mark.parametrize("bs,persistent", [(None, 0), (64, 0), (256, 0), (None, 1), (256, 1)])
+def test_batch_fp64_matches_oracle_per_scene(cuda, batch, bs, persistent):
+    """Per-kernel launches (persistent 0) and the persistent cooperative launch (1): every
+    scene stops at the oracle's sweep with the oracle's positions."""
     ss, ms, cubs, outs = batch
     g = p.Mesh.batch(ss)
     g.precompute_import(*concat_cub(ss, cubs))
     X = np.concatenate([s.X for s in ss])
     V0 = np.concatenate([s.v0 for s in ss])
     x, v = t(X, cuda), t(V0, cuda)
-    opts = p.step_opts(precision=p.FP64, max_sweeps=CAP, rel_tol=TOL, check_every=8)
+    opts = p.step_opts(precision=p.FP64, max_sweeps=CAP, rel_tol=TOL, check_every=8, persistent=persistent)
     if bs is not None:
         chosen = g.autotune(x, v, opts)
         assert chosen in (64, 128, 256)
@@ -104,7 +106,8 @@ def test_batch_equals_single_scene_steps(cuda, batch):
         off += s.n_vertices
 
 
-def test_batch_fp32_matches_oracle_per_scene(cuda, batch):
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_batch_fp32_matches_oracle_per_scene(cuda, batch, persistent):
     """The FP32 batch against the FP64 oracle scene by scene: every scene runs exactly 6
     sweeps (a tolerance out of reach, a cap of 6) with its own line search; per scene, the
     largest vertex error is at most 1e-4 of the largest vertex displacement."""
@@ -114,7 +117,7 @@ def test_batch_fp32_matches_oracle_per_scene(cuda, batch):
     X = np.concatenate([s.X for s in ss])
     V0 = np.concatenate([s.v0 for s in ss])
     x, v = t(X, cuda), t(V0, cuda)
-    g.step(x, v, p.step_opts(precision=p.FP32, max_sweeps=6, rel_tol=1e-14, check_every=3))
+    g.step(x, v, p.step_opts(precision=p.FP32, max_sweeps=6, rel_tol=1e-14, check_every=3, persistent=persistent))
     sw, _, _ = g.batch_report()
     xg_all = x.cpu().numpy()
     off = 0
@@ -125,3 +128,24 @@ def test_batch_fp32_matches_oracle_per_scene(cuda, batch):
         err = np.linalg.norm(xg - o.x, axis=1).max() / np.linalg.norm(o.x - s.X, axis=1).max()
         assert err <= 1e-4, (k, err)
         off += s.n_vertices
+
+
+def test_persistent_barrier_wait_runs_out(cuda, batch):
+    """A bounded device wait that runs out: the test hook makes the persistent launch's first
+    grid barrier wait for one block more than the grid has, with a short wait limit set from
+    the host. Every block gives up after its polls, the step returns JGS2_ETIMEOUT with the
+    state not written, and the next step on the same mesh runs normally."""
+    ss, ms, cubs, outs = batch
+    g = p.Mesh.batch(ss)
+    g.precompute_import(*concat_cub(ss, cubs))
+    X = np.concatenate([s.X for s in ss])
+    V0 = np.concatenate([s.v0 for s in ss])
+    x, v = t(X, cuda), t(V0, cuda)
+    hook = p.step_opts(precision=p.FP32, max_sweeps=CAP, rel_tol=TOL, persistent=1, wait_polls=2000,
+                       test_unreachable_barrier=1)
+    with pytest.raises(p.JGS2Error) as ei:
+        g.step(x, v, hook)
+    assert ei.value.status == 8
+    assert np.array_equal(x.cpu().numpy(), X) and np.array_equal(v.cpu().numpy(), V0)
+    rep = g.step(x, v, p.step_opts(precision=p.FP32, max_sweeps=CAP, rel_tol=TOL, persistent=1))
+    assert rep.sweeps > 0 and np.isfinite(x.cpu().numpy()).all()
