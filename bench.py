@@ -417,7 +417,7 @@ def run_jgs2(args, rank, world, local_rank):
     # (last) sweep of a chunk must fall inside the step
     chunk = max(1, min(16, args.max_sweeps + 1))
     opts = p.step_opts(precision=prec, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4, profile=1,
-                       check_every=chunk)
+                       check_every=chunk, persistent=int(args.persistent and batch))
     x0 = torch.tensor(X, dtype=torch.float64, device=dev)
     v0 = torch.tensor(V0, dtype=torch.float64, device=dev)
     mesh.autotune(x0, v0, opts)
@@ -455,7 +455,8 @@ def run_jgs2(args, rank, world, local_rank):
     ms_step = ms_total / args.steps
     # end to end: host buffers through jgs2_step_host, copies inside the timed region
     xh, vh = X.copy(), V0.copy()
-    opts_e2e = p.step_opts(precision=prec, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4)
+    opts_e2e = p.step_opts(precision=prec, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4,
+                           check_every=chunk, persistent=int(args.persistent and batch))
     torch.cuda.synchronize()
     n_e2e = 0 if args.no_e2e else args.steps
     t0 = time.perf_counter()
@@ -477,6 +478,8 @@ def run_jgs2(args, rank, world, local_rank):
                    "contact": bool(args.contact) if args.workload == "spheres" else False,
                    "correction": args.correction, "line_search": True, "n_cub": args.n_cub, "rel_tol": 1e-4,
                    "max_sweeps": args.max_sweeps, "block_size": bs,
+                   "batch_launch": ("persistent cooperative launch per chunk" if args.persistent else
+                                    "one launch per kernel, graph-captured chunks") if batch else None,
                    "parallelism": f"{'scene shards' if batch else 'replicas'} x{world}",
                    "l2": "per-sweep working set larger than L2 (126 MB); no flush"},
         "sweeps_per_step": float(sweeps.mean()),
@@ -712,6 +715,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-paper-criterion", action="store_true")
+    ap.add_argument("--persistent", type=int, default=1,
+                    help="batch workload: one persistent cooperative launch per chunk of sweeps (1) or one launch "
+                         "per kernel (0)")
     ap.add_argument("--dx-tol", type=float, default=1e-3,
                     help="the paper's position-change tolerance on the unit-normalised scene")
     ap.add_argument("--n-spheres", type=int, default=10)

@@ -281,9 +281,11 @@ jgs2_status jgs2_energy_gradient(jgs2_mesh* mesh, const double* x_t, const doubl
  *     H(x*) lam = gbar over free DOFs (H: the exact Hessian of E at x*, no projection)
  *     dL/dx_t = (M/h^2) lam - dL/dv_{t+1}/h  (free),  dL/dx_{t+1} - H_pf lam  (pinned)
  *     dL/dv_t = (M/h) lam  (free), 0 (pinned);  dL/dE_e += -lam_e . g_e^el(x*) / E_e
- * The linear system is solved by flexible conjugate gradients preconditioned with the JGS2
- * sweep in linear mode (H_ii, R_i and the cubature element Hessians at x*, Eq. cubature
- * applied to the residual); correction = JGS2_CORR_OFF gives block-Jacobi preconditioning.
+ * The linear system is solved by flexible conjugate gradients preconditioned with the local
+ * solves of the corrected sweep at x* (H_ii + H~_i, H~_i the rotated cubature Hessian of
+ * Eq. cubature; symmetric positive definite); correction = JGS2_CORR_OFF gives block-Jacobi
+ * preconditioning (H_ii). The sweep's cubature estimate of the residual's reduced part is
+ * not applied: it makes the preconditioner indefinite, and conjugate gradients stall.
  * All arrays are DEVICE pointers in caller order: x_t, v_t, x_t1, gx_t1, gv_t1, gx_t, gv_t
  * [V][3] double; gE [T] double is ACCUMULATED (+=). Meshes with contact, or without a
  * free vertex, are rejected (JGS2_EINVAL): the barrier is not part of this adjoint. Returns JGS2_ENOTCONVERGED (all
@@ -301,9 +303,8 @@ typedef struct {
   double rel_residual;   /* |H lam - gbar| / |gbar| */
   double ms;
 } jgs2_adjoint_report;
-/* Defaults: max_iters 5000, rel_tol 1e-6, FP64, block-Jacobi preconditioner (the JGS2
- * preconditioner is available but, like the forward correction, its cubature estimate of the
- * residual's reduced part can stall the iteration), check_every 32. */
+/* Defaults: max_iters 5000, rel_tol 1e-6, FP64, block-Jacobi preconditioner (correction
+ * JGS2_CORR_OFF; JGS2_CORR_ASM adds the cubature Hessian to each local matrix), check_every 32. */
 void jgs2_adjoint_opts_default(jgs2_adjoint_opts* o);
 jgs2_status jgs2_step_adjoint(jgs2_mesh* mesh, const double* x_t, const double* v_t, const double* x_t1,
                               const double* gx_t1, const double* gv_t1, double* gx_t, double* gv_t,

@@ -1,10 +1,13 @@
 // Adjoint of a converged step (implicit-function theorem on Eq. 1's optimality condition):
 //     H(x*) lam = gbar = dL/dx_{t+1} + dL/dv_{t+1} / h        (free DOFs)
-// solved by flexible conjugate gradients whose preconditioner is the JGS2 sweep in linear
-// mode: z_i = (H_ii + H~_i)^{-1} (r_i + r~_i), with H_ii, R_i and the rotated cubature
-// element Hessians taken at x* and r~ the cubature sum of the residual r (Eq. cubature,
-// reading R3 "asm"). Without the correction the preconditioner is block Jacobi H_ii^{-1}.
-// Then dL/dx_t, dL/dv_t and dL/dE_e follow from lam (see jgs2_step_adjoint in jgs2.h).
+// solved by flexible conjugate gradients whose preconditioner is the corrected sweep's local
+// solve in linear mode: z_i = (H_ii + H~_i)^{-1} r_i, with H_ii, R_i and the rotated cubature
+// element Hessians (Eq. cubature) taken at x*. The sweep's cubature estimate of the
+// residual's reduced part (k_lin_pool, k_lin_precond<CORR = true>) is kept in the source but
+// not used: it makes the preconditioned operator indefinite (eigenvalues of negative real
+// part), and conjugate gradients stall with it. Without the correction the preconditioner
+// is block Jacobi H_ii^{-1}. Then dL/dx_t, dL/dv_t and dL/dE_e follow from lam (see
+// jgs2_step_adjoint in jgs2.h).
 #pragma once
 #include "jgs2_kernels.cuh"
 

@@ -1033,19 +1033,19 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
           group(JGS2_K_LS_PAIRS, 1, s, [&] { k_pair_trials<T, 0><<<npp, 128, 0, s>>>(d, m->d_state, pp); });
         group(JGS2_K_ENERGY, 1, s, [&] { k_energy<T, 0><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial); });
         group(JGS2_K_LS_DECIDE, 1, s, [&] {
-          k_ls_decide<0><<<1, 256, 0, s>>>(m->d_state, corr ? 1 : 0, m->d_partial, nbE, pp, npp);
+          k_ls_decide<0><<<1, 1024, 0, s>>>(m->d_state, corr ? 1 : 0, m->d_partial, nbE, pp, npp);
         });
         if (corr) {
           if (m->contact)
             group(JGS2_K_LS_PAIRS, 1, s, [&] { k_pair_trials<T, 1><<<npp, 128, 0, s>>>(d, m->d_state, pp); });
           group(JGS2_K_ENERGY, 1, s, [&] { k_energy<T, 1><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial); });
           group(JGS2_K_LS_DECIDE, 1, s,
-                [&] { k_ls_decide<1><<<1, 256, 0, s>>>(m->d_state, 1, m->d_partial, nbE, pp, npp); });
+                [&] { k_ls_decide<1><<<1, 1024, 0, s>>>(m->d_state, 1, m->d_partial, nbE, pp, npp); });
           if (m->contact)
             group(JGS2_K_LS_PAIRS, 1, s, [&] { k_pair_trials<T, 2><<<npp, 128, 0, s>>>(d, m->d_state, pp); });
           group(JGS2_K_ENERGY, 1, s, [&] { k_energy<T, 2><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial); });
           group(JGS2_K_LS_DECIDE, 1, s,
-                [&] { k_ls_decide<2><<<1, 256, 0, s>>>(m->d_state, 1, m->d_partial, nbE, pp, npp); });
+                [&] { k_ls_decide<2><<<1, 1024, 0, s>>>(m->d_state, 1, m->d_partial, nbE, pp, npp); });
         }
       }
       if (nbV > 0) group(JGS2_K_UPDATE, 1, s, [&] { k_update<T><<<nbV, 128, 0, s>>>(d, m->d_state); });
@@ -1858,14 +1858,11 @@ static jgs2_status adjoint_impl(Mesh* m, const double* xt, const double* vt, con
   const int nbD = std::max(1, std::min(nbV, 148 * 8));
   const double tol2 = o->rel_tol * o->rel_tol;
   k_dots<T><<<nbD, 128, 0, s>>>(d, b.a_r, b.a_r, b.a_r, b.a_r, m->d_partial, sc, 2, tol2, o->max_iters);
-  auto precond = [&]() {
-    if (corr) {
-      k_lin_pool<T><<<(m->nP * 12 + 127) / 128, 128, 0, s>>>(d, b.a_r, sc);
-      k_lin_precond<T, true><<<nbV, 128, 0, s>>>(d, b.a_lin, b.a_r, b.a_z, sc);
-    } else {
-      k_lin_precond<T, false><<<nbV, 128, 0, s>>>(d, b.a_lin, b.a_r, b.a_z, sc);
-    }
-  };
+  // preconditioner: the local matrices of the sweep at x* (H_ii, plus the rotated cubature
+  // Hessian H~_i with the correction on; both symmetric positive definite). The cubature
+  // estimate of the residual's reduced part is left out: with it the preconditioned operator
+  // has eigenvalues of negative real part, and conjugate gradients stall
+  auto precond = [&]() { k_lin_precond<T, false><<<nbV, 128, 0, s>>>(d, b.a_lin, b.a_r, b.a_z, sc); };
   precond();
   CK(cudaMemcpyAsync(b.a_p, b.a_z, sizeof(Vec4<T>) * Vf, cudaMemcpyDeviceToDevice, s));
   AdjScalars hs;

@@ -1311,42 +1311,55 @@ __device__ __forceinline__ bool ls_pass_runs(const StepState* st) {
 // Line search, IPC barrier part: the barrier change of the candidate pairs for each trial
 // step a = 2^-j along the pass's direction(s) (not polynomial in a), FP64 sums per block into
 // pp[(d * kLsTrials + j)][blockIdx], d the direction's place in the pass. k_energy adds them.
+// A warp takes 32 candidates at a time; the few within r_c are handed to the whole warp in
+// turn, lane l evaluating trial l % kLsTrials of direction l / kLsTrials, so a pair's trials
+// run side by side instead of one after another in a single lane.
 template <typename T, int DIR>
 __global__ void __launch_bounds__(128) k_pair_trials(DevMesh<T> m, const StepState* __restrict__ st,
                                                      double* __restrict__ pp /* [ND * kLsTrials][grid] */) {
   if (!ls_pass_runs<DIR>(st)) return;
   constexpr int ND = DIR == 2 ? 2 : 1;
   constexpr int NB = ND * kLsTrials;
-  __shared__ double red[32 * NB];
-  double acc[NB];
-#pragma unroll
-  for (int j = 0; j < NB; ++j) acc[j] = 0.0;
+  static_assert(NB <= 32, "one lane per (direction, trial)");
+  __shared__ double red[4][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int my_d = lane / kLsTrials, my_j = lane % kLsTrials;
+  const bool has_slot = lane < NB;
+  const Vec4<T>* my_dir = (DIR == 1 || my_d == 1) ? m.DJ : m.D;
+  const double my_a = 1.0 / double(1 << my_j);
+  double acc = 0.0;  // this lane's (direction, trial) sum
   const int np = min(*m.c.n_pairs, m.c.cap);
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) {
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int base = (blockIdx.x * (blockDim.x >> 5) + wid) * 32; base < np; base += nwarps * 32) {
+    const int q = base + lane;
     // a pair beyond r_c stays beyond dhat for every trial (each vertex moves at most
     // 0.45 (r_c - dhat)): its barrier is zero throughout
-    const double dq = m.c.d0[q];
-    if (!(dq < m.c.rc)) continue;
-    const uint64_t key = m.c.pairs[q];
-    const double b0 = barrier_b(dq, m.c.dhat);
-#pragma unroll
-    for (int dd = 0; dd < ND; ++dd) {
-      const Vec4<T>* dir = (DIR == 1 || dd == 1) ? m.DJ : m.D;
-      // no trial brings the pair within dhat (and it starts outside): zero change throughout
-      if (dq - pair_motion(m, m.c, key, dir) >= m.c.dhat * (1.0 + 1e-9)) continue;
-#pragma unroll 1
-      for (int j = 0; j < kLsTrials; ++j) {
-        int vs[4], nv;
-        P3 Jg[4];
-        const double d = pair_geom(m, m.c, key, 1.0 / double(1 << j), dir, vs, Jg, nv);
-        acc[dd * kLsTrials + j] += m.c.kappa * (barrier_b(d, m.c.dhat) - b0);
+    const double dq_own = q < np ? m.c.d0[q] : INFINITY;
+    unsigned near = __ballot_sync(0xffffffffu, dq_own < m.c.rc);
+    while (near) {
+      const int src = __ffs(near) - 1;
+      near &= near - 1;
+      const int qq = base + src;
+      const double dq = __shfl_sync(0xffffffffu, dq_own, src);
+      if (has_slot) {
+        const uint64_t key = m.c.pairs[qq];
+        // no trial brings the pair within dhat (and it starts outside): zero change
+        if (dq - pair_motion(m, m.c, key, my_dir) < m.c.dhat * (1.0 + 1e-9)) {
+          int vs[4], nv;
+          P3 Jg[4];
+          const double d = pair_geom(m, m.c, key, my_a, my_dir, vs, Jg, nv);
+          acc += m.c.kappa * (barrier_b(d, m.c.dhat) - barrier_b(dq, m.c.dhat));
+        }
       }
     }
   }
-  block_sum<NB>(acc, red);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int j = 0; j < NB; ++j) pp[(size_t)j * gridDim.x + blockIdx.x] = acc[j];
+  // fixed-order sums: per (direction, trial) slot over the block's warps
+  red[wid][lane] = acc;
+  __syncthreads();
+  if (threadIdx.x < NB) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w][threadIdx.x];
+    pp[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = sum;
   }
 }
 
@@ -1454,29 +1467,29 @@ __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st,
 }
 
 // Line search decision (one block, after the pass's k_pair_trials and k_energy): sums every
-// partial array in one pass (FP64), evaluates E(x + a d) - E(x) at a = 2^-j along the
-// pass's direction(s) in order and takes the first Armijo-satisfying trial. has_j = 0 (no
-// correction, D = D_J): a failed D is a rejection.
+// partial array (FP64, one warp per coefficient, fixed order: strided lane sums, then a
+// fixed shuffle tree), evaluates E(x + a d) - E(x) at a = 2^-j along the pass's direction(s)
+// in order and takes the first Armijo-satisfying trial. has_j = 0 (no correction, D = D_J):
+// a failed D is a rejection.
 template <int DIR>
-__global__ void __launch_bounds__(256) k_ls_decide(StepState* st, int has_j, const double* __restrict__ partial,
-                                                   int n_part, const double* __restrict__ pp, int n_pp) {
+__global__ void __launch_bounds__(1024) k_ls_decide(StepState* st, int has_j, const double* __restrict__ partial,
+                                                    int n_part, const double* __restrict__ pp, int n_pp) {
   if (!ls_pass_runs<DIR>(st)) return;
   constexpr int ND = DIR == 2 ? 2 : 1;
   constexpr int NC = 6 * ND;
   constexpr int NB = ND * kLsTrials;
-  __shared__ double red[32 * (NC + NB)];
-  double cf[NC + NB];
-#pragma unroll
-  for (int j = 0; j < NC + NB; ++j) cf[j] = 0.0;
-  for (int q = threadIdx.x; q < n_part; q += blockDim.x) {
-#pragma unroll
-    for (int j = 0; j < NC; ++j) cf[j] += partial[(size_t)j * n_part + q];
+  static_assert(NC + NB <= 32, "one warp per coefficient");
+  __shared__ double cf[NC + NB];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (w < NC + NB) {
+    const double* src = w < NC ? partial + (size_t)w * n_part : pp + (size_t)(w - NC) * n_pp;
+    const int n = w < NC ? n_part : n_pp;
+    double v = 0.0;
+    for (int q = lane; q < n; q += 32) v += src[q];
+    v = warp_sum(v);
+    if (lane == 0) cf[w] = v;
   }
-  for (int q = threadIdx.x; q < n_pp; q += blockDim.x) {
-#pragma unroll
-    for (int j = 0; j < NB; ++j) cf[NC + j] += pp[(size_t)j * n_pp + q];
-  }
-  block_sum<NC + NB>(cf, red);
+  __syncthreads();
   if (threadIdx.x != 0) return;
   double alpha = 0.0;
   int chosen = -1;
