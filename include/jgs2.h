@@ -251,12 +251,14 @@ jgs2_status jgs2_step(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opt
 
 /* The same step by Gauss-Seidel sweeps (Sec. 8.1): the free vertices are coloured greedily
  * in caller order (no two of a colour share a tet); a GS sweep runs the colours in turn,
- * each as one sweep whose directions and line search move only that colour, at the
- * positions the earlier colours left. Use it with records from jgs2_precompute(gs = 1)
- * (or import) or with correction = JGS2_CORR_OFF. The relative residual is taken in FP64 at
- * the start of each GS sweep; report->sweeps counts GS sweeps and the trace holds their
- * residuals. x, v: device [V][3] double as in jgs2_step. Meshes with contact or batches
- * return JGS2_EINVAL. The profile fields of the report are not filled. */
+ * each as one pass of the sweep kernels whose directions and line search move only that
+ * colour, at the positions the earlier colours left. The colour passes of check_every GS
+ * sweeps are captured in one CUDA graph and replayed like jgs2_step's sweeps. Use it with
+ * records from jgs2_precompute(gs = 1) (or import) or with correction = JGS2_CORR_OFF. The
+ * relative residual (full gradient, FP64-class sums) is taken at the start of each GS sweep;
+ * report->sweeps counts GS sweeps and the trace holds their residuals. x, v: device [V][3]
+ * double as in jgs2_step. Meshes with contact or batches return JGS2_EINVAL; dx_tol is
+ * ignored. */
 jgs2_status jgs2_step_gs(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts,
                          void* stream, jgs2_step_report* report);
 

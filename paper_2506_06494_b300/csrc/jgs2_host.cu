@@ -911,7 +911,7 @@ static jgs2_status ensure_gstream(Mesh* m) {
 // kernel group of the chunk's last sweep; their times are read after each replay.
 template <typename T>
 static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs, int max_k, double rel_tol,
-                              bool check, StepState* hs, Launches& L) {
+                              bool check, StepState* hs, Launches& L, int gs_ncol = 0) {
   DevMesh<T> d = dev_view<T>(m);
   const bool corr = o.correction != JGS2_CORR_OFF;
   const int nbV = (m->Vf + 127) / 128;
@@ -934,7 +934,8 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
   init.max_sweeps = max_k;
   init.rel_tol = rel_tol;
   init.alpha = 1.0;
-  if (rel_tol >= 0.0 && o.dx_tol > 0.0) {
+  init.gs_ncol = gs_ncol;
+  if (rel_tol >= 0.0 && o.dx_tol > 0.0 && gs_ncol == 0) {
     // Sec. 8: |x^k - x^{k-1}| on the scene normalised to a unit cube
     const double L = o.length_scale > 0.0 ? o.length_scale : m->extent;
     init.dx2_tol = (o.dx_tol * L) * (o.dx_tol * L);
@@ -953,7 +954,8 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
   key = key * 512 + bs;
   key = key * 512 + gbs;
   key = key * 8 + gtpv;
-  key = key * 8192 + chunk + (1L << 60);
+  key = key * 8192 + chunk;
+  key = key * 64 + gs_ncol + (1L << 60);
   const bool same_view = m->gdev.size() == sizeof(d) && std::memcmp(m->gdev.data(), &d, sizeof(d)) == 0;
   if (m->graph_key != key || !same_view) {
     if (m->graph) cudaGraphExecDestroy(m->graph);
@@ -996,8 +998,12 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
     const bool pool = corr && m->nP > 0;
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    for (int q = 0; q < chunk; ++q) {
-      timed = prof && q == chunk - 1;
+    // a Gauss-Seidel sweep is one pass per colour, each with the colour's vertex mask
+    const int passes = gs_ncol > 0 ? chunk * gs_ncol : chunk;
+    const DevMesh<T> d_base = d;
+    for (int q = 0; q < passes; ++q) {
+      timed = prof && q == passes - 1;
+      if (gs_ncol > 0) d.vmask = m->d_gsmask + (size_t)(q % gs_ncol) * m->Vf;
       // contact pass (positions only) alongside the element pass; both feed the gather
       if (m->contact) {
         fork(m->gfork[0]);
@@ -1050,6 +1056,7 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
       }
       if (nbV > 0) group(JGS2_K_UPDATE, 1, s, [&] { k_update<T><<<nbV, 128, 0, s>>>(d, m->d_state); });
     }
+    d = d_base;
     cudaError_t e = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess) return fail(JGS2_ECUDA, std::string("sweep capture: ") + cudaGetErrorString(e));
     if (cerr != cudaSuccess) {
@@ -1387,7 +1394,7 @@ static jgs2_status check_opts(const Mesh* m, const jgs2_step_opts* o) {
 
 template <typename T>
 static jgs2_status step_impl(Mesh* m, double* x, double* v, const jgs2_step_opts* o, cudaStream_t s,
-                             jgs2_step_report* rep) {
+                             jgs2_step_report* rep, int gs_ncol = 0) {
   jgs2_status st = ensure_prec<T>(m);
   if (st != JGS2_OK) return st;
   DevMesh<T> d = dev_view<T>(m);
@@ -1429,7 +1436,7 @@ static jgs2_status step_impl(Mesh* m, double* x, double* v, const jgs2_step_opts
       if (q.status) hs->status = q.status;
     }
   } else {
-    st = run_sweeps<T>(m, *o, s, o->max_sweeps, o->rel_tol, true, hs, L);
+    st = run_sweeps<T>(m, *o, s, o->max_sweeps, o->rel_tol, true, hs, L, gs_ncol);
   }
   if (st != JGS2_OK) {
     cudaEventDestroy(e0);
@@ -1918,12 +1925,6 @@ jgs2_status step_adjoint(Mesh* m, const double* xt, const double* vt, const doub
                                    : adjoint_impl<float>(m, xt, vt, x1, gx1, gv1, gx, gv, gE, o, s, rep);
 }
 
-// v_{t+1} = (x_{t+1} - x_t) / h over 3V doubles (caller order).
-static __global__ void k_gs_velocity(const double* __restrict__ x1, const double* __restrict__ xt,
-                                     double* __restrict__ v, int n, double ih) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < n) v[q] = (x1[q] - xt[q]) * ih;
-}
 
 // Gauss-Seidel step (Sec. 8.1; readings R19-R21): the free vertices are coloured greedily in
 // caller order; a GS sweep runs the colours in turn, each as one sweep of the Jacobi
@@ -1938,7 +1939,6 @@ jgs2_status step_gs(Mesh* m, double* x, double* v, const jgs2_step_opts* o, void
     return fail(JGS2_EINVAL, "the Gauss-Seidel step takes single scenes without contact");
   cudaStream_t s = (cudaStream_t)stream;
   const int V = m->V, Vf = m->Vf;
-  const size_t n3 = 3 * (size_t)V;
   if (!m->d_gsmask && Vf > 0) {
     // greedy colouring in caller order over the free vertices that share a tet
     std::vector<std::vector<int>> nbr(V);
@@ -1962,68 +1962,12 @@ jgs2_status step_gs(Mesh* m, double* x, double* v, const jgs2_step_opts* o, void
     for (int i = 0; i < Vf; ++i) masks[(size_t)col[m->perm[i]] * Vf + i] = 1;
     CK(dalloc(&m->d_gsmask, masks.size()));
     CK(cudaMemcpy(m->d_gsmask, masks.data(), masks.size(), cudaMemcpyHostToDevice));
-    CK(dalloc(&m->d_vmask, (size_t)Vf));
-    CK(dalloc(&m->d_gs_xt, n3));
-    CK(dalloc(&m->d_gs_xk, n3));
-    CK(dalloc(&m->d_gs_g, n3));
     m->gs_ncol = ncol;
   }
-  if (rep) std::memset(rep, 0, sizeof(*rep));
-  if (Vf == 0) {
-    // no free vertex: x_{t+1} = x_t, v_{t+1} = 0
-    CK(cudaMemsetAsync(v, 0, sizeof(double) * n3, s));
-    CK(cudaStreamSynchronize(s));
-    if (rep) rep->converged = 1;
-    return JGS2_OK;
-  }
-  CK(cudaMemcpyAsync(m->d_gs_xt, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(m->d_gs_xk, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s));
-  std::vector<double> g(n3);
-  double g0 = 0.0, r = 0.0;
-  int k = 0;
-  bool conv = false;
-  for (;;) {
-    st = energy_gradient(m, m->d_gs_xt, v, m->d_gs_xk, nullptr, m->d_gs_g, s);
-    if (st != JGS2_OK) return st;
-    CK(cudaMemcpy(g.data(), m->d_gs_g, sizeof(double) * n3, cudaMemcpyDeviceToHost));
-    double gn = 0.0;
-    for (double q : g) gn += q * q;  // pinned rows are zero
-    gn = std::sqrt(gn);
-    if (k == 0) g0 = gn;
-    r = g0 > 0.0 ? gn / g0 : 0.0;
-    if (!std::isfinite(r)) return fail(JGS2_EDIVERGED, "residual became non-finite; state not written");
-    if (rep && k < JGS2_TRACE_MAX && o->record_trace) {
-      rep->trace[k] = r;
-      rep->trace_len = k + 1;
-    }
-    if (r <= o->rel_tol || g0 == 0.0) {
-      conv = true;
-      break;
-    }
-    if (k >= o->max_sweeps) break;
-    for (int c = 0; c < m->gs_ncol; ++c) {
-      CK(cudaMemcpyAsync(m->d_vmask, m->d_gsmask + (size_t)c * Vf, (size_t)Vf, cudaMemcpyDeviceToDevice, s));
-      m->vmask_on = true;
-      st = sweeps(m, m->d_gs_xt, v, m->d_gs_xk, 1, o, stream);
-      m->vmask_on = false;
-      if (st != JGS2_OK) return st;
-      if (m->h_state->status != 0)
-        return fail((jgs2_status)m->h_state->status, "a Gauss-Seidel colour pass failed; state not written");
-    }
-    ++k;
-  }
-  CK(cudaMemcpyAsync(x, m->d_gs_xk, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s));
-  k_gs_velocity<<<(int)((n3 + 255) / 256), 256, 0, s>>>(m->d_gs_xk, m->d_gs_xt, v, (int)n3, 1.0 / m->h);
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(s));
-  if (rep) {
-    rep->sweeps = k;
-    rep->converged = conv ? 1 : 0;
-    rep->rel_residual = r;
-    rep->g0 = g0;
-  }
-  if (!conv) return fail(JGS2_ENOTCONVERGED, "max_sweeps reached before rel_tol");
-  return JGS2_OK;
+  // the GS sweeps run as graph-captured colour passes of the Jacobi machinery (one pass per
+  // colour with the colour's vertex mask; the stopping test at each GS sweep's first pass)
+  return o->precision == JGS2_FP64 ? step_impl<double>(m, x, v, o, s, rep, m->gs_ncol)
+                                   : step_impl<float>(m, x, v, o, s, rep, m->gs_ncol);
 }
 
 }  // namespace jgs2

@@ -90,7 +90,9 @@ struct StepState {
   int32_t pad_dx;
   double dx2_applied;  // |x^k - x^{k-1}|^2 of the last update applied (for the report)
   int32_t ls_passes[3];  // line-search passes that did work, by pass (D, D_J, both)
-  int32_t pad_ls;
+  int32_t gs_ncol;       // Gauss-Seidel step: colour passes per GS sweep (0: Jacobi sweeps)
+  int32_t pass;          // Gauss-Seidel step: colour passes begun
+  int32_t pad_gs;
 };
 
 // Contact data of a mesh (Sec. 7); pairs: 0 vertex-wall, 1 vertex-face, 2 edge-edge.

@@ -965,6 +965,29 @@ __global__ void __launch_bounds__(32 * kPoolWarps) k_pool(DevMesh<T> m, const St
 __device__ __forceinline__ void finalize_sweep(StepState* st, double r2, double gd, double gdj, double dd2,
                                                double ddj2, double* trace, int record) {
   st->ticket_main = 0;
+  if (st->gs_ncol > 0) {
+    // Gauss-Seidel step: a GS sweep is gs_ncol colour passes; the stopping test (on the
+    // full gradient, which the gather forms for every vertex) is taken at the first
+    const int pass = st->pass;
+    st->pass = pass + 1;
+    if (pass % st->gs_ncol != 0) {
+      st->slope = gd;
+      st->slope_j = gdj;
+      st->alpha = 1.0;
+      st->dir = 0;
+      st->need_j = 0;
+      st->ls_mode = st->prev_dir;
+      st->dd2 = dd2;
+      st->ddj2 = ddj2;
+      st->dx2 = dd2;
+      if (!isfinite(gd) || !isfinite(gdj) || !isfinite(r2)) {
+        st->status = 6;  // JGS2_EDIVERGED
+        st->done = 1;
+        st->sweeps = st->k;
+      }
+      return;
+    }
+  }
   const int k = st->k;
   const double gn = sqrt(r2);
   if (k == 0) st->g0 = gn;
