@@ -361,8 +361,9 @@ def split_cubature(elem, w, u, ss):
     return out
 
 
-def timed_steps(mesh, x, v, opts, n, stream):
-    """n steps between CUDA events on the launching stream; (ms, [report dicts])."""
+def timed_steps(mesh, x, v, opts, n, stream, gs=False):
+    """n steps (Gauss-Seidel steps with gs) between CUDA events on the launching stream;
+    (ms, [report dicts])."""
     import torch
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -370,7 +371,7 @@ def timed_steps(mesh, x, v, opts, n, stream):
     e0.record(stream)
     reps = []
     for _ in range(n):
-        r = mesh.step(x, v, opts, stream)
+        r = mesh.step_gs(x, v, opts, stream) if gs else mesh.step(x, v, opts, stream)
         reps.append({"sweeps": r.sweeps, "converged": r.converged, "rel": r.rel_residual,
                      "kms": list(r.kernel_ms), "kl": list(r.kernel_launches), "launches": r.launches,
                      "fallback": r.fallback, "rejects": r.ls_rejects, "dj": r.dj_steps,
@@ -402,8 +403,11 @@ def run_jgs2(args, rank, world, local_rank):
     Vf = int((~pin.astype(bool)).sum())
     t0 = time.perf_counter()
     mesh = p.Mesh.batch(ss) if batch else p.Mesh.from_scene(ss[0])
+    gs = bool(args.gs)
+    if gs and (batch or (args.workload == "spheres" and args.contact)):
+        raise SystemExit("--gs takes a single scene without contact")
     if args.cubature == "precompute":
-        mesh.precompute(n_cub=args.n_cub)
+        mesh.precompute(n_cub=args.n_cub, gs=int(gs))
     else:
         # seeded synthetic records: same kernel work, no convergence meaning (profiling only)
         import scenes
@@ -425,7 +429,7 @@ def run_jgs2(args, rank, world, local_rank):
     bs = {"gather_block": gbs, "gather_threads_per_vertex": gtpv, "correct_block": cbs}
     x, v = x0.clone(), v0.clone()
     for _ in range(args.warmup):
-        mesh.step(x, v, opts, stream)
+        mesh.step_gs(x, v, opts, stream) if gs else mesh.step(x, v, opts, stream)
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
@@ -433,7 +437,7 @@ def run_jgs2(args, rank, world, local_rank):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     gidx = vis.split(",")[local_rank] if vis else str(local_rank)
     clocks = Clocks(gidx)
-    ms_total, reps = timed_steps(mesh, x, v, opts, args.steps, stream)
+    ms_total, reps = timed_steps(mesh, x, v, opts, args.steps, stream, gs)
     ck = clocks.stop()
     scene_sweeps = None
     if batch:
@@ -458,7 +462,8 @@ def run_jgs2(args, rank, world, local_rank):
     opts_e2e = p.step_opts(precision=prec, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4,
                            check_every=chunk, persistent=int(args.persistent and batch))
     torch.cuda.synchronize()
-    n_e2e = 0 if args.no_e2e else args.steps
+    # (the host-array entry point runs Jacobi steps; the Gauss-Seidel form has no e2e leg)
+    n_e2e = 0 if (args.no_e2e or gs) else args.steps
     t0 = time.perf_counter()
     for _ in range(n_e2e):
         mesh.step_host(xh, vh, opts_e2e, stream)
@@ -477,6 +482,7 @@ def run_jgs2(args, rank, world, local_rank):
                    "vertices": int(len(X)), "free_vertices": Vf,
                    "contact": bool(args.contact) if args.workload == "spheres" else False,
                    "correction": args.correction, "line_search": True, "n_cub": args.n_cub, "rel_tol": 1e-4,
+                   "parallelisation": "Gauss-Seidel (greedy colouring, group subspaces)" if gs else "Jacobi",
                    "max_sweeps": args.max_sweeps, "block_size": bs,
                    "batch_launch": ("persistent cooperative launch per chunk" if args.persistent else
                                     "one launch per kernel, graph-captured chunks") if batch else None,
@@ -572,9 +578,12 @@ def run_jgs2(args, rank, world, local_rank):
     else:
         # every step stopped before the timed last sweep of its first chunk
         out["roofline"] = None
-    if not batch and not args.no_paper_criterion:
+    if not batch and not gs and not args.no_paper_criterion:
         out["paper_criterion"] = paper_criterion(args, p, mesh, x0, v0, stream, prec, corr, X)
-    if not args.no_compare:
+    if gs:
+        if not args.no_compare:
+            out["comparisons"] = compare_gs(args, p, mesh, x0, v0, stream, corr, prec)
+    elif not args.no_compare:
         out["comparisons"] = compare(args, p, mesh, ss, batch, x0, v0, stream, corr, prec)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, float(sweeps.mean()))
@@ -635,6 +644,21 @@ def compare(args, p, mesh, ss, batch, x0, v0, stream, corr, prec):
         g.close()
     res["fp64_per_scene_loop"] = {"ms_per_step": round(tot, 3), "scenes": len(ss), "converged_scenes": conv,
                                   "sweeps_median": float(np.median(sweeps)), "sweeps_max": int(max(sweeps))}
+    return res
+
+
+def compare_gs(args, p, mesh, x0, v0, stream, corr, prec):
+    """The Gauss-Seidel step against its FP64 form and its uncorrected form on the same GPU
+    (one step each)."""
+    res = {}
+    for name, o in [("gs_fp64", p.step_opts(precision=p.FP64, correction=corr, max_sweeps=args.max_sweeps,
+                                            rel_tol=1e-4)),
+                    ("gs_uncorrected", p.step_opts(precision=prec, correction=p.CORR_OFF,
+                                                   max_sweeps=args.max_sweeps, rel_tol=1e-4))]:
+        x, v = x0.clone(), v0.clone()
+        ms, reps = timed_steps(mesh, x, v, o, 1, stream, gs=True)
+        res[name] = {"ms_per_step": round(ms, 3), "gs_sweeps": int(reps[0]["sweeps"]),
+                     "converged": int(reps[0]["converged"]), "rel_residual": float(reps[0]["rel"])}
     return res
 
 
@@ -715,6 +739,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-paper-criterion", action="store_true")
+    ap.add_argument("--gs", type=int, default=0,
+                    help="1: Gauss-Seidel steps (greedy colouring, group precompute) on a single scene without contact")
     ap.add_argument("--persistent", type=int, default=1,
                     help="batch workload: one persistent cooperative launch per chunk of sweeps (1) or one launch "
                          "per kernel (0)")
