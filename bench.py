@@ -425,8 +425,9 @@ def run_jgs2(args, rank, world, local_rank):
     x0 = torch.tensor(X, dtype=torch.float64, device=dev)
     v0 = torch.tensor(V0, dtype=torch.float64, device=dev)
     mesh.autotune(x0, v0, opts)
-    gbs, gtpv, cbs = mesh.launch_config(prec)
-    bs = {"gather_block": gbs, "gather_threads_per_vertex": gtpv, "correct_block": cbs}
+    gbs, gtpv, cbs, cpf = mesh.launch_config(prec)
+    bs = {"gather_block": gbs, "gather_threads_per_vertex": gtpv, "correct_block": cbs,
+          "correct_slot_prefetch": cpf}
     x, v = x0.clone(), v0.clone()
     for _ in range(args.warmup):
         mesh.step_gs(x, v, opts, stream) if gs else mesh.step(x, v, opts, stream)

@@ -208,12 +208,15 @@ jgs2_status jgs2_batch_report(const jgs2_mesh* mesh, int32_t* sweeps, int32_t* c
  * gather kernel in each of its shapes (threads per block x threads per vertex: 64, 128,
  * 256 x 1 and 128, 256 x 4; with 4 threads per vertex the incidences of a vertex are split
  * over the lanes of its group) and the correction kernel at 64, 128 and 256 threads per
- * block, and keeps the fastest of each for opts->precision. *block_size (may be NULL)
+ * block with and without loading every slot's index first, and keeps the fastest of each
+ * for opts->precision. *block_size (may be NULL)
  * receives the correction kernel's choice; jgs2_mesh_launch_config gives all three. */
 jgs2_status jgs2_autotune(jgs2_mesh* mesh, double* x, double* v, const jgs2_step_opts* opts,
                           void* stream, int32_t* block_size);
 /* The mesh's launch shapes for precision: config[0] gather threads per block, config[1]
- * gather threads per vertex, config[2] correction threads per block (host int32_t[3]). */
+ * gather threads per vertex, config[2] correction threads per block, config[3] 1 if the
+ * correction kernel loads every cubature slot's index and weight before the first slot's
+ * work (host int32_t[4]). */
 jgs2_status jgs2_mesh_launch_config(const jgs2_mesh* mesh, int32_t precision, int32_t* config);
 
 /* Offline stage (Secs. 5-6), host FP64: factorises the rest Hessian H_bar = M/h^2 + K_bar

@@ -801,16 +801,20 @@ static void launch_gather(DevMesh<T>& d, const Mesh* m, bool corr, int bs, int t
 #undef JGS2_G
 }
 
+// k_correct with a runtime shape: bs threads per block (64, 128 or 256); pf = 1 loads
+// every slot's pool index and weight first (four slots)
 template <typename T, bool BATCH>
 static void launch_correct(DevMesh<T>& d, int bs, cudaStream_t s, StepState* st, double* partial,
-                           double* trace, int rec) {
+                           double* trace, int rec, int pf = 0) {
   const int Vf = d.Vf;
+#define JGS2_C(B, P) k_correct<T, BATCH, B, P><<<(Vf + B - 1) / B, B, 0, s>>>(d, st, partial, trace, rec)
   if (bs == 64)
-    k_correct<T, BATCH, 64><<<(Vf + 63) / 64, 64, 0, s>>>(d, st, partial, trace, rec);
+    pf ? JGS2_C(64, true) : JGS2_C(64, false);
   else if (bs == 256)
-    k_correct<T, BATCH, 256><<<(Vf + 255) / 256, 256, 0, s>>>(d, st, partial, trace, rec);
+    pf ? JGS2_C(256, true) : JGS2_C(256, false);
   else
-    k_correct<T, BATCH, 128><<<(Vf + 127) / 128, 128, 0, s>>>(d, st, partial, trace, rec);
+    pf ? JGS2_C(128, true) : JGS2_C(128, false);
+#undef JGS2_C
 }
 
 // Launch bookkeeping of one step: counts per kernel kind and, when profiling, a CUDA
@@ -954,6 +958,7 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
   key = key * 512 + bs;
   key = key * 512 + gbs;
   key = key * 8 + gtpv;
+  key = key * 2 + m->cpf[pi];
   key = key * 8192 + chunk;
   key = key * 64 + gs_ncol + (1L << 60);
   const bool same_view = m->gdev.size() == sizeof(d) && std::memcmp(m->gdev.data(), &d, sizeof(d)) == 0;
@@ -1027,7 +1032,9 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
       if (nbV > 0) {
         if (corr)
           group(JGS2_K_CORRECT, 1, s,
-                [&] { launch_correct<T, false>(d, bs, s, m->d_state, m->d_partial, m->d_trace, o.record_trace); });
+                [&] {
+                  launch_correct<T, false>(d, bs, s, m->d_state, m->d_partial, m->d_trace, o.record_trace, m->cpf[pi]);
+                });
       }
       if (o.line_search) {
         // along D; along D_J only when every trial along D failed (those launches return
@@ -1264,7 +1271,8 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
   }
   const bool prof = L.prof;
   const long key = ((((((long)(sizeof(T) == 4) * 3 + o.correction) * 2 + (o.line_search != 0)) * 2 + (prof ? 1 : 0)) *
-                          512 + bs) * 4096 + gbs * 8 + gtpv) * 4096 + chunk + (long)(o.max_sweeps) * 1000003L +
+                          512 + bs) * 4096 + gbs * 8 + gtpv) * 4096 + chunk * 2 + m->cpf[pi] +
+                        (long)(o.max_sweeps) * 1000003L +
                         (long)(o.rel_tol * 1e12);
   const bool same_view = m->gdev.size() == sizeof(d) && std::memcmp(m->gdev.data(), &d, sizeof(d)) == 0;
   if (m->graph_key != key || !same_view) {
@@ -1305,7 +1313,7 @@ static jgs2_status run_sweeps_batch(Mesh* m, const jgs2_step_opts& o, cudaStream
       if (corr) {
         group(JGS2_K_POOL, 1, s, [&] { k_pool<T, true><<<(m->nP + kPoolWarps - 1) / kPoolWarps, 32 * kPoolWarps, 0, s>>>(d, m->d_state); });
         group(JGS2_K_CORRECT, 1, s,
-              [&] { launch_correct<T, true>(d, bs, s, m->d_state, m->d_partial, m->d_trace, 0); });
+              [&] { launch_correct<T, true>(d, bs, s, m->d_state, m->d_partial, m->d_trace, 0, m->cpf[pi]); });
       }
       // per-scene stopping test (counted with the update)
       group(JGS2_K_UPDATE, 1, s, [&] {
@@ -1757,21 +1765,25 @@ static jgs2_status autotune_impl(Mesh* m, double* x, double* v, const jgs2_step_
       gpick = c;
     }
   }
-  int cpick = 128;
+  int cpick = 128, ppick = 0;
   if (corr) {
     best = 1e30f;
-    for (int c : {64, 128, 256}) {
-      const float ms = time_it([&] { launch_correct<T, false>(d, c, s, m->d_state, m->d_partial, m->d_trace, 0); });
-      if (ms < best) {
-        best = ms;
-        cpick = c;
+    for (int pf = 0; pf < 2; ++pf)
+      for (int c : {64, 128, 256}) {
+        const float ms =
+            time_it([&] { launch_correct<T, false>(d, c, s, m->d_state, m->d_partial, m->d_trace, 0, pf); });
+        if (ms < best) {
+          best = ms;
+          cpick = c;
+          ppick = pf;
+        }
       }
-    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CK(cudaGetLastError());
   m->bs[pi] = cpick;
+  m->cpf[pi] = ppick;
   m->gbs[pi] = kGatherShapes[gpick][0];
   m->gtpv[pi] = kGatherShapes[gpick][1];
   m->graph_key = -1;
@@ -2137,6 +2149,7 @@ jgs2_status jgs2_mesh_launch_config(const jgs2_mesh* mesh, int32_t precision, in
   config[0] = m->gbs[pi];
   config[1] = m->gtpv[pi];
   config[2] = m->bs[pi];
+  config[3] = m->cpf[pi];
   return JGS2_OK;
 }
 

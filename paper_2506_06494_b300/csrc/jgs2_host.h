@@ -80,6 +80,7 @@ struct Mesh {
   int bs[2] = {128, 128};
   int gbs[2] = {128, 128};
   int gtpv[2] = {1, 1};
+  int cpf[2] = {0, 0};     // k_correct: load every slot's pool index and weight first
   // captured sweep chunk of a batch step: key = (precision, correction, line search, bs, chunk)
   cudaGraphExec_t graph = nullptr;
   long graph_key = -1;

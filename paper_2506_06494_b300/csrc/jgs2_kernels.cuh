@@ -641,8 +641,35 @@ __device__ __forceinline__ void slot_sums(const T* Hp, T w, const T (&U)[36], T 
 }
 
 // Cubature sums for vertex i over its n_cub slots, records read directly from global memory.
-template <typename T, bool NC = true>
+// Fixed slot count: every slot's pool index and weight are loaded first, so the pool rows'
+// addresses are known before the first slot's work starts.
+template <typename T, bool NC, int NCUB>
+__device__ __forceinline__ void cubature_sums_n(const DevMesh<T>& m, int i, T (&Ht)[6], T (&gt)[3]) {
+  int ps[NCUB];
+  T ws[NCUB];
+#pragma unroll
+  for (int s = 0; s < NCUB; ++s) {
+    ps[s] = m.cub_p[(size_t)s * m.cs + i];
+    ws[s] = m.cub_w[(size_t)s * m.cs + i];
+  }
+#pragma unroll
+  for (int s = 0; s < NCUB; ++s) {
+    if (ps[s] < 0) continue;
+    T U[36];
+    const T* up = m.cub_u + (size_t)s * 36 * m.cs + i;
+#pragma unroll
+    for (int q = 0; q < 36; ++q) U[q] = up[(size_t)q * m.cs];
+    slot_sums<T, NC>(m.pool_H + (size_t)ps[s] * kPoolStride, ws[s], U, Ht, gt);
+  }
+}
+
+// PF: with four slots, take the prefetching form above (the autotuner picks per mesh).
+template <typename T, bool NC = true, bool PF = false>
 __device__ __forceinline__ void cubature_sums(const DevMesh<T>& m, int i, T (&Ht)[6], T (&gt)[3]) {
+  if (PF && m.n_cub == 4) {
+    cubature_sums_n<T, NC, 4>(m, i, Ht, gt);
+    return;
+  }
   for (int s = 0; s < m.n_cub; ++s) {
     const int p = m.cub_p[(size_t)s * m.cs + i];
     if (p < 0) continue;
@@ -1179,7 +1206,7 @@ __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 512) / BS)
 // Sweep phase 2, thread per free vertex: the cubature sums H~_i, g~_i (Eq. cubature) from
 // the rotated pool element data (L2-resident rows), the 3x3 solve of Eq. reduced_local, D_i, and g.D. The
 // last block closes the sweep's reduction with phase 1's partial sums.
-template <typename T, bool BATCH, int BS, bool NC = true>
+template <typename T, bool BATCH, int BS, bool NC = true, bool PF = false>
 __device__ __forceinline__ void correct_body(const DevMesh<T>& m, StepState* st, double* __restrict__ partial,
                                              double* __restrict__ trace, int record, int bid, int nb) {
   __shared__ double red[96];
@@ -1191,7 +1218,7 @@ __device__ __forceinline__ void correct_body(const DevMesh<T>& m, StepState* st,
   const bool active = i < m.Vf && (!BATCH || !m.scenes[sc].done);
   if (active) {
     T Ht[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, gt[3] = {T(0), T(0), T(0)};
-    cubature_sums<T, NC>(m, i, Ht, gt);
+    cubature_sums<T, NC, PF>(m, i, Ht, gt);
     // the vertex's own g, H_ii, R_i from the gather (loaded after the cubature loop, so
     // they hold no registers during it)
     const T* o = m.ghr + i;
@@ -1264,12 +1291,12 @@ __device__ __forceinline__ void correct_body(const DevMesh<T>& m, StepState* st,
   if (threadIdx.x == 0) finalize_sweep(st, r2, gd, gdj, dd, djj, trace, record);
 }
 
-template <typename T, bool BATCH, int BS>
+template <typename T, bool BATCH, int BS, bool PF = false>
 __global__ void __launch_bounds__(BS, (sizeof(T) == 4 ? 768 : 256) / BS) k_correct(DevMesh<T> m, StepState* st,
                                                 double* __restrict__ partial /* [3][grid] */,
                                                 double* __restrict__ trace, int record) {
   if (!BATCH && st->done) return;
-  correct_body<T, BATCH, BS>(m, st, partial, trace, record, blockIdx.x, gridDim.x);
+  correct_body<T, BATCH, BS, true, PF>(m, st, partial, trace, record, blockIdx.x, gridDim.x);
 }
 
 // Exact energy change of a tet for the displacement increment alpha*d (no cancellation):

@@ -253,8 +253,9 @@ class Mesh:
         return bs.value
 
     def launch_config(self, precision):
-        """(gather threads per block, gather threads per vertex, correction threads per block)."""
-        cfg = np.zeros(3, dtype=np.int32)
+        """(gather threads per block, gather threads per vertex, correction threads per block,
+        correction slot prefetch)."""
+        cfg = np.zeros(4, dtype=np.int32)
         _check(lib().jgs2_mesh_launch_config(self.handle, int(precision), cfg.ctypes.data))
         return tuple(int(c) for c in cfg)
 
