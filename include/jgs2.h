@@ -59,14 +59,16 @@ typedef struct {
   const uint8_t* pinned;     /* [V] 1 = vertex held at its position x_t (not a DOF); may be NULL */
   double gravity[3];         /* f_ext / m (m/s^2) */
   double dt;                 /* time step h (s) > 0 */
-  /* IPC contact (Sec. 7, Eq. barrier). contact = 0 disables it; the other fields are
-   * then ignored. Pairs: surface vertex - boundary face, boundary edge - boundary edge
-   * (self-contact included) and surface vertex - wall plane n.x >= c. */
+  /* Contact (Sec. 7). contact = 1: the IPC log barrier kappa B(d) of Eq. barrier; 2: the
+   * implicit quadratic penalty kappa (dhat - d)^2 / 2 for d < dhat (the other contact form the
+   * paper's Table 1 uses); 0 disables contact and the other fields are then ignored. Pairs:
+   * surface vertex - boundary face, boundary edge - boundary edge (self-contact included) and
+   * surface vertex - wall plane n.x >= c; both forms keep the per-vertex step limit. */
   int32_t contact;
   int32_t n_planes;          /* walls */
   const double* planes;      /* [n_planes][4]: unit normal n (3) and offset c; may be NULL if 0 */
   double dhat;               /* barrier support d^ (m) > 0 */
-  double kappa;              /* barrier stiffness (N/m) > 0 */
+  double kappa;              /* barrier or penalty stiffness (N/m) > 0 */
 } jgs2_mesh_desc;
 
 typedef struct jgs2_mesh jgs2_mesh; /* opaque, library-owned */

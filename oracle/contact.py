@@ -2,7 +2,10 @@
 
 Barrier per primitive pair l (Eq. barrier): B(d) = -(d - dhat)^2 log(d / dhat) for
 0 < d < dhat, else 0; the energy adds kappa * sum_l B(d_l) (reading R11: kappa is a
-parameter, d the unsquared Euclidean distance). Pairs (reading R11): surface vertex -
+parameter, d the unsquared Euclidean distance). Sec. 7 admits any contact written as an
+unconstrained energy, and Table 1 uses an implicit penalty in most scenes; reading R23:
+the penalty form replaces B by P(d) = (dhat - d)^2 / 2 for d < dhat (C^1 at dhat, finite at
+d = 0), with the same pairs, per-vertex terms and step limit. Pairs (reading R11): surface vertex -
 boundary triangle not containing it (VF), boundary edges sharing no vertex (EE), and
 vertex - wall plane n.x >= c (VW). Self-contact is included.
 
@@ -49,6 +52,21 @@ def barrier_d2(d, dhat):
     e = d[m] - dhat
     out[m] = -2.0 * np.log(d[m] / dhat) - 4.0 * e / d[m] + e * e / (d[m] * d[m])
     return out
+
+
+def penalty(d, dhat):
+    d = np.asarray(d, dtype=np.float64)
+    return np.where(d < dhat, 0.5 * (dhat - d) ** 2, 0.0)
+
+
+def penalty_d1(d, dhat):
+    d = np.asarray(d, dtype=np.float64)
+    return np.where(d < dhat, d - dhat, 0.0)
+
+
+def penalty_d2(d, dhat):
+    d = np.asarray(d, dtype=np.float64)
+    return np.where(d < dhat, 1.0, 0.0)
 
 
 # ------------------------------------------------------------------ closest points
@@ -145,12 +163,15 @@ def surface(tets, X):
 
 
 class Contact:
-    def __init__(self, tets, X, planes, dhat, kappa, pinned=None):
+    def __init__(self, tets, X, planes, dhat, kappa, pinned=None, use_penalty=False):
         self.faces, self.edges, self.sverts = surface(tets, X)
         self.planes = np.asarray(planes, dtype=np.float64).reshape(-1, 4)
         self.dhat = float(dhat)
         self.kappa = float(kappa)
         self.pinned = None if pinned is None else np.asarray(pinned).astype(bool)
+        # per-pair energy and its d-derivatives: the IPC barrier or the penalty (R23)
+        self.e0, self.e1, self.e2 = (penalty, penalty_d1, penalty_d2) if use_penalty else \
+            (barrier, barrier_d1, barrier_d2)
 
     def canonical(self, pairs):
         """Rows (kind, a, b, c, d) in vertex ids: VW (0, v, plane, -1, -1), VF (1, v, face
@@ -228,7 +249,7 @@ class Contact:
         e = 0.0
         for pr in pairs:
             d, _ = self.pair_geometry(x, pr)
-            e += self.kappa * float(barrier(np.array([d]), self.dhat)[0])
+            e += self.kappa * float(self.e0(np.array([d]), self.dhat)[0])
         return e
 
     def vertex_terms(self, x, pairs, V):
@@ -239,8 +260,8 @@ class Contact:
             d, J = self.pair_geometry(x, pr)
             if not (0 < d < self.dhat):
                 continue
-            b1 = self.kappa * float(barrier_d1(np.array([d]), self.dhat)[0])
-            b2 = self.kappa * float(barrier_d2(np.array([d]), self.dhat)[0])
+            b1 = self.kappa * float(self.e1(np.array([d]), self.dhat)[0])
+            b2 = self.kappa * float(self.e2(np.array([d]), self.dhat)[0])
             for v, jv in J:
                 g[v] += b1 * jv
                 H[v] += b2 * np.outer(jv, jv)

@@ -134,9 +134,9 @@ class Mesh:
         self.contact = None   # oracle.contact.Contact when the IPC barrier is on (Sec. 7)
         self.rc = 0.0         # candidate radius of the step truncation
 
-    def enable_contact(self, planes, dhat, kappa, rc=None):
+    def enable_contact(self, planes, dhat, kappa, rc=None, use_penalty=False):
         from . import contact
-        self.contact = contact.Contact(self.tets, self.X, planes, dhat, kappa, self.pinned)
+        self.contact = contact.Contact(self.tets, self.X, planes, dhat, kappa, self.pinned, use_penalty)
         self.rc = 2.0 * dhat if rc is None else float(rc)
         return self
 

@@ -14,18 +14,24 @@
 
 namespace jgs2 {
 
-__device__ __forceinline__ double barrier_b(double d, double dh) {
+// Contact energy per pair and its derivatives in d: the IPC log barrier of Eq. barrier
+// (pen = 0), or the implicit quadratic penalty (pen = 1): (dh - d)^2 / 2 for d < dh, the
+// other form Sec. 7 admits (any contact written as an unconstrained energy).
+__device__ __forceinline__ double barrier_b(double d, double dh, int pen = 0) {
+  if (pen) return d >= dh ? 0.0 : 0.5 * (dh - d) * (dh - d);
   if (d <= 0.0) return INFINITY;
   if (d >= dh) return 0.0;
   const double e = d - dh;
   return -e * e * log(d / dh);
 }
-__device__ __forceinline__ double barrier_b1(double d, double dh) {
+__device__ __forceinline__ double barrier_b1(double d, double dh, int pen = 0) {
+  if (pen) return d >= dh ? 0.0 : d - dh;
   if (d <= 0.0 || d >= dh) return 0.0;
   const double e = d - dh;
   return -2.0 * e * log(d / dh) - e * e / d;
 }
-__device__ __forceinline__ double barrier_b2(double d, double dh) {
+__device__ __forceinline__ double barrier_b2(double d, double dh, int pen = 0) {
+  if (pen) return d >= dh ? 0.0 : 1.0;
   if (d <= 0.0 || d >= dh) return 0.0;
   const double e = d - dh;
   return -2.0 * log(d / dh) - 4.0 * e / d + e * e / (d * d);
@@ -682,7 +688,7 @@ __global__ void __launch_bounds__(256) k_pair_terms(DevMesh<T> m, ContactView c,
     for (int k = 0; k < nv; ++k)
       atomicMin(reinterpret_cast<unsigned long long*>(c.dmin + vs[k]), (unsigned long long)__double_as_longlong(d));
     if (d >= c.dhat) continue;
-    const double b1 = c.kappa * barrier_b1(d, c.dhat), b2 = c.kappa * barrier_b2(d, c.dhat);
+    const double b1 = c.kappa * barrier_b1(d, c.dhat, c.pen), b2 = c.kappa * barrier_b2(d, c.dhat, c.pen);
     const size_t V = m.V;
     for (int k = 0; k < nv; ++k) {
       const int v = vs[k];
@@ -708,7 +714,7 @@ __global__ void k_pair_energy(DevMesh<T> m, ContactView c, double* out) {
   const int n = min(*c.n_pairs, c.cap);
   double acc[1] = {0.0};
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
-    acc[0] += c.kappa * barrier_b(c.d0[q], c.dhat);
+    acc[0] += c.kappa * barrier_b(c.d0[q], c.dhat, c.pen);
   block_sum<1>(acc, red);
   if (threadIdx.x == 0) atomicAdd(out, acc[0]);
 }

@@ -264,10 +264,12 @@ jgs2_status mesh_create(const jgs2_mesh_desc* d, Mesh** out, const std::vector<i
   }
   // contact surface (Sec. 7): boundary faces (used by one tet) oriented outward, their
   // edges and vertices, in internal vertex ids
+  if (d->contact < 0 || d->contact > 2) return fail(JGS2_EINVAL, "contact must be 0, 1 (IPC) or 2 (penalty)");
   if (d->contact) {
     if (!(d->dhat > 0.0) || !(d->kappa > 0.0) || d->n_planes < 0 || (d->n_planes > 0 && !d->planes))
       return fail(JGS2_EINVAL, "contact needs dhat > 0, kappa > 0 and n_planes planes");
     m->contact = 1;
+    m->penalty = d->contact == 2 ? 1 : 0;
     m->dhat = d->dhat;
     m->kappa = d->kappa;
     m->rc = 2.0 * d->dhat;
@@ -572,6 +574,7 @@ static DevMesh<T> dev_view(Mesh* m) {
   if (m->contact) {
     ContactView& c = d.c;
     c.on = 1;
+    c.pen = m->penalty;
     c.n_planes = (int)m->planes.size() / 4;
     c.n_faces = (int)m->sfaces.size() / 3;
     c.n_edges = (int)m->sedges.size() / 2;

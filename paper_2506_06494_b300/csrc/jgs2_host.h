@@ -100,6 +100,7 @@ struct Mesh {
   std::vector<cudaEvent_t> gevents;
   // contact (Sec. 7): surface in internal vertex ids
   int contact = 0;
+  int penalty = 0;                            // 1: quadratic penalty instead of the IPC barrier
   double dhat = 0.0, kappa = 0.0, rc = 0.0;
   double bp_R = 0.0, bp_trig = 0.0;           // candidate-list radius and rebuild trigger
   int hbits = 0;                              // log2 buckets per hashed grid

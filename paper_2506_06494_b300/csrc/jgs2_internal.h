@@ -98,6 +98,7 @@ struct StepState {
 // Contact data of a mesh (Sec. 7); pairs: 0 vertex-wall, 1 vertex-face, 2 edge-edge.
 struct ContactView {
   int on = 0;
+  int pen = 0;                       // 0: IPC log barrier (Eq. barrier), 1: quadratic penalty
   int n_planes = 0, n_faces = 0, n_edges = 0, n_sverts = 0, n_vertices = 0;
   const double* planes = nullptr;    // [n_planes][4]
   const int32_t* faces = nullptr;    // [n_faces][3] internal vertex ids (outward)

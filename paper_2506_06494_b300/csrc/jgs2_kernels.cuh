@@ -1398,7 +1398,7 @@ __global__ void __launch_bounds__(128) k_pair_trials(DevMesh<T> m, const StepSta
           int vs[4], nv;
           P3 Jg[4];
           const double d = pair_geom(m, m.c, key, my_a, my_dir, vs, Jg, nv);
-          acc += m.c.kappa * (barrier_b(d, m.c.dhat) - barrier_b(dq, m.c.dhat));
+          acc += m.c.kappa * (barrier_b(d, m.c.dhat, m.c.pen) - barrier_b(dq, m.c.dhat, m.c.pen));
         }
       }
     }

@@ -98,6 +98,26 @@ def test_pinned_vertex_outside_every_tet_is_accepted(L):
     L.jgs2_mesh_destroy(h)
 
 
+def test_contact_form_is_validated(L):
+    """contact = 1 (IPC barrier) and 2 (penalty) are accepted; any other value is refused
+    before any device work."""
+    s = scenes.drop_scene()
+    X, T = np.ascontiguousarray(s.X), s.tets.astype(np.int32)   # kept alive for the call
+    E, nu, rho = s.youngs.copy(), s.poisson.copy(), s.density.copy()
+    planes = np.ascontiguousarray(s.planes, dtype=np.float64)
+    for form, want in ((1, 0), (2, 0), (3, 1), (-1, 1)):
+        d = _desc(X, T, E, nu, rho, None)
+        d.contact = form
+        d.n_planes = len(planes)
+        d.planes = planes.ctypes.data_as(C.POINTER(C.c_double))
+        d.dhat = s.dhat
+        d.kappa = s.kappa
+        h = C.c_void_p()
+        assert L.jgs2_mesh_create(C.byref(d), C.byref(h)) == want, form
+        if want == 0:
+            L.jgs2_mesh_destroy(h)
+
+
 def test_null_arguments(L):
     h = C.c_void_p()
     assert L.jgs2_mesh_create(None, C.byref(h)) == 1

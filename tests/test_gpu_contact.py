@@ -1,8 +1,11 @@
-"""GPU parity of the IPC contact path (Sec. 7) against the oracle's brute-force contact.
+"""GPU parity of the contact path (Sec. 7) against the oracle's brute-force contact: the IPC
+barrier (contact = 1) and the implicit quadratic penalty (contact = 2).
 
 Pair lists must match bit-exactly (canonical rows); energies, gradients and sweeps to the
-FP64 / FP32 tolerances of the sweep tests.
+FP64 / FP32 tolerances of the sweep tests (per vertex).
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -22,7 +25,7 @@ def t(a, dev):
 
 def omesh(s):
     m = fem.Mesh(s.X, s.tets, s.youngs, s.poisson, s.density, s.pinned)
-    return m.enable_contact(s.planes, s.dhat, s.kappa)
+    return m.enable_contact(s.planes, s.dhat, s.kappa, use_penalty=s.contact == 2)
 
 
 def near_contact_state(s, seed):
@@ -46,8 +49,9 @@ def test_pair_list_bit_exact(cuda, radius):
     assert kinds == {0, 1, 2} or radius < 2e-3
 
 
-def test_energy_gradient_with_contact(cuda):
-    s = scenes.stack_scene()
+@pytest.mark.parametrize("form", [1, 2])
+def test_energy_gradient_with_contact(cuda, form):
+    s = dataclasses.replace(scenes.stack_scene(), contact=form)
     m = omesh(s)
     x = near_contact_state(s, 2)
     assert len(m.contact.pairs(x, s.dhat)) > 0
@@ -62,8 +66,10 @@ def test_energy_gradient_with_contact(cuda):
 @pytest.mark.parametrize("prec", [p.FP64, p.FP32])
 @pytest.mark.parametrize("corr", [p.CORR_ASM, p.CORR_OFF])
 @pytest.mark.parametrize("name", ["drop", "stack"])
-def test_sweeps_with_contact(cuda, prec, corr, name):
+@pytest.mark.parametrize("form", [1, 2])
+def test_sweeps_with_contact(cuda, prec, corr, name, form):
     s = scenes.drop_scene(nv=3) if name == "drop" else scenes.stack_scene()
+    s = dataclasses.replace(s, contact=form)
     m = omesh(s)
     x = near_contact_state(s, 3)
     elem, w, u = scenes.random_cubature(s.X, s.tets, s.pinned, 4, seed=4, w_max=0.3, u_sigma=0.1)
@@ -79,8 +85,9 @@ def test_sweeps_with_contact(cuda, prec, corr, name):
     assert err <= TOL[prec], err
 
 
-def test_step_with_contact_fp64_matches_oracle(cuda):
-    s = scenes.drop_scene(nv=3)
+@pytest.mark.parametrize("form", [1, 2])
+def test_step_with_contact_fp64_matches_oracle(cuda, form):
+    s = dataclasses.replace(scenes.drop_scene(nv=3), contact=form)
     m = omesh(s)
     g = p.Mesh.from_scene(s)
     x = t(s.X, cuda)

@@ -406,9 +406,43 @@ def test_contact_gradient_fd_and_surface():
         assert np.linalg.eigvalsh(H[v]).min() > -1e-9
 
 
+def test_penalty_closed_form():
+    """Reading R23: P(d) = (dhat - d)^2 / 2 below dhat, zero above; C^1 at dhat (value and
+    slope vanish there), P' = d - dhat and P'' = 1 inside, finite at d = 0; central
+    differences of P and P' match P' and P''."""
+    dh = 1e-3
+    assert ct.penalty(np.array([dh, 2 * dh]), dh).tolist() == [0.0, 0.0]
+    assert ct.penalty_d1(np.array([dh]), dh)[0] == 0.0
+    assert abs(ct.penalty(np.array([0.0]), dh)[0] - 0.5 * dh * dh) < 1e-20
+    for x in [1e-5, 2e-4, 7e-4]:
+        h = 1e-9
+        fd1 = (ct.penalty(np.array([x + h]), dh)[0] - ct.penalty(np.array([x - h]), dh)[0]) / (2 * h)
+        fd2 = (ct.penalty_d1(np.array([x + h]), dh)[0] - ct.penalty_d1(np.array([x - h]), dh)[0]) / (2 * h)
+        assert abs(fd1 - ct.penalty_d1(np.array([x]), dh)[0]) < 1e-6 * abs(fd1)
+        assert abs(fd2 - 1.0) < 1e-6 and ct.penalty_d2(np.array([x]), dh)[0] == 1.0
+
+
+def test_penalty_contact_gradient_fd():
+    X, tets = scenes.kuhn_grid(3, 3, 3, (0.02, 0.02, 0.02))
+    Xa = np.vstack([X, X + [0.0, 0.0, 0.0205]])
+    ta = np.vstack([tets, tets + len(X)])
+    con = ct.Contact(ta, Xa, scenes.box_planes()[:1], 1e-3, 1e4, use_penalty=True)
+    x = Xa + np.random.default_rng(3).normal(0, 1e-4, Xa.shape)
+    x[:, 2] += 5e-4
+    pairs = con.pairs(x, 1e-3)
+    g, H = con.vertex_terms(x, pairs, len(x))
+    for v in np.nonzero(np.abs(g).sum(1))[0][:6]:
+        for k in range(3):
+            e = np.zeros_like(x)
+            e[v, k] = 1e-9
+            fd = (con.energy(x + e, con.pairs(x + e, 1e-3)) - con.energy(x - e, con.pairs(x - e, 1e-3))) / 2e-9
+            assert abs(fd - g[v, k]) <= 1e-5 * abs(g[v]).max() + 1e-12
+        assert np.linalg.eigvalsh(H[v]).min() > -1e-12
+
+
 def _contact_mesh(s):
     m = fem.Mesh(s.X, s.tets, s.youngs, s.poisson, s.density, s.pinned)
-    return m.enable_contact(s.planes, s.dhat, s.kappa)
+    return m.enable_contact(s.planes, s.dhat, s.kappa, use_penalty=s.contact == 2)
 
 
 def test_contact_step_stays_intersection_free():
