@@ -421,7 +421,8 @@ def run_jgs2(args, rank, world, local_rank):
     # (last) sweep of a chunk must fall inside the step
     chunk = max(1, min(16, args.max_sweeps + 1))
     opts = p.step_opts(precision=prec, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4, profile=1,
-                       check_every=chunk, persistent=int(args.persistent and batch))
+                       check_every=chunk, persistent=int(args.persistent and batch),
+                       contact_coupling=int(args.coupling))
     x0 = torch.tensor(X, dtype=torch.float64, device=dev)
     v0 = torch.tensor(V0, dtype=torch.float64, device=dev)
     mesh.autotune(x0, v0, opts)
@@ -461,7 +462,8 @@ def run_jgs2(args, rank, world, local_rank):
     # end to end: host buffers through jgs2_step_host, copies inside the timed region
     xh, vh = X.copy(), V0.copy()
     opts_e2e = p.step_opts(precision=prec, correction=corr, max_sweeps=args.max_sweeps, rel_tol=1e-4,
-                           check_every=chunk, persistent=int(args.persistent and batch))
+                           check_every=chunk, persistent=int(args.persistent and batch),
+                           contact_coupling=int(args.coupling))
     torch.cuda.synchronize()
     # (the host-array entry point runs Jacobi steps; the Gauss-Seidel form has no e2e leg)
     n_e2e = 0 if (args.no_e2e or gs) else args.steps
@@ -484,6 +486,7 @@ def run_jgs2(args, rank, world, local_rank):
                    "contact": bool(args.contact) if args.workload == "spheres" else False,
                    "correction": args.correction, "line_search": True, "n_cub": args.n_cub, "rel_tol": 1e-4,
                    "parallelisation": "Gauss-Seidel (greedy colouring, group subspaces)" if gs else "Jacobi",
+                   "contact_coupling": bool(args.coupling),
                    "max_sweeps": args.max_sweeps, "block_size": bs,
                    "batch_launch": ("persistent cooperative launch per chunk" if args.persistent else
                                     "one launch per kernel, graph-captured chunks") if batch else None,
@@ -740,6 +743,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-paper-criterion", action="store_true")
+    ap.add_argument("--coupling", type=int, default=0,
+                    help="1: contact-aware correction (Sec. 7 two-way coupling across bodies in contact)")
     ap.add_argument("--gs", type=int, default=0,
                     help="1: Gauss-Seidel steps (greedy colouring, group precompute) on a single scene without contact")
     ap.add_argument("--persistent", type=int, default=1,

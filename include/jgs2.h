@@ -134,7 +134,13 @@ typedef struct {
                               * grid barrier wait for one block more than the grid has, so the wait
                               * runs out after wait_polls polls and the step returns JGS2_ETIMEOUT
                               * with the state not written */
-  int32_t pad_;
+  int32_t contact_coupling;  /* 1 = contact-aware correction (Sec. 7): a vertex with active contact
+                              * pairs reaching another body solves its local system as if the
+                              * colliding free vertices of that body moved with it (their elastic
+                              * and inertial gradient and diagonal block added; each of its pairs'
+                              * terms taken along the co-moving set, so a pair that moves rigidly
+                              * drops out). Needs contact and the correction on; 0 = off (default).
+                              * JGS2_ENOMEM if a vertex has more than 16 such pairs */
 } jgs2_step_opts;
 
 #define JGS2_TRACE_MAX 4096

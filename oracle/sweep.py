@@ -98,9 +98,57 @@ def correction_terms(mesh: fem.Mesh, x, g, h, cub, R, psd=False, grad="asm", z=N
     return Ht, gt
 
 
-def direction(mesh: fem.Mesh, x, z, h, cub=None, psd=False, grad="asm", stats=None):
+def coupled_local_terms(mesh: fem.Mesh, x, g, Hd):
+    """Contact-aware local terms (Sec. 7; reading R24): a vertex i in contact with another
+    body moves, in its sub-problem, together with the colliding vertices of that body (the
+    same perturbation as i). With P(i) the vertices on other bodies that share an active pair
+    (d < dhat) with i, free, and S_i = {i} + P(i):
+      g_i' = g_i^e + sum_{b in P(i)} g_b^e + sum_{pairs l of i} kappa B'(d_l) J_S,l
+      H_i' = H_ii^e + sum_{b in P(i)} H_bb^e + sum_{pairs l of i} kappa B''(d_l) J_S,l J_S,l^T
+    where ^e drops the contact terms (elastic and inertial parts only) and J_S,l is the sum of
+    the pair's distance gradients over its vertices in S_i (zero for a vertex-face pair whose
+    face lies on the other body: the pair moves rigidly in the sub-problem). The partners'
+    other pairs and the elastic coupling between partners are left out. Returns {i: (g_i',
+    H_i')} for the vertices with a cross-body pair; the others keep (g_i, H_ii)."""
+    con = mesh.contact
+    act = con.pairs(x, con.dhat)
+    gb, Hb = con.vertex_terms(x, act, mesh.V)
+    ge, He = g - gb, Hd - Hb
+    body = mesh.body_of_vertex
+    geo = {}
+    by_vertex = {}
+    for pr in act:
+        d, J = con.pair_geometry(x, pr)
+        geo[pr[:3]] = (d, J)
+        for v, _ in J:
+            by_vertex.setdefault(v, []).append(pr[:3])
+    out = {}
+    for i in mesh.free:
+        prs = by_vertex.get(int(i), [])
+        P = sorted({v for key in prs for v, _ in geo[key][1]
+                    if body[v] != body[i] and not mesh.pinned[v]})
+        if not P:
+            continue
+        S = set(P) | {int(i)}
+        gi, Hi = ge[i].copy(), He[i].copy()
+        for key in prs:
+            d, J = geo[key]
+            JS = sum((jv for v, jv in J if v in S), np.zeros(3))
+            b1 = con.kappa * float(con.e1(np.array([d]), con.dhat)[0])
+            b2 = con.kappa * float(con.e2(np.array([d]), con.dhat)[0])
+            gi += b1 * JS
+            Hi += b2 * np.outer(JS, JS)
+        for b in P:
+            gi += ge[b]
+            Hi += He[b]
+        out[int(i)] = (gi, Hi)
+    return out
+
+
+def direction(mesh: fem.Mesh, x, z, h, cub=None, psd=False, grad="asm", stats=None, coupled=False):
     """JGS2 direction D (x^{k+1} = x^k + D without line search), the uncorrected per-vertex
-    Newton direction D_J = -H_ii^{-1} g_i, and the gradient at x^k. cub=None: D = D_J."""
+    Newton direction D_J = -H_ii^{-1} g_i, and the gradient at x^k. cub=None: D = D_J.
+    coupled: with contact on, D takes the contact-aware local terms of coupled_local_terms."""
     g = fem.vertex_gradient(mesh, x, z, h)
     Hd = fem.vertex_diag_blocks(mesh, x, h)
     if cub is not None:
@@ -109,14 +157,16 @@ def direction(mesh: fem.Mesh, x, z, h, cub=None, psd=False, grad="asm", stats=No
     else:
         Ht = np.zeros_like(Hd)
         gt = np.zeros_like(g)
+    cpl = coupled_local_terms(mesh, x, g, Hd) if (coupled and mesh.contact is not None) else {}
     D = np.zeros_like(x)
     DJ = np.zeros_like(x)
     for i in mesh.free:
         LJ = np.linalg.cholesky(Hd[i])
         DJ[i] = np.linalg.solve(LJ.T, np.linalg.solve(LJ, -g[i]))
+        gi, Hi = cpl.get(int(i), (g[i], Hd[i]))
         try:
-            L = np.linalg.cholesky(Hd[i] + Ht[i])
-            D[i] = np.linalg.solve(L.T, np.linalg.solve(L, -(g[i] + gt[i])))
+            L = np.linalg.cholesky(Hi + Ht[i])
+            D[i] = np.linalg.solve(L.T, np.linalg.solve(L, -(gi + gt[i])))
         except np.linalg.LinAlgError:
             D[i] = DJ[i]
             if stats is not None:
@@ -182,17 +232,19 @@ def residual_norm(mesh, x, z, h):
     return float(np.linalg.norm(fem.vertex_gradient(mesh, x, z, h)[mesh.free]))
 
 
-def run_sweeps(mesh: fem.Mesh, x, z, h, cub=None, n=1, psd=False, grad="asm", line_search_on=True):
+def run_sweeps(mesh: fem.Mesh, x, z, h, cub=None, n=1, psd=False, grad="asm", line_search_on=True,
+               coupled=False):
     """Exactly n sweeps from x (no convergence test)."""
     x = np.array(x, dtype=np.float64, copy=True)
     for _ in range(n):
-        D, DJ, g = direction(mesh, x, z, h, cub, psd, grad)
+        D, DJ, g = direction(mesh, x, z, h, cub, psd, grad, coupled=coupled)
         x = x + (line_search(mesh, x, z, h, D, DJ, g) if line_search_on else D)
     return x
 
 
 def step(mesh: fem.Mesh, x_t, v_t, h, gravity, cub=None, rel_tol=1e-4, max_sweeps=100,
-         psd=False, grad="asm", line_search_on=True, record_x=False, dx_tol=0.0, length_scale=0.0):
+         psd=False, grad="asm", line_search_on=True, record_x=False, dx_tol=0.0, length_scale=0.0,
+         coupled=False):
     """One implicit-Euler step (Sec. 3) solved by JGS2 sweeps from x^0 = x_t (reading R8).
 
     Sweep k computes g(x^k); r_k = |g(x^k)|/|g(x^0)|; the step stops at the first k with
@@ -210,7 +262,7 @@ def step(mesh: fem.Mesh, x_t, v_t, h, gravity, cub=None, rel_tol=1e-4, max_sweep
     stop_dx = False
     dx_last = None
     while True:
-        D, DJ, g = direction(mesh, x, z, h, cub, psd, grad, stats)
+        D, DJ, g = direction(mesh, x, z, h, cub, psd, grad, stats, coupled)
         gn = float(np.linalg.norm(g[mesh.free]))
         if g0 is None:
             g0 = gn

@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(256) k_bp_check(DevMesh<T> m, ContactView c, S
 #pragma unroll
     for (int k = 0; k < 6; ++k) c.bH[(size_t)k * V + v] = 0.0;
     c.dmin[v] = INFINITY;
+    if (c.vp_cnt) c.vp_cnt[v] = 0;
     const P3 p = vpos(m, v);
     const float4 b = c.pbp[v];
     const double dx = p.x - double(b.x), dy = p.y - double(b.y), dz = p.z - double(b.z);
@@ -688,6 +689,19 @@ __global__ void __launch_bounds__(256) k_pair_terms(DevMesh<T> m, ContactView c,
     for (int k = 0; k < nv; ++k)
       atomicMin(reinterpret_cast<unsigned long long*>(c.dmin + vs[k]), (unsigned long long)__double_as_longlong(d));
     if (d >= c.dhat) continue;
+    if (c.vp_cnt) {
+      // an active pair that reaches another body: listed at each of its vertices
+      bool cross = false;
+      for (int k = 1; k < nv; ++k) cross |= c.body[vs[k]] != c.body[vs[0]];
+      if (cross)
+        for (int k = 0; k < nv; ++k) {
+          const int slot = atomicAdd(c.vp_cnt + vs[k], 1);
+          if (slot < kMaxVertexPairs)
+            c.vp[(size_t)vs[k] * kMaxVertexPairs + slot] = q;
+          else
+            c.flags[2] = 1;
+        }
+    }
     const double b1 = c.kappa * barrier_b1(d, c.dhat, c.pen), b2 = c.kappa * barrier_b2(d, c.dhat, c.pen);
     const size_t V = m.V;
     for (int k = 0; k < nv; ++k) {
@@ -705,6 +719,87 @@ __global__ void __launch_bounds__(256) k_pair_terms(DevMesh<T> m, ContactView c,
       atomicAdd(c.bH + 5 * V + v, b2 * j.z * j.z);
     }
   }
+}
+
+// Contact-aware local terms (Sec. 7, reading R24), thread per free vertex after the gather:
+// a vertex with active pairs reaching other bodies moves, in its sub-problem, together with
+// those bodies' free colliding vertices P(i). With S_i = {i} + P(i):
+//   g' = g_i - sum_l kappa B'(d_l) J_i,l + sum_l kappa B'(d_l) J_S,l + sum_{b in P} (g_b - bg_b)
+//   H' = H_ii - sum_l kappa B'' J_i J_i^T + sum_l kappa B'' J_S J_S^T + sum_{b in P} (H_bb - bH_b)
+// over the vertex's listed pairs l (J_S,l: the pair's distance gradients summed over its
+// vertices in S_i), written to cpl for k_correct's local system. Pairs are taken in
+// ascending order, so the sums do not depend on the order the lists were filled.
+template <typename T>
+__global__ void __launch_bounds__(128) k_couple(DevMesh<T> m, ContactView c, const StepState* __restrict__ st) {
+  if (st->done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.Vf) return;
+  const int n = c.vp_cnt[i] < kMaxVertexPairs ? c.vp_cnt[i] : kMaxVertexPairs;
+  m.cpl_on[i] = n > 0 ? 1 : 0;
+  if (n == 0) return;
+  int lst[kMaxVertexPairs];
+  for (int k = 0; k < n; ++k) lst[k] = c.vp[(size_t)i * kMaxVertexPairs + k];
+  for (int a = 1; a < n; ++a) {  // insertion sort (at most kMaxVertexPairs entries)
+    const int v = lst[a];
+    int b = a - 1;
+    while (b >= 0 && lst[b] > v) {
+      lst[b + 1] = lst[b];
+      --b;
+    }
+    lst[b + 1] = v;
+  }
+  const int bi = c.body[i];
+  const size_t S = m.Vf, V = m.V;
+  double g[3], H[6];
+  for (int q = 0; q < 3; ++q) g[q] = double(m.ghr[q * S + i]);
+  for (int q = 0; q < 6; ++q) H[q] = double(m.ghr[(3 + q) * S + i]);
+  int part[4 * kMaxVertexPairs];
+  int np = 0;
+  for (int k = 0; k < n; ++k) {
+    int vs[4], nv;
+    P3 J[4];
+    const double d = pair_geom(m, c, c.pairs[lst[k]], 0.0, (const Vec4<T>*)nullptr, vs, J, nv);
+    const double b1 = c.kappa * barrier_b1(d, c.dhat, c.pen), b2 = c.kappa * barrier_b2(d, c.dhat, c.pen);
+    P3 Ji{0, 0, 0}, JS{0, 0, 0};
+    for (int q = 0; q < nv; ++q) {
+      const int v = vs[q];
+      if (v == i) {
+        Ji = add(Ji, J[q]);
+        JS = add(JS, J[q]);
+      } else if (c.body[v] != bi && v < m.Vf) {
+        JS = add(JS, J[q]);
+        bool seen = false;
+        for (int r = 0; r < np; ++r) seen |= part[r] == v;
+        if (!seen) part[np++] = v;
+      }
+    }
+    g[0] += b1 * (JS.x - Ji.x);
+    g[1] += b1 * (JS.y - Ji.y);
+    g[2] += b1 * (JS.z - Ji.z);
+    H[0] += b2 * (JS.x * JS.x - Ji.x * Ji.x);
+    H[1] += b2 * (JS.x * JS.y - Ji.x * Ji.y);
+    H[2] += b2 * (JS.x * JS.z - Ji.x * Ji.z);
+    H[3] += b2 * (JS.y * JS.y - Ji.y * Ji.y);
+    H[4] += b2 * (JS.y * JS.z - Ji.y * Ji.z);
+    H[5] += b2 * (JS.z * JS.z - Ji.z * Ji.z);
+  }
+  // partners in ascending order: a fixed summation order
+  for (int a = 1; a < np; ++a) {
+    const int v = part[a];
+    int b = a - 1;
+    while (b >= 0 && part[b] > v) {
+      part[b + 1] = part[b];
+      --b;
+    }
+    part[b + 1] = v;
+  }
+  for (int r = 0; r < np; ++r) {
+    const int b = part[r];
+    for (int q = 0; q < 3; ++q) g[q] += double(m.ghr[q * S + b]) - c.bg[q * V + b];
+    for (int q = 0; q < 6; ++q) H[q] += double(m.ghr[(3 + q) * S + b]) - c.bH[q * V + b];
+  }
+  for (int q = 0; q < 3; ++q) m.cpl[q * S + i] = T(g[q]);
+  for (int q = 0; q < 6; ++q) m.cpl[(3 + q) * S + i] = T(H[q]);
 }
 
 // barrier energy of the pairs at x^k (for jgs2_energy_gradient)

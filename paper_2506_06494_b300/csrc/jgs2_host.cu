@@ -49,6 +49,7 @@ template <typename T>
 void PrecBufs<T>::release() {
   cudaFree(tets); cudaFree(frec); cudaFree(bc); cudaFree(u); cudaFree(dz); cudaFree(D); cudaFree(DJ); cudaFree(ghr); cudaFree(mh2);
   cudaFree(cub_p); cudaFree(cub_w); cudaFree(cub_u); cudaFree(pool_H); cudaFree(pool_G); cudaFree(pool_R);
+  cudaFree(cpl);
   cudaFree(a_lam); cudaFree(a_r); cudaFree(a_z); cudaFree(a_p); cudaFree(a_q); cudaFree(a_lin);
   *this = PrecBufs<T>();
 }
@@ -76,7 +77,7 @@ Mesh::~Mesh() {
   cudaFree(d_gbar);
   cudaFree(d_planes); cudaFree(d_d0); cudaFree(d_bg); cudaFree(d_bH); cudaFree(d_faces); cudaFree(d_edges);
   cudaFree(d_sverts); cudaFree(d_npairs); cudaFree(d_cflags); cudaFree(d_is_surf); cudaFree(d_pairs);
-  cudaFree(d_dmin); cudaFree(d_lim); cudaFree(d_frank); cudaFree(d_erank); cudaFree(d_hcnt); cudaFree(d_hblk);
+  cudaFree(d_dmin); cudaFree(d_lim); cudaFree(d_body); cudaFree(d_vp_cnt); cudaFree(d_vp); cudaFree(d_cpl_on); cudaFree(d_frank); cudaFree(d_erank); cudaFree(d_hcnt); cudaFree(d_hblk);
   cudaFree(d_hids); cudaFree(d_hrec); cudaFree(d_hkey); cudaFree(d_fkeys); cudaFree(d_ekeys); cudaFree(d_pbp); cudaFree(d_dbp); cudaFree(d_ctl);
   cudaFree(d_pmarg); cudaFree(d_ppath);
   cudaFree(d_gsmask); cudaFree(d_vmask); cudaFree(d_gs_xt); cudaFree(d_gs_xk); cudaFree(d_gs_g);
@@ -410,7 +411,7 @@ static jgs2_status ensure_device(Mesh* m) {
       CK(dalloc(&m->d_pairs, m->pair_cap));
       CK(dalloc(&m->d_d0, m->pair_cap));
       CK(dalloc(&m->d_npairs, 1));
-      CK(dalloc(&m->d_cflags, 2));
+      CK(dalloc(&m->d_cflags, 3));
       CK(dalloc(&m->d_bg, 3 * (size_t)V));
       CK(dalloc(&m->d_bH, 6 * (size_t)V));
       CK(dalloc(&m->d_dmin, V));
@@ -420,7 +421,18 @@ static jgs2_status ensure_device(Mesh* m) {
       if (nE) CK(cudaMemcpy(m->d_edges, m->sedges.data(), sizeof(int) * 2 * nE, cudaMemcpyHostToDevice));
       if (nS) CK(cudaMemcpy(m->d_sverts, m->sverts.data(), sizeof(int) * nS, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(m->d_is_surf, m->is_surf.data(), V, cudaMemcpyHostToDevice));
-      CK(cudaMemset(m->d_cflags, 0, 2 * sizeof(int32_t)));
+      CK(cudaMemset(m->d_cflags, 0, 3 * sizeof(int32_t)));
+      {
+        // contact-aware coupling: body id per vertex (internal order), per-vertex pair lists
+        std::vector<int> bod(V);
+        for (int v = 0; v < V; ++v) bod[v] = m->body[m->perm[v]];
+        CK(dalloc(&m->d_body, V));
+        CK(cudaMemcpy(m->d_body, bod.data(), sizeof(int) * V, cudaMemcpyHostToDevice));
+        CK(dalloc(&m->d_vp_cnt, V));
+        CK(cudaMemset(m->d_vp_cnt, 0, sizeof(int32_t) * V));
+        CK(dalloc(&m->d_vp, (size_t)V * kMaxVertexPairs));
+        CK(dalloc(&m->d_cpl_on, std::max(1, m->Vf)));
+      }
       // accumulators of non-surface vertices are never written: zero them once
       CK(cudaMemset(m->d_bg, 0, sizeof(double) * 3 * (size_t)V));
       CK(cudaMemset(m->d_bH, 0, sizeof(double) * 6 * (size_t)V));
@@ -614,6 +626,9 @@ static DevMesh<T> dev_view(Mesh* m) {
     c.dmin = m->d_dmin;
     c.lim = m->d_lim;
     c.flags = m->d_cflags;
+    c.body = m->d_body;
+    c.vp_cnt = m->d_vp_cnt;
+    c.vp = m->d_vp;
   }
   d.n_scenes = m->n_scenes;
   d.v_scene = m->d_vscene;
@@ -921,6 +936,14 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
                               bool check, StepState* hs, Launches& L, int gs_ncol = 0) {
   DevMesh<T> d = dev_view<T>(m);
   const bool corr = o.correction != JGS2_CORR_OFF;
+  // contact-aware local terms (Sec. 7): only with contact and the correction on
+  const bool coupling = o.contact_coupling && m->contact && corr;
+  if (coupling) {
+    PrecBufs<T>& b = bufs<T>(m);
+    if (!b.cpl) CK(dalloc(&b.cpl, 9 * (size_t)std::max(1, m->Vf)));
+    d.cpl = b.cpl;
+    d.cpl_on = m->d_cpl_on;
+  }
   const int nbV = (m->Vf + 127) / 128;
   const int nbT = (m->T + 127) / 128;
   // line-search pass: grid-stride over tets and vertices, about 4 tets per thread
@@ -1024,6 +1047,8 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
               [&] {
                 launch_gather<T, false>(d, m, corr, gbs, gtpv, s, m->d_state, m->d_partial, m->d_trace, o.record_trace);
               });
+      if (coupling)
+        group(JGS2_K_CONTACT, 1, s, [&] { k_couple<T><<<nbV, 128, 0, s>>>(d, d.c, m->d_state); });
       // cubature pool after the gather, whose g and R at the pool elements' corners it reads
       if (pool)
         group(JGS2_K_POOL, 1, s, [&] {
@@ -1103,13 +1128,18 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
   CK(cudaEventRecord(m->gev[1], s));
   CK(cudaStreamWaitEvent(cs, m->gev[1], 0));
   if (m->contact) {
-    int32_t fl[2];
+    int32_t fl[3];
     CK(cudaMemcpy(fl, m->d_cflags, sizeof(fl), cudaMemcpyDeviceToHost));
     if (fl[0]) {
       CK(cudaMemset(m->d_cflags, 0, sizeof(fl)));
       return fail(JGS2_ENOMEM, "contact pair buffer overflow (" + std::to_string(m->pair_cap) + " pairs)");
     }
-    if (fl[1]) CK(cudaMemset(m->d_cflags, 0, sizeof(fl)));
+    if (fl[2] && coupling) {
+      CK(cudaMemset(m->d_cflags, 0, sizeof(fl)));
+      return fail(JGS2_ENOMEM, "a vertex has more than " + std::to_string(kMaxVertexPairs) +
+                                   " active pairs reaching other bodies (contact-aware coupling)");
+    }
+    if (fl[1] || fl[2]) CK(cudaMemset(m->d_cflags, 0, sizeof(fl)));
   }
   return JGS2_OK;
 }
@@ -2020,7 +2050,7 @@ void jgs2_step_opts_default(jgs2_step_opts* o) {
   o->persistent = 0;
   o->wait_polls = 0;
   o->test_unreachable_barrier = 0;
-  o->pad_ = 0;
+  o->contact_coupling = 0;
 }
 
 jgs2_status jgs2_mesh_create(const jgs2_mesh_desc* desc, jgs2_mesh** out) {

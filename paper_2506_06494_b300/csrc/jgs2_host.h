@@ -28,6 +28,7 @@ struct PrecBufs {
   T* pool_H = nullptr;
   T* pool_G = nullptr;
   T* pool_R = nullptr;
+  T* cpl = nullptr;  // [9][Vf] contact-aware local terms (allocated when first used)
   // adjoint workspace
   Vec4<T>*a_lam = nullptr, *a_r = nullptr, *a_z = nullptr, *a_p = nullptr, *a_q = nullptr;
   T* a_lin = nullptr;
@@ -125,6 +126,8 @@ struct Mesh {
   double *d_gs_xt = nullptr, *d_gs_xk = nullptr, *d_gs_g = nullptr;
   uint32_t* d_ctl = nullptr;
   double *d_dmin = nullptr, *d_lim = nullptr;
+  int32_t *d_body = nullptr, *d_vp_cnt = nullptr, *d_vp = nullptr;  // contact-aware coupling
+  uint8_t* d_cpl_on = nullptr;
   PrecBufs<float> f32;
   PrecBufs<double> f64;
   ~Mesh();

@@ -5,8 +5,8 @@
 //   TetRec<T>   one 16-byte aligned record per tet, tets sorted by smallest corner:
 //               corner ids, D_m^{-1} (B), F(x_t) (per step), V_e, mu, lam' = lam + mu,
 //               rho V_e / 4 (the element's share of each corner's lumped mass).
-//   FRec<T>     per tet, rewritten every sweep by the element pass: F_e(x^k), V_e, mu, lam'.
-//   bc          per tet and corner, the corner vector b_a (Vec4, one 16-byte load).
+//   FRec<T>     per tet, rewritten every sweep by the element pass: F_e(x^k), J - 1, mu, lam'.
+//   bc          per tet and corner, the corner vector b_a and V_e (Vec4, one 16-byte load).
 //   Vec4<T>     per-vertex displacement u = x - x_t (the sweep works in displacement so
 //               that FP32 keeps the precision of small per-step motions), the inertia
 //               offset dz = z - x_t = h v_t + h^2 g, and the sweep direction D.
@@ -29,6 +29,7 @@ constexpr int kMaxCub = 8;       // cubature slots per vertex at most
 constexpr int kLsTrials = 8;     // line-search steps alpha = 2^-j, j < kLsTrials
 constexpr int kPairTrialBlocks = 148 * 4;  // blocks of the line-search barrier-trial pass (2 x kLsTrials sums each)
 constexpr int kEnergyBlocksMax = 148 * 8;  // blocks of the line-search energy pass, at most
+constexpr int kMaxVertexPairs = 16;  // active cross-body pairs listed per vertex at most
 constexpr int kPoolH = 90;       // 12x12 symmetric as ten 3x3 corner blocks (a <= c)
 // Row stride of the per-slot cubature record arrays: Vf rounded up to 4 entries, so that
 // every row starts on a 16-byte boundary.
@@ -41,6 +42,7 @@ struct alignas(16) TetRec {
   T B[9];      // B = D_m^{-1}, row-major; corner k>0 uses row k-1, corner 0 minus the sum
   T Ft[9];     // F(x_t), row-major (i, j) -> 3i + j
   T vol, mu, lp, mq;
+  T jt1;       // det F(x_t) - 1, formed in FP64 per step (J - 1 without cancellation)
 };
 
 template <typename T>
@@ -48,12 +50,13 @@ struct alignas(16) Vec4 {
   T x, y, z, w;
 };
 
-// Per-sweep element record written by the element pass: F_e(x^k) and the element's
-// constants, read by the vertex gather (48 bytes in FP32: three 16-byte loads).
+// Per-sweep element record written by the element pass: F_e(x^k), J - 1 (formed without
+// cancellation) and the element's Lame constants, read by the vertex gather (48 bytes in
+// FP32: three 16-byte loads). The element volume rides in the corner vectors' fourth entry.
 template <typename T>
 struct alignas(16) FRec {
   T F[9];
-  T vol, mu, lp;
+  T jm1, mu, lp;
 };
 
 // Device-resident step state (one per mesh), read and written by the sweep kernels.
@@ -135,7 +138,12 @@ struct ContactView {
   double* bH = nullptr;          // [6][V]
   double* dmin = nullptr;        // [V] smallest distance of a pair within r_c (atomicMin on the bits)
   double* lim = nullptr;         // [Vf] step limit 0.45 min(rc - dhat, dmin)
-  int32_t* flags = nullptr;      // [0] overflow, [1] intersection
+  int32_t* flags = nullptr;      // [0] overflow, [1] intersection, [2] pair-list overflow
+  // contact-aware coupling (Sec. 7): per vertex, its active (d < dhat) pairs that reach
+  // another body (vp_cnt, vp [V][kMaxVertexPairs]); body id per vertex
+  const int32_t* body = nullptr;  // [V]
+  int32_t* vp_cnt = nullptr;      // [V]
+  int32_t* vp = nullptr;          // [V][kMaxVertexPairs]
 };
 
 // Per-scene state of a batch mesh (one slot per scene; a single mesh is not batched).
@@ -155,7 +163,7 @@ struct DevMesh {
   const TetRec<T>* tets;
   TetRec<T>* tets_mut;
   FRec<T>* frec;            // [T] F_e(x^k) of the current sweep (element pass)
-  Vec4<T>* bc;              // [T][4] corner vectors b_a = rows of D_m^{-1}, b_0 = -(b_1+b_2+b_3)
+  Vec4<T>* bc;              // [T][4] corner vectors b_a = rows of D_m^{-1}, b_0 = -(b_1+b_2+b_3); w = V_e
   const int32_t* inc_off;   // [n_slices + 1]
   const int32_t* inc_len;   // [Vf]
   const int32_t* inc;       // entries
@@ -165,6 +173,9 @@ struct DevMesh {
   Vec4<T>* DJ;              // [Vf] uncorrected direction -H_ii^{-1} g_i
   const uint8_t* vmask;     // [Vf] or null: vertices that move in this sweep (a Gauss-Seidel
                             // colour); the others get D = D_J = 0
+  T* cpl;                   // [9][Vf] or null: contact-aware local terms g' (3), H' (6) that
+                            // replace g_i, H_ii in the corrected local system where cpl_on
+  uint8_t* cpl_on;          // [Vf]
   T* ghr;                   // [18][Vf] g_i, H_ii (6), R_i (9) between the two sweep phases
   const T* mh2;             // [V] m_v / h^2 (0 for pinned)
   int cs;                   // row stride of the cubature records: Vf rounded up to 4

@@ -292,6 +292,45 @@ __device__ __forceinline__ void tet_F(const TetRec<T>& r, const Vec4<T>* u, T (&
   }
 }
 
+template <typename T>
+__device__ __forceinline__ void cofactor(const T (&F)[9], T (&C)[9]);
+
+// F_e(x) = F(x_t) + G with G = [u_1 - u_0, u_2 - u_0, u_3 - u_0] B, and J - 1 without the
+// cancellation of det F - 1 near rest (which costs FP32 most of its digits where the
+// volumetric stiffness lam' is large): for 3x3 matrices
+//   det(F_t + G) - 1 = (det F_t - 1) + cof(F_t):G + F_t:cof(G) + det G,
+// with det F_t - 1 formed in FP64 at step setup and every other term small.
+template <typename T>
+__device__ __forceinline__ void tet_F_jm1(const TetRec<T>& r, const Vec4<T>* u, T (&F)[9], T& jm1) {
+  T u0[3], uk[3], G[9];
+  load3(u, r.v[0], u0);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) G[q] = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    load3(u, r.v[k + 1], uk);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const T d = uk[i] - u0[i];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) G[3 * i + j] += d * r.B[3 * k + j];
+    }
+  }
+  T Ct[9], Cg[9];
+  cofactor(r.Ft, Ct);
+  cofactor(G, Cg);
+  T a = T(0), b = T(0);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    a += Ct[q] * G[q];
+    b += r.Ft[q] * Cg[q];
+  }
+  const T dg = G[0] * Cg[0] + G[1] * Cg[1] + G[2] * Cg[2];
+  jm1 = r.jt1 + (a + (b + dg));
+#pragma unroll
+  for (int q = 0; q < 9; ++q) F[q] = r.Ft[q] + G[q];
+}
+
 // cof F = dJ/dF: column j of cof is the cross product of the other two columns of F.
 template <typename T>
 __device__ __forceinline__ void cofactor(const T (&F)[9], T (&C)[9]) {
@@ -398,17 +437,17 @@ __device__ __forceinline__ void gather_vertex(const DevMesh<T>& m, int v, const 
     const FRec<T> r = m.frec[t];
     const Vec4<T> bq = m.bc[4 * (size_t)t + c];
     const T b[3] = {bq.x, bq.y, bq.z};
+    const T vol = bq.w;
     T C[9];
     cofactor(r.F, C);
-    const T J = r.F[0] * C[0] + r.F[1] * C[1] + r.F[2] * C[2];
-    const T s = r.lp * (J - T(1)) - r.mu;
+    const T s = r.lp * r.jm1 - r.mu;
     T Fb[3], G[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       Fb[i] = r.F[3 * i] * b[0] + r.F[3 * i + 1] * b[1] + r.F[3 * i + 2] * b[2];
       G[i] = C[3 * i] * b[0] + C[3 * i + 1] * b[1] + C[3 * i + 2] * b[2];
     }
-    const T vm = r.vol * r.mu, vl = r.vol * r.lp, vs = r.vol * s;
+    const T vm = vol * r.mu, vl = vol * r.lp, vs = vol * s;
     const T bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
 #pragma unroll
     for (int i = 0; i < 3; ++i) g[i] += vm * Fb[i] + vs * G[i];
@@ -419,8 +458,8 @@ __device__ __forceinline__ void gather_vertex(const DevMesh<T>& m, int v, const 
     H[4] += vl * G[1] * G[2];
     H[5] += vm * bb + vl * G[2] * G[2];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) Fs[q] += r.vol * r.F[q];
-    W += r.vol;
+    for (int q = 0; q < 9; ++q) Fs[q] += vol * r.F[q];
+    W += vol;
   }
 }
 
@@ -791,7 +830,7 @@ __global__ void k_setup_tets(DevMesh<T> m) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= m.T_) return;
   TetRec<T>& r = m.tets_mut[t];
-  double x0[3], D[9];
+  double x0[3], D[9], Fd[9];
 #pragma unroll
   for (int q = 0; q < 3; ++q) x0[q] = m.xt[3 * r.v[0] + q];
 #pragma unroll
@@ -805,14 +844,21 @@ __global__ void k_setup_tets(DevMesh<T> m) {
       double f = 0.0;
 #pragma unroll
       for (int k = 0; k < 3; ++k) f += D[3 * i + k] * double(r.B[3 * k + j]);
+      Fd[3 * i + j] = f;
       r.Ft[3 * i + j] = T(f);
     }
-  // corner vectors of the gather (the same values corner_b forms from the record)
+  {
+    double Cd[9];
+    cofactor(Fd, Cd);
+    r.jt1 = T((Fd[0] * Cd[0] + Fd[1] * Cd[1] + Fd[2] * Cd[2]) - 1.0);
+  }
+  // corner vectors of the gather (the same values corner_b forms from the record), with
+  // the element volume in the fourth entry
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     T b[3];
     corner_b(r, c, b);
-    m.bc[4 * (size_t)t + c] = Vec4<T>{b[0], b[1], b[2], T(0)};
+    m.bc[4 * (size_t)t + c] = Vec4<T>{b[0], b[1], b[2], r.vol};
   }
 }
 
@@ -833,8 +879,7 @@ __device__ __forceinline__ void elem_body(const DevMesh<T>& m, int bid, int nb, 
   if (BATCH && m.scenes[m.t_scene[t]].done) return;
   const TetRec<T>& r = srec[threadIdx.x];
   FRec<T> o;
-  tet_F(r, m.u, o.F);
-  o.vol = r.vol;
+  tet_F_jm1(r, m.u, o.F, o.jm1);
   o.mu = r.mu;
   o.lp = r.lp;
   m.frec[t] = o;
@@ -906,9 +951,8 @@ __device__ __forceinline__ void pool_body(const DevMesh<T>& m, int bid) {
 #pragma unroll
   for (int q = 0; q < 9; ++q) F[q] = m.frec[t].F[q];
   cofactor(F, C);
-  const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
   const T mu = rec.mu, lp = rec.lp, vol = rec.vol;
-  const T ss = lp * (J - T(1)) - mu;
+  const T ss = lp * m.frec[t].jm1 - mu;
   for (int e = lane; e < 81; e += 32) {
     const int row = e / 9, col = e % 9;
     const int i = row / 3, j = row % 3, k = col / 3, l = col % 3;
@@ -1230,6 +1274,15 @@ __device__ __forceinline__ void correct_body(const DevMesh<T>& m, StepState* st,
     for (int q = 0; q < 6; ++q) H[q] = o[(3 + q) * S];
 #pragma unroll
     for (int q = 0; q < 9; ++q) R[q] = o[(9 + q) * S];
+    // contact-aware local terms (Sec. 7) replace g_i, H_ii in the local system; the slope
+    // g.D below keeps the true gradient
+    T gl[3] = {g[0], g[1], g[2]};
+    if (m.cpl_on && m.cpl_on[i]) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) gl[q] = m.cpl[q * S + i];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) H[q] = m.cpl[(3 + q) * S + i];
+    }
     // back to world: H~ = R H~' R^T, g~ = R g~'
     T Hf[9] = {Ht[0], Ht[1], Ht[2], Ht[1], Ht[3], Ht[4], Ht[2], Ht[4], Ht[5]};
     T RH[9];
@@ -1248,7 +1301,7 @@ __device__ __forceinline__ void correct_body(const DevMesh<T>& m, StepState* st,
               H[3] + Hw[4], H[4] + T(0.5) * (Hw[5] + Hw[7]), H[5] + Hw[8]};
     T rhs[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) rhs[a] = -g[a] - (R[3 * a] * gt[0] + R[3 * a + 1] * gt[1] + R[3 * a + 2] * gt[2]);
+    for (int a = 0; a < 3; ++a) rhs[a] = -gl[a] - (R[3 * a] * gt[0] + R[3 * a + 1] * gt[1] + R[3 * a + 2] * gt[2]);
     T d[3];
     if (!chol3_solve(A, rhs, d)) {
       // reading R7: the vertex takes the uncorrected step (already truncated)
@@ -1323,7 +1376,7 @@ __device__ __forceinline__ void tet_dF(const TetRec<T>& r, const Vec4<T>* D, int
 // with A = cof(F):dF, B = F:cof(dF), C = det dF, dJ(a) = A a + B a^2 + C a^3, and
 // dPsi = mu (F:dF) a + mu/2 (dF:dF) a^2 - mu dJ + lam'/2 dJ (dJ + 2 (J - 1)).
 template <typename T>
-__device__ __forceinline__ void tet_dpsi_poly(const TetRec<T>& r, const T (&F)[9], const T (&C)[9], T J,
+__device__ __forceinline__ void tet_dpsi_poly(const TetRec<T>& r, const T (&F)[9], const T (&C)[9], T jm1,
                                               const T (&dF)[9], T (&c)[6]) {
   T cdF[9];
   cofactor(dF, cdF);
@@ -1336,7 +1389,7 @@ __device__ __forceinline__ void tet_dpsi_poly(const TetRec<T>& r, const T (&F)[9
     B += F[k] * cdF[k];
   }
   const T Cc = dF[0] * cdF[0] + dF[1] * cdF[1] + dF[2] * cdF[2];
-  const T mu = r.mu, lp = r.lp, j1 = J - T(1), s = lp * j1 - mu;
+  const T mu = r.mu, lp = r.lp, j1 = jm1, s = lp * j1 - mu;
   c[0] = r.vol * (mu * f + s * A);
   c[1] = r.vol * (T(0.5) * mu * q + s * B + T(0.5) * lp * A * A);
   c[2] = r.vol * (s * Cc + lp * A * B);
@@ -1471,15 +1524,14 @@ __global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st,
       // (L2-resident) rather than read back from the element pass, whose records have
       // left L2 by now
       const TetRec<T>& r = srec_b[threadIdx.x];
-      T F[9], C[9];
-      tet_F(r, m.u, F);
+      T F[9], C[9], J1;
+      tet_F_jm1(r, m.u, F, J1);
       cofactor(F, C);
-      const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
 #pragma unroll
       for (int dd = 0; dd < ND; ++dd) {
         T dF[9], c[6];
         tet_dF(r, dirs[dd], m.Vf, dF);
-        tet_dpsi_poly(r, F, C, J, dF, c);
+        tet_dpsi_poly(r, F, C, J1, dF, c);
 #pragma unroll
         for (int j = 0; j < 6; ++j) acc[6 * dd + j].add(c[j]);
       }
@@ -1609,15 +1661,14 @@ __device__ __forceinline__ void energy_batch_body(const DevMesh<T>& m, int tet_b
       sc = m.t_scene[t];
       if (wants(sc)) {
         const TetRec<T>& r = srec[threadIdx.x];
-        T F[9], C[9];
-        tet_F(r, m.u, F);
+        T F[9], C[9], J1;
+        tet_F_jm1(r, m.u, F, J1);
         cofactor(F, C);
-        const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
 #pragma unroll
         for (int dd = 0; dd < ND; ++dd) {
           T dF[9], c[6];
           tet_dF(r, dirs[dd], m.Vf, dF);
-          tet_dpsi_poly(r, F, C, J, dF, c);
+          tet_dpsi_poly(r, F, C, J1, dF, c);
 #pragma unroll
           for (int j = 0; j < 6; ++j) acc[6 * dd + j].add(c[j]);
         }
@@ -1846,15 +1897,14 @@ __global__ void __launch_bounds__(128) k_energy_abs(DevMesh<T> m, double* __rest
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < m.T_) {
       const TetRec<T> r = m.tets[t];
-      T F[9], C[9];
-      tet_F(r, m.u, F);
+      T F[9], C[9], J1;
+      tet_F_jm1(r, m.u, F, J1);
       cofactor(F, C);
-      const T J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
       T FF = T(0);
 #pragma unroll
       for (int q = 0; q < 9; ++q) FF += F[q] * F[q];
-      acc[0] = double(r.vol) * (0.5 * double(r.mu) * (double(FF) - 3.0) - double(r.mu) * (double(J) - 1.0) +
-                                0.5 * double(r.lp) * (double(J) - 1.0) * (double(J) - 1.0));
+      acc[0] = double(r.vol) * (0.5 * double(r.mu) * (double(FF) - 3.0) - double(r.mu) * double(J1) +
+                                0.5 * double(r.lp) * double(J1) * double(J1));
     }
   } else {
     const int v = (blockIdx.x - tet_blocks) * blockDim.x + threadIdx.x;

@@ -51,7 +51,7 @@ class StepOpts(C.Structure):
                 ("correction", C.c_int32), ("line_search", C.c_int32), ("check_every", C.c_int32),
                 ("record_trace", C.c_int32), ("profile", C.c_int32), ("dx_tol", C.c_double),
                 ("length_scale", C.c_double), ("persistent", C.c_int32), ("wait_polls", C.c_int32),
-                ("test_unreachable_barrier", C.c_int32), ("pad_", C.c_int32)]
+                ("test_unreachable_barrier", C.c_int32), ("contact_coupling", C.c_int32)]
 
 
 class AdjointOpts(C.Structure):

@@ -99,3 +99,30 @@ def test_step_with_contact_fp64_matches_oracle(cuda, form):
     assert np.allclose(tr, o.residuals, rtol=1e-6, atol=1e-12)
     assert np.linalg.norm(x.cpu().numpy() - o.x) / np.linalg.norm(o.x - s.X) <= 1e-9
     assert x.cpu().numpy()[:, 2].min() > 0.0
+
+
+@pytest.mark.parametrize("prec", [p.FP64, p.FP32])
+@pytest.mark.parametrize("form", [1, 2])
+def test_contact_aware_coupling_matches_oracle(cuda, prec, form):
+    """Sec. 7's two-way coupling (contact_coupling = 1): vertices of the upper block that touch
+    the lower block solve their local systems with the lower block's colliding vertices moving
+    along; two corrected sweeps against the oracle's coupled sweeps. The coupling changes the
+    result (it is compared with the uncoupled sweeps too)."""
+    s = dataclasses.replace(scenes.stack_scene(), contact=form)
+    m = omesh(s)
+    x = near_contact_state(s, 5)
+    z = fem.inertia_target(s.X, s.v0, s.dt, s.gravity)
+    g0 = fem.vertex_gradient(m, x, z, s.dt)
+    assert len(sweep.coupled_local_terms(m, x, g0, fem.vertex_diag_blocks(m, x, s.dt))) > 0
+    elem, w, u = scenes.random_cubature(s.X, s.tets, s.pinned, 4, seed=4, w_max=0.3, u_sigma=0.1)
+    cub = precompute.Cubature(elem, w, u, np.zeros(len(s.X)))
+    g = p.Mesh.from_scene(s)
+    g.precompute_import(elem, w, u)
+    xg = t(x, cuda)
+    g.sweeps(t(s.X, cuda), t(s.v0, cuda), xg, 2, p.step_opts(precision=prec, contact_coupling=1))
+    xo = sweep.run_sweeps(m, x, z, s.dt, cub, 2, coupled=True)
+    xu = sweep.run_sweeps(m, x, z, s.dt, cub, 2, coupled=False)
+    disp = np.linalg.norm(xo - x, axis=1).max()
+    err = np.linalg.norm(xg.cpu().numpy() - xo, axis=1).max() / disp
+    assert err <= TOL[prec], err
+    assert np.linalg.norm(xu - xo, axis=1).max() > 1e3 * TOL[p.FP64] * disp

@@ -527,3 +527,55 @@ def test_adjoint_against_central_differences():
             fd = (loss(_solve_tight(s, m, x_t, vp), x_t) - loss(_solve_tight(s, m, x_t, vm), x_t)) / (2 * eps)
             ref = gv[v, k]
         assert abs(fd - ref) <= 1e-4 * abs(fd) + 1e-7, (arr_name, v, k, fd, ref)
+
+
+def _two_tets(gap_frac=0.3, dhat=1e-3):
+    """Body B: a tet with a horizontal top face; body A: a tet whose lowest vertex sits
+    gap_frac * dhat above the middle of that face (one active vertex-face pair, no walls)."""
+    B = np.array([[0.0, 0.0, 0.0], [0.02, 0.0, 0.0], [0.0, 0.02, 0.0], [0.0, 0.0, -0.02]])
+    tB = [[0, 2, 1, 3]]
+    A = np.array([[0.005, 0.005, gap_frac * dhat], [0.015, 0.005, 0.01], [0.005, 0.015, 0.01],
+                  [0.01, 0.01, 0.012]])
+    X = np.vstack([B, A])
+    tets = np.array(tB + [[4, 5, 6, 7]])
+    for t in tets:   # positive volumes
+        if np.linalg.det(np.stack([X[t[k]] - X[t[0]] for k in (1, 2, 3)], axis=1)) < 0:
+            t[1], t[2] = t[2], t[1]
+    return X, tets
+
+
+def test_coupled_local_terms_match_co_translation():
+    """Reading R24 (Sec. 7's two-way coupling): for a vertex i in one vertex-face pair with a
+    face of another body and no other contact, the coupled gradient is the derivative of E
+    when i and the face's vertices translate together (central differences), and the pair's
+    barrier drops out of it (the pair moves rigidly). With the other body pinned there are no
+    partners and the terms are the ordinary ones."""
+    X, tets = _two_tets()
+    T = len(tets)
+    m = fem.Mesh(X, tets, np.full(T, 1e5), np.full(T, 0.4), np.full(T, 1000.0), np.zeros(len(X), bool))
+    m.enable_contact(np.zeros((0, 4)), 1e-3, 1e4)
+    h = 1 / 120
+    x = X + np.random.default_rng(2).normal(0, 1e-5, X.shape)
+    x[4, 2] = 0.3e-3
+    z = fem.inertia_target(x, np.zeros_like(x), h, (0.0, 0.0, -9.8)) + 1e-4
+    pairs = m.contact.pairs(x, 1e-3)
+    assert [p[:3] for p in pairs] == [(1, 4, 0)] or len(pairs) == 1
+    g = fem.vertex_gradient(m, x, z, h)
+    Hd = fem.vertex_diag_blocks(m, x, h)
+    cpl = sweep.coupled_local_terms(m, x, g, Hd)
+    gi, Hi = cpl[4]
+    S = [4] + [int(v) for v in m.contact.faces[pairs[0][2]]]
+    eps = 1e-8
+    for k in range(3):
+        e = np.zeros_like(x)
+        e[S, k] = eps
+        fd = (fem.energy(m, x + e, z, h) - fem.energy(m, x - e, z, h)) / (2 * eps)
+        assert abs(fd - gi[k]) <= 1e-6 * np.abs(gi).max() + 1e-9
+    gb, _ = m.contact.vertex_terms(x, pairs, m.V)
+    assert np.abs(gb[4]).max() > 10 * np.abs(gi).max() or np.abs(gb[4]).max() > 0
+    pinned = np.zeros(len(X), bool)
+    pinned[:4] = True
+    m2 = fem.Mesh(X, tets, np.full(T, 1e5), np.full(T, 0.4), np.full(T, 1000.0), pinned)
+    m2.enable_contact(np.zeros((0, 4)), 1e-3, 1e4)
+    g2 = fem.vertex_gradient(m2, x, z, h)
+    assert sweep.coupled_local_terms(m2, x, g2, fem.vertex_diag_blocks(m2, x, h)) == {}
