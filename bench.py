@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ms/step to 1e-4 rel. residual at 3.5M tets"
+_CONTACT_NAME = {0: "contact off", 1: "IPC barrier dhat=1e-3 on", 2: "penalty contact dhat=1e-3 on"}
 KIND = ["k_pool", "k_gather", "k_correct", "k_energy", "k_update", "setup", "contact", "k_elem",
         "k_pair_trials", "k_ls_decide", "k_batch_persistent"]
 
@@ -79,7 +80,7 @@ def build_scenes(args, rank=0, world=1):
     if w == "spheres":
         s = scenes.spheres_scene(n_spheres=args.n_spheres, contact=args.contact)
         return [s], (f"{args.n_spheres} voxel spheres r=0.1 m, 48 cells across, {s.n_tets:,} tets, "
-                     f"box walls, IPC dhat=1e-3 {'on' if args.contact else 'off'}"), False
+                     f"box walls, {_CONTACT_NAME[args.contact]}"), False
     if w == "beam":
         return [scenes.beam_scene()], "20x20x100-vertex Kuhn beam 0.02x0.02x0.1 m, 214,434 tets, E=1e7", False
     if w == "cube":
@@ -484,6 +485,8 @@ def run_jgs2(args, rank, world, local_rank):
         "config": {"workload": args.workload, "scene": desc, "cubature": args.cubature, "tets": T,
                    "vertices": int(len(X)), "free_vertices": Vf,
                    "contact": bool(args.contact) if args.workload == "spheres" else False,
+                   "contact_form": ({1: "ipc", 2: "penalty"}.get(args.contact)
+                                    if args.workload == "spheres" else None),
                    "correction": args.correction, "line_search": True, "n_cub": args.n_cub, "rel_tol": 1e-4,
                    "parallelisation": "Gauss-Seidel (greedy colouring, group subspaces)" if gs else "Jacobi",
                    "contact_coupling": bool(args.coupling),
@@ -753,7 +756,8 @@ def main():
     ap.add_argument("--dx-tol", type=float, default=1e-3,
                     help="the paper's position-change tolerance on the unit-normalised scene")
     ap.add_argument("--n-spheres", type=int, default=10)
-    ap.add_argument("--contact", type=int, default=1, help="IPC barrier on the spheres workload")
+    ap.add_argument("--contact", type=int, default=1, choices=[0, 1, 2],
+                    help="spheres workload: 0 no contact, 1 IPC log barrier, 2 quadratic penalty")
     ap.add_argument("--n-scenes", type=int, default=256)
     ap.add_argument("--cubature", default="precompute", choices=["precompute", "synthetic"],
                     help="synthetic: seeded random records instead of the precompute (kernel profiling only)")

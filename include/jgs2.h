@@ -350,8 +350,7 @@ jgs2_status jgs2_mesh_set_youngs(jgs2_mesh* mesh, const double* youngs);
  *    (cudaGetSymbolAddress) while that device is current.
  *  - Every call shares the array; calls that overlap on the GPU race. Each call writes
  *    every slot it reads, so the array needs no clearing.
- *  - Every call copies E to the host and synchronises the stream before it returns, so it
- *    cannot be recorded into a CUDA graph by stream capture.
+ *  - Every call copies E to the host and synchronises the stream before it returns.
  *  - x_t, v_t, x, g: device [V][3] double, caller order (g may be NULL); energy: host
  *    pointer (may be NULL, not both). */
 #define JGS2_STATIC_PARTIALS_MAX 65536

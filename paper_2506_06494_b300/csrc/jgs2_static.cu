@@ -13,9 +13,9 @@
 // with cudaGetSymbolAddress (the first call on a device does that set-up while the device
 // is current). Each call overwrites every slot it reads, so no clearing is needed; calls
 // that overlap on the GPU (on different streams, or from different threads) race on the
-// array. Every call copies E to the host and synchronises its stream, so it cannot be
-// recorded by stream capture. Meshes with contact are rejected: their barrier terms need
-// the candidate list that only the allocating entry point builds.
+// array. Every call copies E to the host and synchronises its stream. Meshes with contact
+// are rejected: their barrier terms need the candidate list that only the allocating entry
+// point builds.
 #include <cuda_runtime.h>
 
 #include <mutex>
