@@ -408,7 +408,7 @@ def run_jgs2(args, rank, world, local_rank):
     if gs and (batch or (args.workload == "spheres" and args.contact)):
         raise SystemExit("--gs takes a single scene without contact")
     if args.cubature == "precompute":
-        mesh.precompute(n_cub=args.n_cub, gs=int(gs))
+        mesh.precompute(n_cub=args.n_cub, gs=int(gs), gpu=int(args.precompute_gpu))
     else:
         # seeded synthetic records: same kernel work, no convergence meaning (profiling only)
         import scenes
@@ -510,6 +510,8 @@ def run_jgs2(args, rank, world, local_rank):
         "contact_rebuilds_per_step": float(np.mean([q["rebuilds"] for q in reps])),
         "contact_pairs_last_step": {"candidates": int(reps[-1]["cand"]), "within_rc_last_sweep": int(reps[-1]["near"])},
         "precompute_s": round(t_pre, 2),
+        "precompute_solves": ("GPU (FP32 substitutions, FP64 refinement)" if args.precompute_gpu else "host FP64")
+        if args.cubature == "precompute" else None,
         "e2e": {"value": e2e_ms, "unit": "ms/step", "h2d_bytes_per_step": int(xh.nbytes + vh.nbytes),
                 "d2h_bytes_per_step": int(xh.nbytes + vh.nbytes)},
         "gpu_launches": launches,
@@ -686,7 +688,7 @@ def run_adjoint(args, rank, world, local_rank):
     s = scenes.beam_scene()
     mesh = p.Mesh.from_scene(s)
     if args.cubature == "precompute":
-        mesh.precompute(n_cub=args.n_cub)
+        mesh.precompute(n_cub=args.n_cub, gpu=int(args.precompute_gpu))
     else:
         mesh.precompute_import(*scenes.random_cubature(s.X, s.tets, s.pinned, args.n_cub, seed=0, w_max=0.5,
                                                        u_sigma=0.2))
@@ -755,6 +757,8 @@ def main():
                          "per kernel (0)")
     ap.add_argument("--dx-tol", type=float, default=1e-3,
                     help="the paper's position-change tolerance on the unit-normalised scene")
+    ap.add_argument("--precompute-gpu", type=int, default=0, choices=[0, 1],
+                    help="1: the precompute's multi-RHS solves run on the GPU (FP32 substitutions, FP64 refinement)")
     ap.add_argument("--n-spheres", type=int, default=10)
     ap.add_argument("--contact", type=int, default=1, choices=[0, 1, 2],
                     help="spheres workload: 0 no contact, 1 IPC log barrier, 2 quadratic penalty")

@@ -87,6 +87,12 @@ typedef struct {
                         * keeps the group's other DOFs fixed (one factorisation per colour).
                         * The records suit a sweep that runs the colours in turn; jgs2_step
                         * runs the Jacobi sweep (0, the default) */
+  int32_t gpu;         /* 1 = the multi-RHS solves of the training poses and of the pool rows
+                        * of H_bar^{-1} run on the current CUDA device (FP32 substitutions with
+                        * the factor, refined in FP64 against H_bar to a relative residual of
+                        * 1e-14, accepted at 1e-10, else JGS2_ENOTCONVERGED); 0 = host FP64
+                        * substitutions. Factorisation, selected inversion and NNLS stay on
+                        * the host either way. Gauss-Seidel groups (gs = 1) solve on the host */
 } jgs2_precompute_opts;
 
 /* Cubature records produced elsewhere (e.g. by an independent implementation), in the

@@ -1,0 +1,592 @@
+// Multi-RHS substitutions with the rest Hessian's supernodal factor on the GPU, for the
+// offline stage (Sec. 6: H_bar is factorised once and every later solve reuses the factor;
+// Sec. 5: the training poses come from block inverse iteration, Eq. u from the rows of
+// H_bar^{-1} at the pool vertices).
+//
+// Device layout:
+//   L32    every supernode's L block (column-major, leading dimension m = 3nJ + 3nR),
+//          rounded to FP32, one after another (offset Loff[s]).
+//   rdof   per supernode, the global DOF of each of its 3nR below-rows.
+//   items  each supernode's 3nJ columns are cut into panels of at most kPW columns, and the
+//          rows below a panel into ranges of at most kRS rows; one work item is a (panel,
+//          row range). Panel q of supernode s runs after panel q-1 of s and after every
+//          panel of s's descendants in the elimination tree: level(s, 0) = max over the
+//          children c of level(c, last) + 1. Items are sorted by level.
+//   H      H_bar in block CSR (both triangles, row-major 3x3 blocks), FP64.
+//   X, B, R row-major [n][k] FP64 (iterate, right-hand sides, residual); W [n][k] FP32.
+//
+// Forward (L y = r), level by level: one block per panel solves the panel's diagonal
+// block in shared memory and stores y_panel; then every item subtracts L_rows y_panel
+// from its row range: rows of the panel's own supernode by plain stores (no other item of
+// the level touches them), ancestor rows by atomicAdd (several supernodes of one level can
+// share an ancestor row). The atomics make the order of the FP32 sums vary from run to
+// run; the FP64 refinement below absorbs it.
+// Backward (L^T x = y), levels in reverse: an item gathers L_rows^T x_rows over its row
+// range (reads of rows that are already final); a panel with several items sums their
+// partials from scratch in a fixed order, then solves with the diagonal block transposed.
+// Refinement: X += solve32(R), R = B - H_bar X in FP64, until every column has
+// |R| <= tol |B|. With kappa(H_bar) eps_32 < 1 each round contracts the error by about
+// kappa eps_32.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "jgs2_precompute.h"
+
+namespace jgs2 {
+namespace pre {
+
+namespace {
+
+constexpr int kPW = 32;    // panel width (columns of L)
+constexpr int kCW = 32;    // right-hand-side columns per block
+constexpr int kRT = 64;    // rows per shared-memory tile
+constexpr int kRS = 1024;  // rows per work item at most
+constexpr int kThreads = 256;
+
+struct SolveDev {
+  const float* L;
+  const long long* Loff;    // [ns]
+  const int* sn_f3;         // [ns] first DOF
+  const int* sn_nJ;         // [ns] 3 nJ
+  const int* sn_m;          // [ns] 3 nJ + 3 nR
+  const int* rdof_off;      // [ns]
+  const int* rdof;          // below-row DOFs
+  const int* it_sn;         // [items] supernode
+  const int* it_c0;         // panel's first column (local)
+  const int* it_c1;         // one past the panel's last column
+  const int* it_r0;         // row range [r0, r1) (local rows, >= c1)
+  const int* it_r1;
+  const int* pn_item0;      // per panel (level order): its first item and item count
+  const int* pn_nitem;
+  const int* it_slot;       // backward scratch slot of an item of a multi-item panel, else -1
+};
+
+__device__ __forceinline__ int dof_of(const SolveDev& d, int s, int f3, int nJ, int r) {
+  return r < nJ ? f3 + r : d.rdof[d.rdof_off[s] + r - nJ];
+}
+
+// Loads the panel's diagonal block (rows and columns [c0, c1)) into Ld (zero padded).
+__device__ __forceinline__ void load_diag(const float* __restrict__ L, int m, int c0, int pw,
+                                          float (&Ld)[kPW][kPW + 1]) {
+  for (int q = threadIdx.x; q < kPW * kPW; q += kThreads) {
+    const int j = q / kPW, i = q % kPW;
+    Ld[i][j] = (i < pw && j < pw) ? L[(size_t)(c0 + j) * m + c0 + i] : 0.f;
+  }
+}
+
+// Loads rows [r0, r0 + nr) of the panel's columns into Lt (zero padded).
+__device__ __forceinline__ void load_rows(const float* __restrict__ L, int m, int c0, int pw, int r0, int nr,
+                                          float (&Lt)[kRT][kPW + 1]) {
+  for (int q = threadIdx.x; q < kRT * kPW; q += kThreads) {
+    const int j = q / kRT, i = q % kRT;
+    Lt[i][j] = (i < nr && j < pw) ? L[(size_t)(c0 + j) * m + r0 + i] : 0.f;
+  }
+}
+
+// Forward, step 1 of a level: y_panel = L_panel^{-1} r_panel for the level's panels.
+__global__ void __launch_bounds__(kThreads) k_fwd_panel(SolveDev d, int pn0, float* __restrict__ W, int k) {
+  __shared__ float Ld[kPW][kPW + 1];
+  __shared__ float xs[kPW][kCW + 1];
+  const int it = d.pn_item0[pn0 + blockIdx.x];
+  const int s = d.it_sn[it], c0 = d.it_c0[it], pw = d.it_c1[it] - c0;
+  const int m = d.sn_m[s], f3 = d.sn_f3[s];
+  const float* L = d.L + d.Loff[s];
+  const int col0 = blockIdx.y * kCW, cw = min(kCW, k - col0);
+  const int tid = threadIdx.x;
+  load_diag(L, m, c0, pw, Ld);
+  for (int q = tid; q < kPW * kCW; q += kThreads) {
+    const int i = q / kCW, c = q % kCW;
+    xs[i][c] = (i < pw && c < cw) ? W[(size_t)(f3 + c0 + i) * k + col0 + c] : 0.f;
+  }
+  __syncthreads();
+  if (tid < kCW) {
+    for (int j = 0; j < pw; ++j) {
+      const float xj = xs[j][tid] / Ld[j][j];
+      xs[j][tid] = xj;
+      for (int i = j + 1; i < pw; ++i) xs[i][tid] -= Ld[i][j] * xj;
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < pw * kCW; q += kThreads) {
+    const int i = q / kCW, c = q % kCW;
+    if (c < cw) W[(size_t)(f3 + c0 + i) * k + col0 + c] = xs[i][c];
+  }
+}
+
+// Forward, step 2 of a level: every item subtracts L_rows y_panel from its row range.
+__global__ void __launch_bounds__(kThreads) k_fwd_update(SolveDev d, int i0, float* __restrict__ W, int k) {
+  __shared__ float xs[kPW][kCW + 1];
+  __shared__ float Lt[kRT][kPW + 1];
+  const int it = i0 + blockIdx.x;
+  const int s = d.it_sn[it], c0 = d.it_c0[it], c1 = d.it_c1[it], pw = c1 - c0;
+  const int r0 = d.it_r0[it], r1 = d.it_r1[it];
+  if (r0 >= r1) return;
+  const int m = d.sn_m[s], nJ = d.sn_nJ[s], f3 = d.sn_f3[s];
+  const float* L = d.L + d.Loff[s];
+  const int col0 = blockIdx.y * kCW, cw = min(kCW, k - col0);
+  const int tid = threadIdx.x;
+  for (int q = tid; q < kPW * kCW; q += kThreads) {
+    const int i = q / kCW, c = q % kCW;
+    xs[i][c] = (i < pw && c < cw) ? W[(size_t)(f3 + c0 + i) * k + col0 + c] : 0.f;
+  }
+  const int c = tid % 32, rg = tid / 32;
+  for (int t0 = r0; t0 < r1; t0 += kRT) {
+    const int nr = min(kRT, r1 - t0);
+    __syncthreads();
+    load_rows(L, m, c0, pw, t0, nr, Lt);
+    __syncthreads();
+    for (int i = rg; i < nr; i += kThreads / 32) {
+      float acc = 0.f;
+#pragma unroll 8
+      for (int j = 0; j < kPW; ++j) acc += Lt[i][j] * xs[j][c];
+      if (c < cw) {
+        const int r = t0 + i;
+        if (r < nJ)
+          W[(size_t)(f3 + r) * k + col0 + c] -= acc;
+        else
+          atomicAdd(&W[(size_t)d.rdof[d.rdof_off[s] + r - nJ] * k + col0 + c], -acc);
+      }
+    }
+  }
+}
+
+// Gathers acc[q] = sum over the item's rows r of L[r][c0 + ig + 8q] x[r] for this thread's
+// column c (ig = warp index).
+__device__ __forceinline__ void bwd_gather(const SolveDev& d, int it, const float* __restrict__ W, int k, int col0,
+                                           int cw, float (&Lt)[kRT][kPW + 1], float (&Wt)[kRT][kCW + 1],
+                                           float (&acc)[kPW / 8]) {
+  const int s = d.it_sn[it], c0 = d.it_c0[it], pw = d.it_c1[it] - c0;
+  const int r0 = d.it_r0[it], r1 = d.it_r1[it];
+  const int m = d.sn_m[s], nJ = d.sn_nJ[s], f3 = d.sn_f3[s];
+  const float* L = d.L + d.Loff[s];
+  const int tid = threadIdx.x, c = tid % 32, ig = tid / 32;
+  for (int t0 = r0; t0 < r1; t0 += kRT) {
+    const int nr = min(kRT, r1 - t0);
+    __syncthreads();
+    load_rows(L, m, c0, pw, t0, nr, Lt);
+    for (int q = tid; q < kRT * kCW; q += kThreads) {
+      const int i = q / kCW, cc = q % kCW;
+      Wt[i][cc] = (i < nr && cc < cw) ? W[(size_t)dof_of(d, s, f3, nJ, t0 + i) * k + col0 + cc] : 0.f;
+    }
+    __syncthreads();
+    for (int i = 0; i < nr; ++i) {
+      const float w = Wt[i][c];
+#pragma unroll
+      for (int q = 0; q < kPW / 8; ++q) acc[q] += Lt[i][ig + 8 * q] * w;
+    }
+  }
+}
+
+// Backward partial sums of the items of multi-item panels: scratch[slot][chunk][kPW][kCW].
+__global__ void __launch_bounds__(kThreads) k_bwd_partial(SolveDev d, int i0, const float* __restrict__ W, int k,
+                                                          float* __restrict__ scratch, int nchunk) {
+  __shared__ float Lt[kRT][kPW + 1];
+  __shared__ float Wt[kRT][kCW + 1];
+  const int it = i0 + blockIdx.x;
+  const int slot = d.it_slot[it];
+  if (slot < 0) return;
+  const int col0 = blockIdx.y * kCW, cw = min(kCW, k - col0);
+  float acc[kPW / 8] = {0.f, 0.f, 0.f, 0.f};
+  bwd_gather(d, it, W, k, col0, cw, Lt, Wt, acc);
+  const int c = threadIdx.x % 32, ig = threadIdx.x / 32;
+  float* o = scratch + ((size_t)slot * nchunk + blockIdx.y) * kPW * kCW;
+#pragma unroll
+  for (int q = 0; q < kPW / 8; ++q) o[(ig + 8 * q) * kCW + c] = acc[q];
+}
+
+// Backward solve of the panels of one level (pn0 .. pn0 + gridDim.x).
+__global__ void __launch_bounds__(kThreads) k_bwd_panel(SolveDev d, int pn0, float* __restrict__ W, int k,
+                                                        const float* __restrict__ scratch, int nchunk) {
+  __shared__ float Ld[kPW][kPW + 1];
+  __shared__ float xs[kPW][kCW + 1];
+  __shared__ float Lt[kRT][kPW + 1];
+  __shared__ float Wt[kRT][kCW + 1];
+  const int pn = pn0 + blockIdx.x;
+  const int it0 = d.pn_item0[pn], nit = d.pn_nitem[pn];
+  const int s = d.it_sn[it0], c0 = d.it_c0[it0], pw = d.it_c1[it0] - c0;
+  const int m = d.sn_m[s], f3 = d.sn_f3[s];
+  const float* L = d.L + d.Loff[s];
+  const int col0 = blockIdx.y * kCW, cw = min(kCW, k - col0);
+  const int tid = threadIdx.x, c = tid % 32, ig = tid / 32;
+  float acc[kPW / 8] = {0.f, 0.f, 0.f, 0.f};
+  if (nit == 1) {
+    bwd_gather(d, it0, W, k, col0, cw, Lt, Wt, acc);
+  } else {
+    for (int q = 0; q < nit; ++q) {  // fixed order
+      const float* o = scratch + ((size_t)d.it_slot[it0 + q] * nchunk + blockIdx.y) * kPW * kCW;
+#pragma unroll
+      for (int u = 0; u < kPW / 8; ++u) acc[u] += o[(ig + 8 * u) * kCW + c];
+    }
+  }
+  __syncthreads();
+  load_diag(L, m, c0, pw, Ld);
+#pragma unroll
+  for (int q = 0; q < kPW / 8; ++q) {
+    const int i = ig + 8 * q;
+    xs[i][c] = (i < pw && c < cw) ? W[(size_t)(f3 + c0 + i) * k + col0 + c] - acc[q] : 0.f;
+  }
+  __syncthreads();
+  if (tid < kCW) {
+    for (int j = pw - 1; j >= 0; --j) {
+      const float xj = xs[j][tid] / Ld[j][j];
+      xs[j][tid] = xj;
+      for (int i = 0; i < j; ++i) xs[i][tid] -= Ld[j][i] * xj;
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < pw * kCW; q += kThreads) {
+    const int i = q / kCW, cc = q % kCW;
+    if (cc < cw) W[(size_t)(f3 + c0 + i) * k + col0 + cc] = xs[i][cc];
+  }
+}
+
+// R = B - H X (FP64), thread per (vertex row, column).
+__global__ void k_residual(const int* __restrict__ hp, const int* __restrict__ hc, const double* __restrict__ hv,
+                           const double* __restrict__ B, const double* __restrict__ X, double* __restrict__ R,
+                           int nv, int k) {
+  const long long total = (long long)nv * k;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(q / k), c = (int)(q % k);
+    double a0 = B[(size_t)(3 * v) * k + c], a1 = B[(size_t)(3 * v + 1) * k + c], a2 = B[(size_t)(3 * v + 2) * k + c];
+    for (int e = hp[v]; e < hp[v + 1]; ++e) {
+      const int u = hc[e];
+      const double* h = hv + (size_t)9 * e;
+      const double x0 = X[(size_t)(3 * u) * k + c], x1 = X[(size_t)(3 * u + 1) * k + c],
+                   x2 = X[(size_t)(3 * u + 2) * k + c];
+      a0 -= h[0] * x0 + h[1] * x1 + h[2] * x2;
+      a1 -= h[3] * x0 + h[4] * x1 + h[5] * x2;
+      a2 -= h[6] * x0 + h[7] * x1 + h[8] * x2;
+    }
+    R[(size_t)(3 * v) * k + c] = a0;
+    R[(size_t)(3 * v + 1) * k + c] = a1;
+    R[(size_t)(3 * v + 2) * k + c] = a2;
+  }
+}
+
+// Column sums of squares of A ([n][k]) added into out[k] (rows split over blockIdx.y).
+__global__ void k_colnorm2(const double* __restrict__ A, int n, int k, double* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  const int rows = (n + gridDim.y - 1) / gridDim.y;
+  const int a = blockIdx.y * rows, b = min(n, a + rows);
+  double s = 0.0;
+  for (int i = a; i < b; ++i) {
+    const double v = A[(size_t)i * k + c];
+    s += v * v;
+  }
+  atomicAdd(&out[c], s);
+}
+
+__global__ void k_to_f32(const double* __restrict__ R, float* __restrict__ W, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    W[q] = (float)R[q];
+}
+
+__global__ void k_add_f32(double* __restrict__ X, const float* __restrict__ W, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    X[q] += (double)W[q];
+}
+
+template <typename T>
+bool dalloc(T** p, size_t n, std::string& err) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+  if (e != cudaSuccess) {
+    err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    *p = nullptr;
+    return false;
+  }
+  return true;
+}
+
+template <typename T>
+bool upload(T** p, const std::vector<T>& v, std::string& err) {
+  if (!dalloc(p, v.size(), err)) return false;
+  if (v.empty()) return true;
+  const cudaError_t e = cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    err = std::string("cudaMemcpy: ") + cudaGetErrorString(e);
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+class GpuSolver {
+ public:
+  int nv = 0, n = 0, ns = 0;
+  // level schedule
+  std::vector<int> lev_item;   // [nlev + 1] item offsets
+  std::vector<int> lev_panel;  // [nlev + 1] panel offsets
+  std::vector<int> lev_slots;  // [nlev] scratch slots used by the level
+  int max_slots = 0;
+  // device
+  float* L = nullptr;
+  long long* Loff = nullptr;
+  int *sn_f3 = nullptr, *sn_nJ = nullptr, *sn_m = nullptr, *rdof_off = nullptr, *rdof = nullptr;
+  int *it_sn = nullptr, *it_c0 = nullptr, *it_c1 = nullptr, *it_r0 = nullptr, *it_r1 = nullptr,
+      *it_slot = nullptr, *pn_item0 = nullptr, *pn_nitem = nullptr;
+  int *hp = nullptr, *hc = nullptr;
+  double* hv = nullptr;
+  cudaStream_t stream = nullptr;
+
+  SolveDev view() const {
+    return SolveDev{L, Loff, sn_f3, sn_nJ, sn_m, rdof_off, rdof, it_sn, it_c0, it_c1, it_r0, it_r1,
+                    pn_item0, pn_nitem, it_slot};
+  }
+
+  ~GpuSolver() {
+    void* ptrs[] = {L, Loff, sn_f3, sn_nJ, sn_m, rdof_off, rdof, it_sn, it_c0, it_c1, it_r0, it_r1,
+                    it_slot, pn_item0, pn_nitem, hp, hc, hv};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+GpuSolver* gpu_solver_create(const Factor& F, const std::vector<BlockCol>& H, std::string& err) {
+  GpuSolver* S = new GpuSolver();
+  S->nv = F.nv;
+  S->n = 3 * F.nv;
+  const int ns = F.nsn();
+  S->ns = ns;
+  // supernode data, parents and panel counts
+  std::vector<int> f3(ns), nJ(ns), m(ns), roff(ns), par(ns, -1), npan(ns);
+  std::vector<long long> Loff(ns);
+  std::vector<int> rd;
+  long long tot = 0;
+  for (int s = 0; s < ns; ++s) {
+    const int f = F.sn_first[s];
+    f3[s] = 3 * f;
+    nJ[s] = 3 * (F.sn_first[s + 1] - f);
+    const std::vector<int>& R = F.sn_rows[s];
+    m[s] = nJ[s] + 3 * (int)R.size();
+    Loff[s] = tot;
+    tot += (long long)m[s] * nJ[s];
+    roff[s] = (int)rd.size();
+    for (int v : R)
+      for (int a = 0; a < 3; ++a) rd.push_back(3 * v + a);
+    if (!R.empty()) par[s] = F.sn_of[R[0]];
+    npan[s] = (nJ[s] + kPW - 1) / kPW;
+  }
+  // level of each supernode's first panel (children come before parents in supernode order)
+  std::vector<int> lvl0(ns, 0);
+  int nlev = 0;
+  for (int s = 0; s < ns; ++s) {
+    const int end = lvl0[s] + npan[s];
+    nlev = std::max(nlev, end);
+    if (par[s] >= 0) {
+      if (par[s] <= s) {
+        err = "supernode order is not topological";
+        delete S;
+        return nullptr;
+      }
+      lvl0[par[s]] = std::max(lvl0[par[s]], end);
+    }
+  }
+  // panels per level, then items (row ranges) per panel
+  std::vector<int> pcount(nlev + 1, 0);
+  for (int s = 0; s < ns; ++s)
+    for (int q = 0; q < npan[s]; ++q) pcount[lvl0[s] + q + 1]++;
+  for (int l = 0; l < nlev; ++l) pcount[l + 1] += pcount[l];
+  const int npanels = pcount[nlev];
+  std::vector<int> p_sn(npanels), p_c0(npanels), p_c1(npanels);
+  {
+    std::vector<int> fill(pcount.begin(), pcount.end() - 1);
+    for (int s = 0; s < ns; ++s)
+      for (int q = 0; q < npan[s]; ++q) {
+        const int at = fill[lvl0[s] + q]++;
+        p_sn[at] = s;
+        p_c0[at] = q * kPW;
+        p_c1[at] = std::min(nJ[s], (q + 1) * kPW);
+      }
+  }
+  std::vector<int> i_sn, i_c0, i_c1, i_r0, i_r1, i_slot, pn_item0(npanels), pn_nitem(npanels);
+  S->lev_item.assign(nlev + 1, 0);
+  S->lev_panel = pcount;
+  S->lev_slots.assign(nlev, 0);
+  for (int l = 0; l < nlev; ++l) {
+    int slots = 0;
+    for (int pn = pcount[l]; pn < pcount[l + 1]; ++pn) {
+      const int s = p_sn[pn], c1 = p_c1[pn];
+      const int rows = m[s] - c1;
+      const int nit = std::max(1, (rows + kRS - 1) / kRS);
+      pn_item0[pn] = (int)i_sn.size();
+      pn_nitem[pn] = nit;
+      for (int q = 0; q < nit; ++q) {
+        i_sn.push_back(s);
+        i_c0.push_back(p_c0[pn]);
+        i_c1.push_back(c1);
+        i_r0.push_back(c1 + q * kRS);
+        i_r1.push_back(std::min(m[s], c1 + (q + 1) * kRS));
+        i_slot.push_back(nit > 1 ? slots++ : -1);
+      }
+    }
+    S->lev_item[l + 1] = (int)i_sn.size();
+    S->lev_slots[l] = slots;
+    S->max_slots = std::max(S->max_slots, slots);
+  }
+  // H_bar in block CSR, both triangles
+  const int nvv = F.nv;
+  std::vector<int> cnt(nvv + 1, 0);
+  for (int c = 0; c < nvv; ++c)
+    for (int u : H[c].row) {
+      cnt[u + 1]++;
+      if (u != c) cnt[c + 1]++;
+    }
+  for (int v = 0; v < nvv; ++v) cnt[v + 1] += cnt[v];
+  std::vector<int> hc(cnt[nvv]);
+  std::vector<double> hv((size_t)9 * cnt[nvv]);
+  {
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (int c = 0; c < nvv; ++c)
+      for (size_t q = 0; q < H[c].row.size(); ++q) {
+        const int u = H[c].row[q];
+        const double* b = &H[c].val[9 * q];  // block (u, c)
+        int at = fill[u]++;
+        hc[at] = c;
+        for (int e = 0; e < 9; ++e) hv[(size_t)9 * at + e] = b[e];
+        if (u != c) {
+          at = fill[c]++;
+          hc[at] = u;
+          for (int a = 0; a < 3; ++a)
+            for (int b2 = 0; b2 < 3; ++b2) hv[(size_t)9 * at + 3 * a + b2] = b[3 * b2 + a];
+        }
+      }
+  }
+  // factor in FP32
+  bool ok = dalloc(&S->L, (size_t)tot, err);
+  if (ok) {
+    std::vector<float> buf;
+    for (int s = 0; s < ns && ok; ++s) {
+      const std::vector<double>& Ls = F.L[s];
+      buf.resize(Ls.size());
+      for (size_t q = 0; q < Ls.size(); ++q) buf[q] = (float)Ls[q];
+      const cudaError_t e =
+          cudaMemcpy(S->L + Loff[s], buf.data(), buf.size() * sizeof(float), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        err = std::string("cudaMemcpy: ") + cudaGetErrorString(e);
+        ok = false;
+      }
+    }
+  }
+  ok = ok && upload(&S->Loff, Loff, err) && upload(&S->sn_f3, f3, err) && upload(&S->sn_nJ, nJ, err) &&
+       upload(&S->sn_m, m, err) && upload(&S->rdof_off, roff, err) && upload(&S->rdof, rd, err) &&
+       upload(&S->it_sn, i_sn, err) && upload(&S->it_c0, i_c0, err) && upload(&S->it_c1, i_c1, err) &&
+       upload(&S->it_r0, i_r0, err) && upload(&S->it_r1, i_r1, err) &&
+       upload(&S->it_slot, i_slot, err) && upload(&S->pn_item0, pn_item0, err) &&
+       upload(&S->pn_nitem, pn_nitem, err) && upload(&S->hp, cnt, err) && upload(&S->hc, hc, err) &&
+       upload(&S->hv, hv, err);
+  if (ok) {
+    const cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      err = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+      ok = false;
+    }
+  }
+  if (!ok) {
+    delete S;
+    return nullptr;
+  }
+  return S;
+}
+
+int gpu_solve_many(GpuSolver* S, double* Bh, int n, int k, double tol, double accept, int max_refine,
+                   std::string& err) {
+  if (!S || n != S->n || k <= 0) {
+    err = "gpu_solve_many: bad arguments";
+    return -1;
+  }
+  const size_t nk = (size_t)n * k;
+  const int nchunk = (k + kCW - 1) / kCW;
+  double *B = nullptr, *X = nullptr, *R = nullptr, *nb = nullptr, *nr = nullptr;
+  float *W = nullptr, *scr = nullptr;
+  auto release = [&] {
+    void* ptrs[] = {B, X, R, nb, nr, W, scr};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+  };
+  if (!dalloc(&B, nk, err) || !dalloc(&X, nk, err) || !dalloc(&R, nk, err) || !dalloc(&W, nk, err) ||
+      !dalloc(&nb, k, err) || !dalloc(&nr, k, err) ||
+      !dalloc(&scr, (size_t)std::max(1, S->max_slots) * nchunk * kPW * kCW, err)) {
+    release();
+    return -1;
+  }
+  cudaStream_t st = S->stream;
+  const SolveDev d = S->view();
+  const int nlev = (int)S->lev_slots.size();
+  const int ew_grid = 148 * 8;
+  std::vector<double> hb(k), hr(k);
+  int rounds = -1;
+  double prev = INFINITY, worst = INFINITY;
+  cudaError_t e = cudaMemcpyAsync(B, Bh, nk * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(X, 0, nk * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(R, B, nk * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(nb, 0, k * sizeof(double), st);
+  if (e == cudaSuccess) {
+    const int gy = std::max(1, std::min(256, n / 256));
+    k_colnorm2<<<dim3((k + 127) / 128, gy), 128, 0, st>>>(B, n, k, nb);
+    e = cudaMemcpyAsync(hb.data(), nb, k * sizeof(double), cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  for (int round = 0; e == cudaSuccess && round < max_refine; ++round) {
+    k_to_f32<<<ew_grid, 256, 0, st>>>(R, W, (long long)nk);
+    for (int l = 0; l < nlev; ++l) {
+      const int np = S->lev_panel[l + 1] - S->lev_panel[l];
+      if (np > 0) k_fwd_panel<<<dim3(np, nchunk), kThreads, 0, st>>>(d, S->lev_panel[l], W, k);
+      const int ni = S->lev_item[l + 1] - S->lev_item[l];
+      if (ni > 0) k_fwd_update<<<dim3(ni, nchunk), kThreads, 0, st>>>(d, S->lev_item[l], W, k);
+    }
+    for (int l = nlev - 1; l >= 0; --l) {
+      const int ni = S->lev_item[l + 1] - S->lev_item[l];
+      if (S->lev_slots[l] > 0) k_bwd_partial<<<dim3(ni, nchunk), kThreads, 0, st>>>(d, S->lev_item[l], W, k, scr, nchunk);
+      const int np = S->lev_panel[l + 1] - S->lev_panel[l];
+      if (np > 0) k_bwd_panel<<<dim3(np, nchunk), kThreads, 0, st>>>(d, S->lev_panel[l], W, k, scr, nchunk);
+    }
+    k_add_f32<<<ew_grid, 256, 0, st>>>(X, W, (long long)nk);
+    k_residual<<<ew_grid, 256, 0, st>>>(S->hp, S->hc, S->hv, B, X, R, S->nv, k);
+    cudaMemsetAsync(nr, 0, k * sizeof(double), st);
+    const int gy = std::max(1, std::min(256, n / 256));
+    k_colnorm2<<<dim3((k + 127) / 128, gy), 128, 0, st>>>(R, n, k, nr);
+    e = cudaMemcpyAsync(hr.data(), nr, k * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) break;
+    worst = 0.0;
+    for (int c = 0; c < k; ++c) {
+      const double rel = hb[c] > 0.0 ? std::sqrt(hr[c] / hb[c]) : std::sqrt(hr[c]);
+      worst = std::max(worst, std::isfinite(rel) ? rel : INFINITY);
+    }
+    rounds = round + 1;
+    // done at tol, or when a round no longer halves the worst residual (the FP64 residual's
+    // own rounding floor, or kappa eps_32 too large to contract)
+    if (worst <= tol || !(worst < 0.5 * prev)) break;
+    prev = worst;
+  }
+  if (!(worst <= accept)) {
+    if (err.empty())
+      err = "gpu_solve_many: refinement ended at relative residual " + std::to_string(worst) + " after " +
+            std::to_string(rounds) + " rounds";
+    rounds = -1;
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Bh, X, nk * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    err = std::string("gpu_solve_many: ") + cudaGetErrorString(e);
+    rounds = -1;
+  }
+  release();
+  return rounds;
+}
+
+void gpu_solver_destroy(GpuSolver* S) { delete S; }
+
+}  // namespace pre
+}  // namespace jgs2

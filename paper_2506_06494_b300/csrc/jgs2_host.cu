@@ -2033,6 +2033,7 @@ void jgs2_precompute_opts_default(jgs2_precompute_opts* o) {
   o->seed = 0;
   o->n_threads = 0;
   o->gs = 0;
+  o->gpu = 0;
 }
 
 void jgs2_step_opts_default(jgs2_step_opts* o) {

@@ -29,7 +29,7 @@ constexpr int kMaxCub = 8;       // cubature slots per vertex at most
 constexpr int kLsTrials = 8;     // line-search steps alpha = 2^-j, j < kLsTrials
 constexpr int kPairTrialBlocks = 148 * 4;  // blocks of the line-search barrier-trial pass (2 x kLsTrials sums each)
 constexpr int kEnergyBlocksMax = 148 * 8;  // blocks of the line-search energy pass, at most
-constexpr int kMaxVertexPairs = 16;  // active cross-body pairs listed per vertex at most
+constexpr int kMaxVertexPairs = 64;  // active cross-body pairs listed per vertex at most
 constexpr int kPoolH = 90;       // 12x12 symmetric as ten 3x3 corner blocks (a <= c)
 // Row stride of the per-slot cubature record arrays: Vf rounded up to 4 entries, so that
 // every row starts on a 16-byte boundary.

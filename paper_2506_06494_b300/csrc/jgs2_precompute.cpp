@@ -34,6 +34,7 @@
 #include "../../include/jgs2.h"
 #include "dense_host.h"
 #include "jgs2_host.h"
+#include "jgs2_precompute.h"
 
 namespace jgs2 {
 namespace pre {
@@ -233,21 +234,6 @@ static double nnls(const vector<double>& A, int m, int n, const vector<double>& 
 }
 
 // ------------------------------------------------------------------ sparse Cholesky
-
-struct Factor {
-  int nv = 0;                          // free vertices of the body (factor order)
-  vector<int> sn_first;                // supernode -> first vertex (factor order)
-  vector<int> sn_of;                   // vertex -> supernode
-  vector<vector<int>> sn_rows;         // supernode -> row structure below (vertices, ascending)
-  vector<vector<double>> L;            // supernode -> (3nJ + 3nR) x 3nJ column-major
-  int nsn() const { return (int)sn_first.size() - 1; }
-};
-
-// Lower block of the rest Hessian in factor order: for column vertex v, rows u >= v.
-struct BlockCol {
-  vector<int> row;
-  vector<double> val;  // 9 per row, row-major 3x3 (row dof of u, col dof of v)
-};
 
 static void nd_order(const vector<double>& P, const vector<vector<int>>& adj, vector<int>& idx,
                      vector<char>& side, vector<int>& out) {
@@ -677,6 +663,32 @@ static jgs2_status body_precompute(const Mesh& M, const vector<int>& bverts, con
     std::fprintf(stderr, "[jgs2_precompute] nf %d supernodes %d L entries %.3e\n", nf, F.nsn(), (double)nnz);
   }
   PHASE("factorize");
+  // multi-RHS solves H_bar X = B: on the GPU (FP32 substitutions, FP64 refinement) when
+  // asked, else the host's FP64 substitutions
+  struct SolverGuard {
+    GpuSolver* s = nullptr;
+    ~SolverGuard() { gpu_solver_destroy(s); }
+  } gsv;
+  if (o.gpu) {
+    gsv.s = gpu_solver_create(F, H, err);
+    if (!gsv.s) return JGS2_ECUDA;
+    PHASE("gpu upload");
+  }
+  jgs2_status solve_st = JGS2_OK;
+  auto solve = [&](vector<double>& B, int k) {
+    if (solve_st != JGS2_OK) return;
+    if (!gsv.s) {
+      solve_many(F, B, n, k);
+      return;
+    }
+    std::string e2;
+    const int rounds = gpu_solve_many(gsv.s, B.data(), n, k, 1e-14, 1e-10, 40, e2);
+    if (verbose()) std::fprintf(stderr, "[jgs2_precompute] gpu solve: %d columns, %d refinement rounds\n", k, rounds);
+    if (rounds < 0) {
+      err = e2 + " (FP32 substitutions need kappa(H_bar) well below 1e7; gpu = 0 solves in FP64 on the host)";
+      solve_st = JGS2_ENOTCONVERGED;
+    }
+  };
   // ---- training poses: lowest eigenpairs by block inverse iteration
   const int nt = std::min(o.n_train, n);
   const int p = std::min(n, nt + std::max(10, nt));
@@ -750,7 +762,8 @@ static jgs2_status body_precompute(const Mesh& M, const vector<int>& bverts, con
   {
     vector<double> HQ;
     for (int it = 0; it < 80; ++it) {
-      solve_many(F, Q, n, p);
+      solve(Q, p);
+      if (solve_st != JGS2_OK) return solve_st;
       orthonormalise(Q, p);
       Hmul(Q, HQ, p);
       vector<double> T((size_t)p * p, 0.0), w, Vv;
@@ -1033,7 +1046,7 @@ static jgs2_status body_precompute(const Mesh& M, const vector<int>& bverts, con
   vector<float> G32(g64 ? 0 : (size_t)nf * np * 9);
   auto Gat = [&](size_t q) -> double { return g64 ? G64[q] : (double)G32[q]; };
   {
-    const int batch = 384;  // RHS per batch (multiple of 3)
+    const int batch = gsv.s ? 768 : 384;  // RHS per batch (multiple of 3)
     for (int q0 = 0; q0 < 3 * np; q0 += batch) {
       const int k = std::min(batch, 3 * np - q0);
       vector<double> Bm((size_t)n * k, 0.0);
@@ -1042,7 +1055,8 @@ static jgs2_status body_precompute(const Mesh& M, const vector<int>& bverts, con
         const int v = pv[col / 3];
         Bm[(size_t)(3 * pos[v] + col % 3) * k + j] = 1.0;
       }
-      solve_many(F, Bm, n, k);
+      solve(Bm, k);
+      if (solve_st != JGS2_OK) return solve_st;
       for (int f = 0; f < nf; ++f)
         for (int j = 0; j < k; ++j) {
           const int col = q0 + j, q = col / 3, c = col % 3;
@@ -1209,7 +1223,7 @@ jgs2_status precompute(Mesh* m, const jgs2_precompute_opts* o) {
   using namespace pre;
   if (!m || !o) return fail(JGS2_EINVAL, "null argument");
   if (o->n_cub < 1 || o->n_cub > kMaxCub || o->n_train < 1 || o->n_cand < 1 || o->n_pool < 1 ||
-      !(o->nnls_tol >= 0.0))
+      !(o->nnls_tol >= 0.0) || (o->gpu != 0 && o->gpu != 1))
     return fail(JGS2_EINVAL, "precompute options out of range");
   const int saved = omp_get_max_threads();
   if (o->n_threads > 0) omp_set_num_threads(o->n_threads);

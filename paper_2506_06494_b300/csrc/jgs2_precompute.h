@@ -1,0 +1,48 @@
+// Shared data of the offline stage (Secs. 5-6): the rest Hessian's block columns, its
+// supernodal Cholesky factor, and the device solver that runs the factor's multi-RHS
+// substitutions on the GPU.
+#pragma once
+#include <string>
+#include <vector>
+
+namespace jgs2 {
+namespace pre {
+
+// Supernodal Cholesky factor H_bar = L L^T of one body (vertex blocks of 3 DOFs).
+struct Factor {
+  int nv = 0;                                // free vertices of the body (factor order)
+  std::vector<int> sn_first;                 // supernode -> first vertex (factor order)
+  std::vector<int> sn_of;                    // vertex -> supernode
+  std::vector<std::vector<int>> sn_rows;     // supernode -> row structure below (vertices, ascending)
+  std::vector<std::vector<double>> L;        // supernode -> (3nJ + 3nR) x 3nJ column-major
+  int nsn() const { return (int)sn_first.size() - 1; }
+};
+
+// Lower block of the rest Hessian in factor order: for column vertex v, rows u >= v.
+struct BlockCol {
+  std::vector<int> row;
+  std::vector<double> val;  // 9 per row, row-major 3x3 (row dof of u, col dof of v)
+};
+
+// Multi-RHS solves H_bar X = B on the GPU (Sec. 6: every solve reuses the one factor).
+// The substitutions run in FP32 over a level schedule of the factor's column panels;
+// FP64 iterative refinement against H_bar itself (residual B - H_bar X in FP64 on the
+// device) brings each column to the FP64 solve's accuracy.
+class GpuSolver;
+
+// Uploads the factor (rounded to FP32) and H_bar (FP64, both triangles) to the current
+// device. Returns nullptr with err set when the device cannot take them.
+GpuSolver* gpu_solver_create(const Factor& F, const std::vector<BlockCol>& H, std::string& err);
+
+// Solves H_bar X = B in place for B row-major [n][nrhs] (host, factor order, n = 3 nv).
+// Refines until every column's residual |B - H_bar X| <= tol |B|, or until a round no
+// longer halves the worst column's (at most max_refine rounds). Returns the rounds taken
+// if every column ended at or below accept, else -1 with err set (B then holds the last
+// iterate).
+int gpu_solve_many(GpuSolver* S, double* B, int n, int nrhs, double tol, double accept, int max_refine,
+                   std::string& err);
+
+void gpu_solver_destroy(GpuSolver* S);
+
+}  // namespace pre
+}  // namespace jgs2

@@ -38,7 +38,7 @@ class MeshDesc(C.Structure):
 class PrecomputeOpts(C.Structure):
     _fields_ = [("n_cub", C.c_int32), ("n_train", C.c_int32), ("n_cand", C.c_int32),
                 ("n_pool", C.c_int32), ("nnls_tol", C.c_double), ("seed", C.c_uint64),
-                ("n_threads", C.c_int32), ("gs", C.c_int32)]
+                ("n_threads", C.c_int32), ("gs", C.c_int32), ("gpu", C.c_int32)]
 
 
 class CubatureBlob(C.Structure):

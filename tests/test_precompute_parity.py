@@ -96,3 +96,11 @@ def test_gs_group_precompute_matches_oracle(name):
     rows = free[same]
     assert np.allclose(w[rows], cub.weight[rows], rtol=1e-5, atol=1e-8)
     assert np.allclose(r[rows], cub.residual[rows], rtol=1e-5, atol=1e-8)
+
+
+def test_precompute_gpu_option_range():
+    # validated before any work: 0 (host solves) or 1 (GPU solves)
+    g = p.Mesh.from_scene(scenes.cube_scene())
+    with pytest.raises(p.JGS2Error):
+        g.precompute(gpu=2)
+    g.close()
