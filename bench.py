@@ -155,13 +155,14 @@ def survey_sweep_bytes(V_f, T, n_cub, fp_bytes=4):
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of
-# one launch, FP32, 2 voxel spheres: 694,272 tets, 126,826 free vertices; k_energy is its
-# one-direction pass).
-# It grows in proportion to the tets, so a launch on another mesh is credited with
-# traffic x T / 694,272. Only kernels whose code has not changed since their capture are
+# one launch each, FP32, 4 voxel spheres: 1,388,544 tets, 253,652 free vertices, synthetic
+# cubature; k_energy is its one-direction pass). It grows in proportion to the tets (the
+# vertices grow with them), so a launch on another mesh of the same kind is credited with
+# traffic x T / 1,388,544. Only kernels whose code has not changed since their capture are
 # listed.
-NCU_TRAFFIC_TETS = 694272
-NCU_TRAFFIC = {"k_energy": 84.397056e6 + 2.023424e6, "k_elem": 79.797504e6 + 5.376768e6}
+NCU_TRAFFIC_TETS = 1388544
+NCU_TRAFFIC = {"k_gather": 198.486528e6 + 19.848448e6, "k_elem": 159.587840e6 + 35.314944e6,
+               "k_energy": 172.158976e6 + 4.227072e6}
 
 
 class Clocks:

@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -47,6 +48,7 @@ constexpr int kCW = 32;    // right-hand-side columns per block
 constexpr int kRT = 64;    // rows per shared-memory tile
 constexpr int kRS = 1024;  // rows per work item at most
 constexpr int kThreads = 256;
+static_assert(kPW == 32, "panel solves keep one panel row per lane");
 
 struct SolveDev {
   const float* L;
@@ -88,6 +90,39 @@ __device__ __forceinline__ void load_rows(const float* __restrict__ L, int m, in
   }
 }
 
+// xs <- L_d^{-1} xs (L_d lower triangular, pw x pw, zero padded), every column of xs: warp w
+// takes columns w, w + 8, ...; lane i holds row i, and step j broadcasts x_j by a shuffle.
+__device__ __forceinline__ void panel_solve_lower(const float (&Ld)[kPW][kPW + 1], float (&xs)[kPW][kCW + 1],
+                                                  int pw) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const float dinv = lane < pw ? 1.f / Ld[lane][lane] : 0.f;
+  for (int c = wid; c < kCW; c += kThreads / 32) {
+    float x = xs[lane][c];
+    for (int j = 0; j < pw; ++j) {
+      const float xj = __shfl_sync(0xffffffffu, x * dinv, j);
+      if (lane == j) x = xj;
+      else if (lane > j) x -= Ld[lane][j] * xj;
+    }
+    xs[lane][c] = x;
+  }
+}
+
+// xs <- L_d^{-T} xs (the transposed panel solve of the backward pass), same layout.
+__device__ __forceinline__ void panel_solve_upper(const float (&Ld)[kPW][kPW + 1], float (&xs)[kPW][kCW + 1],
+                                                  int pw) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const float dinv = lane < pw ? 1.f / Ld[lane][lane] : 0.f;
+  for (int c = wid; c < kCW; c += kThreads / 32) {
+    float x = xs[lane][c];
+    for (int j = pw - 1; j >= 0; --j) {
+      const float xj = __shfl_sync(0xffffffffu, x * dinv, j);
+      if (lane == j) x = xj;
+      else if (lane < j) x -= Ld[j][lane] * xj;
+    }
+    xs[lane][c] = x;
+  }
+}
+
 // Forward, step 1 of a level: y_panel = L_panel^{-1} r_panel for the level's panels.
 __global__ void __launch_bounds__(kThreads) k_fwd_panel(SolveDev d, int pn0, float* __restrict__ W, int k) {
   __shared__ float Ld[kPW][kPW + 1];
@@ -104,13 +139,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_panel(SolveDev d, int pn0, flo
     xs[i][c] = (i < pw && c < cw) ? W[(size_t)(f3 + c0 + i) * k + col0 + c] : 0.f;
   }
   __syncthreads();
-  if (tid < kCW) {
-    for (int j = 0; j < pw; ++j) {
-      const float xj = xs[j][tid] / Ld[j][j];
-      xs[j][tid] = xj;
-      for (int i = j + 1; i < pw; ++i) xs[i][tid] -= Ld[i][j] * xj;
-    }
-  }
+  panel_solve_lower(Ld, xs, pw);
   __syncthreads();
   for (int q = tid; q < pw * kCW; q += kThreads) {
     const int i = q / kCW, c = q % kCW;
@@ -231,13 +260,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_panel(SolveDev d, int pn0, flo
     xs[i][c] = (i < pw && c < cw) ? W[(size_t)(f3 + c0 + i) * k + col0 + c] - acc[q] : 0.f;
   }
   __syncthreads();
-  if (tid < kCW) {
-    for (int j = pw - 1; j >= 0; --j) {
-      const float xj = xs[j][tid] / Ld[j][j];
-      xs[j][tid] = xj;
-      for (int i = 0; i < j; ++i) xs[i][tid] -= Ld[j][i] * xj;
-    }
-  }
+  panel_solve_upper(Ld, xs, pw);
   __syncthreads();
   for (int q = tid; q < pw * kCW; q += kThreads) {
     const int i = q / kCW, cc = q % kCW;
@@ -337,6 +360,10 @@ class GpuSolver {
   int *hp = nullptr, *hc = nullptr;
   double* hv = nullptr;
   cudaStream_t stream = nullptr;
+  // work buffers of gpu_solve_many, kept between calls (grown on demand)
+  size_t cap_nk = 0, cap_k = 0, cap_scr = 0;
+  double *B = nullptr, *X = nullptr, *R = nullptr, *nb = nullptr, *nr = nullptr;
+  float *W = nullptr, *scr = nullptr;
 
   SolveDev view() const {
     return SolveDev{L, Loff, sn_f3, sn_nJ, sn_m, rdof_off, rdof, it_sn, it_c0, it_c1, it_r0, it_r1,
@@ -345,7 +372,7 @@ class GpuSolver {
 
   ~GpuSolver() {
     void* ptrs[] = {L, Loff, sn_f3, sn_nJ, sn_m, rdof_off, rdof, it_sn, it_c0, it_c1, it_r0, it_r1,
-                    it_slot, pn_item0, pn_nitem, hp, hc, hv};
+                    it_slot, pn_item0, pn_nitem, hp, hc, hv, B, X, R, nb, nr, W, scr};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     if (stream) cudaStreamDestroy(stream);
@@ -434,6 +461,14 @@ GpuSolver* gpu_solver_create(const Factor& F, const std::vector<BlockCol>& H, st
     S->lev_slots[l] = slots;
     S->max_slots = std::max(S->max_slots, slots);
   }
+  if (std::getenv("JGS2_VERBOSE")) {
+    int maxp = 0;
+    for (int l = 0; l < nlev; ++l) maxp = std::max(maxp, pcount[l + 1] - pcount[l]);
+    std::fprintf(stderr,
+                 "[jgs2_precompute] gpu schedule: %d supernodes, %d panels, %d items, %d levels "
+                 "(widest %d panels), %d scratch slots, %.3e factor entries\n",
+                 ns, npanels, (int)i_sn.size(), nlev, maxp, S->max_slots, (double)tot);
+  }
   // H_bar in block CSR, both triangles
   const int nvv = F.nv;
   std::vector<int> cnt(nvv + 1, 0);
@@ -507,19 +542,29 @@ int gpu_solve_many(GpuSolver* S, double* Bh, int n, int k, double tol, double ac
   }
   const size_t nk = (size_t)n * k;
   const int nchunk = (k + kCW - 1) / kCW;
-  double *B = nullptr, *X = nullptr, *R = nullptr, *nb = nullptr, *nr = nullptr;
-  float *W = nullptr, *scr = nullptr;
-  auto release = [&] {
-    void* ptrs[] = {B, X, R, nb, nr, W, scr};
-    for (void* p : ptrs)
+  const size_t nscr = (size_t)std::max(1, S->max_slots) * nchunk * kPW * kCW;
+  if (nk > S->cap_nk || (size_t)k > S->cap_k || nscr > S->cap_scr) {
+    void* old[] = {S->B, S->X, S->R, S->nb, S->nr, S->W, S->scr};
+    for (void* p : old)
       if (p) cudaFree(p);
-  };
-  if (!dalloc(&B, nk, err) || !dalloc(&X, nk, err) || !dalloc(&R, nk, err) || !dalloc(&W, nk, err) ||
-      !dalloc(&nb, k, err) || !dalloc(&nr, k, err) ||
-      !dalloc(&scr, (size_t)std::max(1, S->max_slots) * nchunk * kPW * kCW, err)) {
-    release();
-    return -1;
+    S->B = S->X = S->R = S->nb = S->nr = nullptr;
+    S->W = S->scr = nullptr;
+    S->cap_nk = S->cap_k = S->cap_scr = 0;
+    if (!dalloc(&S->B, nk, err) || !dalloc(&S->X, nk, err) || !dalloc(&S->R, nk, err) ||
+        !dalloc(&S->W, nk, err) || !dalloc(&S->nb, k, err) || !dalloc(&S->nr, k, err) ||
+        !dalloc(&S->scr, nscr, err))
+      return -1;
+    S->cap_nk = nk;
+    S->cap_k = k;
+    S->cap_scr = nscr;
   }
+  double *B = S->B, *X = S->X, *R = S->R, *nb = S->nb, *nr = S->nr;
+  float *W = S->W, *scr = S->scr;
+  const bool verbose = std::getenv("JGS2_VERBOSE") != nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  float t_fwd = 0.f, t_bwd = 0.f;
+  if (verbose)
+    for (auto& e : ev) cudaEventCreate(&e);
   cudaStream_t st = S->stream;
   const SolveDev d = S->view();
   const int nlev = (int)S->lev_slots.size();
@@ -539,18 +584,21 @@ int gpu_solve_many(GpuSolver* S, double* Bh, int n, int k, double tol, double ac
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   for (int round = 0; e == cudaSuccess && round < max_refine; ++round) {
     k_to_f32<<<ew_grid, 256, 0, st>>>(R, W, (long long)nk);
+    if (verbose) cudaEventRecord(ev[0], st);
     for (int l = 0; l < nlev; ++l) {
       const int np = S->lev_panel[l + 1] - S->lev_panel[l];
       if (np > 0) k_fwd_panel<<<dim3(np, nchunk), kThreads, 0, st>>>(d, S->lev_panel[l], W, k);
       const int ni = S->lev_item[l + 1] - S->lev_item[l];
       if (ni > 0) k_fwd_update<<<dim3(ni, nchunk), kThreads, 0, st>>>(d, S->lev_item[l], W, k);
     }
+    if (verbose) cudaEventRecord(ev[1], st);
     for (int l = nlev - 1; l >= 0; --l) {
       const int ni = S->lev_item[l + 1] - S->lev_item[l];
       if (S->lev_slots[l] > 0) k_bwd_partial<<<dim3(ni, nchunk), kThreads, 0, st>>>(d, S->lev_item[l], W, k, scr, nchunk);
       const int np = S->lev_panel[l + 1] - S->lev_panel[l];
       if (np > 0) k_bwd_panel<<<dim3(np, nchunk), kThreads, 0, st>>>(d, S->lev_panel[l], W, k, scr, nchunk);
     }
+    if (verbose) cudaEventRecord(ev[2], st);
     k_add_f32<<<ew_grid, 256, 0, st>>>(X, W, (long long)nk);
     k_residual<<<ew_grid, 256, 0, st>>>(S->hp, S->hc, S->hv, B, X, R, S->nv, k);
     cudaMemsetAsync(nr, 0, k * sizeof(double), st);
@@ -559,6 +607,13 @@ int gpu_solve_many(GpuSolver* S, double* Bh, int n, int k, double tol, double ac
     e = cudaMemcpyAsync(hr.data(), nr, k * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) break;
+    if (verbose) {
+      float a = 0.f, b = 0.f;
+      cudaEventElapsedTime(&a, ev[0], ev[1]);
+      cudaEventElapsedTime(&b, ev[1], ev[2]);
+      t_fwd += a;
+      t_bwd += b;
+    }
     worst = 0.0;
     for (int c = 0; c < k; ++c) {
       const double rel = hb[c] > 0.0 ? std::sqrt(hr[c] / hb[c]) : std::sqrt(hr[c]);
@@ -582,7 +637,11 @@ int gpu_solve_many(GpuSolver* S, double* Bh, int n, int k, double tol, double ac
     err = std::string("gpu_solve_many: ") + cudaGetErrorString(e);
     rounds = -1;
   }
-  release();
+  if (verbose) {
+    std::fprintf(stderr, "[jgs2_precompute] gpu solve: %d columns, substitutions %.2f ms forward, %.2f ms backward\n",
+                 k, t_fwd, t_bwd);
+    for (auto& ev1 : ev) cudaEventDestroy(ev1);
+  }
   return rounds;
 }
 

@@ -890,22 +890,19 @@ struct Launches {
   }
 };
 
-// Blocks of k_energy that are resident at once on the device (capped at kEnergyBlocksMax,
-// which sizes the partial-sum buffer).
-template <typename T>
+// Blocks of k_energy<T, DIR> that are resident at once on the device (capped at
+// kEnergyBlocksMax, which sizes the partial-sum buffer).
+template <typename T, int DIR>
 static int energy_blocks() {
   static int nb = 0;
   if (nb == 0) {
-    int dev = 0, sms = 148, per_sm = 8;
+    int dev = 0, sms = 148, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // the variant with the most registers (both directions) sets the wave
-    int per_sm2 = 8;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_energy<T, 0>, 128, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_energy<T, 2>, 128, 0) != cudaSuccess)
-      per_sm = per_sm2 = 1;
-    per_sm = std::max(1, std::min(per_sm, per_sm2));
-    nb = std::max(1, std::min(sms * per_sm, kEnergyBlocksMax));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_energy<T, DIR>, DIR == 2 ? 256 : 128, 0) !=
+        cudaSuccess)
+      per_sm = 1;
+    nb = std::max(1, std::min(sms * std::max(1, per_sm), kEnergyBlocksMax));
   }
   return nb;
 }
@@ -946,10 +943,11 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
   }
   const int nbV = (m->Vf + 127) / 128;
   const int nbT = (m->T + 127) / 128;
-  // line-search pass: grid-stride over tets and vertices, about 4 tets per thread
-  // line-search pass: one full wave of resident blocks (SM count x blocks per SM at this
-  // kernel's registers and shared memory), grid-stride over tet tiles and vertices
-  const int nbE = std::max(1, std::min(std::max(nbT, nbV), energy_blocks<T>()));
+  // line-search passes: one full wave of resident blocks each (SM count x blocks per SM at
+  // the pass's registers and shared memory), grid-stride over tet tiles and vertices
+  const int nbE0 = std::max(1, std::min(std::max(nbT, nbV), energy_blocks<T, 0>()));
+  const int nbE1 = std::max(1, std::min(std::max(nbT, nbV), energy_blocks<T, 1>()));
+  const int nbE2 = std::max(1, std::min(std::max(nbT, nbV), energy_blocks<T, 2>()));
   const int pi = sizeof(T) == 4 ? 1 : 0;
   const int bs = m->bs[pi], gbs = m->gbs[pi], gtpv = m->gtpv[pi];
   const int chunk = std::max(1, o.check_every);
@@ -1068,25 +1066,25 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
         // along D; along D_J only when every trial along D failed (those launches return
         // at once otherwise)
         const int npp = m->contact ? kPairTrialBlocks : 0;
-        double* pp = m->d_partial + (size_t)12 * nbE;
+        double* pp = m->d_partial + (size_t)12 * kEnergyBlocksMax;
         // one timing group per launch, so that each kernel of the pass is timed alone
         if (m->contact)
           group(JGS2_K_LS_PAIRS, 1, s, [&] { k_pair_trials<T, 0><<<npp, 128, 0, s>>>(d, m->d_state, pp); });
-        group(JGS2_K_ENERGY, 1, s, [&] { k_energy<T, 0><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial); });
+        group(JGS2_K_ENERGY, 1, s, [&] { k_energy<T, 0><<<nbE0, 128, 0, s>>>(d, m->d_state, m->d_partial); });
         group(JGS2_K_LS_DECIDE, 1, s, [&] {
-          k_ls_decide<0><<<1, 1024, 0, s>>>(m->d_state, corr ? 1 : 0, m->d_partial, nbE, pp, npp);
+          k_ls_decide<0><<<1, 1024, 0, s>>>(m->d_state, corr ? 1 : 0, m->d_partial, nbE0, pp, npp);
         });
         if (corr) {
           if (m->contact)
             group(JGS2_K_LS_PAIRS, 1, s, [&] { k_pair_trials<T, 1><<<npp, 128, 0, s>>>(d, m->d_state, pp); });
-          group(JGS2_K_ENERGY, 1, s, [&] { k_energy<T, 1><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial); });
+          group(JGS2_K_ENERGY, 1, s, [&] { k_energy<T, 1><<<nbE1, 128, 0, s>>>(d, m->d_state, m->d_partial); });
           group(JGS2_K_LS_DECIDE, 1, s,
-                [&] { k_ls_decide<1><<<1, 1024, 0, s>>>(m->d_state, 1, m->d_partial, nbE, pp, npp); });
+                [&] { k_ls_decide<1><<<1, 1024, 0, s>>>(m->d_state, 1, m->d_partial, nbE1, pp, npp); });
           if (m->contact)
             group(JGS2_K_LS_PAIRS, 1, s, [&] { k_pair_trials<T, 2><<<npp, 128, 0, s>>>(d, m->d_state, pp); });
-          group(JGS2_K_ENERGY, 1, s, [&] { k_energy<T, 2><<<nbE, 128, 0, s>>>(d, m->d_state, m->d_partial); });
+          group(JGS2_K_ENERGY, 1, s, [&] { k_energy<T, 2><<<nbE2, 256, 0, s>>>(d, m->d_state, m->d_partial); });
           group(JGS2_K_LS_DECIDE, 1, s,
-                [&] { k_ls_decide<2><<<1, 1024, 0, s>>>(m->d_state, 1, m->d_partial, nbE, pp, npp); });
+                [&] { k_ls_decide<2><<<1, 1024, 0, s>>>(m->d_state, 1, m->d_partial, nbE2, pp, npp); });
         }
       }
       if (nbV > 0) group(JGS2_K_UPDATE, 1, s, [&] { k_update<T><<<nbV, 128, 0, s>>>(d, m->d_state); });
