@@ -14,6 +14,17 @@ Per-vertex terms (reading R12/R19): the barrier enters the vertex gradient exact
 closest-point weights w_k and unit normal n) and the diagonal block through its
 Gauss-Newton part kappa B''(d) (dd/dx_k)(dd/dx_k)^T (B'' > 0 on (0, dhat), so PSD).
 
+Friction (reading R25): the lagged dissipative potential of IPC's friction model on the
+vertex-wall pairs. At the start of a step, each surface vertex v near wall p gets a lagged
+normal force lam_vp = -kappa E'(d_vp(x_t)) (d < dhat, else 0; E the barrier or penalty), and
+D(x) = mu sum_vp lam_vp f0(|P_p (x_v - x_t,v)|), P_p = I - n_p n_p^T the wall's tangent
+projector. f0 is C^1: f0(y) = -y^3/(3 eps^2) + y^2/eps + eps/3 for y < eps, y beyond, with
+eps = eps_v h (a slip speed eps_v over the step). The walls do not move, so the slip of a
+pair is the vertex's own tangential displacement over the step. D enters the energy, the
+vertex gradient mu lam f1(y)/y P u (f1 = f0'), and the vertex's diagonal block
+mu lam [(f1/y) P + ((f1' y - f1)/y^3) P u u^T P], which is positive semidefinite on both
+branches of f0.
+
 Step truncation (reading R11): a surface vertex's step is scaled so that
 |delta_v| <= 0.45 min(r_c - dhat, d_min,v), d_min,v = the smallest distance of a pair within
 the candidate radius r_c that involves v. No candidate pair's distance can shrink by 90% or
@@ -23,6 +34,27 @@ at x^k holds every barrier term along the sweep's line-search segment.
 from __future__ import annotations
 
 import numpy as np
+
+# ------------------------------------------------------------------ friction (R25)
+
+
+def friction_f0(y, eps):
+    """C^1 smoothing of |u| below the slip eps: -y^3/(3 eps^2) + y^2/eps + eps/3, y beyond."""
+    y = np.asarray(y, dtype=np.float64)
+    return np.where(y < eps, -y ** 3 / (3.0 * eps * eps) + y * y / eps + eps / 3.0, y)
+
+
+def friction_f1(y, eps):
+    """f0'(y): -y^2/eps^2 + 2y/eps below eps, 1 beyond."""
+    y = np.asarray(y, dtype=np.float64)
+    return np.where(y < eps, -y * y / (eps * eps) + 2.0 * y / eps, 1.0)
+
+
+def friction_f1_over_y(y, eps):
+    """f1(y)/y, finite at y = 0 (2/eps)."""
+    y = np.asarray(y, dtype=np.float64)
+    return np.where(y < eps, -y / (eps * eps) + 2.0 / eps, 1.0 / np.maximum(y, 1e-300))
+
 
 # ------------------------------------------------------------------ barrier
 
@@ -163,8 +195,12 @@ def surface(tets, X):
 
 
 class Contact:
-    def __init__(self, tets, X, planes, dhat, kappa, pinned=None, use_penalty=False):
+    def __init__(self, tets, X, planes, dhat, kappa, pinned=None, use_penalty=False, friction_mu=0.0,
+                 friction_eps_v=1e-3):
         self.faces, self.edges, self.sverts = surface(tets, X)
+        self.mu = float(friction_mu)
+        self.eps_v = float(friction_eps_v)
+        self.fr = None  # lagged friction state (x_t, lam[V, planes], eps) of the current step
         self.planes = np.asarray(planes, dtype=np.float64).reshape(-1, 4)
         self.dhat = float(dhat)
         self.kappa = float(kappa)
@@ -276,3 +312,53 @@ class Contact:
             for v, _ in J:
                 lim[v] = min(lim[v], d)
         return 0.45 * lim
+
+    # ---------------------------------------------------------------- friction (R25)
+
+    def lag_friction(self, x_t, h):
+        """Lagged normal forces of the step starting at x_t (none when mu = 0)."""
+        if self.mu <= 0.0:
+            self.fr = None
+            return
+        V = len(x_t)
+        lam = np.zeros((V, len(self.planes)))
+        for k, pl in enumerate(self.planes):
+            d = x_t[self.sverts] @ pl[:3] - pl[3]
+            on = (d > 0) & (d < self.dhat)
+            lam[self.sverts[on], k] = -self.kappa * self.e1(d[on], self.dhat)
+        if self.pinned is not None:
+            lam[self.pinned] = 0.0
+        self.fr = (np.array(x_t, dtype=np.float64, copy=True), lam, self.eps_v * h)
+
+    def _slips(self, x):
+        x_t, lam, eps = self.fr
+        for k, pl in enumerate(self.planes):
+            n = pl[:3]
+            for v in np.nonzero(lam[:, k] > 0)[0]:
+                du = x[v] - x_t[v]
+                yield int(v), lam[v, k], du - (du @ n) * n, n, eps
+
+    def friction_energy(self, x):
+        if self.fr is None:
+            return 0.0
+        e = 0.0
+        for v, lam, ut, n, eps in self._slips(x):
+            e += self.mu * lam * float(friction_f0(np.linalg.norm(ut), eps))
+        return e
+
+    def friction_terms(self, x, V):
+        """Friction gradient (V,3) and diagonal blocks (V,3,3)."""
+        g = np.zeros((V, 3))
+        H = np.zeros((V, 3, 3))
+        if self.fr is None:
+            return g, H
+        for v, lam, ut, n, eps in self._slips(x):
+            y = float(np.linalg.norm(ut))
+            P = np.eye(3) - np.outer(n, n)
+            fy = float(friction_f1_over_y(y, eps))
+            g[v] += self.mu * lam * fy * ut
+            # (f1' y - f1) / y^3: -1/(eps^2 y) below eps, -1/y^2 beyond (no term at y = 0)
+            c2 = 0.0 if y == 0.0 else (-1.0 / (eps * eps * y) if y < eps else -1.0 / (y ** 3))
+            H[v] += self.mu * lam * (fy * P + c2 * np.outer(ut, ut))
+        return g, H
+

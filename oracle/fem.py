@@ -134,9 +134,11 @@ class Mesh:
         self.contact = None   # oracle.contact.Contact when the IPC barrier is on (Sec. 7)
         self.rc = 0.0         # candidate radius of the step truncation
 
-    def enable_contact(self, planes, dhat, kappa, rc=None, use_penalty=False):
+    def enable_contact(self, planes, dhat, kappa, rc=None, use_penalty=False, friction_mu=0.0,
+                       friction_eps_v=1e-3):
         from . import contact
-        self.contact = contact.Contact(self.tets, self.X, planes, dhat, kappa, self.pinned, use_penalty)
+        self.contact = contact.Contact(self.tets, self.X, planes, dhat, kappa, self.pinned, use_penalty,
+                                       friction_mu, friction_eps_v)
         self.rc = 2.0 * dhat if rc is None else float(rc)
         return self
 
@@ -180,6 +182,7 @@ def energy(mesh: Mesh, x, z, h):
     e = el + float(np.sum(0.5 * mesh.mass[mesh.free] / h ** 2 * np.sum(d * d, axis=1)))
     if mesh.contact is not None:
         e += mesh.contact.energy(x, mesh.contact.pairs(x, mesh.contact.dhat))
+        e += mesh.contact.friction_energy(x)
     return e
 
 
@@ -194,6 +197,7 @@ def vertex_gradient(mesh: Mesh, x, z, h):
     if mesh.contact is not None:
         gb, _ = mesh.contact.vertex_terms(x, mesh.contact.pairs(x, mesh.contact.dhat), mesh.V)
         g += gb
+        g += mesh.contact.friction_terms(x, mesh.V)[0]
     g[mesh.pinned] = 0.0
     return g
 
@@ -227,6 +231,7 @@ def vertex_diag_blocks(mesh: Mesh, x, h):
     if mesh.contact is not None:
         _, Hb = mesh.contact.vertex_terms(x, mesh.contact.pairs(x, mesh.contact.dhat), mesh.V)
         Hd += Hb
+        Hd += mesh.contact.friction_terms(x, mesh.V)[1]
     return Hd
 
 

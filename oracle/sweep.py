@@ -205,9 +205,10 @@ def line_search(mesh: fem.Mesh, x, z, h, D, DJ, g, stats=None):
         dE = fem.energy_change(mesh, x, z, h, d, alphas)
         if cand is not None:
             # barrier change over the candidate pairs (truncation keeps every other pair
-            # outside dhat along the whole trial segment)
-            B0 = mesh.contact.energy(x, cand)
-            dE = [de + mesh.contact.energy(x + a * d, cand) - B0 for a, de in zip(alphas, dE)]
+            # outside dhat along the whole trial segment), plus the friction change (R25)
+            B0 = mesh.contact.energy(x, cand) + mesh.contact.friction_energy(x)
+            dE = [de + mesh.contact.energy(x + a * d, cand) + mesh.contact.friction_energy(x + a * d) - B0
+                  for a, de in zip(alphas, dE)]
         for a, de in zip(alphas, dE):
             if de <= ARMIJO_C * a * slope:
                 return a * d
@@ -252,6 +253,8 @@ def step(mesh: fem.Mesh, x_t, v_t, h, gravity, cub=None, rel_tol=1e-4, max_sweep
     and returns x^k (k sweeps applied)."""
     z = fem.inertia_target(x_t, v_t, h, gravity)
     x = np.array(x_t, dtype=np.float64, copy=True)
+    if mesh.contact is not None:
+        mesh.contact.lag_friction(x_t, h)  # lagged normal forces of this step (R25)
     L = length_scale if length_scale > 0 else float(np.max(mesh.X.max(axis=0) - mesh.X.min(axis=0)))
     stats = SweepStats()
     res = []

@@ -46,7 +46,7 @@ namespace {
 constexpr int kPW = 32;    // panel width (columns of L)
 constexpr int kCW = 32;    // right-hand-side columns per block
 constexpr int kRT = 64;    // rows per shared-memory tile
-constexpr int kRS = 1024;  // rows per work item at most
+constexpr int kRS = 256;   // rows per work item at most
 constexpr int kThreads = 256;
 static_assert(kPW == 32, "panel solves keep one panel row per lane");
 
@@ -164,6 +164,10 @@ __global__ void __launch_bounds__(kThreads) k_fwd_update(SolveDev d, int i0, flo
     xs[i][c] = (i < pw && c < cw) ? W[(size_t)(f3 + c0 + i) * k + col0 + c] : 0.f;
   }
   const int c = tid % 32, rg = tid / 32;
+  __syncthreads();
+  float xv[kPW];  // this thread's column of y_panel, in registers
+#pragma unroll
+  for (int j = 0; j < kPW; ++j) xv[j] = xs[j][c];
   for (int t0 = r0; t0 < r1; t0 += kRT) {
     const int nr = min(kRT, r1 - t0);
     __syncthreads();
@@ -171,8 +175,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd_update(SolveDev d, int i0, flo
     __syncthreads();
     for (int i = rg; i < nr; i += kThreads / 32) {
       float acc = 0.f;
-#pragma unroll 8
-      for (int j = 0; j < kPW; ++j) acc += Lt[i][j] * xs[j][c];
+#pragma unroll
+      for (int j = 0; j < kPW; ++j) acc += Lt[i][j] * xv[j];
       if (c < cw) {
         const int r = t0 + i;
         if (r < nJ)

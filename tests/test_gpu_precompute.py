@@ -7,7 +7,7 @@ of H_bar^{-1} agree with the host's to about kappa(H_bar) 1e-14: on the cube and
 the greedy sets (Eq. cubature_weight) are identical, and weights, U_bar rows (Eq. u) and fit
 residuals agree to 1e-7 relative (1e-6 on the free sphere, whose mass-only lowest modes
 make H_bar the worst conditioned). The sphere is large enough that the top separator's
-panels have more than 1024 rows below them, so the split forward updates and the backward
+panels have more than 256 rows below them, so the split forward updates and the backward
 partial sums run."""
 import numpy as np
 import pytest
