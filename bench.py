@@ -758,7 +758,7 @@ def main():
                          "per kernel (0)")
     ap.add_argument("--dx-tol", type=float, default=1e-3,
                     help="the paper's position-change tolerance on the unit-normalised scene")
-    ap.add_argument("--precompute-gpu", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--precompute-gpu", type=int, default=1, choices=[0, 1],
                     help="1: the precompute's multi-RHS solves run on the GPU (FP32 substitutions, FP64 refinement)")
     ap.add_argument("--n-spheres", type=int, default=10)
     ap.add_argument("--contact", type=int, default=1, choices=[0, 1, 2],

@@ -69,6 +69,16 @@ typedef struct {
   const double* planes;      /* [n_planes][4]: unit normal n (3) and offset c; may be NULL if 0 */
   double dhat;               /* barrier support d^ (m) > 0 */
   double kappa;              /* barrier or penalty stiffness (N/m) > 0 */
+  /* Friction on the walls (IPC's lagged friction potential; the paper's friction scenes).
+   * friction_mu >= 0 is the coefficient (0 = none; > 0 needs contact != 0); friction_eps_v
+   * > 0 the slip speed (m/s) below which friction is smoothed (slip eps = eps_v dt). At the
+   * start of every step, each free surface vertex v within dhat of wall p gets the lagged
+   * normal force lam = -kappa E'(d_vp(x_t)) (E the barrier or the penalty), and the step's
+   * energy adds mu lam f0(|P_p (x_v - x_t,v)|) per such pair, P_p = I - n n^T and
+   * f0(y) = -y^3/(3 eps^2) + y^2/eps + eps/3 below eps, y beyond. Vertex-face and edge-edge
+   * pairs carry no friction. Zero-initialised descriptions get no friction. */
+  double friction_mu;
+  double friction_eps_v;
 } jgs2_mesh_desc;
 
 typedef struct jgs2_mesh jgs2_mesh; /* opaque, library-owned */

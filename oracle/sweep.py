@@ -105,7 +105,8 @@ def coupled_local_terms(mesh: fem.Mesh, x, g, Hd):
     (d < dhat) with i, free, and S_i = {i} + P(i):
       g_i' = g_i^e + sum_{b in P(i)} g_b^e + sum_{pairs l of i} kappa B'(d_l) J_S,l
       H_i' = H_ii^e + sum_{b in P(i)} H_bb^e + sum_{pairs l of i} kappa B''(d_l) J_S,l J_S,l^T
-    where ^e drops the contact terms (elastic and inertial parts only) and J_S,l is the sum of
+    where ^e drops the contact terms (elastic and inertial parts only; vertex i's own wall friction
+    stays in its g_i^e, H_ii^e) and J_S,l is the sum of
     the pair's distance gradients over its vertices in S_i (zero for a vertex-face pair whose
     face lies on the other body: the pair moves rigidly in the sub-problem). The partners'
     other pairs and the elastic coupling between partners are left out. Returns {i: (g_i',
@@ -113,7 +114,8 @@ def coupled_local_terms(mesh: fem.Mesh, x, g, Hd):
     con = mesh.contact
     act = con.pairs(x, con.dhat)
     gb, Hb = con.vertex_terms(x, act, mesh.V)
-    ge, He = g - gb, Hd - Hb
+    gf, Hf = con.friction_terms(x, mesh.V)
+    ge, He = g - gb, Hd - Hb  # vertex i keeps its own wall friction (R25)
     body = mesh.body_of_vertex
     geo = {}
     by_vertex = {}
@@ -138,9 +140,9 @@ def coupled_local_terms(mesh: fem.Mesh, x, g, Hd):
             b2 = con.kappa * float(con.e2(np.array([d]), con.dhat)[0])
             gi += b1 * JS
             Hi += b2 * np.outer(JS, JS)
-        for b in P:
-            gi += ge[b]
-            Hi += He[b]
+        for b in P:  # partners: elastic and inertial parts only (their friction left out)
+            gi += ge[b] - gf[b]
+            Hi += He[b] - Hf[b]
         out[int(i)] = (gi, Hi)
     return out
 

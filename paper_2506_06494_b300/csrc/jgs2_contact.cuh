@@ -37,6 +37,25 @@ __device__ __forceinline__ double barrier_b2(double d, double dh, int pen = 0) {
   return -2.0 * log(d / dh) - 4.0 * e / d + e * e / (d * d);
 }
 
+// Friction on the walls (IPC's lagged friction potential): a surface vertex v within dhat of
+// wall p at the step start carries the lagged normal force lam = -kappa E'(d(x_t)), and the
+// step adds mu lam f0(|P_p (x_v - x_t,v)|), P_p = I - n n^T; f0 smooths |u| below the slip
+// eps: -y^3/(3 eps^2) + y^2/eps + eps/3 for y < eps, y beyond (C^1 at eps).
+__device__ __forceinline__ double fric_f0(double y, double e) {
+  return y < e ? -y * y * y / (3.0 * e * e) + y * y / e + e / 3.0 : y;
+}
+__device__ __forceinline__ double fric_f1_over_y(double y, double e) {
+  return y < e ? -y / (e * e) + 2.0 / e : 1.0 / y;
+}
+// tangential part P_p u of a displacement u at wall p (unit normal n)
+__device__ __forceinline__ void fric_tangential(const double* n, const double (&u)[3], double (&ut)[3]) {
+  const double un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+  ut[0] = u[0] - un * n[0];
+  ut[1] = u[1] - un * n[1];
+  ut[2] = u[2] - un * n[2];
+}
+__device__ __forceinline__ double fric_norm(const double (&a)[3]) { return sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]); }
+
 struct P3 {
   double x, y, z;
 };
@@ -802,7 +821,56 @@ __global__ void __launch_bounds__(128) k_couple(DevMesh<T> m, ContactView c, con
   for (int q = 0; q < 6; ++q) m.cpl[(3 + q) * S + i] = T(H[q]);
 }
 
-// barrier energy of the pairs at x^k (for jgs2_energy_gradient)
+// Friction terms at x^k, after k_pair_terms (thread per surface vertex): the gradient
+// mu lam f1(y)/y u_t and the diagonal block mu lam [(f1/y) P + ((f1' y - f1)/y^3) u_t u_t^T]
+// (positive semidefinite on both branches of f0), added to the vertex's contact sums.
+template <typename T>
+__global__ void __launch_bounds__(256) k_friction_terms(DevMesh<T> m, ContactView c, const StepState* st) {
+  if (st->done) return;
+  const size_t V = c.n_vertices;
+  const double e = c.feps;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < c.n_sverts; q += gridDim.x * blockDim.x) {
+    const int v = c.sverts[q];
+    if (v >= m.Vf) continue;
+    const Vec4<T> uv = m.u[v];
+    const double u[3] = {double(uv.x), double(uv.y), double(uv.z)};
+    for (int p = 0; p < c.n_planes; ++p) {
+      const double lam = c.fr_lam[(size_t)p * V + v];
+      if (!(lam > 0.0)) continue;
+      const double* n = c.planes + 4 * p;
+      double ut[3];
+      fric_tangential(n, u, ut);
+      const double y = fric_norm(ut);
+      const double k = c.fmu * lam, fy = fric_f1_over_y(y, e);
+      const double c2 = y == 0.0 ? 0.0 : (y < e ? -1.0 / (e * e * y) : -1.0 / (y * y * y));
+#pragma unroll
+      for (int a = 0; a < 3; ++a) c.bg[(size_t)a * V + v] += k * fy * ut[a];
+      // packed xx xy xz yy yz zz of k (fy (I - n n^T) + c2 ut ut^T)
+      const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        const int a = ia[r], b = ib[r];
+        c.bH[(size_t)r * V + v] += k * (fy * ((a == b ? 1.0 : 0.0) - n[a] * n[b]) + c2 * ut[a] * ut[b]);
+      }
+    }
+  }
+}
+
+// Friction energy of surface vertex v at displacement u (sum over its walls).
+__device__ __forceinline__ double fric_energy_at(const ContactView& c, int v, const double (&u)[3]) {
+  const size_t V = c.n_vertices;
+  double e = 0.0;
+  for (int p = 0; p < c.n_planes; ++p) {
+    const double lam = c.fr_lam[(size_t)p * V + v];
+    if (!(lam > 0.0)) continue;
+    double ut[3];
+    fric_tangential(c.planes + 4 * p, u, ut);
+    e += c.fmu * lam * fric_f0(fric_norm(ut), c.feps);
+  }
+  return e;
+}
+
+// barrier energy of the pairs at x^k, plus the friction energy (for jgs2_energy_gradient)
 template <typename T>
 __global__ void k_pair_energy(DevMesh<T> m, ContactView c, double* out) {
   __shared__ double red[32];
@@ -810,6 +878,15 @@ __global__ void k_pair_energy(DevMesh<T> m, ContactView c, double* out) {
   double acc[1] = {0.0};
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
     acc[0] += c.kappa * barrier_b(c.d0[q], c.dhat, c.pen);
+  if (c.fr_lam) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < c.n_sverts; q += gridDim.x * blockDim.x) {
+      const int v = c.sverts[q];
+      if (v >= m.Vf) continue;
+      const Vec4<T> uv = m.u[v];
+      const double u[3] = {double(uv.x), double(uv.y), double(uv.z)};
+      acc[0] += fric_energy_at(c, v, u);
+    }
+  }
   block_sum<1>(acc, red);
   if (threadIdx.x == 0) atomicAdd(out, acc[0]);
 }

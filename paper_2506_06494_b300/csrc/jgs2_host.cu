@@ -77,6 +77,7 @@ Mesh::~Mesh() {
   cudaFree(d_gbar);
   cudaFree(d_planes); cudaFree(d_d0); cudaFree(d_bg); cudaFree(d_bH); cudaFree(d_faces); cudaFree(d_edges);
   cudaFree(d_sverts); cudaFree(d_npairs); cudaFree(d_cflags); cudaFree(d_is_surf); cudaFree(d_pairs);
+  cudaFree(d_fr_lam);
   cudaFree(d_dmin); cudaFree(d_lim); cudaFree(d_body); cudaFree(d_vp_cnt); cudaFree(d_vp); cudaFree(d_cpl_on); cudaFree(d_frank); cudaFree(d_erank); cudaFree(d_hcnt); cudaFree(d_hblk);
   cudaFree(d_hids); cudaFree(d_hrec); cudaFree(d_hkey); cudaFree(d_fkeys); cudaFree(d_ekeys); cudaFree(d_pbp); cudaFree(d_dbp); cudaFree(d_ctl);
   cudaFree(d_pmarg); cudaFree(d_ppath);
@@ -266,6 +267,15 @@ jgs2_status mesh_create(const jgs2_mesh_desc* d, Mesh** out, const std::vector<i
   // contact surface (Sec. 7): boundary faces (used by one tet) oriented outward, their
   // edges and vertices, in internal vertex ids
   if (d->contact < 0 || d->contact > 2) return fail(JGS2_EINVAL, "contact must be 0, 1 (IPC) or 2 (penalty)");
+  if (!(d->friction_mu >= 0.0) || !std::isfinite(d->friction_mu))
+    return fail(JGS2_EINVAL, "friction_mu must be finite and >= 0");
+  if (d->friction_mu > 0.0) {
+    if (!d->contact) return fail(JGS2_EINVAL, "friction needs contact (the walls' normal forces)");
+    if (!(d->friction_eps_v > 0.0) || !std::isfinite(d->friction_eps_v))
+      return fail(JGS2_EINVAL, "friction_eps_v must be finite and > 0");
+    m->fmu = d->friction_mu;
+    m->feps_v = d->friction_eps_v;
+  }
   if (d->contact) {
     if (!(d->dhat > 0.0) || !(d->kappa > 0.0) || d->n_planes < 0 || (d->n_planes > 0 && !d->planes))
       return fail(JGS2_EINVAL, "contact needs dhat > 0, kappa > 0 and n_planes planes");
@@ -436,6 +446,11 @@ static jgs2_status ensure_device(Mesh* m) {
       // accumulators of non-surface vertices are never written: zero them once
       CK(cudaMemset(m->d_bg, 0, sizeof(double) * 3 * (size_t)V));
       CK(cudaMemset(m->d_bH, 0, sizeof(double) * 6 * (size_t)V));
+      if (m->fmu > 0.0 && !m->planes.empty()) {
+        const size_t nl = m->planes.size() / 4 * (size_t)V;
+        CK(dalloc(&m->d_fr_lam, nl));
+        CK(cudaMemset(m->d_fr_lam, 0, sizeof(double) * nl));
+      }
     }
     if (m->n_scenes > 0) {
       std::vector<int> vs(std::max(1, m->Vf)), ts(T);
@@ -629,6 +644,9 @@ static DevMesh<T> dev_view(Mesh* m) {
     c.body = m->d_body;
     c.vp_cnt = m->d_vp_cnt;
     c.vp = m->d_vp;
+    c.fmu = m->fmu;
+    c.feps = m->feps_v * m->h;
+    c.fr_lam = m->d_fr_lam;
   }
   d.n_scenes = m->n_scenes;
   d.v_scene = m->d_vscene;
@@ -709,7 +727,7 @@ jgs2_status import_cubature(Mesh* m, const jgs2_cubature_blob* b) {
 
 // Candidate pairs within r_c at x^k, the barrier accumulators and the per-vertex minimum
 // distances (Sec. 7). Pair order is not canonical here (the sums use atomics).
-constexpr int kContactKernels = 10;  // launches of one contact_pass
+constexpr int kContactKernels = 10;  // launches of one contact_pass (one more with wall friction)
 
 template <typename T>
 static jgs2_status contact_pass(Mesh* m, DevMesh<T>& d, cudaStream_t s, StepState* st) {
@@ -731,6 +749,8 @@ static jgs2_status contact_pass(Mesh* m, DevMesh<T>& d, cudaStream_t s, StepStat
   k_query_edges<T><<<grid(nE, 128), 128, 0, s>>>(d, c);
   // per sweep: barrier terms of the listed pairs at x^k (k_bp_check cleared the sums)
   k_pair_terms<T><<<grid(c.cap, 256), 256, 0, s>>>(d, c, st);
+  // wall friction (lagged at the step start) into the same per-vertex sums
+  if (c.fr_lam) k_friction_terms<T><<<grid(nS, 256), 256, 0, s>>>(d, c, st);
   CK(cudaGetLastError());
   return JGS2_OK;
 }
@@ -1036,7 +1056,8 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
       // contact pass (positions only) alongside the element pass; both feed the gather
       if (m->contact) {
         fork(m->gfork[0]);
-        group(JGS2_K_CONTACT, kContactKernels, s2, [&] { contact_pass<T>(m, d, s2, m->d_state); });
+        group(JGS2_K_CONTACT, kContactKernels + (m->d_fr_lam ? 1 : 0), s2,
+              [&] { contact_pass<T>(m, d, s2, m->d_state); });
       }
       if (nbV > 0) group(JGS2_K_ELEM, 1, s, [&] { k_elem<T, false><<<nbT, 128, 0, s>>>(d, m->d_state); });
       if (m->contact) join(m->gfork[1]);
@@ -1691,7 +1712,7 @@ jgs2_status mesh_create_batch(const jgs2_mesh_desc* ds, int n, Mesh** out) {
   int V = 0;
   for (int k = 0; k < n; ++k) {
     const jgs2_mesh_desc& d = ds[k];
-    if (d.contact) return fail(JGS2_EINVAL, "batch meshes do not support contact");
+    if (d.contact || d.friction_mu != 0.0) return fail(JGS2_EINVAL, "batch meshes do not support contact");
     if (d.dt != all.dt || d.gravity[0] != all.gravity[0] || d.gravity[1] != all.gravity[1] ||
         d.gravity[2] != all.gravity[2])
       return fail(JGS2_EINVAL, "all scenes of a batch must share dt and gravity");

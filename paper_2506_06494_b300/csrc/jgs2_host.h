@@ -103,6 +103,8 @@ struct Mesh {
   int contact = 0;
   int penalty = 0;                            // 1: quadratic penalty instead of the IPC barrier
   double dhat = 0.0, kappa = 0.0, rc = 0.0;
+  double fmu = 0.0, feps_v = 0.0;             // wall friction coefficient and smoothing slip speed
+  double* d_fr_lam = nullptr;                 // [n_planes][V] lagged normal forces (friction on)
   double bp_R = 0.0, bp_trig = 0.0;           // candidate-list radius and rebuild trigger
   int hbits = 0;                              // log2 buckets per hashed grid
   std::vector<double> planes;                 // [n][4]

@@ -144,6 +144,10 @@ struct ContactView {
   const int32_t* body = nullptr;  // [V]
   int32_t* vp_cnt = nullptr;      // [V]
   int32_t* vp = nullptr;          // [V][kMaxVertexPairs]
+  // friction on the walls (lagged at the step start): coefficient, smoothing slip
+  // eps_v h, and the lagged normal force of each (wall, vertex) [n_planes][V] (null: off)
+  double fmu = 0, feps = 0;
+  double* fr_lam = nullptr;
 };
 
 // Per-scene state of a batch mesh (one slot per scene; a single mesh is not batched).

@@ -861,6 +861,19 @@ __global__ void k_setup_vertices(DevMesh<T> m, const double* __restrict__ x_call
     d.w = T(0);
     m.dz[v] = d;
   }
+  if (m.c.fr_lam) {
+    // friction lagged at the step start: the normal force of each wall within dhat of a free
+    // surface vertex, -kappa E'(d(x_t)) (zero elsewhere)
+    for (int p = 0; p < m.c.n_planes; ++p) {
+      double lam = 0.0;
+      if (v < m.Vf && m.c.is_surf[v]) {
+        const double* pl = m.c.planes + 4 * p;
+        const double d = pl[0] * x[0] + pl[1] * x[1] + pl[2] * x[2] - pl[3];
+        if (d > 0.0 && d < m.c.dhat) lam = -m.c.kappa * barrier_b1(d, m.c.dhat, m.c.pen);
+      }
+      m.c.fr_lam[(size_t)p * m.V + v] = lam;
+    }
+  }
 }
 
 // F(x_t) per tet in FP64 from the FP64 step-start positions (no cancellation in FP32).
@@ -1491,6 +1504,31 @@ __global__ void __launch_bounds__(128) k_pair_trials(DevMesh<T> m, const StepSta
           P3 Jg[4];
           const double d = pair_geom(m, m.c, key, my_a, my_dir, vs, Jg, nv);
           acc += m.c.kappa * (barrier_b(d, m.c.dhat, m.c.pen) - barrier_b(dq, m.c.dhat, m.c.pen));
+        }
+      }
+    }
+  }
+  if (m.c.fr_lam) {
+    // friction change along the trial: mu lam (f0(|P(u + a d)|) - f0(|P u|)) per wall of
+    // every surface vertex with a lagged normal force
+    const size_t V = m.c.n_vertices;
+    for (int base = (blockIdx.x * (blockDim.x >> 5) + wid) * 32; base < m.c.n_sverts; base += nwarps * 32) {
+      const int q = base + lane;
+      const int v_own = q < m.c.n_sverts ? m.c.sverts[q] : -1;
+      bool has = false;
+      if (v_own >= 0 && v_own < m.Vf)
+        for (int p = 0; p < m.c.n_planes; ++p) has |= m.c.fr_lam[(size_t)p * V + v_own] > 0.0;
+      unsigned todo = __ballot_sync(0xffffffffu, has);
+      while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int v = __shfl_sync(0xffffffffu, v_own, src);
+        if (has_slot) {
+          const Vec4<T> uv = m.u[v], dv = my_dir[v];
+          const double u0[3] = {double(uv.x), double(uv.y), double(uv.z)};
+          const double u1[3] = {u0[0] + my_a * double(dv.x), u0[1] + my_a * double(dv.y),
+                                u0[2] + my_a * double(dv.z)};
+          acc += fric_energy_at(m.c, v, u1) - fric_energy_at(m.c, v, u0);
         }
       }
     }

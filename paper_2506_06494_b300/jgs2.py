@@ -32,7 +32,8 @@ class MeshDesc(C.Structure):
                 ("density", C.POINTER(C.c_double)), ("pinned", C.POINTER(C.c_uint8)),
                 ("gravity", C.c_double * 3), ("dt", C.c_double),
                 ("contact", C.c_int32), ("n_planes", C.c_int32), ("planes", C.POINTER(C.c_double)),
-                ("dhat", C.c_double), ("kappa", C.c_double)]
+                ("dhat", C.c_double), ("kappa", C.c_double),
+                ("friction_mu", C.c_double), ("friction_eps_v", C.c_double)]
 
 
 class PrecomputeOpts(C.Structure):
@@ -190,7 +191,8 @@ def _dev(t):
     return C.c_void_p(t.data_ptr())
 
 
-def _desc(X, tets, youngs, poisson, density, pinned, gravity, dt, planes, dhat, kappa, contact, keep):
+def _desc(X, tets, youngs, poisson, density, pinned, gravity, dt, planes, dhat, kappa, contact, keep,
+          friction_mu=0.0, friction_eps_v=1e-3):
     arrs = [np.ascontiguousarray(X, dtype=np.float64),
             np.ascontiguousarray(tets, dtype=np.int32),
             np.ascontiguousarray(youngs, dtype=np.float64),
@@ -217,6 +219,8 @@ def _desc(X, tets, youngs, poisson, density, pinned, gravity, dt, planes, dhat, 
     d.planes = _ptr(pl, C.c_double)
     d.dhat = float(dhat)
     d.kappa = float(kappa)
+    d.friction_mu = float(friction_mu)
+    d.friction_eps_v = float(friction_eps_v)
     return d
 
 
@@ -260,9 +264,10 @@ class Mesh:
         return tuple(int(c) for c in cfg)
 
     def __init__(self, X, tets, youngs, poisson, density, pinned=None, gravity=(0, 0, -9.8), dt=1 / 120,
-                 planes=None, dhat=1e-3, kappa=1e5, contact=0):
+                 planes=None, dhat=1e-3, kappa=1e5, contact=0, friction_mu=0.0, friction_eps_v=1e-3):
         self._keep = []
-        d = _desc(X, tets, youngs, poisson, density, pinned, gravity, dt, planes, dhat, kappa, contact, self._keep)
+        d = _desc(X, tets, youngs, poisson, density, pinned, gravity, dt, planes, dhat, kappa, contact, self._keep,
+                  friction_mu, friction_eps_v)
         h = C.c_void_p()
         _check(lib().jgs2_mesh_create(C.byref(d), C.byref(h)))
         self.handle = h
@@ -270,10 +275,10 @@ class Mesh:
         self.T = int(d.n_tets)
 
     @classmethod
-    def from_scene(cls, s, contact=None):
+    def from_scene(cls, s, contact=None, friction_mu=0.0, friction_eps_v=1e-3):
         c = s.contact if contact is None else contact
         return cls(s.X, s.tets, s.youngs, s.poisson, s.density, s.pinned, s.gravity, s.dt,
-                   s.planes, s.dhat, s.kappa, c)
+                   s.planes, s.dhat, s.kappa, c, friction_mu, friction_eps_v)
 
     def contact_pairs(self, x_t, x, radius, cap=1 << 20, stream=None):
         """Canonical candidate pair rows (kind, a, b, c, d) within radius (jgs2_contact_pairs)."""

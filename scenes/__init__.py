@@ -313,6 +313,19 @@ def drop_scene(nv=4, size=0.02, gap=5e-4, speed=0.3, E=1e5, dhat=1e-3, kappa=1e4
                  np.zeros(len(X), np.uint8), v0, planes=box_planes(), dhat=dhat, kappa=kappa, contact=1)
 
 
+def slide_scene(nv=3, size=0.02, gap=9.8e-4, speed=0.5, E=1e5, dhat=1e-3, kappa=1e4):
+    """A small free block resting within dhat of the floor (the gap puts the barrier force
+    near its weight), sliding along it: exercises wall friction."""
+    X, tets = kuhn_grid(nv, nv, nv, (size, size, size))
+    X = X + np.array([0.3, 0.3, gap])
+    T = len(tets)
+    v0 = np.zeros_like(X)
+    v0[:, 0] = speed
+    v0[:, 1] = 0.4 * speed
+    return Scene("slide", X, tets, np.full(T, E), np.full(T, 0.4), np.full(T, 1000.0),
+                 np.zeros(len(X), np.uint8), v0, planes=box_planes(), dhat=dhat, kappa=kappa, contact=1)
+
+
 def stack_scene(nv=3, size=0.02, gap=1.5e-3, speed=0.3, E=1e5, dhat=1e-3, kappa=1e4):
     """Two small blocks, the upper one moving down onto the lower one resting on the floor
     (vertex-face and edge-edge pairs between bodies, and the floor)."""

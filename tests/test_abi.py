@@ -56,7 +56,8 @@ def _desc(X, T, E, nu, rho, pin=None, dt=1 / 120):
     return d
 
 
-@pytest.mark.parametrize("case", ["inverted", "index", "material", "dt", "empty", "isolated"])
+@pytest.mark.parametrize("case", ["inverted", "index", "material", "dt", "empty", "isolated", "friction_neg",
+                                  "friction_no_contact", "friction_eps"])
 def test_mesh_create_rejects_bad_input(L, case):
     s = scenes.cube_scene()
     X = s.X.copy()
@@ -76,6 +77,13 @@ def test_mesh_create_rejects_bad_input(L, case):
     d = _desc(X, T, E, nu, rho, None, dt)
     if case == "empty":
         d.n_tets = 0
+    elif case == "friction_neg":
+        d.friction_mu = -0.1
+    elif case == "friction_no_contact":  # friction needs the walls' normal forces
+        d.friction_mu, d.friction_eps_v = 0.5, 1e-3
+    elif case == "friction_eps":
+        d.contact, d.dhat, d.kappa = 1, 1e-3, 1e5
+        d.friction_mu, d.friction_eps_v = 0.5, 0.0
     h = C.c_void_p()
     st = L.jgs2_mesh_create(C.byref(d), C.byref(h))
     assert st == 1  # JGS2_EINVAL, raised before any device allocation
