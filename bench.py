@@ -404,7 +404,9 @@ def run_jgs2(args, rank, world, local_rank):
     T = sum(s.n_tets for s in ss)
     Vf = int((~pin.astype(bool)).sum())
     t0 = time.perf_counter()
-    mesh = p.Mesh.batch(ss) if batch else p.Mesh.from_scene(ss[0])
+    if args.friction > 0 and (batch or not ss[0].contact):
+        raise SystemExit("--friction needs a single scene with contact (the spheres workload)")
+    mesh = p.Mesh.batch(ss) if batch else p.Mesh.from_scene(ss[0], friction_mu=args.friction)
     gs = bool(args.gs)
     if gs and (batch or (args.workload == "spheres" and args.contact)):
         raise SystemExit("--gs takes a single scene without contact")
@@ -491,6 +493,7 @@ def run_jgs2(args, rank, world, local_rank):
                    "correction": args.correction, "line_search": True, "n_cub": args.n_cub, "rel_tol": 1e-4,
                    "parallelisation": "Gauss-Seidel (greedy colouring, group subspaces)" if gs else "Jacobi",
                    "contact_coupling": bool(args.coupling),
+                   "wall_friction_mu": args.friction,
                    "max_sweeps": args.max_sweeps, "block_size": bs,
                    "batch_launch": ("persistent cooperative launch per chunk" if args.persistent else
                                     "one launch per kernel, graph-captured chunks") if batch else None,
@@ -758,6 +761,8 @@ def main():
                          "per kernel (0)")
     ap.add_argument("--dx-tol", type=float, default=1e-3,
                     help="the paper's position-change tolerance on the unit-normalised scene")
+    ap.add_argument("--friction", type=float, default=0.0,
+                    help="wall friction coefficient on the spheres workload (lagged IPC friction; 0 = none)")
     ap.add_argument("--precompute-gpu", type=int, default=1, choices=[0, 1],
                     help="1: the precompute's multi-RHS solves run on the GPU (FP32 substitutions, FP64 refinement)")
     ap.add_argument("--n-spheres", type=int, default=10)
