@@ -756,9 +756,9 @@ def main():
                     help="1: contact-aware correction (Sec. 7 two-way coupling across bodies in contact)")
     ap.add_argument("--gs", type=int, default=0,
                     help="1: Gauss-Seidel steps (greedy colouring, group precompute) on a single scene without contact")
-    ap.add_argument("--persistent", type=int, default=1,
+    ap.add_argument("--persistent", type=int, default=0,
                     help="batch workload: one persistent cooperative launch per chunk of sweeps (1) or one launch "
-                         "per kernel (0)")
+                         "per kernel in graph-captured chunks (0, the faster on B300)")
     ap.add_argument("--dx-tol", type=float, default=1e-3,
                     help="the paper's position-change tolerance on the unit-normalised scene")
     ap.add_argument("--friction", type=float, default=0.0,

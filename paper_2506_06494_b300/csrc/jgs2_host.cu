@@ -919,7 +919,7 @@ static int energy_blocks() {
     int dev = 0, sms = 148, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_energy<T, DIR>, DIR == 2 ? 256 : 128, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_energy<T, DIR>, 128, 0) !=
         cudaSuccess)
       per_sm = 1;
     nb = std::max(1, std::min(sms * std::max(1, per_sm), kEnergyBlocksMax));
@@ -1103,7 +1103,7 @@ static jgs2_status run_sweeps(Mesh* m, const jgs2_step_opts& o, cudaStream_t cs,
                 [&] { k_ls_decide<1><<<1, 1024, 0, s>>>(m->d_state, 1, m->d_partial, nbE1, pp, npp); });
           if (m->contact)
             group(JGS2_K_LS_PAIRS, 1, s, [&] { k_pair_trials<T, 2><<<npp, 128, 0, s>>>(d, m->d_state, pp); });
-          group(JGS2_K_ENERGY, 1, s, [&] { k_energy<T, 2><<<nbE2, 256, 0, s>>>(d, m->d_state, m->d_partial); });
+          group(JGS2_K_ENERGY, 1, s, [&] { k_energy<T, 2><<<nbE2, 128, 0, s>>>(d, m->d_state, m->d_partial); });
           group(JGS2_K_LS_DECIDE, 1, s,
                 [&] { k_ls_decide<2><<<1, 1024, 0, s>>>(m->d_state, 1, m->d_partial, nbE2, pp, npp); });
         }

@@ -1545,26 +1545,24 @@ __global__ void __launch_bounds__(128) k_pair_trials(DevMesh<T> m, const StepSta
 
 // Line search (reading R17), passes as in ls_pass_runs: DIR 0 along the sweep direction D,
 // DIR 1 along the uncorrected direction D_J (only when every trial along D failed), DIR 2
-// along both in one pass: a 256-thread block whose two halves take one direction each over
-// the same staged tile (each half holds the accumulators of one direction, as a one-direction
-// pass does). The energy change along a direction is a polynomial in the step a; its
-// coefficients are summed over tets (tiles of 128 records brought into shared memory by bulk
-// copies, double-buffered in FP32) and free vertices, per thread and per block with Acc<T>
-// (FP64-class), into per-block partials [6 ND][grid]; k_ls_decide adds them up and decides.
+// along both in one pass (the tile loads, F and the displacement gathers are shared). The
+// energy change along a direction is a polynomial in the step a; its coefficients are
+// summed over tets (tiles of 128 records brought into shared memory by bulk copies,
+// double-buffered in FP32) and free vertices, per thread and per block with Acc<T>
+// (FP64-class), into per-block partials; k_ls_decide adds them up and decides.
 template <typename T, int DIR>
-__global__ void __launch_bounds__(DIR == 2 ? 256 : 128)
-    k_energy(DevMesh<T> m, StepState* st, double* __restrict__ partial /* [6 ND][grid] */) {
+__global__ void __launch_bounds__(128) k_energy(DevMesh<T> m, StepState* st,
+                                                double* __restrict__ partial /* [6 ND][grid] */) {
   if (!ls_pass_runs<DIR>(st)) return;
-  constexpr int NH = DIR == 2 ? 2 : 1;  // 128-thread halves, one per direction
-  constexpr int NC = 6;
+  constexpr int ND = DIR == 2 ? 2 : 1;
+  constexpr int NC = 6 * ND;
   // tiles of 128 records arrive by bulk copy; FP32 double-buffers them (the next tile is in
   // flight while this one is evaluated), FP64 (records twice as large) uses one buffer
   constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;
   __shared__ __align__(128) TetRec<T> srec[NBUF][128];
   __shared__ __align__(8) uint64_t bar[NBUF];
-  __shared__ Acc<T> sacc[8 * NC];
-  const int half = NH == 2 ? (int)threadIdx.x / 128 : 0, lt = (int)threadIdx.x % 128;
-  const Vec4<T>* dir = (DIR == 1 || half == 1) ? m.DJ : m.D;
+  __shared__ Acc<T> sacc[32 * NC];
+  const Vec4<T>* dirs[2] = {DIR == 1 ? m.DJ : m.D, m.DJ};
   Acc<T> acc[NC];
   const int ntile = (m.T_ + 127) / 128;
   if (threadIdx.x == 0) {
@@ -1598,61 +1596,52 @@ __global__ void __launch_bounds__(DIR == 2 ? 256 : 128)
       return;
     }
     const TetRec<T>* srec_b = srec[b];
-    if (lt < n) {
+    if ((int)threadIdx.x < n) {
       // F_e(x^k) is recomputed from the staged record and the corners' displacements
       // (L2-resident) rather than read back from the element pass, whose records have
       // left L2 by now
-      const TetRec<T>& r = srec_b[lt];
-      T F[9], C[9], J1, dF[9], c[6];
+      const TetRec<T>& r = srec_b[threadIdx.x];
+      T F[9], C[9], J1;
       tet_F_jm1(r, m.u, F, J1);
       cofactor(F, C);
-      tet_dF(r, dir, m.Vf, dF);
-      tet_dpsi_poly(r, F, C, J1, dF, c);
 #pragma unroll
-      for (int j = 0; j < 6; ++j) acc[j].add(c[j]);
+      for (int dd = 0; dd < ND; ++dd) {
+        T dF[9], c[6];
+        tet_dF(r, dirs[dd], m.Vf, dF);
+        tet_dpsi_poly(r, F, C, J1, dF, c);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc[6 * dd + j].add(c[j]);
+      }
     }
     __syncthreads();  // buffer b is read; it may be refilled
     if (NBUF == 1) issue(tile + gridDim.x, 0);
   }
   // inertia: m/(2h^2) (2 a d.(u - dz) + a^2 |d|^2)
-  const int stride = gridDim.x * 128;
-  for (int v = blockIdx.x * 128 + lt; v < m.Vf; v += stride) {
-    T uv[3], dz[3], d[3];
+  const int stride = gridDim.x * blockDim.x;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < m.Vf; v += stride) {
+    T uv[3], dz[3];
     load3(m.u, v, uv);
     load3(m.dz, v, dz);
-    load3(dir, v, d);
     const T mh = m.mh2[v];
-    T dd = T(0), de = T(0);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      dd += d[q] * d[q];
-      de += d[q] * (uv[q] - dz[q]);
+    for (int di = 0; di < ND; ++di) {
+      T d[3];
+      load3(dirs[di], v, d);
+      T dd = T(0), de = T(0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        dd += d[q] * d[q];
+        de += d[q] * (uv[q] - dz[q]);
+      }
+      acc[6 * di].add(mh * de);
+      acc[6 * di + 1].add(T(0.5) * mh * dd);
     }
-    acc[0].add(mh * de);
-    acc[1].add(T(0.5) * mh * dd);
   }
-  // fixed-order block sums, per half: warp shuffles, then the half's first warp adds its
-  // four warps' sums
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double bs[NC];
+  block_sum_acc<T, NC>(acc, bs, sacc);
+  if (threadIdx.x == 0) {
 #pragma unroll
-  for (int j = 0; j < NC; ++j)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[j].add_lane(o);
-  if (lane == 0) {
-#pragma unroll
-    for (int j = 0; j < NC; ++j) sacc[j * 8 + wid] = acc[j];
-  }
-  __syncthreads();
-  if (wid % 4 == 0) {
-    const int h = wid / 4;
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-      Acc<T> x;
-      if (lane < 4) x = sacc[j * 8 + 4 * h + lane];
-#pragma unroll
-      for (int o = 2; o > 0; o >>= 1) x.add_lane(o);
-      if (lane == 0) partial[(size_t)(6 * h + j) * gridDim.x + blockIdx.x] = x.value();
-    }
+    for (int j = 0; j < NC; ++j) partial[(size_t)j * gridDim.x + blockIdx.x] = bs[j];
   }
 }
 
