@@ -338,3 +338,48 @@ def stack_scene(nv=3, size=0.02, gap=1.5e-3, speed=0.3, E=1e5, dhat=1e-3, kappa=
     v0[len(X):, 2] = -speed
     return Scene("stack", Xa, ta, np.full(T, E), np.full(T, 0.4), np.full(T, 1000.0),
                  np.zeros(len(Xa), np.uint8), v0, planes=box_planes(), dhat=dhat, kappa=kappa, contact=1)
+
+
+@dataclass
+class ClothScene:
+    """A triangle-mesh cloth. Arrays are in the generator's vertex order."""
+    name: str
+    X: np.ndarray            # (V,3) float64 rest positions, also the initial positions
+    tris: np.ndarray         # (F,3) int32
+    youngs: float            # Pa
+    poisson: float
+    thickness: float         # m
+    density: float           # kg/m^3
+    bend: float              # bending stiffness (N m)
+    pinned: np.ndarray       # (V,) uint8
+    v0: np.ndarray           # (V,3)
+    dt: float = 1.0 / 120.0
+    gravity: tuple = (0.0, 0.0, -9.8)
+
+
+def cloth_grid(n, size):
+    """n x n vertices on a flat square of side `size` in the z = 0 plane, every cell split
+    into two triangles along alternating diagonals."""
+    g = np.linspace(0.0, size, n)
+    X = np.stack(np.meshgrid(g, g, indexing="ij"), -1).reshape(-1, 2)
+    X = np.hstack([X, np.zeros((len(X), 1))])
+    tris = []
+    for i in range(n - 1):
+        for j in range(n - 1):
+            a, b, c, d = i * n + j, (i + 1) * n + j, (i + 1) * n + j + 1, i * n + j + 1
+            if (i + j) % 2 == 0:
+                tris += [(a, b, c), (a, c, d)]
+            else:
+                tris += [(a, b, d), (b, c, d)]
+    return X, np.array(tris, dtype=np.int32)
+
+
+def cloth_scene(n=21, size=0.5, youngs=1e6, thickness=5e-4, bend=1e-5, seed=0, vel_sigma=0.0):
+    """A square cloth held at two adjacent corners, released flat under gravity."""
+    X, tris = cloth_grid(n, size)
+    pinned = np.zeros(len(X), np.uint8)
+    pinned[0] = pinned[(n - 1) * n] = 1
+    v0 = np.random.default_rng(seed).normal(0.0, vel_sigma, X.shape) if vel_sigma > 0 else np.zeros_like(X)
+    v0[pinned.astype(bool)] = 0.0
+    return ClothScene("cloth", X, tris, youngs, 0.3, thickness, 200.0, bend, pinned, v0)
+
