@@ -390,6 +390,76 @@ jgs2_status jgs2_contact_pairs(jgs2_mesh* mesh, const double* x_t, const double*
  * receives GFLOP/s (2 per FMA). Allocates a small device buffer; synchronises the stream. */
 jgs2_status jgs2_alu_peak(int32_t precision, double* gflops, void* stream);
 
+/* ---------------------------------------------------------------------------------
+ * Cloth (the cloth material of the paper's Table 1 caption; reading R26): StVK membrane
+ * triangles and a quadratic bending energy on interior edges, stepped by the per-vertex
+ * Jacobi sweep with the global Armijo line search. No cubature correction (its records are
+ * built on tets) and no contact. Vertices keep the caller's order.
+ *  - Membrane: per triangle, F = [x_1 - x_0, x_2 - x_0] D_m^-1 (3x2, D_m the rest edges in
+ *    the triangle's plane), E = (F^T F - I)/2, energy A (mu tr(E^2) + lam/2 tr(E)^2) with
+ *    mu = Y t / (2 (1 + nu)), lam = Y t nu / (1 - nu^2).
+ *  - Bending: per interior edge (x_0, x_1) with opposite vertices x_2 (first triangle in
+ *    triangle order) and x_3, rest cotangent weights K = (cot a_1 + cot c_1, cot a_0 + cot c_0,
+ *    -(cot a_0 + cot a_1), -(cot c_0 + cot c_1)) (a_j: rest angle at x_j in (x_0, x_1, x_2),
+ *    c_j: in (x_0, x_1, x_3)); energy (3 k_b / (A_0 + A_1)) |sum_i K_i x_i|^2 / 2.
+ *  - Mass rho t A / 3 per corner; inertia and gravity as for the solids (Sec. 3).
+ *  - Local system per free vertex: inertia + the positive semidefinite part of the summed
+ *    membrane blocks + the bending blocks. */
+typedef struct {
+  int32_t n_vertices;        /* V > 0 */
+  int32_t n_tris;            /* F > 0 */
+  const double* rest_pos;    /* [V][3] rest positions (m); also the usual initial state */
+  const int32_t* tris;       /* [F][3] vertex indices; every triangle must have positive area */
+  double youngs;             /* Y (Pa) > 0 */
+  double poisson;            /* nu in (-1, 0.5) */
+  double thickness;          /* t (m) > 0 */
+  double density;            /* rho (kg/m^3) > 0 */
+  double bend;               /* k_b (N m) >= 0 */
+  const uint8_t* pinned;     /* [V] 1 = held at x_t; may be NULL */
+  double gravity[3];
+  double dt;                 /* h (s) > 0 */
+} jgs2_cloth_desc;
+
+typedef struct jgs2_cloth jgs2_cloth;
+
+typedef struct {
+  int32_t sweeps;            /* sweeps applied */
+  int32_t converged;         /* 1 if rel_tol was reached */
+  int32_t ls_rejects;        /* sweeps where no trial satisfied Armijo (no move) */
+  int32_t pad_;
+  double rel_residual;       /* |g(x_{t+1})| / |g(x_t)| over free DOFs */
+  double g0;                 /* |g(x_t)| */
+} jgs2_cloth_report;
+
+/* Validates the cloth (indices in range, positive areas, material ranges, every free vertex
+ * in a triangle; JGS2_EINVAL otherwise), computes the rest data in FP64 on the host and
+ * finds the interior edges. Device memory is taken on the first call that needs it, on
+ * the then-current device (later calls must use the same device). */
+jgs2_status jgs2_cloth_create(const jgs2_cloth_desc* desc, jgs2_cloth** out);
+
+/* One implicit-Euler step: x, v device [V][3] double (caller order), overwritten with
+ * x_{t+1}, v_{t+1} = (x_{t+1} - x_t)/h. Uses opts->precision, max_sweeps, rel_tol,
+ * line_search and check_every (sweeps between host checks of the stopping test); the
+ * other options are ignored. JGS2_ENOTCONVERGED when the cap was reached (state written),
+ * JGS2_EDIVERGED if the residual became NaN/Inf. Synchronises the stream. */
+jgs2_status jgs2_cloth_step(jgs2_cloth* cloth, double* x, double* v, const jgs2_step_opts* opts, void* stream,
+                            jgs2_cloth_report* report);
+
+/* Exactly n sweeps from x (device [V][3] double, overwritten) for the step starting at
+ * (x_t, v_t); for parity tests. Synchronises the stream. */
+jgs2_status jgs2_cloth_sweeps(jgs2_cloth* cloth, const double* x_t, const double* v_t, double* x, int32_t n,
+                              const jgs2_step_opts* opts, void* stream);
+
+/* E(x) and g(x) (FP64) of the step starting at (x_t, v_t): energy host pointer, g device
+ * [V][3] (zero rows for pinned vertices); either may be NULL, not both. Synchronises. */
+jgs2_status jgs2_cloth_energy_gradient(jgs2_cloth* cloth, const double* x_t, const double* v_t, const double* x,
+                                       double* energy, double* g, void* stream);
+
+/* Interior edges (bending hinges) the cloth found at create. */
+int32_t jgs2_cloth_n_hinges(const jgs2_cloth* cloth);
+
+void jgs2_cloth_destroy(jgs2_cloth* cloth);
+
 void jgs2_mesh_destroy(jgs2_mesh* mesh);
 const char* jgs2_last_error(void);
 

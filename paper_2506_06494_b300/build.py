@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libjgs2.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["jgs2_host.cu", "jgs2_precompute.cpp", "jgs2_static.cu", "jgs2_peaks.cu", "jgs2_gpu_solve.cu"]
+SOURCES = ["jgs2_host.cu", "jgs2_precompute.cpp", "jgs2_static.cu", "jgs2_peaks.cu", "jgs2_gpu_solve.cu", "jgs2_cloth.cu"]
 
 
 def sources():

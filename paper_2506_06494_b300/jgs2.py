@@ -36,6 +36,19 @@ class MeshDesc(C.Structure):
                 ("friction_mu", C.c_double), ("friction_eps_v", C.c_double)]
 
 
+class ClothDesc(C.Structure):
+    _fields_ = [("n_vertices", C.c_int32), ("n_tris", C.c_int32),
+                ("rest_pos", C.POINTER(C.c_double)), ("tris", C.POINTER(C.c_int32)),
+                ("youngs", C.c_double), ("poisson", C.c_double), ("thickness", C.c_double),
+                ("density", C.c_double), ("bend", C.c_double), ("pinned", C.POINTER(C.c_uint8)),
+                ("gravity", C.c_double * 3), ("dt", C.c_double)]
+
+
+class ClothReport(C.Structure):
+    _fields_ = [("sweeps", C.c_int32), ("converged", C.c_int32), ("ls_rejects", C.c_int32), ("pad_", C.c_int32),
+                ("rel_residual", C.c_double), ("g0", C.c_double)]
+
+
 class PrecomputeOpts(C.Structure):
     _fields_ = [("n_cub", C.c_int32), ("n_train", C.c_int32), ("n_cand", C.c_int32),
                 ("n_pool", C.c_int32), ("nnls_tol", C.c_double), ("seed", C.c_uint64),
@@ -85,7 +98,8 @@ EXPORTS = ["jgs2_precompute_opts_default", "jgs2_step_opts_default", "jgs2_mesh_
            "jgs2_energy_gradient", "jgs2_energy_gradient_static", "jgs2_contact_pairs",
            "jgs2_step_adjoint", "jgs2_adjoint_opts_default", "jgs2_mesh_set_youngs",
            "jgs2_mesh_create_batch", "jgs2_batch_report", "jgs2_autotune", "jgs2_mesh_launch_config", "jgs2_alu_peak",
-           "jgs2_mesh_destroy", "jgs2_last_error"]
+           "jgs2_cloth_create", "jgs2_cloth_step", "jgs2_cloth_sweeps", "jgs2_cloth_energy_gradient",
+           "jgs2_cloth_n_hinges", "jgs2_cloth_destroy", "jgs2_mesh_destroy", "jgs2_last_error"]
 
 
 def lib():
@@ -121,10 +135,18 @@ def lib():
     L.jgs2_alu_peak.argtypes = [C.c_int32, C.POINTER(C.c_double), P]
     L.jgs2_mesh_launch_config.argtypes = [P, C.c_int32, P]
     L.jgs2_mesh_destroy.argtypes = [P]
+    L.jgs2_cloth_create.argtypes = [C.POINTER(ClothDesc), C.POINTER(P)]
+    L.jgs2_cloth_step.argtypes = [P, P, P, C.POINTER(StepOpts), P, C.POINTER(ClothReport)]
+    L.jgs2_cloth_sweeps.argtypes = [P, P, P, P, C.c_int32, C.POINTER(StepOpts), P]
+    L.jgs2_cloth_energy_gradient.argtypes = [P, P, P, P, P, P, P]
+    L.jgs2_cloth_n_hinges.argtypes = [P]
+    L.jgs2_cloth_n_hinges.restype = C.c_int32
+    L.jgs2_cloth_destroy.argtypes = [P]
     L.jgs2_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("jgs2_mesh_destroy", "jgs2_last_error", "jgs2_mesh_n_cub",
-                        "jgs2_precompute_opts_default", "jgs2_step_opts_default", "jgs2_adjoint_opts_default"):
+        if name not in ("jgs2_mesh_destroy", "jgs2_last_error", "jgs2_mesh_n_cub", "jgs2_cloth_destroy",
+                        "jgs2_cloth_n_hinges", "jgs2_precompute_opts_default", "jgs2_step_opts_default",
+                        "jgs2_adjoint_opts_default"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -385,3 +407,67 @@ class Mesh:
         _check(lib().jgs2_energy_gradient(self.handle, _dev(x_t), _dev(v_t), _dev(x), C.byref(E), _dev(g),
                                           C.c_void_p(_stream_ptr(stream))))
         return E.value, g
+
+
+class Cloth:
+    """A cloth (jgs2_cloth_*): StVK membrane triangles, quadratic bending, Jacobi sweeps."""
+
+    def __init__(self, X, tris, youngs, poisson, thickness, density, bend, pinned=None, gravity=(0, 0, -9.8),
+                 dt=1 / 120):
+        self._keep = [np.ascontiguousarray(X, dtype=np.float64), np.ascontiguousarray(tris, dtype=np.int32),
+                      None if pinned is None else np.ascontiguousarray(pinned, dtype=np.uint8)]
+        Xa, Ta, Pa = self._keep
+        d = ClothDesc()
+        d.n_vertices, d.n_tris = Xa.shape[0], Ta.shape[0]
+        d.rest_pos = _ptr(Xa, C.c_double)
+        d.tris = _ptr(Ta, C.c_int32)
+        d.youngs, d.poisson, d.thickness = float(youngs), float(poisson), float(thickness)
+        d.density, d.bend = float(density), float(bend)
+        d.pinned = _ptr(Pa, C.c_uint8) if Pa is not None else C.POINTER(C.c_uint8)()
+        for q in range(3):
+            d.gravity[q] = float(gravity[q])
+        d.dt = float(dt)
+        h = C.c_void_p()
+        _check(lib().jgs2_cloth_create(C.byref(d), C.byref(h)))
+        self.handle = h
+        self.V = int(d.n_vertices)
+
+    @classmethod
+    def from_scene(cls, s):
+        return cls(s.X, s.tris, s.youngs, s.poisson, s.thickness, s.density, s.bend, s.pinned, s.gravity, s.dt)
+
+    @property
+    def n_hinges(self):
+        return int(lib().jgs2_cloth_n_hinges(self.handle))
+
+    def step(self, x, v, opts=None, stream=None):
+        """jgs2_cloth_step on float64 CUDA tensors x, v [V,3] (updated in place)."""
+        rep = ClothReport()
+        st = lib().jgs2_cloth_step(self.handle, _dev(x), _dev(v), C.byref(opts or step_opts()),
+                                   C.c_void_p(_stream_ptr(stream)), C.byref(rep))
+        _check(st, ok=(0, 5))
+        return rep
+
+    def sweeps(self, x_t, v_t, x, n, opts=None, stream=None):
+        _check(lib().jgs2_cloth_sweeps(self.handle, _dev(x_t), _dev(v_t), _dev(x), int(n),
+                                       C.byref(opts or step_opts()), C.c_void_p(_stream_ptr(stream))))
+
+    def energy_gradient(self, x_t, v_t, x, stream=None):
+        import torch
+        g = torch.empty_like(x)
+        E = C.c_double()
+        _check(lib().jgs2_cloth_energy_gradient(self.handle, _dev(x_t), _dev(v_t), _dev(x), C.byref(E), _dev(g),
+                                                C.c_void_p(_stream_ptr(stream))))
+        return E.value, g
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().jgs2_cloth_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

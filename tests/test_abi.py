@@ -184,3 +184,34 @@ def test_gs_step_rejects_contact_and_batches(L):
     batch = p.Mesh.batch([scenes.cube_scene(), scenes.cube_scene()])
     assert L.jgs2_step_gs(batch.handle, ptr, ptr, C.byref(opts), None, None) == 1
     batch.close()
+
+
+@pytest.mark.parametrize("case", ["index", "degenerate", "material", "dt", "isolated"])
+def test_cloth_create_rejects_bad_input(case):
+    s = scenes.cloth_scene(n=4)
+    X, T = s.X.copy(), s.tris.copy()
+    kw = dict(youngs=s.youngs, poisson=s.poisson, thickness=s.thickness, density=s.density, bend=s.bend, dt=s.dt)
+    if case == "index":
+        T[3, 1] = len(X)
+    elif case == "degenerate":
+        T[2, 2] = T[2, 1]
+    elif case == "material":
+        kw["poisson"] = 0.5
+    elif case == "dt":
+        kw["dt"] = 0.0
+    elif case == "isolated":
+        X = np.vstack([X, [[2.0, 2.0, 0.0]]])
+    with pytest.raises(J.JGS2Error):
+        J.Cloth(X, T, kw["youngs"], kw["poisson"], kw["thickness"], kw["density"], kw["bend"], None,
+                dt=kw["dt"])
+
+
+def test_cloth_hinges_are_the_interior_edges():
+    # an n x n grid cut into 2 triangles per cell has 2 n (n - 1) + (n - 1)^2 edges, 4 (n - 1)
+    # of them on the boundary
+    for n in (3, 8):
+        s = scenes.cloth_scene(n=n)
+        c = J.Cloth.from_scene(s)
+        assert c.n_hinges == 2 * n * (n - 1) + (n - 1) ** 2 - 4 * (n - 1)
+        c.close()
+
