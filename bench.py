@@ -162,7 +162,7 @@ def survey_sweep_bytes(V_f, T, n_cub, fp_bytes=4):
 # listed.
 NCU_TRAFFIC_TETS = 1388544
 NCU_TRAFFIC = {"k_gather": 198.486528e6 + 19.848448e6, "k_elem": 159.587840e6 + 35.314944e6,
-               "k_energy": 172.158976e6 + 4.227072e6}
+               "k_correct": 175.108096e6 + 5.450752e6, "k_energy": 171.836160e6 + 3.512576e6}
 
 
 class Clocks:
@@ -675,6 +675,76 @@ def compare_gs(args, p, mesh, x0, v0, stream, corr, prec):
     return res
 
 
+def run_cloth(args, rank, world, local_rank):
+    """The cloth workload (reading R26): a square StVK cloth with quadratic bending, held at
+    two corners and released under gravity, stepped by jgs2_cloth_step to rel_tol 1e-4
+    (capped). Default size: 1001 x 1001 vertices, 2M triangles (the scale of the paper's cloth
+    example). No correction and no contact (the cloth path has neither)."""
+    import torch
+    import paper_2506_06494_b300 as p
+    import scenes
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    n = args.cloth_n
+    s = scenes.cloth_scene(n=n, size=1.0)
+    c = p.Cloth.from_scene(s)
+    prec = p.FP32 if args.precision == "fp32" else p.FP64
+    opts = p.step_opts(precision=prec, max_sweeps=args.max_sweeps, rel_tol=1e-4, check_every=16)
+    stream = torch.cuda.current_stream()
+    x = torch.tensor(s.X, dtype=torch.float64, device=dev)
+    v = torch.tensor(s.v0, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        c.step(x, v, opts, stream)
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    clocks = Clocks(vis.split(",")[local_rank] if vis else str(local_rank))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = [c.step(x, v, opts, stream) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    sweeps = np.array([r.sweeps for r in reps], dtype=float)
+    # e2e: host state, copies inside the timed region
+    xh = torch.tensor(s.X, dtype=torch.float64).pin_memory()
+    vh = torch.tensor(s.v0, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xd, vd = xh.to(dev, non_blocking=True), vh.to(dev, non_blocking=True)
+        c.step(xd, vd, opts, stream)
+        xh.copy_(xd)
+        vh.copy_(vd)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    V, F, H = s.X.shape[0], s.tris.shape[0], c.n_hinges
+    fb = 4 if prec == p.FP32 else 8
+    # records read by the gather and the line-search pass (triangles 20, hinges 12 words),
+    # per-vertex state through gather (u, dz, m/h^2, D written), pass and update
+    bytes_sweep = 2 * (F * 20 * fb + H * 12 * fb) + V * (15 * fb + 13 * fb + 12 * fb)
+    ms_sweep = ms / max(1.0, float(np.mean(sweeps)))
+    hbm, hkind = peaks()
+    return {
+        "metric": METRIC, "value": ms, "unit": "ms/step", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == p.FP32 else "f64", "data": "synthetic",
+        "config": {"workload": "cloth", "scene": f"{n}x{n}-vertex square cloth, 1 m, two corners held, gravity",
+                   "vertices": V, "triangles": F, "hinges": H, "rel_tol": 1e-4, "max_sweeps": args.max_sweeps,
+                   "correction": "none (cloth path)", "line_search": True, "parallelism": f"replicas x{world}",
+                   "l2": "per-sweep working set larger than L2 (126 MB); no flush"},
+        "sweeps_per_step": float(np.mean(sweeps)), "converged_steps": int(sum(r.converged for r in reps)),
+        "max_rel_residual": float(max(r.rel_residual for r in reps)),
+        "e2e": {"value": e2e_ms, "unit": "ms/step", "h2d_bytes_per_step": 2 * V * 24, "d2h_bytes_per_step": 2 * V * 24},
+        "gpu_launches": int(sum(4 * r.sweeps + 6 for r in reps)),
+        "clocks": ck,
+        "sweep_roofline": {"bound": "hbm", "achieved": round(bytes_sweep / ms_sweep / 1e6, 1), "peak": hbm,
+                           "unit": "GB/s", "frac": round(bytes_sweep / ms_sweep / 1e6 / hbm, 4),
+                           "bytes_per_sweep": int(bytes_sweep), "ms_per_sweep": round(ms_sweep, 5),
+                           "peak_source": f"{hkind} (MEASURED_PEAKS.json hbm_gbs)"},
+    }
+
+
 def run_adjoint(args, rank, world, local_rank):
     """Differentiation workload: a rollout of the 20x20x100-vertex beam (214,434 tets) with
     per-element Young's moduli E_e = 1e7 U(0.5, 1.5) (seed 0), loss = sum |x_n - xbar_n|^2
@@ -740,7 +810,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="jgs2", choices=["jgs2", "reference"])
-    ap.add_argument("--workload", default="spheres", choices=["spheres", "beam", "cube", "batch", "adjoint"])
+    ap.add_argument("--workload", default="spheres", choices=["spheres", "beam", "cube", "batch", "adjoint", "cloth"])
     ap.add_argument("--rollout-steps", type=int, default=30, help="adjoint workload: steps of the rollout")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--correction", default="asm", choices=["asm", "elem", "off"])
@@ -765,6 +835,7 @@ def main():
                     help="wall friction coefficient on the spheres workload (lagged IPC friction; 0 = none)")
     ap.add_argument("--precompute-gpu", type=int, default=1, choices=[0, 1],
                     help="1: the precompute's multi-RHS solves run on the GPU (FP32 substitutions, FP64 refinement)")
+    ap.add_argument("--cloth-n", type=int, default=1001, help="cloth workload: vertices per side")
     ap.add_argument("--n-spheres", type=int, default=10)
     ap.add_argument("--contact", type=int, default=1, choices=[0, 1, 2],
                     help="spheres workload: 0 no contact, 1 IPC log barrier, 2 quadratic penalty")
@@ -785,7 +856,8 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    out = (run_adjoint if args.workload == "adjoint" else run_jgs2)(args, rank, world, local_rank)
+    runner = {"adjoint": run_adjoint, "cloth": run_cloth}.get(args.workload, run_jgs2)
+    out = runner(args, rank, world, local_rank)
     if out is not None:
         print(json.dumps(out))
     if world > 1:
