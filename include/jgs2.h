@@ -394,7 +394,7 @@ jgs2_status jgs2_alu_peak(int32_t precision, double* gflops, void* stream);
  * Cloth (the cloth material of the paper's Table 1 caption; reading R26): StVK membrane
  * triangles and a quadratic bending energy on interior edges, stepped by the per-vertex
  * Jacobi sweep with the global Armijo line search. No cubature correction (its records are
- * built on tets) and no contact. Vertices keep the caller's order.
+ * built on tets); contact with walls only (no self-contact). Vertices keep the caller's order.
  *  - Membrane: per triangle, F = [x_1 - x_0, x_2 - x_0] D_m^-1 (3x2, D_m the rest edges in
  *    the triangle's plane), E = (F^T F - I)/2, energy A (mu tr(E^2) + lam/2 tr(E)^2) with
  *    mu = Y t / (2 (1 + nu)), lam = Y t nu / (1 - nu^2).
@@ -418,6 +418,14 @@ typedef struct {
   const uint8_t* pinned;     /* [V] 1 = held at x_t; may be NULL */
   double gravity[3];
   double dt;                 /* h (s) > 0 */
+  /* Walls n.x >= c (optional): every free vertex against every wall with the IPC barrier
+   * kappa B(d) below dhat (Sec. 7), its Gauss-Newton block and the per-vertex step limit
+   * 0.45 min(2 dhat - dhat, d_min) of the solids; the line search evaluates the barrier
+   * exactly per trial. n_planes = 0: none (the other fields are then ignored). */
+  int32_t n_planes;
+  const double* planes;      /* [n_planes][4]: unit normal n (3) and offset c */
+  double dhat;               /* barrier support (m) > 0 */
+  double kappa;              /* barrier stiffness (N/m) > 0 */
 } jgs2_cloth_desc;
 
 typedef struct jgs2_cloth jgs2_cloth;

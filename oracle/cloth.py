@@ -24,6 +24,11 @@ Reading R26 (the paper names the materials but gives no formulas):
   semidefinite part of the summed membrane blocks + the bending blocks (StVK's blocks can
   be indefinite under compression); then the global Armijo search of R17 along D (no
   cubature correction: the Ubar records of Eq. u are built on tets only).
+- Walls (optional): every free vertex against every wall plane n.x >= c with the IPC
+  barrier of Sec. 7 (kappa B(d), d = n.x - c, as for the solids, reading R11): gradient
+  kappa B'(d) n, Gauss-Newton block kappa B''(d) n n^T, and the same step limit
+  |D_v| <= 0.45 min(r_c - dhat, d_min,v), r_c = 2 dhat, d_min,v the smallest wall distance
+  below r_c. The line search evaluates the barrier exactly per trial.
 """
 from __future__ import annotations
 
@@ -31,6 +36,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from .contact import barrier, barrier_d1, barrier_d2
 from .fem import psd_clamp
 
 LS_TRIALS = 8
@@ -38,7 +44,10 @@ ARMIJO_C = 1e-4
 
 
 class Cloth:
-    def __init__(self, X, tris, youngs, poisson, thickness, density, bend, pinned=None):
+    def __init__(self, X, tris, youngs, poisson, thickness, density, bend, pinned=None, planes=None, dhat=1e-3,
+                 kappa=1e5):
+        self.planes = np.zeros((0, 4)) if planes is None else np.asarray(planes, dtype=np.float64).reshape(-1, 4)
+        self.dhat, self.kappa, self.rc = float(dhat), float(kappa), 2.0 * float(dhat)
         X = np.asarray(X, dtype=np.float64)
         tris = np.asarray(tris, dtype=np.int64)
         self.X, self.tris = X, tris
@@ -112,12 +121,19 @@ class Cloth:
     def bending_w(self, x):
         return np.einsum("hi,hik->hk", self.K, x[self.hinges])  # [H][3]
 
+    def wall_distances(self, x):
+        """[free vertices][planes] distances n.x - c."""
+        return x[self.free] @ self.planes[:, :3].T - self.planes[:, 3][None, :]
+
     def energy(self, x, z, h):
         em, _, _, _ = self.membrane(x)
         w = self.bending_w(x)
         d = (x - z)[self.free]
-        return float(np.sum(em) + 0.5 * np.sum(self.kb * np.sum(w * w, 1)) +
-                     np.sum(0.5 * self.mass[self.free] / h ** 2 * np.sum(d * d, 1)))
+        e = float(np.sum(em) + 0.5 * np.sum(self.kb * np.sum(w * w, 1)) +
+                  np.sum(0.5 * self.mass[self.free] / h ** 2 * np.sum(d * d, 1)))
+        if len(self.planes):
+            e += self.kappa * float(np.sum(barrier(self.wall_distances(x), self.dhat)))
+        return e
 
     def gradient(self, x, z, h):
         _, F, _, S = self.membrane(x)
@@ -129,6 +145,9 @@ class Cloth:
         gb = (self.kb[:, None, None] * self.K[:, :, None]) * w[:, None, :]
         np.add.at(g, self.hinges.ravel(), gb.reshape(-1, 3))
         g += self.mass[:, None] / h ** 2 * (x - z)
+        if len(self.planes):
+            b1 = self.kappa * barrier_d1(self.wall_distances(x), self.dhat)  # [free][planes]
+            g[self.free] += b1 @ self.planes[:, :3]
         g[self.pinned] = 0.0
         return g
 
@@ -150,7 +169,20 @@ class Cloth:
         kb = (self.kb[:, None] * self.K ** 2).ravel()
         np.add.at(Hd, self.hinges.ravel(), kb[:, None, None] * np.eye(3)[None])
         Hd += (self.mass / h ** 2)[:, None, None] * np.eye(3)[None]
+        if len(self.planes):
+            b2 = self.kappa * barrier_d2(self.wall_distances(x), self.dhat)
+            n = self.planes[:, :3]
+            Hd[self.free] += np.einsum("vp,pi,pj->vij", b2, n, n)
         return Hd
+
+    def step_limits(self, x):
+        """0.45 min(r_c - dhat, d_min) per free vertex (inf without walls), reading R11."""
+        lim = np.full(self.V, np.inf)
+        if len(self.planes):
+            d = self.wall_distances(x)
+            dm = np.where(d < self.rc, d, np.inf).min(axis=1)
+            lim[self.free] = 0.45 * np.minimum(self.rc - self.dhat, dm)
+        return lim
 
 
 def inertia_target(x_t, v_t, h, gravity):
@@ -161,8 +193,12 @@ def direction(c: Cloth, x, z, h):
     g = c.gradient(x, z, h)
     H = c.diag_blocks(x, h)
     D = np.zeros_like(x)
+    lim = c.step_limits(x)
     for v in c.free:
         D[v] = -np.linalg.solve(H[v], g[v])
+        n = np.linalg.norm(D[v])
+        if n > lim[v]:
+            D[v] *= lim[v] / n
     return D, g
 
 

@@ -73,6 +73,10 @@ struct ClothDev {
   double* xt;                // [V][3]
   double h;
   double grav[3];
+  // walls n.x >= c: IPC barrier kappa B(d) below dhat, step limit 0.45 min(rc - dhat, d_min)
+  int n_planes;
+  const double* planes;      // [n_planes][4]
+  double dhat, kappa, rc;
 };
 
 struct ClothState {
@@ -241,8 +245,28 @@ __global__ void __launch_bounds__(128) k_cloth_gather(ClothDev<T> m, const Cloth
     g[1] += mh * (ui.y - dzi.y);
     g[2] += mh * (ui.z - dzi.z);
     T H[6] = {Hm[0] + hb + mh, Hm[1], Hm[2], Hm[3] + hb + mh, Hm[4], Hm[5] + hb + mh};
+    T lim = T(INFINITY);
+    if (m.n_planes > 0) {
+      // walls: barrier gradient and Gauss-Newton block, and the step limit (FP64 distances)
+      const double x[3] = {m.xt[3 * i] + double(ui.x), m.xt[3 * i + 1] + double(ui.y),
+                           m.xt[3 * i + 2] + double(ui.z)};
+      double dmin = INFINITY;
+      for (int p = 0; p < m.n_planes; ++p) {
+        const double* pl = m.planes + 4 * p;
+        const double dd = pl[0] * x[0] + pl[1] * x[1] + pl[2] * x[2] - pl[3];
+        if (dd < m.rc) dmin = fmin(dmin, dd);
+        if (dd > 0.0 && dd < m.dhat) {
+          const double b1 = m.kappa * barrier_b1(dd, m.dhat), b2 = m.kappa * barrier_b2(dd, m.dhat);
+          const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+          for (int k = 0; k < 3; ++k) g[k] += T(b1 * pl[k]);
+          for (int k = 0; k < 6; ++k) H[k] += T(b2 * pl[ia[k]] * pl[ib[k]]);
+        }
+      }
+      lim = T(0.45 * fmin(m.rc - m.dhat, dmin));
+    }
     T rhs[3] = {-g[0], -g[1], -g[2]}, d[3];
     if (!chol3_solve(H, rhs, d)) d[0] = d[1] = d[2] = T(0);
+    truncate3(d, lim);
     m.D[i] = Vec4<T>{d[0], d[1], d[2], T(0)};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -340,24 +364,63 @@ __global__ void __launch_bounds__(128) k_cloth_poly(ClothDev<T> m, const ClothSt
     for (int j = 0; j < 4; ++j) partial[(size_t)j * gridDim.x + blockIdx.x] = bs[j];
 }
 
+// Walls: kappa (B(d + a n.D) - B(d)) per trial a = 2^-j over every free vertex and wall,
+// exact (the barrier is not a polynomial); per-block partials [kClothTrials][grid].
+template <typename T>
+__global__ void __launch_bounds__(128) k_cloth_wall_trials(ClothDev<T> m, const ClothState* __restrict__ st,
+                                                           double* __restrict__ partial) {
+  __shared__ double red[32 * kClothTrials];
+  if (st->done) return;
+  double acc[kClothTrials];
+#pragma unroll
+  for (int j = 0; j < kClothTrials; ++j) acc[j] = 0.0;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m.V && !m.pinned[i]) {
+    const Vec4<T> ui = m.u[i], di = m.D[i];
+    const double x[3] = {m.xt[3 * i] + double(ui.x), m.xt[3 * i + 1] + double(ui.y), m.xt[3 * i + 2] + double(ui.z)};
+    for (int p = 0; p < m.n_planes; ++p) {
+      const double* pl = m.planes + 4 * p;
+      const double d0 = pl[0] * x[0] + pl[1] * x[1] + pl[2] * x[2] - pl[3];
+      const double dn = pl[0] * double(di.x) + pl[1] * double(di.y) + pl[2] * double(di.z);
+      // the step limit keeps every trial of a vertex beyond r_c outside dhat
+      if (!(d0 < m.rc)) continue;
+      const double b0 = barrier_b(d0, m.dhat);
+#pragma unroll
+      for (int j = 0; j < kClothTrials; ++j) {
+        const double a = 1.0 / double(1 << j);
+        acc[j] += m.kappa * (barrier_b(d0 + a * dn, m.dhat) - b0);
+      }
+    }
+  }
+  block_sum<kClothTrials>(acc, red);
+  if (threadIdx.x == 0)
+    for (int j = 0; j < kClothTrials; ++j) partial[(size_t)j * gridDim.x + blockIdx.x] = acc[j];
+}
+
 // One block: fixed-order sums (thread-strided, then a shared-memory tree), residual test,
 // Armijo choice; writes alpha (0 when the step stops or no trial passes).
 __global__ void __launch_bounds__(256) k_cloth_decide(ClothState* st, const double* __restrict__ pg, int nbg,
-                                                      const double* __restrict__ pp, int nbp, int ls) {
-  __shared__ double red[6][256];
+                                                      const double* __restrict__ pp, int nbp,
+                                                      const double* __restrict__ pw, int nbw, int ls) {
+  constexpr int NS = 6 + kClothTrials;
+  __shared__ double red[NS][256];
   if (st->done) return;
-  double s[6] = {0, 0, 0, 0, 0, 0};
+  double s[NS];
+  for (int j = 0; j < NS; ++j) s[j] = 0.0;
   for (int q = threadIdx.x; q < nbg; q += blockDim.x) {
     s[0] += pg[q];
     s[1] += pg[nbg + q];
   }
   for (int q = threadIdx.x; q < nbp; q += blockDim.x)
     for (int j = 0; j < 4; ++j) s[2 + j] += pp[(size_t)j * nbp + q];
-  for (int j = 0; j < 6; ++j) red[j][threadIdx.x] = s[j];
+  if (pw)
+    for (int q = threadIdx.x; q < nbw; q += blockDim.x)
+      for (int j = 0; j < kClothTrials; ++j) s[6 + j] += pw[(size_t)j * nbw + q];
+  for (int j = 0; j < NS; ++j) red[j][threadIdx.x] = s[j];
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w)
-      for (int j = 0; j < 6; ++j) red[j][threadIdx.x] += red[j][threadIdx.x + w];
+      for (int j = 0; j < NS; ++j) red[j][threadIdx.x] += red[j][threadIdx.x + w];
     __syncthreads();
   }
   if (threadIdx.x != 0) return;
@@ -388,7 +451,7 @@ __global__ void __launch_bounds__(256) k_cloth_decide(ClothState* st, const doub
     alpha = 0.0;
     for (int j = 0; j < kClothTrials; ++j) {
       const double a = 1.0 / double(1 << j);
-      const double de = a * (red[2][0] + a * (red[3][0] + a * (red[4][0] + a * red[5][0])));
+      const double de = a * (red[2][0] + a * (red[3][0] + a * (red[4][0] + a * red[5][0]))) + red[6 + j][0];
       if (de <= 1e-4 * a * gd) {
         alpha = a;
         break;
@@ -461,6 +524,12 @@ __global__ void __launch_bounds__(128) k_cloth_energy(ClothDev<double> m, int nb
       const Vec4<double> u = m.u[v], dz = m.dz[v];
       const double a = u.x - dz.x, bb = u.y - dz.y, c = u.z - dz.z;
       e[0] = 0.5 * m.mh2[v] * (a * a + bb * bb + c * c);
+      for (int p = 0; p < m.n_planes; ++p) {
+        const double* pl = m.planes + 4 * p;
+        const double d = pl[0] * (m.xt[3 * v] + u.x) + pl[1] * (m.xt[3 * v + 1] + u.y) + pl[2] * (m.xt[3 * v + 2] + u.z) -
+                         pl[3];
+        if (d < m.dhat) e[0] += m.kappa * barrier_b(d, m.dhat);
+      }
     }
   }
   block_sum<1>(e, red);
@@ -500,6 +569,15 @@ __global__ void __launch_bounds__(128) k_cloth_grad(ClothDev<double> m, double* 
     g[0] += m.mh2[i] * (u.x - dz.x);
     g[1] += m.mh2[i] * (u.y - dz.y);
     g[2] += m.mh2[i] * (u.z - dz.z);
+    for (int p = 0; p < m.n_planes; ++p) {
+      const double* pl = m.planes + 4 * p;
+      const double d = pl[0] * (m.xt[3 * i] + u.x) + pl[1] * (m.xt[3 * i + 1] + u.y) + pl[2] * (m.xt[3 * i + 2] + u.z) -
+                       pl[3];
+      if (d > 0.0 && d < m.dhat) {
+        const double b1 = m.kappa * barrier_b1(d, m.dhat);
+        for (int k = 0; k < 3; ++k) g[k] += b1 * pl[k];
+      }
+    }
   }
   for (int k = 0; k < 3; ++k) g_out[3 * i + k] = g[k];
 }
@@ -541,11 +619,13 @@ struct Cloth {
   std::vector<double> b, area, mu, lam, K, kb, mass;
   std::vector<uint8_t> pinned;
   std::vector<int32_t> tri_off, tri_inc, hin_off, hin_inc;
+  std::vector<double> planes;       // [n][4] walls
+  double dhat = 0.0, kappa = 0.0;
   // device
   bool device_ready = false;
   int32_t *d_tri_off = nullptr, *d_tri_inc = nullptr, *d_hin_off = nullptr, *d_hin_inc = nullptr;
   uint8_t* d_pinned = nullptr;
-  double *d_xt = nullptr, *d_partial = nullptr;
+  double *d_xt = nullptr, *d_partial = nullptr, *d_planes = nullptr;
   ClothState* d_state = nullptr;
   ClothBufs<float> f32;
   ClothBufs<double> f64;
@@ -553,7 +633,7 @@ struct Cloth {
   ~Cloth() {
     f32.release();
     f64.release();
-    void* p[] = {d_tri_off, d_tri_inc, d_hin_off, d_hin_inc, d_pinned, d_xt, d_partial, d_state};
+    void* p[] = {d_tri_off, d_tri_inc, d_hin_off, d_hin_inc, d_pinned, d_xt, d_partial, d_state, d_planes};
     for (void* q : p)
       if (q) cudaFree(q);
   }
@@ -593,7 +673,11 @@ jgs2_status cloth_device(Cloth* c) {
   CKC(cudaMemcpy(c->d_pinned, c->pinned.data(), V, cudaMemcpyHostToDevice));
   const int nbT = (c->F + 127) / 128, nbH = (c->H + 127) / 128, nbV = (V + 127) / 128;
   c->nb_partial = nbT + nbH + nbV;
-  CKC(cdalloc(&c->d_partial, (size_t)6 * c->nb_partial + 16));
+  CKC(cdalloc(&c->d_partial, (size_t)6 * c->nb_partial + (size_t)kClothTrials * nbV + 16));
+  if (!c->planes.empty()) {
+    CKC(cdalloc(&c->d_planes, c->planes.size()));
+    CKC(cudaMemcpy(c->d_planes, c->planes.data(), sizeof(double) * c->planes.size(), cudaMemcpyHostToDevice));
+  }
   CKC(cdalloc(&c->d_state, 1));
   c->device_ready = true;
   return JGS2_OK;
@@ -671,6 +755,11 @@ ClothDev<T> cloth_view(Cloth* c) {
   d.dz = b.dz;
   d.D = b.D;
   d.xt = c->d_xt;
+  d.n_planes = (int)c->planes.size() / 4;
+  d.planes = c->d_planes;
+  d.dhat = c->dhat;
+  d.kappa = c->kappa;
+  d.rc = 2.0 * c->dhat;
   d.h = c->h;
   for (int q = 0; q < 3; ++q) d.grav[q] = c->grav[q];
   return d;
@@ -695,13 +784,16 @@ jgs2_status cloth_run(Cloth* c, const double* x, const double* v, const double* 
   double* pg = c->d_partial;
   double* pp = c->d_partial + 2 * (size_t)nbV;
   const int nbp = nbT + nbH + nbV;
+  double* pw = pp + 4 * (size_t)nbp;
+  const bool walls = !c->planes.empty();
   ClothState h_st;
   const int chunk = std::max(1, check_every);
   for (int k0 = 0;; k0 += chunk) {
     for (int q = 0; q < chunk; ++q) {
       k_cloth_gather<T><<<nbV, 128, 0, s>>>(d, c->d_state, pg);
       if (ls) k_cloth_poly<T><<<nbp, 128, 0, s>>>(d, c->d_state, nbT, nbH, pp);
-      k_cloth_decide<<<1, 256, 0, s>>>(c->d_state, pg, nbV, pp, nbp, ls);
+      if (ls && walls) k_cloth_wall_trials<T><<<nbV, 128, 0, s>>>(d, c->d_state, pw);
+      k_cloth_decide<<<1, 256, 0, s>>>(c->d_state, pg, nbV, pp, nbp, walls ? pw : nullptr, nbV, ls);
       k_cloth_update<T><<<nbV, 128, 0, s>>>(d, c->d_state);
     }
     CKC(cudaGetLastError());
@@ -736,6 +828,13 @@ jgs2_status cloth_create(const jgs2_cloth_desc* d, Cloth** out) {
   c->h = d->dt;
   for (int q = 0; q < 3; ++q) c->grav[q] = d->gravity[q];
   c->tv.assign(d->tris, d->tris + 3 * (size_t)F);
+  if (d->n_planes < 0 || (d->n_planes > 0 && (!d->planes || !(d->dhat > 0.0) || !(d->kappa > 0.0))))
+    return fail(JGS2_EINVAL, "cloth walls need planes, dhat > 0 and kappa > 0");
+  if (d->n_planes > 0) {
+    c->planes.assign(d->planes, d->planes + 4 * (size_t)d->n_planes);
+    c->dhat = d->dhat;
+    c->kappa = d->kappa;
+  }
   c->pinned.assign(V, 0);
   if (d->pinned)
     for (int v = 0; v < V; ++v) c->pinned[v] = d->pinned[v] ? 1 : 0;

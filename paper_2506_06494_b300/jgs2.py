@@ -41,7 +41,9 @@ class ClothDesc(C.Structure):
                 ("rest_pos", C.POINTER(C.c_double)), ("tris", C.POINTER(C.c_int32)),
                 ("youngs", C.c_double), ("poisson", C.c_double), ("thickness", C.c_double),
                 ("density", C.c_double), ("bend", C.c_double), ("pinned", C.POINTER(C.c_uint8)),
-                ("gravity", C.c_double * 3), ("dt", C.c_double)]
+                ("gravity", C.c_double * 3), ("dt", C.c_double),
+                ("n_planes", C.c_int32), ("planes", C.POINTER(C.c_double)), ("dhat", C.c_double),
+                ("kappa", C.c_double)]
 
 
 class ClothReport(C.Structure):
@@ -413,10 +415,11 @@ class Cloth:
     """A cloth (jgs2_cloth_*): StVK membrane triangles, quadratic bending, Jacobi sweeps."""
 
     def __init__(self, X, tris, youngs, poisson, thickness, density, bend, pinned=None, gravity=(0, 0, -9.8),
-                 dt=1 / 120):
+                 dt=1 / 120, planes=None, dhat=1e-3, kappa=1e5):
         self._keep = [np.ascontiguousarray(X, dtype=np.float64), np.ascontiguousarray(tris, dtype=np.int32),
-                      None if pinned is None else np.ascontiguousarray(pinned, dtype=np.uint8)]
-        Xa, Ta, Pa = self._keep
+                      None if pinned is None else np.ascontiguousarray(pinned, dtype=np.uint8),
+                      np.ascontiguousarray(np.zeros((0, 4)) if planes is None else planes, dtype=np.float64)]
+        Xa, Ta, Pa, PLa = self._keep
         d = ClothDesc()
         d.n_vertices, d.n_tris = Xa.shape[0], Ta.shape[0]
         d.rest_pos = _ptr(Xa, C.c_double)
@@ -427,6 +430,9 @@ class Cloth:
         for q in range(3):
             d.gravity[q] = float(gravity[q])
         d.dt = float(dt)
+        d.n_planes = int(PLa.reshape(-1, 4).shape[0])
+        d.planes = _ptr(PLa, C.c_double)
+        d.dhat, d.kappa = float(dhat), float(kappa)
         h = C.c_void_p()
         _check(lib().jgs2_cloth_create(C.byref(d), C.byref(h)))
         self.handle = h
@@ -434,7 +440,8 @@ class Cloth:
 
     @classmethod
     def from_scene(cls, s):
-        return cls(s.X, s.tris, s.youngs, s.poisson, s.thickness, s.density, s.bend, s.pinned, s.gravity, s.dt)
+        return cls(s.X, s.tris, s.youngs, s.poisson, s.thickness, s.density, s.bend, s.pinned, s.gravity, s.dt,
+                   s.planes, s.dhat, s.kappa)
 
     @property
     def n_hinges(self):

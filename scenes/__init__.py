@@ -355,6 +355,9 @@ class ClothScene:
     v0: np.ndarray           # (V,3)
     dt: float = 1.0 / 120.0
     gravity: tuple = (0.0, 0.0, -9.8)
+    planes: np.ndarray = field(default_factory=lambda: np.zeros((0, 4)))  # walls n.x >= c
+    dhat: float = 1e-3
+    kappa: float = 1e5
 
 
 def cloth_grid(n, size):
@@ -382,4 +385,13 @@ def cloth_scene(n=21, size=0.5, youngs=1e6, thickness=5e-4, bend=1e-5, seed=0, v
     v0 = np.random.default_rng(seed).normal(0.0, vel_sigma, X.shape) if vel_sigma > 0 else np.zeros_like(X)
     v0[pinned.astype(bool)] = 0.0
     return ClothScene("cloth", X, tris, youngs, 0.3, thickness, 200.0, bend, pinned, v0)
+
+
+def cloth_floor_scene(n=11, size=0.2, gap=6e-4, youngs=1e5, kappa=1e2):
+    """A small free cloth lying flat just above the floor (z >= 0, within dhat), under gravity:
+    exercises the cloth's wall barrier."""
+    X, tris = cloth_grid(n, size)
+    X = X + np.array([0.3, 0.3, gap])
+    return ClothScene("cloth_floor", X, tris, youngs, 0.3, 5e-4, 200.0, 1e-5, np.zeros(len(X), np.uint8),
+                      np.zeros_like(X), planes=np.array([[0.0, 0.0, 1.0, 0.0]]), dhat=1e-3, kappa=kappa)
 

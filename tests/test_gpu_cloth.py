@@ -84,3 +84,44 @@ def test_cloth_step_converges(cuda, prec):
     pin = s.pinned.astype(bool)
     assert np.all(xs[~pin, 2] < 0.0)
     assert np.abs(xs[pin] - s.X[pin]).max() == 0.0
+
+
+def ocloth_walls(s):
+    return cloth.Cloth(s.X, s.tris, s.youngs, s.poisson, s.thickness, s.density, s.bend, s.pinned,
+                       planes=s.planes, dhat=s.dhat, kappa=s.kappa)
+
+
+def test_cloth_walls_energy_gradient(cuda):
+    s = scenes.cloth_floor_scene()
+    o = ocloth_walls(s)
+    x = s.X + np.random.default_rng(3).normal(0.0, 1e-4, s.X.shape)
+    d = o.wall_distances(x)
+    assert np.all((d > 0) & (d < s.dhat))
+    z = cloth.inertia_target(s.X, s.v0, s.dt, s.gravity)
+    c = p.Cloth.from_scene(s)
+    E, g = c.energy_gradient(t(s.X, cuda), t(s.v0, cuda), t(x, cuda))
+    go = o.gradient(x, z, s.dt)
+    assert np.abs(g.cpu().numpy() - go).max() <= 1e-10 * np.abs(go).max()
+    assert abs(E - o.energy(x, z, s.dt)) <= 1e-10 * abs(E)
+
+
+@pytest.mark.parametrize("prec", [p.FP64, p.FP32])
+def test_cloth_walls_sweeps_and_step(cuda, prec):
+    s = scenes.cloth_floor_scene()
+    o = ocloth_walls(s)
+    c = p.Cloth.from_scene(s)
+    x = s.X + np.random.default_rng(4).normal(0.0, 1e-4, s.X.shape)
+    z = cloth.inertia_target(s.X, s.v0, s.dt, s.gravity)
+    xg = t(x, cuda)
+    c.sweeps(t(s.X, cuda), t(s.v0, cuda), xg, 3, p.step_opts(precision=prec))
+    xo = cloth.run_sweeps(o, x, z, s.dt, 3)
+    disp = np.linalg.norm(xo - x, axis=1).max()
+    assert np.linalg.norm(xg.cpu().numpy() - xo, axis=1).max() / disp <= TOL[prec]
+    # a whole step: above the floor, and (FP64) the oracle's sweep count and positions
+    xs, vs = t(s.X, cuda), t(s.v0, cuda)
+    rep = c.step(xs, vs, p.step_opts(precision=prec, max_sweeps=400, rel_tol=1e-4))
+    assert xs.cpu().numpy()[:, 2].min() > 0.0
+    if prec == p.FP64:
+        r = cloth.step(o, s.X, s.v0, s.dt, s.gravity, rel_tol=1e-4, max_sweeps=400)
+        assert rep.sweeps == r.sweeps
+        assert np.linalg.norm(xs.cpu().numpy() - r.x) / np.linalg.norm(r.x - s.X) <= 1e-9

@@ -141,3 +141,56 @@ def test_sweeps_reach_the_newton_solution():
     r = cloth.step(c, s.X, s.v0, h, s.gravity, rel_tol=1e-8, max_sweeps=5000)
     assert r.converged
     assert np.abs(r.x - x).max() <= 1e-5 * np.abs(x - s.X).max()
+
+
+def floor_cloth(n=5, gap=6e-4):
+    s = scenes.cloth_scene(n=n, youngs=1e5)
+    X = s.X + np.array([0.0, 0.0, gap])
+    c = cloth.Cloth(X, s.tris, s.youngs, s.poisson, s.thickness, s.density, s.bend, s.pinned,
+                    planes=np.array([[0.0, 0.0, 1.0, 0.0]]), dhat=1e-3, kappa=1e2)
+    return s, X, c
+
+
+def test_wall_barrier_by_finite_differences():
+    s, X, c = floor_cloth()
+    r = np.random.default_rng(5)
+    x = X + r.normal(0.0, 1e-4, X.shape)
+    x[c.pinned] = X[c.pinned]
+    h = s.dt
+    z = cloth.inertia_target(X, s.v0, h, s.gravity)
+    g = c.gradient(x, z, h)
+    H = c.diag_blocks(x, h, project=False)
+    d = c.wall_distances(x)
+    assert np.all((d > 0) & (d < c.dhat))  # every free vertex feels the barrier
+    for v in c.free[:6]:
+        for a in range(3):
+            e = np.zeros_like(x)
+            e[v, a] = 1e-9
+            fd = (c.energy(x + e, z, h) - c.energy(x - e, z, h)) / 2e-9
+            assert g[v, a] == pytest.approx(fd, rel=1e-5, abs=1e-8 * np.abs(g).max())
+    # the barrier's block is its Gauss-Newton (here exact) second derivative along n
+    Hn = c.diag_blocks(x, h, project=False)
+    c0 = cloth.Cloth(X, s.tris, s.youngs, s.poisson, s.thickness, s.density, s.bend, s.pinned)
+    Hw = Hn - c0.diag_blocks(x, h, project=False)
+    v = c.free[0]
+    fd = (c.gradient(x + np.eye(3)[2] * 1e-9 * (np.arange(len(x)) == v)[:, None], z, h)[v, 2] -
+          c0.gradient(x + np.eye(3)[2] * 1e-9 * (np.arange(len(x)) == v)[:, None], z, h)[v, 2] -
+          (c.gradient(x, z, h)[v, 2] - c0.gradient(x, z, h)[v, 2])) / 1e-9
+    assert Hw[v][2, 2] == pytest.approx(fd, rel=1e-4)
+    assert abs(Hw[v][0, 0]) + abs(Hw[v][0, 2]) <= 1e-12 * abs(Hw[v][2, 2])
+
+
+def test_cloth_on_the_floor_stays_above_it_and_converges():
+    s, X, c = floor_cloth()
+    h = s.dt
+    r = cloth.step(c, X, s.v0, h, s.gravity, rel_tol=1e-6, max_sweeps=20000)
+    assert r.converged
+    d = c.wall_distances(r.x)
+    assert d.min() > 0.0
+    # at the converged state the barrier holds the sheet up: it sank, but less than a free
+    # fall would take it
+    c0 = cloth.Cloth(X, s.tris, s.youngs, s.poisson, s.thickness, s.density, s.bend, s.pinned)
+    r0 = cloth.step(c0, X, s.v0, h, s.gravity, rel_tol=1e-6, max_sweeps=20000)
+    free = c.free
+    assert np.all(r.x[free, 2] >= r0.x[free, 2] - 1e-12)
+    assert np.any(r.x[free, 2] > r0.x[free, 2] + 1e-9)
