@@ -320,6 +320,132 @@ __global__ void k_add_f32(double* __restrict__ X, const float* __restrict__ W, l
     X[q] += (double)W[q];
 }
 
+// --- block inverse iteration on the device (Sec. 5's training poses): the block Q stays in
+// device memory; the p x p pieces (Gram matrices, Cholesky, Ritz eigenproblem) go through
+// the host.
+
+constexpr int kEigP = 64;     // block width at most
+constexpr int kEigRows = 32;  // rows per shared-memory tile of k_gram
+
+// Per-block partial sums of A^T B (both [n][p] row-major) into partial[blk][p*p].
+__global__ void __launch_bounds__(256) k_gram(const double* __restrict__ A, const double* __restrict__ Bm, int n,
+                                              int p, double* __restrict__ partial) {
+  __shared__ double As[kEigRows][kEigP], Bs[kEigRows][kEigP];
+  double acc[kEigP * kEigP / 256];
+  const int ne = p * p;
+#pragma unroll
+  for (int q = 0; q < kEigP * kEigP / 256; ++q) acc[q] = 0.0;
+  const int rows = (n + gridDim.x - 1) / gridDim.x;
+  const int r0 = blockIdx.x * rows, r1 = min(n, r0 + rows);
+  for (int t0 = r0; t0 < r1; t0 += kEigRows) {
+    const int nr = min(kEigRows, r1 - t0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < kEigRows * p; q += blockDim.x) {
+      const int i = q / p, j = q % p;
+      As[i][j] = i < nr ? A[(size_t)(t0 + i) * p + j] : 0.0;
+      Bs[i][j] = i < nr ? Bm[(size_t)(t0 + i) * p + j] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kEigP * kEigP / 256; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      if (e < ne) {
+        const int a = e / p, b = e % p;
+        double s = 0.0;
+        for (int i = 0; i < nr; ++i) s += As[i][a] * Bs[i][b];
+        acc[q] += s;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kEigP * kEigP / 256; ++q) {
+    const int e = threadIdx.x + 256 * q;
+    if (e < ne) partial[(size_t)blockIdx.x * ne + e] = acc[q];
+  }
+}
+
+// out[e] = sum over blocks of partial[blk][e], in block order.
+__global__ void k_sum_blocks(const double* __restrict__ partial, int nblk, int ne, double* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * ne + e];
+  out[e] = s;
+}
+
+// Row-wise forward substitution x <- x L^-T with L the lower Cholesky factor of the Gram
+// matrix (column-major, element (j, q) at L[j + q p]): X R^-1 with R = L^T.
+__global__ void k_rowsolve(double* __restrict__ X, const double* __restrict__ L, int n, int p) {
+  __shared__ double Ls[kEigP * kEigP];
+  for (int q = threadIdx.x; q < p * p; q += blockDim.x) Ls[q] = L[q];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double x[kEigP];
+  for (int j = 0; j < p; ++j) x[j] = X[(size_t)i * p + j];
+  for (int j = 0; j < p; ++j) {
+    double v = x[j];
+    for (int q = 0; q < j; ++q) v -= x[q] * Ls[j + q * p];
+    x[j] = v / Ls[j + j * p];
+  }
+  for (int j = 0; j < p; ++j) X[(size_t)i * p + j] = x[j];
+}
+
+// out = A M, A [n][p] row-major, M [p][p] row-major.
+__global__ void k_rowmul(const double* __restrict__ A, const double* __restrict__ M, int n, int p,
+                         double* __restrict__ out) {
+  __shared__ double Ms[kEigP * kEigP];
+  for (int q = threadIdx.x; q < p * p; q += blockDim.x) Ms[q] = M[q];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a[kEigP];
+  for (int j = 0; j < p; ++j) a[j] = A[(size_t)i * p + j];
+  for (int j = 0; j < p; ++j) {
+    double s = 0.0;
+    for (int q = 0; q < p; ++q) s += a[q] * Ms[q * p + j];
+    out[(size_t)i * p + j] = s;
+  }
+}
+
+// Y = H_bar X (block CSR, both triangles), thread per (vertex row, column).
+__global__ void k_hmul(const int* __restrict__ hp, const int* __restrict__ hc, const double* __restrict__ hv,
+                       const double* __restrict__ X, double* __restrict__ Y, int nv, int k) {
+  const long long total = (long long)nv * k;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(q / k), c = (int)(q % k);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int e = hp[v]; e < hp[v + 1]; ++e) {
+      const int u = hc[e];
+      const double* h = hv + (size_t)9 * e;
+      const double x0 = X[(size_t)(3 * u) * k + c], x1 = X[(size_t)(3 * u + 1) * k + c],
+                   x2 = X[(size_t)(3 * u + 2) * k + c];
+      a0 += h[0] * x0 + h[1] * x1 + h[2] * x2;
+      a1 += h[3] * x0 + h[4] * x1 + h[5] * x2;
+      a2 += h[6] * x0 + h[7] * x1 + h[8] * x2;
+    }
+    Y[(size_t)(3 * v) * k + c] = a0;
+    Y[(size_t)(3 * v + 1) * k + c] = a1;
+    Y[(size_t)(3 * v + 2) * k + c] = a2;
+  }
+}
+
+// out[j] += sum over rows of (HQ[i][j] - lam[j] Q[i][j])^2 for j < nt (rows split over blockIdx.y).
+__global__ void k_ritz_residual(const double* __restrict__ HQ, const double* __restrict__ Q,
+                                const double* __restrict__ lam, int n, int p, int nt, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nt) return;
+  const int rows = (n + gridDim.y - 1) / gridDim.y;
+  const int a = blockIdx.y * rows, b = min(n, a + rows);
+  double s = 0.0;
+  for (int i = a; i < b; ++i) {
+    const double d = HQ[(size_t)i * p + j] - lam[j] * Q[(size_t)i * p + j];
+    s += d * d;
+  }
+  atomicAdd(&out[j], s);
+}
+
 template <typename T>
 bool dalloc(T** p, size_t n, std::string& err) {
   *p = nullptr;
@@ -368,6 +494,10 @@ class GpuSolver {
   size_t cap_nk = 0, cap_k = 0, cap_scr = 0;
   double *B = nullptr, *X = nullptr, *R = nullptr, *nb = nullptr, *nr = nullptr;
   float *W = nullptr, *scr = nullptr;
+  // block inverse iteration: the block Q, H_bar Q, a rotation target, Gram partials, p x p
+  int en = 0, ep = 0, enblk = 0;
+  double *eQ = nullptr, *eHQ = nullptr, *eT = nullptr, *ePart = nullptr, *eSmall = nullptr, *eLam = nullptr,
+         *eRes = nullptr;
 
   SolveDev view() const {
     return SolveDev{L, Loff, sn_f3, sn_nJ, sn_m, rdof_off, rdof, it_sn, it_c0, it_c1, it_r0, it_r1,
@@ -376,7 +506,8 @@ class GpuSolver {
 
   ~GpuSolver() {
     void* ptrs[] = {L, Loff, sn_f3, sn_nJ, sn_m, rdof_off, rdof, it_sn, it_c0, it_c1, it_r0, it_r1,
-                    it_slot, pn_item0, pn_nitem, hp, hc, hv, B, X, R, nb, nr, W, scr};
+                    it_slot, pn_item0, pn_nitem, hp, hc, hv, B, X, R, nb, nr, W, scr,
+                    eQ, eHQ, eT, ePart, eSmall, eLam, eRes};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     if (stream) cudaStreamDestroy(stream);
@@ -538,12 +669,8 @@ GpuSolver* gpu_solver_create(const Factor& F, const std::vector<BlockCol>& H, st
   return S;
 }
 
-int gpu_solve_many(GpuSolver* S, double* Bh, int n, int k, double tol, double accept, int max_refine,
-                   std::string& err) {
-  if (!S || n != S->n || k <= 0) {
-    err = "gpu_solve_many: bad arguments";
-    return -1;
-  }
+// Work buffers for k right-hand sides (grown on demand).
+static bool ensure_bufs(GpuSolver* S, int n, int k, std::string& err) {
   const size_t nk = (size_t)n * k;
   const int nchunk = (k + kCW - 1) / kCW;
   const size_t nscr = (size_t)std::max(1, S->max_slots) * nchunk * kPW * kCW;
@@ -557,11 +684,19 @@ int gpu_solve_many(GpuSolver* S, double* Bh, int n, int k, double tol, double ac
     if (!dalloc(&S->B, nk, err) || !dalloc(&S->X, nk, err) || !dalloc(&S->R, nk, err) ||
         !dalloc(&S->W, nk, err) || !dalloc(&S->nb, k, err) || !dalloc(&S->nr, k, err) ||
         !dalloc(&S->scr, nscr, err))
-      return -1;
+      return false;
     S->cap_nk = nk;
     S->cap_k = k;
     S->cap_scr = nscr;
   }
+  return true;
+}
+
+// H_bar X = B for the k columns in S->B (device), solution in S->X: FP32 substitutions,
+// FP64 refinement (see gpu_solve_many). Returns the rounds taken, or -1 with err set.
+static int solve_core(GpuSolver* S, int n, int k, double tol, double accept, int max_refine, std::string& err) {
+  const size_t nk = (size_t)n * k;
+  const int nchunk = (k + kCW - 1) / kCW;
   double *B = S->B, *X = S->X, *R = S->R, *nb = S->nb, *nr = S->nr;
   float *W = S->W, *scr = S->scr;
   const bool verbose = std::getenv("JGS2_VERBOSE") != nullptr;
@@ -576,8 +711,7 @@ int gpu_solve_many(GpuSolver* S, double* Bh, int n, int k, double tol, double ac
   std::vector<double> hb(k), hr(k);
   int rounds = -1;
   double prev = INFINITY, worst = INFINITY;
-  cudaError_t e = cudaMemcpyAsync(B, Bh, nk * sizeof(double), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(X, 0, nk * sizeof(double), st);
+  cudaError_t e = cudaMemsetAsync(X, 0, nk * sizeof(double), st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(R, B, nk * sizeof(double), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(nb, 0, k * sizeof(double), st);
   if (e == cudaSuccess) {
@@ -635,7 +769,6 @@ int gpu_solve_many(GpuSolver* S, double* Bh, int n, int k, double tol, double ac
             std::to_string(rounds) + " rounds";
     rounds = -1;
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(Bh, X, nk * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     err = std::string("gpu_solve_many: ") + cudaGetErrorString(e);
@@ -647,6 +780,128 @@ int gpu_solve_many(GpuSolver* S, double* Bh, int n, int k, double tol, double ac
     for (auto& ev1 : ev) cudaEventDestroy(ev1);
   }
   return rounds;
+}
+
+int gpu_solve_many(GpuSolver* S, double* Bh, int n, int k, double tol, double accept, int max_refine,
+                   std::string& err) {
+  if (!S || n != S->n || k <= 0) {
+    err = "gpu_solve_many: bad arguments";
+    return -1;
+  }
+  if (!ensure_bufs(S, n, k, err)) return -1;
+  const size_t nk = (size_t)n * k;
+  cudaError_t e = cudaMemcpyAsync(S->B, Bh, nk * sizeof(double), cudaMemcpyHostToDevice, S->stream);
+  if (e != cudaSuccess) {
+    err = std::string("gpu_solve_many: ") + cudaGetErrorString(e);
+    return -1;
+  }
+  const int rounds = solve_core(S, n, k, tol, accept, max_refine, err);
+  e = cudaMemcpyAsync(Bh, S->X, nk * sizeof(double), cudaMemcpyDeviceToHost, S->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+  if (e != cudaSuccess) {
+    err = std::string("gpu_solve_many: ") + cudaGetErrorString(e);
+    return -1;
+  }
+  return rounds;
+}
+
+// ------------------------------------------------------------------ block inverse iteration
+
+static bool cuda_ok(cudaError_t e, const char* what, std::string& err) {
+  if (e == cudaSuccess) return true;
+  err = std::string(what) + ": " + cudaGetErrorString(e);
+  return false;
+}
+
+bool gpu_eig_begin(GpuSolver* S, const double* Qh, int n, int p, std::string& err) {
+  if (!S || n != S->n || p <= 0 || p > kEigP) {
+    err = "gpu_eig_begin: block wider than the device kernels take";
+    return false;
+  }
+  const size_t np = (size_t)n * p;
+  S->en = n;
+  S->ep = p;
+  S->enblk = std::max(1, std::min(148 * 4, (n + kEigRows - 1) / kEigRows));
+  if (!ensure_bufs(S, n, p, err) || !dalloc(&S->eQ, np, err) || !dalloc(&S->eHQ, np, err) ||
+      !dalloc(&S->eT, np, err) || !dalloc(&S->ePart, (size_t)S->enblk * p * p, err) ||
+      !dalloc(&S->eSmall, (size_t)p * p, err) || !dalloc(&S->eLam, p, err) || !dalloc(&S->eRes, p, err))
+    return false;
+  return cuda_ok(cudaMemcpyAsync(S->eQ, Qh, np * sizeof(double), cudaMemcpyHostToDevice, S->stream), "gpu_eig_begin",
+                 err);
+}
+
+int gpu_eig_solve(GpuSolver* S, double tol, double accept, int max_refine, std::string& err) {
+  const size_t np = (size_t)S->en * S->ep;
+  if (!cuda_ok(cudaMemcpyAsync(S->B, S->eQ, np * sizeof(double), cudaMemcpyDeviceToDevice, S->stream), "gpu_eig_solve",
+               err))
+    return -1;
+  const int rounds = solve_core(S, S->en, S->ep, tol, accept, max_refine, err);
+  if (rounds < 0) return -1;
+  if (!cuda_ok(cudaMemcpyAsync(S->eQ, S->X, np * sizeof(double), cudaMemcpyDeviceToDevice, S->stream), "gpu_eig_solve",
+               err))
+    return -1;
+  return rounds;
+}
+
+bool gpu_eig_gram(GpuSolver* S, bool with_hq, double* out, std::string& err) {
+  const int p = S->ep;
+  k_gram<<<S->enblk, 256, 0, S->stream>>>(S->eQ, with_hq ? S->eHQ : S->eQ, S->en, p, S->ePart);
+  k_sum_blocks<<<(p * p + 255) / 256, 256, 0, S->stream>>>(S->ePart, S->enblk, p * p, S->eSmall);
+  return cuda_ok(cudaMemcpyAsync(out, S->eSmall, sizeof(double) * p * p, cudaMemcpyDeviceToHost, S->stream),
+                 "gpu_eig_gram", err) &&
+         cuda_ok(cudaStreamSynchronize(S->stream), "gpu_eig_gram", err);
+}
+
+bool gpu_eig_rowsolve(GpuSolver* S, const double* L, std::string& err) {
+  const int p = S->ep;
+  if (!cuda_ok(cudaMemcpyAsync(S->eSmall, L, sizeof(double) * p * p, cudaMemcpyHostToDevice, S->stream),
+               "gpu_eig_rowsolve", err))
+    return false;
+  k_rowsolve<<<(S->en + 127) / 128, 128, 0, S->stream>>>(S->eQ, S->eSmall, S->en, p);
+  return cuda_ok(cudaGetLastError(), "gpu_eig_rowsolve", err);
+}
+
+bool gpu_eig_hmul(GpuSolver* S, std::string& err) {
+  k_hmul<<<148 * 8, 256, 0, S->stream>>>(S->hp, S->hc, S->hv, S->eQ, S->eHQ, S->nv, S->ep);
+  return cuda_ok(cudaGetLastError(), "gpu_eig_hmul", err);
+}
+
+bool gpu_eig_rotate(GpuSolver* S, const double* Vs, std::string& err) {
+  const int p = S->ep, nb = (S->en + 127) / 128;
+  if (!cuda_ok(cudaMemcpyAsync(S->eSmall, Vs, sizeof(double) * p * p, cudaMemcpyHostToDevice, S->stream),
+               "gpu_eig_rotate", err))
+    return false;
+  k_rowmul<<<nb, 128, 0, S->stream>>>(S->eQ, S->eSmall, S->en, p, S->eT);
+  std::swap(S->eQ, S->eT);
+  k_rowmul<<<nb, 128, 0, S->stream>>>(S->eHQ, S->eSmall, S->en, p, S->eT);
+  std::swap(S->eHQ, S->eT);
+  return cuda_ok(cudaGetLastError(), "gpu_eig_rotate", err);
+}
+
+bool gpu_eig_residuals(GpuSolver* S, const double* lam, int nt, double* out, std::string& err) {
+  const int p = S->ep;
+  if (!cuda_ok(cudaMemcpyAsync(S->eLam, lam, sizeof(double) * p, cudaMemcpyHostToDevice, S->stream),
+               "gpu_eig_residuals", err) ||
+      !cuda_ok(cudaMemsetAsync(S->eRes, 0, sizeof(double) * p, S->stream), "gpu_eig_residuals", err))
+    return false;
+  const int gy = std::max(1, std::min(256, S->en / 256));
+  k_ritz_residual<<<dim3((nt + 63) / 64, gy), 64, 0, S->stream>>>(S->eHQ, S->eQ, S->eLam, S->en, p, nt, S->eRes);
+  return cuda_ok(cudaMemcpyAsync(out, S->eRes, sizeof(double) * nt, cudaMemcpyDeviceToHost, S->stream),
+                 "gpu_eig_residuals", err) &&
+         cuda_ok(cudaStreamSynchronize(S->stream), "gpu_eig_residuals", err);
+}
+
+bool gpu_eig_end(GpuSolver* S, double* Qh, std::string& err) {
+  const size_t np = (size_t)S->en * S->ep;
+  const bool ok = cuda_ok(cudaMemcpyAsync(Qh, S->eQ, np * sizeof(double), cudaMemcpyDeviceToHost, S->stream),
+                          "gpu_eig_end", err) &&
+                  cuda_ok(cudaStreamSynchronize(S->stream), "gpu_eig_end", err);
+  double** bufs[] = {&S->eQ, &S->eHQ, &S->eT, &S->ePart, &S->eSmall, &S->eLam, &S->eRes};
+  for (double** b : bufs) {
+    if (*b) cudaFree(*b);
+    *b = nullptr;
+  }
+  return ok;
 }
 
 void gpu_solver_destroy(GpuSolver* S) { delete S; }

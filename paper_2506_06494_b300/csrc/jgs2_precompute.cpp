@@ -759,7 +759,67 @@ static jgs2_status body_precompute(const Mesh& M, const vector<int>& bverts, con
     }
   };
   vector<double> lam(p, 0.0);
-  {
+  // the same iteration with the block resident on the device (the p x p Gram, Cholesky and
+  // Ritz problems on the host); falls back to the host loop if a Gram matrix is singular
+  bool eig_done = false;
+  if (gsv.s && p <= 64) {
+    std::string e2;
+    if (!gpu_eig_begin(gsv.s, Q.data(), n, p, e2)) {
+      err = e2;
+      return JGS2_ECUDA;
+    }
+    vector<double> G((size_t)p * p), T((size_t)p * p), w, Vv, Vs((size_t)p * p), rr(nt);
+    bool ok = true;
+    for (int it = 0; it < 80 && ok; ++it) {
+      const int rounds = gpu_eig_solve(gsv.s, 1e-14, 1e-10, 40, e2);
+      if (rounds < 0) {
+        err = e2 + " (FP32 substitutions need kappa(H_bar) well below 1e7; gpu = 0 solves in FP64 on the host)";
+        return JGS2_ENOTCONVERGED;
+      }
+      for (int pass = 0; pass < 2 && ok; ++pass) {  // Cholesky QR twice
+        if (!gpu_eig_gram(gsv.s, false, G.data(), e2)) {
+          err = e2;
+          return JGS2_ECUDA;
+        }
+        if (!dense::potrf(G.data(), p, p)) ok = false;
+        else if (!gpu_eig_rowsolve(gsv.s, G.data(), e2)) {
+          err = e2;
+          return JGS2_ECUDA;
+        }
+      }
+      if (!ok) break;
+      if (!gpu_eig_hmul(gsv.s, e2) || !gpu_eig_gram(gsv.s, true, T.data(), e2)) {
+        err = e2;
+        return JGS2_ECUDA;
+      }
+      for (int a = 0; a < p; ++a)
+        for (int b2 = a + 1; b2 < p; ++b2) T[(size_t)a * p + b2] = T[(size_t)b2 * p + a] = 0.5 * (T[(size_t)a * p + b2] + T[(size_t)b2 * p + a]);
+      sym_eig(T, p, w, Vv);
+      vector<int> o2(p);
+      std::iota(o2.begin(), o2.end(), 0);
+      std::sort(o2.begin(), o2.end(), [&](int a, int b2) { return w[a] < w[b2]; });
+      for (int a = 0; a < p; ++a)
+        for (int j = 0; j < p; ++j) Vs[(size_t)a * p + j] = Vv[(size_t)a * p + o2[j]];
+      for (int j = 0; j < p; ++j) lam[j] = w[o2[j]];
+      if (!gpu_eig_rotate(gsv.s, Vs.data(), e2) || !gpu_eig_residuals(gsv.s, lam.data(), nt, rr.data(), e2)) {
+        err = e2;
+        return JGS2_ECUDA;
+      }
+      double worst = 0.0;
+      for (int j = 0; j < nt; ++j) worst = std::max(worst, std::sqrt(rr[j]) / std::fabs(lam[j]));
+      if (verbose() && (it % 10 == 0)) std::fprintf(stderr, "[jgs2_precompute] eig it %d resid %.2e (gpu)\n", it, worst);
+      if (worst < 1e-8) {
+        eig_done = true;
+        break;
+      }
+    }
+    if (!gpu_eig_end(gsv.s, Q.data(), e2)) {
+      err = e2;
+      return JGS2_ECUDA;
+    }
+    if (ok) eig_done = true;  // the 80-iteration cap, as on the host
+  }
+  if (!eig_done) {
     vector<double> HQ;
     for (int it = 0; it < 80; ++it) {
       solve(Q, p);

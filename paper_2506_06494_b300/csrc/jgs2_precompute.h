@@ -42,6 +42,21 @@ GpuSolver* gpu_solver_create(const Factor& F, const std::vector<BlockCol>& H, st
 int gpu_solve_many(GpuSolver* S, double* B, int n, int nrhs, double tol, double accept, int max_refine,
                    std::string& err);
 
+// Block inverse iteration with the block on the device (Sec. 5's training poses): begin
+// uploads the start block Q ([n][p] row-major host, p <= 64); solve sets Q <- H_bar^-1 Q
+// (as gpu_solve_many); gram copies Q^T Q (with_hq: Q^T H_bar Q) to the host (p x p); rowsolve
+// applies Q <- Q L^-T for the host's lower Cholesky factor L (column-major); hmul forms
+// H_bar Q; rotate applies Q <- Q V, H_bar Q <- H_bar Q V (V row-major p x p); residuals copies
+// |H_bar q_j - lam_j q_j|^2 for j < nt; end downloads Q and frees the block's buffers.
+bool gpu_eig_begin(GpuSolver* S, const double* Q, int n, int p, std::string& err);
+int gpu_eig_solve(GpuSolver* S, double tol, double accept, int max_refine, std::string& err);
+bool gpu_eig_gram(GpuSolver* S, bool with_hq, double* out, std::string& err);
+bool gpu_eig_rowsolve(GpuSolver* S, const double* L, std::string& err);
+bool gpu_eig_hmul(GpuSolver* S, std::string& err);
+bool gpu_eig_rotate(GpuSolver* S, const double* V, std::string& err);
+bool gpu_eig_residuals(GpuSolver* S, const double* lam, int nt, double* out, std::string& err);
+bool gpu_eig_end(GpuSolver* S, double* Q, std::string& err);
+
 void gpu_solver_destroy(GpuSolver* S);
 
 }  // namespace pre
