@@ -100,7 +100,8 @@ typedef struct {
   int32_t gpu;         /* 1 = the multi-RHS solves of the training poses and of the pool rows
                         * of H_bar^{-1} run on the current CUDA device (FP32 substitutions with
                         * the factor, refined in FP64 against H_bar to a relative residual of
-                        * 1e-14, accepted at 1e-10, else JGS2_ENOTCONVERGED); 0 = host FP64
+                        * 1e-14; a body whose refinement stalls above 1e-10, kappa(H_bar) being
+                        * too large for FP32, takes the host's FP64 substitutions); 0 = host FP64
                         * substitutions. Factorisation, selected inversion and NNLS stay on
                         * the host either way. Gauss-Seidel groups (gs = 1) solve on the host */
 } jgs2_precompute_opts;

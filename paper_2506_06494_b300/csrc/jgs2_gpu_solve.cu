@@ -765,7 +765,7 @@ static int solve_core(GpuSolver* S, int n, int k, double tol, double accept, int
   }
   if (!(worst <= accept)) {
     if (err.empty())
-      err = "gpu_solve_many: refinement ended at relative residual " + std::to_string(worst) + " after " +
+      err = "gpu_solve_many: refinement ended at relative residual " + std::to_string(worst * 1e10) + "e-10" + " after " +
             std::to_string(rounds) + " rounds";
     rounds = -1;
   }

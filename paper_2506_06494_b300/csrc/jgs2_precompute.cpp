@@ -674,19 +674,26 @@ static jgs2_status body_precompute(const Mesh& M, const vector<int>& bverts, con
     if (!gsv.s) return JGS2_ECUDA;
     PHASE("gpu upload");
   }
-  jgs2_status solve_st = JGS2_OK;
+  // A body whose FP32-substitution refinement stalls above 1e-10 (kappa(H_bar) too large for
+  // FP32) takes the host's FP64 substitutions from then on.
+  bool use_gpu = gsv.s != nullptr;
+  auto to_host = [&](const std::string& why) {
+    if (verbose()) std::fprintf(stderr, "[jgs2_precompute] gpu solves stopped (%s); host solves\n", why.c_str());
+    use_gpu = false;
+  };
   auto solve = [&](vector<double>& B, int k) {
-    if (solve_st != JGS2_OK) return;
-    if (!gsv.s) {
+    if (!use_gpu) {
       solve_many(F, B, n, k);
       return;
     }
+    vector<double> B0(B);  // the right-hand sides, for a host solve if the refinement stalls
     std::string e2;
     const int rounds = gpu_solve_many(gsv.s, B.data(), n, k, 1e-14, 1e-10, 40, e2);
     if (verbose()) std::fprintf(stderr, "[jgs2_precompute] gpu solve: %d columns, %d refinement rounds\n", k, rounds);
     if (rounds < 0) {
-      err = e2 + " (FP32 substitutions need kappa(H_bar) well below 1e7; gpu = 0 solves in FP64 on the host)";
-      solve_st = JGS2_ENOTCONVERGED;
+      to_host(e2);
+      B.swap(B0);
+      solve_many(F, B, n, k);
     }
   };
   // ---- training poses: lowest eigenpairs by block inverse iteration
@@ -762,7 +769,7 @@ static jgs2_status body_precompute(const Mesh& M, const vector<int>& bverts, con
   // the same iteration with the block resident on the device (the p x p Gram, Cholesky and
   // Ritz problems on the host); falls back to the host loop if a Gram matrix is singular
   bool eig_done = false;
-  if (gsv.s && p <= 64) {
+  if (use_gpu && p <= 64) {
     std::string e2;
     if (!gpu_eig_begin(gsv.s, Q.data(), n, p, e2)) {
       err = e2;
@@ -772,9 +779,10 @@ static jgs2_status body_precompute(const Mesh& M, const vector<int>& bverts, con
     bool ok = true;
     for (int it = 0; it < 80 && ok; ++it) {
       const int rounds = gpu_eig_solve(gsv.s, 1e-14, 1e-10, 40, e2);
-      if (rounds < 0) {
-        err = e2 + " (FP32 substitutions need kappa(H_bar) well below 1e7; gpu = 0 solves in FP64 on the host)";
-        return JGS2_ENOTCONVERGED;
+      if (rounds < 0) {  // the block is still the one before this solve
+        to_host(e2);
+        ok = false;
+        break;
       }
       for (int pass = 0; pass < 2 && ok; ++pass) {  // Cholesky QR twice
         if (!gpu_eig_gram(gsv.s, false, G.data(), e2)) {
@@ -823,7 +831,6 @@ static jgs2_status body_precompute(const Mesh& M, const vector<int>& bverts, con
     vector<double> HQ;
     for (int it = 0; it < 80; ++it) {
       solve(Q, p);
-      if (solve_st != JGS2_OK) return solve_st;
       orthonormalise(Q, p);
       Hmul(Q, HQ, p);
       vector<double> T((size_t)p * p, 0.0), w, Vv;
@@ -1106,7 +1113,7 @@ static jgs2_status body_precompute(const Mesh& M, const vector<int>& bverts, con
   vector<float> G32(g64 ? 0 : (size_t)nf * np * 9);
   auto Gat = [&](size_t q) -> double { return g64 ? G64[q] : (double)G32[q]; };
   {
-    const int batch = gsv.s ? 768 : 384;  // RHS per batch (multiple of 3)
+    const int batch = use_gpu ? 768 : 384;  // RHS per batch (multiple of 3)
     for (int q0 = 0; q0 < 3 * np; q0 += batch) {
       const int k = std::min(batch, 3 * np - q0);
       vector<double> Bm((size_t)n * k, 0.0);
@@ -1116,7 +1123,6 @@ static jgs2_status body_precompute(const Mesh& M, const vector<int>& bverts, con
         Bm[(size_t)(3 * pos[v] + col % 3) * k + j] = 1.0;
       }
       solve(Bm, k);
-      if (solve_st != JGS2_OK) return solve_st;
       for (int f = 0; f < nf; ++f)
         for (int j = 0; j < k; ++j) {
           const int col = q0 + j, q = col / 3, c = col % 3;
