@@ -44,7 +44,8 @@ typedef enum {
                               * along a conjugate-gradient search direction */
   JGS2_ETIMEOUT = 8,         /* a bounded device wait (bulk-copy barrier) gave up; state NOT written */
   JGS2_EINTERSECT = 9        /* contact: a surface pair reached zero distance at a sweep's positions;
-                              * state NOT written */
+                              * state NOT written. jgs2_cloth_create: a free rest vertex on or
+                              * behind a wall */
 } jgs2_status;
 
 /* Mesh description (Sec. 3). All pointers are host pointers, copied at create. */
@@ -441,13 +442,15 @@ typedef struct {
 } jgs2_cloth_report;
 
 /* Validates the cloth (indices in range, positive areas, material ranges, every free vertex
- * in a triangle; JGS2_EINVAL otherwise), computes the rest data in FP64 on the host and
- * finds the interior edges. Device memory is taken on the first call that needs it, on
+ * in a triangle, unit wall normals; JGS2_EINVAL otherwise; JGS2_EINTERSECT when a free rest
+ * vertex is not strictly on the open side n.x > c of every wall), computes the rest data in
+ * FP64 on the host and finds the interior edges. Device memory is taken on the first call that needs it, on
  * the then-current device (later calls must use the same device). */
 jgs2_status jgs2_cloth_create(const jgs2_cloth_desc* desc, jgs2_cloth** out);
 
 /* One implicit-Euler step: x, v device [V][3] double (caller order), overwritten with
- * x_{t+1}, v_{t+1} = (x_{t+1} - x_t)/h. Uses opts->precision, max_sweeps, rel_tol,
+ * x_{t+1}, v_{t+1} = (x_{t+1} - x_t)/h. With walls, every free vertex of x must be strictly
+ * on the open side of every wall (a step keeps it there; the barrier is undefined behind). Uses opts->precision, max_sweeps, rel_tol,
  * line_search and check_every (sweeps between host checks of the stopping test); the
  * other options are ignored. JGS2_ENOTCONVERGED when the cap was reached (state written),
  * JGS2_EDIVERGED if the residual became NaN/Inf. Synchronises the stream. */

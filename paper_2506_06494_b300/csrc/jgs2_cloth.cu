@@ -657,6 +657,15 @@ jgs2_status cloth_device(Cloth* c) {
     return JGS2_OK;
   }
   CKC(cudaGetDevice(&c->device));
+  // a failed earlier call may have left some of these allocated
+  void* prior[] = {c->d_tri_off, c->d_tri_inc, c->d_hin_off, c->d_hin_inc, c->d_pinned,
+                   c->d_xt,      c->d_partial, c->d_state,   c->d_planes};
+  for (void* q : prior)
+    if (q) cudaFree(q);
+  c->d_tri_off = c->d_tri_inc = c->d_hin_off = c->d_hin_inc = nullptr;
+  c->d_pinned = nullptr;
+  c->d_xt = c->d_partial = c->d_planes = nullptr;
+  c->d_state = nullptr;
   const int V = c->V;
   CKC(cdalloc(&c->d_tri_off, V + 1));
   CKC(cdalloc(&c->d_tri_inc, c->tri_inc.size()));
@@ -696,6 +705,7 @@ jgs2_status cloth_prec(Cloth* c) {
   if (st != JGS2_OK) return st;
   ClothBufs<T>& b = cbufs<T>(c);
   if (b.ready) return JGS2_OK;
+  b.release();  // what a failed earlier call left allocated
   const int V = c->V, F = c->F, H = c->H;
   std::vector<TriRec<T>> tr(F);
   for (int t = 0; t < F; ++t) {
@@ -839,6 +849,19 @@ jgs2_status cloth_create(const jgs2_cloth_desc* d, Cloth** out) {
   if (d->pinned)
     for (int v = 0; v < V; ++v) c->pinned[v] = d->pinned[v] ? 1 : 0;
   const double* X = d->rest_pos;
+  // walls: unit normals, and every free vertex of the rest state strictly on the open side
+  // (the barrier is undefined at and behind a wall)
+  for (int p = 0; p < d->n_planes; ++p) {
+    const double* pl = d->planes + 4 * (size_t)p;
+    const double nn = std::sqrt(pl[0] * pl[0] + pl[1] * pl[1] + pl[2] * pl[2]);
+    if (!std::isfinite(pl[3]) || !(std::fabs(nn - 1.0) <= 1e-9))
+      return fail(JGS2_EINVAL, "cloth wall " + std::to_string(p) + ": the normal must be a unit vector, the offset finite");
+    for (int v = 0; v < V; ++v)
+      if (!c->pinned[v] && !(pl[0] * X[3 * (size_t)v] + pl[1] * X[3 * (size_t)v + 1] + pl[2] * X[3 * (size_t)v + 2] -
+                                 pl[3] > 0.0))
+        return fail(JGS2_EINTERSECT, "free rest vertex " + std::to_string(v) + " is on or behind cloth wall " +
+                                         std::to_string(p));
+  }
   c->b.resize(6 * (size_t)F);
   c->area.resize(F);
   c->mu.assign(F, d->youngs * d->thickness / (2.0 * (1.0 + d->poisson)));

@@ -206,6 +206,34 @@ def test_cloth_create_rejects_bad_input(case):
                 dt=kw["dt"])
 
 
+@pytest.mark.parametrize("case", ["normal", "offset", "behind", "on"])
+def test_cloth_walls_are_validated(case):
+    s = scenes.cloth_floor_scene(n=4)
+    X, planes = s.X.copy(), s.planes.copy()
+    want = 1  # JGS2_EINVAL
+    if case == "normal":
+        planes[0, :3] *= 2.0
+    elif case == "offset":
+        planes[0, 3] = np.nan
+    elif case == "behind":
+        X[5, 2] = -1e-4
+        want = 9  # JGS2_EINTERSECT: a free rest vertex behind the floor
+    elif case == "on":
+        X[5, 2] = 0.0
+        want = 9
+    with pytest.raises(J.JGS2Error) as e:
+        J.Cloth(X, s.tris, s.youngs, s.poisson, s.thickness, s.density, s.bend, s.pinned, dt=s.dt,
+                planes=planes, dhat=s.dhat, kappa=s.kappa)
+    assert e.value.status == want
+    # a pinned vertex may sit anywhere
+    if case in ("behind", "on"):
+        pin = s.pinned.copy()
+        pin[5] = 1
+        c = J.Cloth(X, s.tris, s.youngs, s.poisson, s.thickness, s.density, s.bend, pin, dt=s.dt,
+                    planes=planes, dhat=s.dhat, kappa=s.kappa)
+        c.close()
+
+
 def test_cloth_hinges_are_the_interior_edges():
     # an n x n grid cut into 2 triangles per cell has 2 n (n - 1) + (n - 1)^2 edges, 4 (n - 1)
     # of them on the boundary
