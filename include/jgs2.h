@@ -67,7 +67,8 @@ typedef struct {
    * surface vertex - wall plane n.x >= c; both forms keep the per-vertex step limit. */
   int32_t contact;
   int32_t n_planes;          /* walls */
-  const double* planes;      /* [n_planes][4]: unit normal n (3) and offset c; may be NULL if 0 */
+  const double* planes;      /* [n_planes][4]: unit normal n (3) and finite offset c (JGS2_EINVAL
+                              * otherwise); may be NULL if 0 */
   double dhat;               /* barrier support d^ (m) > 0 */
   double kappa;              /* barrier or penalty stiffness (N/m) > 0 */
   /* Friction on the walls (IPC's lagged friction potential; the paper's friction scenes).

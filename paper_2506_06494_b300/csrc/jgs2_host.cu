@@ -285,6 +285,12 @@ jgs2_status mesh_create(const jgs2_mesh_desc* d, Mesh** out, const std::vector<i
     m->kappa = d->kappa;
     m->rc = 2.0 * d->dhat;
     m->planes.assign(d->planes, d->planes + 4 * (size_t)d->n_planes);
+    for (int p = 0; p < d->n_planes; ++p) {
+      const double* pl = &m->planes[4 * (size_t)p];
+      const double nn = std::sqrt(pl[0] * pl[0] + pl[1] * pl[1] + pl[2] * pl[2]);
+      if (!std::isfinite(pl[3]) || !(std::fabs(nn - 1.0) <= 1e-9))
+        return fail(JGS2_EINVAL, "wall " + std::to_string(p) + ": the normal must be a unit vector, the offset finite");
+    }
     std::map<std::array<int, 3>, std::pair<std::array<int, 3>, int>> fc;
     std::map<std::array<int, 3>, int> count;
     for (int t = 0; t < T; ++t) {

@@ -126,6 +126,30 @@ def test_contact_form_is_validated(L):
             L.jgs2_mesh_destroy(h)
 
 
+def test_wall_planes_are_validated(L):
+    """Wall normals must be unit vectors and offsets finite (the barrier's distance n.x - c
+    assumes both)."""
+    s = scenes.drop_scene()
+    X, T = np.ascontiguousarray(s.X), s.tets.astype(np.int32)
+    E, nu, rho = s.youngs.copy(), s.poisson.copy(), s.density.copy()
+    for bad in ("scaled", "nan_offset", "zero"):
+        planes = np.ascontiguousarray(s.planes, dtype=np.float64).copy()
+        if bad == "scaled":
+            planes[1, :3] *= 1.5
+        elif bad == "nan_offset":
+            planes[2, 3] = np.inf
+        else:
+            planes[0, :3] = 0.0
+        d = _desc(X, T, E, nu, rho, None)
+        d.contact = 1
+        d.n_planes = len(planes)
+        d.planes = planes.ctypes.data_as(C.POINTER(C.c_double))
+        d.dhat = s.dhat
+        d.kappa = s.kappa
+        h = C.c_void_p()
+        assert L.jgs2_mesh_create(C.byref(d), C.byref(h)) == 1, bad
+
+
 def test_null_arguments(L):
     h = C.c_void_p()
     assert L.jgs2_mesh_create(None, C.byref(h)) == 1
