@@ -637,7 +637,7 @@ GpuSolver* gpu_solver_create(const Factor& F, const std::vector<BlockCol>& H, st
   if (ok) {
     std::vector<float> buf;
     for (int s = 0; s < ns && ok; ++s) {
-      const std::vector<double>& Ls = F.L[s];
+      const RawVec& Ls = F.L[s];
       buf.resize(Ls.size());
       for (size_t q = 0; q < Ls.size(); ++q) buf[q] = (float)Ls[q];
       const cudaError_t e =

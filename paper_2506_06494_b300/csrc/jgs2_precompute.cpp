@@ -279,6 +279,7 @@ static void nd_order(const vector<double>& P, const vector<vector<int>>& adj, ve
   for (int v : sep) out.push_back(v);
 }
 
+
 // Multifrontal supernodal Cholesky of the block matrix given by its lower block columns.
 static bool factorize(int nv, const vector<BlockCol>& H, Factor& F) {
   F.nv = nv;
@@ -353,17 +354,56 @@ static bool factorize(int nv, const vector<BlockCol>& H, Factor& F) {
     if (parent[last] >= 0) skids[F.sn_of[parent[last]]].push_back(s);
   }
   F.L.assign(ns, {});
-  vector<vector<double>> upd(ns);  // update matrices, (3 nR)^2 column-major lower
-  vector<int> loc(nv, -1);
-  for (int s = 0; s < ns; ++s) {
+  vector<RawVec> upd(ns);  // update matrices, (3 nR)^2 column-major, lower triangle used
+  // Large update matrices are recycled from front to front, one pool per thread: a fresh
+  // allocation of that size costs a page fault per page on first touch, which dominated
+  // the fronts near the root and contends between threads deeper down.
+  const int nthr = std::max(1, omp_get_max_threads());
+  vector<vector<RawVec>> spares(nthr);
+  auto take = [&](size_t n) {
+    RawVec v;
+    vector<RawVec>& spare = spares[omp_get_thread_num() % nthr];
+    if (n >= (size_t)1 << 14) {
+      int best = -1;
+      for (int q = 0; q < (int)spare.size(); ++q)
+        if (spare[q].capacity() >= n && (best < 0 || spare[q].capacity() < spare[best].capacity())) best = q;
+      if (best >= 0) {
+        v.swap(spare[best]);
+        spare.erase(spare.begin() + best);
+      }
+    }
+    v.resize(n);  // not initialised: the caller zeroes what it reads
+    return v;
+  };
+  auto release = [&](RawVec& v) {
+    vector<RawVec>& spare = spares[omp_get_thread_num() % nthr];
+    if (v.capacity() >= (size_t)1 << 14) {
+      spare.push_back(std::move(v));
+      if (spare.size() > 3) {  // keep the largest few
+        auto small = std::min_element(spare.begin(), spare.end(),
+                                      [](const RawVec& a, const RawVec& b) { return a.capacity() < b.capacity(); });
+        spare.erase(small);
+      }
+    }
+    v = RawVec();
+  };
+  // One front: assemble supernode s's columns and its children's updates, factor them,
+  // leave its own update matrix. loc is a scratch map vertex -> front row (-1 elsewhere).
+  auto front = [&](int s, vector<int>& loc) -> bool {
     const int f = F.sn_first[s], l = F.sn_first[s + 1];
     const int nJ = 3 * (l - f);
     const vector<int>& R = F.sn_rows[s];
     const int nR = 3 * (int)R.size();
     const int m = nJ + nR;
-    vector<double>& Fm = F.L[s];
-    Fm.assign((size_t)m * nJ, 0.0);
-    vector<double> U((size_t)nR * nR, 0.0);
+    RawVec& Fm = F.L[s];
+    Fm = RawVec((size_t)m * nJ);
+    // zeroed by columns, in parallel for a large front (its first touch)
+#pragma omp parallel for schedule(static) if (!omp_in_parallel() && (size_t)m * nJ >= ((size_t)1 << 20))
+    for (int j = 0; j < nJ; ++j) std::memset(&Fm[(size_t)j * m], 0, sizeof(double) * m);
+    RawVec U = take((size_t)nR * nR);
+    // only the lower triangle of an update matrix is formed and read
+#pragma omp parallel for schedule(dynamic, 64) if (!omp_in_parallel() && nR >= 768)
+    for (int j = 0; j < nR; ++j) std::memset(&U[(size_t)j * nR + j], 0, sizeof(double) * (nR - j));
     for (int v = f; v < l; ++v) loc[v] = 3 * (v - f);
     for (size_t q = 0; q < R.size(); ++q) loc[R[q]] = nJ + 3 * (int)q;
     // original entries of the columns of J
@@ -384,25 +424,28 @@ static bool factorize(int nv, const vector<BlockCol>& H, Factor& F) {
     for (int c : skids[s]) {
       const vector<int>& Rc = F.sn_rows[c];
       const int nc = 3 * (int)Rc.size();
-      const vector<double>& Uc = upd[c];
+      const RawVec& Uc = upd[c];
       vector<int> map(nc);
       for (size_t q = 0; q < Rc.size(); ++q)
         for (int a = 0; a < 3; ++a) map[3 * q + a] = loc[Rc[q]] + a;
+      // map is increasing (front rows follow vertex order), so column cc of the child's
+      // lower triangle lands in column map[cc] alone: columns are independent
+#pragma omp parallel for schedule(dynamic, 16) if (!omp_in_parallel() && nc >= 384)
       for (int cc = 0; cc < nc; ++cc) {
         const int gc = map[cc];
-        for (int rr = cc; rr < nc; ++rr) {
-          const double val = Uc[rr + (size_t)cc * nc];
-          int gr = map[rr], gcc = gc;
-          if (gr < gcc) std::swap(gr, gcc);
-          if (gcc < nJ)
-            Fm[gr + (size_t)gcc * m] += val;
-          else
-            U[(gr - nJ) + (size_t)(gcc - nJ) * nR] += val;
+        const double* uc = &Uc[(size_t)cc * nc];
+        if (gc < nJ) {
+          double* fc = &Fm[(size_t)gc * m];
+          for (int rr = cc; rr < nc; ++rr) fc[map[rr]] += uc[rr];
+        } else {
+          double* uo = &U[(size_t)(gc - nJ) * nR];
+          for (int rr = cc; rr < nc; ++rr) uo[map[rr] - nJ] += uc[rr];
         }
       }
-      upd[c].clear();
-      upd[c].shrink_to_fit();
+      release(upd[c]);
     }
+    for (int v = f; v < l; ++v) loc[v] = -1;
+    for (int u : R) loc[u] = -1;
     // partial factorisation
     if (!dense::potrf(Fm.data(), nJ, m)) return false;
     if (nR > 0) {
@@ -411,8 +454,46 @@ static bool factorize(int nv, const vector<BlockCol>& H, Factor& F) {
       dense::gemm(false, true, nR, nR, nJ, -1.0, LR, m, LR, m, U.data(), nR, true);
       upd[s].swap(U);
     }
-    for (int v = f; v < l; ++v) loc[v] = -1;
-    for (int u : R) loc[u] = -1;
+    return true;
+  };
+  // Fronts by height in the supernode tree (leaves 0, a parent above all its children):
+  // the fronts of one height are independent. Within a height, a front costing more than
+  // a thread's share of the height runs alone on parallel dense kernels; the others run one
+  // per thread (their kernels single-threaded), largest first. Each front's arithmetic
+  // does not depend on the schedule.
+  vector<int> height(ns, 0);
+  int nh = 0;
+  for (int s = 0; s < ns; ++s) {  // children precede parents
+    for (int c : skids[s]) height[s] = std::max(height[s], height[c] + 1);
+    nh = std::max(nh, height[s] + 1);
+  }
+  vector<vector<int>> by_h(nh);
+  for (int s = 0; s < ns; ++s) by_h[height[s]].push_back(s);
+  vector<vector<int>> locs(nthr, vector<int>(nv, -1));
+  auto cost = [&](int s) {
+    const double nJ = 3.0 * (F.sn_first[s + 1] - F.sn_first[s]), nR = 3.0 * F.sn_rows[s].size();
+    return nJ * nJ * nJ / 3.0 + nJ * nJ * nR + nJ * nR * nR + 4.0 * nR * nR;
+  };
+  for (int h = 0; h < nh; ++h) {
+    vector<int> lv = by_h[h];
+    std::stable_sort(lv.begin(), lv.end(), [&](int a, int b2) { return cost(a) > cost(b2); });
+    double total = 0.0;
+    for (int q : lv) total += cost(q);
+    int nbig = 0;  // the leading fronts above a thread's share
+    while (nbig < (int)lv.size() && cost(lv[nbig]) > total / nthr) ++nbig;
+    for (int q = 0; q < nbig; ++q)
+      if (!front(lv[q], locs[0])) return false;
+    const int rest = (int)lv.size() - nbig;
+    if (rest >= 2 && nthr > 1 && !omp_in_parallel()) {
+      int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthr) reduction(| : bad)
+      for (int q = nbig; q < (int)lv.size(); ++q)
+        if (!front(lv[q], locs[omp_get_thread_num()])) bad |= 1;
+      if (bad) return false;
+    } else {
+      for (int q = nbig; q < (int)lv.size(); ++q)
+        if (!front(lv[q], locs[0])) return false;
+    }
   }
   return true;
 }
@@ -481,20 +562,36 @@ static void solve_many(const Factor& F, vector<double>& B /* n x nrhs row-major 
 static void selected_inverse_diag(Factor& F, vector<double>& Adiag /* nv x 9 */) {
   const int ns = F.nsn();
   Adiag.assign((size_t)F.nv * 9, 0.0);
-  for (int s = ns - 1; s >= 0; --s) {
+  // Work buffers, one set per thread, reused from supernode to supernode (fresh large
+  // allocations cost a page fault per page, which dominated the deep supernodes)
+  struct Bufs {
+    RawVec Li, Y, ZRR, ZRJ, ZJJ;
+  };
+  auto sized = [](RawVec& v, size_t n, bool zero) {
+    if (v.capacity() < n)
+      v = RawVec(n);
+    else
+      v.resize(n);
+    if (zero) std::memset(v.data(), 0, sizeof(double) * n);
+    return v.data();
+  };
+  const int nthr = std::max(1, omp_get_max_threads());
+  vector<Bufs> bufs(nthr);
+  // Z of supernode s from the Z of its ancestors (the supernodes of its rows)
+  auto sel = [&](int s, Bufs& b) {
     const int f = F.sn_first[s], nJ = 3 * (F.sn_first[s + 1] - f);
     const vector<int>& R = F.sn_rows[s];
     const int nR = 3 * (int)R.size();
     const int m = nJ + nR;
-    vector<double>& L = F.L[s];
+    RawVec& L = F.L[s];
     // Li = L_JJ^{-1} (lower), Y = L_RJ Li  (nR x nJ)
-    vector<double> Li((size_t)nJ * nJ);
-    dense::trtri_lower(L.data(), nJ, m, Li.data());
-    vector<double> Y((size_t)nR * nJ, 0.0);
-    dense::gemm(false, false, nR, nJ, nJ, 1.0, L.data() + nJ, m, Li.data(), nJ, Y.data(), nR);
-    // Z_RR gathered from the ancestors (already holding Z)
-    vector<double> ZRR((size_t)nR * nR, 0.0);
-#pragma omp parallel for schedule(dynamic, 4) if (R.size() > 64)
+    double* Li = sized(b.Li, (size_t)nJ * nJ, false);  // trtri writes all of it
+    dense::trtri_lower(L.data(), nJ, m, Li);
+    double* Y = sized(b.Y, (size_t)nR * nJ, true);
+    dense::gemm(false, false, nR, nJ, nJ, 1.0, L.data() + nJ, m, Li, nJ, Y, nR);
+    // Z_RR gathered from the ancestors (already holding Z); the gather writes every entry
+    double* ZRR = sized(b.ZRR, (size_t)nR * nR, false);
+#pragma omp parallel for schedule(dynamic, 4) if (!omp_in_parallel() && R.size() > 64)
     for (int cb = 0; cb < (int)R.size(); ++cb) {
       const int v2 = R[cb];
       const int K = F.sn_of[v2];
@@ -502,36 +599,47 @@ static void selected_inverse_diag(Factor& F, vector<double>& Adiag /* nv x 9 */)
       const vector<int>& RK = F.sn_rows[K];
       const int mK = nJK + 3 * (int)RK.size();
       const double* Z = F.L[K].data();
+      // rows v1 = R[rb] ascend, so their places in K's row structure (which holds every
+      // row of s beyond K's own columns) are found by one forward walk
+      size_t pos = 0;
       for (int rb = cb; rb < (int)R.size(); ++rb) {
         const int v1 = R[rb];
         int lr;
         if (v1 < F.sn_first[K + 1]) {
           lr = 3 * (v1 - fK);
         } else {
-          const auto it = std::lower_bound(RK.begin(), RK.end(), v1);
-          lr = nJK + 3 * (int)(it - RK.begin());
+          while (RK[pos] < v1) ++pos;
+          lr = nJK + 3 * (int)pos;
         }
         const int lc = 3 * (v2 - fK);
-        for (int a = 0; a < 3; ++a)
-          for (int c = 0; c < 3; ++c) {
-            int rr = lr + a, cc = lc + c;
-            double z;
-            if (rr >= cc)
-              z = Z[rr + (size_t)cc * mK];
-            else
-              z = Z[cc + (size_t)rr * mK];  // within the diagonal block of K (symmetric)
-            const int gi = 3 * rb + a, gj = 3 * cb + c;
-            ZRR[gi + (size_t)gj * nR] = z;
-            ZRR[gj + (size_t)gi * nR] = z;
+        // columns of the block's lower triangle (the whole block on the diagonal)
+        for (int c = 0; c < 3; ++c) {
+          double* zc = ZRR + (size_t)(3 * cb + c) * nR + 3 * rb;
+          for (int a = 0; a < 3; ++a) {
+            const int rr = lr + a, cc = lc + c;
+            zc[a] = rr >= cc ? Z[rr + (size_t)cc * mK] : Z[cc + (size_t)rr * mK];  // K's diagonal block is symmetric
           }
+        }
       }
     }
+    // upper triangle from the lower one, by tiles
+    {
+      constexpr int TB = 48;
+      const int nt = (nR + TB - 1) / TB;
+#pragma omp parallel for schedule(dynamic, 1) if (!omp_in_parallel() && nR >= 768)
+      for (int tj = 0; tj < nt; ++tj)
+        for (int ti = tj; ti < nt; ++ti) {
+          const int i0 = ti * TB, i1 = std::min(nR, i0 + TB), j0 = tj * TB, j1 = std::min(nR, j0 + TB);
+          for (int j = j0; j < j1; ++j)
+            for (int i = std::max(i0, j + 1); i < i1; ++i) ZRR[j + (size_t)i * nR] = ZRR[i + (size_t)j * nR];
+        }
+    }
     // Z_RJ = -Z_RR Y ; Z_JJ = Li^T Li - Y^T Z_RJ
-    vector<double> ZRJ((size_t)nR * nJ, 0.0);
-    dense::gemm(false, false, nR, nJ, nR, -1.0, ZRR.data(), nR, Y.data(), nR, ZRJ.data(), nR);
-    vector<double> ZJJ((size_t)nJ * nJ, 0.0);
-    dense::gemm(true, false, nJ, nJ, nJ, 1.0, Li.data(), nJ, Li.data(), nJ, ZJJ.data(), nJ);
-    dense::gemm(true, false, nJ, nJ, nR, -1.0, Y.data(), nR, ZRJ.data(), nR, ZJJ.data(), nJ);
+    double* ZRJ = sized(b.ZRJ, (size_t)nR * nJ, true);
+    dense::gemm(false, false, nR, nJ, nR, -1.0, ZRR, nR, Y, nR, ZRJ, nR);
+    double* ZJJ = sized(b.ZJJ, (size_t)nJ * nJ, true);
+    dense::gemm(true, false, nJ, nJ, nJ, 1.0, Li, nJ, Li, nJ, ZJJ, nJ);
+    dense::gemm(true, false, nJ, nJ, nR, -1.0, Y, nR, ZRJ, nR, ZJJ, nJ);
     // store Z in place of L
     for (int j = 0; j < nJ; ++j) {
       for (int i = 0; i < nJ; ++i) L[i + (size_t)j * m] = ZJJ[i + (size_t)j * nJ];
@@ -541,6 +649,40 @@ static void selected_inverse_diag(Factor& F, vector<double>& Adiag /* nv x 9 */)
       for (int a = 0; a < 3; ++a)
         for (int c = 0; c < 3; ++c)
           Adiag[(size_t)v * 9 + 3 * a + c] = ZJJ[(3 * (v - f) + a) + (size_t)(3 * (v - f) + c) * nJ];
+  };
+  // Supernodes by depth below their root (a parent's depth is less than its children's):
+  // those of one depth read only their ancestors' Z, so they are independent. Within a
+  // depth, a supernode costing more than a thread's share of the depth runs alone on
+  // parallel kernels; the others run one per thread, largest first. The schedule changes
+  // no arithmetic.
+  vector<int> depth(ns, 0);
+  int nd = 0;
+  for (int s = ns - 1; s >= 0; --s) {  // parents come after their children
+    const vector<int>& R = F.sn_rows[s];
+    depth[s] = R.empty() ? 0 : depth[F.sn_of[R[0]]] + 1;
+    nd = std::max(nd, depth[s] + 1);
+  }
+  vector<vector<int>> by_d(nd);
+  for (int s = ns - 1; s >= 0; --s) by_d[depth[s]].push_back(s);
+  auto cost = [&](int s) {
+    const double nJ = 3.0 * (F.sn_first[s + 1] - F.sn_first[s]), nR = 3.0 * F.sn_rows[s].size();
+    return nR * nR * (nJ + 4.0) + nJ * nJ * (nJ + nR);
+  };
+  for (int d = 0; d < nd; ++d) {
+    vector<int> lv = by_d[d];
+    std::stable_sort(lv.begin(), lv.end(), [&](int a, int b2) { return cost(a) > cost(b2); });
+    double total = 0.0;
+    for (int q : lv) total += cost(q);
+    int nbig = 0;  // the leading supernodes above a thread's share
+    while (nbig < (int)lv.size() && cost(lv[nbig]) > total / nthr) ++nbig;
+    for (int q = 0; q < nbig; ++q) sel(lv[q], bufs[0]);
+    const int rest = (int)lv.size() - nbig;
+    if (rest >= 2 && nthr > 1 && !omp_in_parallel()) {
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthr)
+      for (int q = nbig; q < (int)lv.size(); ++q) sel(lv[q], bufs[omp_get_thread_num()]);
+    } else {
+      for (int q = nbig; q < (int)lv.size(); ++q) sel(lv[q], bufs[0]);
+    }
   }
 }
 

@@ -2,11 +2,35 @@
 // supernodal Cholesky factor, and the device solver that runs the factor's multi-RHS
 // substitutions on the GPU.
 #pragma once
+#include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 namespace jgs2 {
 namespace pre {
+
+// An allocator that leaves new doubles uninitialised, so that the first touch of a large
+// buffer happens where its owner writes it (in parallel), not in a serial zero fill.
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <class U>
+  NoInitAlloc(const NoInitAlloc<U>&) {}
+  template <class U>
+  void construct(U* p) {
+    ::new ((void*)p) U;
+  }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) {
+    ::new ((void*)p) U(std::forward<A>(a)...);
+  }
+};
+typedef std::vector<double, NoInitAlloc<double>> RawVec;
 
 // Supernodal Cholesky factor H_bar = L L^T of one body (vertex blocks of 3 DOFs).
 struct Factor {
@@ -14,7 +38,7 @@ struct Factor {
   std::vector<int> sn_first;                 // supernode -> first vertex (factor order)
   std::vector<int> sn_of;                    // vertex -> supernode
   std::vector<std::vector<int>> sn_rows;     // supernode -> row structure below (vertices, ascending)
-  std::vector<std::vector<double>> L;        // supernode -> (3nJ + 3nR) x 3nJ column-major
+  std::vector<RawVec> L;                     // supernode -> (3nJ + 3nR) x 3nJ column-major
   int nsn() const { return (int)sn_first.size() - 1; }
 };
 
