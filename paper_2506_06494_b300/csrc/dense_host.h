@@ -186,6 +186,51 @@ static void trsm_rln(double* B, int m, int n, int ldb, const double* L, int ldl)
   }
 }
 
+// Right-looking forms of the two solves above, for a B with few rows (a block of
+// right-hand sides): after each diagonal block the rest of B is updated by one GEMM whose
+// output spans the remaining columns, so the work splits over threads by columns.
+// B (m x n) <- B L^{-T}.
+static void trsm_rlt_wide(double* B, int m, int n, int ldb, const double* L, int ldl) {
+  const int nb = 96;
+  for (int j0 = 0; j0 < n; j0 += nb) {
+    const int jb = std::min(nb, n - j0), j1 = j0 + jb;
+    for (int j = j0; j < j1; ++j) {
+      double* cj = B + (size_t)j * ldb;
+      for (int p = j0; p < j; ++p) {
+        const double l = L[j + (size_t)p * ldl];
+        const double* cp = B + (size_t)p * ldb;
+        for (int i = 0; i < m; ++i) cj[i] -= cp[i] * l;
+      }
+      const double inv = 1.0 / L[j + (size_t)j * ldl];
+      for (int i = 0; i < m; ++i) cj[i] *= inv;
+    }
+    // B[:, j1:n] -= B[:, j0:j1] L[j1:n, j0:j1]^T
+    if (j1 < n) gemm(false, true, m, n - j1, jb, -1.0, B + (size_t)j0 * ldb, ldb, L + j1 + (size_t)j0 * ldl, ldl,
+                     B + (size_t)j1 * ldb, ldb);
+  }
+}
+
+// B (m x n) <- B L^{-1}.
+static void trsm_rln_wide(double* B, int m, int n, int ldb, const double* L, int ldl) {
+  const int nb = 96;
+  const int nblk = (n + nb - 1) / nb;
+  for (int bk = nblk - 1; bk >= 0; --bk) {
+    const int j0 = bk * nb, jb = std::min(nb, n - j0), j1 = j0 + jb;
+    for (int j = j1 - 1; j >= j0; --j) {
+      double* cj = B + (size_t)j * ldb;
+      for (int p = j + 1; p < j1; ++p) {
+        const double l = L[p + (size_t)j * ldl];
+        const double* cp = B + (size_t)p * ldb;
+        for (int i = 0; i < m; ++i) cj[i] -= cp[i] * l;
+      }
+      const double inv = 1.0 / L[j + (size_t)j * ldl];
+      for (int i = 0; i < m; ++i) cj[i] *= inv;
+    }
+    // B[:, 0:j0] -= B[:, j0:j1] L[j0:j1, 0:j0]
+    if (j0 > 0) gemm(false, false, m, j0, jb, -1.0, B + (size_t)j0 * ldb, ldb, L + j0, ldl, B, ldb);
+  }
+}
+
 // Lower Cholesky in place; false if a pivot is not positive.
 static bool potrf(double* A, int n, int lda) {
   const int nb = 96;

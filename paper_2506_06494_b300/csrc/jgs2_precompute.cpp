@@ -540,8 +540,9 @@ static void solve_inplace(const Factor& F, double* X, int nrhs) {
   }
 }
 
-// Multi-RHS solve: the columns are split into one contiguous chunk per thread.
-static void solve_many(const Factor& F, vector<double>& B /* n x nrhs row-major */, int n, int nrhs) {
+// Multi-RHS solve for many right-hand sides: one contiguous chunk of columns per thread,
+// each a whole sequential solve (compute-bound once a chunk is a few dozen columns wide).
+static void solve_chunked(const Factor& F, vector<double>& B /* n x nrhs row-major */, int n, int nrhs) {
   const int nt = std::max(1, std::min(omp_get_max_threads(), (nrhs + 3) / 4));
   if (nt == 1) {
     solve_inplace(F, B.data(), nrhs);
@@ -555,6 +556,127 @@ static void solve_many(const Factor& F, vector<double>& B /* n x nrhs row-major 
     solve_inplace(F, X.data(), cw);
     for (int i = 0; i < n; ++i) std::memcpy(&B[(size_t)i * nrhs + c0], &X[(size_t)i * cw], sizeof(double) * cw);
   }
+}
+
+// Multi-RHS solve H X = B for a narrow block of right-hand sides (B row-major n x nrhs,
+// overwritten), all of them at once, so that the factor is streamed once per solve. In column-major terms a run of rows
+// of B is an nrhs x (rows) block, and each supernode's steps are right-side solves and GEMMs
+// on it. The supernode tree is walked level by level, a supernode costing more than a
+// thread's share of its level alone on parallel kernels, the others one per thread:
+//  - forward (L Y = B), by height from the leaves: a supernode subtracts its children's
+//    update rows that fall in its own columns and carries the others, solves
+//    Y_J <- Y_J L_JJ^{-T}, and hands W = (carried rows) + Y_J L_RJ^T to its parent;
+//  - backward (L^T X = Y), by depth from the roots: X_J <- (X_J - X_R L_RJ) L_JJ^{-1}, its
+//    rows X_R belonging to ancestors that are already final.
+// Each supernode's arithmetic is independent of the schedule.
+static void solve_tree(const Factor& F, vector<double>& B /* n x nrhs row-major */, int n, int nrhs) {
+  const int ns = F.nsn();
+  if (ns == 0 || nrhs <= 0 || n <= 0) return;
+  double* X = B.data();
+  vector<int> par(ns, -1);
+  vector<vector<int>> kids(ns);
+  for (int s = 0; s < ns; ++s)
+    if (!F.sn_rows[s].empty()) {
+      par[s] = F.sn_of[F.sn_rows[s][0]];
+      kids[par[s]].push_back(s);
+    }
+  vector<int> height(ns, 0), depth(ns, 0);
+  int nh = 0, nd = 0;
+  for (int s = 0; s < ns; ++s) {  // children come before parents
+    for (int c : kids[s]) height[s] = std::max(height[s], height[c] + 1);
+    nh = std::max(nh, height[s] + 1);
+  }
+  for (int s = ns - 1; s >= 0; --s) {
+    depth[s] = par[s] < 0 ? 0 : depth[par[s]] + 1;
+    nd = std::max(nd, depth[s] + 1);
+  }
+  vector<vector<int>> by_h(nh), by_d(nd);
+  for (int s = 0; s < ns; ++s) by_h[height[s]].push_back(s);
+  for (int s = ns - 1; s >= 0; --s) by_d[depth[s]].push_back(s);
+  const int nthr = std::max(1, omp_get_max_threads());
+  auto cost = [&](int s) {
+    const double nJ = 3.0 * (F.sn_first[s + 1] - F.sn_first[s]), nR = 3.0 * F.sn_rows[s].size();
+    return nJ * (nJ + 2.0 * nR) + nR;
+  };
+  // runs fn over the supernodes of one level: the costly ones alone, the rest in parallel
+  auto run_level = [&](vector<int> lv, auto&& fn) {
+    std::stable_sort(lv.begin(), lv.end(), [&](int a, int b2) { return cost(a) > cost(b2); });
+    double total = 0.0;
+    for (int q : lv) total += cost(q);
+    int nbig = 0;
+    while (nbig < (int)lv.size() && cost(lv[nbig]) > total / nthr) ++nbig;
+    for (int q = 0; q < nbig; ++q) fn(lv[q], 0);
+    if ((int)lv.size() - nbig >= 2 && nthr > 1 && !omp_in_parallel()) {
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthr)
+      for (int q = nbig; q < (int)lv.size(); ++q) fn(lv[q], omp_get_thread_num());
+    } else {
+      for (int q = nbig; q < (int)lv.size(); ++q) fn(lv[q], 0);
+    }
+  };
+  // forward
+  vector<RawVec> W(ns);  // update rows handed to the parent: [nR][nrhs]
+  vector<vector<int>> locs(nthr, vector<int>(F.nv, -1));
+  auto fwd = [&](int s, int t) {
+    vector<int>& loc = locs[t];
+    const int f = F.sn_first[s], l = F.sn_first[s + 1], nJ = 3 * (l - f);
+    const vector<int>& R = F.sn_rows[s];
+    const int nR = 3 * (int)R.size(), m = nJ + nR;
+    const double* L = F.L[s].data();
+    double* XJ = X + (size_t)3 * f * nrhs;
+    RawVec Ws((size_t)nR * nrhs);
+    std::memset(Ws.data(), 0, sizeof(double) * Ws.size());
+    for (size_t q = 0; q < R.size(); ++q) loc[R[q]] = (int)q;
+    for (int c : kids[s]) {
+      const vector<int>& Rc = F.sn_rows[c];
+      const double* Wc = W[c].data();
+      for (size_t qc = 0; qc < Rc.size(); ++qc) {
+        const int v = Rc[qc];
+        const double* src = Wc + (size_t)3 * qc * nrhs;
+        if (v < l) {
+          double* dst = X + (size_t)3 * v * nrhs;
+          for (int i = 0; i < 3 * nrhs; ++i) dst[i] -= src[i];
+        } else {
+          double* dst = Ws.data() + (size_t)3 * loc[v] * nrhs;
+          for (int i = 0; i < 3 * nrhs; ++i) dst[i] += src[i];
+        }
+      }
+      W[c] = RawVec();
+    }
+    for (int u : R) loc[u] = -1;
+    dense::trsm_rlt_wide(XJ, nrhs, nJ, nrhs, L, m);
+    if (nR > 0) {
+      dense::gemm(false, true, nrhs, nR, nJ, 1.0, XJ, nrhs, L + nJ, m, Ws.data(), nrhs);
+      W[s].swap(Ws);
+    }
+  };
+  for (int h = 0; h < nh; ++h) run_level(by_h[h], fwd);
+  // backward
+  vector<RawVec> XRs(nthr);
+  auto bwd = [&](int s, int t) {
+    const int f = F.sn_first[s], nJ = 3 * (F.sn_first[s + 1] - f);
+    const vector<int>& R = F.sn_rows[s];
+    const int nR = 3 * (int)R.size(), m = nJ + nR;
+    const double* L = F.L[s].data();
+    double* XJ = X + (size_t)3 * f * nrhs;
+    if (nR > 0) {
+      RawVec& XR = XRs[t];
+      XR.resize((size_t)nR * nrhs);
+      for (size_t q = 0; q < R.size(); ++q)
+        std::memcpy(XR.data() + (size_t)3 * q * nrhs, X + (size_t)3 * R[q] * nrhs, sizeof(double) * 3 * nrhs);
+      dense::gemm(false, false, nrhs, nJ, nR, -1.0, XR.data(), nrhs, L + nJ, m, XJ, nrhs);
+    }
+    dense::trsm_rln_wide(XJ, nrhs, nJ, nrhs, L, m);
+  };
+  for (int d = 0; d < nd; ++d) run_level(by_d[d], bwd);
+}
+
+// H X = B: narrow blocks (the inverse iteration's) by the tree pass, which streams the
+// factor once; wide ones (the pool rows) by per-thread column chunks.
+static void solve_many(const Factor& F, vector<double>& B /* n x nrhs row-major */, int n, int nrhs) {
+  if (nrhs >= 32 * std::max(1, omp_get_max_threads()))
+    solve_chunked(F, B, n, nrhs);
+  else
+    solve_tree(F, B, n, nrhs);
 }
 
 // Diagonal 3x3 blocks of H^{-1} by the Takahashi recurrences on the supernodal pattern
