@@ -1563,20 +1563,46 @@ jgs2_status precompute(Mesh* m, const jgs2_precompute_opts* o) {
   for (int t = 0; t < m->T; ++t) be[m->body[m->tets_c[4 * (size_t)t]]].push_back(t);
   vector<int> rep(nb, -1);
   vector<BodyResult> res(nb);
-  jgs2_status st = JGS2_OK;
-  std::string err;
-  for (int b = 0; b < nb && st == JGS2_OK; ++b) {
+  vector<int> todo;  // one body of each distinct shape
+  for (int b = 0; b < nb; ++b) {
     for (int c = 0; c < b; ++c)
       if (rep[c] == c && same_body(*m, bv[c], be[c], bv[b], be[b])) {
         rep[b] = c;
         break;
       }
-    if (rep[b] >= 0) continue;
-    rep[b] = b;
-    st = body_precompute(*m, bv[b], be[b], *o, res[b], err);
+    if (rep[b] < 0) {
+      rep[b] = b;
+      todo.push_back(b);
+    }
+  }
+  vector<jgs2_status> bst(nb, JGS2_OK);
+  vector<std::string> berr(nb);
+  // With host solves, bodies below kSmallBody vertices run side by side, one thread each
+  // (their own tree passes are too small to keep the threads busy), largest first; larger
+  // bodies then run one at a time on all threads. GPU solves keep one body at a time.
+  constexpr size_t kSmallBody = 20000;
+  vector<int> small, large;
+  for (int b : todo) (o->gpu == 0 && bv[b].size() < kSmallBody && omp_get_max_threads() > 1 ? small : large).push_back(b);
+  if (small.size() < 2) {  // a lone small body runs on all threads
+    large.insert(large.begin(), small.begin(), small.end());
+    small.clear();
+  }
+  std::stable_sort(small.begin(), small.end(), [&](int a, int b2) { return bv[a].size() > bv[b2].size(); });
+  if (!small.empty()) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int q = 0; q < (int)small.size(); ++q) {
+      omp_set_num_threads(1);  // nested regions of this body run on its own thread
+      const int b = small[q];
+      bst[b] = body_precompute(*m, bv[b], be[b], *o, res[b], berr[b]);
+    }
+  }
+  for (int b : large) {
+    bst[b] = body_precompute(*m, bv[b], be[b], *o, res[b], berr[b]);
+    if (bst[b] != JGS2_OK) break;
   }
   omp_set_num_threads(saved);
-  if (st != JGS2_OK) return fail(st, "jgs2_precompute: " + err);
+  for (int b : todo)  // the first failure in body order
+    if (bst[b] != JGS2_OK) return fail(bst[b], "jgs2_precompute: " + berr[b]);
   const int nc = o->n_cub;
   const size_t Vf = m->Vf;
   vector<int> e_int(Vf * nc, -1);
