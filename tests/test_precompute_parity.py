@@ -104,3 +104,28 @@ def test_precompute_gpu_option_range():
     with pytest.raises(p.JGS2Error):
         g.precompute(gpu=2)
     g.close()
+
+
+def test_batch_precompute_matches_each_scene_alone():
+    """A mesh of several scenes precomputes each body on its own: the bodies of a batch run
+    side by side (one thread each) and must give the cubature each scene gets alone: the
+    same element sets, and weights, U_bar rows and residuals equal to rounding (a scene of
+    one body runs it on all threads, which splits its pool solves into column chunks)."""
+    idx = [24, 35, 18, 8]  # four small seeded blobs (1-2k tets)
+    ss = [scenes.blob_scene(i) for i in idx]
+    g = p.Mesh.batch(ss)
+    g.precompute(n_cub=4)
+    e, w, u, r = g.precompute_export()
+    g.close()
+    v0 = t0 = 0  # the batch numbers vertices and tets scene after scene
+    for s in ss:
+        es, ws, us, rs = lib_precompute(s)
+        nv = len(s.X)
+        free = ~s.pinned.astype(bool)
+        eb = e[v0:v0 + nv][free]
+        assert np.array_equal(np.where(eb >= 0, eb - t0, -1), es[free])
+        assert np.allclose(w[v0:v0 + nv][free], ws[free], rtol=1e-9, atol=1e-12 * np.abs(ws).max())
+        assert np.max(np.abs(u[v0:v0 + nv][free] - us[free])) <= 1e-9 * np.abs(us).max()
+        assert np.allclose(r[v0:v0 + nv][free], rs[free], rtol=1e-7, atol=1e-12)
+        v0 += nv
+        t0 += len(s.tets)
