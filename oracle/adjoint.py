@@ -9,6 +9,9 @@ With L a function of x_{t+1} = x* and v_{t+1} = (x* - x_t)/h, and gbar = dL/dx* 
     dL/dE_e  = -sum_{a in e} lam_a . (V_e P(F_e) b_a) / E_e
                (P is linear in (mu, lam') and both are proportional to E at fixed nu)
 Dense FP64; small meshes only. No contact (the barrier is left out of the adjoint).
+
+Test infrastructure: only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and
+reference legs use this module; the CUDA path never imports it.
 """
 from __future__ import annotations
 

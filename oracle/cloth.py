@@ -29,6 +29,9 @@ Reading R26 (the paper names the materials but gives no formulas):
   kappa B'(d) n, Gauss-Newton block kappa B''(d) n n^T, and the same step limit
   |D_v| <= 0.45 min(r_c - dhat, d_min,v), r_c = 2 dhat, d_min,v the smallest wall distance
   below r_c. The line search evaluates the barrier exactly per trial.
+
+Test infrastructure: only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and
+reference legs use this module; the CUDA path never imports it.
 """
 from __future__ import annotations
 

@@ -30,6 +30,9 @@ Step truncation (reading R11): a surface vertex's step is scaled so that
 the candidate radius r_c that involves v. No candidate pair's distance can shrink by 90% or
 more within one sweep, and no pair outside r_c can come within dhat, so the candidate list
 at x^k holds every barrier term along the sweep's line-search segment.
+
+Test infrastructure: only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and
+reference legs use this module; the CUDA path never imports it.
 """
 from __future__ import annotations
 

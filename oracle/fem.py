@@ -9,6 +9,9 @@ formula; the form used here (reading R1) is the rest-stable one
 
 whose linearisation at F = I is linear elasticity with Lame parameters (mu, lam).
 Plain numpy, FP64, vectorised over elements only.
+
+Test infrastructure: only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and
+reference legs use this module; the CUDA path never imports it.
 """
 from __future__ import annotations
 

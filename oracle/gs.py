@@ -1,7 +1,8 @@
 """Gauss-Seidel parallelisation of JGS2 (Sec. 8.1), FP64, for the oracle.
 
-TEST INFRASTRUCTURE ONLY: tests/ alone import this module; the CUDA path has no GS mode
-yet and shares nothing with it.
+Test infrastructure: only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and
+reference legs use this module; the CUDA path never imports it. The CUDA Gauss-Seidel step
+(jgs2_step_gs) shares nothing with it.
 
 Sec. 8.1: the vertex sub-problems are grouped by a graph colouring so that no two
 vertices of a group share an element. A GS sweep solves the groups one after another,

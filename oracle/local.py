@@ -3,6 +3,9 @@
 Same definitions as sweep.direction, evaluated for a few sampled vertices using only
 the tets around them, so that full-size meshes (millions of tets) can be checked vertex
 by vertex. Plain loops over the handful of tets involved; FP64.
+
+Test infrastructure: only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and
+reference legs use this module; the CUDA path never imports it.
 """
 from __future__ import annotations
 

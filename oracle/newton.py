@@ -1,5 +1,9 @@
 """Full-space references: projected Newton (Sec. 8.3, Eq. newton_system) and the
-exact dynamic subspace of Secs. 4.1-4.2 used to check the optimality theorem."""
+exact dynamic subspace of Secs. 4.1-4.2 used to check the optimality theorem.
+
+Test infrastructure: only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and
+reference legs use this module; the CUDA path never imports it.
+"""
 from __future__ import annotations
 
 import numpy as np

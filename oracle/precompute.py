@@ -23,6 +23,9 @@
   in round r = draw(keyed(seed, l, r), eligible pool elements in ascending order, n_cand).
 
 Dense linear algebra (numpy) for the small meshes the tests use.
+
+Test infrastructure: only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and
+reference legs use this module; the CUDA path never imports it.
 """
 from __future__ import annotations
 

@@ -6,6 +6,9 @@ sides implement this one published generator independently so their draws coinci
 keyed(seed, a, b) derives a stream state from a seed and two integer keys by feeding the
 keys through two generator outputs; draws are `next() % n` (modulo bias accepted, it is
 part of the definition).
+
+Test infrastructure: only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and
+reference legs use this module; the CUDA path never imports it.
 """
 M64 = (1 << 64) - 1
 GAMMA = 0x9E3779B97F4A7C15

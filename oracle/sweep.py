@@ -24,6 +24,9 @@ check: the paper normalises a scene into a unit cube and stops when the position
 less than a tolerance between two consecutive iterations; read here as the 2-norm over all
 free DOFs, |x^k - x^{k-1}| <= dx_tol * L (k >= 1), L the normalising length (default: the
 largest extent of the rest positions' bounding box), tested after the residual test.
+
+Test infrastructure: only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and
+reference legs use this module; the CUDA path never imports it.
 """
 from __future__ import annotations
 
