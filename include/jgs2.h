@@ -246,11 +246,16 @@ jgs2_status jgs2_autotune(jgs2_mesh* mesh, double* x, double* v, const jgs2_step
  * work (host int32_t[4]). */
 jgs2_status jgs2_mesh_launch_config(const jgs2_mesh* mesh, int32_t precision, int32_t* config);
 
-/* Offline stage (Secs. 5-6), host FP64: factorises the rest Hessian H_bar = M/h^2 + K_bar
+/* Offline stage (Secs. 5-6), FP64 results: factorises the rest Hessian H_bar = M/h^2 + K_bar
  * of each distinct body once, computes A_i = (H_bar^{-1})_ii and the rows of
  * U_bar_i = H_bar^{-1} S_i^T A_i^{-1} (Eq. u) that the cubature needs, the lowest
  * eigenvectors of H_bar as training poses, and the greedy NNLS cubature sets
- * (Eq. cubature_weight), then uploads the packed per-vertex records. */
+ * (Eq. cubature_weight), then uploads the packed per-vertex records. The factorisation,
+ * selected inversion and NNLS run on the host on opts->n_threads OpenMP threads (0 = all
+ * cores, the OpenMP default; the caller's setting is restored on return); the multi-RHS solves run
+ * there too, or on the current device with opts->gpu = 1. With host solves, bodies under
+ * 20,000 vertices run side by side, one thread each. Synchronous; the mesh must not be
+ * stepped concurrently. */
 jgs2_status jgs2_precompute(jgs2_mesh* mesh, const jgs2_precompute_opts* opts);
 
 /* Loads cubature records computed elsewhere instead of running jgs2_precompute. */
