@@ -514,7 +514,9 @@ def run_jgs2(args, rank, world, local_rank):
         "contact_rebuilds_per_step": float(np.mean([q["rebuilds"] for q in reps])),
         "contact_pairs_last_step": {"candidates": int(reps[-1]["cand"]), "within_rc_last_sweep": int(reps[-1]["near"])},
         "precompute_s": round(t_pre, 2),
-        "precompute_solves": ("GPU (FP32 substitutions, FP64 refinement)" if args.precompute_gpu else "host FP64")
+        "precompute_solves": (("GPU (FP32 substitutions, FP64 refinement) for bodies of 20k vertices and "
+                               "more; smaller bodies, when several, host FP64 side by side")
+                              if args.precompute_gpu else "host FP64")
         if args.cubature == "precompute" else None,
         "e2e": {"value": e2e_ms, "unit": "ms/step", "h2d_bytes_per_step": int(xh.nbytes + vh.nbytes),
                 "d2h_bytes_per_step": int(xh.nbytes + vh.nbytes)},

@@ -105,7 +105,8 @@ typedef struct {
                         * 1e-14; a body whose refinement stalls above 1e-10, kappa(H_bar) being
                         * too large for FP32, takes the host's FP64 substitutions); 0 = host FP64
                         * substitutions. Factorisation, selected inversion and NNLS stay on
-                        * the host either way. Gauss-Seidel groups (gs = 1) solve on the host */
+                        * the host either way. Gauss-Seidel groups (gs = 1) solve on the host,
+                        * and so do small bodies run side by side (see jgs2_precompute) */
 } jgs2_precompute_opts;
 
 /* Cubature records produced elsewhere (e.g. by an independent implementation), in the
@@ -253,9 +254,10 @@ jgs2_status jgs2_mesh_launch_config(const jgs2_mesh* mesh, int32_t precision, in
  * (Eq. cubature_weight), then uploads the packed per-vertex records. The factorisation,
  * selected inversion and NNLS run on the host on opts->n_threads OpenMP threads (0 = all
  * cores, the OpenMP default; the caller's setting is restored on return); the multi-RHS solves run
- * there too, or on the current device with opts->gpu = 1. With host solves, bodies under
- * 20,000 vertices run side by side, one thread each. Synchronous; the mesh must not be
- * stepped concurrently. */
+ * there too, or on the current device with opts->gpu = 1. A mesh with several bodies under
+ * 20,000 vertices (a batch of small scenes) runs those side by side on the host, one thread
+ * each and with host solves whatever opts->gpu says; the larger bodies, and a lone small
+ * one, run one at a time. Synchronous; the mesh must not be stepped concurrently. */
 jgs2_status jgs2_precompute(jgs2_mesh* mesh, const jgs2_precompute_opts* opts);
 
 /* Loads cubature records computed elsewhere instead of running jgs2_precompute. */

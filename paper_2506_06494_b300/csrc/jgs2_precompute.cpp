@@ -1577,23 +1577,27 @@ jgs2_status precompute(Mesh* m, const jgs2_precompute_opts* o) {
   }
   vector<jgs2_status> bst(nb, JGS2_OK);
   vector<std::string> berr(nb);
-  // With host solves, bodies below kSmallBody vertices run side by side, one thread each
-  // (their own tree passes are too small to keep the threads busy), largest first; larger
-  // bodies then run one at a time on all threads. GPU solves keep one body at a time.
+  // Bodies below kSmallBody vertices, when there are several, run side by side on the host,
+  // one thread each, largest first: their own tree passes are too small to keep the threads
+  // busy, and their GPU solves too short to hide the level schedule's launch latency. Larger
+  // bodies (and a lone small one) then run one at a time on all threads, with GPU solves if
+  // asked for.
   constexpr size_t kSmallBody = 20000;
   vector<int> small, large;
-  for (int b : todo) (o->gpu == 0 && bv[b].size() < kSmallBody && omp_get_max_threads() > 1 ? small : large).push_back(b);
+  for (int b : todo) (bv[b].size() < kSmallBody && omp_get_max_threads() > 1 ? small : large).push_back(b);
   if (small.size() < 2) {  // a lone small body runs on all threads
     large.insert(large.begin(), small.begin(), small.end());
     small.clear();
   }
   std::stable_sort(small.begin(), small.end(), [&](int a, int b2) { return bv[a].size() > bv[b2].size(); });
   if (!small.empty()) {
+    jgs2_precompute_opts oh = *o;
+    oh.gpu = 0;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int q = 0; q < (int)small.size(); ++q) {
       omp_set_num_threads(1);  // nested regions of this body run on its own thread
       const int b = small[q];
-      bst[b] = body_precompute(*m, bv[b], be[b], *o, res[b], berr[b]);
+      bst[b] = body_precompute(*m, bv[b], be[b], oh, res[b], berr[b]);
     }
   }
   for (int b : large) {
