@@ -5,7 +5,7 @@
 //      element blocks are V_e (mu (b_a.b_c) I + mu b_c b_a^T + lam b_a b_c^T)).
 //   2. Nested-dissection order (recursive coordinate bisection with one-sided vertex
 //      separators), elimination tree, fundamental supernodes, multifrontal Cholesky
-//      H_bar = L L^T with dense fronts (Sec. 6: "we only factorize H_bar once").
+//      H_bar = L L^T with dense fronts (Sec. 6: one factorisation serves every solve).
 //   3. Training poses: the n_train lowest eigenpairs of H_bar by block inverse iteration
 //      with Rayleigh-Ritz (Sec. 5, last paragraph).
 //   4. Rows of H_bar^{-1} at the vertices of the body's cubature pool, by multi-RHS

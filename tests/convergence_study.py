@@ -25,9 +25,9 @@ the iteration is globalised:
   training        n_train lowest eigenvectors (4, 8, 20), n_cub elements (4, 6), candidates
                   from a 256-element pool or from the whole body (the paper's draw)
   globalisation   "global" Armijo on E every sweep (reading R17); "global/k" only every k-th
-                  sweep (Sec. 3: global line search "should not be frequently used");
-                  "local" backtracking per vertex on its own sub-problem energy (Sec. 9:
-                  line search "at each sub-problem in parallel"); "none" the plain sweep
+                  sweep (Sec. 3 advises using the global line search sparingly);
+                  "local" backtracking per vertex on its own sub-problem energy (Sec. 9: a
+                  line search per sub-problem, all in parallel); "none" the plain sweep
 
 Two measurements:
   linear    at the rest state (R = I) the sweep is the linear iteration
