@@ -142,7 +142,7 @@ def sweep_bytes(V_f, T, n_cub, fp_bytes=4):
     return T * per_tet + V_f * per_vertex
 
 
-def survey_sweep_bytes(V_f, T, n_cub, fp_bytes=4):
+def scope_sweep_bytes(V_f, T, n_cub, fp_bytes=4):
     """The per-unit byte model of the hot-path scope (FP32, each datum once): 76 B per tet
     (corner ids 16, B 36, V_e 4, E 4, incidence 16) and, per free vertex, x read and
     written, z and m (40 B), R written (36), g/H written and read (72) and the cubature
@@ -529,7 +529,7 @@ def run_jgs2(args, rank, world, local_rank):
     sw_tot = max(int(sweeps.sum()), 1)
     ms_sweep = ms_total / sw_tot
     for key, b in (("sweep_roofline", sweep_bytes(Vf, T, n_cub, fpb)),
-                   ("sweep_roofline_scope_model", survey_sweep_bytes(Vf, T, n_cub, fpb))):
+                   ("sweep_roofline_scope_model", scope_sweep_bytes(Vf, T, n_cub, fpb))):
         gbs = b / (ms_sweep * 1e-3) / 1e9
         out[key] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(gbs / hbm, 4), "bytes_per_sweep": b, "ms_per_sweep": round(ms_sweep, 5),

@@ -33,9 +33,9 @@ def test_scope_byte_model():
     """The hot-path scope's per-unit figures: 76 B per tet and 756 B per free vertex in FP32
     (743 MB per sweep at 3.47M tets)."""
     b = _bench()
-    assert b.survey_sweep_bytes(0, 1, 4) == 76
-    assert b.survey_sweep_bytes(1, 0, 4) == 756
-    assert abs(b.survey_sweep_bytes(634_130, 3_471_360, 4) - 743e6) < 1e6
+    assert b.scope_sweep_bytes(0, 1, 4) == 76
+    assert b.scope_sweep_bytes(1, 0, 4) == 756
+    assert abs(b.scope_sweep_bytes(634_130, 3_471_360, 4) - 743e6) < 1e6
 
 
 def test_makespan():
