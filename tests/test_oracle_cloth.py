@@ -194,3 +194,19 @@ def test_cloth_on_the_floor_stays_above_it_and_converges():
     free = c.free
     assert np.all(r.x[free, 2] >= r0.x[free, 2] - 1e-12)
     assert np.any(r.x[free, 2] > r0.x[free, 2] + 1e-9)
+
+
+def test_lumped_mass_and_free_fall():
+    """The cloth's lumped masses sum to rho t times its area (a 0.5 m square, 200 kg/m^3,
+    5e-4 m thick: 0.025 kg), and an unpinned cloth moving rigidly steps to the
+    implicit-Euler free-fall position x_t + h v_t + h^2 g (a translation changes neither
+    the membrane strain nor the bending vectors)."""
+    s = scenes.cloth_scene(n=6)
+    c = cloth.Cloth(s.X, s.tris, 1e-3, s.poisson, s.thickness, s.density, 1e-9)
+    assert np.sum(c.mass) == pytest.approx(s.density * s.thickness * 0.5 ** 2, rel=1e-12)
+    assert np.sum(c.area) == pytest.approx(0.5 ** 2, rel=1e-12)
+    h = s.dt
+    v0 = np.tile([0.2, 0.1, -0.3], (len(s.X), 1))
+    r = cloth.step(c, s.X, v0, h, s.gravity, rel_tol=1e-12, max_sweeps=400)
+    want = s.X + h * v0 + h * h * np.asarray(s.gravity)
+    assert np.abs(r.x - want).max() <= 1e-9 * np.abs(h * v0).max()

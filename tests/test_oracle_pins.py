@@ -579,3 +579,20 @@ def test_coupled_local_terms_match_co_translation():
     m2.enable_contact(np.zeros((0, 4)), 1e-3, 1e4)
     g2 = fem.vertex_gradient(m2, x, z, h)
     assert sweep.coupled_local_terms(m2, x, g2, fem.vertex_diag_blocks(m2, x, h)) == {}
+
+
+def test_lumped_mass_and_free_fall(cube):
+    """Sec. 3's inertia term: the lumped masses sum to rho times the mesh volume (the cube is
+    0.1 m on a side at 1000 kg/m^3: 1 kg), and an unpinned body moving rigidly steps to the
+    implicit-Euler free-fall position x_t + h v_t + h^2 g (a translation leaves F = I, so
+    that is the minimiser whatever the stiffness; a soft body lets the plain sweep reach it
+    quickly)."""
+    s, m = cube
+    assert np.sum(m.mass) == pytest.approx(1000.0 * 0.1 ** 3, rel=1e-12)
+    h = s.dt
+    for E in (1e-6, 1.0):
+        body = fem.Mesh(s.X, s.tets, np.full(len(s.tets), E), s.poisson, s.density, np.zeros(len(s.X), np.uint8))
+        v0 = np.tile([0.3, -0.1, 0.2], (len(s.X), 1))
+        r = sweep.step(body, s.X, v0, h, s.gravity, None, rel_tol=1e-12, max_sweeps=400)
+        want = s.X + h * v0 + h * h * np.asarray(s.gravity)
+        assert np.abs(r.x - want).max() <= 1e-9 * np.abs(h * v0).max(), E
