@@ -134,3 +134,23 @@ def test_batch_precompute_matches_each_scene_alone():
         assert np.allclose(r[v0:v0 + nv][free], rs[free], rtol=1e-7, atol=1e-12)
         v0 += nv
         t0 += len(s.tets)
+
+
+def test_precompute_does_not_depend_on_the_thread_count():
+    """The host precompute's tree passes run level by level in parallel; a supernode's
+    arithmetic does not depend on the schedule, so one thread and several give the same
+    cubature sets, and values equal to rounding (the pool solves split their columns into
+    one chunk per thread)."""
+    s = scenes.small_beam_scene(nvx=21, nvy=6, nvz=6, E=1e7)  # 756 vertices, a deeper tree
+    outs = []
+    for nt in (1, 4):
+        g = p.Mesh.from_scene(s)
+        g.precompute(n_cub=4, n_threads=nt)
+        outs.append(g.precompute_export())
+        g.close()
+    (e1, w1, u1, r1), (e4, w4, u4, r4) = outs
+    free = ~s.pinned.astype(bool)
+    assert np.array_equal(e1, e4)
+    assert np.allclose(w1[free], w4[free], rtol=1e-9, atol=1e-12 * np.abs(w1).max())
+    assert np.max(np.abs(u1 - u4)) <= 1e-10 * np.abs(u1).max()
+    assert np.allclose(r1[free], r4[free], rtol=1e-8, atol=1e-14)
