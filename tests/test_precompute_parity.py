@@ -154,3 +154,22 @@ def test_precompute_does_not_depend_on_the_thread_count():
     assert np.allclose(w1[free], w4[free], rtol=1e-9, atol=1e-12 * np.abs(w1).max())
     assert np.max(np.abs(u1 - u4)) <= 1e-10 * np.abs(u1).max()
     assert np.allclose(r1[free], r4[free], rtol=1e-8, atol=1e-14)
+
+
+@pytest.mark.parametrize("name", ["cube", "beam"])
+def test_cubature_import_export_round_trip(name):
+    """jgs2_precompute_import takes records in the caller's vertex and tet order and stores
+    them in the library's (Morton-ordered vertices, sorted tets); the export maps them back.
+    The round trip is exact for free vertices; pinned vertices export empty slots."""
+    s = scenes.cube_scene() if name == "cube" else scenes.small_beam_scene(nvx=21, nvy=6, nvz=6, E=1e7)
+    m = fem.Mesh(s.X, s.tets, s.youngs, s.poisson, s.density, s.pinned)
+    cub = precompute.train_cubature(m, s.dt)
+    g = p.Mesh.from_scene(s)
+    g.precompute_import(cub.elem, cub.weight, cub.ubar)
+    e, w, u, _ = g.precompute_export()
+    g.close()
+    free = ~s.pinned.astype(bool)
+    assert np.array_equal(e[free], cub.elem[free])
+    assert np.array_equal(w[free], cub.weight[free])
+    assert np.array_equal(u[free], cub.ubar[free])
+    assert np.all(e[~free] == -1) and np.all(w[~free] == 0.0)
