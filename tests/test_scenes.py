@@ -2,6 +2,7 @@
 scenes are replaced by): sizes, pinning, materials, velocities, placement and, for the
 blobs, the tet-count target. The seeds are fixed, so these are exact."""
 import numpy as np
+import pytest
 
 import scenes
 
@@ -52,3 +53,38 @@ def test_blobs_hit_their_tet_targets():
         pin = s.pinned.astype(bool)
         assert pin.any() and np.all(np.isclose(s.X[pin, 2], s.X[:, 2].min()))
         assert 1e4 <= s.youngs[0] <= 1e7 and 0.3 <= s.poisson[0] <= 0.48
+
+
+def test_contact_scenes():
+    """The small contact scenes: free blocks inside the box's walls, within or just beyond
+    the barrier's reach of the floor, with the stated motions."""
+    d = scenes.drop_scene()
+    assert len(d.X) == 64 and d.pinned.sum() == 0 and d.contact == 1
+    assert d.X[:, 2].min() == pytest.approx(5e-4) and np.all(d.v0[:, 2] == -0.3)
+    s = scenes.slide_scene()
+    assert len(s.X) == 27 and s.X[:, 2].min() == pytest.approx(9.8e-4) and s.X[:, 2].min() < s.dhat
+    assert np.all(s.v0[:, 0] == 0.5) and np.all(s.v0[:, 1] == pytest.approx(0.2))
+    k = scenes.stack_scene()
+    n = len(k.X) // 2
+    assert len(k.X) == 54 and np.all(k.v0[:n] == 0.0) and np.all(k.v0[n:, 2] == -0.3)
+    # the lower block rests 0.8 dhat above the floor, the upper one starts 0.7 mm above it
+    assert k.X[:n, 2].min() == pytest.approx(0.8 * k.dhat)
+    assert k.X[n:, 2].min() - k.X[:n, 2].max() == pytest.approx(0.7e-3)
+    for sc in (d, s, k):
+        P = sc.planes
+        assert np.allclose(np.linalg.norm(P[:, :3], axis=1), 1.0)
+        assert np.all(sc.X @ P[:, :3].T - P[:, 3] > 0)  # strictly inside every wall
+
+
+def test_cloths():
+    """Cloth grids: n x n vertices, 2 (n - 1)^2 triangles of equal area on the square, two
+    adjacent corners held; the floor cloth is free and just above its wall."""
+    c = scenes.cloth_scene(n=11)
+    assert len(c.X) == 121 and len(c.tris) == 200
+    e1 = c.X[c.tris[:, 1]] - c.X[c.tris[:, 0]]
+    e2 = c.X[c.tris[:, 2]] - c.X[c.tris[:, 0]]
+    area = 0.5 * np.linalg.norm(np.cross(e1, e2), axis=1)
+    assert np.allclose(area, 0.5 * 0.05 ** 2) and area.sum() == pytest.approx(0.25)
+    assert list(np.nonzero(c.pinned)[0]) == [0, 110]
+    f = scenes.cloth_floor_scene()
+    assert f.pinned.sum() == 0 and f.X[:, 2].min() == pytest.approx(6e-4) and f.X[:, 2].min() < f.dhat
